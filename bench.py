@@ -1,0 +1,375 @@
+"""Benchmark: ms per stereo frame of gs_render_stereo (the method) beside the
+same-GPU sequential two-pass render, on a synthetic 500k-surfel object scene
+(SH degree 3) at 1600x1200, eight head poses on a 30-degree arc.
+
+One step = one stereo frame through the C ABI with the scene resident in HBM.
+L2 is flushed (a 256 MB write) before every timed step; each step is timed with
+CUDA events on the rendering stream. `--impl reference` times the FP64 oracle on
+the host cores instead (a bounded sample per step, extrapolated to a frame).
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run every rank renders its own frames (replicas, no
+collective on the data path) and rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ms/stereo frame vs same-GPU two-pass render at stated PSNR; plain vs learned"
+WORKLOAD = "object-centric 500k surfels (450k Gaussian cluster + 50k ground plane), SH3, 1600x1200, f=1600, 0.064 m baseline, 8 poses on a 30 deg arc"
+# PSNR the method must reach against the full render so that the loss against a
+# capture whose full render scores 28.83 dB (DTU two-pass, Table 2) is <= 1.3 dB:
+# 10 log10(1 + MSE/s^2) <= 1.3  <=>  PSNR_vs_full >= 28.83 - 10 log10(10^0.13 - 1)
+PSNR_FLOOR_DTU = 28.83
+PSNR_GATE = PSNR_FLOOR_DTU - 10 * math.log10(10 ** 0.13 - 1)
+# FP32 lane operations of one tiled (pixel, surfel) evaluation and the extra
+# ones of a contribution (roofline of the blend kernel)
+OPS_EVAL, OPS_CONTRIB = 19, 12
+SM_COUNT, FP32_LANES_PER_SM = 152, 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=16)
+    ap.add_argument("--warmup", type=int, default=4)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=500_000, help="surfels (default: the 500k workload)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-once", action="store_true",
+                    help="for profilers: one warm-up then one stereo and one two-pass frame, no timing")
+    return ap.parse_args()
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+
+def oracle_sample(scene, cam, pose, k, win=48):
+    """One bounded oracle sample: the per-pixel render of a win x win window of
+    the dominant eye plus the fixed per-frame preparation, timed on the host."""
+    import oracle
+    rng = np.random.default_rng(100 + k)
+    x0 = int(rng.integers(cam.width // 4, 3 * cam.width // 4 - win))
+    y0 = int(rng.integers(cam.height // 4, 3 * cam.height // 4 - win))
+    t0 = time.perf_counter()
+    oracle.render(scene, pose, cam, window=(x0, y0, 4, 4))
+    t_small = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(scene, pose, cam, window=(x0, y0, win, win))
+    t_big = time.perf_counter() - t0
+    per_px = max(t_big - t_small, 1e-9) / (win * win - 16)
+    prep = max(t_small - 16 * per_px, 0.0)
+    return prep, per_px, t_small + t_big
+
+
+def oracle_frame_ms(prep, per_px, npix, roi_frac):
+    # dominant eye: preparation + every pixel; affiliated eye: preparation + the
+    # ROI pixels (reprojection, gaps and components are per-pixel and cheap)
+    return 1e3 * (2 * prep + per_px * npix * (1.0 + roi_frac))
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2609_30741_gb300 import synth
+    scene, cam, dom, aff = synth.workload_object(n=args.n)
+    poses = synth.arc_poses()
+    npix = cam.width * cam.height
+    roi_frac = 0.12  # ROI tile share of the affiliated eye on this workload
+    vals = []
+    t_all = 0.0
+    for k in range(args.warmup + args.steps):
+        d, _ = synth.eye_pair(poses[k % len(poses)])
+        prep, per_px, t = oracle_sample(scene, cam, d, k)
+        t_all += t
+        if k >= args.warmup:
+            vals.append(oracle_frame_ms(prep, per_px, npix, roi_frac))
+    v = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": "per step: oracle render of a 48x48 dominant-eye window plus the per-frame "
+                                       "surfel preparation, extrapolated to both eyes (dominant frame + ROI share)"},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def psnr(a, b):
+    import torch
+    mse = torch.mean((a - b) ** 2).item()
+    return 10 * math.log10(1.0 / max(mse, 1e-20))
+
+
+def run_ours(args):
+    import torch
+    ws_, rank, local = dist_info()
+    if ws_ > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2609_30741_gb300 import build
+    build.build()
+    from paper_2609_30741_gb300 import gs, synth
+
+    scene, cam, _, _ = synth.workload_object(n=args.n)
+    poses = [synth.eye_pair(p) for p in synth.arc_poses()]
+    # replicas: rank r renders poses r, r + N, ... (independent frames)
+    poses = poses[rank % len(poses):] + poses[: rank % len(poses)]
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 27, device=dev)
+    ds = gs.DeviceScene(scene, device=dev)
+    out = ctx.alloc_outputs(cam)
+    out2 = ctx.alloc_outputs(cam, with_cls=False)
+    roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def stereo(k):
+        d, a = poses[k % len(poses)]
+        ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+
+    def two_pass(k):
+        d, a = poses[k % len(poses)]
+        ctx.render_two_pass(ds, d, a, cam, out=out2)
+
+    if args.profile_once:
+        for k in range(2):
+            stereo(0)
+            two_pass(0)
+        ctx.check_ok()
+        torch.cuda.synchronize(dev)
+        print(json.dumps({"profile_once": "ok", "launches_per_stereo_and_two_pass": gs.kernel_launches() // 2}))
+        return
+
+    # quality and work counts (untimed): every pose once
+    ctx.set_counting(True)
+    ps, roi_fracs, pairs_eval, pairs_contrib = [], [], [], []
+    for k in range(len(poses)):
+        stereo(k)
+        e, c = ctx.pair_counts()
+        pairs_eval.append(e[0])
+        pairs_contrib.append(c[0])
+        cls = out["cls_aff"].clone()
+        two_pass(k)
+        ctx.check_ok()
+        ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
+        roi_fracs.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
+    ctx.set_counting(False)
+
+    def timed(fn, steps, warmup, profile=False):
+        for k in range(warmup):
+            fn(k)
+        ctx.check_ok()
+        ctx.set_profiling(profile)
+        times, stages = [], []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if ws_ > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush.fill_(k & 255)  # evict L2 between steps
+            ev[k][0].record(stream)
+            fn(warmup + k)
+            ev[k][1].record(stream)
+            if profile:
+                stages.append(ctx.stage_times())
+        torch.cuda.synchronize(dev)
+        if ws_ > 1:
+            torch.distributed.barrier()
+        ctx.set_profiling(False)
+        times = [a.elapsed_time(b) for a, b in ev]
+        ctx.check_ok()
+        return float(np.mean(times)), times, stages
+
+    with ClockSampler(local) as clk:
+        l0 = gs.kernel_launches()
+        ms_stereo, t_stereo, _ = timed(stereo, args.steps, args.warmup)
+        launches_stereo = (gs.kernel_launches() - l0) * args.steps // (args.steps + args.warmup)
+        ms_two, t_two, _ = timed(two_pass, args.steps, args.warmup)
+    clocks = clk.summary()
+    # per-stage times (events at the stage boundaries; a separate pass)
+    _, _, st_stereo = timed(stereo, len(poses), 1, profile=True)
+    _, _, st_two = timed(two_pass, len(poses), 1, profile=True)
+    st_stereo = np.mean(np.array(st_stereo), 0).tolist()
+    st_two = np.mean(np.array(st_two), 0).tolist()
+
+    # end to end through the public call with host buffers: pose structs in,
+    # both eyes' images out to pinned host memory, inside the timed region
+    H, W = cam.height, cam.width
+    host_out = torch.empty(2, 3, H, W, dtype=torch.float32, pin_memory=True)
+    h2d = 2 * (12 * 8) + 4 * 8 + 8  # two poses (R, t doubles) + intrinsics, per call
+    d2h = host_out.numel() * 4
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(k & 255)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        stereo(k)
+        host_out[0].copy_(out["rgb_dom"], non_blocking=True)
+        host_out[1].copy_(out["rgb_aff"], non_blocking=True)
+        torch.cuda.synchronize(dev)
+        if k >= args.warmup:
+            e2e_t.append(1e3 * (time.perf_counter() - t0))
+    e2e_ms = float(np.mean(e2e_t))
+
+    # replicas: whole-job ms per frame = max rank time / frames of all ranks
+    ms_job = ms_stereo
+    if ws_ > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_stereo * args.steps], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_job = t.item() / (args.steps * ws_)
+
+    pk, pk_kind = peaks()
+    sm_mhz_peak = float(pk.get("sm_max_mhz", 2070.0))
+    blend_ms = st_stereo[2]
+    ops = OPS_EVAL * float(np.mean(pairs_eval)) + OPS_CONTRIB * float(np.mean(pairs_contrib))
+    achieved = ops / (blend_ms * 1e-3) / 1e9
+    peak_gops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz_peak * 1e6 / 1e9
+    prof_traffic = None
+    pf = os.path.join(ROOT, "profiles", "blend_traffic.json")
+    if os.path.exists(pf):
+        prof_traffic = json.load(open(pf)).get("bytes_per_launch")
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            prep, per_px, t = oracle_sample(scene, cam, poses[0][0], 0)
+            cpu = {"value": oracle_frame_ms(prep, per_px, W * H, float(np.mean(roi_fracs))), "unit": "ms",
+                   "cores": oracle.num_threads(), "kind": "oracle",
+                   "sample": f"oracle render of a 48x48 dominant-eye window + per-frame surfel preparation "
+                             f"({t:.1f} s of CPU work), extrapolated to the dominant frame plus the measured "
+                             f"ROI share of the affiliated eye"}
+        except Exception as ex:  # the CPU baseline is reported, not required
+            cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
+
+    line = {
+        "metric": METRIC, "value": ms_job, "unit": "ms", "n_gpus": ws_, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_stereo, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "surfels": scene.n, "width": W, "height": H, "gap_thresh": 2,
+                   "margin": 32, "samples_per_edge": 32, "enable_center": 1, "repair": "plain",
+                   "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{ws_}"},
+        "two_pass_ms": ms_two, "speedup_vs_two_pass": ms_two / ms_stereo, "fps": 1e3 / ms_job,
+        "psnr_aff_vs_full_db": float(np.mean(ps)), "psnr_gate_db": PSNR_GATE,
+        "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
+        "stage_ms_stereo": dict(zip(["preprocess", "bin_dom", "blend_dom", "warp_edge_gaps", "centre_rois",
+                                     "bin_roi", "blend_roi", "outputs"], st_stereo)),
+        "stage_ms_two_pass": dict(zip(["preprocess", "bin_dom", "blend_dom", "bin_aff", "blend_aff"], st_two)),
+        "clocks": clocks,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches_stereo),
+        "roofline": {"bound": "alu", "kernel": "blend (dominant eye)", "achieved": achieved, "peak": peak_gops,
+                     "unit": "Gop/s", "frac": achieved / peak_gops, "traffic": prof_traffic,
+                     "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz_peak:.0f} MHz ({pk_kind} max clock)",
+                     "ops_per_launch": ops, "launch_ms": blend_ms},
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws_ > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,206 @@
+/*
+ * gs.h - C ABI of a GB300 (sm_103a) renderer for binocular 2D Gaussian
+ * splatting by reprojection and selective patching (Zhu & Zhou, "From Mono to
+ * Stereo: Accelerating Binocular Gaussian Splatting via Reprojection and
+ * Selective Patching").
+ *
+ * The library renders the dominant eye in full (Sec. 3.1 Stage 1), warps it to
+ * the affiliated eye with the depth proxy (Stage 2, Eq. 3-5), sorts the holes
+ * into interpolated gaps and regions of interest (Stage 3, Sec. 3.5) and
+ * re-rasterises only the tiles of those regions (Stage 4). Every stage runs in
+ * this library's CUDA kernels on the caller's stream.
+ *
+ * Conventions
+ *   - All scene and image pointers are DEVICE pointers owned by the caller; the
+ *     library never frees them. Host structs (poses, intrinsics, parameters) are
+ *     read during the call only.
+ *   - Scene arrays, float32, structure of arrays:
+ *       pos[n][4] surfel centre p_k (x, y, z, unused pad), 16-byte aligned
+ *       quat[n][4] rotation (w, x, y, z), any non-zero norm (Sec. 3.3, Eq. 1)
+ *       scale[n][2] in-plane scales (s_u, s_v) (Eq. 1)
+ *       opacity[n]
+ *       sh[n][(sh_degree+1)^2][3] real SH colour coefficients, degree 0..3
+ *   - Poses are camera-to-world, double precision: P_world = R X_cam + t with
+ *     R row-major (Eq. 4). Camera axes: x right, y down, z forward.
+ *   - Intrinsics: pinhole K = [[fx,0,cx],[0,fy,cy],[0,0,1]] (Eq. 3); pixel
+ *     centres at integer coordinates, so a centred principal point is
+ *     ((W-1)/2, (H-1)/2). Both eyes share the intrinsics.
+ *   - Images are planar float32: rgb[3][H][W], depth[H][W], trans[H][W].
+ *     depth is the unnormalised depth proxy D = sum_i d_i w_i with
+ *     w_i = alpha_i T_i (Stage 1); trans is the final transmittance T.
+ *   - Calls are asynchronous on the context's stream. A call returns GS_OK once
+ *     its kernels are enqueued; errors found on the device (an instance buffer
+ *     too small, a bounded wait that ran out) are recorded in a device status
+ *     word that gs_context_check() reads back.
+ *
+ * Rendering rule (the 2DGS rasterizer conventions; the paper does not restate
+ * them): alpha = min(0.99, o * Ghat) with Ghat = max(G(u,v), exp(-|x-c|^2))
+ * (Eq. 2 plus the 2DGS low-pass term); contributions with alpha < 1/255 are
+ * skipped; a pixel stops before the contribution that would bring T below
+ * 1e-4; surfels are ordered by their float32 camera depth, ties by index.
+ * A surfel is culled when its quaternion is zero, 255 o < 1, its centre is
+ * within 0.2 m of the camera plane, or its support square reaches that plane.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GS_OK = 0,
+  GS_ERR_BAD_ARG = 1,   /* a NULL pointer, a size out of the context's limits, ... */
+  GS_ERR_CAPACITY = 2,  /* a device buffer was too small (instances, ROI rectangles) */
+  GS_ERR_TIMEOUT = 3,   /* a bounded device loop gave up; results are incomplete */
+  GS_ERR_CUDA = 4,      /* a CUDA runtime call failed */
+  GS_ERR_WORKSPACE = 5, /* the workspace is smaller than gs_workspace_size() asks */
+  GS_ERR_NOT_LOADED = 6 /* no repair network has been loaded */
+} gs_status;
+
+typedef struct gs_context gs_context;
+
+typedef struct {
+  const float *pos, *quat, *scale, *opacity, *sh;
+  int n;
+  int sh_degree;
+} gs_scene;
+
+typedef struct {
+  double R[9];
+  double t[3];
+} gs_pose;
+
+typedef struct {
+  double fx, fy, cx, cy;
+  int width, height;
+} gs_intrinsics;
+
+/* Adaptive ROI generator settings (Sec. 3.5). */
+typedef struct {
+  int margin;           /* m in Eq. 7-8 and Step 2; the paper fixes 32 */
+  int samples_per_edge; /* N boundary samples per image edge (>= 2) */
+  int enable_center;    /* Step 2 (centre ROIs) on/off, chosen before rendering */
+  int depth_mode;       /* 0: d_min/d_max = per-frame range of the normalised depth
+                           D/(1-T) over pixels with coverage 1-T >= 0.5; 1: fixed */
+  float d_min, d_max;   /* the two depth hypotheses when depth_mode = 1 */
+  int repair_mode;      /* 0: plain interpolation + ROI re-render; 1: learned repair
+                           in BF16; 2: learned repair in FP8 (needs gs_repair_load) */
+  float gate_tau;       /* learned repair: a tile uses the network fill when
+                           sigmoid(gate logit) >= gate_tau, else the plain path */
+} gs_roi_params;
+
+/* Outputs of the stereo and two-pass calls (device pointers, caller-owned). */
+typedef struct {
+  float *rgb_dom, *depth_dom, *trans_dom; /* dominant eye, [3][H][W], [H][W], [H][W] */
+  float *rgb_aff;                         /* affiliated eye, [3][H][W] */
+  uint8_t *cls_aff;   /* optional [H][W] class bits: 1 hole after the warp, 2 gap
+                         (interpolated), 4 centre hole, 8 inside an edge strip,
+                         16 re-rendered tile, 32 filled by the repair network */
+  int32_t *roi_rects; /* optional [max_rects][4] centre ROIs x0, y0, x1, y1 (half-open
+                         pixels, tile aligned), in the order of each component's
+                         smallest linear pixel index */
+  int32_t *roi_count; /* optional [1]: number of centre components found */
+  int32_t *edge_widths; /* optional [4]: left, right, top, bottom widths (Eq. 7-8) */
+} gs_outputs;
+
+/* Upper bounds a context is sized for. */
+typedef struct {
+  int max_surfels;
+  int max_width, max_height;
+  int64_t max_instances; /* (surfel, tile) pairs per eye; < 2^31 */
+  int max_rects;         /* centre ROI rectangles */
+  int keep_intermediates;/* 1: also store per-surfel float bounds for inspection */
+} gs_limits;
+
+/* Bytes of device workspace a context with these limits needs. */
+gs_status gs_workspace_size(const gs_limits *lim, size_t *bytes);
+
+/* Creates a context on the current device. `workspace` is a caller-owned device
+ * allocation of at least gs_workspace_size() bytes (256-byte aligned) that the
+ * context uses for all scratch; the context allocates no device memory itself.
+ * `stream` is a cudaStream_t (NULL = the legacy default stream). */
+gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *workspace,
+                            size_t workspace_bytes, void *stream);
+gs_status gs_context_destroy(gs_context *ctx);
+gs_status gs_context_set_stream(gs_context *ctx, void *stream);
+
+/* Synchronises the context's stream, returns the device status word (0 = no
+ * error, else a GS_ERR_* code) in *device_status and clears it. */
+gs_status gs_context_check(gs_context *ctx, int *device_status);
+
+/* Full render of one eye (Sec. 3.1 Stage 1): RGB, depth proxy and transmittance
+ * from the same blending weights. bg: host float[3] background or NULL (black). */
+gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *pose,
+                         const gs_intrinsics *intr, const float *bg, float *rgb, float *depth,
+                         float *trans);
+
+/* The method (Sec. 3.1-3.5, the pipeline of Sec. 4.3): full dominant render,
+ * forward warp to the affiliated eye with a depth test, edge ROIs (Eq. 6-8),
+ * gaps of at most gap_thresh pixels interpolated, centre ROIs (optional), and
+ * re-rasterisation of the ROI tiles only. Black background. */
+gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                           const gs_pose *pose_aff, const gs_intrinsics *intr, int gap_thresh,
+                           const gs_roi_params *roi, const gs_outputs *out);
+
+/* The sequential two-pass reference of Sec. 4.3: full dominant render, then a
+ * full affiliated render, built from the same kernels. Black background. */
+gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                             const gs_pose *pose_aff, const gs_intrinsics *intr,
+                             const gs_outputs *out);
+
+/* Intermediate buffers of the last call, for inspection by tests. *dev_ptr points
+ * into the workspace; *count is the element count the call produced (read from
+ * the device, so this synchronises the stream). DEPTH_ORDER, INST_KEYS,
+ * INST_VALS and RANGES hold the last binning of the call (the affiliated eye's
+ * ROI binning after gs_render_stereo or gs_render_two_pass). */
+typedef enum {
+  GS_BUF_RECORDS = 0,     /* float4[eye][max_surfels][4]: per-surfel blend records */
+  GS_BUF_RECTS = 1,       /* uint16x4[eye][max_surfels]: tile rect tx0, ty0, tx1, ty1 */
+  GS_BUF_BOUNDS = 2,      /* float4[eye][max_surfels]: xmin, xmax, ymin, ymax (keep_intermediates) */
+  GS_BUF_COUNTS = 3,      /* uint32[eye][max_surfels]: tiles touched per surfel (0 = culled) */
+  GS_BUF_DEPTH_ORDER = 4, /* uint32[max_surfels]: surfel ids of the last binning in depth order */
+  GS_BUF_INST_KEYS = 5,   /* uint32[max_instances]: tile id per instance, sorted */
+  GS_BUF_INST_VALS = 6,   /* uint32[max_instances]: surfel id per instance, sorted */
+  GS_BUF_RANGES = 7,      /* uint32x2[tiles]: [start, end) of each tile's instances */
+  GS_BUF_WARP = 8,        /* uint64[pixels]: (float depth bits << 32) | source index, ~0 = hole */
+  GS_BUF_TILE_MASK = 9,   /* uint8[tiles]: tiles of the ROI re-render */
+  GS_BUF_DEPTH_RANGE = 10,/* float[2]: d_min, d_max used by the edge ROI */
+  GS_BUF_STRIPS = 11,     /* int32[4][4]: edge strips x0, y0, x1, y1 (left, right, top, bottom) */
+  GS_BUF_WARP_DEPTH = 12, /* float[pixels]: warped depth (+inf background, 0 hole) */
+  GS_BUF_PAIRS = 13,      /* uint64[2]: evaluated (pixel, surfel) pairs per eye, when counting */
+  GS_BUF_EYE1 = 0x100     /* OR into RECORDS/RECTS/BOUNDS/COUNTS for the affiliated eye */
+} gs_buffer_id;
+
+gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *bytes,
+                            int64_t *count);
+
+/* 1: the blend kernels count evaluated (pixel, surfel) pairs, and those that
+ * contributed, into GS_BUF_PAIRS (uint64 evaluated[2], contributed[2]). */
+gs_status gs_context_set_counting(gs_context *ctx, int enable);
+
+/* 1: record a CUDA event on the context's stream at every stage boundary of the
+ * following calls (the paper reports a per-stage time breakdown, Sec. 4.5). */
+gs_status gs_context_set_profiling(gs_context *ctx, int enable);
+
+/* Milliseconds of each stage of the last profiled call (synchronises the stream):
+ *   gs_render_stereo:   preprocess, bin dominant, blend dominant, warp + edge ROI +
+ *                       gaps, centre ROIs, bin ROI tiles, blend ROI tiles, outputs
+ *   gs_render_two_pass: preprocess, bin dominant, blend dominant, bin affiliated,
+ *                       blend affiliated
+ *   gs_render_mono:     preprocess, bin, blend */
+gs_status gs_context_stage_times(gs_context *ctx, float *ms, int max_stages, int *n_stages);
+
+const char *gs_status_str(gs_status s);
+
+/* Number of CUDA kernels this library has enqueued since it was loaded, over all
+ * contexts and threads (diagnostics; host-side count, no synchronisation). */
+unsigned long long gs_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_H */

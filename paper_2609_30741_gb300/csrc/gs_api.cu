@@ -1,0 +1,421 @@
+// C ABI: contexts, workspace layout and the entry points of include/gs.h.
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "gs_internal.cuh"
+
+namespace gs {
+
+unsigned long long g_launches = 0;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  bool dry;
+  template <class T>
+  T *take(size_t count) {
+    off = (off + kAlign - 1) / kAlign * kAlign;
+    T *p = dry ? nullptr : reinterpret_cast<T *>(base + off);
+    off += sizeof(T) * (count ? count : 1);
+    return p;
+  }
+};
+
+void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
+  const size_t N = (size_t)lim.max_surfels;
+  const size_t P = (size_t)lim.max_width * (size_t)lim.max_height;
+  const size_t tiles = (size_t)((lim.max_width + kTile - 1) / kTile) * (size_t)((lim.max_height + kTile - 1) / kTile);
+  const size_t I = (size_t)lim.max_instances;
+  const size_t scan_blocks = ((N > P ? N : P) + kScanTile - 1) / kScanTile + 2;
+  ws.cams = c.take<CamBlock>(1);
+  ws.ctr = c.take<Counters>(1);
+  for (int e = 0; e < 2; ++e) {
+    ws.rec[e] = c.take<float4>(4 * N);
+    ws.rect[e] = c.take<ushort4>(N);
+    ws.bounds[e] = c.take<float4>(lim.keep_intermediates ? N : 1);
+    ws.cnt[e] = c.take<uint32_t>(N);
+    ws.zkey[e] = c.take<uint32_t>(N);
+    ws.dkey[e] = c.take<uint32_t>(N);
+    ws.dval[e] = c.take<uint32_t>(N);
+    ws.ikey[e] = c.take<uint32_t>(I);
+    ws.ival[e] = c.take<uint32_t>(I);
+  }
+  ws.cnt_roi = c.take<uint32_t>(N);
+  ws.offs = c.take<uint32_t>(N + 1);
+  ws.ranges = c.take<uint2>(tiles);
+  ws.tile_mask = c.take<uint8_t>(tiles);
+  ws.hist = c.take<uint32_t>(256 * (size_t)kSortBlocks);
+  ws.scan_sums = c.take<uint32_t>(scan_blocks);
+  ws.warpbuf = c.take<unsigned long long>(P);
+  ws.warp_depth = c.take<float>(P);
+  ws.cls = c.take<uint8_t>(P);
+  ws.labels = c.take<int32_t>(P);
+  ws.slots = c.take<uint32_t>(P + 1);
+  ws.rects = c.take<int4>((size_t)lim.max_rects);
+  ws.strips = c.take<int32_t>(16);
+  ws.drange = c.take<float>(2);
+  ws.widths = c.take<int32_t>(4);
+  ws.max_surfels = lim.max_surfels;
+  ws.max_w = lim.max_width;
+  ws.max_h = lim.max_height;
+  ws.max_rects = lim.max_rects;
+  ws.max_tiles = (int)tiles;
+  ws.max_instances = (int64_t)I;
+  ws.max_pixels = (int64_t)P;
+  ws.keep_intermediates = lim.keep_intermediates;
+}
+
+bool limits_ok(const gs_limits *lim) {
+  return lim && lim->max_surfels >= 0 && lim->max_width > 0 && lim->max_height > 0 && lim->max_instances > 0 &&
+         lim->max_instances < (int64_t(1) << 31) && lim->max_rects > 0 &&
+         (int64_t)lim->max_width * lim->max_height < (int64_t(1) << 31) && lim->max_surfels < (1 << 30);
+}
+
+__global__ void reset_counters_kernel(Counters *c) {
+  if (threadIdx.x == 0) {
+    c->n_vis[0] = c->n_vis[1] = 0;
+    c->n_inst[0] = c->n_inst[1] = 0;
+    c->n_sort[0] = c->n_sort[1] = 0;
+    c->dmin_bits = 0x7f800000u;
+    c->dmax_bits = 0u;
+    c->n_rects = 0;
+    c->pairs[0] = c->pairs[1] = 0ull;
+    c->contrib[0] = c->contrib[1] = 0ull;
+  }
+}
+
+}  // namespace
+
+size_t workspace_bytes(const gs_limits &lim) {
+  Carver c{nullptr, 0, true};
+  Workspace ws;
+  layout(lim, c, ws);
+  return c.off + kAlign;
+}
+
+bool carve_workspace(const gs_limits &lim, void *base, size_t bytes, Workspace *ws) {
+  if (workspace_bytes(lim) > bytes + kAlign) return false;
+  Carver c{reinterpret_cast<char *>(base), 0, false};
+  layout(lim, c, *ws);
+  return c.off <= bytes;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+constexpr int kMaxMarks = 16;
+
+struct gs_context {
+  Workspace ws;
+  gs_limits lim;
+  cudaStream_t stream;
+  int counting;
+  int last_tiles;  // tile count of the last binning (selects the sorted buffer)
+  int profiling;
+  int nmarks;
+  cudaEvent_t ev[kMaxMarks];
+};
+
+static gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+static bool scene_ok(const gs_context *ctx, const gs_scene *sc) {
+  if (!sc || sc->n < 0 || sc->n > ctx->lim.max_surfels || sc->sh_degree < 0 || sc->sh_degree > 3) return false;
+  if (sc->n == 0) return true;
+  if (!sc->pos || !sc->quat || !sc->scale || !sc->opacity || !sc->sh) return false;
+  // float4 loads need 16-byte alignment; scales are read as float2
+  if (((uintptr_t)sc->pos & 15) || ((uintptr_t)sc->quat & 15) || ((uintptr_t)sc->scale & 7) ||
+      ((uintptr_t)sc->opacity & 3))
+    return false;
+  if (sc->sh_degree == 3 && ((uintptr_t)sc->sh & 15)) return false;
+  return true;
+}
+
+static bool intr_ok(const gs_context *ctx, const gs_intrinsics *in) {
+  return in && in->width > 0 && in->height > 0 && in->width <= ctx->lim.max_width &&
+         in->height <= ctx->lim.max_height && in->fx > 0 && in->fy > 0 && in->width < 65536 * kTile &&
+         in->height < 65536 * kTile;
+}
+
+static PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in) {
+  PoseArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  memcpy(pa.R[0], a->R, sizeof(double) * 9);
+  memcpy(pa.t[0], a->t, sizeof(double) * 3);
+  if (b) {
+    memcpy(pa.R[1], b->R, sizeof(double) * 9);
+    memcpy(pa.t[1], b->t, sizeof(double) * 3);
+  }
+  pa.neyes = b ? 2 : 1;
+  pa.fx = in->fx; pa.fy = in->fy; pa.cx = in->cx; pa.cy = in->cy;
+  pa.W = in->width; pa.H = in->height;
+  return pa;
+}
+
+extern "C" {
+
+const char *gs_status_str(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_BAD_ARG: return "bad argument";
+    case GS_ERR_CAPACITY: return "device buffer capacity exceeded";
+    case GS_ERR_TIMEOUT: return "bounded device loop gave up";
+    case GS_ERR_CUDA: return "CUDA runtime error";
+    case GS_ERR_WORKSPACE: return "workspace too small";
+    case GS_ERR_NOT_LOADED: return "no repair network loaded";
+  }
+  return "unknown status";
+}
+
+unsigned long long gs_kernel_launches(void) { return g_launches; }
+
+gs_status gs_workspace_size(const gs_limits *lim, size_t *bytes) {
+  if (!limits_ok(lim) || !bytes) return GS_ERR_BAD_ARG;
+  *bytes = workspace_bytes(*lim);
+  return GS_OK;
+}
+
+gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *workspace, size_t workspace_bytes_,
+                            void *stream) {
+  if (!out || !limits_ok(lim) || !workspace) return GS_ERR_BAD_ARG;
+  if (((uintptr_t)workspace & 255) != 0) return GS_ERR_BAD_ARG;
+  if (workspace_bytes(*lim) > workspace_bytes_) return GS_ERR_WORKSPACE;
+  gs_context *ctx = new (std::nothrow) gs_context;
+  if (!ctx) return GS_ERR_BAD_ARG;
+  memset(ctx, 0, sizeof(*ctx));
+  ctx->lim = *lim;
+  ctx->stream = (cudaStream_t)stream;
+  if (!carve_workspace(*lim, workspace, workspace_bytes_, &ctx->ws)) {
+    delete ctx;
+    return GS_ERR_WORKSPACE;
+  }
+  cudaError_t e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return GS_ERR_CUDA;
+  }
+  *out = ctx;
+  return GS_OK;
+}
+
+gs_status gs_context_destroy(gs_context *ctx) {
+  if (!ctx) return GS_ERR_BAD_ARG;
+  for (int i = 0; i < kMaxMarks; ++i)
+    if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  delete ctx;
+  return GS_OK;
+}
+
+gs_status gs_context_set_profiling(gs_context *ctx, int enable) {
+  if (!ctx) return GS_ERR_BAD_ARG;
+  ctx->profiling = enable ? 1 : 0;
+  return GS_OK;
+}
+
+gs_status gs_context_stage_times(gs_context *ctx, float *ms, int max_stages, int *n_stages) {
+  if (!ctx || !ms || max_stages < 0) return GS_ERR_BAD_ARG;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return GS_ERR_CUDA;
+  int n = ctx->nmarks > 1 ? ctx->nmarks - 1 : 0;
+  if (n > max_stages) n = max_stages;
+  for (int i = 0; i < n; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) return GS_ERR_CUDA;
+    ms[i] = t;
+  }
+  if (n_stages) *n_stages = n;
+  return GS_OK;
+}
+
+gs_status gs_context_set_stream(gs_context *ctx, void *stream) {
+  if (!ctx) return GS_ERR_BAD_ARG;
+  ctx->stream = (cudaStream_t)stream;
+  return GS_OK;
+}
+
+gs_status gs_context_set_counting(gs_context *ctx, int enable) {
+  if (!ctx) return GS_ERR_BAD_ARG;
+  ctx->counting = enable ? 1 : 0;
+  return GS_OK;
+}
+
+gs_status gs_context_check(gs_context *ctx, int *device_status) {
+  if (!ctx) return GS_ERR_BAD_ARG;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  uint32_t st = 0;
+  e = cudaMemcpy(&st, &ctx->ws.ctr->status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  const uint32_t zero = 0;
+  e = cudaMemcpy(&ctx->ws.ctr->status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  int code = GS_OK;
+  if (st & kStCapacity) code = GS_ERR_CAPACITY;
+  else if (st & kStTimeout) code = GS_ERR_TIMEOUT;
+  if (device_status) *device_status = code;
+  return GS_OK;
+}
+
+// Stage timing: with profiling on, an event is recorded on the context's stream
+// at each stage boundary (slot 0 before the first kernel).
+static void mark(gs_context *ctx, int slot) {
+  if (!ctx->profiling || slot >= kMaxMarks) return;
+  if (!ctx->ev[slot] && cudaEventCreate(&ctx->ev[slot]) != cudaSuccess) return;
+  cudaEventRecord(ctx->ev[slot], ctx->stream);
+  ctx->nmarks = slot + 1 > ctx->nmarks ? slot + 1 : ctx->nmarks;
+}
+
+static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye, int W, int H, float3 bg,
+                                 float *rgb, float *depth, float *trans, bool stats, int slot) {
+  const Workspace &ws = ctx->ws;
+  cudaStream_t s = ctx->stream;
+  const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+  ctx->last_tiles = tx * ty;
+  cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  mark(ctx, slot);
+  e = launch_blend(ws, eye, W, H, nullptr, bg, rgb, depth, trans, nullptr, stats, ctx->counting != 0, s);
+  mark(ctx, slot + 1);
+  return cuda_status(e);
+}
+
+static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const gs_pose *a, const gs_pose *b,
+                            const gs_intrinsics *intr) {
+  cudaStream_t s = ctx->stream;
+  ctx->nmarks = 0;
+  mark(ctx, 0);
+  reset_counters_kernel<<<1, 32, 0, s>>>(ctx->ws.ctr);
+  GS_LAUNCHED(1);
+  PoseArgs pa = pose_args(a, b, intr);
+  cudaError_t e = launch_setup_cams(pa, ctx->ws.cams, s);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  e = launch_preprocess(*scene, ctx->ws, b ? 2 : 1, intr->width, intr->height, s);
+  mark(ctx, 1);
+  return cuda_status(e);
+}
+
+gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *pose, const gs_intrinsics *intr,
+                         const float *bg, float *rgb, float *depth, float *trans) {
+  if (!ctx || !pose || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !rgb) return GS_ERR_BAD_ARG;
+  gs_status st = begin_call(ctx, scene, pose, nullptr, intr);
+  if (st != GS_OK) return st;
+  const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
+  return render_eye_full(ctx, scene, 0, intr->width, intr->height, b, rgb, depth, trans, false, 2);
+}
+
+static bool outputs_ok(const gs_outputs *o) {
+  return o && o->rgb_dom && o->depth_dom && o->trans_dom && o->rgb_aff;
+}
+
+static gs_status copy_optional(gs_context *ctx, const gs_outputs *out, int W, int H) {
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (out->cls_aff) e = cudaMemcpyAsync(out->cls_aff, ctx->ws.cls, (size_t)W * H, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && out->roi_rects)
+    e = cudaMemcpyAsync(out->roi_rects, ctx->ws.rects, sizeof(int4) * (size_t)ctx->lim.max_rects,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && out->roi_count)
+    e = cudaMemcpyAsync(out->roi_count, &ctx->ws.ctr->n_rects, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && out->edge_widths)
+    e = cudaMemcpyAsync(out->edge_widths, ctx->ws.widths, sizeof(int32_t) * 4, cudaMemcpyDeviceToDevice, s);
+  return cuda_status(e);
+}
+
+gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom, const gs_pose *pose_aff,
+                           const gs_intrinsics *intr, int gap_thresh, const gs_roi_params *roi,
+                           const gs_outputs *out) {
+  if (!ctx || !pose_dom || !pose_aff || !roi || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
+    return GS_ERR_BAD_ARG;
+  if (gap_thresh < 0 || roi->margin < 0 || roi->samples_per_edge < 2 || roi->samples_per_edge > 1 << 20 ||
+      (roi->depth_mode != 0 && roi->depth_mode != 1))
+    return GS_ERR_BAD_ARG;
+  if (roi->repair_mode != 0) return GS_ERR_NOT_LOADED;
+  const int W = intr->width, H = intr->height;
+  const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+  gs_status st = begin_call(ctx, scene, pose_dom, pose_aff, intr);
+  if (st != GS_OK) return st;
+  const float3 black = make_float3(0.f, 0.f, 0.f);
+  // Stage 1: dominant eye, RGB + depth proxy (+ the per-frame depth range)
+  st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2);
+  if (st != GS_OK) return st;
+  // Stages 2-3: warp, edge ROIs, gaps
+  cudaError_t e = launch_warp_classify(ctx->ws, W, H, gap_thresh, *roi, out->rgb_dom, out->depth_dom,
+                                       out->trans_dom, out->rgb_aff, ctx->stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  mark(ctx, 4);
+  // Step 2: connected centre holes -> ROIs
+  if (roi->enable_center) {
+    if ((e = launch_centre_rois(ctx->ws, W, H, roi->margin, ctx->stream)) != cudaSuccess) return GS_ERR_CUDA;
+  }
+  mark(ctx, 5);
+  // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
+  ctx->last_tiles = tx * ty;
+  e = launch_binning(ctx->ws, 1, scene->n, tx, ty, ctx->ws.tile_mask, ctx->stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  mark(ctx, 6);
+  e = launch_blend(ctx->ws, 1, W, H, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ctx->ws.cls, false,
+                   ctx->counting != 0, ctx->stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  mark(ctx, 7);
+  st = copy_optional(ctx, out, W, H);
+  mark(ctx, 8);
+  return st;
+}
+
+gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                             const gs_pose *pose_aff, const gs_intrinsics *intr, const gs_outputs *out) {
+  if (!ctx || !pose_dom || !pose_aff || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
+    return GS_ERR_BAD_ARG;
+  const int W = intr->width, H = intr->height;
+  gs_status st = begin_call(ctx, scene, pose_dom, pose_aff, intr);
+  if (st != GS_OK) return st;
+  const float3 black = make_float3(0.f, 0.f, 0.f);
+  st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, false, 2);
+  if (st != GS_OK) return st;
+  return render_eye_full(ctx, scene, 1, W, H, black, out->rgb_aff, nullptr, nullptr, false, 4);
+}
+
+gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *bytes, int64_t *count) {
+  if (!ctx || !dev_ptr) return GS_ERR_BAD_ARG;
+  const Workspace &ws = ctx->ws;
+  const size_t N = (size_t)ws.max_surfels, P = (size_t)ws.max_pixels, I = (size_t)ws.max_instances;
+  Counters c;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaMemcpy(&c, ws.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+  void *p = nullptr;
+  size_t b = 0;
+  int64_t n = -1;
+  const int nt = ws.max_tiles;
+  const int eye = (which & GS_BUF_EYE1) ? 1 : 0;
+  const int sb = sorted_buffer(ctx->last_tiles > 0 ? ctx->last_tiles : 1);
+  // the last binning is the affiliated eye's when it ran, else the dominant eye's
+  const int last = c.n_vis[1] || c.n_inst[1] ? 1 : 0;
+  switch (which & ~GS_BUF_EYE1) {
+    case GS_BUF_RECORDS: p = ws.rec[eye]; b = 64 * N; n = (int64_t)N; break;
+    case GS_BUF_RECTS: p = ws.rect[eye]; b = 8 * N; n = (int64_t)N; break;
+    case GS_BUF_BOUNDS: p = ws.bounds[eye]; b = ws.keep_intermediates ? 16 * N : 0; n = (int64_t)N; break;
+    case GS_BUF_COUNTS: p = ws.cnt[eye]; b = 4 * N; n = (int64_t)N; break;
+    case GS_BUF_DEPTH_ORDER: p = ws.dval[0]; b = 4 * N; n = c.n_vis[last]; break;
+    case GS_BUF_INST_KEYS: p = ws.ikey[sb]; b = 4 * I; n = c.n_sort[last]; break;
+    case GS_BUF_INST_VALS: p = ws.ival[sb]; b = 4 * I; n = c.n_sort[last]; break;
+    case GS_BUF_RANGES: p = ws.ranges; b = 8 * (size_t)nt; n = nt; break;
+    case GS_BUF_WARP: p = ws.warpbuf; b = 8 * P; n = (int64_t)P; break;
+    case GS_BUF_TILE_MASK: p = ws.tile_mask; b = (size_t)nt; n = nt; break;
+    case GS_BUF_DEPTH_RANGE: p = ws.drange; b = 8; n = 2; break;
+    case GS_BUF_STRIPS: p = ws.strips; b = 64; n = 16; break;
+    case GS_BUF_WARP_DEPTH: p = ws.warp_depth; b = 4 * P; n = (int64_t)P; break;
+    case GS_BUF_PAIRS: p = &ws.ctr->pairs[0]; b = 32; n = 4; break;
+    default: return GS_ERR_BAD_ARG;
+  }
+  *dev_ptr = p;
+  if (bytes) *bytes = b;
+  if (count) *count = n;
+  return GS_OK;
+}
+
+}  // extern "C"

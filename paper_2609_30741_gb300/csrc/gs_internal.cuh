@@ -1,0 +1,138 @@
+// Internal declarations shared by the CUDA translation units of the renderer.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gs.h"
+
+namespace gs {
+
+constexpr int kTile = 16;            // rasterizer tile edge, pixels (Sec. 3.5: 16x16 tiles)
+constexpr float kZNear = 0.2f;       // near plane, metres
+constexpr float kAlphaMax = 0.99f;   // alpha clamp
+constexpr float kTMin = 1e-4f;       // transmittance stop
+// log2(1/255): a contribution with log2(o * Ghat) below this is skipped
+constexpr float kLog2AlphaMin = -7.9943534368588579f;
+// -log2(e) / 2: Ghat = exp(-rho / 2) = 2^(rho * kNegHalfLog2e)
+constexpr float kNegHalfLog2e = -0.72134752044448170f;
+// the bounds of a surfel's support are grown by this many pixels so that the
+// float32 blend never evaluates a contributing pair outside its tile rectangle
+constexpr float kBoundPad = 1.0e-2f;
+
+constexpr uint32_t kClsHole = 1, kClsGap = 2, kClsCentre = 4, kClsStrip = 8, kClsRender = 16,
+                   kClsNet = 32;
+
+// Device status bits (mapped to gs_status by the host).
+constexpr uint32_t kStCapacity = 1, kStTimeout = 2;
+
+struct EyeCam {
+  float R[9];       // world -> camera rotation, row-major: X_c = R P + t
+  float t[3];
+  float centre[3];  // camera centre in world coordinates (SH view direction)
+  float fx, fy, cx, cy;
+  int W, H, tiles_x, tiles_y;
+};
+
+struct CamBlock {
+  EyeCam eye[2];
+  float Rrel[9];  // dominant camera -> affiliated camera: X_a = Rrel X_d + trel
+  float trel[3];
+};
+
+// Host-side copy of what the FP64 set-up kernel needs.
+struct PoseArgs {
+  double R[2][9];
+  double t[2][3];
+  double fx, fy, cx, cy;
+  int W, H;
+  int neyes;
+};
+
+struct Counters {
+  uint32_t status;
+  uint32_t n_vis[2];     // visible (binned) surfels of the last binning per eye
+  uint32_t n_inst[2];    // instances requested per eye (may exceed capacity)
+  uint32_t dmin_bits, dmax_bits;  // range of the normalised depth (positive float bits)
+  uint32_t n_rects;      // centre components found
+  uint32_t n_sort[2];    // instances actually binned per eye (capacity-clamped)
+  uint32_t pad[5];
+  unsigned long long pairs[2];    // evaluated (pixel, surfel) pairs per eye (counting mode)
+  unsigned long long contrib[2];  // of which contributed (alpha >= 1/255, before termination)
+};
+
+// The per-surfel blend record, 64 bytes = 4 float4:
+//  r0 = (c.x, c.y, log2(o), z_c)          projected centre, opacity, centre depth
+//  r1 = (V1, -V0, -U1, U0)                p.xy = [dx dy] * these (see preprocess)
+//  r2 = (Az, Bz, Cz, dz_u)                p.z = Az + dx Bz + dy Cz; depth slope along u
+//  r3 = (dz_v, r, g, b)                   depth slope along v; colour
+struct Record {
+  float4 r0, r1, r2, r3;
+};
+
+// Views of the caller-owned workspace.
+struct Workspace {
+  CamBlock *cams;
+  Counters *ctr;
+  float4 *rec[2];
+  ushort4 *rect[2];
+  float4 *bounds[2];
+  uint32_t *cnt[2];
+  uint32_t *zkey[2];            // float bits of the centre depth per surfel and eye
+  uint32_t *cnt_roi;            // per-surfel tile count restricted to the ROI tile mask
+  uint32_t *dkey[2], *dval[2];  // depth sort double buffers
+  uint32_t *offs;               // per-sorted-surfel instance offsets (+1)
+  uint32_t *ikey[2], *ival[2];  // instance sort double buffers
+  uint2 *ranges;
+  uint8_t *tile_mask;
+  uint32_t *hist;               // radix histograms [256][kSortBlocks]
+  uint32_t *scan_sums;          // scan block sums
+  unsigned long long *warpbuf;
+  float *warp_depth;
+  uint8_t *cls;
+  int32_t *labels;
+  uint32_t *slots;              // scan of component roots (+1)
+  int4 *rects;                  // centre ROI rectangles
+  int32_t *strips;              // [4][4]
+  float *drange;                // [2]
+  int32_t *widths;              // [4]
+  // limits
+  int max_surfels, max_w, max_h, max_rects, max_tiles;
+  int64_t max_instances, max_pixels;
+  int keep_intermediates;
+};
+
+constexpr int kSortBlocks = 304;     // 2 CTAs per SM on 152 SMs
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;        // items per thread per sort tile
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+// Host-side count of the kernels this library has enqueued (diagnostics).
+extern unsigned long long g_launches;
+#define GS_LAUNCHED(n) (::gs::g_launches += (n))
+
+size_t workspace_bytes(const gs_limits &lim);
+bool carve_workspace(const gs_limits &lim, void *base, size_t bytes, Workspace *ws);
+
+// ---- launches (each returns the launch error) ----
+cudaError_t launch_setup_cams(const PoseArgs &pa, CamBlock *cams, cudaStream_t s);
+cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes, int W, int H,
+                              cudaStream_t s);
+// Bins the visible surfels of `eye` (restricted to tile_mask when given) into
+// sorted per-tile instance lists and their ranges.
+cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
+                           const uint8_t *tile_mask, cudaStream_t s);
+int sorted_buffer(int ntiles);
+cudaError_t launch_blend(const Workspace &ws, int eye, int W, int H, const uint8_t *tile_mask,
+                         float3 bg, float *rgb, float *depth, float *trans, uint8_t *cls,
+                         bool depth_stats, bool count_pairs, cudaStream_t s);
+// Warp, edge ROIs, hole classification and gap filling (writes rgb_aff and cls).
+cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
+                                 const float *rgb_dom, const float *depth_dom, const float *trans_dom,
+                                 float *rgb_aff, cudaStream_t s);
+// Connected centre holes -> ROI rectangles -> tile mask.
+cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,239 @@
+// Camera set-up (FP64) and per-surfel preprocessing for one or both eyes.
+//
+// Paper: Sec. 3.3 (2D Gaussian surfels, Eq. 1-2, ray-splat intersection),
+// Sec. 3.4 (pinhole projection, Eq. 3; poses, Eq. 4-5), Sec. 3.1 Stage 1.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+// ---------------------------------------------------------------- FP64 set-up
+//
+// The only double-precision work on the GPU: inverting the camera-to-world
+// poses (world -> camera) and composing the relative pose between the eyes,
+// X_aff = R_aff^T R_dom X_dom + R_aff^T (t_dom - t_aff) (Eq. 4 followed by Eq. 5).
+__global__ void setup_cams_kernel(PoseArgs pa, CamBlock *cams) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  CamBlock cb;
+  for (int e = 0; e < 2; ++e) {
+    const int src = e < pa.neyes ? e : 0;
+    const double *R = pa.R[src], *t = pa.t[src];
+    EyeCam &c = cb.eye[e];
+    for (int i = 0; i < 3; ++i) {
+      double ti = 0.0;
+      for (int j = 0; j < 3; ++j) {
+        c.R[i * 3 + j] = (float)R[j * 3 + i];  // transpose
+        ti -= R[j * 3 + i] * t[j];
+      }
+      c.t[i] = (float)ti;
+      c.centre[i] = (float)t[i];
+    }
+    c.fx = (float)pa.fx; c.fy = (float)pa.fy; c.cx = (float)pa.cx; c.cy = (float)pa.cy;
+    c.W = pa.W; c.H = pa.H;
+    c.tiles_x = (pa.W + kTile - 1) / kTile;
+    c.tiles_y = (pa.H + kTile - 1) / kTile;
+  }
+  const int a = pa.neyes > 1 ? 1 : 0;
+  const double *Rd = pa.R[0], *td = pa.t[0], *Ra = pa.R[a], *ta = pa.t[a];
+  for (int i = 0; i < 3; ++i) {
+    double tr = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      double r = 0.0;
+      for (int k = 0; k < 3; ++k) r += Ra[k * 3 + i] * Rd[k * 3 + j];
+      cb.Rrel[i * 3 + j] = (float)r;
+      tr += Ra[j * 3 + i] * (td[j] - ta[j]);
+    }
+    cb.trel[i] = (float)tr;
+  }
+  *cams = cb;
+}
+
+cudaError_t launch_setup_cams(const PoseArgs &pa, CamBlock *cams, cudaStream_t s) {
+  setup_cams_kernel<<<1, 32, 0, s>>>(pa, cams);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- SH colour
+//
+// Real spherical harmonics up to degree 3 (3DGS sign convention). Constants are
+// the closed forms sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times each polynomial's
+// normalisation, written out to float precision.
+__device__ __forceinline__ void sh_rgb(const float *__restrict__ c, int deg, float x, float y, float z,
+                                       float out[3]) {
+  const float Y00 = 0.28209479177387814f;        // 1 / (2 sqrt(pi))
+  const float Y1 = 0.48860251190291992f;         // sqrt(3 / (4 pi))
+  const float Y2a = 1.0925484305920792f;         // sqrt(15 / pi) / 2
+  const float Y2b = 0.31539156525252001f;        // sqrt(5 / pi) / 4
+  const float Y2c = 0.54627421529603959f;        // sqrt(15 / pi) / 4
+  const float Y3a = 0.59004358992664352f;        // sqrt(35 / (2 pi)) / 4
+  const float Y3b = 2.8906114426405538f;         // sqrt(105 / pi) / 2
+  const float Y3c = 0.45704579946446572f;        // sqrt(21 / (2 pi)) / 4
+  const float Y3d = 0.37317633259011540f;        // sqrt(7 / pi) / 4
+  const float Y3e = 1.4453057213202769f;         // sqrt(105 / pi) / 4
+  float b[16];
+  b[0] = Y00;
+  int K = 1;
+  if (deg >= 1) {
+    b[1] = -Y1 * y; b[2] = Y1 * z; b[3] = -Y1 * x;
+    K = 4;
+  }
+  if (deg >= 2) {
+    const float xx = x * x, yy = y * y, zz = z * z;
+    b[4] = Y2a * x * y; b[5] = -Y2a * y * z; b[6] = Y2b * (2.f * zz - xx - yy);
+    b[7] = -Y2a * x * z; b[8] = Y2c * (xx - yy);
+    K = 9;
+    if (deg >= 3) {
+      b[9] = -Y3a * y * (3.f * xx - yy);
+      b[10] = Y3b * x * y * z;
+      b[11] = -Y3c * y * (4.f * zz - xx - yy);
+      b[12] = Y3d * z * (2.f * zz - 3.f * xx - 3.f * yy);
+      b[13] = -Y3c * x * (4.f * zz - xx - yy);
+      b[14] = Y3e * z * (xx - yy);
+      b[15] = -Y3a * x * (xx - 3.f * yy);
+      K = 16;
+    }
+  }
+  float r = 0.5f, g = 0.5f, bl = 0.5f;
+  for (int k = 0; k < K; ++k) {
+    r = fmaf(b[k], c[3 * k + 0], r);
+    g = fmaf(b[k], c[3 * k + 1], g);
+    bl = fmaf(b[k], c[3 * k + 2], bl);
+  }
+  out[0] = fmaxf(r, 0.f);
+  out[1] = fmaxf(g, 0.f);
+  out[2] = fmaxf(bl, 0.f);
+}
+
+// ---------------------------------------------------------------- preprocess
+//
+// One thread per surfel; the attributes are read once (coalesced float4 loads)
+// and both eyes are prepared from registers.
+//
+// Blend record. With M = [s_u t_u^c, s_v t_v^c, p_c] (Eq. 1 in the camera frame)
+// the pixel ray through (x, y) meets the surfel plane at the local (u, v) with
+// (u, v, 1) ~ (T_u - x T_w) x (T_v - y T_w) where T = K M (the 2DGS plane
+// intersection). Writing x = c_x + dx, y = c_y + dy around the projected centre c
+// and dividing by p_c.z > 0 gives the affine form
+//   p.x = dx V1 - dy U1,   p.y = -dx V0 + dy U0,   p.z = Az + dx Bz + dy Cz
+// with U = fx (M_row0 - (p_x/p_z) M_row2), V = fy (M_row1 - (p_y/p_z) M_row2)
+// (both zero in the third column), Az = (U0 V1 - U1 V0)/p_z,
+// Bz = (V0 M21 - V1 M20)/p_z, Cz = (M20 U1 - M21 U0)/p_z, so u = p.x/p.z,
+// v = p.y/p.z. Expanding around c keeps the terms small (well conditioned).
+// The intersection depth is z = M20 u + M21 v + p_z.
+__global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamBlock *__restrict__ cams,
+                                                         Workspace ws, int neyes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.n) return;
+  const float4 p4 = reinterpret_cast<const float4 *>(sc.pos)[i];
+  float4 q = reinterpret_cast<const float4 *>(sc.quat)[i];
+  const float2 s2 = reinterpret_cast<const float2 *>(sc.scale)[i];
+  const float o = sc.opacity[i];
+  const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  bool alive = qn2 > 0.f && 255.f * o >= 1.f;
+  // normalise (w, x, y, z) and build the two tangent columns of R (Eq. 1)
+  const float qi = alive ? rsqrtf(qn2) : 0.f;
+  const float w = q.x * qi, x = q.y * qi, y = q.z * qi, z = q.w * qi;
+  const float tu[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y)};
+  const float tv[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
+  const float l2o = alive ? __log2f(o) : 0.f;
+  // support radius in (u, v): o G >= 1/255  <=>  u^2 + v^2 <= 2 ln(255 o)
+  const float rc2 = alive ? 2.f * logf(255.f * o) : 0.f;
+  const float rc = sqrtf(fmaxf(rc2, 0.f));
+  const float lp = sqrtf(fmaxf(0.5f * rc2, 0.f));  // low-pass support radius, pixels
+  const int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+  float shc[48];
+  if (alive) {
+    const float *src = sc.sh + (size_t)i * K * 3;
+    if (sc.sh_degree == 3) {
+      const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) {
+        const float4 v = s4[k];
+        shc[4 * k] = v.x; shc[4 * k + 1] = v.y; shc[4 * k + 2] = v.z; shc[4 * k + 3] = v.w;
+      }
+    } else {
+      for (int k = 0; k < 3 * K; ++k) shc[k] = src[k];
+    }
+  }
+  for (int e = 0; e < neyes; ++e) {
+    const EyeCam &c = cams->eye[e];
+    bool vis = alive;
+    float pc[3], tuc[3], tvc[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      pc[r] = fmaf(c.R[r * 3 + 0], p4.x, fmaf(c.R[r * 3 + 1], p4.y, fmaf(c.R[r * 3 + 2], p4.z, c.t[r])));
+      tuc[r] = fmaf(c.R[r * 3 + 0], tu[0], fmaf(c.R[r * 3 + 1], tu[1], c.R[r * 3 + 2] * tu[2]));
+      tvc[r] = fmaf(c.R[r * 3 + 0], tv[0], fmaf(c.R[r * 3 + 1], tv[1], c.R[r * 3 + 2] * tv[2]));
+    }
+    vis = vis && pc[2] > kZNear;
+    const float M0[3] = {s2.x * tuc[0], s2.y * tvc[0], pc[0]};
+    const float M1[3] = {s2.x * tuc[1], s2.y * tvc[1], pc[1]};
+    const float M2[3] = {s2.x * tuc[2], s2.y * tvc[2], pc[2]};
+    // screen bounds: the four projected corners of the support square plus the
+    // low-pass disc around the projected centre
+    float xmin = 3.0e38f, xmax = -3.0e38f, ymin = 3.0e38f, ymax = -3.0e38f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float a = (k & 1) ? rc : -rc, b = (k & 2) ? rc : -rc;
+      const float X = fmaf(a, M0[0], fmaf(b, M0[1], pc[0]));
+      const float Y = fmaf(a, M1[0], fmaf(b, M1[1], pc[1]));
+      const float Z = fmaf(a, M2[0], fmaf(b, M2[1], pc[2]));
+      vis = vis && Z > kZNear;
+      const float iz = 1.f / fmaxf(Z, kZNear);
+      const float u = fmaf(c.fx * X, iz, c.cx), v = fmaf(c.fy * Y, iz, c.cy);
+      xmin = fminf(xmin, u); xmax = fmaxf(xmax, u);
+      ymin = fminf(ymin, v); ymax = fmaxf(ymax, v);
+    }
+    const float izc = 1.f / fmaxf(pc[2], kZNear);
+    const float rx = pc[0] * izc, ry = pc[1] * izc;
+    const float cxp = fmaf(c.fx, rx, c.cx), cyp = fmaf(c.fy, ry, c.cy);
+    xmin = fminf(xmin, cxp - lp) - kBoundPad; xmax = fmaxf(xmax, cxp + lp) + kBoundPad;
+    ymin = fminf(ymin, cyp - lp) - kBoundPad; ymax = fmaxf(ymax, cyp + lp) + kBoundPad;
+    // tile rectangle of the pixels whose centres lie inside the bounds
+    uint32_t count = 0;
+    ushort4 rect = make_ushort4(0, 0, 0, 0);
+    if (vis && xmax >= 0.f && ymax >= 0.f && xmin <= c.W - 1.f && ymin <= c.H - 1.f) {
+      const int px0 = xmin <= 0.f ? 0 : (int)ceilf(xmin);
+      const int px1 = xmax >= c.W - 1.f ? c.W - 1 : (int)floorf(xmax);
+      const int py0 = ymin <= 0.f ? 0 : (int)ceilf(ymin);
+      const int py1 = ymax >= c.H - 1.f ? c.H - 1 : (int)floorf(ymax);
+      if (px0 <= px1 && py0 <= py1) {
+        rect = make_ushort4(px0 / kTile, py0 / kTile, px1 / kTile, py1 / kTile);
+        count = (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
+      }
+    }
+    if (!vis) count = 0;
+    ws.cnt[e][i] = count;
+    ws.rect[e][i] = rect;
+    ws.zkey[e][i] = __float_as_uint(pc[2]);
+    if (ws.keep_intermediates) ws.bounds[e][i] = make_float4(xmin, xmax, ymin, ymax);
+    if (count == 0) continue;
+    const float U0 = c.fx * fmaf(-rx, M2[0], M0[0]), U1 = c.fx * fmaf(-rx, M2[1], M0[1]);
+    const float V0 = c.fy * fmaf(-ry, M2[0], M1[0]), V1 = c.fy * fmaf(-ry, M2[1], M1[1]);
+    const float Az = fmaf(U0, V1, -U1 * V0) * izc;
+    const float Bz = fmaf(V0, M2[1], -V1 * M2[0]) * izc;
+    const float Cz = fmaf(M2[0], U1, -M2[1] * U0) * izc;
+    // view-dependent colour from this eye's centre
+    float dx = p4.x - c.centre[0], dy = p4.y - c.centre[1], dz = p4.z - c.centre[2];
+    const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    dx *= dn; dy *= dn; dz *= dn;
+    float rgb[3];
+    sh_rgb(shc, sc.sh_degree, dx, dy, dz, rgb);
+    float4 *r = ws.rec[e] + 4 * (size_t)i;
+    r[0] = make_float4(cxp, cyp, l2o, pc[2]);
+    r[1] = make_float4(V1, -V0, -U1, U0);
+    r[2] = make_float4(Az, Bz, Cz, M2[0]);
+    r[3] = make_float4(M2[1], rgb[0], rgb[1], rgb[2]);
+  }
+}
+
+cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes, int W, int H,
+                              cudaStream_t s) {
+  (void)W; (void)H;
+  if (sc.n == 0) return cudaSuccess;
+  preprocess_kernel<<<(sc.n + 255) / 256, 256, 0, s>>>(sc, ws.cams, ws, neyes);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

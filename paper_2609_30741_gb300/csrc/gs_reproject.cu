@@ -1,0 +1,416 @@
+// Reprojection to the affiliated eye, hole categorisation and the adaptive ROI
+// generator.
+//
+// Paper: Sec. 3.1 Stages 2-4; Sec. 3.4 Eq. 3-5 (unproject with the depth proxy,
+// transfer, project); Sec. 3.5 Step 1 (edge ROIs, Eq. 6-8, margin m, 16x16
+// tiles) and Step 2 (connected centre holes -> box -> margin -> tiles).
+//
+// Readings of passages the paper leaves open (the oracle states the same):
+//  - a source pixel is a surface sample when its coverage 1 - T >= 0.5 and warps
+//    with D / (1 - T); otherwise it is a background sample at infinite depth
+//    (direction-only transfer) that loses every depth test;
+//  - a sample lands on pixel (floor(x + 0.5), floor(y + 0.5)); the packed key
+//    (float depth bits << 32 | source index) resolves the depth test with one
+//    64-bit atomicMin, smallest depth first and then smallest source index;
+//  - edge ROI samples are taken at the pixel they round to;
+//  - gaps: holes outside the edge strips whose horizontal or vertical hole run is
+//    at most gap_thresh long with valid pixels at both ends, filled by linear
+//    interpolation along the shorter such run (horizontal on ties); the other
+//    holes are centre holes (4-connected components -> ROIs).
+#include "gs_internal.cuh"
+#include "gs_scan.cuh"
+
+namespace gs {
+
+constexpr unsigned long long kNoSample = ~0ull;
+constexpr uint32_t kInfBits = 0x7f800000u;
+
+__device__ __forceinline__ bool transfer(const CamBlock &cb, float x, float y, float d, bool surface, float &u,
+                                         float &v, float &z) {
+  const EyeCam &c = cb.eye[0];
+  const float rx = (x - c.cx) / c.fx, ry = (y - c.cy) / c.fy;
+  const float *R = cb.Rrel;
+  float X, Y, Z;
+  if (surface) {  // Eq. 4 then Eq. 5 with the composed relative pose
+    X = fmaf(R[0], rx * d, fmaf(R[1], ry * d, fmaf(R[2], d, cb.trel[0])));
+    Y = fmaf(R[3], rx * d, fmaf(R[4], ry * d, fmaf(R[5], d, cb.trel[1])));
+    Z = fmaf(R[6], rx * d, fmaf(R[7], ry * d, fmaf(R[8], d, cb.trel[2])));
+    if (!(Z > kZNear)) return false;
+  } else {  // direction only
+    X = fmaf(R[0], rx, fmaf(R[1], ry, R[2]));
+    Y = fmaf(R[3], rx, fmaf(R[4], ry, R[5]));
+    Z = fmaf(R[6], rx, fmaf(R[7], ry, R[8]));
+    if (!(Z > 0.f)) return false;
+  }
+  const EyeCam &a = cb.eye[1];
+  u = fmaf(a.fx, X / Z, a.cx);  // Eq. 3
+  v = fmaf(a.fy, Y / Z, a.cy);
+  z = Z;
+  return true;
+}
+
+// ---------------------------------------------------------------- forward warp
+__global__ void __launch_bounds__(256) warp_scatter_kernel(const CamBlock *__restrict__ cams,
+                                                           const float *__restrict__ depth,
+                                                           const float *__restrict__ trans,
+                                                           unsigned long long *__restrict__ buf, int W, int H) {
+  const CamBlock &cb = *cams;
+  const int64_t npix = (int64_t)W * H;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    const float cov = 1.f - trans[p];
+    const bool surface = cov >= 0.5f;
+    const float d = surface ? depth[p] / cov : 0.f;
+    float u, v, z;
+    if (!transfer(cb, (float)(p % W), (float)(p / W), d, surface, u, v, z)) continue;
+    const float fx = floorf(u + 0.5f), fy = floorf(v + 0.5f);
+    if (!(fx >= 0.f && fx <= (float)(W - 1) && fy >= 0.f && fy <= (float)(H - 1))) continue;
+    const uint32_t zb = surface ? __float_as_uint(z) : kInfBits;
+    const int64_t q = (int64_t)fy * W + (int64_t)fx;
+    atomicMin(buf + q, ((unsigned long long)zb << 32) | (unsigned long long)(uint32_t)p);
+  }
+}
+
+// ---------------------------------------------------------------- edge ROI (Step 1)
+__global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restrict__ cams, Counters *__restrict__ ctr,
+                                                       int N, int m, int depth_mode, float fixed_min,
+                                                       float fixed_max, int32_t *__restrict__ strips,
+                                                       int32_t *__restrict__ widths, float *__restrict__ drange,
+                                                       uint8_t *__restrict__ tile_mask) {
+  const CamBlock &cb = *cams;
+  const int W = cb.eye[1].W, H = cb.eye[1].H, tiles_x = cb.eye[1].tiles_x;
+  __shared__ int sxmin, sxmax, symin, symax, sany;
+  __shared__ int sstrip[16];
+  float dmin = fixed_min, dmax = fixed_max;
+  if (depth_mode == 0) {
+    dmin = __uint_as_float(ctr->dmin_bits);
+    dmax = __uint_as_float(ctr->dmax_bits);
+    if (ctr->dmax_bits == 0u) dmin = dmax = 0.f;  // no valid pixel
+  }
+  if (threadIdx.x == 0) {
+    sxmin = symin = 0x7fffffff;
+    sxmax = symax = -0x7fffffff;
+    sany = 0;
+    drange[0] = dmin;
+    drange[1] = dmax;
+  }
+  __syncthreads();
+  const int nsamp = 4 * N * 2;
+  for (int k = threadIdx.x; k < nsamp; k += blockDim.x) {
+    const int e = k / (2 * N), r = (k / 2) % N, h = k & 1;
+    const int along = e < 2 ? W : H;
+    const int pos = (int)(((long long)2 * r * (along - 1) + (N - 1)) / (2LL * (N - 1)));
+    const int x = e == 0 ? pos : e == 1 ? pos : e == 2 ? 0 : W - 1;
+    const int y = e == 0 ? 0 : e == 1 ? H - 1 : pos;
+    const float d = h ? dmax : dmin;
+    float u, v, z;
+    if (!(d > 0.f) || !transfer(cb, (float)x, (float)y, d, true, u, v, z)) continue;
+    u = fminf(fmaxf(u, -1e9f), 1e9f);
+    v = fminf(fmaxf(v, -1e9f), 1e9f);
+    const int ix = (int)floorf(u + 0.5f), iy = (int)floorf(v + 0.5f);
+    atomicMin(&sxmin, ix); atomicMax(&sxmax, ix);
+    atomicMin(&symin, iy); atomicMax(&symax, iy);
+    sany = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int lw, rw, th, bh;
+    if (!sany) {
+      lw = rw = W / 2;
+      th = bh = H / 2;
+    } else {  // Eq. 7, Eq. 8 and the vertical analogues
+      lw = sxmin > 0 ? min(max(min(sxmin, W) + m, 0), W / 2) : 0;
+      rw = sxmax < W - 1 ? min(max((W - 1) - max(sxmax, -1) + m, 0), W / 2) : 0;
+      th = symin > 0 ? min(max(min(symin, H) + m, 0), H / 2) : 0;
+      bh = symax < H - 1 ? min(max((H - 1) - max(symax, -1) + m, 0), H / 2) : 0;
+    }
+    widths[0] = lw; widths[1] = rw; widths[2] = th; widths[3] = bh;
+    // tile-aligned strips (half-open pixels): left, right, top, bottom
+    const int lx1 = lw > 0 ? min((lw + kTile - 1) / kTile * kTile, W) : 0;
+    const int rx0 = rw > 0 ? (W - rw) / kTile * kTile : W;
+    const int ty1 = th > 0 ? min((th + kTile - 1) / kTile * kTile, H) : 0;
+    const int by0 = bh > 0 ? (H - bh) / kTile * kTile : H;
+    const int s[16] = {0, 0, lx1, lw > 0 ? H : 0, rx0, 0, W, rw > 0 ? H : 0,
+                       0, 0, th > 0 ? W : 0, ty1, 0, by0, bh > 0 ? W : 0, H};
+    for (int k = 0; k < 16; ++k) {
+      strips[k] = s[k];
+      sstrip[k] = s[k];
+    }
+  }
+  __syncthreads();
+  const int ntiles = tiles_x * cb.eye[1].tiles_y;
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
+    const int x0 = (t % tiles_x) * kTile, y0 = (t / tiles_x) * kTile;
+    bool in = false;
+    for (int k = 0; k < 4; ++k) {
+      const int *r = sstrip + 4 * k;
+      in |= x0 < r[2] && x0 + kTile > r[0] && y0 < r[3] && y0 + kTile > r[1];
+    }
+    if (in) tile_mask[t] = 1;
+  }
+}
+
+// ------------------------------------------------ resolve + classification + fill
+//
+// Per affiliated pixel: resolve the warp buffer, then (outside the edge strips)
+// classify holes into gaps and centre holes and fill gaps by interpolation. All
+// neighbour reads go to the warp buffer (read-only here), so pixels never read
+// another pixel's output.
+struct WarpView {
+  const unsigned long long *buf;
+  const float *rgb_dom;
+  int W, H;
+  size_t hw;
+  __device__ bool hole(int x, int y) const { return buf[(size_t)y * W + x] == kNoSample; }
+  __device__ void colour(int x, int y, float c[3]) const {
+    const uint32_t s = (uint32_t)(buf[(size_t)y * W + x] & 0xffffffffull);
+    c[0] = rgb_dom[s];
+    c[1] = rgb_dom[hw + s];
+    c[2] = rgb_dom[2 * hw + s];
+  }
+};
+
+__global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_t *__restrict__ strips, int gap,
+                                                       int center_enabled, float *__restrict__ rgb_aff,
+                                                       float *__restrict__ warp_depth, uint8_t *__restrict__ cls) {
+  const int W = wv.W, H = wv.H;
+  const int64_t npix = (int64_t)W * H;
+  __shared__ int s[16];
+  if (threadIdx.x < 16) s[threadIdx.x] = strips[threadIdx.x];
+  __syncthreads();
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(p % W), y = (int)(p / W);
+    const unsigned long long key = wv.buf[p];
+    const bool hole = key == kNoSample;
+    bool strip = false;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) strip |= x >= s[4 * k] && x < s[4 * k + 2] && y >= s[4 * k + 1] && y < s[4 * k + 3];
+    uint8_t c = (hole ? kClsHole : 0u) | (strip ? kClsStrip : 0u);
+    float out[3] = {0.f, 0.f, 0.f};
+    if (!hole) {
+      wv.colour(x, y, out);
+      const uint32_t zb = (uint32_t)(key >> 32);
+      warp_depth[p] = __uint_as_float(zb);
+    } else {
+      warp_depth[p] = 0.f;
+    }
+    if (hole && !strip) {
+      // bounded runs up to gap + 1 long decide gaps; longer runs are scanned in
+      // full only for the centre-off fallback
+      int a = x, b = x, at = y, bt = y;
+      const int lim = gap + 1;
+      while (a - 1 >= 0 && x - (a - 1) <= lim && wv.hole(a - 1, y)) --a;
+      while (b + 1 <= W - 1 && (b + 1) - x <= lim && wv.hole(b + 1, y)) ++b;
+      while (at - 1 >= 0 && y - (at - 1) <= lim && wv.hole(x, at - 1)) --at;
+      while (bt + 1 <= H - 1 && (bt + 1) - y <= lim && wv.hole(x, bt + 1)) ++bt;
+      const bool endL = a - 1 >= 0 && !wv.hole(a - 1, y), endR = b + 1 <= W - 1 && !wv.hole(b + 1, y);
+      const bool endU = at - 1 >= 0 && !wv.hole(x, at - 1), endD = bt + 1 <= H - 1 && !wv.hole(x, bt + 1);
+      const int Lh = b - a + 1, Lv = bt - at + 1;
+      const bool gh = endL && endR && Lh <= gap, gv = endU && endD && Lv <= gap;
+      int axis = -1;
+      if (gh && gv) axis = Lv < Lh ? 1 : 0;
+      else if (gh) axis = 0;
+      else if (gv) axis = 1;
+      if (axis >= 0) {
+        c |= kClsGap;
+        float e0[3], e1[3];
+        float t;
+        if (axis == 0) {
+          wv.colour(a - 1, y, e0);
+          wv.colour(b + 1, y, e1);
+          t = (float)(x - (a - 1)) / (float)(b + 1 - (a - 1));
+        } else {
+          wv.colour(x, at - 1, e0);
+          wv.colour(x, bt + 1, e1);
+          t = (float)(y - (at - 1)) / (float)(bt + 1 - (at - 1));
+        }
+        for (int k = 0; k < 3; ++k) out[k] = fmaf(t, e1[k], fmaf(-t, e0[k], e0[k]));
+      } else {
+        c |= kClsCentre;
+        if (!center_enabled) {
+          // fallback fill along the row (full run), else the column
+          while (a - 1 >= 0 && wv.hole(a - 1, y)) --a;
+          while (b + 1 <= W - 1 && wv.hole(b + 1, y)) ++b;
+          const bool hl = a - 1 >= 0, hr = b + 1 <= W - 1;
+          int ex0 = -1, ey0 = -1, ex1 = -1, ey1 = -1;
+          float t = 0.f;
+          if (hl || hr) {
+            if (hl) { ex0 = a - 1; ey0 = y; }
+            if (hr) { ex1 = b + 1; ey1 = y; }
+            t = (float)(x - (a - 1)) / (float)(b + 1 - (a - 1));
+          } else {
+            while (at - 1 >= 0 && wv.hole(x, at - 1)) --at;
+            while (bt + 1 <= H - 1 && wv.hole(x, bt + 1)) ++bt;
+            if (at - 1 >= 0) { ex0 = x; ey0 = at - 1; }
+            if (bt + 1 <= H - 1) { ex1 = x; ey1 = bt + 1; }
+            t = (float)(y - (at - 1)) / (float)(bt + 1 - (at - 1));
+          }
+          float e0[3], e1[3];
+          if (ex0 >= 0 && ex1 >= 0) {
+            wv.colour(ex0, ey0, e0);
+            wv.colour(ex1, ey1, e1);
+            for (int k = 0; k < 3; ++k) out[k] = fmaf(t, e1[k], fmaf(-t, e0[k], e0[k]));
+          } else if (ex0 >= 0) {
+            wv.colour(ex0, ey0, out);
+          } else if (ex1 >= 0) {
+            wv.colour(ex1, ey1, out);
+          }
+        }
+      }
+    }
+    rgb_aff[p] = out[0];
+    rgb_aff[wv.hw + p] = out[1];
+    rgb_aff[2 * wv.hw + p] = out[2];
+    cls[p] = c;
+  }
+}
+
+// ---------------------------------------------------------------- centre ROIs (Step 2)
+//
+// Union-find labelling of the 4-connected centre-hole components; every root is
+// the component's smallest linear index (links always go from the larger root to
+// the smaller one), which also gives the canonical rectangle order.
+constexpr int kMaxUnionSteps = 1 << 22;
+
+__device__ __forceinline__ int find_root(const int32_t *L, int x) {
+  int steps = 0;
+  int p = __ldcg(L + x);
+  while (p != x && steps < kMaxUnionSteps) {
+    x = p;
+    p = __ldcg(L + x);
+    ++steps;
+  }
+  return x;
+}
+
+__device__ void unite(int32_t *L, int a, int b, uint32_t *status) {
+  for (int it = 0; it < kMaxUnionSteps; ++it) {
+    a = find_root(L, a);
+    b = find_root(L, b);
+    if (a == b) return;
+    if (a < b) {
+      const int t = a;
+      a = b;
+      b = t;
+    }
+    // link the larger root a below b; succeeds only if a is still a root
+    const int old = atomicMin(L + a, b);
+    if (old == a) return;
+    a = old;
+  }
+  atomicOr(status, kStTimeout);
+}
+
+__global__ void cc_init_kernel(const uint8_t *__restrict__ cls, int32_t *__restrict__ L, int64_t npix) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
+    L[p] = (cls[p] & kClsCentre) ? (int32_t)p : -1;
+}
+
+__global__ void cc_merge_kernel(const uint8_t *__restrict__ cls, int32_t *L, int W, int H, uint32_t *status) {
+  const int64_t npix = (int64_t)W * H;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    if (!(cls[p] & kClsCentre)) continue;
+    const int x = (int)(p % W);
+    if (x > 0 && (cls[p - 1] & kClsCentre)) unite(L, (int)p, (int)p - 1, status);
+    if (p >= W && (cls[p - W] & kClsCentre)) unite(L, (int)p, (int)(p - W), status);
+  }
+}
+
+__global__ void cc_flatten_kernel(int32_t *L, int64_t npix) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
+    if (L[p] >= 0) L[p] = find_root(L, (int)p);
+}
+
+struct RootLoad {
+  const int32_t *L;
+  __device__ uint32_t operator()(uint32_t p) const { return L[p] == (int32_t)p ? 1u : 0u; }
+};
+
+struct RootApply {
+  uint32_t *slots;
+  int4 *rects;
+  uint32_t cap;
+  Counters *ctr;
+  int W, H;
+  __device__ void operator()(uint32_t p, uint32_t prefix, uint32_t v) const {
+    if (!v) return;
+    slots[p] = prefix;
+    if (prefix < cap) rects[prefix] = make_int4(W, H, -1, -1);
+  }
+  __device__ void end(uint32_t, uint32_t total) const {
+    ctr->n_rects = total;
+    if (total > cap) atomicOr(&ctr->status, kStCapacity);
+  }
+};
+
+__global__ void cc_bbox_kernel(const int32_t *__restrict__ L, const uint32_t *__restrict__ slots, int4 *rects,
+                               uint32_t cap, int W, int64_t npix) {
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    const int r = L[p];
+    if (r < 0) continue;
+    const uint32_t s = slots[r];
+    if (s >= cap) continue;
+    const int x = (int)(p % W), y = (int)(p / W);
+    int *q = reinterpret_cast<int *>(rects + s);
+    atomicMin(q + 0, x);
+    atomicMin(q + 1, y);
+    atomicMax(q + 2, x);
+    atomicMax(q + 3, y);
+  }
+}
+
+// expand by m, align outward to tiles, clip; mark the tiles
+__global__ void cc_finalize_kernel(int4 *rects, const Counters *__restrict__ ctr, uint32_t cap, int W, int H, int m,
+                                   int tiles_x, int tiles_y, uint8_t *__restrict__ tile_mask) {
+  const uint32_t n = min(ctr->n_rects, cap);
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const int4 b = rects[s];
+    const int tx0 = b.x - m <= 0 ? 0 : (b.x - m) / kTile, ty0 = b.y - m <= 0 ? 0 : (b.y - m) / kTile;
+    const int tx1 = min((b.z + m) / kTile, tiles_x - 1), ty1 = min((b.w + m) / kTile, tiles_y - 1);
+    rects[s] = make_int4(tx0 * kTile, ty0 * kTile, min((tx1 + 1) * kTile, W), min((ty1 + 1) * kTile, H));
+    for (int ty = ty0; ty <= ty1; ++ty)
+      for (int tx = tx0; tx <= tx1; ++tx) tile_mask[ty * tiles_x + tx] = 1;
+  }
+}
+
+static int grid_for(int64_t n, int per_block = 256) {
+  const int64_t b = (n + per_block - 1) / per_block;
+  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
+                                 const float *rgb_dom, const float *depth_dom, const float *trans_dom,
+                                 float *rgb_aff, cudaStream_t s) {
+  cudaError_t err;
+  const int64_t npix = (int64_t)W * H;
+  const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+  if ((err = cudaMemsetAsync(ws.tile_mask, 0, (size_t)tiles_x * tiles_y, s)) != cudaSuccess) return err;
+  if ((err = cudaMemsetAsync(ws.warpbuf, 0xff, sizeof(unsigned long long) * (size_t)npix, s)) != cudaSuccess)
+    return err;
+  edge_roi_kernel<<<1, 256, 0, s>>>(ws.cams, ws.ctr, roi.samples_per_edge, roi.margin, roi.depth_mode, roi.d_min,
+                                    roi.d_max, ws.strips, ws.widths, ws.drange, ws.tile_mask);
+  warp_scatter_kernel<<<grid_for(npix), 256, 0, s>>>(ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H);
+  WarpView wv{ws.warpbuf, rgb_dom, W, H, (size_t)npix};
+  classify_kernel<<<grid_for(npix), 256, 0, s>>>(wv, ws.strips, gap_thresh, roi.enable_center, rgb_aff,
+                                                  ws.warp_depth, ws.cls);
+  GS_LAUNCHED(3);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cudaStream_t s) {
+  const int64_t npix = (int64_t)W * H;
+  const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+  cc_init_kernel<<<grid_for(npix), 256, 0, s>>>(ws.cls, ws.labels, npix);
+  cc_merge_kernel<<<grid_for(npix), 256, 0, s>>>(ws.cls, ws.labels, W, H, &ws.ctr->status);
+  cc_flatten_kernel<<<grid_for(npix), 256, 0, s>>>(ws.labels, npix);
+  const uint32_t cap = (uint32_t)ws.max_rects;
+  cudaError_t err = scan_launch(RootLoad{ws.labels}, RootApply{ws.slots, ws.rects, cap, ws.ctr, W, H},
+                                (const uint32_t *)nullptr, (uint32_t)npix, ws.scan_sums, nullptr, s);
+  if (err != cudaSuccess) return err;
+  cc_bbox_kernel<<<grid_for(npix), 256, 0, s>>>(ws.labels, ws.slots, ws.rects, cap, W, npix);
+  cc_finalize_kernel<<<grid_for(ws.max_rects), 256, 0, s>>>(ws.rects, ws.ctr, cap, W, H, margin, tiles_x, tiles_y,
+                                                             ws.tile_mask);
+  GS_LAUNCHED(5);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,275 @@
+"""Python binding of the C ABI in include/gs.h (ctypes; argument marshalling only).
+
+Every stage of the pipeline runs in libgs.so's CUDA kernels. PyTorch supplies the
+device memory (scene, outputs and the context workspace) and the CUDA stream.
+Importing this module loads the in-tree libgs.so and fails loudly when it is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgs.so")
+
+GS_OK, GS_ERR_BAD_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_WORKSPACE, GS_ERR_NOT_LOADED = range(7)
+(BUF_RECORDS, BUF_RECTS, BUF_BOUNDS, BUF_COUNTS, BUF_DEPTH_ORDER, BUF_INST_KEYS, BUF_INST_VALS, BUF_RANGES,
+ BUF_WARP, BUF_TILE_MASK, BUF_DEPTH_RANGE, BUF_STRIPS, BUF_WARP_DEPTH, BUF_PAIRS) = range(14)
+BUF_EYE1 = 0x100
+CLS_HOLE, CLS_GAP, CLS_CENTRE, CLS_STRIP, CLS_RENDER, CLS_NET = 1, 2, 4, 8, 16, 32
+
+
+class GsError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})")
+
+
+class Scene(C.Structure):
+    _fields_ = [("pos", C.c_void_p), ("quat", C.c_void_p), ("scale", C.c_void_p), ("opacity", C.c_void_p),
+                ("sh", C.c_void_p), ("n", C.c_int), ("sh_degree", C.c_int)]
+
+
+class Pose(C.Structure):
+    _fields_ = [("R", C.c_double * 9), ("t", C.c_double * 3)]
+
+
+class Intrinsics(C.Structure):
+    _fields_ = [("fx", C.c_double), ("fy", C.c_double), ("cx", C.c_double), ("cy", C.c_double),
+                ("width", C.c_int), ("height", C.c_int)]
+
+
+class RoiParams(C.Structure):
+    _fields_ = [("margin", C.c_int), ("samples_per_edge", C.c_int), ("enable_center", C.c_int),
+                ("depth_mode", C.c_int), ("d_min", C.c_float), ("d_max", C.c_float),
+                ("repair_mode", C.c_int), ("gate_tau", C.c_float)]
+
+
+class Outputs(C.Structure):
+    _fields_ = [("rgb_dom", C.c_void_p), ("depth_dom", C.c_void_p), ("trans_dom", C.c_void_p),
+                ("rgb_aff", C.c_void_p), ("cls_aff", C.c_void_p), ("roi_rects", C.c_void_p),
+                ("roi_count", C.c_void_p), ("edge_widths", C.c_void_p)]
+
+
+class Limits(C.Structure):
+    _fields_ = [("max_surfels", C.c_int), ("max_width", C.c_int), ("max_height", C.c_int),
+                ("max_instances", C.c_int64), ("max_rects", C.c_int), ("keep_intermediates", C.c_int)]
+
+
+EXPORTS = {
+    "gs_status_str": (C.c_char_p, [C.c_int]),
+    "gs_kernel_launches": (C.c_ulonglong, []),
+    "gs_workspace_size": (C.c_int, [C.POINTER(Limits), C.POINTER(C.c_size_t)]),
+    "gs_context_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Limits), C.c_void_p, C.c_size_t, C.c_void_p]),
+    "gs_context_destroy": (C.c_int, [C.c_void_p]),
+    "gs_context_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "gs_context_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "gs_context_set_counting": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_context_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_context_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
+    "gs_context_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t),
+                                    C.POINTER(C.c_int64)]),
+    "gs_render_mono": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Intrinsics),
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_render_stereo": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Pose),
+                                   C.POINTER(Intrinsics), C.c_int, C.POINTER(RoiParams), C.POINTER(Outputs)]),
+    "gs_render_two_pass": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Pose),
+                                     C.POINTER(Intrinsics), C.POINTER(Outputs)]),
+}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with paper_2609_30741_gb300.build.build() "
+                              "(there is no CPU fallback)")
+        lib_ = C.CDLL(LIB_PATH)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(lib_, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib_
+    return _lib
+
+
+def kernel_launches() -> int:
+    """Kernels libgs.so has enqueued since it was loaded."""
+    return int(lib().gs_kernel_launches())
+
+
+def status_str(s: int) -> str:
+    return lib().gs_status_str(int(s)).decode()
+
+
+def _check(s, what):
+    if s != GS_OK:
+        raise GsError(s, what)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def pose_struct(pose) -> Pose:
+    import numpy as np
+    return Pose((C.c_double * 9)(*np.asarray(pose.R, np.float64).ravel()),
+                (C.c_double * 3)(*np.asarray(pose.t, np.float64).ravel()))
+
+
+def intr_struct(cam) -> Intrinsics:
+    return Intrinsics(cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height)
+
+
+def roi_params(margin=32, samples_per_edge=32, enable_center=1, depth_mode=0, d_min=0.0, d_max=0.0,
+               repair_mode=0, gate_tau=0.5) -> RoiParams:
+    return RoiParams(margin, samples_per_edge, enable_center, depth_mode, d_min, d_max, repair_mode, gate_tau)
+
+
+class DeviceScene:
+    """Surfel attributes resident on the GPU (torch tensors) + the C struct."""
+
+    def __init__(self, scene, device="cuda"):
+        def t(a):
+            return torch.as_tensor(a).to(device=device, dtype=torch.float32).contiguous()
+        self.pos, self.quat, self.scale = t(scene.pos), t(scene.quat), t(scene.scale)
+        self.opacity, self.sh = t(scene.opacity), t(scene.sh)
+        self.n, self.sh_degree = int(scene.n), int(scene.sh_degree)
+        self.c = Scene(self.pos.data_ptr(), self.quat.data_ptr(), self.scale.data_ptr(),
+                       self.opacity.data_ptr(), self.sh.data_ptr(), self.n, self.sh_degree)
+
+    def nbytes(self):
+        return sum(x.numel() * 4 for x in (self.pos, self.quat, self.scale, self.opacity, self.sh))
+
+
+class Context:
+    """A renderer context: owns its workspace tensor, runs on a torch stream."""
+
+    def __init__(self, max_surfels, max_width, max_height, max_instances=1 << 24, max_rects=1 << 16,
+                 keep_intermediates=False, device="cuda", stream=None):
+        self.lim = Limits(int(max_surfels), int(max_width), int(max_height), int(max_instances),
+                          int(max_rects), int(bool(keep_intermediates)))
+        nbytes = C.c_size_t()
+        _check(lib().gs_workspace_size(C.byref(self.lim), C.byref(nbytes)), "gs_workspace_size")
+        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        off = (-base) % 256
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = C.c_void_p()
+        _check(lib().gs_context_create(C.byref(h), C.byref(self.lim), C.c_void_p(base + off),
+                                       C.c_size_t(nbytes.value), C.c_void_p(self.stream.cuda_stream)),
+               "gs_context_create")
+        self.h = h
+        self.ws_offset = off
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self.stream = stream
+        _check(lib().gs_context_set_stream(self.h, C.c_void_p(stream.cuda_stream)), "gs_context_set_stream")
+
+    def set_counting(self, on: bool):
+        _check(lib().gs_context_set_counting(self.h, int(bool(on))), "gs_context_set_counting")
+
+    def set_profiling(self, on: bool):
+        _check(lib().gs_context_set_profiling(self.h, int(bool(on))), "gs_context_set_profiling")
+
+    def stage_times(self):
+        buf = (C.c_float * 16)()
+        n = C.c_int()
+        _check(lib().gs_context_stage_times(self.h, buf, 16, C.byref(n)), "gs_context_stage_times")
+        return [buf[i] for i in range(n.value)]
+
+    def pair_counts(self):
+        """(evaluated[2], contributed[2]) pairs of the last call in counting mode."""
+        v, _ = self.buffer(BUF_PAIRS, torch.int64)
+        a = v[:4].cpu().tolist()
+        return a[:2], a[2:]
+
+    def check(self) -> int:
+        st = C.c_int()
+        _check(lib().gs_context_check(self.h, C.byref(st)), "gs_context_check")
+        return st.value
+
+    def check_ok(self):
+        st = self.check()
+        if st != GS_OK:
+            raise GsError(st, "device status")
+
+    def buffer(self, which, dtype, shape=None, eye=0):
+        """A torch view of a workspace intermediate (see gs_buffer_id)."""
+        p, nb, cnt = C.c_void_p(), C.c_size_t(), C.c_int64()
+        _check(lib().gs_context_buffer(self.h, which | (BUF_EYE1 if eye else 0), C.byref(p), C.byref(nb),
+                                       C.byref(cnt)), "gs_context_buffer")
+        start = p.value - self.workspace.data_ptr()
+        raw = self.workspace[start:start + nb.value]
+        v = raw.view(dtype)
+        if shape is not None:
+            v = v.view(*shape)
+        return v, cnt.value
+
+    # ---------------------------------------------------------------- entry points
+
+    def render_mono(self, scene: DeviceScene, pose, cam, bg=None, out=None):
+        H, W = cam.height, cam.width
+        if out is None:
+            out = (torch.empty(3, H, W, device=self.device), torch.empty(H, W, device=self.device),
+                   torch.empty(H, W, device=self.device))
+        rgb, dep, tr = out
+        bgp = (C.c_float * 3)(*bg) if bg is not None else None
+        _check(lib().gs_render_mono(self.h, C.byref(scene.c), C.byref(pose_struct(pose)),
+                                    C.byref(intr_struct(cam)), C.cast(bgp, C.c_void_p) if bgp else None,
+                                    _ptr(rgb), _ptr(dep), _ptr(tr)), "gs_render_mono")
+        return rgb, dep, tr
+
+    def alloc_outputs(self, cam, with_cls=True):
+        H, W = cam.height, cam.width
+        d = self.device
+        o = dict(rgb_dom=torch.empty(3, H, W, device=d), depth_dom=torch.empty(H, W, device=d),
+                 trans_dom=torch.empty(H, W, device=d), rgb_aff=torch.empty(3, H, W, device=d))
+        if with_cls:
+            o.update(cls_aff=torch.empty(H, W, dtype=torch.uint8, device=d),
+                     roi_rects=torch.empty(self.lim.max_rects, 4, dtype=torch.int32, device=d),
+                     roi_count=torch.zeros(1, dtype=torch.int32, device=d),
+                     edge_widths=torch.zeros(4, dtype=torch.int32, device=d))
+        return o
+
+    @staticmethod
+    def _outputs_struct(o):
+        return Outputs(*[(o[k].data_ptr() if o.get(k) is not None else None) for k in
+                         ("rgb_dom", "depth_dom", "trans_dom", "rgb_aff", "cls_aff", "roi_rects", "roi_count",
+                          "edge_widths")])
+
+    def render_stereo(self, scene: DeviceScene, pose_dom, pose_aff, cam, gap_thresh=2, roi=None, out=None):
+        if out is None:
+            out = self.alloc_outputs(cam)
+        roi = roi if roi is not None else roi_params()
+        os_ = self._outputs_struct(out)
+        _check(lib().gs_render_stereo(self.h, C.byref(scene.c), C.byref(pose_struct(pose_dom)),
+                                      C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), int(gap_thresh),
+                                      C.byref(roi), C.byref(os_)), "gs_render_stereo")
+        return out
+
+    def render_two_pass(self, scene: DeviceScene, pose_dom, pose_aff, cam, out=None):
+        if out is None:
+            out = self.alloc_outputs(cam, with_cls=False)
+        os_ = self._outputs_struct(out)
+        _check(lib().gs_render_two_pass(self.h, C.byref(scene.c), C.byref(pose_struct(pose_dom)),
+                                        C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), C.byref(os_)),
+               "gs_render_two_pass")
+        return out

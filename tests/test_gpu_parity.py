@@ -1,0 +1,421 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP32 images within max-abs 2e-4 per RGB channel and 1e-4 relative
+depth (on pixels whose decisions are not within the margin of a threshold; the
+excluded pixels are counted and must stay below 0.1%). Integer stages (tile
+rectangles, sorted instance lists, hole masks, gap classes, ROI rectangles) are
+bit-exact when the oracle is fed the same inputs as the GPU stage.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_30741_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RGB_TOL = 2e-4
+DEPTH_RTOL = 1e-4
+MARGIN = 1e-5          # relative distance of a decision to its threshold
+MAX_MARGINAL = 1e-3    # fraction of pixels allowed to be excluded
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30741_gb300 import build
+    build.build()
+    from paper_2609_30741_gb300 import gs as gsmod
+    return gsmod
+
+
+def _np(t):
+    return t.detach().double().cpu().numpy()
+
+
+def compare_render(g_rgb, g_dep, g_tr, o_rgb, o_dep, o_tr, margin, what=""):
+    """Depth is compared relative to max(|D|, 1e-3 * d_max): the float32 sum of
+    weighted depths carries an absolute error of about 1e-7 of the depth range,
+    so pixels with almost no coverage (D -> 0) are judged on that floor."""
+    ok = margin >= MARGIN
+    frac = 1.0 - ok.mean()
+    assert frac <= MAX_MARGINAL, f"{what}: {frac:.4%} marginal pixels"
+    e_rgb_map = np.abs(g_rgb - o_rgb).max(0)
+    cov = 1.0 - o_tr
+    dnorm = np.where(cov > 1e-3, o_dep / np.maximum(cov, 1e-3), 0.0)
+    floor = 1e-3 * max(float(dnorm.max(initial=0.0)), 1e-3)
+    e_dep_map = np.abs(g_dep - o_dep) / np.maximum(np.abs(o_dep), floor)
+    e_tr_map = np.abs(g_tr - o_tr)
+
+    def worst(m):
+        mm = np.where(ok, m, -1.0)
+        idx = np.unravel_index(np.argmax(mm), mm.shape)
+        return (f"at (y, x) = {idx}: gpu rgb {g_rgb[(slice(None),) + idx]}, oracle {o_rgb[(slice(None),) + idx]}, "
+                f"gpu D {g_dep[idx]:.8g}, oracle D {o_dep[idx]:.8g}, T {o_tr[idx]:.6g} / {g_tr[idx]:.6g}, "
+                f"margin {margin[idx]:.3g}")
+
+    e_rgb = e_rgb_map[ok].max(initial=0.0)
+    e_dep = e_dep_map[ok].max(initial=0.0)
+    e_tr = e_tr_map[ok].max(initial=0.0)
+    assert e_rgb <= RGB_TOL, f"{what}: rgb max-abs {e_rgb} {worst(e_rgb_map)}"
+    assert e_dep <= DEPTH_RTOL, f"{what}: depth rel {e_dep} {worst(e_dep_map)}"
+    assert e_tr <= RGB_TOL, f"{what}: transmittance max-abs {e_tr} {worst(e_tr_map)}"
+    return e_rgb, e_dep, frac
+
+
+def make_ctx(gs, scene, cam, **kw):
+    kw.setdefault("max_instances", 1 << 22)
+    return gs.Context(max(scene.n, 1), cam.width, cam.height, **kw)
+
+
+# ----------------------------------------------------------------------------- Stage 1
+
+
+@pytest.mark.parametrize("which", ["small", "small_ragged", "random_sh3"])
+def test_mono_render_matches_oracle(gs, orc, which):
+    if which == "small":
+        scene, cam, dom, _ = synth.workload_small()
+    elif which == "small_ragged":
+        scene, cam, dom, _ = synth.workload_small()
+        cam = synth.centred_camera(250, 171, 300.0)  # ragged tiles on both axes
+    else:
+        scene = synth.random_scene(17, 3000, sh_degree=3, z_range=(1.0, 5.0), scale_mu=math.log(0.04))
+        cam = synth.centred_camera(200, 136, 180.0)
+        dom = synth.look_at((0.2, -0.1, -0.3), (0.0, 0.0, 3.0))
+    ctx = make_ctx(gs, scene, cam)
+    ds = gs.DeviceScene(scene)
+    rgb, dep, tr = ctx.render_mono(ds, dom, cam, bg=(0.1, 0.2, 0.3))
+    ctx.check_ok()
+    o_rgb, o_dep, o_tr, mrg, _ = orc.render(scene, dom, cam, bg=(0.1, 0.2, 0.3))
+    compare_render(_np(rgb), _np(dep), _np(tr), o_rgb, o_dep, o_tr, mrg, which)
+
+
+def test_tile_rects_and_counts_bit_exact(gs, orc):
+    scene, cam, dom, aff = synth.workload_small()
+    ctx = make_ctx(gs, scene, cam, keep_intermediates=True)
+    ds = gs.DeviceScene(scene)
+    ctx.render_two_pass(ds, dom, aff, cam)
+    ctx.check_ok()
+    for eye in (0, 1):
+        bounds, _ = ctx.buffer(gs.BUF_BOUNDS, torch.float32, (-1, 4), eye=eye)
+        rects, _ = ctx.buffer(gs.BUF_RECTS, torch.int16, (-1, 4), eye=eye)
+        counts, _ = ctx.buffer(gs.BUF_COUNTS, torch.int32, None, eye=eye)
+        b = bounds[: scene.n].cpu().numpy()
+        r = rects[: scene.n].cpu().numpy().astype(np.int32)
+        c = counts[: scene.n].cpu().numpy()
+        sp = orc.prepare(scene, [dom, aff][eye], cam)
+        vis = np.array([s.visible for s in sp], bool)
+        nz = c > 0
+        assert not (nz & ~vis).any(), "GPU bins a surfel the oracle culls"
+        for i in np.where(nz)[0]:
+            rr, cc = orc.tile_rect(b[i], cam.width, cam.height)
+            assert cc == c[i] and list(rr) == list(r[i]), i
+        # the FP32 bounds enclose the oracle's FP64 support boxes
+        for i in np.where(nz)[0][:2000]:
+            bx = sp[i].box
+            assert b[i, 0] <= bx[0] + 1e-3 and b[i, 1] >= bx[1] - 1e-3
+            assert b[i, 2] <= bx[2] + 1e-3 and b[i, 3] >= bx[3] - 1e-3
+
+
+def test_sorted_instances_bit_exact(gs, orc):
+    scene, cam, dom, _ = synth.workload_small()
+    ctx = make_ctx(gs, scene, cam)
+    ds = gs.DeviceScene(scene)
+    ctx.render_mono(ds, dom, cam)
+    ctx.check_ok()
+    rects, _ = ctx.buffer(gs.BUF_RECTS, torch.int16, (-1, 4))
+    counts, _ = ctx.buffer(gs.BUF_COUNTS, torch.int32, None)
+    recs, _ = ctx.buffer(gs.BUF_RECORDS, torch.float32, (-1, 16))
+    keys, nk = ctx.buffer(gs.BUF_INST_KEYS, torch.int32, None)
+    vals, _ = ctx.buffer(gs.BUF_INST_VALS, torch.int32, None)
+    ranges, _ = ctx.buffer(gs.BUF_RANGES, torch.int32, (-1, 2))
+    r = rects[: scene.n].cpu().numpy().astype(np.int64)
+    c = counts[: scene.n].cpu().numpy()
+    zbits = recs[: scene.n, 3].contiguous().view(torch.int32).cpu().numpy().astype(np.uint32)
+    tiles_x = (cam.width + 15) // 16
+    k_list, v_list = [], []
+    for i in np.where(c > 0)[0]:
+        for ty in range(r[i, 1], r[i, 3] + 1):
+            for tx in range(r[i, 0], r[i, 2] + 1):
+                k_list.append((np.uint64(ty * tiles_x + tx) << np.uint64(32)) | np.uint64(zbits[i]))
+                v_list.append(i)
+    ok_, ov = orc.sort_pairs(np.array(k_list, np.uint64), np.array(v_list, np.uint32))
+    assert nk == len(ok_)
+    gk = keys[:nk].cpu().numpy().astype(np.uint32)
+    gv = vals[:nk].cpu().numpy().astype(np.uint32)
+    assert np.array_equal(gk.astype(np.uint64), ok_ >> np.uint64(32))
+    assert np.array_equal(gv, ov)
+    rg = ranges.cpu().numpy()
+    t = (ok_ >> np.uint64(32)).astype(np.int64)
+    for tile in range(rg.shape[0]):
+        idx = np.where(t == tile)[0]
+        if idx.size:
+            assert rg[tile, 0] == idx[0] and rg[tile, 1] == idx[-1] + 1
+        else:
+            assert rg[tile, 0] == rg[tile, 1]
+
+
+def test_empty_and_culled_scenes(gs):
+    cam = synth.centred_camera(64, 48, 100.0)
+    ctx = gs.Context(16, 64, 48, max_instances=1 << 12)
+    empty = synth.Scene(np.zeros((0, 4), np.float32), np.zeros((0, 4), np.float32), np.zeros((0, 2), np.float32),
+                        np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0)
+    ds = gs.DeviceScene(empty)
+    rgb, dep, tr = ctx.render_mono(ds, synth.identity_pose(), cam, bg=(0.25, 0.5, 0.75))
+    ctx.check_ok()
+    assert torch.all(tr == 1) and torch.all(dep == 0)
+    assert torch.allclose(rgb[:, 5, 5].cpu(), torch.tensor([0.25, 0.5, 0.75]))
+    behind = synth.random_scene(3, 16, z_range=(-3.0, -1.0))
+    rgb, dep, tr = ctx.render_mono(gs.DeviceScene(behind), synth.identity_pose(), cam)
+    ctx.check_ok()
+    assert torch.all(tr == 1)
+    out = ctx.render_stereo(ds, *synth.eye_pair(synth.identity_pose()), cam)
+    ctx.check_ok()
+    assert torch.all(out["rgb_aff"] == 0)
+
+
+def test_capacity_overflow_is_reported(gs):
+    scene, cam, dom, _ = synth.workload_small()
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1000)
+    ctx.render_mono(gs.DeviceScene(scene), dom, cam)
+    assert ctx.check() == gs.GS_ERR_CAPACITY
+    assert ctx.check() == gs.GS_OK  # cleared by the read
+
+
+def test_bad_arguments_are_rejected(gs):
+    scene, cam, dom, aff = synth.workload_small()
+    ctx = gs.Context(100, 64, 64, max_instances=1 << 12)
+    ds = gs.DeviceScene(scene)  # n = 20000 > max_surfels
+    with pytest.raises(gs.GsError) as e:
+        ctx.render_mono(ds, dom, synth.centred_camera(64, 64, 100.0))
+    assert e.value.status == gs.GS_ERR_BAD_ARG
+    small = gs.DeviceScene(scene.subset(np.arange(50)))
+    with pytest.raises(gs.GsError):
+        ctx.render_mono(small, dom, synth.centred_camera(128, 64, 100.0))  # wider than the context
+    with pytest.raises(gs.GsError):
+        ctx.render_stereo(small, dom, aff, synth.centred_camera(64, 64, 100.0), roi=gs.roi_params(samples_per_edge=1))
+
+
+# ----------------------------------------------------------------------------- Stages 2-4
+
+
+@pytest.fixture(scope="module")
+def stereo_small(gs):
+    scene, cam, dom, aff = synth.workload_small()
+    ctx = make_ctx(gs, scene, cam)
+    ds = gs.DeviceScene(scene)
+    out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
+    ctx.check_ok()
+    warp, _ = ctx.buffer(gs.BUF_WARP, torch.int64, None)
+    npix = cam.width * cam.height
+    strips, _ = ctx.buffer(gs.BUF_STRIPS, torch.int32, (4, 4))
+    drange, _ = ctx.buffer(gs.BUF_DEPTH_RANGE, torch.float32, None)
+    tmask, _ = ctx.buffer(gs.BUF_TILE_MASK, torch.uint8, None)
+    wd, _ = ctx.buffer(gs.BUF_WARP_DEPTH, torch.float32, None)
+    snap = dict(out={k: v.clone() for k, v in out.items()},
+                warp=warp[:npix].clone().cpu().numpy().view(np.uint64).reshape(cam.height, cam.width),
+                strips=strips.cpu().numpy().copy(), drange=drange[:2].cpu().numpy().copy(),
+                tmask=tmask[: ((cam.width + 15) // 16) * ((cam.height + 15) // 16)].cpu().numpy().copy(),
+                warp_depth=wd[:npix].cpu().numpy().reshape(cam.height, cam.width).copy())
+    return dict(scene=scene, cam=cam, dom=dom, aff=aff, ctx=ctx, ds=ds, **snap)
+
+
+def test_stereo_dominant_eye_matches_oracle(stereo_small, orc):
+    s = stereo_small
+    o_rgb, o_dep, o_tr, mrg, _ = orc.render(s["scene"], s["dom"], s["cam"])
+    o = s["out"]
+    compare_render(_np(o["rgb_dom"]), _np(o["depth_dom"]), _np(o["trans_dom"]), o_rgb, o_dep, o_tr, mrg, "dom")
+
+
+def test_warp_matches_oracle_on_gpu_depth(stereo_small, orc):
+    """The oracle warp fed the GPU's dominant RGB, depth proxy and transmittance
+    gives the same winner at every destination pixel whose sources are not within
+    1e-4 px of a rounding boundary and whose depth keys are not within 4 ulp."""
+    s = stereo_small
+    cam, o = s["cam"], s["out"]
+    W, H = cam.width, cam.height
+    w = orc.warp(cam, s["dom"], s["aff"], _np(o["rgb_dom"]), _np(o["depth_dom"]), _np(o["trans_dom"]))
+    g = s["warp"]
+    g_hole = g == np.uint64(0xFFFFFFFFFFFFFFFF)
+    g_src = np.where(g_hole, -1, (g & np.uint64(0xFFFFFFFF)).astype(np.int64))
+    # destinations touched by a marginal source, or with a near-tie in depth
+    marg = np.zeros(W * H, bool)
+    tg, tm, zk = w["tgt"], w["tmargin"], w["zkey"]
+    bad_src = (tg >= 0) & (tm < 1e-4)
+    for sidx in np.where(bad_src)[0]:
+        x, y = sidx % W, sidx // W
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                xx, yy = int(tg[sidx] % W) + dx, int(tg[sidx] // W) + dy
+                if 0 <= xx < W and 0 <= yy < H:
+                    marg[yy * W + xx] = True
+    zbits = zk.view(np.uint32).astype(np.int64)
+    order = np.lexsort((zbits, tg))
+    tg_s, zb_s = tg[order], zbits[order]
+    same = (tg_s[1:] == tg_s[:-1]) & (tg_s[1:] >= 0)
+    near = same & (np.abs(zb_s[1:] - zb_s[:-1]) <= 4)
+    marg[tg_s[1:][near]] = True
+    marg = marg.reshape(H, W)
+    assert marg.mean() < 0.01
+    ok = ~marg
+    assert np.array_equal(g_hole[ok], w["hole"].astype(bool)[ok])
+    assert np.array_equal(g_src[ok], w["winner"][ok])
+    # warped depth is the winner's depth (float32 arithmetic vs float64 rounded
+    # to float32: a few ulp apart)
+    wz = s["warp_depth"]
+    valid = ok & ~g_hole
+    np.testing.assert_allclose(wz[valid], w["zdst"][valid], rtol=2e-6)
+    assert np.array_equal(np.isinf(wz[valid]), np.isinf(w["zdst"][valid]))
+
+
+def test_edge_roi_bit_exact_given_depth_range(stereo_small, orc):
+    s = stereo_small
+    cam = s["cam"]
+    dmin, dmax = float(s["drange"][0]), float(s["drange"][1])
+    o = s["out"]
+    o_min, o_max, _ = orc.depth_range(_np(o["depth_dom"]), _np(o["trans_dom"]))
+    assert abs(o_min - dmin) <= 1e-5 * o_min and abs(o_max - dmax) <= 1e-5 * o_max
+    widths, strips, mrg = orc.edge_roi(cam, s["dom"], s["aff"], dmin, dmax, nsamples=32, m=32)
+    assert mrg > 1e-4
+    assert list(widths) == list(o["edge_widths"].cpu().numpy())
+    assert np.array_equal(strips, s["strips"])
+
+
+def test_classification_bit_exact_given_warp(stereo_small, orc):
+    s = stereo_small
+    cam, o = s["cam"], s["out"]
+    g = s["warp"]
+    hole = (g == np.uint64(0xFFFFFFFFFFFFFFFF)).astype(np.uint8)
+    src = np.where(hole.astype(bool), 0, (g & np.uint64(0xFFFFFFFF)).astype(np.int64)).ravel()
+    rgb_dom = _np(o["rgb_dom"]).reshape(3, -1)
+    warped = rgb_dom[:, src].reshape(3, cam.height, cam.width) * (1 - hole)[None]
+    sm = orc.strip_mask(s["strips"], cam.width, cam.height)
+    cls, filled = orc.classify(hole, warped, sm, gap_thresh=2, center_enabled=1)
+    g_cls = o["cls_aff"].cpu().numpy()
+    assert np.array_equal(g_cls & 15, cls)
+    rend = (g_cls & 16) > 0
+    g_aff = _np(o["rgb_aff"])
+    np.testing.assert_allclose(g_aff[:, ~rend], filled[:, ~rend], atol=1e-6)
+    assert (cls & 2).any() and (cls & 4).any()
+
+
+def test_centre_rois_bit_exact_given_classes(stereo_small, orc):
+    s = stereo_small
+    o = s["out"]
+    g_cls = o["cls_aff"].cpu().numpy()
+    rects, n = orc.center_rois(g_cls & 15, m=32, tile=16)
+    assert int(o["roi_count"].item()) == n and n > 0
+    assert np.array_equal(o["roi_rects"][:n].cpu().numpy(), rects)
+    # tile mask = strips + rects
+    cam = s["cam"]
+    tx, ty = (cam.width + 15) // 16, (cam.height + 15) // 16
+    tm = np.zeros((ty, tx), np.uint8)
+    for x0, y0, x1, y1 in list(s["strips"]) + list(rects):
+        if x1 > x0 and y1 > y0:
+            tm[y0 // 16:(y1 - 1) // 16 + 1, x0 // 16:(x1 - 1) // 16 + 1] = 1
+    assert np.array_equal(tm.ravel(), s["tmask"])
+
+
+def test_roi_tiles_equal_the_full_affiliated_render(gs, stereo_small):
+    """Per-tile blending is independent of other tiles, so the ROI re-render gives
+    exactly the two-pass affiliated pixels on every ROI tile (same kernels)."""
+    s = stereo_small
+    ctx2 = make_ctx(gs, s["scene"], s["cam"])
+    tp = ctx2.render_two_pass(s["ds"], s["dom"], s["aff"], s["cam"])
+    ctx2.check_ok()
+    o = s["out"]
+    rend = (o["cls_aff"] & 16) > 0
+    assert torch.equal(o["rgb_aff"][:, rend], tp["rgb_aff"][:, rend])
+    assert torch.equal(o["rgb_dom"], tp["rgb_dom"])
+
+
+def test_roi_render_matches_oracle(stereo_small, orc):
+    s = stereo_small
+    cam = s["cam"]
+    o_rgb, o_dep, o_tr, mrg, _ = orc.render(s["scene"], s["aff"], cam)
+    o = s["out"]
+    rend = ((o["cls_aff"] & 16) > 0).cpu().numpy()
+    ok = rend & (mrg >= MARGIN)
+    assert (rend & (mrg < MARGIN)).sum() <= MAX_MARGINAL * rend.size
+    err = np.abs(_np(o["rgb_aff"]) - o_rgb)[:, ok].max()
+    assert err <= RGB_TOL
+
+
+def test_stereo_end_to_end_against_oracle(stereo_small, orc):
+    """Whole method vs the oracle's own pipeline: images agree within tolerance on
+    every pixel whose class (and tile) agrees; almost all pixels agree."""
+    s = stereo_small
+    ref = orc.stereo(s["scene"], s["dom"], s["aff"], s["cam"], gap_thresh=2)
+    o = s["out"]
+    g_cls = o["cls_aff"].cpu().numpy()
+    same = g_cls == ref["cls"]
+    assert same.mean() > 0.99
+    assert np.array_equal(ref["widths"], o["edge_widths"].cpu().numpy())
+    err = np.abs(_np(o["rgb_aff"]) - ref["rgb_aff"])[:, same]
+    assert np.quantile(err, 0.999) <= RGB_TOL
+
+
+def test_identity_pose_stereo_is_identity(gs):
+    scene, cam, dom, _ = synth.workload_small()
+    ctx = make_ctx(gs, scene, cam)
+    out = ctx.render_stereo(gs.DeviceScene(scene), dom, dom, cam)
+    ctx.check_ok()
+    assert int(out["roi_count"].item()) == 0
+    assert list(out["edge_widths"].cpu().numpy()) == [0, 0, 0, 0]
+    assert torch.equal(out["rgb_aff"], out["rgb_dom"])
+
+
+def test_centre_step_off_fills_every_hole(gs, orc, stereo_small):
+    s = stereo_small
+    ctx = make_ctx(gs, s["scene"], s["cam"])
+    out = ctx.render_stereo(s["ds"], s["dom"], s["aff"], s["cam"], roi=gs.roi_params(enable_center=0))
+    ctx.check_ok()
+    ref = orc.stereo(s["scene"], s["dom"], s["aff"], s["cam"], enable_center=0)
+    g_cls = out["cls_aff"].cpu().numpy()
+    same = g_cls == ref["cls"]
+    assert same.mean() > 0.99
+    err = np.abs(_np(out["rgb_aff"]) - ref["rgb_aff"])[:, same]
+    assert np.quantile(err, 0.999) <= RGB_TOL
+
+
+# ----------------------------------------------------------------------------- full size
+
+
+@pytest.fixture(scope="module")
+def object_scene(gs):
+    scene, cam, dom, aff = synth.workload_object()
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 26)
+    ds = gs.DeviceScene(scene)
+    out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
+    ctx.check_ok()
+    return dict(scene=scene, cam=cam, dom=dom, aff=aff, ctx=ctx, ds=ds, out=out)
+
+
+def test_full_size_sampled_pixels_match_oracle(object_scene, orc):
+    """1600x1200, 500k surfels: 64x64 windows in the dense centre and at a corner,
+    computed by the oracle pixel by pixel."""
+    s = object_scene
+    o = s["out"]
+    for (x0, y0) in [(768, 568), (0, 0), (1536, 1136), (400, 1000)]:
+        win = (x0, y0, 64, 64)
+        o_rgb, o_dep, o_tr, mrg, _ = orc.render(s["scene"], s["dom"], s["cam"], window=win)
+        sl = (slice(y0, y0 + 64), slice(x0, x0 + 64))
+        compare_render(_np(o["rgb_dom"][:, sl[0], sl[1]]), _np(o["depth_dom"][sl]), _np(o["trans_dom"][sl]),
+                       o_rgb, o_dep, o_tr, mrg, f"window {win}")
+
+
+def test_full_size_two_pass_agrees_on_roi_tiles(gs, object_scene):
+    s = object_scene
+    ctx2 = gs.Context(s["scene"].n, s["cam"].width, s["cam"].height, max_instances=1 << 26)
+    tp = ctx2.render_two_pass(s["ds"], s["dom"], s["aff"], s["cam"])
+    ctx2.check_ok()
+    o = s["out"]
+    rend = (o["cls_aff"] & 16) > 0
+    assert torch.equal(o["rgb_aff"][:, rend], tp["rgb_aff"][:, rend])
+    # the method's affiliated eye against the full render (quality, reported)
+    mse = torch.mean((o["rgb_aff"] - tp["rgb_aff"]) ** 2).item()
+    psnr = 10 * math.log10(1.0 / max(mse, 1e-12))
+    assert psnr > 20.0
