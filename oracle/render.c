@@ -245,12 +245,14 @@ static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_
     double dep, rho3, rho2;
     const double oG = or_eval(s, cam, x, y, &dep, &rho3, &rho2);
     ++pairs;
-    /* margins: only decisions whose flip can move the result by more than ~1e-5 */
-    if (T >= 0.01) mrg = fmin(mrg, fabs(oG * 255.0 - 1.0));
+    /* margins of the skip and stop decisions, at any transmittance: a flip adds
+     * or drops a weight alpha T, and a deep surfel behind a near one moves the
+     * depth proxy by alpha T d, relatively more than the colour */
+    mrg = fmin(mrg, fabs(oG * 255.0 - 1.0));
     const double a = oG < OR_ALPHA_MAX ? oG : OR_ALPHA_MAX;
     if (a < OR_ALPHA_MIN) continue;
     const double Tn = T * (1.0 - a);
-    if (T >= 1e-3) mrg = fmin(mrg, fabs(Tn - OR_T_MIN) / OR_T_MIN);
+    mrg = fmin(mrg, fabs(Tn - OR_T_MIN) / OR_T_MIN);
     if (Tn < OR_T_MIN) break;
     const double w = a * T;
     if (isfinite(rho3) && w * fabs(dep - s->pc[2]) > 1e-5 * s->pc[2])
