@@ -111,7 +111,7 @@ typedef struct {
 typedef struct {
   int max_surfels;
   int max_width, max_height;
-  int64_t max_instances; /* (surfel, tile) pairs per eye; < 2^31 */
+  int64_t max_instances; /* (surfel, tile) pairs per eye; < 2^30 */
   int max_rects;         /* centre ROI rectangles */
   int keep_intermediates;/* 1: also store per-surfel float bounds for inspection */
 } gs_limits;
@@ -172,6 +172,8 @@ typedef enum {
   GS_BUF_STRIPS = 11,     /* int32[4][4]: edge strips x0, y0, x1, y1 (left, right, top, bottom) */
   GS_BUF_WARP_DEPTH = 12, /* float[pixels]: warped depth (+inf background, 0 hole) */
   GS_BUF_PAIRS = 13,      /* uint64[2]: evaluated (pixel, surfel) pairs per eye, when counting */
+  GS_BUF_BIN_COUNTS = 14, /* uint32[max_surfels]: tiles each surfel's support reaches in the
+                             last binning (within the ROI tile mask for the ROI pass) */
   GS_BUF_EYE1 = 0x100     /* OR into RECORDS/RECTS/BOUNDS/COUNTS for the affiliated eye */
 } gs_buffer_id;
 
@@ -181,6 +183,13 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
 /* 1: the blend kernels count evaluated (pixel, surfel) pairs, and those that
  * contributed, into GS_BUF_PAIRS (uint64 evaluated[2], contributed[2]). */
 gs_status gs_context_set_counting(gs_context *ctx, int enable);
+
+/* 1 (the default): the first call of an entry point with a given scene, image
+ * size, output set and parameters captures its kernels into a CUDA graph, and
+ * later calls only patch the poses into it and replay it on the context's
+ * stream. 0: every call enqueues its kernels one by one. Calls made while the
+ * context's stream is being captured by the caller always enqueue directly. */
+gs_status gs_context_set_graphs(gs_context *ctx, int enable);
 
 /* 1: record a CUDA event on the context's stream at every stage boundary of the
  * following calls (the paper reports a per-stage time breakdown, Sec. 4.5). */

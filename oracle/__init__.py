@@ -241,3 +241,23 @@ def stereo(scene, dom, aff, cam, gap_thresh=2, margin=32, nsamples=32, enable_ce
     return dict(rgb_dom=rgb_dom, depth_dom=dd, trans_dom=td, rgb_aff=rgb_aff, cls=cls,
                 widths=widths, rects=rects[: min(nrects.value, rect_cap)].copy(),
                 nrects=nrects.value, tile_mask=tmask)
+
+
+def support_pairs(scene, pose, cam, tile=16, cap=1 << 26):
+    """(surfel ids, tile ids) of every pair whose tile holds a pixel centre with
+    alpha >= 1/255, surfels in index order, tiles ascending per surfel."""
+    ref = _SceneRef(scene)
+    ids = np.zeros(cap, np.uint32)
+    tiles = np.zeros(cap, np.uint32)
+    lib().or_support_pairs.restype = C.c_int64
+    n = lib().or_support_pairs(C.byref(ref.s), C.byref(pose_struct(pose)), C.byref(cam_struct(cam)), tile,
+                               C.c_int64(cap), _p(ids), _p(tiles))
+    if n > cap:
+        raise ValueError("support_pairs: capacity too small")
+    return ids[:n].copy(), tiles[:n].copy()
+
+
+def tile_test(rec12, k, x0, x1, y0, y1):
+    r = np.ascontiguousarray(rec12, np.float32)
+    return bool(lib().or_tile_test(_p(r), C.c_double(k), C.c_double(x0), C.c_double(x1), C.c_double(y0),
+                                   C.c_double(y1)))

@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["render.c", "reproject.c", "repair.c"]
+SOURCES = ["render.c", "reproject.c", "tiles.c", "repair.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

@@ -106,6 +106,17 @@ int or_render_tiles(const or_scene *sc, const or_pose *pose, const or_cam *cam, 
  * tx1, ty1 inclusive; returns the tile count (0 if the bounds miss the image). */
 int or_tile_rect(const float bounds[4], int W, int H, int tile, int rect[4]);
 
+/* Every (surfel, tile) pair such that some pixel centre of the tile has
+ * alpha >= 1/255 (the minimal binning of a tile rasterizer). Returns the count;
+ * only the first cap pairs are written. */
+int64_t or_support_pairs(const or_scene *sc, const or_pose *pose, const or_cam *cam, int tile, int64_t cap,
+                         uint32_t *ids, uint32_t *tiles);
+
+/* Whether the rectangle [x0,x1]x[y0,y1] meets the support of a surfel given as a
+ * 12-float blend record (centre, log2 o, depth | 2x2 plane map | Az, Bz, Cz, _)
+ * with squared radius k (FP64 evaluation of float inputs). */
+int or_tile_test(const float rec[12], double k, double x0, double x1, double y0, double y1);
+
 /* Stable sort of (key, value) pairs by key (merge sort). */
 void or_sort_pairs(int64_t n, uint64_t *keys, uint32_t *vals);
 

@@ -5,6 +5,7 @@
 #include <new>
 
 #include "gs_internal.cuh"
+#include "gs_sort.cuh"
 
 namespace gs {
 
@@ -46,11 +47,17 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     ws.ikey[e] = c.take<uint32_t>(I);
     ws.ival[e] = c.take<uint32_t>(I);
   }
-  ws.cnt_roi = c.take<uint32_t>(N);
+  ws.cnt_bin = c.take<uint32_t>(N);
   ws.offs = c.take<uint32_t>(N + 1);
   ws.ranges = c.take<uint2>(tiles);
   ws.tile_mask = c.take<uint8_t>(tiles);
-  ws.hist = c.take<uint32_t>(256 * (size_t)kSortBlocks);
+  ws.mask_prefix = c.take<uint16_t>((size_t)((lim.max_height + kTile - 1) / kTile) *
+                                    (size_t)((lim.max_width + kTile - 1) / kTile + 1));
+  const size_t rs_words = radix_table_words(N > I ? N : I);
+  ws.rs_table = c.take<uint32_t>(rs_words);
+  ws.rs_offs = c.take<uint32_t>(rs_words);
+  ws.rs_n = c.take<uint32_t>(1);
+  ws.rs_sums = c.take<uint32_t>(rs_words / kScanTile + 2);
   ws.scan_sums = c.take<uint32_t>(scan_blocks);
   ws.warpbuf = c.take<unsigned long long>(P);
   ws.warp_depth = c.take<float>(P);
@@ -73,7 +80,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
 
 bool limits_ok(const gs_limits *lim) {
   return lim && lim->max_surfels >= 0 && lim->max_width > 0 && lim->max_height > 0 && lim->max_instances > 0 &&
-         lim->max_instances < (int64_t(1) << 31) && lim->max_rects > 0 &&
+         lim->max_instances < (int64_t(1) << 30) && lim->max_rects > 0 &&
          (int64_t)lim->max_width * lim->max_height < (int64_t(1) << 31) && lim->max_surfels < (1 << 30);
 }
 
@@ -112,6 +119,17 @@ using namespace gs;
 
 constexpr int kMaxMarks = 16;
 
+// One captured kernel sequence per entry point.
+struct GraphSlot {
+  bool valid;
+  unsigned char key[512];
+  size_t key_len;
+  cudaGraphExec_t exec;
+  cudaGraphNode_t setup_node;
+  unsigned long long launches;  // kernels in the graph
+  int nmarks;
+};
+
 struct gs_context {
   Workspace ws;
   gs_limits lim;
@@ -121,6 +139,10 @@ struct gs_context {
   int profiling;
   int nmarks;
   cudaEvent_t ev[kMaxMarks];
+  int use_graphs;
+  int capturing;
+  cudaStream_t cap_stream;
+  GraphSlot graphs[3];  // mono, stereo, two-pass
 };
 
 static gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
@@ -191,6 +213,7 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
   memset(ctx, 0, sizeof(*ctx));
   ctx->lim = *lim;
   ctx->stream = (cudaStream_t)stream;
+  ctx->use_graphs = 1;
   if (!carve_workspace(*lim, workspace, workspace_bytes_, &ctx->ws)) {
     delete ctx;
     return GS_ERR_WORKSPACE;
@@ -208,6 +231,9 @@ gs_status gs_context_destroy(gs_context *ctx) {
   if (!ctx) return GS_ERR_BAD_ARG;
   for (int i = 0; i < kMaxMarks; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+  for (int k = 0; k < 3; ++k)
+    if (ctx->graphs[k].valid) cudaGraphExecDestroy(ctx->graphs[k].exec);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
   return GS_OK;
 }
@@ -266,7 +292,8 @@ gs_status gs_context_check(gs_context *ctx, int *device_status) {
 static void mark(gs_context *ctx, int slot) {
   if (!ctx->profiling || slot >= kMaxMarks) return;
   if (!ctx->ev[slot] && cudaEventCreate(&ctx->ev[slot]) != cudaSuccess) return;
-  cudaEventRecord(ctx->ev[slot], ctx->stream);
+  if (ctx->capturing) cudaEventRecordWithFlags(ctx->ev[slot], ctx->stream, cudaEventRecordExternal);
+  else cudaEventRecord(ctx->ev[slot], ctx->stream);
   ctx->nmarks = slot + 1 > ctx->nmarks ? slot + 1 : ctx->nmarks;
 }
 
@@ -284,28 +311,147 @@ static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye
   return cuda_status(e);
 }
 
-static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const gs_pose *a, const gs_pose *b,
-                            const gs_intrinsics *intr) {
+static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const PoseArgs &pa) {
   cudaStream_t s = ctx->stream;
   ctx->nmarks = 0;
   mark(ctx, 0);
   reset_counters_kernel<<<1, 32, 0, s>>>(ctx->ws.ctr);
   GS_LAUNCHED(1);
-  PoseArgs pa = pose_args(a, b, intr);
   cudaError_t e = launch_setup_cams(pa, ctx->ws.cams, s);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  e = launch_preprocess(*scene, ctx->ws, b ? 2 : 1, intr->width, intr->height, s);
+  e = launch_preprocess(*scene, ctx->ws, pa.neyes, pa.W, pa.H, s);
   mark(ctx, 1);
   return cuda_status(e);
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------- CUDA graphs
+//
+// Each entry point enqueues the same kernel sequence for a given scene, image
+// size, output set and parameter set; only the poses (and focal lengths) change
+// between frames, and they reach the device through the arguments of the FP64
+// set-up kernel alone. The first call with a new configuration captures the
+// sequence into a graph on an internal stream; later calls patch the set-up
+// kernel's arguments in the instantiated graph and replay it on the caller's
+// stream. When the caller's stream is itself being captured, kernels are
+// enqueued directly (they become part of the caller's graph).
+
+static bool direct_launch(gs_context *ctx) {
+  if (!ctx->use_graphs) return true;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) return true;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+template <class Enqueue>
+static gs_status run_graph(gs_context *ctx, int kind, const void *key, size_t key_len, const PoseArgs &pa,
+                           Enqueue &&enqueue) {
+  if (direct_launch(ctx)) return enqueue(pa);
+  GraphSlot &g = ctx->graphs[kind];
+  if (key_len > sizeof(g.key)) return enqueue(pa);
+  const bool hit = g.valid && g.key_len == key_len && memcmp(g.key, key, key_len) == 0;
+  if (!hit) {
+    if (g.valid) cudaGraphExecDestroy(g.exec);
+    g.valid = false;
+    if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+      return GS_ERR_CUDA;
+    cudaStream_t user = ctx->stream;
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GS_ERR_CUDA;
+    const unsigned long long l0 = g_launches;
+    ctx->stream = ctx->cap_stream;
+    ctx->capturing = 1;
+    const gs_status st = enqueue(pa);
+    ctx->stream = user;
+    ctx->capturing = 0;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    g.launches = g_launches - l0;
+    g_launches = l0;
+    if (st != GS_OK || e != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      return st != GS_OK ? st : GS_ERR_CUDA;
+    }
+    // the set-up kernel node, whose arguments carry the poses
+    size_t nn = 0;
+    cudaGraphGetNodes(graph, nullptr, &nn);
+    cudaGraphNode_t *nodes = (cudaGraphNode_t *)malloc(sizeof(cudaGraphNode_t) * (nn ? nn : 1));
+    cudaGraphGetNodes(graph, nodes, &nn);
+    g.setup_node = nullptr;
+    for (size_t i = 0; i < nn && !g.setup_node; ++i) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[i], &t) != cudaSuccess || t != cudaGraphNodeTypeKernel) continue;
+      cudaKernelNodeParams kp;
+      if (cudaGraphKernelNodeGetParams(nodes[i], &kp) == cudaSuccess && kp.func == setup_cams_kernel_ptr())
+        g.setup_node = nodes[i];
+    }
+    free(nodes);
+    const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess || !g.setup_node) {
+      if (ie == cudaSuccess) cudaGraphExecDestroy(g.exec);
+      return GS_ERR_CUDA;
+    }
+    memcpy(g.key, key, key_len);
+    g.key_len = key_len;
+    g.nmarks = ctx->nmarks;
+    g.valid = true;
+  } else {
+    PoseArgs arg = pa;
+    CamBlock *cams = ctx->ws.cams;
+    void *args[2] = {(void *)&arg, (void *)&cams};
+    cudaKernelNodeParams kp;
+    memset(&kp, 0, sizeof(kp));
+    kp.func = const_cast<void *>(setup_cams_kernel_ptr());
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    if (cudaGraphExecKernelNodeSetParams(g.exec, g.setup_node, &kp) != cudaSuccess) return GS_ERR_CUDA;
+  }
+  const cudaError_t le = cudaGraphLaunch(g.exec, ctx->stream);
+  g_launches += g.launches;
+  ctx->nmarks = g.nmarks;
+  return cuda_status(le);
+}
+
+// Byte key of everything a captured sequence depends on besides the poses.
+struct KeyBuilder {
+  unsigned char buf[512];
+  size_t len = 0;
+  template <class T>
+  void add(const T &v) {
+    if (len + sizeof(T) <= sizeof(buf)) memcpy(buf + len, &v, sizeof(T));
+    len += sizeof(T);
+  }
+};
+
+static void key_common(KeyBuilder &kb, gs_context *ctx, int kind, const gs_scene *scene, const gs_intrinsics *intr) {
+  kb.add(kind);
+  kb.add(*scene);
+  kb.add(intr->width);
+  kb.add(intr->height);
+  kb.add(ctx->counting);
+  kb.add(ctx->profiling);
+}
+
+extern "C" {
+
 gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *pose, const gs_intrinsics *intr,
                          const float *bg, float *rgb, float *depth, float *trans) {
   if (!ctx || !pose || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !rgb) return GS_ERR_BAD_ARG;
-  gs_status st = begin_call(ctx, scene, pose, nullptr, intr);
-  if (st != GS_OK) return st;
   const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
-  return render_eye_full(ctx, scene, 0, intr->width, intr->height, b, rgb, depth, trans, false, 2);
+  const PoseArgs pa = pose_args(pose, nullptr, intr);
+  KeyBuilder kb;
+  key_common(kb, ctx, 0, scene, intr);
+  kb.add(b);
+  kb.add(rgb);
+  kb.add(depth);
+  kb.add(trans);
+  return run_graph(ctx, 0, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
+    gs_status st = begin_call(ctx, scene, p);
+    if (st != GS_OK) return st;
+    return render_eye_full(ctx, scene, 0, intr->width, intr->height, b, rgb, depth, trans, false, 2);
+  });
 }
 
 static bool outputs_ok(const gs_outputs *o) {
@@ -337,34 +483,42 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
   if (roi->repair_mode != 0) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
-  gs_status st = begin_call(ctx, scene, pose_dom, pose_aff, intr);
-  if (st != GS_OK) return st;
-  const float3 black = make_float3(0.f, 0.f, 0.f);
-  // Stage 1: dominant eye, RGB + depth proxy (+ the per-frame depth range)
-  st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2);
-  if (st != GS_OK) return st;
-  // Stages 2-3: warp, edge ROIs, gaps
-  cudaError_t e = launch_warp_classify(ctx->ws, W, H, gap_thresh, *roi, out->rgb_dom, out->depth_dom,
-                                       out->trans_dom, out->rgb_aff, ctx->stream);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
-  mark(ctx, 4);
-  // Step 2: connected centre holes -> ROIs
-  if (roi->enable_center) {
-    if ((e = launch_centre_rois(ctx->ws, W, H, roi->margin, ctx->stream)) != cudaSuccess) return GS_ERR_CUDA;
-  }
-  mark(ctx, 5);
-  // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
-  ctx->last_tiles = tx * ty;
-  e = launch_binning(ctx->ws, 1, scene->n, tx, ty, ctx->ws.tile_mask, ctx->stream);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
-  mark(ctx, 6);
-  e = launch_blend(ctx->ws, 1, W, H, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ctx->ws.cls, false,
-                   ctx->counting != 0, ctx->stream);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
-  mark(ctx, 7);
-  st = copy_optional(ctx, out, W, H);
-  mark(ctx, 8);
-  return st;
+  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr);
+  KeyBuilder kb;
+  key_common(kb, ctx, 1, scene, intr);
+  kb.add(gap_thresh);
+  kb.add(*roi);
+  kb.add(*out);
+  return run_graph(ctx, 1, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
+    gs_status st = begin_call(ctx, scene, p);
+    if (st != GS_OK) return st;
+    const float3 black = make_float3(0.f, 0.f, 0.f);
+    // Stage 1: dominant eye, RGB + depth proxy (+ the per-frame depth range)
+    st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2);
+    if (st != GS_OK) return st;
+    // Stages 2-3: warp, edge ROIs, gaps
+    cudaError_t e = launch_warp_classify(ctx->ws, W, H, gap_thresh, *roi, out->rgb_dom, out->depth_dom,
+                                         out->trans_dom, out->rgb_aff, ctx->stream);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    mark(ctx, 4);
+    // Step 2: connected centre holes -> ROIs
+    if (roi->enable_center) {
+      if ((e = launch_centre_rois(ctx->ws, W, H, roi->margin, ctx->stream)) != cudaSuccess) return GS_ERR_CUDA;
+    }
+    mark(ctx, 5);
+    // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
+    ctx->last_tiles = tx * ty;
+    e = launch_binning(ctx->ws, 1, scene->n, tx, ty, ctx->ws.tile_mask, ctx->stream);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    mark(ctx, 6);
+    e = launch_blend(ctx->ws, 1, W, H, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ctx->ws.cls, false,
+                     ctx->counting != 0, ctx->stream);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+    mark(ctx, 7);
+    st = copy_optional(ctx, out, W, H);
+    mark(ctx, 8);
+    return st;
+  });
 }
 
 gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
@@ -372,12 +526,24 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
   if (!ctx || !pose_dom || !pose_aff || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
     return GS_ERR_BAD_ARG;
   const int W = intr->width, H = intr->height;
-  gs_status st = begin_call(ctx, scene, pose_dom, pose_aff, intr);
-  if (st != GS_OK) return st;
-  const float3 black = make_float3(0.f, 0.f, 0.f);
-  st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, false, 2);
-  if (st != GS_OK) return st;
-  return render_eye_full(ctx, scene, 1, W, H, black, out->rgb_aff, nullptr, nullptr, false, 4);
+  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr);
+  KeyBuilder kb;
+  key_common(kb, ctx, 2, scene, intr);
+  kb.add(*out);
+  return run_graph(ctx, 2, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
+    gs_status st = begin_call(ctx, scene, p);
+    if (st != GS_OK) return st;
+    const float3 black = make_float3(0.f, 0.f, 0.f);
+    st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, false, 2);
+    if (st != GS_OK) return st;
+    return render_eye_full(ctx, scene, 1, W, H, black, out->rgb_aff, nullptr, nullptr, false, 4);
+  });
+}
+
+gs_status gs_context_set_graphs(gs_context *ctx, int enable) {
+  if (!ctx) return GS_ERR_BAD_ARG;
+  ctx->use_graphs = enable ? 1 : 0;
+  return GS_OK;
 }
 
 gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *bytes, int64_t *count) {
@@ -410,6 +576,7 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
     case GS_BUF_STRIPS: p = ws.strips; b = 64; n = 16; break;
     case GS_BUF_WARP_DEPTH: p = ws.warp_depth; b = 4 * P; n = (int64_t)P; break;
     case GS_BUF_PAIRS: p = &ws.ctr->pairs[0]; b = 32; n = 4; break;
+    case GS_BUF_BIN_COUNTS: p = ws.cnt_bin; b = 4 * N; n = (int64_t)N; break;
     default: return GS_ERR_BAD_ARG;
   }
   *dev_ptr = p;

@@ -62,7 +62,9 @@ struct Counters {
 };
 
 // The per-surfel blend record, 64 bytes = 4 float4:
-//  r0 = (c.x, c.y, log2(o), z_c)          projected centre, opacity, centre depth
+//  r0 = (c.x, c.y, r_c^2, z_c)            projected centre, support radius^2
+//                                         2 ln(255 o) (alpha >= 1/255 iff rho <= it),
+//                                         centre depth
 //  r1 = (V1, -V0, -U1, U0)                p.xy = [dx dy] * these (see preprocess)
 //  r2 = (Az, Bz, Cz, dz_u)                p.z = Az + dx Bz + dy Cz; depth slope along u
 //  r3 = (dz_v, r, g, b)                   depth slope along v; colour
@@ -77,15 +79,17 @@ struct Workspace {
   float4 *rec[2];
   ushort4 *rect[2];
   float4 *bounds[2];
-  uint32_t *cnt[2];
+  uint32_t *cnt[2];             // tiles of each surfel's bounding rectangle (0 = culled)
   uint32_t *zkey[2];            // float bits of the centre depth per surfel and eye
-  uint32_t *cnt_roi;            // per-surfel tile count restricted to the ROI tile mask
+  uint32_t *cnt_bin;            // tiles each surfel reaches in the last binning
   uint32_t *dkey[2], *dval[2];  // depth sort double buffers
   uint32_t *offs;               // per-sorted-surfel instance offsets (+1)
   uint32_t *ikey[2], *ival[2];  // instance sort double buffers
   uint2 *ranges;
   uint8_t *tile_mask;
-  uint32_t *hist;               // radix histograms [256][kSortBlocks]
+  uint16_t *mask_prefix;        // row prefix counts of the tile mask [tiles_y][tiles_x + 1]
+  uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
+  uint32_t *rs_n, *rs_sums;     // length of the table, scan block sums
   uint32_t *scan_sums;          // scan block sums
   unsigned long long *warpbuf;
   float *warp_depth;
@@ -102,9 +106,6 @@ struct Workspace {
   int keep_intermediates;
 };
 
-constexpr int kSortBlocks = 304;     // 2 CTAs per SM on 152 SMs
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;        // items per thread per sort tile
 constexpr int kScanThreads = 512;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
@@ -118,6 +119,8 @@ bool carve_workspace(const gs_limits &lim, void *base, size_t bytes, Workspace *
 
 // ---- launches (each returns the launch error) ----
 cudaError_t launch_setup_cams(const PoseArgs &pa, CamBlock *cams, cudaStream_t s);
+// Address of the set-up kernel (its graph node carries the per-frame poses).
+const void *setup_cams_kernel_ptr();
 cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes, int W, int H,
                               cudaStream_t s);
 // Bins the visible surfels of `eye` (restricted to tile_mask when given) into

@@ -47,6 +47,8 @@ __global__ void setup_cams_kernel(PoseArgs pa, CamBlock *cams) {
   *cams = cb;
 }
 
+const void *setup_cams_kernel_ptr() { return (const void *)setup_cams_kernel; }
+
 cudaError_t launch_setup_cams(const PoseArgs &pa, CamBlock *cams, cudaStream_t s) {
   setup_cams_kernel<<<1, 32, 0, s>>>(pa, cams);
   GS_LAUNCHED(1);
@@ -135,7 +137,6 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
   const float w = q.x * qi, x = q.y * qi, y = q.z * qi, z = q.w * qi;
   const float tu[3] = {1.f - 2.f * (y * y + z * z), 2.f * (x * y + w * z), 2.f * (x * z - w * y)};
   const float tv[3] = {2.f * (x * y - w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z + w * x)};
-  const float l2o = alive ? __log2f(o) : 0.f;
   // support radius in (u, v): o G >= 1/255  <=>  u^2 + v^2 <= 2 ln(255 o)
   const float rc2 = alive ? 2.f * logf(255.f * o) : 0.f;
   const float rc = sqrtf(fmaxf(rc2, 0.f));
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
     float rgb[3];
     sh_rgb(shc, sc.sh_degree, dx, dy, dz, rgb);
     float4 *r = ws.rec[e] + 4 * (size_t)i;
-    r[0] = make_float4(cxp, cyp, l2o, pc[2]);
+    r[0] = make_float4(cxp, cyp, rc2, pc[2]);
     r[1] = make_float4(V1, -V0, -U1, U0);
     r[2] = make_float4(Az, Bz, Cz, M2[0]);
     r[3] = make_float4(M2[1], rgb[0], rgb[1], rgb[2]);

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libgs.so")
 
 GS_OK, GS_ERR_BAD_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_WORKSPACE, GS_ERR_NOT_LOADED = range(7)
 (BUF_RECORDS, BUF_RECTS, BUF_BOUNDS, BUF_COUNTS, BUF_DEPTH_ORDER, BUF_INST_KEYS, BUF_INST_VALS, BUF_RANGES,
- BUF_WARP, BUF_TILE_MASK, BUF_DEPTH_RANGE, BUF_STRIPS, BUF_WARP_DEPTH, BUF_PAIRS) = range(14)
+ BUF_WARP, BUF_TILE_MASK, BUF_DEPTH_RANGE, BUF_STRIPS, BUF_WARP_DEPTH, BUF_PAIRS, BUF_BIN_COUNTS) = range(15)
 BUF_EYE1 = 0x100
 CLS_HOLE, CLS_GAP, CLS_CENTRE, CLS_STRIP, CLS_RENDER, CLS_NET = 1, 2, 4, 8, 16, 32
 
@@ -69,6 +69,7 @@ EXPORTS = {
     "gs_context_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "gs_context_set_counting": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_context_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "gs_context_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t),
                                     C.POINTER(C.c_int64)]),
@@ -185,6 +186,9 @@ class Context:
 
     def set_counting(self, on: bool):
         _check(lib().gs_context_set_counting(self.h, int(bool(on))), "gs_context_set_counting")
+
+    def set_graphs(self, on: bool):
+        _check(lib().gs_context_set_graphs(self.h, int(bool(on))), "gs_context_set_graphs")
 
     def set_profiling(self, on: bool):
         _check(lib().gs_context_set_profiling(self.h, int(bool(on))), "gs_context_set_profiling")

@@ -66,6 +66,33 @@ def compare_render(g_rgb, g_dep, g_tr, o_rgb, o_dep, o_tr, margin, what=""):
     return e_rgb, e_dep, frac
 
 
+def conic_well_conditioned(rec, k):
+    """Float64 restatement of the binning's choice between the closed-form row
+    ranges (a well-conditioned ellipse) and the whole bounding rectangle: True,
+    False, or None within a factor 2 of the threshold (1e-4 of Sxx Syy)."""
+    ax, ay, bx, by = (float(v) for v in rec[4:8])
+    A0, az, bz = float(rec[8]), float(rec[9]), float(rec[10])
+    Sxx = ax * ax + ay * ay - k * az * az
+    Syy = bx * bx + by * by - k * bz * bz
+    Sxy = ax * bx + ay * by - k * az * bz
+    if Sxx <= 0 or Syy <= 0:
+        return False
+    det = Sxx * Syy - Sxy * Sxy
+    ratio = det / (Sxx * Syy)
+    gx, gy, h = -k * A0 * az, -k * A0 * bz, -k * A0 * A0
+    if ratio > 0:
+        dcx = (Sxy * gy - Syy * gx) / det
+        dcy = (Sxy * gx - Sxx * gy) / det
+        Qc = gx * dcx + gy * dcy + h
+    else:
+        Qc = 1.0
+    if ratio > 2e-4 and Qc < -1e-3 * abs(h):
+        return True
+    if ratio < 0.5e-4 or Qc > 1e-3 * abs(h):
+        return False
+    return None
+
+
 def make_ctx(gs, scene, cam, **kw):
     kw.setdefault("max_instances", 1 << 22)
     return gs.Context(max(scene.n, 1), cam.width, cam.height, **kw)
@@ -128,34 +155,72 @@ def test_sorted_instances_bit_exact(gs, orc):
     ctx.check_ok()
     rects, _ = ctx.buffer(gs.BUF_RECTS, torch.int16, (-1, 4))
     counts, _ = ctx.buffer(gs.BUF_COUNTS, torch.int32, None)
+    bins, _ = ctx.buffer(gs.BUF_BIN_COUNTS, torch.int32, None)
     recs, _ = ctx.buffer(gs.BUF_RECORDS, torch.float32, (-1, 16))
     keys, nk = ctx.buffer(gs.BUF_INST_KEYS, torch.int32, None)
     vals, _ = ctx.buffer(gs.BUF_INST_VALS, torch.int32, None)
     ranges, _ = ctx.buffer(gs.BUF_RANGES, torch.int32, (-1, 2))
     r = rects[: scene.n].cpu().numpy().astype(np.int64)
     c = counts[: scene.n].cpu().numpy()
+    b = bins[: scene.n].cpu().numpy()
+    rec = recs[: scene.n].cpu().numpy()
     zbits = recs[: scene.n, 3].contiguous().view(torch.int32).cpu().numpy().astype(np.uint32)
-    tiles_x = (cam.width + 15) // 16
-    k_list, v_list = [], []
-    for i in np.where(c > 0)[0]:
-        for ty in range(r[i, 1], r[i, 3] + 1):
-            for tx in range(r[i, 0], r[i, 2] + 1):
-                k_list.append((np.uint64(ty * tiles_x + tx) << np.uint64(32)) | np.uint64(zbits[i]))
-                v_list.append(i)
-    ok_, ov = orc.sort_pairs(np.array(k_list, np.uint64), np.array(v_list, np.uint32))
-    assert nk == len(ok_)
+    W, H = cam.width, cam.height
+    tiles_x = (W + 15) // 16
     gk = keys[:nk].cpu().numpy().astype(np.uint32)
     gv = vals[:nk].cpu().numpy().astype(np.uint32)
-    assert np.array_equal(gk.astype(np.uint64), ok_ >> np.uint64(32))
-    assert np.array_equal(gv, ov)
+    # (1) the list is the unique sort of its pairs by (tile, depth bits, surfel id)
+    order = np.lexsort((gv, zbits[gv], gk))
+    assert np.array_equal(order, np.arange(nk))
+    assert np.array_equal(np.bincount(gv, minlength=scene.n), b)
+    # (2) per-surfel tile decisions equal the oracle's FP64 test on the same record
+    # (the continuous tile rectangle against the support with r_c^2 grown by 1e-3)
+    gset = set(zip(gv.tolist(), gk.tolist()))
+    by_surfel = {}
+    for sid, t in gset:
+        by_surfel.setdefault(sid, set()).add((sid, t))
+    mism, tested, full_rect = 0, 0, 0
+    for i in np.where(c > 0)[0][::3]:
+        k = max(float(rec[i, 2]), 0.0) * 1.001 + 1e-6  # the record carries r_c^2 = 2 ln(255 o)
+        ok = conic_well_conditioned(rec[i], k)
+        rect_tiles = {(int(i), ty * tiles_x + tx) for ty in range(r[i, 1], r[i, 3] + 1)
+                      for tx in range(r[i, 0], r[i, 2] + 1)}
+        mine = by_surfel.get(int(i), set())
+        assert mine <= rect_tiles
+        if ok is None:
+            continue  # near the conditioning threshold: either treatment is valid
+        if not ok:
+            # an ellipse too thin and oblique for float32 keeps its whole rectangle
+            assert mine == rect_tiles
+            full_rect += 1
+            continue
+        for ty in range(r[i, 1], r[i, 3] + 1):
+            for tx in range(r[i, 0], r[i, 2] + 1):
+                x0, y0 = tx * 16 - 0.01, ty * 16 - 0.01
+                x1, y1 = min(tx * 16 + 15, W - 1) + 0.01, min(ty * 16 + 15, H - 1) + 0.01
+                o = orc.tile_test(rec[i, :12], k, x0, x1, y0, y1)
+                g = (int(i), ty * tiles_x + tx) in gset
+                tested += 1
+                if o != g:
+                    # allowed only where the support grazes the tile: the decision
+                    # flips within +-0.2% of r_c^2 (the float32 safety slack)
+                    assert orc.tile_test(rec[i, :12], k * (1 + 2e-3), x0, x1, y0, y1) != \
+                        orc.tile_test(rec[i, :12], k * (1 - 2e-3), x0, x1, y0, y1), (i, tx, ty, o, g)
+                    mism += 1
+    assert tested > 10000 and mism <= 1e-3 * tested
+    assert full_rect <= 0.01 * len(np.where(c > 0)[0][::3])
+    # (3) every (surfel, tile) with a pixel centre where alpha >= 1/255 is binned
+    oi, ot = orc.support_pairs(scene, dom, cam)
+    missing = [(i, t) for i, t in zip(oi.tolist(), ot.tolist()) if (i, t) not in gset]
+    assert not missing, missing[:10]
+    assert nk <= 1.6 * len(oi)  # the culling stays close to the minimal binning
+    # (4) ranges
     rg = ranges.cpu().numpy()
-    t = (ok_ >> np.uint64(32)).astype(np.int64)
-    for tile in range(rg.shape[0]):
-        idx = np.where(t == tile)[0]
-        if idx.size:
-            assert rg[tile, 0] == idx[0] and rg[tile, 1] == idx[-1] + 1
-        else:
-            assert rg[tile, 0] == rg[tile, 1]
+    starts = np.searchsorted(gk, np.arange(rg.shape[0]), side="left")
+    ends = np.searchsorted(gk, np.arange(rg.shape[0]), side="right")
+    nonempty = ends > starts
+    assert np.array_equal(rg[nonempty, 0], starts[nonempty]) and np.array_equal(rg[nonempty, 1], ends[nonempty])
+    assert np.all(rg[~nonempty, 0] == rg[~nonempty, 1])
 
 
 def test_empty_and_culled_scenes(gs):
@@ -419,3 +484,28 @@ def test_full_size_two_pass_agrees_on_roi_tiles(gs, object_scene):
     mse = torch.mean((o["rgb_aff"] - tp["rgb_aff"]) ** 2).item()
     psnr = 10 * math.log10(1.0 / max(mse, 1e-12))
     assert psnr > 20.0
+
+
+def test_graph_replay_matches_direct_launches(gs):
+    """Captured-and-patched graphs give bit-identical frames to kernel-by-kernel
+    launches, for a second pose (the patched set-up kernel arguments)."""
+    scene = synth.scene_object_ground(1300, n=60_000)
+    cam = synth.centred_camera(640, 480, 640.0)
+    poses = [synth.eye_pair(p) for p in synth.arc_poses()[:3]]
+    ds = gs.DeviceScene(scene)
+    outs = []
+    for graphs in (False, True):
+        ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24)
+        ctx.set_graphs(graphs)
+        res = []
+        for d, a in poses:
+            o = ctx.render_stereo(ds, d, a, cam)
+            t = ctx.render_two_pass(ds, d, a, cam)
+            m = ctx.render_mono(ds, a, cam)
+            ctx.check_ok()
+            res.append([o["rgb_aff"].clone(), o["cls_aff"].clone(), o["rgb_dom"].clone(), t["rgb_aff"].clone(),
+                        m[0].clone(), m[1].clone()])
+        outs.append(res)
+    for a, b in zip(outs[0], outs[1]):
+        for x, y in zip(a, b):
+            assert torch.equal(x, y)

@@ -584,3 +584,38 @@ def test_stereo_composes_its_stages(orc):
     np.testing.assert_array_equal(out["rgb_aff"][:, pix], full[:, pix])
     np.testing.assert_array_equal(out["rgb_aff"][:, ~pix], filled[:, ~pix])
     assert np.array_equal(out["cls"] & 15, cls) and np.array_equal((out["cls"] & 16) > 0, pix)
+
+
+def test_tile_test_matches_dense_sampling(orc):
+    """The conic-rectangle test agrees with a dense sampling of the rectangle
+    wherever the sampled minimum is clearly away from the boundary."""
+    rng = np.random.default_rng(21)
+    checked = 0
+    for _ in range(300):
+        rec = np.zeros(12, np.float32)
+        rec[0:2] = rng.uniform(-20, 20, 2)
+        th = rng.uniform(0, np.pi)
+        su, sv = rng.uniform(2, 30, 2)
+        # an ellipse map: p.xy = R(th) diag(1/su, 1/sv) d scaled, p.z ~ 1 + small tilt
+        Rm = np.array([[np.cos(th), np.sin(th)], [-np.sin(th), np.cos(th)]])
+        Mxy = np.diag([1 / su, 1 / sv]) @ Rm
+        rec[4], rec[6] = Mxy[0, 0], Mxy[0, 1]
+        rec[5], rec[7] = Mxy[1, 0], Mxy[1, 1]
+        rec[8] = 1.0
+        rec[9:11] = rng.uniform(-0.01, 0.01, 2)
+        k = float(rng.uniform(1, 11))
+        x0, y0 = rng.uniform(-60, 40, 2)
+        x1, y1 = x0 + 15, y0 + 15
+        xs, ys = np.meshgrid(np.linspace(x0, x1, 121), np.linspace(y0, y1, 121))
+        dx, dy = xs - rec[0], ys - rec[1]
+        px = dx * rec[4] + dy * rec[6]
+        py = dx * rec[5] + dy * rec[7]
+        pz = rec[8] + dx * rec[9] + dy * rec[10]
+        rho = (px ** 2 + py ** 2) / pz ** 2
+        rho = np.minimum(rho, 2 * (dx ** 2 + dy ** 2))
+        mn = rho.min()
+        if abs(mn - k) < 0.05 * k:
+            continue
+        assert orc.tile_test(rec, k, x0, x1, y0, y1) == (mn <= k)
+        checked += 1
+    assert checked > 200
