@@ -205,6 +205,10 @@ gs_status gs_context_stage_times(gs_context *ctx, float *ms, int max_stages, int
 
 const char *gs_status_str(gs_status s);
 
+/* Text of the CUDA runtime error behind the last GS_ERR_CUDA returned on the
+ * calling host thread. */
+const char *gs_last_cuda_error(void);
+
 /* Number of CUDA kernels this library has enqueued since it was loaded, over all
  * contexts and threads (diagnostics; host-side count, no synchronisation). */
 unsigned long long gs_kernel_launches(void);

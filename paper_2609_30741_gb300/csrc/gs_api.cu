@@ -1,4 +1,5 @@
 // C ABI: contexts, workspace layout and the entry points of include/gs.h.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -124,6 +125,7 @@ struct GraphSlot {
   bool valid;
   unsigned char key[512];
   size_t key_len;
+  cudaGraph_t graph;             // kept alive: setup_node belongs to it
   cudaGraphExec_t exec;
   cudaGraphNode_t setup_node;
   unsigned long long launches;  // kernels in the graph
@@ -145,7 +147,28 @@ struct gs_context {
   GraphSlot graphs[3];  // mono, stereo, two-pass
 };
 
-static gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+static void release_slot(GraphSlot &g) {
+  if (g.valid) {
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+  }
+  g.valid = false;
+}
+
+
+// The CUDA error behind the last GS_ERR_CUDA of this host thread.
+static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+static thread_local int g_last_cuda_line = 0;
+static thread_local char g_last_cuda_text[160];
+
+static gs_status cuda_fail_at(int line, cudaError_t e) {
+  g_last_cuda_error = e != cudaSuccess ? e : cudaErrorUnknown;
+  g_last_cuda_line = line;
+  return GS_ERR_CUDA;
+}
+#define cuda_fail(e) cuda_fail_at(__LINE__, (e))
+
+static gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : cuda_fail(e); }
 
 static bool scene_ok(const gs_context *ctx, const gs_scene *sc) {
   if (!sc || sc->n < 0 || sc->n > ctx->lim.max_surfels || sc->sh_degree < 0 || sc->sh_degree > 3) return false;
@@ -197,6 +220,12 @@ const char *gs_status_str(gs_status s) {
 
 unsigned long long gs_kernel_launches(void) { return g_launches; }
 
+const char *gs_last_cuda_error(void) {
+  snprintf(g_last_cuda_text, sizeof(g_last_cuda_text), "%s (gs_api.cu:%d)", cudaGetErrorString(g_last_cuda_error),
+           g_last_cuda_line);
+  return g_last_cuda_text;
+}
+
 gs_status gs_workspace_size(const gs_limits *lim, size_t *bytes) {
   if (!limits_ok(lim) || !bytes) return GS_ERR_BAD_ARG;
   *bytes = workspace_bytes(*lim);
@@ -221,7 +250,7 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
   cudaError_t e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
   if (e != cudaSuccess) {
     delete ctx;
-    return GS_ERR_CUDA;
+    return cuda_fail(cudaGetLastError());
   }
   *out = ctx;
   return GS_OK;
@@ -231,8 +260,7 @@ gs_status gs_context_destroy(gs_context *ctx) {
   if (!ctx) return GS_ERR_BAD_ARG;
   for (int i = 0; i < kMaxMarks; ++i)
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
-  for (int k = 0; k < 3; ++k)
-    if (ctx->graphs[k].valid) cudaGraphExecDestroy(ctx->graphs[k].exec);
+  for (int k = 0; k < 3; ++k) release_slot(ctx->graphs[k]);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
   delete ctx;
   return GS_OK;
@@ -246,12 +274,12 @@ gs_status gs_context_set_profiling(gs_context *ctx, int enable) {
 
 gs_status gs_context_stage_times(gs_context *ctx, float *ms, int max_stages, int *n_stages) {
   if (!ctx || !ms || max_stages < 0) return GS_ERR_BAD_ARG;
-  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(cudaGetLastError());
   int n = ctx->nmarks > 1 ? ctx->nmarks - 1 : 0;
   if (n > max_stages) n = max_stages;
   for (int i = 0; i < n; ++i) {
     float t = 0.f;
-    if (cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaEventElapsedTime(&t, ctx->ev[i], ctx->ev[i + 1]) != cudaSuccess) return cuda_fail(cudaGetLastError());
     ms[i] = t;
   }
   if (n_stages) *n_stages = n;
@@ -273,13 +301,13 @@ gs_status gs_context_set_counting(gs_context *ctx, int enable) {
 gs_status gs_context_check(gs_context *ctx, int *device_status) {
   if (!ctx) return GS_ERR_BAD_ARG;
   cudaError_t e = cudaStreamSynchronize(ctx->stream);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_fail(e);
   uint32_t st = 0;
   e = cudaMemcpy(&st, &ctx->ws.ctr->status, sizeof(st), cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_fail(e);
   const uint32_t zero = 0;
   e = cudaMemcpy(&ctx->ws.ctr->status, &zero, sizeof(zero), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_fail(e);
   int code = GS_OK;
   if (st & kStCapacity) code = GS_ERR_CAPACITY;
   else if (st & kStTimeout) code = GS_ERR_TIMEOUT;
@@ -304,7 +332,7 @@ static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
   ctx->last_tiles = tx * ty;
   cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_fail(e);
   mark(ctx, slot);
   e = launch_blend(ws, eye, W, H, nullptr, bg, rgb, depth, trans, nullptr, stats, ctx->counting != 0, s);
   mark(ctx, slot + 1);
@@ -318,7 +346,7 @@ static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const PoseAr
   reset_counters_kernel<<<1, 32, 0, s>>>(ctx->ws.ctr);
   GS_LAUNCHED(1);
   cudaError_t e = launch_setup_cams(pa, ctx->ws.cams, s);
-  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (e != cudaSuccess) return cuda_fail(e);
   e = launch_preprocess(*scene, ctx->ws, pa.neyes, pa.W, pa.H, s);
   mark(ctx, 1);
   return cuda_status(e);
@@ -331,11 +359,12 @@ static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const PoseAr
 // Each entry point enqueues the same kernel sequence for a given scene, image
 // size, output set and parameter set; only the poses (and focal lengths) change
 // between frames, and they reach the device through the arguments of the FP64
-// set-up kernel alone. The first call with a new configuration captures the
-// sequence into a graph on an internal stream; later calls patch the set-up
-// kernel's arguments in the instantiated graph and replay it on the caller's
-// stream. When the caller's stream is itself being captured, kernels are
-// enqueued directly (they become part of the caller's graph).
+// set-up kernel alone. The first call with a new configuration enqueues its
+// kernels one by one (so every kernel is loaded before any capture); the second
+// captures the sequence into a graph on an internal stream; later calls patch
+// the set-up kernel's arguments in the instantiated graph and replay it on the
+// caller's stream. When the caller's stream is itself being captured, kernels
+// are enqueued directly (they become part of the caller's graph).
 
 static bool direct_launch(gs_context *ctx) {
   if (!ctx->use_graphs) return true;
@@ -350,14 +379,22 @@ static gs_status run_graph(gs_context *ctx, int kind, const void *key, size_t ke
   if (direct_launch(ctx)) return enqueue(pa);
   GraphSlot &g = ctx->graphs[kind];
   if (key_len > sizeof(g.key)) return enqueue(pa);
-  const bool hit = g.valid && g.key_len == key_len && memcmp(g.key, key, key_len) == 0;
+  const bool same = g.key_len == key_len && memcmp(g.key, key, key_len) == 0;
+  const bool hit = g.valid && same;
+  if (!same) {
+    // a configuration seen for the first time runs kernel by kernel: every
+    // kernel is then loaded before the next call captures the sequence
+    release_slot(g);
+    memcpy(g.key, key, key_len);
+    g.key_len = key_len;
+    return enqueue(pa);
+  }
   if (!hit) {
-    if (g.valid) cudaGraphExecDestroy(g.exec);
-    g.valid = false;
+    release_slot(g);
     if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-      return GS_ERR_CUDA;
+      return cuda_fail(cudaGetLastError());
     cudaStream_t user = ctx->stream;
-    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return cuda_fail(cudaGetLastError());
     const unsigned long long l0 = g_launches;
     ctx->stream = ctx->cap_stream;
     ctx->capturing = 1;
@@ -370,7 +407,7 @@ static gs_status run_graph(gs_context *ctx, int kind, const void *key, size_t ke
     g_launches = l0;
     if (st != GS_OK || e != cudaSuccess || !graph) {
       if (graph) cudaGraphDestroy(graph);
-      return st != GS_OK ? st : GS_ERR_CUDA;
+      return st != GS_OK ? st : cuda_fail(e);
     }
     // the set-up kernel node, whose arguments carry the poses
     size_t nn = 0;
@@ -387,11 +424,12 @@ static gs_status run_graph(gs_context *ctx, int kind, const void *key, size_t ke
     }
     free(nodes);
     const cudaError_t ie = cudaGraphInstantiate(&g.exec, graph, 0);
-    cudaGraphDestroy(graph);
     if (ie != cudaSuccess || !g.setup_node) {
       if (ie == cudaSuccess) cudaGraphExecDestroy(g.exec);
-      return GS_ERR_CUDA;
+      cudaGraphDestroy(graph);
+      return cuda_fail(ie != cudaSuccess ? ie : cudaErrorInvalidKernelImage);
     }
+    g.graph = graph;
     memcpy(g.key, key, key_len);
     g.key_len = key_len;
     g.nmarks = ctx->nmarks;
@@ -406,7 +444,7 @@ static gs_status run_graph(gs_context *ctx, int kind, const void *key, size_t ke
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(32);
     kp.kernelParams = args;
-    if (cudaGraphExecKernelNodeSetParams(g.exec, g.setup_node, &kp) != cudaSuccess) return GS_ERR_CUDA;
+    if (cudaGraphExecKernelNodeSetParams(g.exec, g.setup_node, &kp) != cudaSuccess) return cuda_fail(cudaGetLastError());
   }
   const cudaError_t le = cudaGraphLaunch(g.exec, ctx->stream);
   g_launches += g.launches;
@@ -499,21 +537,21 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     // Stages 2-3: warp, edge ROIs, gaps
     cudaError_t e = launch_warp_classify(ctx->ws, W, H, gap_thresh, *roi, out->rgb_dom, out->depth_dom,
                                          out->trans_dom, out->rgb_aff, ctx->stream);
-    if (e != cudaSuccess) return GS_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 4);
     // Step 2: connected centre holes -> ROIs
     if (roi->enable_center) {
-      if ((e = launch_centre_rois(ctx->ws, W, H, roi->margin, ctx->stream)) != cudaSuccess) return GS_ERR_CUDA;
+      if ((e = launch_centre_rois(ctx->ws, W, H, roi->margin, ctx->stream)) != cudaSuccess) return cuda_fail(e);
     }
     mark(ctx, 5);
     // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
     ctx->last_tiles = tx * ty;
     e = launch_binning(ctx->ws, 1, scene->n, tx, ty, ctx->ws.tile_mask, ctx->stream);
-    if (e != cudaSuccess) return GS_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
     e = launch_blend(ctx->ws, 1, W, H, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ctx->ws.cls, false,
                      ctx->counting != 0, ctx->stream);
-    if (e != cudaSuccess) return GS_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 7);
     st = copy_optional(ctx, out, W, H);
     mark(ctx, 8);
@@ -551,8 +589,8 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
   const Workspace &ws = ctx->ws;
   const size_t N = (size_t)ws.max_surfels, P = (size_t)ws.max_pixels, I = (size_t)ws.max_instances;
   Counters c;
-  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return GS_ERR_CUDA;
-  if (cudaMemcpy(&c, ws.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return GS_ERR_CUDA;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(cudaGetLastError());
+  if (cudaMemcpy(&c, ws.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(cudaGetLastError());
   void *p = nullptr;
   size_t b = 0;
   int64_t n = -1;

@@ -25,7 +25,10 @@ CLS_HOLE, CLS_GAP, CLS_CENTRE, CLS_STRIP, CLS_RENDER, CLS_NET = 1, 2, 4, 8, 16, 
 class GsError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
-        super().__init__(f"{what}: {status_str(status)} ({status})")
+        detail = ""
+        if status == GS_ERR_CUDA:
+            detail = f" [{lib().gs_last_cuda_error().decode()}]"
+        super().__init__(f"{what}: {status_str(status)} ({status}){detail}")
 
 
 class Scene(C.Structure):
@@ -62,6 +65,7 @@ class Limits(C.Structure):
 EXPORTS = {
     "gs_status_str": (C.c_char_p, [C.c_int]),
     "gs_kernel_launches": (C.c_ulonglong, []),
+    "gs_last_cuda_error": (C.c_char_p, []),
     "gs_workspace_size": (C.c_int, [C.POINTER(Limits), C.POINTER(C.c_size_t)]),
     "gs_context_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Limits), C.c_void_p, C.c_size_t, C.c_void_p]),
     "gs_context_destroy": (C.c_int, [C.c_void_p]),
