@@ -152,6 +152,47 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
                              const gs_pose *pose_aff, const gs_intrinsics *intr,
                              const gs_outputs *out);
 
+/* Allocation-free forward warp (no counterpart in the paper; a deployment aid).
+ *
+ * For callers that cannot allocate device memory: a plugin or compositor inside
+ * a host application that owns the GPU memory pool and forbids allocations from
+ * outside it, or a frame loop with a hard deadline where a cudaMalloc could stall
+ * or fail. It needs no gs_context and no workspace, and calls no cudaMalloc,
+ * cudaFree or other allocating routine. It computes the depth-tested forward warp
+ * of the stereo pipeline (the same arithmetic and tie-breaking as
+ * gs_render_stereo's warp stage): every dominant pixel with coverage 1 - T >= 0.5
+ * is unprojected with depth D / (1 - T), moved to the affiliated camera and
+ * projected to pixel (floor(u + 0.5), floor(v + 0.5)); other pixels travel as
+ * background samples at infinite depth; the nearest sample wins, then the
+ * smallest source index.
+ *
+ * Inputs (device pointers, the dominant eye's gs_render_* outputs, planar):
+ *   rgb_dom float[3][H][W], depth_dom float[H][W] (D), trans_dom float[H][W] (T);
+ *   pose_dom, pose_aff, intr: host structs (both eyes share intr).
+ * Outputs (device pointers, caller-owned):
+ *   rgb_warp float[3][H][W]: the winner's colour, 0 at holes;
+ *   depth_warp float[H][W] (may be NULL): the winner's camera-space depth in the
+ *     affiliated eye, +inf for a background sample, 0 at holes;
+ *   hole uint8[H][W] (may be NULL): 1 where no sample landed.
+ *
+ * Scratch: one 64-bit key per pixel in a static device array of
+ * GS_WARP_NOALLOC_MAX_PIXELS entries (32 MiB), held by every device that loads
+ * this library until the process exits. Frames with more pixels return
+ * GS_ERR_CAPACITY. The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. The call clears the array's first W*H keys before
+ * it scatters, so no state carries over from an earlier call; but every call on
+ * a device shares the one array, so calls that overlap on the GPU (other streams,
+ * other host threads) race and give wrong results: serialise them.
+ * Asynchronous on `stream` (a cudaStream_t; NULL = legacy default stream).
+ * Errors: GS_ERR_BAD_ARG (NULL input or output, non-positive size or focal
+ * length), GS_ERR_CAPACITY (W*H above the limit), GS_ERR_CUDA (lookup or launch
+ * failure; see gs_last_cuda_error). */
+#define GS_WARP_NOALLOC_MAX_PIXELS (1 << 22)
+gs_status gs_warp_noalloc(const float *rgb_dom, const float *depth_dom, const float *trans_dom,
+                          const gs_pose *pose_dom, const gs_pose *pose_aff, const gs_intrinsics *intr,
+                          float *rgb_warp, float *depth_warp, uint8_t *hole, void *stream);
+
 /* Intermediate buffers of the last call, for inspection by tests. *dev_ptr points
  * into the workspace; *count is the element count the call produced (read from
  * the device, so this synchronises the stream). DEPTH_ORDER, INST_KEYS,

@@ -160,13 +160,23 @@ static void release_slot(GraphSlot &g) {
 static thread_local cudaError_t g_last_cuda_error = cudaSuccess;
 static thread_local int g_last_cuda_line = 0;
 static thread_local char g_last_cuda_text[160];
+static thread_local const char *g_last_cuda_file = "gs_api.cu";
 
 static gs_status cuda_fail_at(int line, cudaError_t e) {
   g_last_cuda_error = e != cudaSuccess ? e : cudaErrorUnknown;
   g_last_cuda_line = line;
+  g_last_cuda_file = "gs_api.cu";
   return GS_ERR_CUDA;
 }
 #define cuda_fail(e) cuda_fail_at(__LINE__, (e))
+
+namespace gs {
+gs_status record_cuda_failure(const char *file, int line, cudaError_t e) {
+  cuda_fail_at(line, e);
+  g_last_cuda_file = file;
+  return GS_ERR_CUDA;
+}
+}  // namespace gs
 
 static gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : cuda_fail(e); }
 
@@ -221,8 +231,8 @@ const char *gs_status_str(gs_status s) {
 unsigned long long gs_kernel_launches(void) { return g_launches; }
 
 const char *gs_last_cuda_error(void) {
-  snprintf(g_last_cuda_text, sizeof(g_last_cuda_text), "%s (gs_api.cu:%d)", cudaGetErrorString(g_last_cuda_error),
-           g_last_cuda_line);
+  snprintf(g_last_cuda_text, sizeof(g_last_cuda_text), "%s (%s:%d)", cudaGetErrorString(g_last_cuda_error),
+           g_last_cuda_file, g_last_cuda_line);
   return g_last_cuda_text;
 }
 

@@ -114,6 +114,10 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 extern unsigned long long g_launches;
 #define GS_LAUNCHED(n) (::gs::g_launches += (n))
 
+// Records a CUDA runtime error for gs_last_cuda_error (file:line of the caller)
+// and returns GS_ERR_CUDA.
+gs_status record_cuda_failure(const char *file, int line, cudaError_t e);
+
 size_t workspace_bytes(const gs_limits &lim);
 bool carve_workspace(const gs_limits &lim, void *base, size_t bytes, Workspace *ws);
 

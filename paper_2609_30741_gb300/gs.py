@@ -83,7 +83,11 @@ EXPORTS = {
                                    C.POINTER(Intrinsics), C.c_int, C.POINTER(RoiParams), C.POINTER(Outputs)]),
     "gs_render_two_pass": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Pose),
                                      C.POINTER(Intrinsics), C.POINTER(Outputs)]),
+    "gs_warp_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Pose), C.POINTER(Pose),
+                                  C.POINTER(Intrinsics), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
+
+WARP_NOALLOC_MAX_PIXELS = 1 << 22
 
 _lib = None
 
@@ -281,3 +285,22 @@ class Context:
                                         C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), C.byref(os_)),
                "gs_render_two_pass")
         return out
+
+
+def warp_noalloc(rgb_dom, depth_dom, trans_dom, pose_dom, pose_aff, cam, rgb_warp, depth_warp=None, hole=None,
+                 stream=None):
+    """Depth-tested forward warp of a dominant-eye render into the affiliated eye
+    through gs_warp_noalloc, which allocates no device memory (for callers inside
+    a host application that owns the GPU memory pool). All tensors are caller-
+    owned CUDA tensors: rgb_dom (3, H, W), depth_dom and trans_dom (H, W) float32
+    in; rgb_warp (3, H, W) float32, optional depth_warp (H, W) float32 and hole
+    (H, W) uint8 out. Calls that overlap on the GPU share one static scratch
+    array and race: serialise them."""
+    for t in (rgb_dom, depth_dom, trans_dom, rgb_warp, depth_warp, hole):
+        if t is not None and (not t.is_cuda or not t.is_contiguous()):
+            raise ValueError("warp_noalloc takes contiguous CUDA tensors")
+    st = stream if stream is not None else torch.cuda.current_stream(rgb_dom.device)
+    _check(lib().gs_warp_noalloc(_ptr(rgb_dom), _ptr(depth_dom), _ptr(trans_dom), C.byref(pose_struct(pose_dom)),
+                                 C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), _ptr(rgb_warp),
+                                 _ptr(depth_warp), _ptr(hole), C.c_void_p(st.cuda_stream)),
+           "gs_warp_noalloc")
