@@ -318,9 +318,11 @@ def run_ours(args):
     achieved = ops / (blend_ms * 1e-3) / 1e9
     peak_gops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz_peak * 1e6 / 1e9
     prof_traffic = None
-    pf = os.path.join(ROOT, "profiles", "blend_traffic.json")
-    if os.path.exists(pf):
-        prof_traffic = json.load(open(pf)).get("bytes_per_launch")
+    pf = os.path.join(ROOT, "profiles", "blend_object500k.md")
+    if os.path.exists(pf):  # dram read + write bytes of one ncu-captured launch of this blend kernel
+        for ln in open(pf):
+            if ln.startswith("traffic_bytes_per_launch ="):
+                prof_traffic = int(ln.split("=")[1])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
