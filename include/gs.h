@@ -110,10 +110,11 @@ typedef struct {
 /* Upper bounds a context is sized for. */
 typedef struct {
   int max_surfels;
-  int max_width, max_height;
+  int max_width, max_height; /* each <= 8192 */
   int64_t max_instances; /* (surfel, tile) pairs per eye; < 2^30 */
   int max_rects;         /* centre ROI rectangles */
-  int keep_intermediates;/* 1: also store per-surfel float bounds for inspection */
+  int keep_intermediates;/* 1: also store per-surfel float bounds, per-instance tile
+                            ids and per-surfel tile counts for inspection */
 } gs_limits;
 
 /* Bytes of device workspace a context with these limits needs. */
@@ -204,8 +205,8 @@ typedef enum {
   GS_BUF_BOUNDS = 2,      /* float4[eye][max_surfels]: xmin, xmax, ymin, ymax (keep_intermediates) */
   GS_BUF_COUNTS = 3,      /* uint32[eye][max_surfels]: tiles touched per surfel (0 = culled) */
   GS_BUF_DEPTH_ORDER = 4, /* uint32[max_surfels]: surfel ids of the last binning in depth order */
-  GS_BUF_INST_KEYS = 5,   /* uint32[max_instances]: tile id per instance, sorted */
-  GS_BUF_INST_VALS = 6,   /* uint32[max_instances]: surfel id per instance, sorted */
+  GS_BUF_INST_KEYS = 5,   /* uint32[max_instances]: tile id per instance, sorted (keep_intermediates) */
+  GS_BUF_INST_VALS = 6,   /* uint32[max_instances]: surfel id per instance: tile by tile, depth order */
   GS_BUF_RANGES = 7,      /* uint32x2[tiles]: [start, end) of each tile's instances */
   GS_BUF_WARP = 8,        /* uint64[pixels]: (float depth bits << 32) | source index, ~0 = hole */
   GS_BUF_TILE_MASK = 9,   /* uint8[tiles]: tiles of the ROI re-render */
@@ -214,7 +215,8 @@ typedef enum {
   GS_BUF_WARP_DEPTH = 12, /* float[pixels]: warped depth (+inf background, 0 hole) */
   GS_BUF_PAIRS = 13,      /* uint64[2]: evaluated (pixel, surfel) pairs per eye, when counting */
   GS_BUF_BIN_COUNTS = 14, /* uint32[max_surfels]: tiles each surfel's support reaches in the
-                             last binning (within the ROI tile mask for the ROI pass) */
+                             last binning (within the ROI tile mask for the ROI pass;
+                             keep_intermediates) */
   GS_BUF_EYE1 = 0x100     /* OR into RECORDS/RECTS/BOUNDS/COUNTS for the affiliated eye */
 } gs_buffer_id;
 

@@ -15,6 +15,9 @@ unsigned long long g_launches = 0;
 namespace {
 
 constexpr size_t kAlign = 256;
+// widest image: the binning keeps 8 warps x 4 tile rows x 2 counters per tile
+// column in shared memory (64 KB at 4096 pixels, 128 KB at this limit)
+constexpr int kMaxWidth = 8192;
 
 struct Carver {
   char *base;
@@ -34,7 +37,10 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   const size_t P = (size_t)lim.max_width * (size_t)lim.max_height;
   const size_t tiles = (size_t)((lim.max_width + kTile - 1) / kTile) * (size_t)((lim.max_height + kTile - 1) / kTile);
   const size_t I = (size_t)lim.max_instances;
-  const size_t scan_blocks = ((N > P ? N : P) + kScanTile - 1) / kScanTile + 2;
+  const size_t table_max = tiles * bin_chunks(lim.max_surfels);
+  size_t scan_n = N > P ? N : P;
+  if (table_max > scan_n) scan_n = table_max;
+  const size_t scan_blocks = (scan_n + kScanTile - 1) / kScanTile + 2;
   ws.cams = c.take<CamBlock>(1);
   ws.ctr = c.take<Counters>(1);
   for (int e = 0; e < 2; ++e) {
@@ -45,16 +51,27 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     ws.zkey[e] = c.take<uint32_t>(N);
     ws.dkey[e] = c.take<uint32_t>(N);
     ws.dval[e] = c.take<uint32_t>(N);
-    ws.ikey[e] = c.take<uint32_t>(I);
-    ws.ival[e] = c.take<uint32_t>(I);
   }
-  ws.cnt_bin = c.take<uint32_t>(N);
-  ws.offs = c.take<uint32_t>(N + 1);
+  ws.bin_warp_surfels = bin_warp_surfels(lim.max_surfels);
+  ws.bin_nch = bin_chunks(lim.max_surfels);
+  const size_t table = tiles * ws.bin_nch;
+  ws.ival = c.take<uint32_t>(I);
+  ws.ikey = c.take<uint32_t>(lim.keep_intermediates ? I : 1);
+  ws.cnt_bin = c.take<uint32_t>(lim.keep_intermediates ? N : 1);
+  ws.bin_table = c.take<uint4>(table);
+  ws.band_pool_cap = (uint32_t)(8 * N + 1024);
+  ws.band_pool = reinterpret_cast<BandEntry *>(c.take<char>(kBandEntryBytes * ws.band_pool_cap));
+  ws.band_lists = c.take<uint2>(band_list_words(lim.max_surfels, (lim.max_height + kTile - 1) / kTile));
+  ws.bin_offs = c.take<uint32_t>(table);
   ws.ranges = c.take<uint2>(tiles);
   ws.tile_mask = c.take<uint8_t>(tiles);
-  ws.mask_prefix = c.take<uint16_t>((size_t)((lim.max_height + kTile - 1) / kTile) *
-                                    (size_t)((lim.max_width + kTile - 1) / kTile + 1));
-  const size_t rs_words = radix_table_words(N > I ? N : I);
+  ws.mask_sat = c.take<uint32_t>((size_t)((lim.max_height + kTile - 1) / kTile + 1) *
+                                 (size_t)((lim.max_width + kTile - 1) / kTile + 1));
+  for (int e = 0; e < 2; ++e) {
+    ws.row_off[e] = c.take<uint32_t>(N);
+    ws.spans[e] = c.take<uint2>(I);
+  }
+  const size_t rs_words = radix_table_words(N);
   ws.rs_table = c.take<uint32_t>(rs_words);
   ws.rs_offs = c.take<uint32_t>(rs_words);
   ws.rs_n = c.take<uint32_t>(1);
@@ -82,7 +99,8 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
 bool limits_ok(const gs_limits *lim) {
   return lim && lim->max_surfels >= 0 && lim->max_width > 0 && lim->max_height > 0 && lim->max_instances > 0 &&
          lim->max_instances < (int64_t(1) << 30) && lim->max_rects > 0 &&
-         (int64_t)lim->max_width * lim->max_height < (int64_t(1) << 31) && lim->max_surfels < (1 << 30);
+         (int64_t)lim->max_width * lim->max_height < (int64_t(1) << 31) && lim->max_surfels < (1 << 30) &&
+         lim->max_width <= kMaxWidth && lim->max_height <= kMaxWidth;
 }
 
 __global__ void reset_counters_kernel(Counters *c) {
@@ -90,6 +108,8 @@ __global__ void reset_counters_kernel(Counters *c) {
     c->n_vis[0] = c->n_vis[1] = 0;
     c->n_inst[0] = c->n_inst[1] = 0;
     c->n_sort[0] = c->n_sort[1] = 0;
+    c->n_rows[0] = c->n_rows[1] = 0;
+    c->n_band[0] = c->n_band[1] = 0;
     c->dmin_bits = 0x7f800000u;
     c->dmax_bits = 0u;
     c->n_rects = 0;
@@ -257,10 +277,11 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
     delete ctx;
     return GS_ERR_WORKSPACE;
   }
-  cudaError_t e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
+  cudaError_t e = prepare_binning((lim->max_width + kTile - 1) / kTile);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
   if (e != cudaSuccess) {
     delete ctx;
-    return cuda_fail(cudaGetLastError());
+    return cuda_fail(e);
   }
   *out = ctx;
   return GS_OK;
@@ -358,6 +379,7 @@ static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const PoseAr
   cudaError_t e = launch_setup_cams(pa, ctx->ws.cams, s);
   if (e != cudaSuccess) return cuda_fail(e);
   e = launch_preprocess(*scene, ctx->ws, pa.neyes, pa.W, pa.H, s);
+  for (int eye = 0; eye < pa.neyes && e == cudaSuccess; ++eye) e = launch_rows(ctx->ws, eye, scene->n, s);
   mark(ctx, 1);
   return cuda_status(e);
 }
@@ -606,7 +628,6 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
   int64_t n = -1;
   const int nt = ws.max_tiles;
   const int eye = (which & GS_BUF_EYE1) ? 1 : 0;
-  const int sb = sorted_buffer(ctx->last_tiles > 0 ? ctx->last_tiles : 1);
   // the last binning is the affiliated eye's when it ran, else the dominant eye's
   const int last = c.n_vis[1] || c.n_inst[1] ? 1 : 0;
   switch (which & ~GS_BUF_EYE1) {
@@ -615,8 +636,10 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
     case GS_BUF_BOUNDS: p = ws.bounds[eye]; b = ws.keep_intermediates ? 16 * N : 0; n = (int64_t)N; break;
     case GS_BUF_COUNTS: p = ws.cnt[eye]; b = 4 * N; n = (int64_t)N; break;
     case GS_BUF_DEPTH_ORDER: p = ws.dval[0]; b = 4 * N; n = c.n_vis[last]; break;
-    case GS_BUF_INST_KEYS: p = ws.ikey[sb]; b = 4 * I; n = c.n_sort[last]; break;
-    case GS_BUF_INST_VALS: p = ws.ival[sb]; b = 4 * I; n = c.n_sort[last]; break;
+    case GS_BUF_INST_KEYS:
+      if (!ws.keep_intermediates) return GS_ERR_BAD_ARG;
+      p = ws.ikey; b = 4 * I; n = c.n_sort[last]; break;
+    case GS_BUF_INST_VALS: p = ws.ival; b = 4 * I; n = c.n_sort[last]; break;
     case GS_BUF_RANGES: p = ws.ranges; b = 8 * (size_t)nt; n = nt; break;
     case GS_BUF_WARP: p = ws.warpbuf; b = 8 * P; n = (int64_t)P; break;
     case GS_BUF_TILE_MASK: p = ws.tile_mask; b = (size_t)nt; n = nt; break;
@@ -624,7 +647,9 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
     case GS_BUF_STRIPS: p = ws.strips; b = 64; n = 16; break;
     case GS_BUF_WARP_DEPTH: p = ws.warp_depth; b = 4 * P; n = (int64_t)P; break;
     case GS_BUF_PAIRS: p = &ws.ctr->pairs[0]; b = 32; n = 4; break;
-    case GS_BUF_BIN_COUNTS: p = ws.cnt_bin; b = 4 * N; n = (int64_t)N; break;
+    case GS_BUF_BIN_COUNTS:
+      if (!ws.keep_intermediates) return GS_ERR_BAD_ARG;
+      p = ws.cnt_bin; b = 4 * N; n = (int64_t)N; break;
     default: return GS_ERR_BAD_ARG;
   }
   *dev_ptr = p;

@@ -1,14 +1,18 @@
-// Tile binning: an on-device LSD radix sort of packed (tile id | depth) keys.
+// Tile binning: every tile's list of the surfels that can reach it, in the
+// order of the packed (tile id | depth) key sort of the 2DGS/3DGS tile
+// rasterizer.
 //
 // Paper: Sec. 3.1 Stage 1 and Sec. 3.5 (16x16 tiles of the 2DGS/3DGS tile
 // rasterizer; Sec. 2.2 keeps its depth ordering).
 //
-// The sort key of an instance is (tile id << 32) | float_bits(z_c). Every
-// instance of a surfel shares the depth digits, so the LSD passes over the low
-// 32 bits run on the visible surfels *before* they are duplicated into
-// instances, and only the tile digits are sorted per instance. LSD passes are
-// stable, so this yields exactly the order of a full 64-bit LSD sort of the
-// packed keys (ties broken by surfel index), with far less data moved.
+// Sorting by (tile, depth) is the same as sorting the surfels by depth first and
+// then grouping them by tile without changing their order. So the surfels are
+// radix sorted once on their 32 depth bits (ties keep the index order), and
+// the grouping by tile is a stable counting sort: the depth-ordered surfels are
+// cut into chunks, a first pass counts each chunk's hits per tile into a
+// [tile][chunk] table, one scan of that table gives every (tile, chunk) run its
+// place, and a second pass writes the surfel ids straight into their slots. The
+// per-instance (tile, surfel) pairs are never materialised or radix sorted.
 //
 // A surfel is binned to a tile only when its support can reach one of the
 // tile's pixel centres: the support {o Ghat >= 1/255} is the union of the
@@ -20,14 +24,12 @@
 // float32 keep their whole bounding rectangle.
 //
 // Pipeline per eye (all counts stay on the device):
-//   1. count the tiles each surfel reaches (warp-cooperative; ROI-masked tiles
-//      only when a mask is given)
-//   2. compact the surfels with a non-zero count (scan) -> (depth bits, id)
-//   3. radix sort over the 32 depth bits
-//   4. scan of the counts in depth order -> instance offsets
-//   5. emit (tile id, surfel id) in that order, coalesced per surfel
-//   6. radix sort over the tile-id bits (stable: depth order kept per tile)
-//   7. [start, end) range of every tile
+//   1. compact the surfels with a non-empty rectangle (reaching an ROI tile when
+//      a mask is given) -> (depth bits, id)
+//   2. radix sort over the 32 depth bits
+//   3. per-(tile, chunk) counts (bin_kernel, mode 0)
+//   4. tile-major scan of the counts -> run offsets, tile ranges
+//   5. placement of every surfel id (bin_kernel, mode 1)
 #include "gs_internal.cuh"
 #include "gs_scan.cuh"
 #include "gs_sort.cuh"
@@ -157,198 +159,139 @@ __device__ __forceinline__ void row_ranges(const Conic &q, const float4 r0, int 
   }
 }
 
-// Tiles of [lo, hi] in tile row ty set in the ROI mask, from the row prefix
-// counts mp[ty][x] = number of masked tiles of row ty left of column x.
-__device__ __forceinline__ int masked_in(const uint16_t *mp, int tiles_x, int ty, int lo, int hi) {
-  if (lo > hi) return 0;
-  const uint16_t *row = mp + (size_t)ty * (tiles_x + 1);
-  return (int)row[hi + 1] - (int)row[lo];
-}
-
-// Per-surfel tile count, one thread per surfel: rows of the bounding rectangle
-// are walked with the closed-form ranges. A surfel whose screen ellipse is too
-// thin and oblique for float32 (under 0.5% of surfels) keeps its whole bounding
-// rectangle: binning more tiles than needed never changes the image, because
-// the blend still evaluates alpha exactly, and it avoids a serial per-tile test.
-__global__ void __launch_bounds__(256) count_kernel(uint32_t n, const float4 *__restrict__ rec,
-                                                    const ushort4 *__restrict__ rect,
-                                                    const uint32_t *__restrict__ aabb_cnt,
-                                                    const uint8_t *__restrict__ mask, const uint16_t *__restrict__ mp,
-                                                    const CamBlock *__restrict__ cams, int eye,
-                                                    uint32_t *__restrict__ cnt_out) {
-  const uint32_t id = blockIdx.x * blockDim.x + threadIdx.x;
-  if (id >= n) return;
-  if (aabb_cnt[id] == 0u) {
-    cnt_out[id] = 0u;
-    return;
-  }
-  const int W = cams->eye[eye].W, H = cams->eye[eye].H, tiles_x = cams->eye[eye].tiles_x;
-  const float4 *r = rec + 4 * (size_t)id;
-  const float4 r0 = r[0], r1 = r[1], r2 = r[2];
-  const ushort4 rc = rect[id];
-  const Conic q = make_conic(r0, r1, r2);
-  uint32_t count = 0;
-  if (q.ok) {
-    for (int ty = rc.y; ty <= rc.w; ++ty) {
-      int a0, a1, c0, c1;
-      row_ranges(q, r0, ty, W, H, rc.x, rc.z, a0, a1, c0, c1);
-      if (mask) count += masked_in(mp, tiles_x, ty, a0, a1) + masked_in(mp, tiles_x, ty, c0, c1);
-      else count += (uint32_t)(max(a1 - a0 + 1, 0) + max(c1 - c0 + 1, 0));
+// Summed-area table of the ROI tile mask: sat[y][x] = masked tiles with row < y
+// and column < x, (tiles_y + 1) x (tiles_x + 1) entries. One block: rows, then
+// columns.
+__global__ void __launch_bounds__(1024) mask_sat_kernel(const uint8_t *__restrict__ mask, int tiles_x, int tiles_y,
+                                                        uint32_t *__restrict__ sat) {
+  const int sx = tiles_x + 1;
+  for (int y = threadIdx.x; y <= tiles_y; y += blockDim.x) {
+    uint32_t acc = 0;
+    sat[(size_t)y * sx] = 0u;
+    for (int x = 0; x < tiles_x; ++x) {
+      if (y > 0) acc += mask[(size_t)(y - 1) * tiles_x + x] ? 1u : 0u;
+      sat[(size_t)y * sx + x + 1] = acc;
     }
-  } else {
-    for (int ty = rc.y; ty <= rc.w; ++ty)
-      count += mask ? (uint32_t)masked_in(mp, tiles_x, ty, rc.x, rc.z) : (uint32_t)(rc.z - rc.x + 1);
   }
-  cnt_out[id] = count;
+  __syncthreads();
+  for (int x = threadIdx.x; x <= tiles_x; x += blockDim.x) {
+    uint32_t acc = 0;
+    for (int y = 1; y <= tiles_y; ++y) {
+      acc += sat[(size_t)y * sx + x];
+      sat[(size_t)y * sx + x] = acc;
+    }
+  }
 }
 
-// Emission, warp-cooperative: a warp takes one depth-sorted surfel at a time.
-// Lane r computes the ranges of tile row r of a 32-row chunk; a warp scan of
-// the row lengths gives every row's first slot, and each lane then fills slots
-// lane, lane + 32, ..., finding its row by a binary search over the scan
-// (consecutive lanes write consecutive slots). With a mask, rows are walked one
-// by one and masked tiles compacted by ballot. Ill-conditioned ellipses take
-// every tile of their rectangle (see count_kernel).
-__global__ void __launch_bounds__(256) emit_kernel(const uint32_t *__restrict__ ids, const uint32_t *n_ptr,
-                                                   uint32_t n_max, const float4 *__restrict__ rec,
-                                                   const ushort4 *__restrict__ rect, const uint8_t *__restrict__ mask,
+// Any ROI tile in tile rows [y0, y1] x columns [x0, x1]?
+__device__ __forceinline__ bool sat_any(const uint32_t *sat, int tiles_x, int y0, int y1, int x0, int x1) {
+  if (y0 > y1 || x0 > x1) return false;
+  const int sx = tiles_x + 1;
+  const uint32_t v = sat[(size_t)(y1 + 1) * sx + x1 + 1] - sat[(size_t)y0 * sx + x1 + 1] -
+                     sat[(size_t)(y1 + 1) * sx + x0] + sat[(size_t)y0 * sx + x0];
+  return v != 0u;
+}
+
+// ---------------------------------------------------------------- row spans
+// Once per eye and frame, every tile row of every surfel's bounding rectangle
+// gets its tile ranges [a0, a1] u [c0, c1] (row_ranges; an ill-conditioned
+// ellipse keeps the whole row of its rectangle), packed as 4 x 16 bits. A warp
+// takes 32 consecutive surfels (one per lane), reserves slots for all their rows
+// with one atomic, and then computes the rows 32 at a time, one per lane, so no
+// lane idles while another walks a large surfel. row_off[i] is the slot of
+// surfel i's first rectangle row.
+__global__ void __launch_bounds__(256) rows_kernel(uint32_t n, const float4 *__restrict__ rec,
+                                                   const ushort4 *__restrict__ rect, const uint32_t *__restrict__ cnt,
                                                    const CamBlock *__restrict__ cams, int eye,
-                                                   const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ offs,
-                                                   uint32_t cap, uint32_t *__restrict__ ikey,
-                                                   uint32_t *__restrict__ ival, uint32_t *__restrict__ n_sort) {
+                                                   uint32_t *__restrict__ row_off, uint2 *__restrict__ spans,
+                                                   uint32_t cap, uint32_t *__restrict__ n_rows,
+                                                   uint32_t *__restrict__ status) {
   const int lane = threadIdx.x & 31;
-  const uint32_t lt = (1u << lane) - 1u;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t n = load_n(n_ptr, n_max);
-  const int W = cams->eye[eye].W, H = cams->eye[eye].H, tiles_x = cams->eye[eye].tiles_x;
-  for (uint32_t j = warp; j < n; j += nwarps) {
-    const uint32_t id = ids[j];
-    const uint32_t base = offs[j];
-    const uint32_t c = cnt[id];  // slots reserved for this surfel: never written past
-    if ((uint64_t)base + c > cap) {
-      // the first surfel that does not fit ends the binned instances
-      if (lane == 0 && base <= cap) atomicMin(n_sort, base);
-      continue;
-    }
-    const float4 *r = rec + 4 * (size_t)id;
+  const uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+  if (i0 >= n) return;  // warp-uniform
+  const uint32_t i = i0 + (uint32_t)lane;
+  const int W = cams->eye[eye].W, H = cams->eye[eye].H;
+  int nr = 0, ry = 0, rx0 = 0, rx1 = -1;
+  Conic q{};
+  float cx = 0.f, cy = 0.f;
+  if (i < n && cnt[i] > 0u) {
+    const ushort4 rc = rect[i];
+    nr = (int)rc.w - (int)rc.y + 1;
+    ry = rc.y;
+    rx0 = rc.x;
+    rx1 = rc.z;
+    const float4 *r = rec + 4 * (size_t)i;
     const float4 r0 = r[0], r1 = r[1], r2 = r[2];
-    const ushort4 rc = rect[id];
-    const int rows = rc.w - rc.y + 1;
-    const Conic q = make_conic(r0, r1, r2);
-    uint32_t count = 0;
-    if (q.ok) {
-      for (int rb = 0; rb < rows; rb += 32) {
-        int a0 = 1, a1 = 0, c0 = 1, c1 = 0;
-        if (rb + lane < rows) row_ranges(q, r0, rc.y + rb + lane, W, H, rc.x, rc.z, a0, a1, c0, c1);
-        if (!mask) {
-          const int len0 = max(a1 - a0 + 1, 0);
-          const int len = len0 + max(c1 - c0 + 1, 0);
-          int incl = len;
+    q = make_conic(r0, r1, r2);
+    cx = r0.x;
+    cy = r0.y;
+  }
+  int incl = nr;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-          }
-          const int total = __shfl_sync(0xffffffffu, incl, 31);
-          // warp-uniform trip count: every lane takes part in the shuffles
-          for (int s0 = 0; s0 < total; s0 += 32) {
-            const int s = s0 + lane;
-            // row of slot s: the first lane whose inclusive prefix exceeds s
-            int lo = 0, hi = 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  uint32_t base = 0;
+  if (lane == 31 && total > 0) base = atomicAdd(n_rows, (uint32_t)total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  if (lane == 0 && total > 0 && (uint64_t)base + (uint64_t)total > cap) atomicOr(status, kStCapacity);
+  if (i < n) row_off[i] = base + (uint32_t)(incl - nr);
+  for (int q0 = 0; q0 < total; q0 += 32) {
+    const int qq = q0 + lane;
+    int kl = 0, kh = 31;
 #pragma unroll
-            for (int it = 0; it < 5; ++it) {
-              const int mid = (lo + hi) >> 1;
-              if (__shfl_sync(0xffffffffu, incl, mid) > s) hi = mid; else lo = mid + 1;
-            }
-            const int row = lo;
-            const int before = __shfl_sync(0xffffffffu, incl - len, row);
-            const int rs0 = __shfl_sync(0xffffffffu, a0, row);
-            const int rl0 = __shfl_sync(0xffffffffu, len0, row);
-            const int rt0 = __shfl_sync(0xffffffffu, c0, row);
-            const int o = s - before;
-            const int tx = o < rl0 ? rs0 + o : rt0 + (o - rl0);
-            if (s < total && count + (uint32_t)s < c) {
-              const uint32_t pos = base + count + (uint32_t)s;
-              ikey[pos] = (uint32_t)((rc.y + rb + row) * tiles_x + tx);
-              ival[pos] = id;
-            }
-          }
-          count += (uint32_t)total;
-          continue;
-        }
-        const int nr = min(32, rows - rb);
-        for (int k = 0; k < nr; ++k) {
-          const int ty_k = rc.y + rb + k;
-          const int s0 = __shfl_sync(0xffffffffu, a0, k), s1 = __shfl_sync(0xffffffffu, a1, k);
-          const int u0 = __shfl_sync(0xffffffffu, c0, k), u1 = __shfl_sync(0xffffffffu, c1, k);
-          const int len0 = max(s1 - s0 + 1, 0), len = len0 + max(u1 - u0 + 1, 0);
-          for (int t0 = 0; t0 < len; t0 += 32) {
-            const int t = t0 + lane;
-            bool hit = false;
-            uint32_t tile = 0;
-            if (t < len) {
-              const int tx = t < len0 ? s0 + t : u0 + (t - len0);
-              tile = (uint32_t)(ty_k * tiles_x + tx);
-              hit = mask[tile] != 0;
-            }
-            const uint32_t ballot = __ballot_sync(0xffffffffu, hit);
-            const uint32_t rank = count + __popc(ballot & lt);
-            if (hit && rank < c) {
-              ikey[base + rank] = tile;
-              ival[base + rank] = id;
-            }
-            count += __popc(ballot);
-          }
-        }
-      }
-    } else {
-      const int w = rc.z - rc.x + 1;
-      const int total = w * rows;
-      for (int t0 = 0; t0 < total; t0 += 32) {
-        const int t = t0 + lane;
-        bool hit = false;
-        uint32_t tile = 0;
-        if (t < total) {
-          const int tx = rc.x + t % w, ty = rc.y + t / w;
-          tile = (uint32_t)(ty * tiles_x + tx);
-          hit = !mask || mask[tile];  // the whole rectangle, as counted
-        }
-        const uint32_t ballot = __ballot_sync(0xffffffffu, hit);
-        const uint32_t rank = count + __popc(ballot & lt);
-        if (hit && rank < c) {
-          ikey[base + rank] = tile;
-          ival[base + rank] = id;
-        }
-        count += __popc(ballot);
-      }
+    for (int it = 0; it < 5; ++it) {
+      const int mid = (kl + kh) >> 1;
+      if (__shfl_sync(0xffffffffu, incl, mid) > qq) kh = mid; else kl = mid + 1;
     }
-    // should a recount come out below the reserved slots, fill the rest with a
-    // tile id past every real tile (sorted last, never ranged, never blended)
-    for (uint32_t s = count + lane; s < c; s += 32) {
-      ikey[base + s] = 0xffffffffu;
-      ival[base + s] = id;
+    const int k = kl;
+    const int excl_k = __shfl_sync(0xffffffffu, incl, k) - __shfl_sync(0xffffffffu, nr, k);
+    const int ty = __shfl_sync(0xffffffffu, ry, k) + (qq - excl_k);
+    const int sx0 = __shfl_sync(0xffffffffu, rx0, k), sx1 = __shfl_sync(0xffffffffu, rx1, k);
+    Conic qk;
+    qk.Sxx = __shfl_sync(0xffffffffu, q.Sxx, k);
+    qk.Sxy = __shfl_sync(0xffffffffu, q.Sxy, k);
+    qk.Syy = __shfl_sync(0xffffffffu, q.Syy, k);
+    qk.gx = __shfl_sync(0xffffffffu, q.gx, k);
+    qk.gy = __shfl_sync(0xffffffffu, q.gy, k);
+    qk.h = __shfl_sync(0xffffffffu, q.h, k);
+    qk.dcx = __shfl_sync(0xffffffffu, q.dcx, k);
+    qk.dcy = __shfl_sync(0xffffffffu, q.dcy, k);
+    qk.ex = __shfl_sync(0xffffffffu, q.ex, k);
+    qk.ey = __shfl_sync(0xffffffffu, q.ey, k);
+    qk.rl2 = __shfl_sync(0xffffffffu, q.rl2, k);
+    qk.inv_sxx = __shfl_sync(0xffffffffu, q.inv_sxx, k);
+    qk.slope = __shfl_sync(0xffffffffu, q.slope, k);
+    qk.ok = __shfl_sync(0xffffffffu, q.ok ? 1 : 0, k) != 0;
+    const float4 ck = make_float4(__shfl_sync(0xffffffffu, cx, k), __shfl_sync(0xffffffffu, cy, k), 0.f, 0.f);
+    const uint32_t slot = base + (uint32_t)qq;
+    if (qq < total && slot < cap) {
+      int a0 = sx0, a1 = sx1, c0 = 1, c1 = 0;
+      if (qk.ok) row_ranges(qk, ck, ty, W, H, sx0, sx1, a0, a1, c0, c1);
+      // empty ranges are stored as [1, 0]
+      if (a0 > a1) { a0 = 1; a1 = 0; }
+      if (c0 > c1) { c0 = 1; c1 = 0; }
+      spans[slot] = make_uint2((uint32_t)a0 | ((uint32_t)a1 << 16), (uint32_t)c0 | ((uint32_t)c1 << 16));
     }
   }
 }
 
-// Row prefix counts of the ROI tile mask: mp[ty][x] = masked tiles of row ty
-// with column < x (one thread per row).
-__global__ void mask_prefix_kernel(const uint8_t *__restrict__ mask, int tiles_x, int tiles_y, uint16_t *__restrict__ mp) {
-  const int ty = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ty >= tiles_y) return;
-  uint16_t *row = mp + (size_t)ty * (tiles_x + 1);
-  int acc = 0;
-  row[0] = 0;
-  for (int tx = 0; tx < tiles_x; ++tx) {
-    acc += mask[ty * tiles_x + tx] ? 1 : 0;
-    row[tx + 1] = (uint16_t)acc;
-  }
-}
-
-struct FlagLoad {
+// ---------------------------------------------------------------- compaction
+// A surfel enters the depth sort when its bounding rectangle is not empty and,
+// for an ROI binning, when that rectangle holds at least one ROI tile.
+struct VisibleLoad {
   const uint32_t *cnt;
-  __device__ uint32_t operator()(uint32_t i) const { return cnt[i] > 0u ? 1u : 0u; }
+  const ushort4 *rect;
+  const uint32_t *sat;  // summed-area table of the ROI mask, or null
+  int tiles_x;
+  __device__ uint32_t operator()(uint32_t i) const {
+    if (cnt[i] == 0u) return 0u;
+    if (!sat) return 1u;
+    const ushort4 rc = rect[i];
+    return sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z) ? 1u : 0u;
+  }
 };
 
 struct CompactApply {
@@ -364,51 +307,386 @@ struct CompactApply {
   __device__ void end(uint32_t, uint32_t total) const { *n_out = total; }
 };
 
-struct SortedCountLoad {
-  const uint32_t *cnt;
-  const uint32_t *ids;
-  __device__ uint32_t operator()(uint32_t j) const { return cnt[ids[j]]; }
+// ---------------------------------------------------------------- counting sort by tile
+//
+// The depth-ordered surfels are cut into chunks of kBinWarps sub-chunks of
+// `warp_surfels` consecutive surfels (one per warp) and the tile rows into bands
+// of kBandRows.
+//
+//   band lists (one CTA per chunk): every warp lists, per band, the surfels of
+//     its sub-chunk that reach the band (in depth order) with the span slot and
+//     rows of their band part;
+//   mode 0 (CTA per (chunk, band)): each warp counts its list's hits per tile;
+//     the 8 counts of a (tile, chunk) go to table[tile][chunk] as 8 x 16 bits;
+//   (a tile-major scan of the per-(tile, chunk) sums gives offs[tile][chunk],
+//    where chunk c's run of the tile starts; offs[tile][0] starts the tile's list)
+//   mode 1: each warp starts at offs[tile][c] plus the counts of the warps before
+//     it and writes every surfel id to its slot.
+//
+// In modes 0 and 1 every warp keeps private per-tile counters for the band in
+// shared memory and walks its list's rows 32 at a time, one (surfel, tile row)
+// per lane, reading the row's tile ranges from the spans. The lanes of one step
+// hold rows of surfels in depth order; lanes that reach the same tile are ranked
+// by a per-tile bit mask of lanes, so every tile's list comes out in depth
+// order. Both modes run the same walk code in one kernel, so the counts of mode
+// 0 and the slots written in mode 1 always agree.
+constexpr int kBinWarps = 8;
+constexpr int kBinThreads = kBinWarps * 32;
+constexpr int kBandRows = 4;
+constexpr int kMaxBands = 128;  // image height <= kMaxBands * kBandRows * kTile = 8192 pixels
+
+// One (surfel, band) entry: surfel id, span slot of its first row in the band,
+// first row << 4 | rows in the band (1..kBandRows).
+struct BandEntry {
+  uint32_t id, sp, rows;
+};
+static_assert(sizeof(BandEntry) == kBandEntryBytes, "band entry layout");
+
+struct BandArgs {
+  const uint32_t *ids;     // depth-ordered binned surfels
+  const uint32_t *n_vis;
+  uint32_t n_max;
+  const ushort4 *rect;
+  const uint32_t *row_off;
+  const uint32_t *sat;     // ROI mask summed-area table, or null
+  int tiles_x, tiles_y;
+  uint32_t warp_surfels;
+  BandEntry *pool;         // all lists
+  uint32_t pool_cap;
+  uint32_t *pool_n;        // entries taken (device counter)
+  uint2 *lists;            // [chunk][band][warp]: (first entry, entries)
+  uint32_t *status;
 };
 
-struct OffsetApply {
+__global__ void __launch_bounds__(kBinThreads) band_list_kernel(BandArgs a) {
+  __shared__ uint32_t s_cnt[kBinWarps][kMaxBands];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t nv = load_n(a.n_vis, a.n_max);
+  const uint32_t c = blockIdx.x;
+  const uint32_t chunk = kBinWarps * a.warp_surfels;
+  const int nb = (a.tiles_y + kBandRows - 1) / kBandRows;
+  uint2 *my_lists = a.lists + ((size_t)c * nb) * kBinWarps + w;  // stride kBinWarps per band
+  uint32_t *cnt = s_cnt[w];
+  const uint32_t j0 = c * chunk + (uint32_t)w * a.warp_surfels;
+  const uint32_t j1 = min(j0 + a.warp_surfels, nv);
+  for (int b = lane; b < nb; b += 32) cnt[b] = 0u;
+  __syncwarp();
+  // pass 0 counts the entries per band, pass 1 writes them
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      uint32_t total = 0;
+      for (int b = 0; b < nb; ++b) total += cnt[b];
+      uint32_t base = 0;
+      if (lane == 0 && total > 0) base = atomicAdd(a.pool_n, total);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (lane == 0 && total > 0 && (uint64_t)base + total > a.pool_cap) atomicOr(a.status, kStCapacity);
+      __syncwarp();
+      if (lane == 0) {  // lists and their running write positions
+        uint32_t at = base;
+        for (int b = 0; b < nb; ++b) {
+          const uint32_t n = cnt[b];
+          const uint32_t keep = at >= a.pool_cap ? 0u : min(n, a.pool_cap - at);
+          my_lists[(size_t)b * kBinWarps] = make_uint2(at, keep);
+          cnt[b] = at;
+          at += n;
+        }
+      }
+      __syncwarp();
+    }
+    for (uint32_t sub = j0; sub < j1; sub += 32) {  // warp-uniform
+      const uint32_t j = sub + (uint32_t)lane;
+      int b0 = 1, b1 = 0, y0 = 0, y1 = -1, x0 = 0, x1 = -1;
+      uint32_t id = 0, ro = 0;
+      if (j < j1) {
+        id = a.ids[j];
+        const ushort4 rc = a.rect[id];
+        y0 = rc.y; y1 = rc.w; x0 = rc.x; x1 = rc.z;
+        b0 = y0 / kBandRows;
+        b1 = y1 / kBandRows;
+        if (pass == 1) ro = a.row_off[id];
+      }
+      int bmin = b0 <= b1 ? b0 : 0x7fffffff, bmax = b0 <= b1 ? b1 : -1;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        bmin = min(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+        bmax = max(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+      }
+      for (int b = bmin; b <= bmax; ++b) {  // warp-uniform
+        const int lo = max(y0, b * kBandRows), hi = min(y1, b * kBandRows + kBandRows - 1);
+        bool in = b >= b0 && b <= b1 && lo <= hi;
+        if (in && a.sat) in = sat_any(a.sat, a.tiles_x, lo, hi, x0, x1);
+        const uint32_t ball = __ballot_sync(0xffffffffu, in);
+        if (pass == 0) {
+          if (lane == 0) cnt[b] += (uint32_t)__popc(ball);
+        } else {
+          const uint32_t at = cnt[b] + (uint32_t)__popc(ball & lt);
+          if (in && at < a.pool_cap)
+            a.pool[at] = BandEntry{id, ro + (uint32_t)(lo - y0), ((uint32_t)lo << 4) | (uint32_t)(hi - lo + 1)};
+          __syncwarp();
+          if (lane == 0) cnt[b] += (uint32_t)__popc(ball);
+        }
+        __syncwarp();
+      }
+    }
+  }
+}
+
+struct BinArgs {
+  const uint32_t *n_vis;   // binned surfels (device)
+  uint32_t n_max;
+  const BandEntry *pool;
+  const uint2 *lists;      // [chunk][band][warp]
+  const uint2 *spans;      // tile ranges of every rectangle row (rows_kernel)
+  uint32_t span_cap;
+  const uint8_t *mask;     // ROI tile mask, or null
+  int tiles_x, tiles_y;
+  uint32_t warp_surfels;   // surfels per warp sub-chunk (< 65536)
+  uint32_t nch;            // chunks (row length of the tables)
+  uint4 *table;            // [tile][chunk] 8 x 16-bit per-warp counts
+  const uint32_t *offs;    // [tile][chunk] exclusive offsets (mode 1)
+  uint32_t cap;            // instance capacity
+  uint32_t *ival;          // surfel id per instance
+  uint32_t *ikey;          // tile id per instance, or null
+  uint32_t *cnt_bin;       // tiles per surfel, or null (mode 0)
+};
+
+__device__ __forceinline__ int shi(int v, int k) { return __shfl_sync(0xffffffffu, v, k); }
+
+__device__ __forceinline__ uint32_t half16(const uint4 &v, int w) {
+  const uint32_t x = w < 2 ? v.x : w < 4 ? v.y : w < 6 ? v.z : v.w;
+  return (w & 1) ? x >> 16 : x & 0xffffu;
+}
+
+__global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(BinArgs a, int mode) {
+  extern __shared__ uint32_t s_dyn[];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const uint32_t nv = load_n(a.n_vis, a.n_max);
+  const uint32_t c = blockIdx.x;
+  if (c * kBinWarps * a.warp_surfels >= nv) return;  // the scan reads these counts as 0
+  const int tx_n = a.tiles_x;
+  const int nb = (a.tiles_y + kBandRows - 1) / kBandRows;
+  const int by0 = (int)blockIdx.y * kBandRows;
+  const int by1 = min(by0 + kBandRows, a.tiles_y) - 1;
+  const int BT = (by1 - by0 + 1) * tx_n;
+  const int BTmax = kBandRows * tx_n;
+  uint32_t *s_cnt = s_dyn;                      // [kBinWarps][BTmax]
+  uint32_t *s_msk = s_dyn + kBinWarps * BTmax;  // [kBinWarps][BTmax], mode 1
+  const size_t t0 = (size_t)by0 * tx_n;         // first tile of the band
+  const uint2 *lists = a.lists + ((size_t)c * nb + blockIdx.y) * kBinWarps;
+  if (!__syncthreads_or(tid < kBinWarps && lists[tid].y > 0u)) {  // nothing reaches the band
+    if (mode == 0)
+      for (int bt = tid; bt < BT; bt += kBinThreads) a.table[(t0 + bt) * a.nch + c] = make_uint4(0, 0, 0, 0);
+    return;
+  }
+  if (mode == 0) {
+    for (int i = tid; i < kBinWarps * BTmax; i += kBinThreads) s_dyn[i] = 0u;
+  } else {  // each warp's first slot per tile; masks cleared
+    for (int bt = tid; bt < BT; bt += kBinThreads) {
+      const size_t e = (t0 + bt) * a.nch + c;
+      const uint4 v = a.table[e];
+      uint32_t base = a.offs[e];
+#pragma unroll
+      for (int ww = 0; ww < kBinWarps; ++ww) {
+        s_cnt[ww * BTmax + bt] = base;
+        s_msk[ww * BTmax + bt] = 0u;
+        base += half16(v, ww);
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t *my_cnt = s_cnt + w * BTmax;
+  uint32_t *my_msk = s_msk + w * BTmax;
+  const uint2 li = lists[w];
+  const BandEntry *q = a.pool + li.x;
+  const int qn = (int)li.y;
+  // all loops below are warp-uniform: qn, qpos and total agree on all lanes
+  int qpos = 0, rdone = 0;  // list cursor; rows of entry qpos already taken
+  while (qpos < qn) {
+    const int e = qpos + lane;
+    uint32_t id = 0, sp = 0;
+    int lo = 0, nr = 0;
+    if (e < qn) {
+      const BandEntry en = q[e];
+      id = en.id;
+      sp = en.sp;
+      lo = (int)(en.rows >> 4);
+      nr = (int)(en.rows & 15u);
+      if (lane == 0) {
+        lo += rdone;
+        sp += (uint32_t)rdone;
+        nr -= rdone;
+      }
+    }
+    int incl = nr;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const int total = shi(incl, 31);
+    int kl = 0, kh = 31;  // entry of row `lane`: first lane whose inclusive prefix exceeds it
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const int mid = (kl + kh) >> 1;
+      if (shi(incl, mid) > lane) kh = mid; else kl = mid + 1;
+    }
+    const int k = kl;
+    const bool act = lane < total;
+    const uint32_t sid = (uint32_t)shi((int)id, k);
+    const int excl_k = shi(incl, k) - shi(nr, k);
+    const int ty = shi(lo, k) + (lane - excl_k);
+    const uint32_t spk = (uint32_t)shi((int)sp, k) + (uint32_t)(lane - excl_k);
+    // advance past the rows taken in this step
+    if (total <= 32) {
+      qpos += 32;
+      rdone = 0;
+    } else {
+      int ml = 0, mh = 31;  // entry holding row 31
+#pragma unroll
+      for (int it = 0; it < 5; ++it) {
+        const int mid = (ml + mh) >> 1;
+        if (shi(incl, mid) > 31) mh = mid; else ml = mid + 1;
+      }
+      const int taken = 32 - (shi(incl, ml) - shi(nr, ml));
+      if (taken == shi(nr, ml)) {
+        qpos += ml + 1;
+        rdone = 0;
+      } else {
+        rdone = (ml == 0 ? rdone : 0) + taken;
+        qpos += ml;
+      }
+    }
+    int a0 = 1, a1 = 0, c0 = 1, c1 = 0;
+    if (act && spk < a.span_cap) {
+      const uint2 v = a.spans[spk];
+      a0 = (int)(v.x & 0xffffu);
+      a1 = (int)(v.x >> 16);
+      c0 = (int)(v.y & 0xffffu);
+      c1 = (int)(v.y >> 16);
+    }
+    const int rowb = (ty - by0) * tx_n;
+    const uint8_t *mrow = a.mask ? a.mask + (size_t)ty * tx_n : nullptr;
+    if (mode == 0) {
+      uint32_t nrow = 0;
+      for (int s2 = 0; s2 < 2; ++s2)
+        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
+          if (!mrow || mrow[tx]) {
+            atomicAdd(&my_cnt[rowb + tx], 1u);
+            ++nrow;
+          }
+      if (a.cnt_bin && nrow) atomicAdd(&a.cnt_bin[sid], nrow);
+    } else {
+      for (int s2 = 0; s2 < 2; ++s2)
+        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
+          if (!mrow || mrow[tx]) atomicOr(&my_msk[rowb + tx], 1u << lane);
+      __syncwarp();
+      for (int s2 = 0; s2 < 2; ++s2)
+        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
+          if (!mrow || mrow[tx]) {
+            const int bt = rowb + tx;
+            const uint32_t pos = my_cnt[bt] + (uint32_t)__popc(my_msk[bt] & lt);
+            if (pos < a.cap) {
+              a.ival[pos] = sid;
+              if (a.ikey) a.ikey[pos] = (uint32_t)(ty * tx_n + tx);
+            }
+          }
+      __syncwarp();
+      // the highest lane on a tile advances its counter and clears its mask
+      for (int s2 = 0; s2 < 2; ++s2)
+        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
+          if (!mrow || mrow[tx]) {
+            const int bt = rowb + tx;
+            const uint32_t m = my_msk[bt];
+            if (m != 0u && lane == 31 - __clz(m)) {
+              my_cnt[bt] += (uint32_t)__popc(m);
+              my_msk[bt] = 0u;
+            }
+          }
+      __syncwarp();
+    }
+  }
+  if (mode == 0) {
+    __syncthreads();
+    for (int bt = tid; bt < BT; bt += kBinThreads) {
+      uint32_t h[kBinWarps];
+#pragma unroll
+      for (int ww = 0; ww < kBinWarps; ++ww) h[ww] = s_cnt[ww * BTmax + bt];
+      a.table[(t0 + bt) * a.nch + c] =
+          make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+    }
+  }
+}
+
+// Sum of a (tile, chunk)'s per-warp counts; chunks past the binned surfels read as 0.
+struct BinTableLoad {
+  const uint4 *table;
+  const uint32_t *n_vis;
+  uint32_t n_max, nch, chunk;
+  __device__ uint32_t operator()(uint32_t i) const {
+    if ((i % nch) * chunk >= load_n(n_vis, n_max)) return 0u;
+    const uint4 v = table[i];
+    const uint32_t lo = (v.x & 0xffffu) + (v.y & 0xffffu) + (v.z & 0xffffu) + (v.w & 0xffffu);
+    return lo + (v.x >> 16) + (v.y >> 16) + (v.z >> 16) + (v.w >> 16);
+  }
+};
+
+struct BinOffsetApply {
   uint32_t *offs;
-  uint32_t *n_inst;
-  uint32_t *n_sort;
+  uint32_t *n_inst, *n_sort;
   uint32_t cap;
   uint32_t *status;
-  __device__ void operator()(uint32_t j, uint32_t prefix, uint32_t) const { offs[j] = prefix; }
-  __device__ void end(uint32_t n, uint32_t total) const {
-    offs[n] = total;
+  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const { offs[i] = prefix; }
+  __device__ void end(uint32_t, uint32_t total) const {
     *n_inst = total;
     *n_sort = total < cap ? total : cap;
     if (total > cap) atomicOr(status, kStCapacity);
   }
 };
 
-__global__ void __launch_bounds__(256) ranges_kernel(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ n_ptr,
-                                                     uint32_t ntiles, uint2 *__restrict__ ranges) {
-  const uint32_t n = *n_ptr;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint32_t t = keys[i];
-    if (t >= ntiles) continue;
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = i;
-    if (i == n - 1 || keys[i + 1] != t) ranges[t].y = i + 1;
-  }
+__global__ void bin_ranges_kernel(const uint32_t *__restrict__ offs, uint32_t nch, int ntiles,
+                                  const uint32_t *__restrict__ n_inst, uint32_t cap, uint2 *__restrict__ ranges) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ntiles) return;
+  const uint32_t s0 = offs[(size_t)t * nch];
+  const uint32_t s1 = t + 1 < ntiles ? offs[(size_t)(t + 1) * nch] : *n_inst;
+  ranges[t] = make_uint2(min(s0, cap), min(s1, cap));
 }
 
-static int bits_for(int ntiles) {
-  int b = 0;
-  while ((1 << b) < ntiles) ++b;
-  return b < 1 ? 1 : b;
+uint32_t bin_warp_surfels(int max_surfels) {
+  const uint32_t per = ((uint32_t)max_surfels + kBinWarps * 256 - 1) / (kBinWarps * 256);
+  uint32_t r = (per + 31) / 32 * 32;
+  if (r < 64) r = 64;
+  if (r > 32768) r = 32768;  // per-warp counts are 16-bit
+  return r;
 }
 
-// Buffer index holding the sorted instances: one pass per 8 tile bits, each pass
-// flips between the two buffers.
-int sorted_buffer(int ntiles) { return ((bits_for(ntiles) + 7) / 8) & 1; }
+size_t band_list_words(int max_surfels, int max_tiles_y) {
+  return (size_t)bin_chunks(max_surfels) * ((max_tiles_y + kBandRows - 1) / kBandRows) * kBinWarps;
+}
 
-static int warp_grid(uint32_t n) {
-  const uint32_t blocks = (n + 7) / 8;  // 8 warps per block, one surfel per warp
-  return (int)(blocks < 1 ? 1 : (blocks > 152 * 16 ? 152 * 16 : blocks));
+uint32_t bin_chunks(int max_surfels) {
+  const uint32_t chunk = kBinWarps * bin_warp_surfels(max_surfels);
+  const uint32_t n = ((uint32_t)max_surfels + chunk - 1) / chunk;
+  return n < 1 ? 1 : n;
+}
+
+size_t bin_smem_bytes(int tiles_x) { return 2 * sizeof(uint32_t) * kBinWarps * kBandRows * (size_t)tiles_x; }
+
+cudaError_t prepare_binning(int max_tiles_x) {
+  return cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bin_smem_bytes(max_tiles_x));
+}
+
+cudaError_t launch_rows(const Workspace &ws, int eye, int n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  rows_kernel<<<(n + 255) / 256, 256, 0, s>>>((uint32_t)n, ws.rec[eye], ws.rect[eye], ws.cnt[eye], ws.cams, eye,
+                                              ws.row_off[eye], ws.spans[eye], (uint32_t)ws.max_instances,
+                                              &ws.ctr->n_rows[eye], &ws.ctr->status);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
@@ -418,42 +696,74 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   const int ntiles = tiles_x * tiles_y;
   const uint32_t cap = (uint32_t)ws.max_instances;
   const RadixScratch rs{ws.rs_table, ws.rs_offs, ws.rs_n, ws.rs_sums};
-  if ((err = cudaMemsetAsync(ws.ranges, 0, sizeof(uint2) * (size_t)ntiles, s)) != cudaSuccess) return err;
-  // 1. exact tile counts
   if (tile_mask) {
-    mask_prefix_kernel<<<(tiles_y + 127) / 128, 128, 0, s>>>(tile_mask, tiles_x, tiles_y, ws.mask_prefix);
+    mask_sat_kernel<<<1, 1024, 0, s>>>(tile_mask, tiles_x, tiles_y, ws.mask_sat);
     GS_LAUNCHED(1);
   }
-  if (n > 0) {
-    count_kernel<<<(n + 255) / 256, 256, 0, s>>>((uint32_t)n, ws.rec[eye], ws.rect[eye], ws.cnt[eye], tile_mask,
-                                                 ws.mask_prefix, ws.cams, eye, ws.cnt_bin);
-    GS_LAUNCHED(1);
-  }
-  // 2. compact the binned surfels: (depth bits, surfel id)
-  err = scan_launch(FlagLoad{ws.cnt_bin}, CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
+  // 1. compact the binned surfels: (depth bits, surfel id)
+  err = scan_launch(VisibleLoad{ws.cnt[eye], ws.rect[eye], tile_mask ? ws.mask_sat : nullptr, tiles_x},
+                    CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
                     (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, nullptr, s);
   if (err != cudaSuccess) return err;
-  // 3. depth digits (the low 32 bits of the packed key)
+  // 2. depth order (the low 32 bits of the packed key; stable, so ties keep id order)
   int which = 0;
   if ((err = radix_sort(ws.dkey, ws.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
     return err;
-  const uint32_t *ids = ws.dval[which];
-  // 4. instance offsets in depth order
-  err = scan_launch(SortedCountLoad{ws.cnt_bin, ids},
-                    OffsetApply{ws.offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status}, &ctr->n_vis[eye],
-                    (uint32_t)n, ws.scan_sums, nullptr, s);
-  if (err != cudaSuccess) return err;
-  // 5. emission
-  emit_kernel<<<warp_grid((uint32_t)n), 256, 0, s>>>(ids, &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye], ws.rect[eye],
-                                                     tile_mask, ws.cams, eye, ws.cnt_bin, ws.offs, cap, ws.ikey[0],
-                                                     ws.ival[0], &ctr->n_sort[eye]);
+  const int nbands = (tiles_y + kBandRows - 1) / kBandRows;
+  // 3. per chunk: each warp's depth-ordered (surfel, band) lists
+  BandArgs ba;
+  ba.ids = ws.dval[which];
+  ba.n_vis = &ctr->n_vis[eye];
+  ba.n_max = (uint32_t)n;
+  ba.rect = ws.rect[eye];
+  ba.row_off = ws.row_off[eye];
+  ba.sat = tile_mask ? ws.mask_sat : nullptr;
+  ba.tiles_x = tiles_x;
+  ba.tiles_y = tiles_y;
+  ba.warp_surfels = ws.bin_warp_surfels;
+  ba.pool = ws.band_pool;
+  ba.pool_cap = ws.band_pool_cap;
+  ba.pool_n = &ctr->n_band[eye];
+  ba.lists = ws.band_lists;
+  ba.status = &ctr->status;
+  if ((err = cudaMemsetAsync(&ctr->n_band[eye], 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
+  band_list_kernel<<<ws.bin_nch, kBinThreads, 0, s>>>(ba);
   GS_LAUNCHED(1);
-  // 6. tile digits (the high bits of the packed key)
-  if ((err = radix_sort(ws.ikey, ws.ival, &ctr->n_sort[eye], cap, bits_for(ntiles), rs, &which, s)) != cudaSuccess)
+  BinArgs a;
+  a.n_vis = &ctr->n_vis[eye];
+  a.n_max = (uint32_t)n;
+  a.pool = ws.band_pool;
+  a.lists = ws.band_lists;
+  a.spans = ws.spans[eye];
+  a.span_cap = (uint32_t)ws.max_instances;
+  a.mask = tile_mask;
+  a.tiles_x = tiles_x;
+  a.tiles_y = tiles_y;
+  a.warp_surfels = ws.bin_warp_surfels;
+  a.nch = ws.bin_nch;
+  a.table = ws.bin_table;
+  a.offs = ws.bin_offs;
+  a.cap = cap;
+  a.ival = ws.ival;
+  a.ikey = ws.keep_intermediates ? ws.ikey : nullptr;
+  a.cnt_bin = ws.keep_intermediates ? ws.cnt_bin : nullptr;
+  if (a.cnt_bin && n > 0 && (err = cudaMemsetAsync(a.cnt_bin, 0, sizeof(uint32_t) * (size_t)n, s)) != cudaSuccess)
     return err;
-  // 7. ranges
-  ranges_kernel<<<152 * 8, 256, 0, s>>>(ws.ikey[which], &ctr->n_sort[eye], (uint32_t)ntiles, ws.ranges);
+  const dim3 grid(ws.bin_nch, (unsigned)nbands);
+  // 4. per-warp counts per (tile, chunk)
+  bin_kernel<<<grid, kBinThreads, bin_smem_bytes(tiles_x) / 2, s>>>(a, 0);
   GS_LAUNCHED(1);
+  // 5. tile-major scan: where every (tile, chunk) run starts
+  err = scan_launch(BinTableLoad{ws.bin_table, &ctr->n_vis[eye], (uint32_t)n, ws.bin_nch,
+                                 kBinWarps * ws.bin_warp_surfels},
+                    BinOffsetApply{ws.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status},
+                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, ws.scan_sums, nullptr, s);
+  if (err != cudaSuccess) return err;
+  bin_ranges_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(ws.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
+                                                         ws.ranges);
+  // 6. every surfel id to its slot
+  bin_kernel<<<grid, kBinThreads, bin_smem_bytes(tiles_x), s>>>(a, 1);
+  GS_LAUNCHED(2);
   return cudaGetLastError();
 }
 

@@ -212,7 +212,7 @@ cudaError_t launch_blend(const Workspace &ws, int eye, int W, int H, const uint8
                          cudaStream_t s) {
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile, ntiles = tx * ty;
   if (ntiles == 0) return cudaSuccess;
-  const uint32_t *ids = ws.ival[sorted_buffer(ntiles)];
+  const uint32_t *ids = ws.ival;
   const bool m = tile_mask != nullptr;
 #define GS_BLEND(M, S, C) launch_variant<M, S, C>(ntiles, s, ws, ids, eye, tile_mask, bg, rgb, depth, trans, cls)
   if (m) {

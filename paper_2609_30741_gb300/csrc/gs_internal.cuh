@@ -56,7 +56,9 @@ struct Counters {
   uint32_t dmin_bits, dmax_bits;  // range of the normalised depth (positive float bits)
   uint32_t n_rects;      // centre components found
   uint32_t n_sort[2];    // instances actually binned per eye (capacity-clamped)
-  uint32_t pad[5];
+  uint32_t n_rows[2];    // (surfel, tile row) spans per eye
+  uint32_t n_band[2];    // (surfel, band) list entries of the last binning per eye
+  uint32_t pad[1];
   unsigned long long pairs[2];    // evaluated (pixel, surfel) pairs per eye (counting mode)
   unsigned long long contrib[2];  // of which contributed (alpha >= 1/255, before termination)
 };
@@ -81,13 +83,20 @@ struct Workspace {
   float4 *bounds[2];
   uint32_t *cnt[2];             // tiles of each surfel's bounding rectangle (0 = culled)
   uint32_t *zkey[2];            // float bits of the centre depth per surfel and eye
-  uint32_t *cnt_bin;            // tiles each surfel reaches in the last binning
+  uint32_t *cnt_bin;            // tiles each surfel reaches in the last binning (keep_intermediates)
   uint32_t *dkey[2], *dval[2];  // depth sort double buffers
-  uint32_t *offs;               // per-sorted-surfel instance offsets (+1)
-  uint32_t *ikey[2], *ival[2];  // instance sort double buffers
+  uint4 *bin_table;             // [tile][chunk] per-warp instance counts (8 x 16 bits)
+  struct BandEntry *band_pool;  // (surfel, band) entries of every warp's lists
+  uint32_t band_pool_cap;
+  uint2 *band_lists;            // [chunk][band][warp]: first entry, entries
+  uint32_t *bin_offs;           // their tile-major exclusive scan
+  uint32_t *ival;               // surfel id per instance, grouped by tile, depth order inside
+  uint32_t *ikey;               // tile id per instance (keep_intermediates)
   uint2 *ranges;
   uint8_t *tile_mask;
-  uint16_t *mask_prefix;        // row prefix counts of the tile mask [tiles_y][tiles_x + 1]
+  uint32_t *mask_sat;           // summed-area table of the tile mask [tiles_y + 1][tiles_x + 1]
+  uint32_t *row_off[2];         // per surfel and eye: slot of its first rectangle row in spans
+  uint2 *spans[2];              // per (surfel, tile row): tile ranges [a0, a1] u [c0, c1], 4 x 16 bits
   uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
   uint32_t *rs_n, *rs_sums;     // length of the table, scan block sums
   uint32_t *scan_sums;          // scan block sums
@@ -104,6 +113,7 @@ struct Workspace {
   int max_surfels, max_w, max_h, max_rects, max_tiles;
   int64_t max_instances, max_pixels;
   int keep_intermediates;
+  uint32_t bin_warp_surfels, bin_nch;  // binning chunk geometry (see launch_binning)
 };
 
 constexpr int kScanThreads = 512;
@@ -131,7 +141,16 @@ cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes
 // sorted per-tile instance lists and their ranges.
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
                            const uint8_t *tile_mask, cudaStream_t s);
-int sorted_buffer(int ntiles);
+// Tile ranges of every (surfel, tile row) of the eye's bounding rectangles;
+// after preprocessing, before any binning of the eye.
+cudaError_t launch_rows(const Workspace &ws, int eye, int n, cudaStream_t s);
+// Chunk geometry of the binning for a surfel capacity, and the one-time
+// shared-memory opt-in of its kernel for the widest image.
+uint32_t bin_warp_surfels(int max_surfels);
+uint32_t bin_chunks(int max_surfels);
+size_t band_list_words(int max_surfels, int max_tiles_y);
+constexpr size_t kBandEntryBytes = 12;
+cudaError_t prepare_binning(int max_tiles_x);
 cudaError_t launch_blend(const Workspace &ws, int eye, int W, int H, const uint8_t *tile_mask,
                          float3 bg, float *rgb, float *depth, float *trans, uint8_t *cls,
                          bool depth_stats, bool count_pairs, cudaStream_t s);

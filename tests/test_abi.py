@@ -51,11 +51,13 @@ def test_workspace_size_and_limit_checks(gslib):
     lim = gs.Limits(20000, 256, 192, 1 << 20, 1024, 0)
     n = C.c_size_t()
     assert gs.lib().gs_workspace_size(C.byref(lim), C.byref(n)) == gs.GS_OK
-    # records + rects + counts + depth keys for two eyes, instance double buffers
-    assert n.value > 2 * 20000 * 64 + 4 * (1 << 20) * 4
+    # records for two eyes and one surfel id per instance at least
+    assert n.value > 2 * 20000 * 64 + (1 << 20) * 4
     bad = gs.Limits(20000, 256, 192, 1 << 31, 1024, 0)  # instances must stay below 2^31
     assert gs.lib().gs_workspace_size(C.byref(bad), C.byref(n)) == gs.GS_ERR_BAD_ARG
     bad = gs.Limits(20000, 0, 192, 1 << 20, 1024, 0)
+    assert gs.lib().gs_workspace_size(C.byref(bad), C.byref(n)) == gs.GS_ERR_BAD_ARG
+    bad = gs.Limits(20000, 8200, 192, 1 << 20, 1024, 0)  # wider than the binning's shared memory allows
     assert gs.lib().gs_workspace_size(C.byref(bad), C.byref(n)) == gs.GS_ERR_BAD_ARG
 
 

@@ -149,7 +149,7 @@ def test_tile_rects_and_counts_bit_exact(gs, orc):
 
 def test_sorted_instances_bit_exact(gs, orc):
     scene, cam, dom, _ = synth.workload_small()
-    ctx = make_ctx(gs, scene, cam)
+    ctx = make_ctx(gs, scene, cam, keep_intermediates=True)
     ds = gs.DeviceScene(scene)
     ctx.render_mono(ds, dom, cam)
     ctx.check_ok()
