@@ -77,6 +77,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.rs_n = c.take<uint32_t>(1);
   ws.rs_sums = c.take<uint32_t>(rs_words / kScanTile + 2);
   ws.scan_sums = c.take<uint32_t>(scan_blocks);
+  ws.scan_ticket = c.take<uint32_t>(1);
   ws.warpbuf = c.take<unsigned long long>(P);
   ws.warp_depth = c.take<float>(P);
   ws.cls = c.take<uint8_t>(P);
@@ -279,6 +280,7 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
   }
   cudaError_t e = prepare_binning((lim->max_width + kTile - 1) / kTile);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.scan_ticket, 0, sizeof(uint32_t), ctx->stream);
   if (e != cudaSuccess) {
     delete ctx;
     return cuda_fail(e);
@@ -379,7 +381,6 @@ static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const PoseAr
   cudaError_t e = launch_setup_cams(pa, ctx->ws.cams, s);
   if (e != cudaSuccess) return cuda_fail(e);
   e = launch_preprocess(*scene, ctx->ws, pa.neyes, pa.W, pa.H, s);
-  for (int eye = 0; eye < pa.neyes && e == cudaSuccess; ++eye) e = launch_rows(ctx->ws, eye, scene->n, s);
   mark(ctx, 1);
   return cuda_status(e);
 }

@@ -26,10 +26,12 @@
 // Pipeline per eye (all counts stay on the device):
 //   1. compact the surfels with a non-empty rectangle (reaching an ROI tile when
 //      a mask is given) -> (depth bits, id)
-//   2. radix sort over the 32 depth bits
-//   3. per-(tile, chunk) counts (bin_kernel, mode 0)
-//   4. tile-major scan of the counts -> run offsets, tile ranges
-//   5. placement of every surfel id (bin_kernel, mode 1)
+//   2. tile ranges of every rectangle row of those surfels (rows_kernel)
+//   3. radix sort over the 32 depth bits
+//   4. per-chunk, per-warp lists of the surfels reaching each band of tile rows
+//   5. per-(tile, chunk) counts (bin_kernel, mode 0)
+//   6. tile-major scan of the counts -> run offsets, tile ranges
+//   7. placement of every surfel id (bin_kernel, mode 1)
 #include "gs_internal.cuh"
 #include "gs_scan.cuh"
 #include "gs_sort.cuh"
@@ -160,17 +162,22 @@ __device__ __forceinline__ void row_ranges(const Conic &q, const float4 r0, int 
 }
 
 // Summed-area table of the ROI tile mask: sat[y][x] = masked tiles with row < y
-// and column < x, (tiles_y + 1) x (tiles_x + 1) entries. One block: rows, then
-// columns.
+// and column < x, (tiles_y + 1) x (tiles_x + 1) entries. One block: each warp
+// takes whole rows (prefix counts by ballot, 32 columns at a time), then each
+// thread adds one column down the rows.
 __global__ void __launch_bounds__(1024) mask_sat_kernel(const uint8_t *__restrict__ mask, int tiles_x, int tiles_y,
                                                         uint32_t *__restrict__ sat) {
   const int sx = tiles_x + 1;
-  for (int y = threadIdx.x; y <= tiles_y; y += blockDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int y = wid; y <= tiles_y; y += nw) {
     uint32_t acc = 0;
-    sat[(size_t)y * sx] = 0u;
-    for (int x = 0; x < tiles_x; ++x) {
-      if (y > 0) acc += mask[(size_t)(y - 1) * tiles_x + x] ? 1u : 0u;
-      sat[(size_t)y * sx + x + 1] = acc;
+    if (lane == 0) sat[(size_t)y * sx] = 0u;
+    for (int x0 = 0; x0 < tiles_x; x0 += 32) {  // warp-uniform
+      const int x = x0 + lane;
+      const bool on = y > 0 && x < tiles_x && mask[(size_t)(y - 1) * tiles_x + x] != 0;
+      const uint32_t b = __ballot_sync(0xffffffffu, on);
+      if (x < tiles_x) sat[(size_t)y * sx + x + 1] = acc + (uint32_t)__popc(b & (0xffffffffu >> (31 - lane)));
+      acc += (uint32_t)__popc(b);
     }
   }
   __syncthreads();
@@ -200,21 +207,24 @@ __device__ __forceinline__ bool sat_any(const uint32_t *sat, int tiles_x, int y0
 // with one atomic, and then computes the rows 32 at a time, one per lane, so no
 // lane idles while another walks a large surfel. row_off[i] is the slot of
 // surfel i's first rectangle row.
-__global__ void __launch_bounds__(256) rows_kernel(uint32_t n, const float4 *__restrict__ rec,
+__global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ ids, const uint32_t *n_ptr,
+                                                   uint32_t n_max, const float4 *__restrict__ rec,
                                                    const ushort4 *__restrict__ rect, const uint32_t *__restrict__ cnt,
                                                    const CamBlock *__restrict__ cams, int eye,
                                                    uint32_t *__restrict__ row_off, uint2 *__restrict__ spans,
                                                    uint32_t cap, uint32_t *__restrict__ n_rows,
                                                    uint32_t *__restrict__ status) {
   const int lane = threadIdx.x & 31;
-  const uint32_t i0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
-  if (i0 >= n) return;  // warp-uniform
-  const uint32_t i = i0 + (uint32_t)lane;
+  const uint32_t n = load_n(n_ptr, n_max);
+  const uint32_t j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+  if (j0 >= n) return;  // warp-uniform
+  const uint32_t j = j0 + (uint32_t)lane;
+  const uint32_t i = j < n ? ids[j] : 0u;  // the surfels being binned
   const int W = cams->eye[eye].W, H = cams->eye[eye].H;
   int nr = 0, ry = 0, rx0 = 0, rx1 = -1;
   Conic q{};
   float cx = 0.f, cy = 0.f;
-  if (i < n && cnt[i] > 0u) {
+  if (j < n && cnt[i] > 0u) {
     const ushort4 rc = rect[i];
     nr = (int)rc.w - (int)rc.y + 1;
     ry = rc.y;
@@ -237,7 +247,7 @@ __global__ void __launch_bounds__(256) rows_kernel(uint32_t n, const float4 *__r
   if (lane == 31 && total > 0) base = atomicAdd(n_rows, (uint32_t)total);
   base = __shfl_sync(0xffffffffu, base, 31);
   if (lane == 0 && total > 0 && (uint64_t)base + (uint64_t)total > cap) atomicOr(status, kStCapacity);
-  if (i < n) row_off[i] = base + (uint32_t)(incl - nr);
+  if (j < n) row_off[i] = base + (uint32_t)(incl - nr);
   for (int q0 = 0; q0 < total; q0 += 32) {
     const int qq = q0 + lane;
     int kl = 0, kh = 31;
@@ -358,16 +368,21 @@ struct BandArgs {
   uint32_t *status;
 };
 
-__global__ void __launch_bounds__(kBinThreads) band_list_kernel(BandArgs a) {
-  __shared__ uint32_t s_cnt[kBinWarps][kMaxBands];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Band lists are built by small CTAs (kListWarps warps each) for parallelism;
+// CTA b of a chunk handles warps [b * kListWarps, (b + 1) * kListWarps).
+constexpr int kListWarps = 2;
+
+__global__ void __launch_bounds__(32 * kListWarps) band_list_kernel(BandArgs a) {
+  __shared__ uint32_t s_cnt[kListWarps][kMaxBands];
+  const int lane = threadIdx.x & 31;
+  const int w = (int)(blockIdx.x % (kBinWarps / kListWarps)) * kListWarps + (int)(threadIdx.x >> 5);
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t nv = load_n(a.n_vis, a.n_max);
-  const uint32_t c = blockIdx.x;
+  const uint32_t c = blockIdx.x / (kBinWarps / kListWarps);
   const uint32_t chunk = kBinWarps * a.warp_surfels;
   const int nb = (a.tiles_y + kBandRows - 1) / kBandRows;
   uint2 *my_lists = a.lists + ((size_t)c * nb) * kBinWarps + w;  // stride kBinWarps per band
-  uint32_t *cnt = s_cnt[w];
+  uint32_t *cnt = s_cnt[threadIdx.x >> 5];
   const uint32_t j0 = c * chunk + (uint32_t)w * a.warp_surfels;
   const uint32_t j1 = min(j0 + a.warp_surfels, nv);
   for (int b = lane; b < nb; b += 32) cnt[b] = 0u;
@@ -680,22 +695,13 @@ cudaError_t prepare_binning(int max_tiles_x) {
                               (int)bin_smem_bytes(max_tiles_x));
 }
 
-cudaError_t launch_rows(const Workspace &ws, int eye, int n, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
-  rows_kernel<<<(n + 255) / 256, 256, 0, s>>>((uint32_t)n, ws.rec[eye], ws.rect[eye], ws.cnt[eye], ws.cams, eye,
-                                              ws.row_off[eye], ws.spans[eye], (uint32_t)ws.max_instances,
-                                              &ws.ctr->n_rows[eye], &ws.ctr->status);
-  GS_LAUNCHED(1);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
                            const uint8_t *tile_mask, cudaStream_t s) {
   cudaError_t err;
   Counters *ctr = ws.ctr;
   const int ntiles = tiles_x * tiles_y;
   const uint32_t cap = (uint32_t)ws.max_instances;
-  const RadixScratch rs{ws.rs_table, ws.rs_offs, ws.rs_n, ws.rs_sums};
+  const RadixScratch rs{ws.rs_table, ws.rs_offs, ws.rs_n, ws.rs_sums, ws.scan_ticket};
   if (tile_mask) {
     mask_sat_kernel<<<1, 1024, 0, s>>>(tile_mask, tiles_x, tiles_y, ws.mask_sat);
     GS_LAUNCHED(1);
@@ -703,14 +709,23 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   // 1. compact the binned surfels: (depth bits, surfel id)
   err = scan_launch(VisibleLoad{ws.cnt[eye], ws.rect[eye], tile_mask ? ws.mask_sat : nullptr, tiles_x},
                     CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
-                    (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, nullptr, s);
+                    (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
   if (err != cudaSuccess) return err;
-  // 2. depth order (the low 32 bits of the packed key; stable, so ties keep id order)
+  // 2. tile ranges of every rectangle row of those surfels
+  if ((err = cudaMemsetAsync(&ctr->n_rows[eye], 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
+  if (n > 0) {
+    rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(ws.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
+                                                ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.row_off[eye],
+                                                ws.spans[eye], (uint32_t)ws.max_instances, &ctr->n_rows[eye],
+                                                &ctr->status);
+    GS_LAUNCHED(1);
+  }
+  // 3. depth order (the low 32 bits of the packed key; stable, so ties keep id order)
   int which = 0;
   if ((err = radix_sort(ws.dkey, ws.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
     return err;
   const int nbands = (tiles_y + kBandRows - 1) / kBandRows;
-  // 3. per chunk: each warp's depth-ordered (surfel, band) lists
+  // 4. per chunk: each warp's depth-ordered (surfel, band) lists
   BandArgs ba;
   ba.ids = ws.dval[which];
   ba.n_vis = &ctr->n_vis[eye];
@@ -727,7 +742,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   ba.lists = ws.band_lists;
   ba.status = &ctr->status;
   if ((err = cudaMemsetAsync(&ctr->n_band[eye], 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
-  band_list_kernel<<<ws.bin_nch, kBinThreads, 0, s>>>(ba);
+  band_list_kernel<<<ws.bin_nch * (kBinWarps / kListWarps), 32 * kListWarps, 0, s>>>(ba);
   GS_LAUNCHED(1);
   BinArgs a;
   a.n_vis = &ctr->n_vis[eye];
@@ -750,18 +765,19 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   if (a.cnt_bin && n > 0 && (err = cudaMemsetAsync(a.cnt_bin, 0, sizeof(uint32_t) * (size_t)n, s)) != cudaSuccess)
     return err;
   const dim3 grid(ws.bin_nch, (unsigned)nbands);
-  // 4. per-warp counts per (tile, chunk)
+  // 5. per-warp counts per (tile, chunk)
   bin_kernel<<<grid, kBinThreads, bin_smem_bytes(tiles_x) / 2, s>>>(a, 0);
   GS_LAUNCHED(1);
-  // 5. tile-major scan: where every (tile, chunk) run starts
+  // 6. tile-major scan: where every (tile, chunk) run starts
   err = scan_launch(BinTableLoad{ws.bin_table, &ctr->n_vis[eye], (uint32_t)n, ws.bin_nch,
                                  kBinWarps * ws.bin_warp_surfels},
                     BinOffsetApply{ws.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status},
-                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, ws.scan_sums, nullptr, s);
+                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, ws.scan_sums, ws.scan_ticket,
+                    nullptr, s);
   if (err != cudaSuccess) return err;
   bin_ranges_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(ws.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
                                                          ws.ranges);
-  // 6. every surfel id to its slot
+  // 7. every surfel id to its slot
   bin_kernel<<<grid, kBinThreads, bin_smem_bytes(tiles_x), s>>>(a, 1);
   GS_LAUNCHED(2);
   return cudaGetLastError();

@@ -100,6 +100,7 @@ struct Workspace {
   uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
   uint32_t *rs_n, *rs_sums;     // length of the table, scan block sums
   uint32_t *scan_sums;          // scan block sums
+  uint32_t *scan_ticket;        // scan completion counter, 0 between scans
   unsigned long long *warpbuf;
   float *warp_depth;
   uint8_t *cls;
@@ -141,9 +142,6 @@ cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes
 // sorted per-tile instance lists and their ranges.
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
                            const uint8_t *tile_mask, cudaStream_t s);
-// Tile ranges of every (surfel, tile row) of the eye's bounding rectangles;
-// after preprocessing, before any binning of the eye.
-cudaError_t launch_rows(const Workspace &ws, int eye, int n, cudaStream_t s);
 // Chunk geometry of the binning for a surfel capacity, and the one-time
 // shared-memory opt-in of its kernel for the widest image.
 uint32_t bin_warp_surfels(int max_surfels);

@@ -42,11 +42,15 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *e
   return total;
 }
 
-// Pass 1: per-tile sums.
+// Pass 1: per-tile sums. The last block to finish (counted on *ticket, which
+// it resets to 0) then scans the tile sums in place, so no block ever waits on
+// another.
 template <class Load>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load ld, const uint32_t *n_ptr,
-                                                                   uint32_t n_max, uint32_t *sums) {
+                                                                   uint32_t n_max, uint32_t *sums,
+                                                                   uint32_t *ticket, uint32_t *total_out) {
   __shared__ uint32_t smem[32];
+  __shared__ uint32_t s_last;
   const uint32_t n = load_n(n_ptr, n_max);
   const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
   uint32_t acc = 0;
@@ -59,30 +63,36 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load ld, cons
   }
   uint32_t ex;
   const uint32_t tot = block_exclusive_scan<kScanThreads>(acc, &ex, smem);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
-}
-
-// Pass 2: exclusive scan of the tile sums in place (one block); total -> *total.
-static __global__ void __launch_bounds__(1024) scan_sums_kernel(uint32_t *sums, int nblocks, uint32_t *total) {
-  __shared__ uint32_t smem[32];
-  const int per = (nblocks + 1023) / 1024;
+  if (threadIdx.x == 0) {
+    sums[blockIdx.x] = tot;
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nb = (int)gridDim.x;
+  const int per = (nb + kScanThreads - 1) / kScanThreads;
   const int b0 = threadIdx.x * per;
-  uint32_t acc = 0;
+  uint32_t a2 = 0;
   for (int k = 0; k < per; ++k)
-    if (b0 + k < nblocks) acc += sums[b0 + k];
-  uint32_t ex;
-  const uint32_t tot = block_exclusive_scan<1024>(acc, &ex, smem);
+    if (b0 + k < nb) a2 += __ldcg(sums + b0 + k);
+  uint32_t ex2;
+  const uint32_t all = block_exclusive_scan<kScanThreads>(a2, &ex2, smem);
   for (int k = 0; k < per; ++k) {
-    if (b0 + k < nblocks) {
-      const uint32_t v = sums[b0 + k];
-      sums[b0 + k] = ex;
-      ex += v;
+    if (b0 + k < nb) {
+      const uint32_t v = __ldcg(sums + b0 + k);
+      sums[b0 + k] = ex2;
+      ex2 += v;
     }
   }
-  if (threadIdx.x == 0 && total) *total = tot;
+  if (threadIdx.x == 0) {
+    if (total_out) *total_out = all;
+    *ticket = 0u;
+  }
 }
 
-// Pass 3: per-element exclusive prefix; ap(i, prefix, value) for every i < n and
+// Pass 2: per-element exclusive prefix; ap(i, prefix, value) for every i < n and
 // ap.end(n, total) once.
 template <class Load, class Apply>
 __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(Load ld, Apply ap, const uint32_t *n_ptr,
@@ -110,30 +120,31 @@ __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(Load ld, Apply
   }
   uint32_t ex;
   const uint32_t tot = block_exclusive_scan<kScanThreads>(acc, &ex, smem);
-  ex += sums[blockIdx.x];
+  if (sums) ex += sums[blockIdx.x];
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     const uint32_t i = base + threadIdx.x * kScanItems + k;
     if (i < n) ap(i, ex, loc[k]);
     ex += loc[k];
   }
-  if (base + kScanTile >= n && threadIdx.x == 0) ap.end(n, sums[blockIdx.x] + tot);
+  if (base + kScanTile >= n && threadIdx.x == 0) ap.end(n, (sums ? sums[blockIdx.x] : 0u) + tot);
 }
 
+// block_sums: one word per tile of kScanTile elements (+1); ticket: one word that
+// is 0 between scans (the scans of one workspace run one after another).
 template <class Load, class Apply>
 cudaError_t scan_launch(Load ld, Apply ap, const uint32_t *n_ptr, uint32_t n_max, uint32_t *block_sums,
-                        uint32_t *total_out, cudaStream_t s) {
+                        uint32_t *ticket, uint32_t *total_out, cudaStream_t s) {
   const int nblocks = (int)((n_max + kScanTile - 1) / kScanTile);
-  if (nblocks == 0) {
-    // still report an empty result
-    scan_apply_kernel<<<1, kScanThreads, 0, s>>>(ld, ap, n_ptr, 0u, block_sums);
+  if (nblocks <= 1) {
+    // one tile (or an empty result): its prefix starts at 0
+    scan_apply_kernel<<<1, kScanThreads, 0, s>>>(ld, ap, n_ptr, n_max, (const uint32_t *)nullptr);
     GS_LAUNCHED(1);
     return cudaGetLastError();
   }
-  scan_reduce_kernel<<<nblocks, kScanThreads, 0, s>>>(ld, n_ptr, n_max, block_sums);
-  scan_sums_kernel<<<1, 1024, 0, s>>>(block_sums, nblocks, total_out);
+  scan_reduce_kernel<<<nblocks, kScanThreads, 0, s>>>(ld, n_ptr, n_max, block_sums, ticket, total_out);
   scan_apply_kernel<<<nblocks, kScanThreads, 0, s>>>(ld, ap, n_ptr, n_max, block_sums);
-  GS_LAUNCHED(3);
+  GS_LAUNCHED(2);
   return cudaGetLastError();
 }
 

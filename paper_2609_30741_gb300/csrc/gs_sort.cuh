@@ -82,11 +82,12 @@ static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const 
     s_global[tid] = offs[(size_t)tid * ntiles + t];
     __syncthreads();
     // warp w owns pairs [w * 32 * kRsItems, (w + 1) * 32 * kRsItems) of the tile
-    uint32_t k[kRsItems], r[kRsItems];
+    uint32_t k[kRsItems], r[kRsItems], v[kRsItems];
 #pragma unroll
-    for (int j = 0; j < kRsItems; ++j) {
+    for (int j = 0; j < kRsItems; ++j) {  // values loaded with the keys: no second wait
       const uint32_t i = base + (uint32_t)(wid * 32 * kRsItems + j * 32 + lane);
       k[j] = i < n ? kin[i] : 0u;
+      v[j] = i < n ? vin[i] : 0u;
     }
 #pragma unroll
     for (int j = 0; j < kRsItems; ++j) {
@@ -130,7 +131,7 @@ static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const 
         const uint32_t d = (k[j] >> shift) & 255u;
         const uint32_t pos = s_local_base[d] + s_warp[wid][d] + r[j];
         s_keys[pos] = k[j];
-        s_vals[pos] = vin[i];
+        s_vals[pos] = v[j];
       }
     }
     __syncthreads();
@@ -151,6 +152,7 @@ struct RadixScratch {
   uint32_t *offs;    // [256][tiles]
   uint32_t *n_table; // one word
   uint32_t *sums;    // scan block sums
+  uint32_t *ticket;  // scan completion counter (0 between scans)
 };
 
 inline size_t radix_table_words(size_t n_max) { return 256 * ((n_max + kRsTile - 1) / kRsTile + 1); }
@@ -170,7 +172,8 @@ inline cudaError_t radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], 
   for (int p = 0; p < npass; ++p) {
     rs_hist_kernel<<<grid, kRsThreads, 0, s>>>(keys[cur], n_ptr, n_max, 8 * p, sc.table, sc.n_table);
     GS_LAUNCHED(1);
-    cudaError_t e = scan_launch(TableLoad{sc.table}, TableApply{sc.offs}, sc.n_table, table_max, sc.sums, nullptr, s);
+    cudaError_t e = scan_launch(TableLoad{sc.table}, TableApply{sc.offs}, sc.n_table, table_max, sc.sums, sc.ticket,
+                                nullptr, s);
     if (e != cudaSuccess) return e;
     rs_scatter_kernel<<<grid, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_ptr, n_max,
                                                   8 * p, sc.offs);
