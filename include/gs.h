@@ -153,6 +153,72 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
                              const gs_pose *pose_aff, const gs_intrinsics *intr,
                              const gs_outputs *out);
 
+/* ---- Learned hole repair (no counterpart in the paper: the paper repairs holes
+ * by interpolation and ROI re-rendering only, Sec. 3.1 Stage 3 and Sec. 3.5).
+ *
+ * A small network fills the holes the forward warp leaves and decides, per
+ * 16x16 tile, whether its fill replaces that tile's plain repair:
+ *   features per affiliated pixel (8 x bf16, channels 6 and 7 zero):
+ *     0-2 warped RGB (0 at holes), 3 inverse depth 1/z of the winner (0 at holes
+ *     and background samples), 4 hole mask, 5 min(distance to the nearest hole,
+ *     8) / 8 in pixels;
+ *   network: six 3x3 convolutions (cross-correlation, zero padding at the image
+ *     border) 6 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, ReLU after the first five,
+ *     BF16 weights and activations, FP32 accumulation on the tensor cores;
+ *     outputs 0-2 are the RGB fill, output 3 a gate logit;
+ *   gate: the mean of output 3 over a tile's pixels; with repair_mode = 1 in
+ *     gs_render_stereo, a tile with holes whose sigmoid(gate) >= gate_tau takes
+ *     max(fill, 0) at its hole pixels (class bit 32) and is not re-rendered; the
+ *     other tiles keep the plain path.
+ * Parameters: GS_REPAIR_PARAMS floats in the canonical order: for each layer,
+ * W[c_out][3][3][c_in] then b[c_out]. */
+#define GS_REPAIR_PARAMS 39908
+
+/* Copies the FP32 parameters (host array) into the context (synchronises its
+ * stream), resets the AdamW state and packs the BF16 weights. */
+gs_status gs_repair_load(gs_context *ctx, const float *weights, int64_t count);
+
+/* Reads back the FP32 parameters (which = 0) or the gradients of the last
+ * training step (which = 1) into a host array; synchronises the stream. */
+gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count);
+
+/* Features of the affiliated eye from the forward warp of the last
+ * gs_render_stereo call on this context: rgb_dom is that call's dominant image
+ * (device, [3][H][W]); feat receives [H][W][8] bf16 (device, 16-byte aligned). */
+gs_status gs_repair_features(gs_context *ctx, const float *rgb_dom, int width, int height, uint16_t *feat);
+
+/* Runs the network on listed tiles of a stack of feature images.
+ * feat: device [frames][H][W][8] bf16; tiles: device uint32 entries
+ * frame << 24 | tile_y << 12 | tile_x (16x16 tiles); fill: device
+ * [frames][3][H][W] (written inside the listed tiles; may be NULL); gate: device
+ * float[n_tiles], the mean gate logit of each listed tile. */
+gs_status gs_repair_infer(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,
+                          const uint32_t *tiles, int n_tiles, float *fill, float *gate);
+
+/* One training step on listed tiles: forward (keeping activations), loss, FP32
+ * gradients, and an AdamW update of the FP32 parameters when lr > 0 (lr = 0
+ * leaves them unchanged and only computes gradients).
+ * Loss = mean over the tiles' hole pixels of |fill - target| (averaged over RGB)
+ *      + gate_weight * mean over tiles of BCE(sigmoid(gate), label), where the
+ *        label is 1 when the tile's composite with the network fill scores a PSNR
+ *        against the target at least that of the plain image and at least 30 dB.
+ * loss (host float[4], may be NULL): total, L1 term, BCE term, share of positive
+ * labels; reading it synchronises the stream. */
+typedef struct {
+  const uint16_t *feat;  /* device [frames][H][W][8] bf16 */
+  const float *target;   /* device [frames][3][H][W]: full affiliated render */
+  const float *plain;    /* device [frames][3][H][W]: plain-method affiliated image */
+  int frames, width, height;
+  const uint32_t *tiles; /* device, as for gs_repair_infer */
+  int n_tiles;
+  void *scratch;         /* device, gs_repair_train_scratch_size() bytes */
+} gs_repair_batch;
+typedef struct {
+  float lr, beta1, beta2, eps, weight_decay, gate_weight;
+} gs_adamw;
+gs_status gs_repair_train_scratch_size(int n_tiles, size_t *bytes);
+gs_status gs_repair_train_step(gs_context *ctx, const gs_repair_batch *batch, const gs_adamw *opt, float *loss);
+
 /* Allocation-free forward warp (no counterpart in the paper; a deployment aid).
  *
  * For callers that cannot allocate device memory: a plugin or compositor inside

@@ -84,6 +84,18 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.labels = c.take<int32_t>(P);
   ws.slots = c.take<uint32_t>(P + 1);
   ws.rects = c.take<int4>((size_t)lim.max_rects);
+  ws.rp_master = c.take<float>(kRepairParams);
+  ws.rp_grad = c.take<float>(kRepairParams);
+  ws.rp_m = c.take<float>(kRepairParams);
+  ws.rp_v = c.take<float>(kRepairParams);
+  ws.rp_wpack = c.take<uint8_t>(92160);
+  ws.rp_bias = c.take<float>(6 * 32);
+  ws.rp_feat = c.take<uint4>(P);
+  ws.rp_fill = c.take<float>(3 * P);
+  ws.rp_gate = c.take<float>(tiles);
+  ws.rp_flags = c.take<uint8_t>(tiles);
+  ws.rp_list = c.take<uint32_t>(tiles);
+  ws.rp_nlist = c.take<uint32_t>(1);
   ws.strips = c.take<int32_t>(16);
   ws.drange = c.take<float>(2);
   ws.widths = c.take<int32_t>(4);
@@ -166,6 +178,8 @@ struct gs_context {
   int capturing;
   cudaStream_t cap_stream;
   GraphSlot graphs[3];  // mono, stereo, two-pass
+  int rp_loaded;        // repair network weights present
+  int rp_step;          // AdamW steps taken
 };
 
 static void release_slot(GraphSlot &g) {
@@ -279,6 +293,7 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
     return GS_ERR_WORKSPACE;
   }
   cudaError_t e = prepare_binning((lim->max_width + kTile - 1) / kTile);
+  if (e == cudaSuccess) e = prepare_repair();
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.scan_ticket, 0, sizeof(uint32_t), ctx->stream);
   if (e != cudaSuccess) {
@@ -551,7 +566,9 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
   if (gap_thresh < 0 || roi->margin < 0 || roi->samples_per_edge < 2 || roi->samples_per_edge > 1 << 20 ||
       (roi->depth_mode != 0 && roi->depth_mode != 1))
     return GS_ERR_BAD_ARG;
-  if (roi->repair_mode != 0) return GS_ERR_NOT_LOADED;
+  if (roi->repair_mode < 0 || roi->repair_mode > 2 || !(roi->gate_tau > 0.f && roi->gate_tau < 1.f))
+    return GS_ERR_BAD_ARG;
+  if (roi->repair_mode == 2 || (roi->repair_mode == 1 && !ctx->rp_loaded)) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
   const PoseArgs pa = pose_args(pose_dom, pose_aff, intr);
@@ -575,6 +592,12 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     // Step 2: connected centre holes -> ROIs
     if (roi->enable_center) {
       if ((e = launch_centre_rois(ctx->ws, W, H, roi->margin, ctx->stream)) != cudaSuccess) return cuda_fail(e);
+    }
+    // learned repair: tiles with holes whose gate passes take the network fill
+    // and leave the ROI tile mask
+    if (roi->repair_mode == 1) {
+      if ((e = repair_stereo(ctx->ws, W, H, out->rgb_dom, roi->gate_tau, out->rgb_aff, ctx->stream)) != cudaSuccess)
+        return cuda_fail(e);
     }
     mark(ctx, 5);
     // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
@@ -657,6 +680,71 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
   if (bytes) *bytes = b;
   if (count) *count = n;
   return GS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- learned repair
+extern "C" {
+
+gs_status gs_repair_load(gs_context *ctx, const float *weights, int64_t count) {
+  if (!ctx || !weights || count != kRepairParams) return GS_ERR_BAD_ARG;
+  const Workspace &ws = ctx->ws;
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(ws.rp_master, weights, sizeof(float) * kRepairParams, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.rp_m, 0, sizeof(float) * kRepairParams, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ws.rp_v, 0, sizeof(float) * kRepairParams, s);
+  if (e == cudaSuccess) e = repair_pack(ws, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host array may go away after the call
+  if (e != cudaSuccess) return cuda_fail(e);
+  ctx->rp_loaded = 1;
+  ctx->rp_step = 0;
+  return GS_OK;
+}
+
+gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count) {
+  if (!ctx || !out || count != kRepairParams || (which != 0 && which != 1)) return GS_ERR_BAD_ARG;
+  if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
+  const float *src = which == 0 ? ctx->ws.rp_master : ctx->ws.rp_grad;
+  cudaError_t e = cudaMemcpyAsync(out, src, sizeof(float) * kRepairParams, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return cuda_status(e);
+}
+
+gs_status gs_repair_features(gs_context *ctx, const float *rgb_dom, int width, int height, uint16_t *feat) {
+  if (!ctx || !rgb_dom || !feat || width <= 0 || height <= 0 || width > ctx->lim.max_width ||
+      height > ctx->lim.max_height || ((uintptr_t)feat & 15))
+    return GS_ERR_BAD_ARG;
+  return cuda_status(repair_features(ctx->ws, width, height, rgb_dom, (uint4 *)feat, ctx->stream));
+}
+
+gs_status gs_repair_infer(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,
+                          const uint32_t *tiles, int n_tiles, float *fill, float *gate) {
+  if (!ctx || !feat || !tiles || !gate || frames <= 0 || frames > 255 || width <= 0 || height <= 0 ||
+      width > 4095 * 16 || height > 4095 * 16 || n_tiles < 0 || ((uintptr_t)feat & 15))
+    return GS_ERR_BAD_ARG;
+  if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
+  return cuda_status(repair_forward(ctx->ws, (const uint4 *)feat, width, height, tiles, nullptr, (uint32_t)n_tiles,
+                                    fill, gate, nullptr, nullptr, ctx->stream));
+}
+
+gs_status gs_repair_train_scratch_size(int n_tiles, size_t *bytes) {
+  if (n_tiles <= 0 || !bytes) return GS_ERR_BAD_ARG;
+  *bytes = repair_train_scratch_bytes(n_tiles);
+  return GS_OK;
+}
+
+gs_status gs_repair_train_step(gs_context *ctx, const gs_repair_batch *b, const gs_adamw *opt, float *loss) {
+  if (!ctx || !b || !opt || !b->feat || !b->target || !b->plain || !b->tiles || !b->scratch || b->n_tiles <= 0 ||
+      b->frames <= 0 || b->frames > 255 || b->width <= 0 || b->height <= 0 || b->width > 4095 * 16 ||
+      b->height > 4095 * 16 || ((uintptr_t)b->feat & 15) || !(opt->lr >= 0.f))
+    return GS_ERR_BAD_ARG;
+  if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
+  RepairBatch rb{(const uint4 *)b->feat, b->target, b->plain, b->width, b->height, b->tiles, b->n_tiles, b->scratch};
+  if (opt->lr > 0.f) ++ctx->rp_step;
+  RepairOpt ro{opt->lr, opt->beta1, opt->beta2, opt->eps, opt->weight_decay, opt->gate_weight,
+               ctx->rp_step > 0 ? ctx->rp_step : 1};
+  return cuda_status(repair_train_step(ctx->ws, rb, ro, loss, ctx->stream));
 }
 
 }  // extern "C"

@@ -110,6 +110,15 @@ struct Workspace {
   int32_t *strips;              // [4][4]
   float *drange;                // [2]
   int32_t *widths;              // [4]
+  // learned repair network
+  float *rp_master, *rp_grad, *rp_m, *rp_v;  // FP32 parameters, gradients, AdamW moments
+  uint8_t *rp_wpack;            // BF16 B-operand images of the six layers
+  float *rp_bias;               // [6][32]
+  uint4 *rp_feat;               // [pixels] 8 x bf16 features of the affiliated eye
+  float *rp_fill;               // [3][pixels] network fill
+  float *rp_gate;               // [tiles] gate logit per listed tile
+  uint8_t *rp_flags;            // [tiles] tile has a hole
+  uint32_t *rp_list, *rp_nlist; // listed tiles and their number
   // limits
   int max_surfels, max_w, max_h, max_rects, max_tiles;
   int64_t max_instances, max_pixels;
@@ -149,6 +158,35 @@ uint32_t bin_chunks(int max_surfels);
 size_t band_list_words(int max_surfels, int max_tiles_y);
 constexpr size_t kBandEntryBytes = 12;
 cudaError_t prepare_binning(int max_tiles_x);
+// ---- learned repair network ----
+constexpr int kRepairParams = 39908;
+struct RepairBatch {
+  const uint4 *feat;     // [frames][H][W] 8 x bf16
+  const float *target;   // [frames][3][H][W]
+  const float *plain;    // [frames][3][H][W]
+  int W, H;
+  const uint32_t *tiles; // frame << 24 | ty << 12 | tx
+  int n_tiles;
+  void *scratch;         // repair_train_scratch_bytes(n_tiles)
+};
+struct RepairOpt {
+  float lr, beta1, beta2, eps, weight_decay, gate_weight;
+  int step;
+};
+cudaError_t prepare_repair();
+size_t repair_train_scratch_bytes(int n_tiles);
+cudaError_t repair_pack(const Workspace &ws, cudaStream_t s);
+cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_dom, uint4 *feat, cudaStream_t s);
+cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
+                           const uint32_t *n_ptr, uint32_t n_max, float *fill, float *gate, float *out4,
+                           uint4 *acts, cudaStream_t s);
+// Features, tile list, network and gated merge for the affiliated eye of the last
+// warp; gated tiles leave ws.tile_mask.
+cudaError_t repair_stereo(const Workspace &ws, int W, int H, const float *rgb_dom, float gate_tau, float *rgb_aff,
+                          cudaStream_t s);
+cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const RepairOpt &o, float *host_loss,
+                              cudaStream_t s);
+
 cudaError_t launch_blend(const Workspace &ws, int eye, int W, int H, const uint8_t *tile_mask,
                          float3 bg, float *rgb, float *depth, float *trans, uint8_t *cls,
                          bool depth_stats, bool count_pairs, cudaStream_t s);

@@ -62,6 +62,17 @@ class Limits(C.Structure):
                 ("max_instances", C.c_int64), ("max_rects", C.c_int), ("keep_intermediates", C.c_int)]
 
 
+class RepairBatch(C.Structure):
+    _fields_ = [("feat", C.c_void_p), ("target", C.c_void_p), ("plain", C.c_void_p), ("frames", C.c_int),
+                ("width", C.c_int), ("height", C.c_int), ("tiles", C.c_void_p), ("n_tiles", C.c_int),
+                ("scratch", C.c_void_p)]
+
+
+class AdamW(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("weight_decay", C.c_float), ("gate_weight", C.c_float)]
+
+
 EXPORTS = {
     "gs_status_str": (C.c_char_p, [C.c_int]),
     "gs_kernel_launches": (C.c_ulonglong, []),
@@ -85,7 +96,16 @@ EXPORTS = {
                                      C.POINTER(Intrinsics), C.POINTER(Outputs)]),
     "gs_warp_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Pose), C.POINTER(Pose),
                                   C.POINTER(Intrinsics), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_repair_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "gs_repair_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "gs_repair_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "gs_repair_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
+                                  C.c_void_p, C.c_void_p]),
+    "gs_repair_train_scratch_size": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
+    "gs_repair_train_step": (C.c_int, [C.c_void_p, C.POINTER(RepairBatch), C.POINTER(AdamW), C.c_void_p]),
 }
+
+REPAIR_PARAMS = 39908
 
 WARP_NOALLOC_MAX_PIXELS = 1 << 22
 
@@ -276,6 +296,57 @@ class Context:
                                       C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), int(gap_thresh),
                                       C.byref(roi), C.byref(os_)), "gs_render_stereo")
         return out
+
+    # ---- learned repair ----
+    def repair_load(self, weights):
+        import numpy as np
+        w = np.ascontiguousarray(np.asarray(weights, np.float32).ravel())
+        if w.size != REPAIR_PARAMS:
+            raise ValueError(f"expected {REPAIR_PARAMS} parameters, got {w.size}")
+        _check(lib().gs_repair_load(self.h, w.ctypes.data_as(C.c_void_p), C.c_int64(w.size)), "gs_repair_load")
+
+    def repair_read(self, which=0):
+        import numpy as np
+        out = np.empty(REPAIR_PARAMS, np.float32)
+        _check(lib().gs_repair_read(self.h, int(which), out.ctypes.data_as(C.c_void_p), C.c_int64(out.size)),
+               "gs_repair_read")
+        return out
+
+    def repair_features(self, rgb_dom, cam, out=None):
+        """Features of the last gs_render_stereo call's warp: (H, W, 8) bfloat16."""
+        if out is None:
+            out = torch.empty(cam.height, cam.width, 8, dtype=torch.bfloat16, device=self.device)
+        _check(lib().gs_repair_features(self.h, _ptr(rgb_dom), cam.width, cam.height, _ptr(out)),
+               "gs_repair_features")
+        return out
+
+    def repair_infer(self, feat, tiles, fill=None, gate=None):
+        """feat (F, H, W, 8) bfloat16; tiles int32 tensor of frame << 24 | ty << 12 | tx."""
+        F, H, W = feat.shape[0], feat.shape[1], feat.shape[2]
+        if gate is None:
+            gate = torch.empty(tiles.numel(), dtype=torch.float32, device=self.device)
+        _check(lib().gs_repair_infer(self.h, _ptr(feat), F, W, H, _ptr(tiles), tiles.numel(), _ptr(fill),
+                                     _ptr(gate)), "gs_repair_infer")
+        return fill, gate
+
+    def repair_train_step(self, feat, target, plain, tiles, scratch=None, lr=1e-3, beta1=0.9, beta2=0.999,
+                          eps=1e-8, weight_decay=0.0, gate_weight=0.1, want_loss=True):
+        import numpy as np
+        F, H, W = feat.shape[0], feat.shape[1], feat.shape[2]
+        if scratch is None:
+            scratch = self.repair_scratch(tiles.numel())
+        b = RepairBatch(_ptr(feat), _ptr(target), _ptr(plain), F, W, H, _ptr(tiles), tiles.numel(), _ptr(scratch))
+        o = AdamW(lr, beta1, beta2, eps, weight_decay, gate_weight)
+        loss = np.zeros(4, np.float32)
+        _check(lib().gs_repair_train_step(self.h, C.byref(b), C.byref(o),
+                                          loss.ctypes.data_as(C.c_void_p) if want_loss else None),
+               "gs_repair_train_step")
+        return loss
+
+    def repair_scratch(self, n_tiles):
+        n = C.c_size_t()
+        _check(lib().gs_repair_train_scratch_size(int(n_tiles), C.byref(n)), "gs_repair_train_scratch_size")
+        return torch.empty(n.value, dtype=torch.uint8, device=self.device)
 
     def render_two_pass(self, scene: DeviceScene, pose_dom, pose_aff, cam, out=None):
         if out is None:

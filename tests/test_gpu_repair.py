@@ -1,0 +1,231 @@
+"""The learned repair network on the GPU (tcgen05 forward, FP32 backward,
+AdamW) against the FP64 oracle in oracle/repair.py.
+
+Tolerances: the oracle rounds inputs, weights and stored activations to
+bfloat16 at the points where the GPU stores them and sums in float64; the GPU
+sums the same bfloat16 products in FP32. A stored activation can then land on
+the other side of a bfloat16 rounding boundary (relative step 2^-8), rarely,
+and that one-ulp difference propagates through later layers. So outputs are
+compared with a 2e-2 relative bound on the worst element (scaled by the
+output's magnitude), and 99% of them must agree within 2e-3 of that scale.
+"""
+import numpy as np
+import pytest
+
+from oracle import repair as R
+from paper_2609_30741_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30741_gb300 import build
+    build.build()
+    from paper_2609_30741_gb300 import gs as gsmod
+    return gsmod
+
+
+def _features(rng, H, W, hole_frac=0.2):
+    hole = rng.random((H, W)) < hole_frac
+    x = np.zeros((6, H, W))
+    x[:3] = rng.random((3, H, W))
+    x[3] = rng.uniform(0.2, 2.0, (H, W))
+    x[:4, hole] = 0.0
+    x[4] = hole
+    x[5] = R.distance_to_hole(hole)
+    return R.round_bf16(x), hole
+
+
+def _to_device(x):
+    """(6, H, W) float64 (bf16 values) -> (1, H, W, 8) bfloat16 CUDA tensor."""
+    f = np.zeros((1, x.shape[1], x.shape[2], 8), np.float32)
+    f[0, :, :, :6] = np.moveaxis(x, 0, -1)
+    return torch.tensor(f).to(torch.bfloat16).cuda()
+
+
+def _tiles(H, W, frame=0):
+    ty, tx = (H + 15) // 16, (W + 15) // 16
+    t = [(frame << 24) | (y << 12) | x for y in range(ty) for x in range(tx)]
+    return torch.tensor(np.array(t, np.int64).astype(np.int32), device="cuda")
+
+
+def _weights(seed, gate_bias=0.0):
+    W, b = R.init_weights(seed)
+    rng = np.random.default_rng(seed + 1)
+    b = [rng.normal(0, 0.05, bb.shape) for bb in b]
+    b[5][3] += gate_bias
+    return W, b
+
+
+def _ctx(gs, W, H):
+    return gs.Context(16, W, H, max_instances=1 << 12)
+
+
+def _close(gpu, ref, what):
+    scale = max(float(np.abs(ref).max()), 1e-3)
+    err = np.abs(gpu - ref)
+    assert err.max() <= 2e-2 * scale, f"{what}: max err {err.max()} vs scale {scale}"
+    assert np.quantile(err, 0.99) <= 2e-3 * scale, f"{what}: 99th pct err {np.quantile(err, 0.99)}"
+
+
+@pytest.mark.parametrize("H,W", [(40, 56), (16, 16), (67, 45)])
+def test_forward_matches_oracle(gs, H, W):
+    rng = np.random.default_rng(H * 1000 + W)
+    x, hole = _features(rng, H, W)
+    Wt, b = _weights(3)
+    ctx = _ctx(gs, W, H)
+    ctx.repair_load(R.pack(Wt, b))
+    feat = _to_device(x)
+    tiles = _tiles(H, W)
+    fill = torch.zeros(1, 3, H, W, device="cuda")
+    _, gate = ctx.repair_infer(feat, tiles, fill=fill)
+    ctx.check_ok()
+    out, _ = R.forward(x, Wt, b, bf16=True)
+    _close(fill[0].cpu().double().numpy(), out[:3], "fill")
+    g_ref = R.tile_gate(out[3]).ravel()
+    _close(gate.cpu().double().numpy(), g_ref, "gate")
+
+
+def test_forward_is_tile_local_and_listed_only(gs):
+    """Listing a subset of tiles writes exactly those tiles, with the same values."""
+    rng = np.random.default_rng(9)
+    H, W = 48, 64
+    x, _ = _features(rng, H, W)
+    Wt, b = _weights(4)
+    ctx = _ctx(gs, W, H)
+    ctx.repair_load(R.pack(Wt, b))
+    feat = _to_device(x)
+    full = torch.full((1, 3, H, W), -7.0, device="cuda")
+    ctx.repair_infer(feat, _tiles(H, W), fill=full)
+    part = torch.full((1, 3, H, W), -7.0, device="cuda")
+    sub = torch.tensor([(1 << 12) | 2, 0], dtype=torch.int32, device="cuda")  # tiles (2, 1) and (0, 0)
+    ctx.repair_infer(feat, sub, fill=part)
+    ctx.check_ok()
+    f, p = full.cpu().numpy(), part.cpu().numpy()
+    listed = np.zeros((H, W), bool)
+    listed[16:32, 32:48] = True
+    listed[0:16, 0:16] = True
+    assert np.array_equal(p[:, :, listed], f[:, :, listed])
+    assert np.all(p[:, :, ~listed] == -7.0)
+
+
+def test_gradients_match_oracle(gs):
+    rng = np.random.default_rng(11)
+    H, W = 32, 48
+    x, hole = _features(rng, H, W, 0.3)
+    Wt, b = _weights(5)
+    flat = R.pack(Wt, b).astype(np.float32).astype(np.float64)
+    Wt, b = R.unpack(flat)
+    ctx = _ctx(gs, W, H)
+    ctx.repair_load(flat)
+    feat = _to_device(x)
+    # target far above every output (L1 sign fixed) and a perfect plain image
+    # (gate label 0 on every tile), so no discrete decision sits near a boundary
+    target = np.full((3, H, W), 10.0)
+    tgt = torch.tensor(target[None], dtype=torch.float32, device="cuda")
+    loss = ctx.repair_train_step(feat, tgt, tgt.clone(), _tiles(H, W), lr=0.0, gate_weight=0.1)
+    g_gpu = ctx.repair_read(1).astype(np.float64)
+    out, acts = R.forward(x, Wt, b, bf16=True)
+    L, dout = R.loss(out, target, hole, np.zeros((2, 3)), lam=0.1)
+    dW, db = R.backward(acts, Wt, dout)
+    g_ref = R.pack(dW, db)
+    assert abs(loss[0] - L) <= 1e-3 * abs(L)
+    rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    assert rel <= 5e-3, rel
+    # every layer's weight and bias gradients, each against its own scale
+    o = 0
+    for l in range(6):
+        ci, co = R.CHANNELS[l], R.CHANNELS[l + 1]
+        for n in (co * 9 * ci, co):
+            seg_g, seg_r = g_gpu[o:o + n], g_ref[o:o + n]
+            assert np.abs(seg_g - seg_r).max() <= 2e-2 * np.abs(seg_r).max() + 1e-9, (l, n)
+            o += n
+    # lr = 0 leaves the parameters untouched
+    assert np.array_equal(ctx.repair_read(0), flat.astype(np.float32))
+
+
+def test_adamw_steps_reduce_the_loss(gs):
+    rng = np.random.default_rng(12)
+    H, W = 32, 32
+    x, hole = _features(rng, H, W, 0.3)
+    target = rng.random((3, H, W))
+    Wt, b = _weights(6)
+    ctx = _ctx(gs, W, H)
+    ctx.repair_load(R.pack(Wt, b))
+    feat = _to_device(x)
+    tgt = torch.tensor(target[None], dtype=torch.float32, device="cuda")
+    tiles = _tiles(H, W)
+    scratch = ctx.repair_scratch(tiles.numel())
+    losses = [ctx.repair_train_step(feat, tgt, tgt, tiles, scratch=scratch, lr=3e-3)[0] for _ in range(30)]
+    assert losses[-1] < 0.6 * losses[0], losses[::5]
+
+
+def test_features_match_oracle(gs):
+    scene, cam, dom, aff = synth.workload_small()
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 22)
+    ds = gs.DeviceScene(scene)
+    out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
+    feat = ctx.repair_features(out["rgb_dom"], cam)
+    ctx.check_ok()
+    H, W = cam.height, cam.width
+    warp, _ = ctx.buffer(gs.BUF_WARP, torch.int64, None)
+    key = warp[:H * W].cpu().numpy().view(np.uint64).reshape(H, W)
+    hole = key == np.uint64(0xFFFFFFFFFFFFFFFF)
+    src = np.where(hole, 0, (key & np.uint64(0xFFFFFFFF)).astype(np.int64))
+    rgb_dom = out["rgb_dom"].cpu().double().numpy().reshape(3, -1)
+    rgb_w = rgb_dom[:, src.ravel()].reshape(3, H, W)
+    z = (key >> np.uint64(32)).astype(np.uint32).view(np.float32).astype(np.float64)
+    ref = R.round_bf16(R.features(rgb_w, z, hole))
+    got = feat.float().cpu().double().numpy()
+    got = np.moveaxis(got, -1, 0)
+    assert np.all(got[6:] == 0)
+    assert np.array_equal(got[4], ref[4])
+    assert np.array_equal(got[:3], ref[:3])
+    for ch in (3, 5):  # one bfloat16 step at most (float32 vs float64 before rounding)
+        assert np.all(np.abs(got[ch] - ref[ch]) <= 2.0 ** -7 * np.maximum(np.abs(ref[ch]), 1e-30)), ch
+
+
+def _stereo(gs, ctx, ds, dom, aff, cam, mode, tau=0.5):
+    roi = gs.roi_params(repair_mode=mode, gate_tau=tau)
+    out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2, roi=roi)
+    ctx.check_ok()
+    return {k: v.clone() for k, v in out.items()}
+
+
+def test_stereo_gate_closed_and_open(gs):
+    scene, cam, dom, aff = synth.workload_small()
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 22)
+    ds = gs.DeviceScene(scene)
+    plain = _stereo(gs, ctx, ds, dom, aff, cam, 0)
+    with pytest.raises(gs.GsError) as e:
+        _stereo(gs, gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 22), ds, dom, aff, cam, 1)
+    assert e.value.status == gs.GS_ERR_NOT_LOADED
+    # gate never passes: exactly the plain method
+    Wt, b = _weights(7, gate_bias=-1e4)
+    ctx.repair_load(R.pack(Wt, b))
+    closed = _stereo(gs, ctx, ds, dom, aff, cam, 1)
+    for k in ("rgb_aff", "cls_aff"):
+        assert torch.equal(closed[k], plain[k]), k
+    # gate always passes: every hole pixel of a tile with holes takes max(fill, 0)
+    # and no tile with a hole is re-rendered
+    Wt, b = _weights(7, gate_bias=1e4)
+    ctx.repair_load(R.pack(Wt, b))
+    opened = _stereo(gs, ctx, ds, dom, aff, cam, 1)
+    feat = ctx.repair_features(opened["rgb_dom"], cam)
+    H, W = cam.height, cam.width
+    fill = torch.zeros(1, 3, H, W, device="cuda")
+    ctx.repair_infer(feat[None], _tiles(H, W), fill=fill)
+    hole = (plain["cls_aff"] & gs.CLS_HOLE) > 0
+    cls = opened["cls_aff"]
+    assert torch.equal((cls & gs.CLS_NET) > 0, hole)
+    want = torch.clamp(fill[0], min=0.0)
+    assert torch.equal(opened["rgb_aff"][:, hole], want[:, hole])
+    # tiles without holes are unchanged from the plain method
+    th = hole.reshape(H // 16, 16, W // 16, 16).any(3).any(1)
+    keep = ~th.repeat_interleave(16, 0).repeat_interleave(16, 1)
+    assert torch.equal(opened["rgb_aff"][:, keep], plain["rgb_aff"][:, keep])
+    assert not torch.any((cls[~keep] & gs.CLS_RENDER) > 0)
