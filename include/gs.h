@@ -88,7 +88,9 @@ typedef struct {
                            D/(1-T) over pixels with coverage 1-T >= 0.5; 1: fixed */
   float d_min, d_max;   /* the two depth hypotheses when depth_mode = 1 */
   int repair_mode;      /* 0: plain interpolation + ROI re-render; 1: learned repair
-                           in BF16; 2: learned repair in FP8 (needs gs_repair_load) */
+                           in BF16; 2: learned repair in FP8 (both need
+                           gs_repair_load); 3: plain output, plus the repair
+                           network's features for gs_repair_features */
   float gate_tau;       /* learned repair: a tile uses the network fill when
                            sigmoid(gate logit) >= gate_tau, else the plain path */
 } gs_roi_params;
@@ -159,17 +161,21 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
  * A small network fills the holes the forward warp leaves and decides, per
  * 16x16 tile, whether its fill replaces that tile's plain repair:
  *   features per affiliated pixel (8 x bf16, channels 6 and 7 zero):
- *     0-2 warped RGB (0 at holes), 3 inverse depth 1/z of the winner (0 at holes
- *     and background samples), 4 hole mask, 5 min(distance to the nearest hole,
- *     8) / 8 in pixels;
+ *     0-2 the affiliated image after hole classification: the warped colour, at
+ *     holes outside the edge strips the method's own fill (gap interpolation,
+ *     else the row/column fill), 0 at holes inside the strips; 3 inverse depth
+ *     1/z of the winner (0 at holes and background samples); 4 hole mask;
+ *     5 min(distance to the nearest hole, 8) / 8 in pixels;
  *   network: six 3x3 convolutions (cross-correlation, zero padding at the image
  *     border) 6 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, ReLU after the first five,
  *     BF16 weights and activations, FP32 accumulation on the tensor cores;
- *     outputs 0-2 are the RGB fill, output 3 a gate logit;
+ *     outputs 0-2 are a correction added to feature channels 0-2 (the fill =
+ *     features + correction), output 3 a gate logit;
  *   gate: the mean of output 3 over a tile's pixels; with repair_mode = 1 in
- *     gs_render_stereo, a tile with holes whose sigmoid(gate) >= gate_tau takes
- *     max(fill, 0) at its hole pixels (class bit 32) and is not re-rendered; the
- *     other tiles keep the plain path.
+ *     gs_render_stereo the network runs on the ROI tiles that hold a hole
+ *     outside the edge strips, and such a tile whose sigmoid(gate) >= gate_tau
+ *     takes max(fill, 0) at its hole pixels (class bit 32) and is not
+ *     re-rendered; every other tile keeps the plain path.
  * Parameters: GS_REPAIR_PARAMS floats in the canonical order: for each layer,
  * W[c_out][3][3][c_in] then b[c_out]. */
 #define GS_REPAIR_PARAMS 39908
@@ -182,10 +188,11 @@ gs_status gs_repair_load(gs_context *ctx, const float *weights, int64_t count);
  * training step (which = 1) into a host array; synchronises the stream. */
 gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count);
 
-/* Features of the affiliated eye from the forward warp of the last
- * gs_render_stereo call on this context: rgb_dom is that call's dominant image
- * (device, [3][H][W]); feat receives [H][W][8] bf16 (device, 16-byte aligned). */
-gs_status gs_repair_features(gs_context *ctx, const float *rgb_dom, int width, int height, uint16_t *feat);
+/* The features of the last gs_render_stereo call on this context made with
+ * repair_mode != 0 (same width and height), copied to feat: device [H][W][8]
+ * bf16, 16-byte aligned. repair_mode = 3 computes them without running the
+ * network (training data). */
+gs_status gs_repair_features(gs_context *ctx, int width, int height, uint16_t *feat);
 
 /* Runs the network on listed tiles of a stack of feature images.
  * feat: device [frames][H][W][8] bf16; tiles: device uint32 entries
@@ -200,8 +207,9 @@ gs_status gs_repair_infer(gs_context *ctx, const uint16_t *feat, int frames, int
  * leaves them unchanged and only computes gradients).
  * Loss = mean over the tiles' hole pixels of |fill - target| (averaged over RGB)
  *      + gate_weight * mean over tiles of BCE(sigmoid(gate), label), where the
- *        label is 1 when the tile's composite with the network fill scores a PSNR
- *        against the target at least that of the plain image and at least 30 dB.
+ *        label is 1 when, over the tile's hole pixels, max(fill, 0) scores a PSNR
+ *        against the target of at least 30 dB and at most 0.5 dB below that of
+ *        the plain image at the same pixels.
  * loss (host float[4], may be NULL): total, L1 term, BCE term, share of positive
  * labels; reading it synchronises the stream. */
 typedef struct {

@@ -7,14 +7,18 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, the smoke check and bench.py's
 CPU baseline. Plain numpy in float64, written from the definitions below with no
 tiling, fusion or reordering:
 
-  features (per affiliated-eye pixel, after the forward warp of Stage 2):
-    0-2  warped RGB (the winning source pixel's colour; 0 at holes)
+  features (per affiliated-eye pixel, after the forward warp of Stage 2 and the
+  hole classification of Stage 3):
+    0-2  the affiliated image after classification: the warped colour, at a hole
+         outside the edge strips the method's own fill (gap interpolation, else
+         the row/column fill), 0 at a hole inside the strips
     3    inverse depth 1/z of the winner (0 at holes and for background samples)
     4    hole mask (1 where no sample landed)
     5    distance to the nearest hole pixel, min(d, 8) / 8 (Euclidean, pixels)
   network: six 3x3 convolutions (cross-correlation, zero padding, stride 1),
     channels 6 -> 32 -> 32 -> 32 -> 32 -> 32 -> 4, ReLU after the first five;
-    output channels 0-2 are the RGB fill, channel 3 a per-pixel gate logit
+    output channels 0-2 are a correction added to features 0-2 (the fill),
+    channel 3 a per-pixel gate logit
   gate: the mean of channel 3 over a 16x16 tile; the tile uses the network fill
     for its hole pixels when sigmoid(gate) >= tau
   loss: mean over hole pixels of |fill - target| (averaged over RGB) plus
@@ -87,14 +91,15 @@ def distance_to_hole(hole):
     return d / DIST_CLAMP
 
 
-def features(rgb_warp, z_warp, hole):
-    """(6, H, W) float64 from the warp's outputs: rgb_warp (3, H, W), z_warp
-    (H, W) camera depth of the winner (+inf for a background sample), hole (H, W)."""
+def features(rgb, z_warp, hole):
+    """(6, H, W) float64: rgb (3, H, W) the affiliated image after hole
+    classification, z_warp (H, W) camera depth of the winner (+inf for a
+    background sample), hole (H, W)."""
     hole = np.asarray(hole, bool)
     z = np.asarray(z_warp, np.float64)
     inv = np.where(hole | ~np.isfinite(z) | (z <= 0), 0.0, 1.0 / np.where(z > 0, z, 1.0))
-    rgb = np.where(hole[None], 0.0, np.asarray(rgb_warp, np.float64))
-    return np.concatenate([rgb, inv[None], hole[None].astype(np.float64), distance_to_hole(hole)[None]], 0)
+    return np.concatenate([np.asarray(rgb, np.float64), inv[None], hole[None].astype(np.float64),
+                           distance_to_hole(hole)[None]], 0)
 
 
 def conv3x3(x, W, b):
@@ -140,11 +145,13 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-x))
 
 
-def loss(out, target, hole, label, lam=0.1, tile=TILE):
-    """L1 of the fill on hole pixels + lam * gate BCE; returns (L, dL/dout)."""
+def loss(out, target, hole, label, lam=0.1, tile=TILE, base=None):
+    """L1 of the fill (base + out[:3], base = features 0-2) on hole pixels +
+    lam * gate BCE; returns (L, dL/dout)."""
     hole = np.asarray(hole, bool)
     nh = max(int(hole.sum()), 1)
-    diff = out[:3] - target
+    fill = out[:3] if base is None else np.asarray(base, np.float64) + out[:3]
+    diff = fill - target
     L1 = (np.abs(diff) * hole[None]).sum() / (3.0 * nh)
     g = tile_gate(out[3], tile)
     p = sigmoid(g)

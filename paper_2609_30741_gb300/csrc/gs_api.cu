@@ -566,7 +566,7 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
   if (gap_thresh < 0 || roi->margin < 0 || roi->samples_per_edge < 2 || roi->samples_per_edge > 1 << 20 ||
       (roi->depth_mode != 0 && roi->depth_mode != 1))
     return GS_ERR_BAD_ARG;
-  if (roi->repair_mode < 0 || roi->repair_mode > 2 || !(roi->gate_tau > 0.f && roi->gate_tau < 1.f))
+  if (roi->repair_mode < 0 || roi->repair_mode > 3 || !(roi->gate_tau > 0.f && roi->gate_tau < 1.f))
     return GS_ERR_BAD_ARG;
   if (roi->repair_mode == 2 || (roi->repair_mode == 1 && !ctx->rp_loaded)) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
@@ -588,6 +588,10 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     cudaError_t e = launch_warp_classify(ctx->ws, W, H, gap_thresh, *roi, out->rgb_dom, out->depth_dom,
                                          out->trans_dom, out->rgb_aff, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e);
+    if (roi->repair_mode != 0) {  // the repair network's inputs, kept for gs_repair_features
+      if ((e = repair_features(ctx->ws, W, H, out->rgb_aff, ctx->ws.rp_feat, ctx->stream)) != cudaSuccess)
+        return cuda_fail(e);
+    }
     mark(ctx, 4);
     // Step 2: connected centre holes -> ROIs
     if (roi->enable_center) {
@@ -596,7 +600,7 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     // learned repair: tiles with holes whose gate passes take the network fill
     // and leave the ROI tile mask
     if (roi->repair_mode == 1) {
-      if ((e = repair_stereo(ctx->ws, W, H, out->rgb_dom, roi->gate_tau, out->rgb_aff, ctx->stream)) != cudaSuccess)
+      if ((e = repair_stereo(ctx->ws, W, H, roi->gate_tau, out->rgb_aff, ctx->stream)) != cudaSuccess)
         return cuda_fail(e);
     }
     mark(ctx, 5);
@@ -711,11 +715,12 @@ gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count) 
   return cuda_status(e);
 }
 
-gs_status gs_repair_features(gs_context *ctx, const float *rgb_dom, int width, int height, uint16_t *feat) {
-  if (!ctx || !rgb_dom || !feat || width <= 0 || height <= 0 || width > ctx->lim.max_width ||
-      height > ctx->lim.max_height || ((uintptr_t)feat & 15))
+gs_status gs_repair_features(gs_context *ctx, int width, int height, uint16_t *feat) {
+  if (!ctx || !feat || width <= 0 || height <= 0 || width > ctx->lim.max_width || height > ctx->lim.max_height ||
+      ((uintptr_t)feat & 15))
     return GS_ERR_BAD_ARG;
-  return cuda_status(repair_features(ctx->ws, width, height, rgb_dom, (uint4 *)feat, ctx->stream));
+  return cuda_status(cudaMemcpyAsync(feat, ctx->ws.rp_feat, (size_t)width * height * 16, cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
 }
 
 gs_status gs_repair_infer(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,

@@ -176,14 +176,15 @@ struct RepairOpt {
 cudaError_t prepare_repair();
 size_t repair_train_scratch_bytes(int n_tiles);
 cudaError_t repair_pack(const Workspace &ws, cudaStream_t s);
-cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_dom, uint4 *feat, cudaStream_t s);
+// Features from the warp buffer and the affiliated image after hole
+// classification (rgb_aff before the ROI re-render).
+cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_aff, uint4 *feat, cudaStream_t s);
 cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
                            const uint32_t *n_ptr, uint32_t n_max, float *fill, float *gate, float *out4,
                            uint4 *acts, cudaStream_t s);
-// Features, tile list, network and gated merge for the affiliated eye of the last
-// warp; gated tiles leave ws.tile_mask.
-cudaError_t repair_stereo(const Workspace &ws, int W, int H, const float *rgb_dom, float gate_tau, float *rgb_aff,
-                          cudaStream_t s);
+// Tile list, network and gated merge for the affiliated eye of the last warp
+// (features already in ws.rp_feat); gated tiles leave ws.tile_mask.
+cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s);
 cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const RepairOpt &o, float *host_loss,
                               cudaStream_t s);
 

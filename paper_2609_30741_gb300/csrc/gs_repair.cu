@@ -58,11 +58,13 @@ __host__ __device__ constexpr int poff(int l) {  // canonical flat parameter off
 }
 __host__ __device__ constexpr int mtiles(int l) { return ((kGW - 2 * (l + 1)) * kGW + 127) / 128; }
 
+constexpr int kMaxMT = 6;  // M tiles of the widest layer
 constexpr int kWPackBytes = woff(6);
 static_assert(kWPackBytes == 92160, "packed weight image size");
 static_assert(poff(6) == kRepairParams, "parameter count");
 constexpr int kBufBytes = 4 * kNPos * 16;
-constexpr size_t kNetSmem = 1024 + 2 * (size_t)kBufBytes + kWPackBytes + 6 * 32 * 4 + 64;
+constexpr size_t kNetSmem = 1024 + 2 * (size_t)kBufBytes + kWPackBytes + 6 * 32 * 4 + 8 * kMaxMT + 64;
+static_assert(mtiles(0) <= kMaxMT, "M tiles per layer");
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -98,8 +100,11 @@ __global__ void repair_pack_kernel(const float *__restrict__ master, uint16_t *_
 // ---------------------------------------------------------------- features
 // One block per 16x16 tile; the hole bits of the tile plus an 8-pixel border are
 // staged in shared memory and every pixel takes the nearest hole by brute force.
+// RGB is the affiliated image after hole classification: the warped colour, or
+// at a hole outside the edge strips the method's own fill (gap interpolation,
+// else the row/column fill), 0 inside the strips.
 __global__ void __launch_bounds__(256) repair_features_kernel(const unsigned long long *__restrict__ warp,
-                                                              const float *__restrict__ rgb_dom, int W, int H,
+                                                              const float *__restrict__ rgb_aff, int W, int H,
                                                               uint4 *__restrict__ feat) {
   __shared__ uint8_t s_hole[32][33];
   const int tx0 = blockIdx.x * kRT, ty0 = blockIdx.y * kRT;
@@ -122,13 +127,10 @@ __global__ void __launch_bounds__(256) repair_features_kernel(const unsigned lon
       if (d2 < best && s_hole[(threadIdx.x >> 4) + 8 + dy][(threadIdx.x & 15) + 8 + dx]) best = d2;
     }
   const float dist = fminf(sqrtf((float)best), 8.f) * 0.125f;
-  float r = 0.f, g = 0.f, b = 0.f, inv = 0.f;
+  const size_t hw = (size_t)W * H;
+  const float r = rgb_aff[p], g = rgb_aff[hw + p], b = rgb_aff[2 * hw + p];
+  float inv = 0.f;
   if (!hole) {
-    const uint32_t s = (uint32_t)(k & 0xffffffffull);
-    const size_t hw = (size_t)W * H;
-    r = rgb_dom[s];
-    g = rgb_dom[hw + s];
-    b = rgb_dom[2 * hw + s];
     const float z = __uint_as_float((uint32_t)(k >> 32));
     inv = isfinite(z) && z > 0.f ? 1.f / z : 0.f;
   }
@@ -158,8 +160,8 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
   uint8_t *bufB = smem + kBufBytes;
   uint8_t *wsm = smem + 2 * kBufBytes;
   float *s_bias = (float *)(wsm + kWPackBytes);
-  uint64_t *mbar = (uint64_t *)(s_bias + 6 * 32);
-  uint32_t *s_taddr = (uint32_t *)(mbar + 1);
+  uint64_t *mbar = (uint64_t *)(s_bias + 6 * 32);  // one per M tile of a layer
+  uint32_t *s_taddr = (uint32_t *)(mbar + kMaxMT);
   float *s_red = (float *)(s_taddr + 1);  // [4 warps][2]
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t n = load_n(a.n_tiles, a.n_max);
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
     for (int i = tid; i < 6 * 32; i += kNetThreads) s_bias[i] = a.bias[i];
     uint4 *z = (uint4 *)smem;
     for (int i = tid; i < 2 * kBufBytes / 16; i += kNetThreads) z[i] = make_uint4(0, 0, 0, 0);
-    if (tid == 0) umma::mbar_init(mbar, 1);
+    if (tid < kMaxMT) umma::mbar_init(mbar + tid, 1);
     if (wid == 0) {
       umma::tmem_alloc(s_taddr, kTmemCols);
       umma::tmem_relinquish();
@@ -184,7 +186,7 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
   }
   const uint32_t taddr = *s_taddr;
   const uint32_t sA = umma::smem_u32(bufA), sB = umma::smem_u32(bufB), sW = umma::smem_u32(wsm);
-  uint32_t phase = 0;
+  uint32_t phases = 0;  // bit mt: parity the next completion of mbar[mt] flips to
   bool failed = false;
 
   for (uint32_t t = blockIdx.x; t < n && !failed; t += gridDim.x) {
@@ -220,6 +222,8 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
         const uint4 *srcb = (const uint4 *)in;
         for (int i = tid; i < kg * kNPos; i += kNetThreads) dst[i] = srcb[i];
       }
+      // one thread issues every MMA of the layer, committing each M tile to its
+      // own barrier, so the epilogue of tile mt overlaps the MMAs of mt + 1
       if (tid == 0) {
         const uint32_t idesc = umma::idesc_bf16(128, N);
         const uint32_t wl = sW + (uint32_t)woff(l);
@@ -233,20 +237,22 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
               umma::mma_bf16(taddr + (uint32_t)(mt * N), ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
             }
           }
+          umma::mma_commit(mbar + mt);
         }
-        umma::mma_commit(mbar);
       }
-      const bool ok = umma::mbar_wait(mbar, phase);
-      phase ^= 1u;
-      failed = __syncthreads_or(!ok) != 0;  // the same decision on every thread
-      umma::fence_after_sync();
-      if (failed) {
-        if (tid == 0) atomicOr(a.status, kStTimeout);
-        break;
-      }
+      __syncwarp();
       // epilogue: accumulator rows -> bias, ReLU, border zeroing -> next buffer
       const int shiftL = l + 1;  // this layer's output grid starts (l + 1) pixels in
+      bool layer_ok = true;
       for (int mt = 0; mt < MT; ++mt) {
+        // the same decision on every lane of the warp (tcgen05.ld is warp-wide)
+        const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(mbar + mt, (phases >> mt) & 1u));
+        phases ^= 1u << mt;
+        if (!ok) {
+          layer_ok = false;
+          break;
+        }
+        umma::fence_after_sync();
         const int q = mt * 128 + wid * 32 + lane;
         const int r = q / kGW, c = q % kGW;
         const int y = ty0 - kHalo + shiftL + r, x = tx0 - kHalo + shiftL + c;
@@ -287,12 +293,13 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
               o[3 * kRT * kRT] = o3;
             }
             if (inside) {
-              if (a.fill) {
+              if (a.fill) {  // the network corrects the method's fill (feature RGB)
                 const size_t hw = (size_t)a.W * a.H;
+                const uint4 fv = fin[(size_t)y * a.W + x];
                 float *f = a.fill + (size_t)frame * 3 * hw + (size_t)y * a.W + x;
-                f[0] = o0;
-                f[hw] = o1;
-                f[2 * hw] = o2;
+                f[0] = bf16_lo(fv.x) + o0;
+                f[hw] = bf16_hi(fv.x) + o1;
+                f[2 * hw] = bf16_lo(fv.y) + o2;
               }
               gsum += o3;
               gcnt += 1.f;
@@ -301,6 +308,11 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
         }
       }
       umma::fence_before_sync();
+      failed = __syncthreads_or(!layer_ok) != 0;  // the same decision on every thread
+      if (failed) {
+        if (tid == 0) atomicOr(a.status, kStTimeout);
+        break;
+      }
     }
     if (failed) break;
     // gate logit: mean over the tile's pixels inside the image
@@ -324,22 +336,33 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
   umma::fence_before_sync();
   __syncthreads();
   if (failed) {
-    // an MMA batch may still be in flight: give it a bounded chance to finish
-    // before the accumulator columns are released
-    umma::mbar_wait(mbar, phase ^ 1u, 1u << 20);
+    // MMA batches may still be in flight: give each barrier a bounded chance to
+    // complete before the accumulator columns are released
+    for (int mt = 0; mt < kMaxMT; ++mt) umma::mbar_wait(mbar + mt, (phases >> mt) & 1u, 1u << 18);
   }
   if (wid == 0) umma::tmem_dealloc(taddr, kTmemCols);
 }
 
 // ---------------------------------------------------------------- inference wiring
-// Tiles with at least one hole pixel -> list entries (frame 0).
-__global__ void repair_tile_flags_kernel(const unsigned long long *__restrict__ warp, int W, int H,
-                                         uint8_t *__restrict__ flags) {
-  const int tx0 = blockIdx.x * kRT, ty0 = blockIdx.y * kRT;
-  const int x = tx0 + (threadIdx.x & 15), y = ty0 + (threadIdx.x >> 4);
-  const bool h = x < W && y < H && warp[(size_t)y * W + x] == ~0ull;
+// Candidate tiles (frame 0): tiles the ROI re-render would redraw that hold a hole
+// outside the edge strips. Only there can the gate save work; gap-only tiles
+// keep the cheap interpolation, and strip holes show content the dominant eye
+// never saw.
+__global__ void repair_tile_flags_kernel(const uint8_t *__restrict__ cls, const uint8_t *__restrict__ tile_mask,
+                                         int W, int H, uint8_t *__restrict__ flags) {
+  const int t = blockIdx.y * gridDim.x + blockIdx.x;
+  if (!tile_mask[t]) {
+    if (threadIdx.x == 0) flags[t] = 0;
+    return;
+  }
+  const int x = blockIdx.x * kRT + (threadIdx.x & 15), y = blockIdx.y * kRT + (threadIdx.x >> 4);
+  bool h = false;
+  if (x < W && y < H) {
+    const uint8_t c = cls[(size_t)y * W + x];
+    h = (c & kClsHole) && !(c & kClsStrip);
+  }
   const int any = __syncthreads_or(h);
-  if (threadIdx.x == 0) flags[blockIdx.y * gridDim.x + blockIdx.x] = any ? 1 : 0;
+  if (threadIdx.x == 0) flags[t] = any ? 1 : 0;
 }
 
 struct TileFlagLoad {
@@ -395,8 +418,10 @@ struct TrainArgs {
   float lam;
 };
 
-// per tile: squared errors of the net composite and of the plain image, hole and
-// pixel counts (the loss normalisers and the gate labels)
+// per tile: squared errors at the tile's hole pixels of the network fill and of
+// the plain image, hole and pixel counts (the loss normalisers and the gate
+// labels; the warped pixels carry view-dependent colour the features cannot
+// see, so the label judges the fill alone)
 __global__ void __launch_bounds__(256) repair_stats_kernel(TrainArgs a) {
   const int t = blockIdx.x;
   const uint32_t te = a.tiles[t];
@@ -407,15 +432,17 @@ __global__ void __launch_bounds__(256) repair_stats_kernel(TrainArgs a) {
     const size_t hw = (size_t)a.W * a.H, p = (size_t)y * a.W + x;
     const uint4 f = a.feat[(size_t)frame * hw + p];
     const bool hole = bf16_lo(f.z) > 0.5f;
-    const float warped[3] = {bf16_lo(f.x), bf16_hi(f.x), bf16_lo(f.y)};
+    const float base[3] = {bf16_lo(f.x), bf16_hi(f.x), bf16_lo(f.y)};
     for (int ch = 0; ch < 3; ++ch) {
       const float tg = a.target[(size_t)frame * 3 * hw + ch * hw + p];
       const float pl = a.plain[(size_t)frame * 3 * hw + ch * hw + p];
-      const float o = a.out4[(size_t)t * 4 * kRT * kRT + ch * kRT * kRT + r * kRT + c];
-      const float comp = hole ? fmaxf(o, 0.f) : warped[ch];
-      en += (comp - tg) * (comp - tg);
-      ep += (pl - tg) * (pl - tg);
-      if (hole) l1 += fabsf(o - tg);
+      const float fl = base[ch] + a.out4[(size_t)t * 4 * kRT * kRT + ch * kRT * kRT + r * kRT + c];
+      if (hole) {
+        const float comp = fmaxf(fl, 0.f);
+        en += (comp - tg) * (comp - tg);
+        ep += (pl - tg) * (pl - tg);
+        l1 += fabsf(fl - tg);
+      }
     }
     nh = hole ? 1.f : 0.f;
     np_ = 1.f;
@@ -434,8 +461,8 @@ __global__ void __launch_bounds__(256) repair_stats_kernel(TrainArgs a) {
     float s[5] = {0, 0, 0, 0, 0};
     for (int ww = 0; ww < 8; ++ww)
       for (int k = 0; k < 5; ++k) s[k] += wred[ww][k];
-    a.tile_stats[t * 4 + 0] = s[3] > 0.f ? s[0] / (3.f * s[3]) : 0.f;
-    a.tile_stats[t * 4 + 1] = s[3] > 0.f ? s[1] / (3.f * s[3]) : 0.f;
+    a.tile_stats[t * 4 + 0] = s[2] > 0.f ? s[0] / (3.f * s[2]) : 1.f;  // a tile without holes never passes
+    a.tile_stats[t * 4 + 1] = s[2] > 0.f ? s[1] / (3.f * s[2]) : 0.f;
     a.tile_stats[t * 4 + 2] = s[2];
     a.tile_stats[t * 4 + 3] = s[3];
     atomicAdd(&a.sums[0], s[2]);
@@ -454,7 +481,10 @@ __global__ void __launch_bounds__(256) repair_dout_kernel(TrainArgs a) {
   for (int i = threadIdx.x; i < 32 * kQ; i += 256) dy[i] = 0.f;
   __syncthreads();
   const float net_psnr = psnr_of(a.tile_stats[t * 4 + 0]), plain_psnr = psnr_of(a.tile_stats[t * 4 + 1]);
-  const float label = (net_psnr >= plain_psnr && net_psnr >= 30.f) ? 1.f : 0.f;
+  // positive: the fill reaches 30 dB at the tile's holes and loses at most 0.5 dB
+  // against the plain image there (exactly the re-render inside the edge strips,
+  // so strip tiles stay negative)
+  const float label = (net_psnr >= plain_psnr - 0.5f && net_psnr >= 30.f) ? 1.f : 0.f;
   const float p = 1.f / (1.f + expf(-a.gate[t]));
   const float npx = a.tile_stats[t * 4 + 3];
   const float nh_total = fmaxf(a.sums[0], 1.f);
@@ -468,8 +498,9 @@ __global__ void __launch_bounds__(256) repair_dout_kernel(TrainArgs a) {
   const uint4 f = a.feat[(size_t)frame * hw + pix];
   const bool hole = bf16_lo(f.z) > 0.5f;
   const int q = r * kGW + c;
+  const float base[3] = {bf16_lo(f.x), bf16_hi(f.x), bf16_lo(f.y)};
   for (int ch = 0; ch < 3; ++ch) {
-    const float o = a.out4[(size_t)t * 4 * kRT * kRT + ch * kRT * kRT + r * kRT + c];
+    const float o = base[ch] + a.out4[(size_t)t * 4 * kRT * kRT + ch * kRT * kRT + r * kRT + c];
     const float tg = a.target[(size_t)frame * 3 * hw + ch * hw + pix];
     const float d = o - tg;
     dy[ch * kQ + q] = hole ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (3.f * nh_total) : 0.f;
@@ -565,9 +596,9 @@ cudaError_t repair_pack(const Workspace &ws, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_dom, uint4 *feat, cudaStream_t s) {
+cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_aff, uint4 *feat, cudaStream_t s) {
   const dim3 grid((W + kRT - 1) / kRT, (H + kRT - 1) / kRT);
-  repair_features_kernel<<<grid, 256, 0, s>>>(ws.warpbuf, rgb_dom, W, H, feat);
+  repair_features_kernel<<<grid, 256, 0, s>>>(ws.warpbuf, rgb_aff, W, H, feat);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -597,12 +628,10 @@ cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H,
   return cudaGetLastError();
 }
 
-cudaError_t repair_stereo(const Workspace &ws, int W, int H, const float *rgb_dom, float gate_tau, float *rgb_aff,
-                          cudaStream_t s) {
+cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s) {
   cudaError_t e;
   const int tx = (W + kRT - 1) / kRT, ty = (H + kRT - 1) / kRT, nt = tx * ty;
-  if ((e = repair_features(ws, W, H, rgb_dom, ws.rp_feat, s)) != cudaSuccess) return e;
-  repair_tile_flags_kernel<<<dim3(tx, ty), 256, 0, s>>>(ws.warpbuf, W, H, ws.rp_flags);
+  repair_tile_flags_kernel<<<dim3(tx, ty), 256, 0, s>>>(ws.cls, ws.tile_mask, W, H, ws.rp_flags);
   GS_LAUNCHED(1);
   if ((e = scan_launch(TileFlagLoad{ws.rp_flags}, TileListApply{ws.rp_list, ws.rp_nlist, tx},
                        (const uint32_t *)nullptr, (uint32_t)nt, ws.scan_sums, ws.scan_ticket, nullptr, s)) !=

@@ -390,7 +390,11 @@ cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thre
                                     roi.d_max, ws.strips, ws.widths, ws.drange, ws.tile_mask);
   warp_scatter_kernel<<<grid_for(npix), 256, 0, s>>>(ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H);
   WarpView wv{ws.warpbuf, rgb_dom, W, H, (size_t)npix};
-  classify_kernel<<<grid_for(npix), 256, 0, s>>>(wv, ws.strips, gap_thresh, roi.enable_center, rgb_aff,
+  // the row/column fill of the remaining holes is the output when the centre step
+  // is off, and the repair network's starting point in the repair modes (there
+  // the ROI re-render or the network overwrites those pixels)
+  const int fill_all = !roi.enable_center || roi.repair_mode != 0;
+  classify_kernel<<<grid_for(npix), 256, 0, s>>>(wv, ws.strips, gap_thresh, fill_all ? 0 : 1, rgb_aff,
                                                   ws.warp_depth, ws.cls);
   GS_LAUNCHED(3);
   return cudaGetLastError();

@@ -98,7 +98,7 @@ EXPORTS = {
                                   C.POINTER(Intrinsics), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_repair_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "gs_repair_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
-    "gs_repair_features": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
+    "gs_repair_features": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "gs_repair_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                   C.c_void_p, C.c_void_p]),
     "gs_repair_train_scratch_size": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
@@ -312,12 +312,12 @@ class Context:
                "gs_repair_read")
         return out
 
-    def repair_features(self, rgb_dom, cam, out=None):
-        """Features of the last gs_render_stereo call's warp: (H, W, 8) bfloat16."""
+    def repair_features(self, cam, out=None):
+        """Features of the last gs_render_stereo call made with repair_mode != 0:
+        (H, W, 8) bfloat16."""
         if out is None:
             out = torch.empty(cam.height, cam.width, 8, dtype=torch.bfloat16, device=self.device)
-        _check(lib().gs_repair_features(self.h, _ptr(rgb_dom), cam.width, cam.height, _ptr(out)),
-               "gs_repair_features")
+        _check(lib().gs_repair_features(self.h, cam.width, cam.height, _ptr(out)), "gs_repair_features")
         return out
 
     def repair_infer(self, feat, tiles, fill=None, gate=None):

@@ -1,0 +1,231 @@
+"""Training of the learned hole-repair network on pairs the method generates.
+
+A pair is one stereo frame of a seeded synthetic scene: the features of the
+affiliated eye after the forward warp (gs_repair_features), the full affiliated
+render (gs_render_two_pass) as the target, and the interpolation-only
+affiliated image (gs_render_stereo with the centre step off: gaps interpolated,
+remaining holes filled along their row or column) as the plain fill the gate
+compares against. Frames stay resident on the GPU; every step draws a random
+set of 16x16 tiles that contain holes outside the edge strips (the tiles the
+network serves at inference) and runs gs_repair_train_step (forward on the
+tensor cores, FP32 gradients, AdamW) through the C ABI.
+
+    python -m paper_2609_30741_gb300.repair_train --scene object --scenes 4 \\
+        --poses 6 --steps 1500 --out weights.npy
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import gs, synth
+
+
+def init_weights(seed: int, gate_bias: float = -2.0) -> np.ndarray:
+    """He-normal weights and zero biases for the first five layers; the last
+    layer starts at zero (the fill starts as the method's own fill) with a gate
+    bias that keeps every tile on the plain path until training opens it."""
+    rng = np.random.default_rng(seed)
+    chans = (6, 32, 32, 32, 32, 32, 4)
+    parts = []
+    for l in range(6):
+        ci, co = chans[l], chans[l + 1]
+        if l < 5:
+            parts.append(rng.normal(0.0, math.sqrt(2.0 / (9 * ci)), co * 9 * ci))
+            parts.append(np.zeros(co))
+        else:
+            parts.append(np.zeros(co * 9 * ci))
+            parts.append(np.array([0.0, 0.0, 0.0, gate_bias]))
+    w = np.concatenate(parts).astype(np.float32)
+    assert w.size == gs.REPAIR_PARAMS
+    return w
+
+
+def scene_and_camera(kind: str, seed: int, n: int | None = None):
+    """A seeded scene of the named distribution and its camera."""
+    if kind == "object":
+        scene = synth.scene_object_ground(seed, n or 500_000)
+        cam = synth.centred_camera(1600, 1200, 1600.0)
+        centre = np.array([0.0, 0.0, 2.0])
+        radius = 2.0
+    elif kind == "unbounded":
+        scene = synth.scene_unbounded(seed, n or 1_500_000)
+        cam = synth.centred_camera(1920, 1080, 1600.0)
+        centre = np.zeros(3)
+        radius = 3.0
+    elif kind == "small":
+        scene = synth.scene_slab_ball(seed)
+        cam = synth.centred_camera(256, 192, 300.0)
+        centre = np.array([0.0, 0.0, 3.0])
+        radius = 3.0
+    else:
+        raise ValueError(kind)
+    return scene, cam, centre, radius
+
+
+def random_pose(rng, centre, radius, kind):
+    """A head pose looking at the scene centre from a random direction on a band
+    of yaw (+-30 deg) and pitch (+-10 deg)."""
+    yaw = math.radians(rng.uniform(-30, 30))
+    pitch = math.radians(rng.uniform(-10, 10))
+    if kind == "small":  # stay in front of the slab
+        eye = np.array([rng.uniform(-0.3, 0.3), rng.uniform(-0.2, 0.2), rng.uniform(-0.2, 0.2)])
+        target = eye + np.array([math.sin(yaw) * 0.3, math.sin(pitch) * 0.3, 1.0])
+        return synth.eye_pair(synth.look_at(eye, target))
+    d = np.array([math.sin(yaw) * math.cos(pitch), math.sin(pitch), -math.cos(yaw) * math.cos(pitch)])
+    return synth.eye_pair(synth.look_at(np.asarray(centre) + radius * d, centre))
+
+
+class PairSet:
+    """Resident training frames: features, target, interpolation-only image."""
+
+    def __init__(self, ctx: gs.Context, cam, frames: int, device):
+        H, W = cam.height, cam.width
+        self.cam, self.ctx = cam, ctx
+        self.feat = torch.zeros(frames, H, W, 8, dtype=torch.bfloat16, device=device)
+        self.target = torch.zeros(frames, 3, H, W, device=device)
+        self.plain = torch.zeros(frames, 3, H, W, device=device)
+        self.tiles = []  # hole tiles: frame << 24 | ty << 12 | tx
+        self.n = 0
+
+    def add(self, ds, dom, aff):
+        ctx, cam, k = self.ctx, self.cam, self.n
+        interp = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2,
+                                   roi=gs.roi_params(enable_center=0, repair_mode=3))
+        self.plain[k].copy_(interp["rgb_aff"])
+        ctx.repair_features(cam, out=self.feat[k])
+        full = ctx.render_two_pass(ds, dom, aff, cam)
+        self.target[k].copy_(full["rgb_aff"])
+        # the tiles the network serves: holes outside the edge strips
+        strip = (interp["cls_aff"] & gs.CLS_STRIP) > 0
+        hole = (self.feat[k, :, :, 4].float() > 0.5) & ~strip
+        H, W = cam.height, cam.width
+        th = torch.nn.functional.max_pool2d(hole[None, None].float(), 16, 16, ceil_mode=True)[0, 0] > 0
+        ys, xs = torch.nonzero(th, as_tuple=True)
+        ids = (k << 24) | (ys.to(torch.int64) << 12) | xs.to(torch.int64)
+        self.tiles.append(ids)
+        self.n += 1
+
+    def tile_tensor(self):
+        return torch.cat(self.tiles).to(torch.int32)
+
+
+def build_pairs(kind: str, scenes: int, poses_per_scene: int, seed: int, device, n_surfels=None):
+    """Renders `scenes` x `poses_per_scene` pairs; returns (ctx, PairSet)."""
+    rng = np.random.default_rng(seed)
+    scene, cam, centre, radius = scene_and_camera(kind, seed, n_surfels)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 26, device=device)
+    pairs = PairSet(ctx, cam, scenes * poses_per_scene, device)
+    for s in range(scenes):
+        if s > 0:
+            scene, _, _, _ = scene_and_camera(kind, seed + s, n_surfels)
+        ds = gs.DeviceScene(scene, device=device)
+        for _ in range(poses_per_scene):
+            dom, aff = random_pose(rng, centre, radius, kind)
+            pairs.add(ds, dom, aff)
+    ctx.check_ok()
+    return ctx, pairs
+
+
+def train(ctx: gs.Context, pairs: PairSet, steps: int, batch_tiles: int, lr: float, seed: int,
+          weights: np.ndarray | None = None, log_every: int = 50, gate_weight: float = 1.0):
+    ctx.repair_load(weights if weights is not None else init_weights(seed))
+    all_tiles = pairs.tile_tensor()
+    g = torch.Generator(device=all_tiles.device)
+    g.manual_seed(seed)
+    nb = min(batch_tiles, all_tiles.numel())
+    scratch = ctx.repair_scratch(nb)
+    history = []
+    t0 = time.time()
+    for step in range(steps):
+        pick = torch.randperm(all_tiles.numel(), generator=g, device=all_tiles.device)[:nb]
+        tiles = all_tiles[pick].contiguous()
+        # cosine decay to 10% of the rate
+        lr_s = lr * (0.1 + 0.9 * 0.5 * (1 + math.cos(math.pi * step / max(steps - 1, 1))))
+        loss = ctx.repair_train_step(pairs.feat, pairs.target, pairs.plain, tiles, scratch=scratch, lr=lr_s,
+                                     gate_weight=gate_weight, want_loss=(step % log_every == 0 or step == steps - 1))
+        if step % log_every == 0 or step == steps - 1:
+            history.append((step, float(loss[0]), float(loss[1]), float(loss[2]), float(loss[3])))
+    torch.cuda.synchronize()
+    return ctx.repair_read(0), history, time.time() - t0
+
+
+def psnr(a, b) -> float:
+    mse = torch.mean((a - b) ** 2).item()
+    return 10 * math.log10(1.0 / max(mse, 1e-20))
+
+
+def evaluate(ctx: gs.Context, kind: str, seeds, poses_per_scene: int, seed: int, tau: float, device,
+             n_surfels=None):
+    """Held-out frames: PSNR against the full render of the plain method, of the
+    learned repair, and of the interpolation-only fill; hole-pixel L1 of the
+    network fill and of the interpolation fill; share of ROI tiles the gate took
+    out of the re-render."""
+    rng = np.random.default_rng(seed)
+    rows = []
+    for sd in seeds:
+        scene, cam, centre, radius = scene_and_camera(kind, sd, n_surfels)
+        ds = gs.DeviceScene(scene, device=device)
+        H, W = cam.height, cam.width
+        fill = torch.zeros(1, 3, H, W, device=device)
+        for _ in range(poses_per_scene):
+            dom, aff = random_pose(rng, centre, radius, kind)
+            full = {k: v.clone() for k, v in ctx.render_two_pass(ds, dom, aff, cam).items()}
+            interp = {k: v.clone() for k, v in
+                      ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2, roi=gs.roi_params(enable_center=0)).items()}
+            plain = {k: v.clone() for k, v in ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2).items()}
+            ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2, roi=gs.roi_params(repair_mode=3))
+            feat = ctx.repair_features(cam)
+            learned = {k: v.clone() for k, v in ctx.render_stereo(
+                ds, dom, aff, cam, gap_thresh=2, roi=gs.roi_params(repair_mode=1, gate_tau=tau)).items()}
+            ty, tx = (H + 15) // 16, (W + 15) // 16
+            tiles = torch.tensor([(y << 12) | x for y in range(ty) for x in range(tx)], dtype=torch.int32,
+                                 device=device)
+            ctx.repair_infer(feat[None], tiles, fill=fill)
+            strip = (plain["cls_aff"] & gs.CLS_STRIP) > 0
+            hole = (feat[:, :, 4].float() > 0.5) & ~strip  # holes the method fills itself
+            tgt = full["rgb_aff"]
+            base = feat[:, :, :3].float().permute(2, 0, 1)
+            l1_net = (torch.clamp(fill[0], min=0) - tgt).abs()[:, hole].mean().item() if hole.any() else 0.0
+            # the method's fill of the same holes (the network's starting point)
+            l1_interp = (base - tgt).abs()[:, hole].mean().item() if hole.any() else 0.0
+            roi_plain = ((plain["cls_aff"] & gs.CLS_RENDER) > 0).float().mean().item()
+            roi_learned = ((learned["cls_aff"] & gs.CLS_RENDER) > 0).float().mean().item()
+            net_px = ((learned["cls_aff"] & gs.CLS_NET) > 0).float().mean().item()
+            rows.append(dict(psnr_plain=psnr(plain["rgb_aff"], tgt), psnr_learned=psnr(learned["rgb_aff"], tgt),
+                             psnr_interp=psnr(interp["rgb_aff"], tgt), l1_net=l1_net, l1_interp=l1_interp,
+                             roi_plain=roi_plain, roi_learned=roi_learned, net_pixels=net_px))
+    ctx.check_ok()
+    return {k: float(np.mean([r[k] for r in rows])) for k in rows[0]}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--scene", default="object", choices=["object", "unbounded", "small"])
+    ap.add_argument("--scenes", type=int, default=4)
+    ap.add_argument("--poses", type=int, default=6)
+    ap.add_argument("--surfels", type=int, default=None)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--gate-weight", type=float, default=1.0)
+    ap.add_argument("--seed", type=int, default=7000)
+    ap.add_argument("--out", required=True)
+    args = ap.parse_args()
+    dev = torch.device("cuda", 0)
+    from . import build
+    build.build()
+    ctx, pairs = build_pairs(args.scene, args.scenes, args.poses, args.seed, dev, args.surfels)
+    w, hist, secs = train(ctx, pairs, args.steps, args.batch, args.lr, args.seed, gate_weight=args.gate_weight)
+    np.save(args.out, w)
+    for h in hist:
+        print(f"step {h[0]:5d} loss {h[1]:.5f} l1 {h[2]:.5f} bce {h[3]:.5f} pos {h[4]:.3f}")
+    print(f"trained {args.steps} steps in {secs:.1f} s on {pairs.n} frames, {pairs.tile_tensor().numel()} hole tiles")
+
+
+if __name__ == "__main__":
+    main()

@@ -85,7 +85,7 @@ def test_forward_matches_oracle(gs, H, W):
     _, gate = ctx.repair_infer(feat, tiles, fill=fill)
     ctx.check_ok()
     out, _ = R.forward(x, Wt, b, bf16=True)
-    _close(fill[0].cpu().double().numpy(), out[:3], "fill")
+    _close(fill[0].cpu().double().numpy(), x[:3] + out[:3], "fill")
     g_ref = R.tile_gate(out[3]).ravel()
     _close(gate.cpu().double().numpy(), g_ref, "gate")
 
@@ -130,7 +130,7 @@ def test_gradients_match_oracle(gs):
     loss = ctx.repair_train_step(feat, tgt, tgt.clone(), _tiles(H, W), lr=0.0, gate_weight=0.1)
     g_gpu = ctx.repair_read(1).astype(np.float64)
     out, acts = R.forward(x, Wt, b, bf16=True)
-    L, dout = R.loss(out, target, hole, np.zeros((2, 3)), lam=0.1)
+    L, dout = R.loss(out, target, hole, np.zeros((2, 3)), lam=0.1, base=x[:3])
     dW, db = R.backward(acts, Wt, dout)
     g_ref = R.pack(dW, db)
     assert abs(loss[0] - L) <= 1e-3 * abs(L)
@@ -164,28 +164,34 @@ def test_adamw_steps_reduce_the_loss(gs):
     assert losses[-1] < 0.6 * losses[0], losses[::5]
 
 
-def test_features_match_oracle(gs):
+def test_features_match_oracle(gs, orc):
     scene, cam, dom, aff = synth.workload_small()
     ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 22)
     ds = gs.DeviceScene(scene)
-    out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
-    feat = ctx.repair_features(out["rgb_dom"], cam)
+    out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2, roi=gs.roi_params(repair_mode=3))
+    feat = ctx.repair_features(cam)
     ctx.check_ok()
     H, W = cam.height, cam.width
     warp, _ = ctx.buffer(gs.BUF_WARP, torch.int64, None)
+    strips, _ = ctx.buffer(gs.BUF_STRIPS, torch.int32, (4, 4))
     key = warp[:H * W].cpu().numpy().view(np.uint64).reshape(H, W)
     hole = key == np.uint64(0xFFFFFFFFFFFFFFFF)
     src = np.where(hole, 0, (key & np.uint64(0xFFFFFFFF)).astype(np.int64))
     rgb_dom = out["rgb_dom"].cpu().double().numpy().reshape(3, -1)
-    rgb_w = rgb_dom[:, src.ravel()].reshape(3, H, W)
+    rgb_w = np.where(hole[None], 0.0, rgb_dom[:, src.ravel()].reshape(3, H, W))
+    in_strip = np.zeros((H, W), bool)
+    for x0, y0, x1, y1 in strips.cpu().numpy():
+        in_strip[y0:y1, x0:x1] = True
+    # the method's fill of the non-strip holes (the centre-off fallback included)
+    _, rgb_c = orc.classify(hole, rgb_w, in_strip, 2, center_enabled=0)
     z = (key >> np.uint64(32)).astype(np.uint32).view(np.float32).astype(np.float64)
-    ref = R.round_bf16(R.features(rgb_w, z, hole))
-    got = feat.float().cpu().double().numpy()
-    got = np.moveaxis(got, -1, 0)
+    ref = R.round_bf16(R.features(rgb_c, z, hole))
+    got = np.moveaxis(feat.float().cpu().double().numpy(), -1, 0)
     assert np.all(got[6:] == 0)
     assert np.array_equal(got[4], ref[4])
-    assert np.array_equal(got[:3], ref[:3])
-    for ch in (3, 5):  # one bfloat16 step at most (float32 vs float64 before rounding)
+    assert hole.mean() > 0.005 and (hole & ~in_strip).sum() > 0
+    # at most one bfloat16 step apart (float32 vs float64 before rounding)
+    for ch in (0, 1, 2, 3, 5):
         assert np.all(np.abs(got[ch] - ref[ch]) <= 2.0 ** -7 * np.maximum(np.abs(ref[ch]), 1e-30)), ch
 
 
@@ -210,22 +216,66 @@ def test_stereo_gate_closed_and_open(gs):
     closed = _stereo(gs, ctx, ds, dom, aff, cam, 1)
     for k in ("rgb_aff", "cls_aff"):
         assert torch.equal(closed[k], plain[k]), k
-    # gate always passes: every hole pixel of a tile with holes takes max(fill, 0)
-    # and no tile with a hole is re-rendered
+    # gate always passes: the candidate tiles (re-rendered by the plain method and
+    # holding a hole outside the edge strips) take max(fill, 0) at their hole
+    # pixels and are not re-rendered; every other tile is the plain method's
     Wt, b = _weights(7, gate_bias=1e4)
     ctx.repair_load(R.pack(Wt, b))
     opened = _stereo(gs, ctx, ds, dom, aff, cam, 1)
-    feat = ctx.repair_features(opened["rgb_dom"], cam)
+    feat = ctx.repair_features(cam)
     H, W = cam.height, cam.width
     fill = torch.zeros(1, 3, H, W, device="cuda")
     ctx.repair_infer(feat[None], _tiles(H, W), fill=fill)
-    hole = (plain["cls_aff"] & gs.CLS_HOLE) > 0
+    pc = plain["cls_aff"]
+    hole = (pc & gs.CLS_HOLE) > 0
+
+    def per_tile(m):
+        return m.reshape(H // 16, 16, W // 16, 16).any(3).any(1)
+
+    def per_pixel(t):
+        return t.repeat_interleave(16, 0).repeat_interleave(16, 1)
+
+    cand = per_pixel(per_tile((pc & gs.CLS_RENDER) > 0) & per_tile(hole & ((pc & gs.CLS_STRIP) == 0)))
+    assert cand.any() and (~cand & per_pixel(per_tile((pc & gs.CLS_RENDER) > 0))).any()
     cls = opened["cls_aff"]
-    assert torch.equal((cls & gs.CLS_NET) > 0, hole)
+    assert torch.equal((cls & gs.CLS_NET) > 0, hole & cand)
     want = torch.clamp(fill[0], min=0.0)
-    assert torch.equal(opened["rgb_aff"][:, hole], want[:, hole])
-    # tiles without holes are unchanged from the plain method
-    th = hole.reshape(H // 16, 16, W // 16, 16).any(3).any(1)
-    keep = ~th.repeat_interleave(16, 0).repeat_interleave(16, 1)
-    assert torch.equal(opened["rgb_aff"][:, keep], plain["rgb_aff"][:, keep])
-    assert not torch.any((cls[~keep] & gs.CLS_RENDER) > 0)
+    assert torch.equal(opened["rgb_aff"][:, hole & cand], want[:, hole & cand])
+    assert torch.equal(opened["rgb_aff"][:, ~cand], plain["rgb_aff"][:, ~cand])
+    assert not torch.any((cls[cand] & gs.CLS_RENDER) > 0)
+
+
+def test_gate_learns_a_rule_the_features_carry(gs):
+    """Targets are built so that a tile's label is 1 exactly when under 10% of its
+    pixels are holes: there the starting fill is exact, elsewhere the target
+    carries zero-mean noise no fill can predict. Training must separate the two
+    kinds of tile through the gate."""
+    rng = np.random.default_rng(21)
+    H, W = 128, 128
+    frac = rng.choice([0.03, 0.3], size=(H // 16, W // 16))
+    hole = rng.random((H, W)) < np.kron(frac, np.ones((16, 16)))
+    x = np.zeros((6, H, W))
+    x[:3] = rng.random((3, H, W))
+    x[3] = rng.uniform(0.2, 2.0, (H, W))
+    x[3, hole] = 0.0
+    x[4] = hole
+    x[5] = R.distance_to_hole(hole)
+    x = R.round_bf16(x)
+    pos = np.kron(frac < 0.1, np.ones((16, 16), bool))
+    target = np.where(pos[None], x[:3], x[:3] + rng.uniform(-0.5, 0.5, x[:3].shape))
+    plain = target + 0.05  # the plain image is never perfect
+    Wt, b = R.unpack(__import__("paper_2609_30741_gb300.repair_train", fromlist=["x"]).init_weights(3))
+    ctx = _ctx(gs, W, H)
+    ctx.repair_load(R.pack(Wt, b))
+    feat = _to_device(x)
+    tgt = torch.tensor(target[None], dtype=torch.float32, device="cuda")
+    pl = torch.tensor(plain[None], dtype=torch.float32, device="cuda")
+    tiles = _tiles(H, W)
+    scratch = ctx.repair_scratch(tiles.numel())
+    for _ in range(300):
+        loss = ctx.repair_train_step(feat, tgt, pl, tiles, scratch=scratch, lr=2e-3, gate_weight=1.0,
+                                     want_loss=False)
+    loss = ctx.repair_train_step(feat, tgt, pl, tiles, scratch=scratch, lr=0.0, gate_weight=1.0)
+    _, gate = ctx.repair_infer(feat, tiles)
+    g = gate.cpu().numpy().reshape(H // 16, W // 16)
+    assert np.all(g[frac < 0.1] > g[frac > 0.1].max()), (g[frac < 0.1].min(), g[frac > 0.1].max())

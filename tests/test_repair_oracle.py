@@ -78,7 +78,7 @@ def test_shifted_tap_translates():
 def _net_loss(flat, x, target, hole, label):
     W, b = R.unpack(flat)
     out, _ = R.forward(x, W, b)
-    return R.loss(out, target, hole, label)[0]
+    return R.loss(out, target, hole, label, base=x[:3])[0]
 
 
 def test_backward_matches_finite_differences():
@@ -91,7 +91,7 @@ def test_backward_matches_finite_differences():
     flat = R.pack(W, b)
     label = np.array([[1.0, 0.0], [0.0, 1.0]])
     out, acts = R.forward(x, W, b)
-    L, dout = R.loss(out, target, hole, label)
+    L, dout = R.loss(out, target, hole, label, base=x[:3])
     dW, db = R.backward(acts, W, dout)
     g = R.pack(dW, db)
     idx = rng.choice(flat.size, 60, replace=False)
@@ -115,6 +115,20 @@ def test_loss_gate_gradient_closed_form():
     np.testing.assert_allclose(d[3], 0.5 * (p - 1.0) / 256, rtol=1e-12)
 
 
+def test_residual_fill_starts_at_the_base():
+    # a zero last layer reproduces the base fill: the L1 term is the base's error
+    rng = np.random.default_rng(13)
+    x = rng.random((6, 16, 16))
+    W, b = R.init_weights(1)
+    W[5][:] = 0.0
+    b[5][:] = 0.0
+    out, _ = R.forward(x, W, b)
+    hole = rng.random((16, 16)) < 0.5
+    target = rng.random((3, 16, 16))
+    L, _ = R.loss(out, target, hole, np.array([[0.5]]), lam=0.0, base=x[:3])
+    assert abs(L - (np.abs(x[:3] - target) * hole).sum() / (3 * hole.sum())) < 1e-12
+
+
 def test_features():
     rgb = np.full((3, 5, 6), 0.25)
     z = np.full((5, 6), 2.0)
@@ -124,5 +138,5 @@ def test_features():
     f = R.features(rgb, z, hole)
     assert f.shape == (6, 5, 6)
     assert f[3, 1, 1] == 0.5 and f[3, 0, 0] == 0.0 and f[3, 2, 3] == 0.0
-    assert np.all(f[:3, 2, 3] == 0) and f[4, 2, 3] == 1.0
+    assert np.all(f[:3] == 0.25) and f[4, 2, 3] == 1.0
     assert abs(f[5, 2, 5] - 2.0 / 8.0) < 1e-15 and abs(f[5, 0, 0] - np.hypot(2, 3) / 8) < 1e-15
