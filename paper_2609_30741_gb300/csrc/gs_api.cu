@@ -1,4 +1,5 @@
 // C ABI: contexts, workspace layout and the entry points of include/gs.h.
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -52,6 +53,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     ws.dkey[e] = c.take<uint32_t>(N);
     ws.dval[e] = c.take<uint32_t>(N);
   }
+  ws.uval = c.take<uint32_t>(N);
   ws.bin_warp_surfels = bin_warp_surfels(lim.max_surfels);
   ws.bin_nch = bin_chunks(lim.max_surfels);
   const size_t table = tiles * ws.bin_nch;
@@ -123,6 +125,7 @@ __global__ void reset_counters_kernel(Counters *c) {
     c->n_sort[0] = c->n_sort[1] = 0;
     c->n_rows[0] = c->n_rows[1] = 0;
     c->n_band[0] = c->n_band[1] = 0;
+    c->n_union = 0;
     c->dmin_bits = 0x7f800000u;
     c->dmax_bits = 0u;
     c->n_rects = 0;
@@ -243,6 +246,17 @@ static PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsic
     memcpy(pa.t[1], b->t, sizeof(double) * 3);
   }
   pa.neyes = b ? 2 : 1;
+  pa.parallel = 0;
+  if (b && memcmp(a->R, b->R, sizeof(double) * 9) == 0) {
+    // baseline along the optical axis (column 2 of R)?
+    double d[3], along = 0.0, len2 = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      d[k] = b->t[k] - a->t[k];
+      along += d[k] * a->R[k * 3 + 2];
+      len2 += d[k] * d[k];
+    }
+    pa.parallel = fabs(along) <= 1e-12 + 1e-9 * sqrt(len2) ? 1 : 0;
+  }
   pa.fx = in->fx; pa.fy = in->fy; pa.cx = in->cx; pa.cy = in->cy;
   pa.W = in->width; pa.H = in->height;
   return pa;
@@ -374,12 +388,12 @@ static void mark(gs_context *ctx, int slot) {
 }
 
 static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye, int W, int H, float3 bg,
-                                 float *rgb, float *depth, float *trans, bool stats, int slot) {
+                                 float *rgb, float *depth, float *trans, bool stats, int slot, int order) {
   const Workspace &ws = ctx->ws;
   cudaStream_t s = ctx->stream;
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
   ctx->last_tiles = tx * ty;
-  cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s);
+  cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s, order);
   if (e != cudaSuccess) return cuda_fail(e);
   mark(ctx, slot);
   e = launch_blend(ws, eye, W, H, nullptr, bg, rgb, depth, trans, nullptr, stats, ctx->counting != 0, s);
@@ -536,7 +550,7 @@ gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *
   return run_graph(ctx, 0, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
     gs_status st = begin_call(ctx, scene, p);
     if (st != GS_OK) return st;
-    return render_eye_full(ctx, scene, 0, intr->width, intr->height, b, rgb, depth, trans, false, 2);
+    return render_eye_full(ctx, scene, 0, intr->width, intr->height, b, rgb, depth, trans, false, 2, kOrderOwn);
   });
 }
 
@@ -577,12 +591,14 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
   kb.add(gap_thresh);
   kb.add(*roi);
   kb.add(*out);
+  kb.add(pa.parallel);  // selects the depth-order path of the affiliated eye
   return run_graph(ctx, 1, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
     gs_status st = begin_call(ctx, scene, p);
     if (st != GS_OK) return st;
     const float3 black = make_float3(0.f, 0.f, 0.f);
     // Stage 1: dominant eye, RGB + depth proxy (+ the per-frame depth range)
-    st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2);
+    st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2,
+                         p.parallel ? kOrderUnion : kOrderOwn);
     if (st != GS_OK) return st;
     // Stages 2-3: warp, edge ROIs, gaps
     cudaError_t e = launch_warp_classify(ctx->ws, W, H, gap_thresh, *roi, out->rgb_dom, out->depth_dom,
@@ -606,7 +622,8 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     mark(ctx, 5);
     // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
     ctx->last_tiles = tx * ty;
-    e = launch_binning(ctx->ws, 1, scene->n, tx, ty, ctx->ws.tile_mask, ctx->stream);
+    e = launch_binning(ctx->ws, 1, scene->n, tx, ty, ctx->ws.tile_mask, ctx->stream,
+                       p.parallel ? kOrderReuse : kOrderOwn);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
     e = launch_blend(ctx->ws, 1, W, H, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ctx->ws.cls, false,
@@ -628,13 +645,16 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
   KeyBuilder kb;
   key_common(kb, ctx, 2, scene, intr);
   kb.add(*out);
+  kb.add(pa.parallel);
   return run_graph(ctx, 2, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
     gs_status st = begin_call(ctx, scene, p);
     if (st != GS_OK) return st;
     const float3 black = make_float3(0.f, 0.f, 0.f);
-    st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, false, 2);
+    st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, false, 2,
+                         p.parallel ? kOrderUnion : kOrderOwn);
     if (st != GS_OK) return st;
-    return render_eye_full(ctx, scene, 1, W, H, black, out->rgb_aff, nullptr, nullptr, false, 4);
+    return render_eye_full(ctx, scene, 1, W, H, black, out->rgb_aff, nullptr, nullptr, false, 4,
+                           p.parallel ? kOrderReuse : kOrderOwn);
   });
 }
 

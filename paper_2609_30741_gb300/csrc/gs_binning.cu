@@ -290,14 +290,19 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
 
 // ---------------------------------------------------------------- compaction
 // A surfel enters the depth sort when its bounding rectangle is not empty and,
-// for an ROI binning, when that rectangle holds at least one ROI tile.
+// for an ROI binning, when that rectangle holds at least one ROI tile. The union
+// variant (dominant eye of a parallel two-eye call) takes every surfel either
+// eye bins.
 struct VisibleLoad {
   const uint32_t *cnt;
+  const uint32_t *cnt_other;  // union with the other eye's binned set, or null
   const ushort4 *rect;
-  const uint32_t *sat;  // summed-area table of the ROI mask, or null
+  const uint32_t *sat;        // summed-area table of the ROI mask, or null
   int tiles_x;
   __device__ uint32_t operator()(uint32_t i) const {
-    if (cnt[i] == 0u) return 0u;
+    const bool mine = cnt[i] > 0u;
+    if (cnt_other) return (mine || cnt_other[i] > 0u) ? 1u : 0u;
+    if (!mine) return 0u;
     if (!sat) return 1u;
     const ushort4 rc = rect[i];
     return sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z) ? 1u : 0u;
@@ -312,6 +317,40 @@ struct CompactApply {
     if (v) {
       key_out[prefix] = zkey[i];
       val_out[prefix] = i;
+    }
+  }
+  __device__ void end(uint32_t, uint32_t total) const { *n_out = total; }
+};
+
+// The affiliated eye's surfels in the dominant eye's depth order: a stable filter
+// of that order. For a parallel rig both eyes' keys are identical, so the
+// filtered order is exactly the affiliated (depth, index) order.
+struct ReuseLoad {
+  const uint32_t *uval, *n_union;
+  uint32_t n_max;
+  const uint32_t *cnt;
+  const ushort4 *rect;
+  const uint32_t *sat;
+  int tiles_x;
+  __device__ uint32_t operator()(uint32_t i) const {
+    if (i >= load_n(n_union, n_max)) return 0u;
+    const uint32_t id = uval[i];
+    if (cnt[id] == 0u) return 0u;
+    if (!sat) return 1u;
+    const ushort4 rc = rect[id];
+    return sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z) ? 1u : 0u;
+  }
+};
+
+struct ReuseApply {
+  const uint32_t *uval, *zkey;
+  uint32_t *key_out, *val_out;
+  uint32_t *n_out;
+  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
+    if (v) {
+      const uint32_t id = uval[i];
+      key_out[prefix] = zkey[id];
+      val_out[prefix] = id;
     }
   }
   __device__ void end(uint32_t, uint32_t total) const { *n_out = total; }
@@ -356,6 +395,7 @@ struct BandArgs {
   const uint32_t *ids;     // depth-ordered binned surfels
   const uint32_t *n_vis;
   uint32_t n_max;
+  const uint32_t *cnt;     // this eye's rectangle tile counts (0: not binned by this eye)
   const ushort4 *rect;
   const uint32_t *row_off;
   const uint32_t *sat;     // ROI mask summed-area table, or null
@@ -414,8 +454,8 @@ __global__ void __launch_bounds__(32 * kListWarps) band_list_kernel(BandArgs a) 
       const uint32_t j = sub + (uint32_t)lane;
       int b0 = 1, b1 = 0, y0 = 0, y1 = -1, x0 = 0, x1 = -1;
       uint32_t id = 0, ro = 0;
-      if (j < j1) {
-        id = a.ids[j];
+      if (j < j1) id = a.ids[j];
+      if (j < j1 && a.cnt[id] > 0u) {
         const ushort4 rc = a.rect[id];
         y0 = rc.y; y1 = rc.w; x0 = rc.x; x1 = rc.z;
         b0 = y0 / kBandRows;
@@ -696,7 +736,7 @@ cudaError_t prepare_binning(int max_tiles_x) {
 }
 
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
-                           const uint8_t *tile_mask, cudaStream_t s) {
+                           const uint8_t *tile_mask, cudaStream_t s, int order) {
   cudaError_t err;
   Counters *ctr = ws.ctr;
   const int ntiles = tiles_x * tiles_y;
@@ -707,9 +747,17 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
     GS_LAUNCHED(1);
   }
   // 1. compact the binned surfels: (depth bits, surfel id)
-  err = scan_launch(VisibleLoad{ws.cnt[eye], ws.rect[eye], tile_mask ? ws.mask_sat : nullptr, tiles_x},
-                    CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
-                    (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
+  const uint32_t *sat = tile_mask ? ws.mask_sat : nullptr;
+  if (order == kOrderReuse) {  // the dominant order, filtered: already depth-ordered
+    err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, ws.cnt[eye], ws.rect[eye], sat, tiles_x},
+                      ReuseApply{ws.uval, ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
+                      (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
+  } else {
+    err = scan_launch(VisibleLoad{ws.cnt[eye], order == kOrderUnion ? ws.cnt[1 - eye] : nullptr, ws.rect[eye], sat,
+                                  tiles_x},
+                      CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
+                      (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
+  }
   if (err != cudaSuccess) return err;
   // 2. tile ranges of every rectangle row of those surfels
   if ((err = cudaMemsetAsync(&ctr->n_rows[eye], 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
@@ -722,14 +770,24 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   }
   // 3. depth order (the low 32 bits of the packed key; stable, so ties keep id order)
   int which = 0;
-  if ((err = radix_sort(ws.dkey, ws.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
+  if (order != kOrderReuse &&
+      (err = radix_sort(ws.dkey, ws.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
     return err;
+  if (order == kOrderUnion && n > 0) {  // kept for the affiliated eye
+    if ((err = cudaMemcpyAsync(ws.uval, ws.dval[which], sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+      return err;
+    if ((err = cudaMemcpyAsync(&ctr->n_union, &ctr->n_vis[eye], sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) !=
+        cudaSuccess)
+      return err;
+  }
   const int nbands = (tiles_y + kBandRows - 1) / kBandRows;
   // 4. per chunk: each warp's depth-ordered (surfel, band) lists
   BandArgs ba;
   ba.ids = ws.dval[which];
   ba.n_vis = &ctr->n_vis[eye];
   ba.n_max = (uint32_t)n;
+  ba.cnt = ws.cnt[eye];
   ba.rect = ws.rect[eye];
   ba.row_off = ws.row_off[eye];
   ba.sat = tile_mask ? ws.mask_sat : nullptr;

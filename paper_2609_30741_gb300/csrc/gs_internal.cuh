@@ -47,6 +47,7 @@ struct PoseArgs {
   double fx, fy, cx, cy;
   int W, H;
   int neyes;
+  int parallel;  // the eyes share orientation and the baseline lies in the image plane
 };
 
 struct Counters {
@@ -58,7 +59,8 @@ struct Counters {
   uint32_t n_sort[2];    // instances actually binned per eye (capacity-clamped)
   uint32_t n_rows[2];    // (surfel, tile row) spans per eye
   uint32_t n_band[2];    // (surfel, band) list entries of the last binning per eye
-  uint32_t pad[1];
+  uint32_t n_union;      // surfels in the dominant binning's depth order (both eyes' visible set)
+  uint32_t pad[5];
   unsigned long long pairs[2];    // evaluated (pixel, surfel) pairs per eye (counting mode)
   unsigned long long contrib[2];  // of which contributed (alpha >= 1/255, before termination)
 };
@@ -85,6 +87,7 @@ struct Workspace {
   uint32_t *zkey[2];            // float bits of the centre depth per surfel and eye
   uint32_t *cnt_bin;            // tiles each surfel reaches in the last binning (keep_intermediates)
   uint32_t *dkey[2], *dval[2];  // depth sort double buffers
+  uint32_t *uval;               // depth-ordered union of both eyes' binned surfels (dominant keys)
   uint4 *bin_table;             // [tile][chunk] per-warp instance counts (8 x 16 bits)
   struct BandEntry *band_pool;  // (surfel, band) entries of every warp's lists
   uint32_t band_pool_cap;
@@ -148,9 +151,17 @@ const void *setup_cams_kernel_ptr();
 cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes, int W, int H,
                               cudaStream_t s);
 // Bins the visible surfels of `eye` (restricted to tile_mask when given) into
-// sorted per-tile instance lists and their ranges.
+// sorted per-tile instance lists and their ranges. Depth order:
+//   kOrderOwn     sort this eye's binned surfels by their own keys;
+//   kOrderUnion   (dominant eye of a parallel two-eye call) sort every surfel
+//                 either eye bins by the dominant keys and keep that order in
+//                 ws.uval;
+//   kOrderReuse   (affiliated eye after kOrderUnion) filter the kept order: for
+//                 a parallel rig both eyes' depth keys are identical, so the
+//                 filtered order is the affiliated (depth, index) order.
+enum BinOrder { kOrderOwn = 0, kOrderUnion = 1, kOrderReuse = 2 };
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
-                           const uint8_t *tile_mask, cudaStream_t s);
+                           const uint8_t *tile_mask, cudaStream_t s, int order = kOrderOwn);
 // Chunk geometry of the binning for a surfel capacity, and the one-time
 // shared-memory opt-in of its kernel for the widest image.
 uint32_t bin_warp_surfels(int max_surfels);

@@ -32,6 +32,11 @@ __global__ void setup_cams_kernel(PoseArgs pa, CamBlock *cams) {
     c.tiles_x = (pa.W + kTile - 1) / kTile;
     c.tiles_y = (pa.H + kTile - 1) / kTile;
   }
+  // A parallel rig (equal orientation, baseline in the image plane, Sec. 4.2):
+  // both cameras measure the same depth, z_aff = z_dom in exact arithmetic. The
+  // two offsets differ only by FP64 rounding of R^T R = I, so the affiliated eye
+  // takes the dominant one and both eyes' depth keys are bit-identical.
+  if (pa.parallel) cb.eye[1].t[2] = cb.eye[0].t[2];
   const int a = pa.neyes > 1 ? 1 : 0;
   const double *Rd = pa.R[0], *td = pa.t[0], *Ra = pa.R[a], *ta = pa.t[a];
   for (int i = 0; i < 3; ++i) {

@@ -22,11 +22,15 @@ constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 pairs per tile
 
 // n_table = 256 * number of tiles, written by phase 1 for the scan of phase 2.
+// With `offs` given (small tables), the last block to finish (counted on
+// *ticket, which it resets) also runs phase 2: thread d scans digit d's row.
 static __global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint32_t *__restrict__ keys,
                                                                      const uint32_t *n_ptr, uint32_t n_max, int shift,
                                                                      uint32_t *__restrict__ table,
-                                                                     uint32_t *__restrict__ n_table) {
+                                                                     uint32_t *__restrict__ n_table,
+                                                                     uint32_t *__restrict__ offs, uint32_t *ticket) {
   __shared__ uint32_t h[kRsThreads / 32][256];
+  __shared__ uint32_t s_last, s_scan[32];
   const uint32_t n = load_n(n_ptr, n_max);
   const uint32_t ntiles = (n + kRsTile - 1) / kRsTile;
   if (blockIdx.x == 0 && threadIdx.x == 0) *n_table = 256u * ntiles;
@@ -47,6 +51,26 @@ static __global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint32
     table[(size_t)threadIdx.x * ntiles + t] = c;
     __syncthreads();
   }
+  if (!offs) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const uint32_t *row = table + (size_t)threadIdx.x * ntiles;
+  uint32_t tot = 0;
+  for (uint32_t t = 0; t < ntiles; ++t) tot += __ldcg(row + t);
+  uint32_t base;
+  block_exclusive_scan<kRsThreads>(tot, &base, s_scan);
+  uint32_t *orow = offs + (size_t)threadIdx.x * ntiles;
+  for (uint32_t t = 0; t < ntiles; ++t) {
+    const uint32_t v = __ldcg(row + t);
+    orow[t] = base;
+    base += v;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 struct TableLoad {
@@ -168,13 +192,19 @@ inline cudaError_t radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], 
   const int npass = (bits + 7) / 8;
   const int grid = radix_grid(n_max);
   const uint32_t table_max = (uint32_t)radix_table_words(n_max);
+  // small tables (<= 32 tiles per digit row) are scanned by the histogram
+  // kernel's last block: one launch fewer; larger rows scan faster in parallel
+  const bool fused = (n_max + kRsTile - 1) / kRsTile <= 32;
   int cur = 0;
   for (int p = 0; p < npass; ++p) {
-    rs_hist_kernel<<<grid, kRsThreads, 0, s>>>(keys[cur], n_ptr, n_max, 8 * p, sc.table, sc.n_table);
+    rs_hist_kernel<<<grid, kRsThreads, 0, s>>>(keys[cur], n_ptr, n_max, 8 * p, sc.table, sc.n_table,
+                                               fused ? sc.offs : nullptr, sc.ticket);
     GS_LAUNCHED(1);
-    cudaError_t e = scan_launch(TableLoad{sc.table}, TableApply{sc.offs}, sc.n_table, table_max, sc.sums, sc.ticket,
-                                nullptr, s);
-    if (e != cudaSuccess) return e;
+    if (!fused) {
+      cudaError_t e = scan_launch(TableLoad{sc.table}, TableApply{sc.offs}, sc.n_table, table_max, sc.sums,
+                                  sc.ticket, nullptr, s);
+      if (e != cudaSuccess) return e;
+    }
     rs_scatter_kernel<<<grid, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_ptr, n_max,
                                                   8 * p, sc.offs);
     GS_LAUNCHED(1);
