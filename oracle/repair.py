@@ -206,3 +206,68 @@ def init_weights(seed, scale=1.0):
         W.append(rng.normal(0.0, scale * np.sqrt(2.0 / (9 * ci)), (co, 3, 3, ci)))
         b.append(np.zeros(co))
     return W, b
+
+
+# ---------------------------------------------------------------- FP8 (e4m3) path
+# The network's FP8 variant: every layer input x_l[c] is stored as an e4m3 code
+# q = e4m3(x / sx[l][c]) with a per-channel scale sx from calibration (the
+# largest |x_l[c]| seen by the BF16 network over calibration tiles, mapped to
+# 448, the largest finite e4m3 value); the input scale is folded into the weights,
+# W'[o, ., ., c] = W[o, ., ., c] sx[l][c], which are stored per output channel as
+# e4m3(W' / sw[l][o]) with sw = max |W'[o]| / 448; a layer computes
+# y[o] = sw[o] * sum(qW * qx) + b[o] in FP32, then ReLU and the next layer's
+# quantisation.
+E4M3_MAX = 448.0
+
+
+def round_e4m3(x):
+    """float64 -> nearest e4m3 value (ties to even), saturating at +-448."""
+    x = np.asarray(x, np.float64)
+    a = np.minimum(np.abs(x), E4M3_MAX)
+    e = np.floor(np.log2(np.maximum(a, 2.0 ** -9)))
+    e = np.maximum(e, -6.0)              # subnormals below 2^-6: spacing 2^-9
+    step = 2.0 ** (e - 3)                # 3 mantissa bits
+    q = a / step
+    r = np.floor(q)
+    frac = q - r
+    r = np.where((frac > 0.5) | ((frac == 0.5) & (np.mod(r, 2) == 1)), r + 1, r)
+    v = np.minimum(r * step, E4M3_MAX)
+    return np.sign(x) * np.where(a == 0, 0.0, v)
+
+
+def activation_maxima(x, W, b):
+    """Per-layer, per-channel largest |input| of the BF16 network (the
+    calibration statistic), shape (6, 32); unused channels 0."""
+    _, acts = forward(x, W, b, bf16=True)
+    amax = np.zeros((6, 32))
+    for l in range(6):
+        a = np.abs(acts[l]).reshape(acts[l].shape[0], -1).max(1)
+        amax[l, :a.size] = a
+    return amax
+
+
+def fp8_scales(amax, W):
+    """Activation scales sx (6, 32) and output-channel weight scales sw (6, 32)."""
+    sx = np.maximum(amax, 1e-30) / E4M3_MAX
+    sw = np.zeros((6, 32))
+    for l in range(6):
+        ci, co = CHANNELS[l], CHANNELS[l + 1]
+        Wf = W[l] * sx[l, :ci][None, None, None, :]
+        m = np.abs(Wf).reshape(co, -1).max(1)
+        sw[l, :co] = np.maximum(m, 1e-30) / E4M3_MAX
+    return sx, sw
+
+
+def forward_fp8(x, W, b, sx, sw):
+    """FP8 network forward; returns out (4, H, W) (float64, exact sums)."""
+    h = round_e4m3(x / sx[0, :6][:, None, None])
+    for l in range(6):
+        ci, co = CHANNELS[l], CHANNELS[l + 1]
+        Wf = W[l] * sx[l, :ci][None, None, None, :]
+        qW = round_e4m3(Wf / sw[l, :co][:, None, None, None])
+        y = conv3x3(h, qW, np.zeros(co)) * sw[l, :co][:, None, None] + b[l][:, None, None]
+        if l < 5:
+            h = round_e4m3(np.maximum(y, 0.0) / sx[l + 1, :co][:, None, None])
+        else:
+            return y
+    raise AssertionError

@@ -140,3 +140,34 @@ def test_features():
     assert f[3, 1, 1] == 0.5 and f[3, 0, 0] == 0.0 and f[3, 2, 3] == 0.0
     assert np.all(f[:3] == 0.25) and f[4, 2, 3] == 1.0
     assert abs(f[5, 2, 5] - 2.0 / 8.0) < 1e-15 and abs(f[5, 0, 0] - np.hypot(2, 3) / 8) < 1e-15
+
+
+def test_e4m3_rounding_matches_torch():
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8 in this torch")
+    rng = np.random.default_rng(31)
+    x = np.concatenate([rng.normal(size=4000) * 10.0 ** rng.uniform(-3, 2.5, 4000),
+                        [0.0, 2.0 ** -9, 2.0 ** -10, 3 * 2.0 ** -10, 1.0625, 1.1875, 448.0, -448.0]])
+    x = x[np.abs(x) <= 448.0]  # beyond the range torch gives no finite code
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(R.round_e4m3(x), ref)
+    # saturation at the largest finite code
+    assert R.round_e4m3(1000.0) == 448.0 and R.round_e4m3(-470.0) == -448.0
+
+
+def test_fp8_network_with_exact_codes_is_the_fp64_network():
+    # weights and inputs that are exact e4m3 codes at unit scales and an exact
+    # network: the FP8 path reproduces the float64 one
+    W = [np.zeros((R.CHANNELS[l + 1], 3, 3, R.CHANNELS[l])) for l in range(6)]
+    b = [np.zeros(R.CHANNELS[l + 1]) for l in range(6)]
+    for l in range(6):
+        W[l][0, 1, 1, 0] = 1.0
+        W[l][1, 0, 1, 0] = 0.5
+    x = np.zeros((6, 8, 8))
+    x[0] = np.random.default_rng(32).integers(0, 8, (8, 8)) * 0.25
+    sx = np.ones((6, 32))
+    sw = np.full((6, 32), 1.0 / 448.0 * 448.0)  # unit weight scales
+    out8 = R.forward_fp8(x, W, b, sx, sw)
+    out, _ = R.forward(x, W, b)
+    np.testing.assert_array_equal(out8, out)
