@@ -198,9 +198,23 @@ gs_status gs_repair_features(gs_context *ctx, int width, int height, uint16_t *f
  * feat: device [frames][H][W][8] bf16; tiles: device uint32 entries
  * frame << 24 | tile_y << 12 | tile_x (16x16 tiles); fill: device
  * [frames][3][H][W] (written inside the listed tiles; may be NULL); gate: device
- * float[n_tiles], the mean gate logit of each listed tile. */
+ * float[n_tiles], the mean gate logit of each listed tile. fp8 = 1 runs the
+ * e4m3 network (needs gs_repair_calibrate_fp8). */
 gs_status gs_repair_infer(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,
-                          const uint32_t *tiles, int n_tiles, float *fill, float *gate);
+                          const uint32_t *tiles, int n_tiles, float *fill, float *gate, int fp8);
+
+/* FP8 (e4m3) network, FP32 accumulation with per-channel scales. Calibration
+ * runs the BF16 network over the listed tiles and records, per layer and input
+ * channel, the largest |input|; the input scale sx = max / 448 (the largest
+ * finite e4m3 value) is folded into the weights W' = W * sx, which are stored
+ * per output channel as e4m3(W' / sw) with sw = max |W'| / 448. A layer computes
+ * y = sw * sum(codes) + b in FP32, then ReLU and the next layer's e4m3 input.
+ * Needed by gs_repair_infer(fp8 = 1) and gs_render_stereo(repair_mode = 2);
+ * loading weights or a training step with lr > 0 invalidates it. */
+gs_status gs_repair_calibrate_fp8(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,
+                                  const uint32_t *tiles, int n_tiles);
+/* The calibrated scales: out (host float[384]) = sx[6][32] then sw[6][32]. */
+gs_status gs_repair_read_fp8_scales(gs_context *ctx, float *out);
 
 /* One training step on listed tiles: forward (keeping activations), loss, FP32
  * gradients, and an AdamW update of the FP32 parameters when lr > 0 (lr = 0

@@ -92,6 +92,10 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.rp_v = c.take<float>(kRepairParams);
   ws.rp_wpack = c.take<uint8_t>(92160);
   ws.rp_bias = c.take<float>(6 * 32);
+  ws.rp_wpack8 = c.take<uint8_t>(50688);
+  ws.rp_sx = c.take<float>(6 * 32);
+  ws.rp_sw = c.take<float>(6 * 32);
+  ws.rp_amax = c.take<uint32_t>(6 * 32);
   ws.rp_feat = c.take<uint4>(P);
   ws.rp_fill = c.take<float>(3 * P);
   ws.rp_gate = c.take<float>(tiles);
@@ -182,6 +186,7 @@ struct gs_context {
   cudaStream_t cap_stream;
   GraphSlot graphs[3];  // mono, stereo, two-pass
   int rp_loaded;        // repair network weights present
+  int rp_fp8;           // FP8 scales and weights calibrated for the current weights
   int rp_step;          // AdamW steps taken
 };
 
@@ -582,7 +587,7 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     return GS_ERR_BAD_ARG;
   if (roi->repair_mode < 0 || roi->repair_mode > 3 || !(roi->gate_tau > 0.f && roi->gate_tau < 1.f))
     return GS_ERR_BAD_ARG;
-  if (roi->repair_mode == 2 || (roi->repair_mode == 1 && !ctx->rp_loaded)) return GS_ERR_NOT_LOADED;
+  if ((roi->repair_mode == 1 && !ctx->rp_loaded) || (roi->repair_mode == 2 && !ctx->rp_fp8)) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
   const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
   const PoseArgs pa = pose_args(pose_dom, pose_aff, intr);
@@ -615,8 +620,9 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     }
     // learned repair: tiles with holes whose gate passes take the network fill
     // and leave the ROI tile mask
-    if (roi->repair_mode == 1) {
-      if ((e = repair_stereo(ctx->ws, W, H, roi->gate_tau, out->rgb_aff, ctx->stream)) != cudaSuccess)
+    if (roi->repair_mode == 1 || roi->repair_mode == 2) {
+      if ((e = repair_stereo(ctx->ws, W, H, roi->gate_tau, out->rgb_aff, ctx->stream, roi->repair_mode == 2)) !=
+          cudaSuccess)
         return cuda_fail(e);
     }
     mark(ctx, 5);
@@ -722,6 +728,7 @@ gs_status gs_repair_load(gs_context *ctx, const float *weights, int64_t count) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host array may go away after the call
   if (e != cudaSuccess) return cuda_fail(e);
   ctx->rp_loaded = 1;
+  ctx->rp_fp8 = 0;  // the FP8 image belongs to the previous weights
   ctx->rp_step = 0;
   return GS_OK;
 }
@@ -744,13 +751,36 @@ gs_status gs_repair_features(gs_context *ctx, int width, int height, uint16_t *f
 }
 
 gs_status gs_repair_infer(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,
-                          const uint32_t *tiles, int n_tiles, float *fill, float *gate) {
+                          const uint32_t *tiles, int n_tiles, float *fill, float *gate, int fp8) {
   if (!ctx || !feat || !tiles || !gate || frames <= 0 || frames > 255 || width <= 0 || height <= 0 ||
-      width > 4095 * 16 || height > 4095 * 16 || n_tiles < 0 || ((uintptr_t)feat & 15))
+      width > 4095 * 16 || height > 4095 * 16 || n_tiles < 0 || ((uintptr_t)feat & 15) || (fp8 != 0 && fp8 != 1))
+    return GS_ERR_BAD_ARG;
+  if (!ctx->rp_loaded || (fp8 && !ctx->rp_fp8)) return GS_ERR_NOT_LOADED;
+  return cuda_status(repair_forward(ctx->ws, (const uint4 *)feat, width, height, tiles, nullptr, (uint32_t)n_tiles,
+                                    fill, gate, nullptr, nullptr, ctx->stream, fp8 != 0, nullptr));
+}
+
+gs_status gs_repair_calibrate_fp8(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,
+                                  const uint32_t *tiles, int n_tiles) {
+  if (!ctx || !feat || !tiles || frames <= 0 || frames > 255 || width <= 0 || height <= 0 || width > 4095 * 16 ||
+      height > 4095 * 16 || n_tiles <= 0 || ((uintptr_t)feat & 15) || (int64_t)n_tiles > 3 * ctx->ws.max_pixels)
     return GS_ERR_BAD_ARG;
   if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
-  return cuda_status(repair_forward(ctx->ws, (const uint4 *)feat, width, height, tiles, nullptr, (uint32_t)n_tiles,
-                                    fill, gate, nullptr, nullptr, ctx->stream));
+  cudaError_t e = repair_calibrate_fp8(ctx->ws, (const uint4 *)feat, width, height, tiles, (uint32_t)n_tiles,
+                                       ctx->ws.rp_fill, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  ctx->rp_fp8 = 1;
+  return GS_OK;
+}
+
+gs_status gs_repair_read_fp8_scales(gs_context *ctx, float *out) {
+  if (!ctx || !out) return GS_ERR_BAD_ARG;
+  if (!ctx->rp_fp8) return GS_ERR_NOT_LOADED;
+  cudaError_t e = cudaMemcpyAsync(out, ctx->ws.rp_sx, sizeof(float) * 6 * 32, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out + 6 * 32, ctx->ws.rp_sw, sizeof(float) * 6 * 32, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  return cuda_status(e);
 }
 
 gs_status gs_repair_train_scratch_size(int n_tiles, size_t *bytes) {
@@ -766,7 +796,10 @@ gs_status gs_repair_train_step(gs_context *ctx, const gs_repair_batch *b, const 
     return GS_ERR_BAD_ARG;
   if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
   RepairBatch rb{(const uint4 *)b->feat, b->target, b->plain, b->width, b->height, b->tiles, b->n_tiles, b->scratch};
-  if (opt->lr > 0.f) ++ctx->rp_step;
+  if (opt->lr > 0.f) {
+    ++ctx->rp_step;
+    ctx->rp_fp8 = 0;  // the weights change; the FP8 image needs a new calibration
+  }
   RepairOpt ro{opt->lr, opt->beta1, opt->beta2, opt->eps, opt->weight_decay, opt->gate_weight,
                ctx->rp_step > 0 ? ctx->rp_step : 1};
   return cuda_status(repair_train_step(ctx->ws, rb, ro, loss, ctx->stream));

@@ -116,6 +116,9 @@ struct Workspace {
   // learned repair network
   float *rp_master, *rp_grad, *rp_m, *rp_v;  // FP32 parameters, gradients, AdamW moments
   uint8_t *rp_wpack;            // BF16 B-operand images of the six layers
+  uint8_t *rp_wpack8;           // FP8 (e4m3) B-operand images
+  float *rp_sx, *rp_sw;         // FP8 input scales and output-channel weight scales, [6][32] each
+  uint32_t *rp_amax;            // calibration maxima of the layer inputs [6][32]
   float *rp_bias;               // [6][32]
   uint4 *rp_feat;               // [pixels] 8 x bf16 features of the affiliated eye
   float *rp_fill;               // [3][pixels] network fill
@@ -192,10 +195,15 @@ cudaError_t repair_pack(const Workspace &ws, cudaStream_t s);
 cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_aff, uint4 *feat, cudaStream_t s);
 cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
                            const uint32_t *n_ptr, uint32_t n_max, float *fill, float *gate, float *out4,
-                           uint4 *acts, cudaStream_t s);
+                           uint4 *acts, cudaStream_t s, bool fp8 = false, uint32_t *amax = nullptr);
+// FP8 scales from the BF16 network's activation maxima over the listed tiles,
+// then the e4m3 weight images.
+cudaError_t repair_calibrate_fp8(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
+                                 uint32_t n_tiles, float *gate_scratch, cudaStream_t s);
 // Tile list, network and gated merge for the affiliated eye of the last warp
 // (features already in ws.rp_feat); gated tiles leave ws.tile_mask.
-cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s);
+cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s,
+                          bool fp8 = false);
 cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const RepairOpt &o, float *host_loss,
                               cudaStream_t s);
 

@@ -25,6 +25,7 @@
 // loss kernel, data-parallel FP32 weight- and input-gradient kernels and AdamW
 // on FP32 master weights.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "gs_internal.cuh"
 #include "gs_scan.cuh"
@@ -36,7 +37,7 @@ namespace {
 constexpr int kRT = 16;                 // output tile edge
 constexpr int kHalo = 6;                // receptive-field radius of six 3x3 layers
 constexpr int kGW = kRT + 2 * kHalo;    // 28: width of the position grid
-constexpr int kNPos = 960;              // positions per activation buffer (7 M tiles + tap reach)
+constexpr int kNPos = 832;              // positions per activation buffer (6 M tiles + tap reach)
 constexpr int kQ = 26 * kGW;            // gradient grid: rows < 26 of any layer >= 1 output
 constexpr int kNetThreads = 128;
 constexpr int kTmemCols = 256;
@@ -61,10 +62,24 @@ __host__ __device__ constexpr int mtiles(int l) { return ((kGW - 2 * (l + 1)) * 
 constexpr int kMaxMT = 6;  // M tiles of the widest layer
 constexpr int kWPackBytes = woff(6);
 static_assert(kWPackBytes == 92160, "packed weight image size");
+// FP8 images: [tap][2 c_in groups of 16][c_out groups][8][16 B]
+__host__ __device__ constexpr int wbytes8(int l) { return 9 * 2 * ngroups(l) * 128; }
+__host__ __device__ constexpr int woff8(int l) {
+  int o = 0;
+  for (int i = 0; i < l; ++i) o += wbytes8(i);
+  return o;
+}
+constexpr int kWPack8Bytes = woff8(6);
+static_assert(kWPack8Bytes == 50688, "packed FP8 weight image size");
 static_assert(poff(6) == kRepairParams, "parameter count");
-constexpr int kBufBytes = 4 * kNPos * 16;
-constexpr size_t kNetSmem = 1024 + 2 * (size_t)kBufBytes + kWPackBytes + 6 * 32 * 4 + 8 * kMaxMT + 64;
 static_assert(mtiles(0) <= kMaxMT, "M tiles per layer");
+static_assert(kMaxMT * 128 + 2 * kGW + 2 <= kNPos, "activation buffer reach");
+// shared memory of the network kernel: two activation buffers, the weight image,
+// bias, FP8 scales, barriers, reductions and calibration maxima
+__host__ __device__ constexpr size_t net_smem(bool fp8) {
+  return 128 + 2 * (size_t)((fp8 ? 2 : 4) * kNPos * 16) + (fp8 ? kWPack8Bytes : kWPackBytes) + 3 * 6 * 32 * 4 +
+         8 * kMaxMT + 4 + 8 * 4 + 6 * 32 * 4 + 64;
+}
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -144,37 +159,63 @@ struct NetArgs {
   const uint32_t *tiles;     // frame << 24 | ty << 12 | tx
   const uint32_t *n_tiles;   // device count, or null for n_max
   uint32_t n_max;
-  const uint16_t *wpack;
-  const float *bias;
+  const uint8_t *wpack;      // BF16 or FP8 B-operand images
+  const float *bias;         // [6][32]
+  const float *sx;           // FP8: [6][32] input scales of every layer
+  const float *sw;           // FP8: [6][32] output-channel weight scales
   float *fill;               // [frames][3][H][W], or null
   float *gate;               // [n] mean gate logit per listed tile
   float *out4;               // training: [n][4][16][16] raw outputs, or null
   uint4 *acts;               // training: [n][6 layer inputs][4 groups][kNPos] (16 B each), or null
+  uint32_t *amax;            // calibration: [6][32] largest |layer input| (float bits), or null
   uint32_t *status;
 };
 
+__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
+  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+  return (lo & 0xffffu) | (hi << 16);
+}
+
+template <bool FP8>
 __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
+  // BF16: 8 channels per 16-byte group, 4 groups, K = 16 per MMA (two per tap);
+  // FP8: 16 channels per group, 2 groups, K = 32 per MMA (one per tap)
+  constexpr int kChPerGroup = FP8 ? 16 : 8;
+  constexpr int kGroups = 32 / kChPerGroup;
+  constexpr int kBuf = kGroups * kNPos * 16;
+  constexpr int kWBytes = FP8 ? kWPack8Bytes : kWPackBytes;
   extern __shared__ uint8_t s_raw[];
-  uint8_t *smem = (uint8_t *)(((uintptr_t)s_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t *smem = (uint8_t *)(((uintptr_t)s_raw + 127) & ~(uintptr_t)127);
   uint8_t *bufA = smem;
-  uint8_t *bufB = smem + kBufBytes;
-  uint8_t *wsm = smem + 2 * kBufBytes;
-  float *s_bias = (float *)(wsm + kWPackBytes);
-  uint64_t *mbar = (uint64_t *)(s_bias + 6 * 32);  // one per M tile of a layer
+  uint8_t *bufB = smem + kBuf;
+  uint8_t *wsm = smem + 2 * kBuf;
+  float *s_bias = (float *)(wsm + kWBytes);
+  float *s_sw = s_bias + 6 * 32;        // FP8: weight scales
+  float *s_isx = s_sw + 6 * 32;         // FP8: reciprocal input scales
+  uint64_t *mbar = (uint64_t *)(s_isx + 6 * 32);  // one per M tile of a layer
   uint32_t *s_taddr = (uint32_t *)(mbar + kMaxMT);
-  float *s_red = (float *)(s_taddr + 1);  // [4 warps][2]
+  float *s_red = (float *)(s_taddr + 1);          // [4 warps][2]
+  uint32_t *s_amax = (uint32_t *)(s_red + 8);     // [6][32] calibration maxima
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t n = load_n(a.n_tiles, a.n_max);
   if (blockIdx.x >= n) return;
 
-  // one-time set-up: weights, biases, cleared activation buffers, barrier, TMEM
+  // one-time set-up: weights, scales, cleared activation buffers, barriers, TMEM
   {
     const uint4 *src = (const uint4 *)a.wpack;
     uint4 *dst = (uint4 *)wsm;
-    for (int i = tid; i < kWPackBytes / 16; i += kNetThreads) dst[i] = src[i];
-    for (int i = tid; i < 6 * 32; i += kNetThreads) s_bias[i] = a.bias[i];
+    for (int i = tid; i < kWBytes / 16; i += kNetThreads) dst[i] = src[i];
+    for (int i = tid; i < 6 * 32; i += kNetThreads) {
+      s_bias[i] = a.bias[i];
+      if (FP8) {
+        s_sw[i] = a.sw[i];
+        s_isx[i] = 1.f / a.sx[i];
+      }
+      s_amax[i] = 0u;
+    }
     uint4 *z = (uint4 *)smem;
-    for (int i = tid; i < 2 * kBufBytes / 16; i += kNetThreads) z[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < 2 * kBuf / 16; i += kNetThreads) z[i] = make_uint4(0, 0, 0, 0);
     if (tid < kMaxMT) umma::mbar_init(mbar + tid, 1);
     if (wid == 0) {
       umma::tmem_alloc(s_taddr, kTmemCols);
@@ -193,16 +234,25 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
     const uint32_t te = a.tiles[t];
     const int frame = (int)(te >> 24), ty0 = (int)((te >> 12) & 0xfffu) * kRT, tx0 = (int)(te & 0xfffu) * kRT;
     const uint4 *fin = a.feat + (size_t)frame * a.W * a.H;
-    // layer-1 input: the 28x28 feature window (zeros outside the image), channel
-    // groups 0 (the 6 features + 2 zeros) and 1 (zeros: K padded to 16)
+    // layer-1 input: the 28x28 feature window (zeros outside the image); the
+    // 6 features + zeros fill channel group 0, the other groups are zero (K padding)
     for (int q = tid; q < kNPos; q += kNetThreads) {
       uint4 v = make_uint4(0, 0, 0, 0);
       if (q < kGW * kGW) {
         const int y = ty0 - kHalo + q / kGW, x = tx0 - kHalo + q % kGW;
         if (y >= 0 && y < a.H && x >= 0 && x < a.W) v = fin[(size_t)y * a.W + x];
       }
+      if (a.amax) {
+        const float f[6] = {bf16_lo(v.x), bf16_hi(v.x), bf16_lo(v.y), bf16_hi(v.y), bf16_lo(v.z), bf16_hi(v.z)};
+        for (int c = 0; c < 6; ++c) atomicMax(&s_amax[c], __float_as_uint(fabsf(f[c])));
+      }
+      if (FP8) {
+        const float *is = s_isx;  // layer-0 input scales
+        v = make_uint4(e4m3x4(bf16_lo(v.x) * is[0], bf16_hi(v.x) * is[1], bf16_lo(v.y) * is[2], bf16_hi(v.y) * is[3]),
+                       e4m3x4(bf16_lo(v.z) * is[4], bf16_hi(v.z) * is[5], 0.f, 0.f), 0u, 0u);
+      }
       ((uint4 *)bufA)[q] = v;
-      ((uint4 *)bufA)[kNPos + q] = make_uint4(0, 0, 0, 0);
+      for (int g = 1; g < kGroups; ++g) ((uint4 *)bufA)[g * kNPos + q] = make_uint4(0, 0, 0, 0);
     }
     float gsum = 0.f, gcnt = 0.f;
 #pragma unroll 1
@@ -210,14 +260,15 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
       uint8_t *in = (l & 1) ? bufB : bufA;
       uint8_t *out = (l & 1) ? bufA : bufB;
       const uint32_t sin = (l & 1) ? sB : sA;
-      const int kg = kgroups(l), ng = ngroups(l), N = ng * 8, MT = mtiles(l);
+      const int ng = ngroups(l), N = ng * 8, MT = mtiles(l);
+      const int kg = FP8 ? 2 : kgroups(l);  // 16-byte K groups of this layer's input
       // this layer's input (written by all threads) is complete and visible to
       // the tensor core
       umma::fence_proxy_async();
       umma::fence_before_sync();
       __syncthreads();
       umma::fence_after_sync();
-      if (a.acts) {  // training: keep this layer's input (read beside the MMAs)
+      if (!FP8 && a.acts) {  // training: keep this layer's input (read beside the MMAs)
         uint4 *dst = a.acts + ((size_t)t * 6 + l) * 4 * kNPos;
         const uint4 *srcb = (const uint4 *)in;
         for (int i = tid; i < kg * kNPos; i += kNetThreads) dst[i] = srcb[i];
@@ -225,23 +276,24 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
       // one thread issues every MMA of the layer, committing each M tile to its
       // own barrier, so the epilogue of tile mt overlaps the MMAs of mt + 1
       if (tid == 0) {
-        const uint32_t idesc = umma::idesc_bf16(128, N);
-        const uint32_t wl = sW + (uint32_t)woff(l);
+        const uint32_t idesc = FP8 ? umma::idesc_e4m3(128, N) : umma::idesc_bf16(128, N);
+        const uint32_t wl = sW + (uint32_t)(FP8 ? woff8(l) : woff(l));
         for (int mt = 0; mt < MT; ++mt) {
           for (int tap = 0; tap < 9; ++tap) {
             const int shift = (tap / 3) * kGW + (tap % 3);
-            for (int kp = 0; kp < kg / 2; ++kp) {
+            for (int kp = 0; kp < kg / 2; ++kp) {  // two 16-byte groups per MMA
               const uint64_t ad =
                   umma::desc(sin + (uint32_t)(((2 * kp) * kNPos + mt * 128 + shift) * 16), kNPos * 16, 128);
               const uint64_t bd = umma::desc(wl + (uint32_t)((tap * kg + 2 * kp) * ng * 128), ng * 128, 128);
-              umma::mma_bf16(taddr + (uint32_t)(mt * N), ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
+              if (FP8) umma::mma_e4m3(taddr + (uint32_t)(mt * N), ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
+              else umma::mma_bf16(taddr + (uint32_t)(mt * N), ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
             }
           }
           umma::mma_commit(mbar + mt);
         }
       }
       __syncwarp();
-      // epilogue: accumulator rows -> bias, ReLU, border zeroing -> next buffer
+      // epilogue: accumulator rows -> scale, bias, ReLU, border zeroing -> next buffer
       const int shiftL = l + 1;  // this layer's output grid starts (l + 1) pixels in
       bool layer_ok = true;
       for (int mt = 0; mt < MT; ++mt) {
@@ -258,6 +310,8 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
         const int y = ty0 - kHalo + shiftL + r, x = tx0 - kHalo + shiftL + c;
         const bool inside = y >= 0 && y < a.H && x >= 0 && x < a.W;
         const uint32_t tl = taddr + ((uint32_t)(wid * 32) << 16) + (uint32_t)(mt * N);
+        const float *bl = s_bias + l * 32;
+        const float *swl = s_sw + l * 32;
         if (l < 5) {
           float v[32];
           float h[16];
@@ -267,24 +321,49 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
           umma::tmem_ld16(tl + 16, h);
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[16 + i] = h[i];
-          const float *bl = s_bias + l * 32;
 #pragma unroll
-          for (int g = 0; g < 4; ++g) {
-            uint32_t w4[4];
+          for (int i = 0; i < 32; ++i) {
+            const float yv = FP8 ? fmaf(v[i], swl[i], bl[i]) : v[i] + bl[i];
+            v[i] = inside ? fmaxf(yv, 0.f) : 0.f;
+          }
+          if (FP8) {
+            const float *is = s_isx + (l + 1) * 32;  // next layer's input scales
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const float u0 = inside ? fmaxf(v[g * 8 + 2 * j] + bl[g * 8 + 2 * j], 0.f) : 0.f;
-              const float u1 = inside ? fmaxf(v[g * 8 + 2 * j + 1] + bl[g * 8 + 2 * j + 1], 0.f) : 0.f;
-              w4[j] = pack_bf16(u0, u1);
+            for (int g = 0; g < 2; ++g) {
+              const int o = g * 16;
+              ((uint4 *)out)[g * kNPos + q] =
+                  make_uint4(e4m3x4(v[o] * is[o], v[o + 1] * is[o + 1], v[o + 2] * is[o + 2], v[o + 3] * is[o + 3]),
+                             e4m3x4(v[o + 4] * is[o + 4], v[o + 5] * is[o + 5], v[o + 6] * is[o + 6],
+                                    v[o + 7] * is[o + 7]),
+                             e4m3x4(v[o + 8] * is[o + 8], v[o + 9] * is[o + 9], v[o + 10] * is[o + 10],
+                                    v[o + 11] * is[o + 11]),
+                             e4m3x4(v[o + 12] * is[o + 12], v[o + 13] * is[o + 13], v[o + 14] * is[o + 14],
+                                    v[o + 15] * is[o + 15]));
             }
-            ((uint4 *)out)[g * kNPos + q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+          } else {
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+              uint32_t w4[4];
+#pragma unroll
+              for (int j = 0; j < 4; ++j) w4[j] = pack_bf16(v[g * 8 + 2 * j], v[g * 8 + 2 * j + 1]);
+              ((uint4 *)out)[g * kNPos + q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+              if (a.amax && inside && r < kGW - 2 * (l + 1) && c < kGW - 2 * (l + 1)) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  atomicMax(&s_amax[(l + 1) * 32 + g * 8 + 2 * j], w4[j] << 16);
+                  atomicMax(&s_amax[(l + 1) * 32 + g * 8 + 2 * j + 1], w4[j] & 0xffff0000u);
+                }
+              }
+            }
           }
         } else {
           float v[16];
           umma::tmem_ld16(tl, v);
           if (r < kRT && c < kRT) {
-            const float o0 = v[0] + s_bias[160], o1 = v[1] + s_bias[161], o2 = v[2] + s_bias[162],
-                        o3 = v[3] + s_bias[163];
+            const float o0 = FP8 ? fmaf(v[0], swl[0], bl[0]) : v[0] + bl[0];
+            const float o1 = FP8 ? fmaf(v[1], swl[1], bl[1]) : v[1] + bl[1];
+            const float o2 = FP8 ? fmaf(v[2], swl[2], bl[2]) : v[2] + bl[2];
+            const float o3 = FP8 ? fmaf(v[3], swl[3], bl[3]) : v[3] + bl[3];
             if (a.out4) {
               float *o = a.out4 + (size_t)t * 4 * kRT * kRT + r * kRT + c;
               o[0] = o0;
@@ -327,20 +406,64 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
     }
     __syncthreads();
     if (tid == 0) {
-      const float s = s_red[0] + s_red[2] + s_red[4] + s_red[6];
-      const float c = s_red[1] + s_red[3] + s_red[5] + s_red[7];
-      a.gate[t] = c > 0.f ? s / c : 0.f;
+      const float sm = s_red[0] + s_red[2] + s_red[4] + s_red[6];
+      const float cn = s_red[1] + s_red[3] + s_red[5] + s_red[7];
+      a.gate[t] = cn > 0.f ? sm / cn : 0.f;
     }
     __syncthreads();
   }
   umma::fence_before_sync();
   __syncthreads();
+  if (a.amax)
+    for (int i = tid; i < 6 * 32; i += kNetThreads) atomicMax(&a.amax[i], s_amax[i]);
   if (failed) {
     // MMA batches may still be in flight: give each barrier a bounded chance to
     // complete before the accumulator columns are released
     for (int mt = 0; mt < kMaxMT; ++mt) umma::mbar_wait(mbar + mt, (phases >> mt) & 1u, 1u << 18);
   }
   if (wid == 0) umma::tmem_dealloc(taddr, kTmemCols);
+}
+
+// FP8 weights: W' = W * sx (input scales folded in), per output channel
+// sw = max |W'| / 448 and codes e4m3(W' / sw) in the B-operand image
+// [tap][c_in group of 16][c_out group][8 c_out][16 c_in]. One block per (layer,
+// output channel); scales of the layer inputs come from the calibration maxima.
+__global__ void __launch_bounds__(256) repair_pack8_kernel(const float *__restrict__ master,
+                                                           const uint32_t *__restrict__ amax,
+                                                           uint8_t *__restrict__ wpack8, float *__restrict__ sx,
+                                                           float *__restrict__ sw) {
+  __shared__ float s_max[8];
+  const int l = blockIdx.x / 32, co = blockIdx.x % 32;
+  const int ci_n = cin(l), ng = ngroups(l);
+  if (threadIdx.x < 32 && co == 0) sx[l * 32 + threadIdx.x] = fmaxf(__uint_as_float(amax[l * 32 + threadIdx.x]), 1e-30f) / 448.f;
+  float m = 0.f;
+  if (co < cout(l))
+    for (int i = threadIdx.x; i < 9 * ci_n; i += blockDim.x) {
+      const int ci = i % ci_n;
+      const float s = fmaxf(__uint_as_float(amax[l * 32 + ci]), 1e-30f) / 448.f;
+      m = fmaxf(m, fabsf(master[poff(l) + co * 9 * ci_n + i] * s));
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = m;
+  __syncthreads();
+  float wmax = 0.f;
+  for (int i = 0; i < 8; ++i) wmax = fmaxf(wmax, s_max[i]);
+  const float s_w = fmaxf(wmax, 1e-30f) / 448.f;
+  if (threadIdx.x == 0) sw[l * 32 + co] = co < cout(l) ? s_w : 1.f;
+  if (co >= ng * 8) return;  // beyond the padded output channels
+  // this output channel's 9 x 32 codes (zero for padded input channels)
+  for (int i = threadIdx.x; i < 9 * 32; i += blockDim.x) {
+    const int tap = i / 32, ci = i % 32;
+    float v = 0.f;
+    if (co < cout(l) && ci < ci_n) {
+      const float s = fmaxf(__uint_as_float(amax[l * 32 + ci]), 1e-30f) / 448.f;
+      v = master[poff(l) + (co * 9 + tap) * ci_n + ci] * s / s_w;
+    }
+    const int kgi = ci / 16, ngi = co / 8;
+    const size_t byte = (size_t)woff8(l) + ((size_t)((tap * 2 + kgi) * ng + ngi) * 8 + (co % 8)) * 16 + (ci % 16);
+    wpack8[byte] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  }
 }
 
 // ---------------------------------------------------------------- inference wiring
@@ -586,7 +709,12 @@ size_t repair_train_scratch_bytes(int n_tiles) {
 }
 
 cudaError_t prepare_repair() {
-  return cudaFuncSetAttribute(repair_net_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNetSmem);
+  cudaError_t e = cudaFuncSetAttribute(repair_net_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)net_smem(false));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(repair_net_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)net_smem(true));
+  return e;
 }
 
 cudaError_t repair_pack(const Workspace &ws, cudaStream_t s) {
@@ -607,7 +735,7 @@ static int net_grid(uint32_t n_max) { return (int)(n_max < 152u ? (n_max < 1u ? 
 
 cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
                            const uint32_t *n_ptr, uint32_t n_max, float *fill, float *gate, float *out4,
-                           uint4 *acts, cudaStream_t s) {
+                           uint4 *acts, cudaStream_t s, bool fp8, uint32_t *amax) {
   if (n_max == 0) return cudaSuccess;
   NetArgs a;
   a.feat = feat;
@@ -616,19 +744,41 @@ cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H,
   a.tiles = tiles;
   a.n_tiles = n_ptr;
   a.n_max = n_max;
-  a.wpack = (const uint16_t *)ws.rp_wpack;
+  a.wpack = fp8 ? ws.rp_wpack8 : ws.rp_wpack;
   a.bias = ws.rp_bias;
+  a.sx = ws.rp_sx;
+  a.sw = ws.rp_sw;
   a.fill = fill;
   a.gate = gate;
   a.out4 = out4;
   a.acts = acts;
+  a.amax = amax;
   a.status = &ws.ctr->status;
-  repair_net_kernel<<<net_grid(n_max), kNetThreads, kNetSmem, s>>>(a);
+  if (fp8) {  // two CTAs per SM fit the FP8 kernel's shared memory
+    const uint32_t g = n_max < 304u ? (n_max < 1u ? 1u : n_max) : 304u;
+    repair_net_kernel<true><<<g, kNetThreads, net_smem(true), s>>>(a);
+  } else {
+    repair_net_kernel<false><<<net_grid(n_max), kNetThreads, net_smem(false), s>>>(a);
+  }
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }
 
-cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s) {
+cudaError_t repair_calibrate_fp8(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
+                                 uint32_t n_tiles, float *gate_scratch, cudaStream_t s) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ws.rp_amax, 0, 6 * 32 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+  if ((e = repair_forward(ws, feat, W, H, tiles, nullptr, n_tiles, nullptr, gate_scratch, nullptr, nullptr, s, false,
+                          ws.rp_amax)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(ws.rp_wpack8, 0, kWPack8Bytes, s)) != cudaSuccess) return e;
+  repair_pack8_kernel<<<6 * 32, 256, 0, s>>>(ws.rp_master, ws.rp_amax, ws.rp_wpack8, ws.rp_sx, ws.rp_sw);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s,
+                          bool fp8) {
   cudaError_t e;
   const int tx = (W + kRT - 1) / kRT, ty = (H + kRT - 1) / kRT, nt = tx * ty;
   repair_tile_flags_kernel<<<dim3(tx, ty), 256, 0, s>>>(ws.cls, ws.tile_mask, W, H, ws.rp_flags);
@@ -638,7 +788,7 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
       cudaSuccess)
     return e;
   if ((e = repair_forward(ws, ws.rp_feat, W, H, ws.rp_list, ws.rp_nlist, (uint32_t)nt, ws.rp_fill, ws.rp_gate,
-                          nullptr, nullptr, s)) != cudaSuccess)
+                          nullptr, nullptr, s, fp8, nullptr)) != cudaSuccess)
     return e;
   // sigmoid(g) >= tau  <=>  g >= log(tau / (1 - tau))
   const float tau = fminf(fmaxf(gate_tau, 1e-6f), 1.f - 1e-6f);
@@ -669,8 +819,8 @@ cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const R
   float *sums = (float *)p;
   if ((e = cudaMemsetAsync(sums, 0, 8 * sizeof(float), s)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(ws.rp_grad, 0, kRepairParams * sizeof(float), s)) != cudaSuccess) return e;
-  if ((e = repair_forward(ws, b.feat, b.W, b.H, b.tiles, nullptr, (uint32_t)n, nullptr, gate, out4, acts, s)) !=
-      cudaSuccess)
+  if ((e = repair_forward(ws, b.feat, b.W, b.H, b.tiles, nullptr, (uint32_t)n, nullptr, gate, out4, acts, s, false,
+                          nullptr)) != cudaSuccess)
     return e;
   TrainArgs a;
   a.feat = b.feat;

@@ -100,7 +100,9 @@ EXPORTS = {
     "gs_repair_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "gs_repair_features": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "gs_repair_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
-                                  C.c_void_p, C.c_void_p]),
+                                  C.c_void_p, C.c_void_p, C.c_int]),
+    "gs_repair_calibrate_fp8": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    "gs_repair_read_fp8_scales": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gs_repair_train_scratch_size": (C.c_int, [C.c_int, C.POINTER(C.c_size_t)]),
     "gs_repair_train_step": (C.c_int, [C.c_void_p, C.POINTER(RepairBatch), C.POINTER(AdamW), C.c_void_p]),
 }
@@ -320,14 +322,26 @@ class Context:
         _check(lib().gs_repair_features(self.h, cam.width, cam.height, _ptr(out)), "gs_repair_features")
         return out
 
-    def repair_infer(self, feat, tiles, fill=None, gate=None):
+    def repair_infer(self, feat, tiles, fill=None, gate=None, fp8=False):
         """feat (F, H, W, 8) bfloat16; tiles int32 tensor of frame << 24 | ty << 12 | tx."""
         F, H, W = feat.shape[0], feat.shape[1], feat.shape[2]
         if gate is None:
             gate = torch.empty(tiles.numel(), dtype=torch.float32, device=self.device)
         _check(lib().gs_repair_infer(self.h, _ptr(feat), F, W, H, _ptr(tiles), tiles.numel(), _ptr(fill),
-                                     _ptr(gate)), "gs_repair_infer")
+                                     _ptr(gate), 1 if fp8 else 0), "gs_repair_infer")
         return fill, gate
+
+    def repair_calibrate_fp8(self, feat, tiles):
+        F, H, W = feat.shape[0], feat.shape[1], feat.shape[2]
+        _check(lib().gs_repair_calibrate_fp8(self.h, _ptr(feat), F, W, H, _ptr(tiles), tiles.numel()),
+               "gs_repair_calibrate_fp8")
+
+    def repair_fp8_scales(self):
+        """(sx, sw): the calibrated input and weight scales, (6, 32) each."""
+        import numpy as np
+        out = np.empty(384, np.float32)
+        _check(lib().gs_repair_read_fp8_scales(self.h, out.ctypes.data_as(C.c_void_p)), "gs_repair_read_fp8_scales")
+        return out[:192].reshape(6, 32), out[192:].reshape(6, 32)
 
     def repair_train_step(self, feat, target, plain, tiles, scratch=None, lr=1e-3, beta1=0.9, beta2=0.999,
                           eps=1e-8, weight_decay=0.0, gate_weight=0.1, want_loss=True):
