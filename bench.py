@@ -389,38 +389,47 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev):
     tctx, pairs = T.build_pairs("object", 4, 6, 7000, dev)
     w, hist, secs = T.train(tctx, pairs, 1500, 512, 1e-3, 7000, gate_weight=1.0)
     n_frames, n_tiles = pairs.n, int(pairs.tile_tensor().numel())
+    ctx.repair_load(w)
+    # FP8 scales from the BF16 network over (a sample of) the training tiles
+    ctx.repair_calibrate_fp8(pairs.feat, pairs.tile_tensor()[:8192].contiguous())
     del tctx, pairs
     torch.cuda.empty_cache()
-    ctx.repair_load(w)
-    roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1, repair_mode=1, gate_tau=0.5)
 
-    def stereo(k):
-        d, a = poses[k % len(poses)]
-        ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+    def variant(mode):
+        roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1, repair_mode=mode, gate_tau=0.5)
 
-    ps, roi_fracs, net_fracs = [], [], []
-    for k in range(len(poses)):
-        stereo(k)
-        cls = out["cls_aff"].clone()
-        d, a = poses[k]
-        ctx.render_two_pass(ds, d, a, cam, out=out2)
-        ctx.check_ok()
-        ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
-        roi_fracs.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
-        net_fracs.append(((cls & gs.CLS_NET) > 0).float().mean().item())
-    ms, _, _ = timed(stereo, args.steps, args.warmup)
-    _, _, st = timed(stereo, len(poses), 1, profile=True)
-    st = np.mean(np.array(st), 0).tolist()
-    return {"ms_per_stereo_frame": ms, "gate_tau": 0.5, "psnr_aff_vs_full_db": float(np.mean(ps)),
-            "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
-            "net_filled_pixel_share": float(np.mean(net_fracs)), "dtype": "bf16 network, f32 rendering",
-            "stage_ms": dict(zip(["preprocess", "bin_dom", "blend_dom", "warp_edge_gaps_features",
-                                  "centre_rois_and_repair", "bin_roi", "blend_roi", "outputs"], st)),
-            "training": {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "batch_tiles": 512,
-                         "seconds": round(secs, 2), "setup_seconds": round(time.time() - t0 - secs, 2),
-                         "loss_first_last": [hist[0][1], hist[-1][1]],
-                         "data": "object-scene seeds 7000-7003, 6 random head poses each (held out from "
-                                 "the bench scene and poses)"}}
+        def stereo(k):
+            d, a = poses[k % len(poses)]
+            ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+
+        ps, roi_fracs, net_fracs = [], [], []
+        for k in range(len(poses)):
+            stereo(k)
+            cls = out["cls_aff"].clone()
+            d, a = poses[k]
+            ctx.render_two_pass(ds, d, a, cam, out=out2)
+            ctx.check_ok()
+            ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
+            roi_fracs.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
+            net_fracs.append(((cls & gs.CLS_NET) > 0).float().mean().item())
+        ms, _, _ = timed(stereo, args.steps, args.warmup)
+        _, _, st = timed(stereo, len(poses), 1, profile=True)
+        st = np.mean(np.array(st), 0).tolist()
+        return {"ms_per_stereo_frame": ms, "gate_tau": 0.5, "psnr_aff_vs_full_db": float(np.mean(ps)),
+                "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
+                "net_filled_pixel_share": float(np.mean(net_fracs)),
+                "dtype": ("fp8 e4m3" if mode == 2 else "bf16") + " network, f32 rendering",
+                "stage_ms": dict(zip(["preprocess", "bin_dom", "blend_dom", "warp_edge_gaps_features",
+                                      "centre_rois_and_repair", "bin_roi", "blend_roi", "outputs"], st))}
+
+    res = variant(1)
+    res["fp8"] = variant(2)
+    res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "batch_tiles": 512,
+                       "seconds": round(secs, 2), "setup_seconds": round(time.time() - t0 - secs, 2),
+                       "loss_first_last": [hist[0][1], hist[-1][1]],
+                       "data": "object-scene seeds 7000-7003, 6 random head poses each (held out from "
+                               "the bench scene and poses)"}
+    return res
 
 
 def main():
