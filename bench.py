@@ -390,8 +390,9 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev):
     w, hist, secs = T.train(tctx, pairs, 1500, 512, 1e-3, 7000, gate_weight=1.0)
     n_frames, n_tiles = pairs.n, int(pairs.tile_tensor().numel())
     ctx.repair_load(w)
-    # FP8 scales from the BF16 network over (a sample of) the training tiles
-    ctx.repair_calibrate_fp8(pairs.feat, pairs.tile_tensor()[:8192].contiguous())
+    # FP8 scales from the BF16 network over an even sample of the training tiles
+    tiles = pairs.tile_tensor()
+    ctx.repair_calibrate_fp8(pairs.feat, tiles[::max(1, tiles.numel() // 8192)].contiguous())
     del tctx, pairs
     torch.cuda.empty_cache()
 
