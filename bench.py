@@ -35,13 +35,14 @@ WORKLOAD = "object-centric 500k surfels (450k Gaussian cluster + 50k ground plan
 # 10 log10(1 + MSE/s^2) <= 1.3  <=>  PSNR_vs_full >= 28.83 - 10 log10(10^0.13 - 1)
 PSNR_FLOOR_DTU = 28.83
 PSNR_GATE = PSNR_FLOOR_DTU - 10 * math.log10(10 ** 0.13 - 1)
-# FP32 lane operations the blend kernel spends per evaluated (pixel, surfel) pair:
-# reciprocal, u and v, rho3 (2), rho2 (2), min, threshold compare, the three
-# incremental plane-point adds and the row step (13), a quarter of the per-surfel
-# set-up shared by a thread's 4 pixels (3) and the live-bit test (3); and per
-# contributing pair: exponent fma, ex2, alpha clamp, T update, stop compare,
-# depth (2 fma + select), weight, RGB and depth accumulation (4) = 12.
-OPS_EVAL, OPS_CONTRIB = 19, 12
+# FP32 lane operations the rasterizer spends per evaluated (pixel, surfel) pair:
+# the row offset and the three plane-point FMAs (4), reciprocal, u and v (3),
+# rho3 (2), rho2 (2), min and the threshold compare (2) = 13, the live-bit test
+# (3) and a 1/pix share of the per-surfel column set-up (dx, its three plane
+# terms and dx^2: 5) that a thread's pix pixels share; and per contributing
+# pair: exponent fma, ex2, alpha clamp, T update, stop compare, depth (2 fma +
+# select), weight, RGB and depth accumulation (4) = 12.
+OPS_EVAL_PIXEL, OPS_EVAL_COLUMN, OPS_CONTRIB = 16, 5, 12
 SM_COUNT, FP32_LANES_PER_SM = 152, 128
 
 
@@ -377,7 +378,9 @@ def run_ours(args):
     pk, pk_kind = peaks()
     sm_mhz_peak = float(pk.get("sm_max_mhz", 2070.0))
     blend_ms = st_stereo[2]
-    ops = OPS_EVAL * float(np.mean(pairs_eval)) + OPS_CONTRIB * float(np.mean(pairs_contrib))
+    pix = ctx.raster()[1]
+    ops = (OPS_EVAL_PIXEL + OPS_EVAL_COLUMN / pix) * float(np.mean(pairs_eval)) + \
+        OPS_CONTRIB * float(np.mean(pairs_contrib))
     achieved = ops / (blend_ms * 1e-3) / 1e9
     peak_gops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz_peak * 1e6 / 1e9
     prof_traffic = None

@@ -117,6 +117,8 @@ typedef struct {
   int max_rects;         /* centre ROI rectangles */
   int keep_intermediates;/* 1: also store per-surfel float bounds, per-instance tile
                             ids and per-surfel tile counts for inspection */
+  int min_tile;          /* smallest rasterizer tile edge the context will run: 8, 16
+                            or 32 (0 = 16); max_width / min_tile <= 512 */
 } gs_limits;
 
 /* Bytes of device workspace a context with these limits needs. */
@@ -314,6 +316,113 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
 /* 1: the blend kernels count evaluated (pixel, surfel) pairs, and those that
  * contributed, into GS_BUF_PAIRS (uint64 evaluated[2], contributed[2]). */
 gs_status gs_context_set_counting(gs_context *ctx, int enable);
+
+/* Rasterizer configuration (no counterpart in the paper, which fixes 16x16
+ * tiles for the ROI grid, Sec. 3.5; the tile edge of the rasterizer itself is a
+ * free choice of the 2DGS/3DGS tile rasterizer it builds on).
+ *   tile  8, 16 or 32: edge of the rasterizer's square tiles, pixels; at least
+ *         the context's min_tile. The ROI generator keeps the 16-pixel grid:
+ *         with 32-pixel tiles only the pixels of ROI 16-pixel tiles are written.
+ *   pix   pixels per thread, i.e. the block shape (tile^2 / pix threads): 1 or 2
+ *         at tile 8, 2 or 4 at tile 16, 4 or 8 at tile 32.
+ *   batch 32, 64, 128 or 256 surfel records per shared-memory stage.
+ * Every configuration produces the same images bit for bit; they differ in
+ * speed only. The default is {16, 4, 128} ({32, 8, 128} when min_tile = 32).
+ * Returns GS_ERR_BAD_ARG for any other value. */
+typedef struct {
+  int tile, pix, batch;
+} gs_raster_config;
+gs_status gs_context_set_raster(gs_context *ctx, const gs_raster_config *rc);
+gs_status gs_context_get_raster(gs_context *ctx, gs_raster_config *rc);
+
+/* ---------------------------------------------------------------------------
+ * Batched rendering (a serving mode; the paper renders one stereo frame at a
+ * time, Sec. 4.3).
+ *
+ * A batch renders up to GS_BATCH_MAX_FRAMES stereo frames - of different
+ * scenes, surfel counts and image sizes - in one call. Frame f runs in slot f:
+ * a context the caller created with limits that fit that frame, whose
+ * workspace, counters and repair weights it uses (a slot serves one frame per
+ * call). The per-frame stages (pose set-up, preprocessing, binning, warp, hole
+ * classification, ROIs, repair) run on one stream per frame; each rasterizer
+ * pass is ONE persistent launch over all frames: the dominant eyes, then the ROI
+ * tiles. From the second call with a configuration on, the whole call is one
+ * CUDA graph replay on the batch's stream (poses are patched in). Frame f's
+ * outputs equal those of gs_render_stereo (gs_render_two_pass) on slot f with
+ * the batch's rasterizer configuration, bit for bit. A slot must not be used by
+ * another call while a batch call using it is in flight.
+ *
+ * gs_batch_create: slots are n_slots distinct contexts (1..GS_BATCH_MAX_FRAMES);
+ *   stream is a cudaStream_t (NULL = legacy default stream). The batch owns CUDA
+ *   streams and events (no device memory) and starts with the default rasterizer
+ *   configuration. gs_batch_destroy releases them; the slots stay the caller's.
+ * gs_render_stereo_batch: frames[0..n_frames) with n_frames <= n_slots; the
+ *   gap threshold and ROI parameters apply to every frame. Errors: BAD_ARG (a
+ *   frame that does not fit its slot, an invalid parameter), NOT_LOADED
+ *   (repair_mode 1 or 2 on a slot without weights / FP8 calibration), CUDA.
+ * gs_batch_check: synchronises the batch's stream; *device_status is the worst
+ *   device status of the slots (cleared). */
+#define GS_BATCH_MAX_FRAMES 32
+typedef struct gs_batch gs_batch;
+typedef struct {
+  const gs_scene *scene;            /* device SoA, as for gs_render_stereo */
+  gs_pose pose_dom, pose_aff;
+  gs_intrinsics intr;
+  gs_outputs out;                   /* caller-owned device outputs of this frame */
+} gs_frame;
+gs_status gs_batch_create(gs_batch **out, gs_context *const *slots, int n_slots, void *stream);
+gs_status gs_batch_destroy(gs_batch *b);
+gs_status gs_batch_set_raster(gs_batch *b, const gs_raster_config *rc); /* tile >= every slot's min_tile */
+gs_status gs_batch_get_raster(gs_batch *b, gs_raster_config *rc);
+gs_status gs_batch_set_graphs(gs_batch *b, int enable);
+gs_status gs_batch_set_counting(gs_batch *b, int enable); /* pair counts land in each slot's GS_BUF_PAIRS */
+/* With profiling on, stage times of the last call (synchronises): per-frame
+ * set-up + preprocessing + dominant binning, dominant rasterizer launch,
+ * per-frame warp .. ROI binning, ROI rasterizer launch, outputs. */
+gs_status gs_batch_set_profiling(gs_batch *b, int enable);
+gs_status gs_batch_stage_times(gs_batch *b, float *ms, int max_stages, int *n_stages);
+gs_status gs_batch_check(gs_batch *b, int *device_status);
+gs_status gs_render_stereo_batch(gs_batch *b, const gs_frame *frames, int n_frames, int gap_thresh,
+                                 const gs_roi_params *roi);
+/* The sequential comparator (Sec. 4.3) in the same batched mode: both eyes of
+ * every frame rendered in full (rgb_dom, depth_dom, trans_dom, rgb_aff). */
+gs_status gs_render_two_pass_batch(gs_batch *b, const gs_frame *frames, int n_frames);
+
+/* ---------------------------------------------------------------------------
+ * Rasterizer autotuner. Runs the call - gs_render_stereo(_batch) with `roi`, or
+ * the two-pass comparator gs_render_two_pass(_batch) when roi is NULL (gap
+ * threshold unused) - on the caller's inputs once per rasterizer configuration
+ * the slots allow (two untimed calls, then `reps` calls timed with CUDA events
+ * on the call's stream; the median counts) and leaves the fastest set on the
+ * batch / context. results[0..*n_results) gets
+ * every configuration tried with its median ms (-1: the configuration
+ * overflowed a buffer or failed). Results are cached for the process under a
+ * key of the GPU (name, compute capability, SM count) and the frames' shapes
+ * (image size, surfel-count power-of-two bucket, SH degree; stereo with plain
+ * or learned repair, or two-pass); with use_cache = 1 a cached entry is applied without timing
+ * (*n_results = 0). The outputs of the tuned calls are overwritten. */
+typedef struct {
+  gs_raster_config rc;
+  float ms;
+} gs_tune_result;
+gs_status gs_autotune_batch(gs_batch *b, const gs_frame *frames, int n_frames, int gap_thresh,
+                            const gs_roi_params *roi, int reps, int use_cache, gs_tune_result *results,
+                            int max_results, int *n_results, gs_raster_config *best, float *best_ms);
+gs_status gs_autotune_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                             const gs_pose *pose_aff, const gs_intrinsics *intr, int gap_thresh,
+                             const gs_roi_params *roi, const gs_outputs *out, int reps, int use_cache,
+                             gs_tune_result *results, int max_results, int *n_results,
+                             gs_raster_config *best, float *best_ms);
+/* The process-wide tuning cache (host only; no GPU needed). Text file, one
+ * entry per line: "<key> <tile> <pix> <batch> <ms>", keys without blanks.
+ * Loading merges a file's entries (a malformed file changes nothing and gives
+ * BAD_ARG); get gives NOT_LOADED for a missing key. */
+gs_status gs_tune_cache_save(const char *path);
+gs_status gs_tune_cache_load(const char *path);
+gs_status gs_tune_cache_clear(void);
+gs_status gs_tune_cache_size(int *n);
+gs_status gs_tune_cache_put(const char *key, const gs_raster_config *rc, float ms);
+gs_status gs_tune_cache_get(const char *key, gs_raster_config *rc, float *ms);
 
 /* 1 (the default): the first call of an entry point with a given scene, image
  * size, output set and parameters captures its kernels into a CUDA graph, and

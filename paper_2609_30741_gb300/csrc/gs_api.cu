@@ -6,7 +6,7 @@
 
 #include <new>
 
-#include "gs_internal.cuh"
+#include "gs_context.cuh"
 #include "gs_sort.cuh"
 
 namespace gs {
@@ -17,8 +17,11 @@ namespace {
 
 constexpr size_t kAlign = 256;
 // widest image: the binning keeps 8 warps x 4 tile rows x 2 counters per tile
-// column in shared memory (64 KB at 4096 pixels, 128 KB at this limit)
+// column in shared memory (128 KB at 512 tile columns, the limit)
 constexpr int kMaxWidth = 8192;
+constexpr int kMaxTileCols = 512;
+
+
 
 struct Carver {
   char *base;
@@ -36,7 +39,12 @@ struct Carver {
 void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   const size_t N = (size_t)lim.max_surfels;
   const size_t P = (size_t)lim.max_width * (size_t)lim.max_height;
-  const size_t tiles = (size_t)((lim.max_width + kTile - 1) / kTile) * (size_t)((lim.max_height + kTile - 1) / kTile);
+  // the ROI grid (16 pixels) and the finest rasterizer grid the context serves
+  const size_t roi_tiles =
+      (size_t)((lim.max_width + kTile - 1) / kTile) * (size_t)((lim.max_height + kTile - 1) / kTile);
+  const int msh = min_tshift(lim), mts = 1 << msh;
+  const size_t rtx = (size_t)((lim.max_width + mts - 1) >> msh), rty = (size_t)((lim.max_height + mts - 1) >> msh);
+  const size_t tiles = rtx * rty > roi_tiles ? rtx * rty : roi_tiles;
   const size_t I = (size_t)lim.max_instances;
   const size_t table_max = tiles * bin_chunks(lim.max_surfels);
   size_t scan_n = N > P ? N : P;
@@ -63,12 +71,14 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.bin_table = c.take<uint4>(table);
   ws.band_pool_cap = (uint32_t)(8 * N + 1024);
   ws.band_pool = reinterpret_cast<BandEntry *>(c.take<char>(kBandEntryBytes * ws.band_pool_cap));
-  ws.band_lists = c.take<uint2>(band_list_words(lim.max_surfels, (lim.max_height + kTile - 1) / kTile));
+  ws.band_lists = c.take<uint2>(band_list_words(lim.max_surfels, (int)rty));  // the binning runs on the raster grid
   ws.bin_offs = c.take<uint32_t>(table);
   ws.ranges = c.take<uint2>(tiles);
   ws.tile_mask = c.take<uint8_t>(tiles);
-  ws.mask_sat = c.take<uint32_t>((size_t)((lim.max_height + kTile - 1) / kTile + 1) *
-                                 (size_t)((lim.max_width + kTile - 1) / kTile + 1));
+  ws.rmask = c.take<uint8_t>(tiles);
+  ws.items = c.take<uint32_t>(tiles);
+  ws.rqueue = c.take<uint32_t>(2);
+  ws.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
   for (int e = 0; e < 2; ++e) {
     ws.row_off[e] = c.take<uint32_t>(N);
     ws.spans[e] = c.take<uint2>(I);
@@ -110,6 +120,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.max_h = lim.max_height;
   ws.max_rects = lim.max_rects;
   ws.max_tiles = (int)tiles;
+  ws.min_tshift = msh;
   ws.max_instances = (int64_t)I;
   ws.max_pixels = (int64_t)P;
   ws.keep_intermediates = lim.keep_intermediates;
@@ -119,7 +130,9 @@ bool limits_ok(const gs_limits *lim) {
   return lim && lim->max_surfels >= 0 && lim->max_width > 0 && lim->max_height > 0 && lim->max_instances > 0 &&
          lim->max_instances < (int64_t(1) << 30) && lim->max_rects > 0 &&
          (int64_t)lim->max_width * lim->max_height < (int64_t(1) << 31) && lim->max_surfels < (1 << 30) &&
-         lim->max_width <= kMaxWidth && lim->max_height <= kMaxWidth;
+         lim->max_width <= kMaxWidth && lim->max_height <= kMaxWidth &&
+         (lim->min_tile == 0 || lim->min_tile == 8 || lim->min_tile == 16 || lim->min_tile == 32) &&
+         ((lim->max_width + (1 << min_tshift(*lim)) - 1) >> min_tshift(*lim)) <= kMaxTileCols;
 }
 
 __global__ void reset_counters_kernel(Counters *c) {
@@ -130,6 +143,7 @@ __global__ void reset_counters_kernel(Counters *c) {
     c->n_rows[0] = c->n_rows[1] = 0;
     c->n_band[0] = c->n_band[1] = 0;
     c->n_union = 0;
+    c->n_items = 0;
     c->dmin_bits = 0x7f800000u;
     c->dmax_bits = 0u;
     c->n_rects = 0;
@@ -139,6 +153,9 @@ __global__ void reset_counters_kernel(Counters *c) {
 }
 
 }  // namespace
+
+// log2 of the smallest rasterizer tile edge a context is sized for (0 = 16)
+int min_tshift(const gs_limits &lim) { return lim.min_tile == 8 ? 3 : lim.min_tile == 32 ? 5 : 4; }
 
 size_t workspace_bytes(const gs_limits &lim) {
   Carver c{nullptr, 0, true};
@@ -157,38 +174,6 @@ bool carve_workspace(const gs_limits &lim, void *base, size_t bytes, Workspace *
 }  // namespace gs
 
 using namespace gs;
-
-constexpr int kMaxMarks = 16;
-
-// One captured kernel sequence per entry point.
-struct GraphSlot {
-  bool valid;
-  unsigned char key[512];
-  size_t key_len;
-  cudaGraph_t graph;             // kept alive: setup_node belongs to it
-  cudaGraphExec_t exec;
-  cudaGraphNode_t setup_node;
-  unsigned long long launches;  // kernels in the graph
-  int nmarks;
-};
-
-struct gs_context {
-  Workspace ws;
-  gs_limits lim;
-  cudaStream_t stream;
-  int counting;
-  int last_tiles;  // tile count of the last binning (selects the sorted buffer)
-  int profiling;
-  int nmarks;
-  cudaEvent_t ev[kMaxMarks];
-  int use_graphs;
-  int capturing;
-  cudaStream_t cap_stream;
-  GraphSlot graphs[3];  // mono, stereo, two-pass
-  int rp_loaded;        // repair network weights present
-  int rp_fp8;           // FP8 scales and weights calibrated for the current weights
-  int rp_step;          // AdamW steps taken
-};
 
 static void release_slot(GraphSlot &g) {
   if (g.valid) {
@@ -223,7 +208,9 @@ gs_status record_cuda_failure(const char *file, int line, cudaError_t e) {
 
 static gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : cuda_fail(e); }
 
-static bool scene_ok(const gs_context *ctx, const gs_scene *sc) {
+namespace gs {
+
+bool scene_ok(const gs_context *ctx, const gs_scene *sc) {
   if (!sc || sc->n < 0 || sc->n > ctx->lim.max_surfels || sc->sh_degree < 0 || sc->sh_degree > 3) return false;
   if (sc->n == 0) return true;
   if (!sc->pos || !sc->quat || !sc->scale || !sc->opacity || !sc->sh) return false;
@@ -235,15 +222,16 @@ static bool scene_ok(const gs_context *ctx, const gs_scene *sc) {
   return true;
 }
 
-static bool intr_ok(const gs_context *ctx, const gs_intrinsics *in) {
+bool intr_ok(const gs_context *ctx, const gs_intrinsics *in) {
   return in && in->width > 0 && in->height > 0 && in->width <= ctx->lim.max_width &&
          in->height <= ctx->lim.max_height && in->fx > 0 && in->fy > 0 && in->width < 65536 * kTile &&
          in->height < 65536 * kTile;
 }
 
-static PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in) {
+PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in, const RasterConfig &rc) {
   PoseArgs pa;
   memset(&pa, 0, sizeof(pa));
+  pa.tshift = raster_tshift(rc);
   memcpy(pa.R[0], a->R, sizeof(double) * 9);
   memcpy(pa.t[0], a->t, sizeof(double) * 3);
   if (b) {
@@ -266,6 +254,37 @@ static PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsic
   pa.W = in->width; pa.H = in->height;
   return pa;
 }
+
+bool outputs_ok(const gs_outputs *o) { return o && o->rgb_dom && o->depth_dom && o->trans_dom && o->rgb_aff; }
+
+bool roi_ok(int gap_thresh, const gs_roi_params *roi) {
+  if (!roi || gap_thresh < 0 || roi->margin < 0 || roi->samples_per_edge < 2 || roi->samples_per_edge > 1 << 20 ||
+      (roi->depth_mode != 0 && roi->depth_mode != 1))
+    return false;
+  return roi->repair_mode >= 0 && roi->repair_mode <= 3 && roi->gate_tau > 0.f && roi->gate_tau < 1.f;
+}
+
+cudaError_t copy_optional(gs_context *ctx, const gs_outputs *out, int W, int H) {
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaSuccess;
+  if (out->cls_aff) e = cudaMemcpyAsync(out->cls_aff, ctx->ws.cls, (size_t)W * H, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && out->roi_rects)
+    e = cudaMemcpyAsync(out->roi_rects, ctx->ws.rects, sizeof(int4) * (size_t)ctx->lim.max_rects,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && out->roi_count)
+    e = cudaMemcpyAsync(out->roi_count, &ctx->ws.ctr->n_rects, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess && out->edge_widths)
+    e = cudaMemcpyAsync(out->edge_widths, ctx->ws.widths, sizeof(int32_t) * 4, cudaMemcpyDeviceToDevice, s);
+  return e;
+}
+
+cudaError_t launch_reset_counters(Counters *c, cudaStream_t s) {
+  reset_counters_kernel<<<1, 32, 0, s>>>(c);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+}  // namespace gs
 
 extern "C" {
 
@@ -307,12 +326,15 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
   ctx->lim = *lim;
   ctx->stream = (cudaStream_t)stream;
   ctx->use_graphs = 1;
+  ctx->rc = lim->min_tile == 32 ? RasterConfig{32, 8, 128} : RasterConfig{16, 4, 128};
   if (!carve_workspace(*lim, workspace, workspace_bytes_, &ctx->ws)) {
     delete ctx;
     return GS_ERR_WORKSPACE;
   }
-  cudaError_t e = prepare_binning((lim->max_width + kTile - 1) / kTile);
+  const int msh = min_tshift(*lim);
+  cudaError_t e = prepare_binning((lim->max_width + (1 << msh) - 1) >> msh);
   if (e == cudaSuccess) e = prepare_repair();
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.rqueue, 0, 2 * sizeof(uint32_t), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.scan_ticket, 0, sizeof(uint32_t), ctx->stream);
   if (e != cudaSuccess) {
@@ -392,16 +414,25 @@ static void mark(gs_context *ctx, int slot) {
   ctx->nmarks = slot + 1 > ctx->nmarks ? slot + 1 : ctx->nmarks;
 }
 
+// One eye through the persistent rasterizer (a table of one frame).
+static cudaError_t raster_one(gs_context *ctx, const RasterFrame &f) {
+  RasterTable t;
+  t.n = 1;
+  t.f[0] = f;
+  return launch_raster(t, ctx->rc, ctx->counting != 0, ctx->ws.rqueue, ctx->stream);
+}
+
 static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye, int W, int H, float3 bg,
                                  float *rgb, float *depth, float *trans, bool stats, int slot, int order) {
   const Workspace &ws = ctx->ws;
   cudaStream_t s = ctx->stream;
-  const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
+  const int sh = raster_tshift(ctx->rc), ts = 1 << sh;
+  const int tx = (W + ts - 1) >> sh, ty = (H + ts - 1) >> sh;
   ctx->last_tiles = tx * ty;
   cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s, order);
   if (e != cudaSuccess) return cuda_fail(e);
   mark(ctx, slot);
-  e = launch_blend(ws, eye, W, H, nullptr, bg, rgb, depth, trans, nullptr, stats, ctx->counting != 0, s);
+  e = raster_one(ctx, raster_frame(ws, eye, W, H, sh, nullptr, bg, rgb, depth, trans, nullptr, stats));
   mark(ctx, slot + 1);
   return cuda_status(e);
 }
@@ -410,9 +441,8 @@ static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const PoseAr
   cudaStream_t s = ctx->stream;
   ctx->nmarks = 0;
   mark(ctx, 0);
-  reset_counters_kernel<<<1, 32, 0, s>>>(ctx->ws.ctr);
-  GS_LAUNCHED(1);
-  cudaError_t e = launch_setup_cams(pa, ctx->ws.cams, s);
+  cudaError_t e = launch_reset_counters(ctx->ws.ctr, s);
+  if (e == cudaSuccess) e = launch_setup_cams(pa, ctx->ws.cams, s);
   if (e != cudaSuccess) return cuda_fail(e);
   e = launch_preprocess(*scene, ctx->ws, pa.neyes, pa.W, pa.H, s);
   mark(ctx, 1);
@@ -519,16 +549,6 @@ static gs_status run_graph(gs_context *ctx, int kind, const void *key, size_t ke
   return cuda_status(le);
 }
 
-// Byte key of everything a captured sequence depends on besides the poses.
-struct KeyBuilder {
-  unsigned char buf[512];
-  size_t len = 0;
-  template <class T>
-  void add(const T &v) {
-    if (len + sizeof(T) <= sizeof(buf)) memcpy(buf + len, &v, sizeof(T));
-    len += sizeof(T);
-  }
-};
 
 static void key_common(KeyBuilder &kb, gs_context *ctx, int kind, const gs_scene *scene, const gs_intrinsics *intr) {
   kb.add(kind);
@@ -537,6 +557,7 @@ static void key_common(KeyBuilder &kb, gs_context *ctx, int kind, const gs_scene
   kb.add(intr->height);
   kb.add(ctx->counting);
   kb.add(ctx->profiling);
+  kb.add(ctx->rc);
 }
 
 extern "C" {
@@ -545,7 +566,7 @@ gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *
                          const float *bg, float *rgb, float *depth, float *trans) {
   if (!ctx || !pose || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !rgb) return GS_ERR_BAD_ARG;
   const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
-  const PoseArgs pa = pose_args(pose, nullptr, intr);
+  const PoseArgs pa = pose_args(pose, nullptr, intr, ctx->rc);
   KeyBuilder kb;
   key_common(kb, ctx, 0, scene, intr);
   kb.add(b);
@@ -559,38 +580,17 @@ gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *
   });
 }
 
-static bool outputs_ok(const gs_outputs *o) {
-  return o && o->rgb_dom && o->depth_dom && o->trans_dom && o->rgb_aff;
-}
-
-static gs_status copy_optional(gs_context *ctx, const gs_outputs *out, int W, int H) {
-  cudaStream_t s = ctx->stream;
-  cudaError_t e = cudaSuccess;
-  if (out->cls_aff) e = cudaMemcpyAsync(out->cls_aff, ctx->ws.cls, (size_t)W * H, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && out->roi_rects)
-    e = cudaMemcpyAsync(out->roi_rects, ctx->ws.rects, sizeof(int4) * (size_t)ctx->lim.max_rects,
-                        cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && out->roi_count)
-    e = cudaMemcpyAsync(out->roi_count, &ctx->ws.ctr->n_rects, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && out->edge_widths)
-    e = cudaMemcpyAsync(out->edge_widths, ctx->ws.widths, sizeof(int32_t) * 4, cudaMemcpyDeviceToDevice, s);
-  return cuda_status(e);
-}
-
 gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom, const gs_pose *pose_aff,
                            const gs_intrinsics *intr, int gap_thresh, const gs_roi_params *roi,
                            const gs_outputs *out) {
   if (!ctx || !pose_dom || !pose_aff || !roi || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
     return GS_ERR_BAD_ARG;
-  if (gap_thresh < 0 || roi->margin < 0 || roi->samples_per_edge < 2 || roi->samples_per_edge > 1 << 20 ||
-      (roi->depth_mode != 0 && roi->depth_mode != 1))
-    return GS_ERR_BAD_ARG;
-  if (roi->repair_mode < 0 || roi->repair_mode > 3 || !(roi->gate_tau > 0.f && roi->gate_tau < 1.f))
-    return GS_ERR_BAD_ARG;
+  if (!roi_ok(gap_thresh, roi)) return GS_ERR_BAD_ARG;
   if ((roi->repair_mode == 1 && !ctx->rp_loaded) || (roi->repair_mode == 2 && !ctx->rp_fp8)) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
-  const int tx = (W + kTile - 1) / kTile, ty = (H + kTile - 1) / kTile;
-  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr);
+  const int sh = raster_tshift(ctx->rc), ts = 1 << sh;
+  const int tx = (W + ts - 1) >> sh, ty = (H + ts - 1) >> sh;
+  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc);
   KeyBuilder kb;
   key_common(kb, ctx, 1, scene, intr);
   kb.add(gap_thresh);
@@ -627,18 +627,25 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     }
     mark(ctx, 5);
     // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
+    // (the ROI mask lives on the 16-pixel grid; other tile edges bin on a copy
+    // on their own grid)
     ctx->last_tiles = tx * ty;
-    e = launch_binning(ctx->ws, 1, scene->n, tx, ty, ctx->ws.tile_mask, ctx->stream,
-                       p.parallel ? kOrderReuse : kOrderOwn);
+    const uint8_t *bmask = ctx->ws.tile_mask;
+    if (sh != 4) {
+      if ((e = launch_raster_mask(ctx->ws.tile_mask, W, H, sh, ctx->ws.rmask, ctx->stream)) != cudaSuccess)
+        return cuda_fail(e);
+      bmask = ctx->ws.rmask;
+    }
+    e = launch_binning(ctx->ws, 1, scene->n, tx, ty, bmask, ctx->stream, p.parallel ? kOrderReuse : kOrderOwn);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
-    e = launch_blend(ctx->ws, 1, W, H, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ctx->ws.cls, false,
-                     ctx->counting != 0, ctx->stream);
+    e = raster_one(ctx, raster_frame(ctx->ws, 1, W, H, sh, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr,
+                                     ctx->ws.cls, false));
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 7);
-    st = copy_optional(ctx, out, W, H);
+    e = copy_optional(ctx, out, W, H);
     mark(ctx, 8);
-    return st;
+    return cuda_status(e);
   });
 }
 
@@ -647,7 +654,7 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
   if (!ctx || !pose_dom || !pose_aff || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
     return GS_ERR_BAD_ARG;
   const int W = intr->width, H = intr->height;
-  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr);
+  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc);
   KeyBuilder kb;
   key_common(kb, ctx, 2, scene, intr);
   kb.add(*out);
@@ -662,6 +669,22 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
     return render_eye_full(ctx, scene, 1, W, H, black, out->rgb_aff, nullptr, nullptr, false, 4,
                            p.parallel ? kOrderReuse : kOrderOwn);
   });
+}
+
+gs_status gs_context_set_raster(gs_context *ctx, const gs_raster_config *rc) {
+  if (!ctx || !rc) return GS_ERR_BAD_ARG;
+  const RasterConfig c{rc->tile, rc->pix, rc->batch};
+  if (!raster_config_ok(c) || raster_tshift(c) < ctx->ws.min_tshift) return GS_ERR_BAD_ARG;
+  ctx->rc = c;
+  return GS_OK;
+}
+
+gs_status gs_context_get_raster(gs_context *ctx, gs_raster_config *rc) {
+  if (!ctx || !rc) return GS_ERR_BAD_ARG;
+  rc->tile = ctx->rc.tile;
+  rc->pix = ctx->rc.pix;
+  rc->batch = ctx->rc.batch;
+  return GS_OK;
 }
 
 gs_status gs_context_set_graphs(gs_context *ctx, int enable) {

@@ -32,6 +32,8 @@
 //   5. per-(tile, chunk) counts (bin_kernel, mode 0)
 //   6. tile-major scan of the counts -> run offsets, tile ranges
 //   7. placement of every surfel id (bin_kernel, mode 1)
+#include <mutex>
+
 #include "gs_internal.cuh"
 #include "gs_scan.cuh"
 #include "gs_sort.cuh"
@@ -128,27 +130,31 @@ __device__ __forceinline__ void band_slices(const Conic &q, float b0, float b1, 
   }
 }
 
-// Tile columns [t0, t1] whose pixel centres meet the absolute interval [xa, xb].
-__device__ __forceinline__ void tile_span(float xa, float xb, int W, int rx0, int rx1, int &t0, int &t1) {
+// Tile columns [t0, t1] (tile edge ts = 1 << tshift) whose pixel centres meet the
+// absolute interval [xa, xb].
+__device__ __forceinline__ void tile_span(float xa, float xb, int W, int rx0, int rx1, int tshift, int &t0,
+                                          int &t1) {
   if (!(xa <= xb) || xa > (float)(W - 1) + kBoundPad || xb < -kBoundPad) {
     t0 = 1;
     t1 = 0;
     return;
   }
-  t0 = max(rx0, (int)ceilf((xa - kBoundPad - (float)(kTile - 1)) * (1.f / kTile)));
-  t1 = min(rx1, (int)floorf((xb + kBoundPad) * (1.f / kTile)));
+  const float ts = (float)(1 << tshift), its = 1.f / ts;  // exact: a power of two
+  t0 = max(rx0, (int)ceilf((xa - kBoundPad - (ts - 1.f)) * its));
+  t1 = min(rx1, (int)floorf((xb + kBoundPad) * its));
 }
 
 // Up to two tile ranges [a0, a1] u [c0, c1] (disjoint, a before c) of tile row ty
 // that the surfel's support reaches; empty ranges have lo > hi.
 __device__ __forceinline__ void row_ranges(const Conic &q, const float4 r0, int ty, int W, int H, int rx0, int rx1,
-                                           int &a0, int &a1, int &c0, int &c1) {
-  const float y0 = (float)(ty * kTile) - kBoundPad;
-  const float y1 = (float)min(ty * kTile + kTile - 1, H - 1) + kBoundPad;
+                                           int tshift, int &a0, int &a1, int &c0, int &c1) {
+  const int ts = 1 << tshift;
+  const float y0 = (float)(ty * ts) - kBoundPad;
+  const float y1 = (float)min(ty * ts + ts - 1, H - 1) + kBoundPad;
   float elo, ehi, dlo, dhi;
   band_slices(q, y0 - r0.y, y1 - r0.y, elo, ehi, dlo, dhi);
-  tile_span(r0.x + elo, r0.x + ehi, W, rx0, rx1, a0, a1);
-  tile_span(r0.x + dlo, r0.x + dhi, W, rx0, rx1, c0, c1);
+  tile_span(r0.x + elo, r0.x + ehi, W, rx0, rx1, tshift, a0, a1);
+  tile_span(r0.x + dlo, r0.x + dhi, W, rx0, rx1, tshift, c0, c1);
   if (a0 > a1) {
     a0 = c0; a1 = c1; c0 = 1; c1 = 0;
   } else if (c0 <= c1) {
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
   if (j0 >= n) return;  // warp-uniform
   const uint32_t j = j0 + (uint32_t)lane;
   const uint32_t i = j < n ? ids[j] : 0u;  // the surfels being binned
-  const int W = cams->eye[eye].W, H = cams->eye[eye].H;
+  const int W = cams->eye[eye].W, H = cams->eye[eye].H, tshift = cams->eye[eye].tshift;
   int nr = 0, ry = 0, rx0 = 0, rx1 = -1;
   Conic q{};
   float cx = 0.f, cy = 0.f;
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
     const uint32_t slot = base + (uint32_t)qq;
     if (qq < total && slot < cap) {
       int a0 = sx0, a1 = sx1, c0 = 1, c1 = 0;
-      if (qk.ok) row_ranges(qk, ck, ty, W, H, sx0, sx1, a0, a1, c0, c1);
+      if (qk.ok) row_ranges(qk, ck, ty, W, H, sx0, sx1, tshift, a0, a1, c0, c1);
       // empty ranges are stored as [1, 0]
       if (a0 > a1) { a0 = 1; a1 = 0; }
       if (c0 > c1) { c0 = 1; c1 = 0; }
@@ -382,7 +388,7 @@ struct ReuseApply {
 constexpr int kBinWarps = 8;
 constexpr int kBinThreads = kBinWarps * 32;
 constexpr int kBandRows = 4;
-constexpr int kMaxBands = 128;  // image height <= kMaxBands * kBandRows * kTile = 8192 pixels
+constexpr int kMaxBands = 256;  // tile rows <= kMaxBands * kBandRows = 1024 (8192 pixels at tile edge 8)
 
 // One (surfel, band) entry: surfel id, span slot of its first row in the band,
 // first row << 4 | rows in the band (1..kBandRows).
@@ -693,21 +699,36 @@ struct BinOffsetApply {
   uint32_t *n_inst, *n_sort;
   uint32_t cap;
   uint32_t *status;
+  uint32_t *n_items;  // cleared for the tile list of a masked binning, or null
   __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const { offs[i] = prefix; }
   __device__ void end(uint32_t, uint32_t total) const {
     *n_inst = total;
     *n_sort = total < cap ? total : cap;
     if (total > cap) atomicOr(status, kStCapacity);
+    if (n_items) *n_items = 0u;
   }
 };
 
+// Tile ranges; a masked binning also lists its masked tiles (in any order: the
+// rasterizer's tiles are independent) for the persistent rasterizer.
 __global__ void bin_ranges_kernel(const uint32_t *__restrict__ offs, uint32_t nch, int ntiles,
-                                  const uint32_t *__restrict__ n_inst, uint32_t cap, uint2 *__restrict__ ranges) {
+                                  const uint32_t *__restrict__ n_inst, uint32_t cap, uint2 *__restrict__ ranges,
+                                  const uint8_t *__restrict__ mask, uint32_t *__restrict__ items,
+                                  uint32_t *__restrict__ n_items) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ntiles) return;
-  const uint32_t s0 = offs[(size_t)t * nch];
-  const uint32_t s1 = t + 1 < ntiles ? offs[(size_t)(t + 1) * nch] : *n_inst;
-  ranges[t] = make_uint2(min(s0, cap), min(s1, cap));
+  if (t < ntiles) {
+    const uint32_t s0 = offs[(size_t)t * nch];
+    const uint32_t s1 = t + 1 < ntiles ? offs[(size_t)(t + 1) * nch] : *n_inst;
+    ranges[t] = make_uint2(min(s0, cap), min(s1, cap));
+  }
+  if (!mask) return;
+  const bool on = t < ntiles && mask[t] != 0;
+  const uint32_t ball = __ballot_sync(0xffffffffu, on);
+  const int lane = threadIdx.x & 31;
+  uint32_t base = 0;
+  if (lane == 0 && ball) base = atomicAdd(n_items, (uint32_t)__popc(ball));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (on) items[base + (uint32_t)__popc(ball & ((1u << lane) - 1u))] = (uint32_t)t;
 }
 
 uint32_t bin_warp_surfels(int max_surfels) {
@@ -730,9 +751,21 @@ uint32_t bin_chunks(int max_surfels) {
 
 size_t bin_smem_bytes(int tiles_x) { return 2 * sizeof(uint32_t) * kBinWarps * kBandRows * (size_t)tiles_x; }
 
+// The opt-in is a property of the kernel on the device, shared by every
+// context: it only ever grows, so a small context created after a large one
+// keeps the large one's limit.
 cudaError_t prepare_binning(int max_tiles_x) {
-  return cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)bin_smem_bytes(max_tiles_x));
+  static std::mutex mu;
+  static int granted[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int want = (int)bin_smem_bytes(max_tiles_x);
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && granted[dev] >= want) return cudaSuccess;
+  e = cudaFuncSetAttribute(bin_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+  if (e == cudaSuccess && dev >= 0 && dev < 64) granted[dev] = want;
+  return e;
 }
 
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
@@ -829,12 +862,13 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   // 6. tile-major scan: where every (tile, chunk) run starts
   err = scan_launch(BinTableLoad{ws.bin_table, &ctr->n_vis[eye], (uint32_t)n, ws.bin_nch,
                                  kBinWarps * ws.bin_warp_surfels},
-                    BinOffsetApply{ws.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status},
+                    BinOffsetApply{ws.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status,
+                                   tile_mask ? &ctr->n_items : nullptr},
                     (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, ws.scan_sums, ws.scan_ticket,
                     nullptr, s);
   if (err != cudaSuccess) return err;
   bin_ranges_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(ws.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
-                                                         ws.ranges);
+                                                         ws.ranges, tile_mask, ws.items, &ctr->n_items);
   // 7. every surfel id to its slot
   bin_kernel<<<grid, kBinThreads, bin_smem_bytes(tiles_x), s>>>(a, 1);
   GS_LAUNCHED(2);

@@ -8,7 +8,9 @@
 
 namespace gs {
 
-constexpr int kTile = 16;            // rasterizer tile edge, pixels (Sec. 3.5: 16x16 tiles)
+// ROI grid: the ROI generator aligns its rectangles to 16x16 tiles (Sec. 3.5),
+// whatever tile edge the rasterizer runs with (8, 16 or 32 pixels).
+constexpr int kTile = 16;
 constexpr float kZNear = 0.2f;       // near plane, metres
 constexpr float kAlphaMax = 0.99f;   // alpha clamp
 constexpr float kTMin = 1e-4f;       // transmittance stop
@@ -31,7 +33,8 @@ struct EyeCam {
   float t[3];
   float centre[3];  // camera centre in world coordinates (SH view direction)
   float fx, fy, cx, cy;
-  int W, H, tiles_x, tiles_y;
+  int W, H, tiles_x, tiles_y;  // tiles of the rasterizer grid
+  int tshift;                   // rasterizer tile edge = 1 << tshift pixels
 };
 
 struct CamBlock {
@@ -48,6 +51,7 @@ struct PoseArgs {
   int W, H;
   int neyes;
   int parallel;  // the eyes share orientation and the baseline lies in the image plane
+  int tshift;    // rasterizer tile edge = 1 << tshift pixels
 };
 
 struct Counters {
@@ -60,7 +64,8 @@ struct Counters {
   uint32_t n_rows[2];    // (surfel, tile row) spans per eye
   uint32_t n_band[2];    // (surfel, band) list entries of the last binning per eye
   uint32_t n_union;      // surfels in the dominant binning's depth order (both eyes' visible set)
-  uint32_t pad[5];
+  uint32_t n_items;      // rasterizer tiles listed by the last masked binning
+  uint32_t pad[4];
   unsigned long long pairs[2];    // evaluated (pixel, surfel) pairs per eye (counting mode)
   unsigned long long contrib[2];  // of which contributed (alpha >= 1/255, before termination)
 };
@@ -95,8 +100,11 @@ struct Workspace {
   uint32_t *bin_offs;           // their tile-major exclusive scan
   uint32_t *ival;               // surfel id per instance, grouped by tile, depth order inside
   uint32_t *ikey;               // tile id per instance (keep_intermediates)
-  uint2 *ranges;
-  uint8_t *tile_mask;
+  uint2 *ranges;                // per rasterizer tile: [first, end) of its instances
+  uint8_t *tile_mask;           // ROI mask on the 16-pixel grid
+  uint8_t *rmask;               // the ROI mask on the rasterizer grid (tile edge 8 or 32)
+  uint32_t *items;              // rasterizer tiles of the last masked binning
+  uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
   uint32_t *mask_sat;           // summed-area table of the tile mask [tiles_y + 1][tiles_x + 1]
   uint32_t *row_off[2];         // per surfel and eye: slot of its first rectangle row in spans
   uint2 *spans[2];              // per (surfel, tile row): tile ranges [a0, a1] u [c0, c1], 4 x 16 bits
@@ -126,7 +134,8 @@ struct Workspace {
   uint8_t *rp_flags;            // [tiles] tile has a hole
   uint32_t *rp_list, *rp_nlist; // listed tiles and their number
   // limits
-  int max_surfels, max_w, max_h, max_rects, max_tiles;
+  int max_surfels, max_w, max_h, max_rects, max_tiles;  // max_tiles: rasterizer tiles at min_tshift
+  int min_tshift;               // smallest rasterizer tile edge the buffers hold (log2)
   int64_t max_instances, max_pixels;
   int keep_intermediates;
   uint32_t bin_warp_surfels, bin_nch;  // binning chunk geometry (see launch_binning)
@@ -207,9 +216,48 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
 cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const RepairOpt &o, float *host_loss,
                               cudaStream_t s);
 
-cudaError_t launch_blend(const Workspace &ws, int eye, int W, int H, const uint8_t *tile_mask,
-                         float3 bg, float *rgb, float *depth, float *trans, uint8_t *cls,
-                         bool depth_stats, bool count_pairs, cudaStream_t s);
+// ---- persistent rasterizer ----
+// One launch blends the tiles of up to kRasterFrames (frame, eye) images: its
+// CTAs stay resident and take (frame, tile) work items from a device counter.
+constexpr int kRasterFrames = 32;
+struct RasterFrame {
+  const uint2 *ranges;      // per rasterizer tile: [first, end) into ids
+  const uint32_t *ids;      // surfel id per instance, grouped by tile, depth order inside
+  const float4 *rec;        // this eye's blend records
+  const uint8_t *roi;       // 16-pixel ROI mask: only its pixels are written, or null
+  const uint32_t *items;    // listed tiles, or null: every tile in raster order
+  const uint32_t *n_items;  // device count of the listed tiles
+  float *rgb, *depth, *trans;  // [3][H][W], [H][W] (or null), [H][W] (or null)
+  uint8_t *cls;             // class map: written pixels get kClsRender, or null
+  Counters *ctr;            // depth range and pair counts of this frame
+  float bg[3];
+  int W, H, tiles_x, ntiles, tshift;
+  int eye;
+  int stats;                // 1: record the range of D / (1 - T) over pixels with coverage >= 0.5
+  uint32_t n_rec;           // records available (ids beyond are ignored)
+};
+struct RasterTable {
+  RasterFrame f[kRasterFrames];
+  int n;
+};
+// Tile edge, pixels per thread (the block has tile^2 / pix threads) and surfel
+// records per shared-memory stage.
+struct RasterConfig {
+  int tile, pix, batch;
+};
+bool raster_config_ok(const RasterConfig &c);
+int raster_tshift(const RasterConfig &c);
+// `queue` holds two words that are zero between launches (the launch's last CTA
+// clears them).
+cudaError_t launch_raster(const RasterTable &t, const RasterConfig &c, bool count_pairs, uint32_t *queue,
+                          cudaStream_t s);
+// Fills a RasterFrame for eye `eye` of a workspace; mask: 16-pixel ROI mask of a
+// masked pass (the listed tiles of the last masked binning), or null.
+RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift, const uint8_t *mask, float3 bg,
+                         float *rgb, float *depth, float *trans, uint8_t *cls, bool stats);
+// ROI mask (16-pixel grid) -> rasterizer grid of tile edge 1 << tshift (a tile is
+// masked when it holds a masked pixel).
+cudaError_t launch_raster_mask(const uint8_t *roi, int W, int H, int tshift, uint8_t *rmask, cudaStream_t s);
 // Warp, edge ROIs, hole classification and gap filling (writes rgb_aff and cls).
 cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
                                  const float *rgb_dom, const float *depth_dom, const float *trans_dom,

@@ -29,8 +29,9 @@ __global__ void setup_cams_kernel(PoseArgs pa, CamBlock *cams) {
     }
     c.fx = (float)pa.fx; c.fy = (float)pa.fy; c.cx = (float)pa.cx; c.cy = (float)pa.cy;
     c.W = pa.W; c.H = pa.H;
-    c.tiles_x = (pa.W + kTile - 1) / kTile;
-    c.tiles_y = (pa.H + kTile - 1) / kTile;
+    c.tshift = pa.tshift;
+    c.tiles_x = (pa.W + (1 << pa.tshift) - 1) >> pa.tshift;
+    c.tiles_y = (pa.H + (1 << pa.tshift) - 1) >> pa.tshift;
   }
   // A parallel rig (equal orientation, baseline in the image plane, Sec. 4.2):
   // both cameras measure the same depth, z_aff = z_dom in exact arithmetic. The
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
       const int py0 = ymin <= 0.f ? 0 : (int)ceilf(ymin);
       const int py1 = ymax >= c.H - 1.f ? c.H - 1 : (int)floorf(ymax);
       if (px0 <= px1 && py0 <= py1) {
-        rect = make_ushort4(px0 / kTile, py0 / kTile, px1 / kTile, py1 / kTile);
+        rect = make_ushort4(px0 >> c.tshift, py0 >> c.tshift, px1 >> c.tshift, py1 >> c.tshift);
         count = (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
       }
     }

@@ -1,0 +1,407 @@
+// Persistent per-tile front-to-back alpha blending with the joint depth proxy.
+//
+// Paper: Sec. 3.1 Stage 1 - every contributing surfel gets the weight
+// w_i = alpha_i T_i, and the same weight accumulates the colour C = sum c_i w_i
+// and the depth proxy D = sum d_i w_i in one pass (no separate depth pass).
+// Sec. 3.3 (Eq. 2 and the ray-splat intersection) gives alpha.
+//
+// One launch serves up to kRasterFrames (frame, eye) images - one eye of one
+// frame, or one eye of every frame of a batch of scenes with different surfel
+// counts and resolutions. The grid fills the SMs once; every CTA takes work
+// items, (frame, tile) pairs numbered frame by frame, from a device counter
+// until none is left, so the heavy tiles of one frame overlap the light tiles of
+// the others and no CTA is launched per tile. A frame either offers every tile
+// of its grid or a device list of tiles (the ROI tiles of a masked binning).
+//
+// A CTA renders one TS x TS tile with TS^2 / PIX threads; every thread blends
+// PIX pixels of one column, TS / PIX rows apart. The homogeneous plane point p
+// of a pixel is affine in the pixel offset (dx, dy) from the projected centre;
+// the thread forms the dx terms once per surfel and adds the dy terms per pixel
+// with three FMAs, so each surfel record read from shared memory serves PIX
+// evaluations, and a pixel's arithmetic depends on its position only - not on
+// the tile edge or block shape. The tile's depth-sorted surfel ids are
+// consumed in batches of BATCH whose 64-byte records are staged in shared
+// memory (structure of arrays: one broadcast float4 per field); cp.async
+// double-buffers the next batch behind the current one. A tile ends as soon as
+// all its pixels have terminated (__syncthreads_count). The result of a pixel
+// does not depend on TS, PIX or BATCH: a tile's list holds every surfel whose
+// support reaches any pixel centre of the tile, in depth order, and the others
+// contribute nothing to its pixels.
+#include "gs_internal.cuh"
+
+namespace gs {
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// 1 / (2 ln 2): log2(o Ghat) = (r_c^2 - rho) / (2 ln 2) + log2(1/255)
+constexpr float kHalfLog2e = 0.72134752044448170f;
+
+template <int TS, int PIX, int BATCH, bool COUNT>
+__global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_constant__ RasterTable tab,
+                                                               uint32_t *__restrict__ queue) {
+  constexpr int NT = TS * TS / PIX;  // threads
+  constexpr int RS = TS / PIX;       // rows between a thread's pixels
+  static_assert(NT % 32 == 0 && PIX <= 8, "block shape");
+  __shared__ float4 s0[2][BATCH], s1[2][BATCH], s2[2][BATCH], s3[2][BATCH];
+  __shared__ uint32_t s_first[kRasterFrames + 1];  // first work item of every frame
+  __shared__ uint32_t s_item[2];                   // double-buffered: one barrier per item
+
+  if (threadIdx.x < 32) {
+    const int f = threadIdx.x;
+    uint32_t c = 0;
+    if (f < tab.n) {
+      const RasterFrame &fr = tab.f[f];
+      c = (uint32_t)fr.ntiles;
+      if (fr.items) c = min(c, *fr.n_items);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, c, o);
+      if (f >= o) c += y;
+    }
+    s_first[f + 1] = c;
+    if (f == 0) s_first[0] = 0u;
+  }
+  const int lx = threadIdx.x % TS, ly = threadIdx.x / TS;
+
+  if (threadIdx.x == 0) s_item[0] = atomicAdd(queue, 1u);
+  for (int it = 0;; it ^= 1) {
+    // orders the item (and, the first time, s_first) before its reads, and every
+    // read of the previous tile's shared records before this tile's staging
+    __syncthreads();
+    const uint32_t g = s_item[it];
+    if (g >= s_first[tab.n]) break;  // CTA-uniform
+    int f = 0;
+    while (f + 1 < tab.n && s_first[f + 1] <= g) ++f;
+    const RasterFrame &fr = tab.f[f];
+    const uint32_t k = g - s_first[f];
+    const int tile = fr.items ? (int)fr.items[k] : (int)k;
+
+    const int W = fr.W, H = fr.H;
+    const int px = (tile % fr.tiles_x) * TS + lx;
+    const int py = (tile / fr.tiles_x) * TS + ly;  // first of rows py, py + RS, ...
+    const uint2 rg = fr.ranges[tile];
+    const int rtx = (W + kTile - 1) / kTile;
+
+    const float fx = (float)px;
+    float fy[PIX];  // the thread's pixel rows
+    float T[PIX], C0[PIX], C1[PIX], C2[PIX], D[PIX];
+    unsigned live = 0;  // bit k: pixel k still blending
+#pragma unroll
+    for (int q = 0; q < PIX; ++q) {
+      T[q] = 1.f; C0[q] = C1[q] = C2[q] = D[q] = 0.f;
+      const int y = py + RS * q;
+      fy[q] = (float)y;
+      bool on = px < W && y < H;
+      if (on && fr.roi) on = fr.roi[(y / kTile) * rtx + px / kTile] != 0;
+      if (on) live |= 1u << q;
+    }
+    const unsigned wmask = live;  // pixels this thread writes
+    unsigned npairs = 0, ncontrib = 0;
+
+    auto stage = [&](int buf, uint32_t b0) {
+      for (int slot = threadIdx.x; slot < BATCH; slot += NT) {
+        const uint32_t i = b0 + (uint32_t)slot;
+        if (i < rg.y) {
+          const uint32_t id = fr.ids[i];
+          if (id < fr.n_rec) {
+            const float4 *r = fr.rec + 4 * (size_t)id;
+            cp_async16(&s0[buf][slot], r + 0);
+            cp_async16(&s1[buf][slot], r + 1);
+            cp_async16(&s2[buf][slot], r + 2);
+            cp_async16(&s3[buf][slot], r + 3);
+          } else {  // never expected; a record that cannot contribute keeps reads in bounds
+            s0[buf][slot] = make_float4(0.f, 0.f, -1.f, 1.f);
+            s1[buf][slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+            s2[buf][slot] = make_float4(1.f, 0.f, 0.f, 0.f);
+            s3[buf][slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+          }
+        }
+      }
+      cp_async_commit();
+    };
+
+    int buf = 0;
+    if (rg.x < rg.y) stage(0, rg.x);
+    for (uint32_t b0 = rg.x; b0 < rg.y; b0 += BATCH, buf ^= 1) {
+      cp_async_wait_all();
+      // barrier: the batch in `buf` is visible to all, and every thread has
+      // finished reading the other buffer, which the prefetch below overwrites
+      if (__syncthreads_count(live == 0u) == NT) break;
+      if (b0 + BATCH < rg.y) stage(buf ^ 1, b0 + BATCH);
+      const int nb = (int)min((uint32_t)BATCH, rg.y - b0);
+      for (int j = 0; j < nb && live; ++j) {
+        const float4 a = s0[buf][j];
+        const float4 b = s1[buf][j];
+        const float4 c = s2[buf][j];
+        // homogeneous plane point p = (dx b.x + dy b.z, dx b.y + dy b.w,
+        // c.x + dx c.y + dy c.z): the column's dx terms, then dy per pixel
+        const float dx = fx - a.x;
+        const float px0 = dx * b.x, py0 = dx * b.y, pz0 = fmaf(dx, c.y, c.x);
+        const float dx2 = dx * dx;
+        float dyv[PIX], qxv[PIX], qyv[PIX], qzv[PIX];  // independent per pixel: issued back to back
+#pragma unroll
+        for (int q = 0; q < PIX; ++q) {
+          dyv[q] = fy[q] - a.y;
+          qxv[q] = fmaf(dyv[q], b.z, px0);
+          qyv[q] = fmaf(dyv[q], b.w, py0);
+          qzv[q] = fmaf(dyv[q], c.z, pz0);
+        }
+#pragma unroll
+        for (int q = 0; q < PIX; ++q) {
+          if (live & (1u << q)) {
+            const float dyk = dyv[q], qx = qxv[q], qy = qyv[q];
+            const float iq = rcp_approx(qzv[q]);
+            const float u = qx * iq, v = qy * iq;
+            const float rho3 = fmaf(u, u, v * v);
+            const float h = fmaf(dyk, dyk, dx2);
+            const float rho2 = h + h;  // low-pass term 2 |x - c|^2, same exponent units
+            const float rho = fminf(rho3, rho2);
+            if (COUNT) ++npairs;
+            if (rho <= a.z) {  // alpha >= 1/255
+              const float alpha = fminf(kAlphaMax, ex2_approx(fmaf(a.z - rho, kHalfLog2e, kLog2AlphaMin)));
+              const float Tn = fmaf(-T[q], alpha, T[q]);
+              if (Tn < kTMin) {
+                live &= ~(1u << q);
+              } else {
+                const float4 d = s3[buf][j];
+                const float z = rho3 <= rho2 ? fmaf(c.w, u, fmaf(d.x, v, a.w)) : a.w;
+                const float w = alpha * T[q];
+                if (COUNT) ++ncontrib;
+                C0[q] = fmaf(w, d.y, C0[q]);
+                C1[q] = fmaf(w, d.z, C1[q]);
+                C2[q] = fmaf(w, d.w, C2[q]);
+                D[q] = fmaf(w, z, D[q]);
+                T[q] = Tn;
+              }
+            }
+          }
+        }
+      }
+    }
+    cp_async_wait_all();
+    // the next item: its round trip overlaps the output stores below
+    uint32_t next = 0;
+    if (threadIdx.x == 0) next = atomicAdd(queue, 1u);
+
+    const size_t hw = (size_t)W * H;
+    float lo = 3.0e38f, hi = 0.f;
+#pragma unroll
+    for (int q = 0; q < PIX; ++q) {
+      if (!(wmask & (1u << q))) continue;
+      const size_t p = (size_t)(py + RS * q) * W + px;
+      fr.rgb[p] = fmaf(T[q], fr.bg[0], C0[q]);
+      fr.rgb[hw + p] = fmaf(T[q], fr.bg[1], C1[q]);
+      fr.rgb[2 * hw + p] = fmaf(T[q], fr.bg[2], C2[q]);
+      if (fr.depth) fr.depth[p] = D[q];
+      if (fr.trans) fr.trans[p] = T[q];
+      if (fr.cls) fr.cls[p] |= (uint8_t)kClsRender;
+      if (1.f - T[q] >= 0.5f) {
+        // range of the alpha-normalised depth D / (1 - T) over pixels with coverage >= 0.5
+        const float dh = D[q] / (1.f - T[q]);
+        lo = fminf(lo, dh);
+        hi = fmaxf(hi, dh);
+      }
+    }
+    if (fr.stats) {  // CTA-uniform
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      }
+      if ((threadIdx.x & 31) == 0 && hi > 0.f) {
+        atomicMin(&fr.ctr->dmin_bits, __float_as_uint(fmaxf(lo, 0.f)));
+        atomicMax(&fr.ctr->dmax_bits, __float_as_uint(hi));
+      }
+    }
+    if (threadIdx.x == 0) s_item[it ^ 1] = next;  // read after the next barrier
+    if (COUNT) {
+      unsigned long long v = npairs, cc = ncontrib;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+        cc += __shfl_xor_sync(0xffffffffu, cc, o);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&fr.ctr->pairs[fr.eye], v);
+        atomicAdd(&fr.ctr->contrib[fr.eye], cc);
+      }
+    }
+  }
+  // the last CTA out clears the counter and the ticket for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1u) == gridDim.x - 1) {
+      queue[0] = 0u;
+      queue[1] = 0u;
+    }
+  }
+}
+
+// ROI mask (16-pixel grid) -> rasterizer grid of tile edge 1 << tshift.
+__global__ void raster_mask_kernel(const uint8_t *__restrict__ roi, int rtx, int rty, int tx, int ty, int tshift,
+                                   uint8_t *__restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= tx * ty) return;
+  const int x = t % tx, y = t / tx;
+  uint8_t v = 0;
+  if (tshift <= 4) {
+    v = roi[(y >> (4 - tshift)) * rtx + (x >> (4 - tshift))];
+  } else {
+    const int s = 1 << (tshift - 4);
+    for (int dy = 0; dy < s; ++dy)
+      for (int dx = 0; dx < s; ++dx) {
+        const int yy = y * s + dy, xx = x * s + dx;
+        if (yy < rty && xx < rtx) v |= roi[yy * rtx + xx];
+      }
+  }
+  out[t] = v ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- host side
+
+namespace {
+
+struct Variant {
+  const void *fn;
+  int threads;
+  int occupancy;  // resident CTAs per SM, 0 until queried
+};
+
+constexpr int kShapes = 6;  // (tile, pix): (8,1) (8,2) (16,2) (16,4) (32,4) (32,8)
+constexpr int kBatches = 4; // 32 64 128 256
+
+template <int TS, int PIX, bool C>
+void fill_batches(Variant *v) {
+  v[0] = Variant{(const void *)raster_kernel<TS, PIX, 32, C>, TS * TS / PIX, 0};
+  v[1] = Variant{(const void *)raster_kernel<TS, PIX, 64, C>, TS * TS / PIX, 0};
+  v[2] = Variant{(const void *)raster_kernel<TS, PIX, 128, C>, TS * TS / PIX, 0};
+  v[3] = Variant{(const void *)raster_kernel<TS, PIX, 256, C>, TS * TS / PIX, 0};
+}
+
+struct VariantTable {
+  Variant v[2][kShapes][kBatches];
+  VariantTable() {
+    fill_batches<8, 1, false>(v[0][0]);
+    fill_batches<8, 2, false>(v[0][1]);
+    fill_batches<16, 2, false>(v[0][2]);
+    fill_batches<16, 4, false>(v[0][3]);
+    fill_batches<32, 4, false>(v[0][4]);
+    fill_batches<32, 8, false>(v[0][5]);
+    fill_batches<8, 1, true>(v[1][0]);
+    fill_batches<8, 2, true>(v[1][1]);
+    fill_batches<16, 2, true>(v[1][2]);
+    fill_batches<16, 4, true>(v[1][3]);
+    fill_batches<32, 4, true>(v[1][4]);
+    fill_batches<32, 8, true>(v[1][5]);
+  }
+};
+
+VariantTable g_variants;
+
+int shape_index(const RasterConfig &c) {
+  switch (c.tile) {
+    case 8: return c.pix == 1 ? 0 : c.pix == 2 ? 1 : -1;
+    case 16: return c.pix == 2 ? 2 : c.pix == 4 ? 3 : -1;
+    case 32: return c.pix == 4 ? 4 : c.pix == 8 ? 5 : -1;
+  }
+  return -1;
+}
+
+int batch_index(int b) { return b == 32 ? 0 : b == 64 ? 1 : b == 128 ? 2 : b == 256 ? 3 : -1; }
+
+int sm_count() {
+  static int cached[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+  if (dev < 64 && cached[dev] > 0) return cached[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (dev < 64) cached[dev] = n;
+  return n;
+}
+
+}  // namespace
+
+bool raster_config_ok(const RasterConfig &c) { return shape_index(c) >= 0 && batch_index(c.batch) >= 0; }
+
+int raster_tshift(const RasterConfig &c) { return c.tile == 8 ? 3 : c.tile == 32 ? 5 : 4; }
+
+cudaError_t launch_raster(const RasterTable &t, const RasterConfig &c, bool count_pairs, uint32_t *queue,
+                          cudaStream_t s) {
+  if (!raster_config_ok(c) || t.n < 0 || t.n > kRasterFrames) return cudaErrorInvalidValue;
+  if (t.n == 0) return cudaSuccess;
+  Variant &v = g_variants.v[count_pairs ? 1 : 0][shape_index(c)][batch_index(c.batch)];
+  if (v.occupancy <= 0) {
+    int occ = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, v.fn, v.threads, 0);
+    if (e != cudaSuccess) return e;
+    v.occupancy = occ > 0 ? occ : 1;
+  }
+  const int sms = sm_count();
+  if (sms <= 0) return cudaErrorNoDevice;
+  RasterTable arg = t;
+  void *args[2] = {(void *)&arg, (void *)&queue};
+  const cudaError_t e = cudaLaunchKernel(v.fn, dim3((unsigned)(sms * v.occupancy)), dim3((unsigned)v.threads), args,
+                                         0, s);
+  GS_LAUNCHED(1);
+  return e;
+}
+
+RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift, const uint8_t *mask, float3 bg,
+                         float *rgb, float *depth, float *trans, uint8_t *cls, bool stats) {
+  RasterFrame f;
+  const int ts = 1 << tshift;
+  f.ranges = ws.ranges;
+  f.ids = ws.ival;
+  f.rec = ws.rec[eye];
+  f.roi = (mask && tshift > 4) ? mask : nullptr;  // a 32-pixel tile may hold unmasked 16-pixel tiles
+  f.items = mask ? ws.items : nullptr;
+  f.n_items = mask ? &ws.ctr->n_items : nullptr;
+  f.rgb = rgb;
+  f.depth = depth;
+  f.trans = trans;
+  f.cls = cls;
+  f.ctr = ws.ctr;
+  f.bg[0] = bg.x;
+  f.bg[1] = bg.y;
+  f.bg[2] = bg.z;
+  f.W = W;
+  f.H = H;
+  f.tiles_x = (W + ts - 1) >> tshift;
+  f.ntiles = f.tiles_x * ((H + ts - 1) >> tshift);
+  f.tshift = tshift;
+  f.eye = eye;
+  f.stats = stats ? 1 : 0;
+  f.n_rec = (uint32_t)ws.max_surfels;
+  return f;
+}
+
+cudaError_t launch_raster_mask(const uint8_t *roi, int W, int H, int tshift, uint8_t *rmask, cudaStream_t s) {
+  const int ts = 1 << tshift;
+  const int rtx = (W + kTile - 1) / kTile, rty = (H + kTile - 1) / kTile;
+  const int tx = (W + ts - 1) >> tshift, ty = (H + ts - 1) >> tshift;
+  if (tx * ty == 0) return cudaSuccess;
+  raster_mask_kernel<<<(tx * ty + 255) / 256, 256, 0, s>>>(roi, rtx, rty, tx, ty, tshift, rmask);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restric
                                                        int32_t *__restrict__ widths, float *__restrict__ drange,
                                                        uint8_t *__restrict__ tile_mask) {
   const CamBlock &cb = *cams;
-  const int W = cb.eye[1].W, H = cb.eye[1].H, tiles_x = cb.eye[1].tiles_x;
+  const int W = cb.eye[1].W, H = cb.eye[1].H;
+  const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;  // the ROI grid
   __shared__ int sxmin, sxmax, symin, symax, sany;
   __shared__ int sstrip[16];
   float dmin = fixed_min, dmax = fixed_max;
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restric
     }
   }
   __syncthreads();
-  const int ntiles = tiles_x * cb.eye[1].tiles_y;
+  const int ntiles = tiles_x * tiles_y;
   for (int t = threadIdx.x; t < ntiles; t += blockDim.x) {
     const int x0 = (t % tiles_x) * kTile, y0 = (t / tiles_x) * kTile;
     bool in = false;

@@ -59,7 +59,31 @@ class Outputs(C.Structure):
 
 class Limits(C.Structure):
     _fields_ = [("max_surfels", C.c_int), ("max_width", C.c_int), ("max_height", C.c_int),
-                ("max_instances", C.c_int64), ("max_rects", C.c_int), ("keep_intermediates", C.c_int)]
+                ("max_instances", C.c_int64), ("max_rects", C.c_int), ("keep_intermediates", C.c_int),
+                ("min_tile", C.c_int)]
+
+
+class RasterConfig(C.Structure):
+    """Rasterizer tile edge, pixels per thread and records per shared-memory stage."""
+    _fields_ = [("tile", C.c_int), ("pix", C.c_int), ("batch", C.c_int)]
+
+    def astuple(self):
+        return (self.tile, self.pix, self.batch)
+
+
+class Frame(C.Structure):
+    """One frame of a batch (gs_frame)."""
+    _fields_ = [("scene", C.c_void_p), ("pose_dom", Pose), ("pose_aff", Pose), ("intr", Intrinsics),
+                ("out", Outputs)]
+
+
+class TuneResult(C.Structure):
+    _fields_ = [("rc", RasterConfig), ("ms", C.c_float)]
+
+
+# every valid (tile, pix, batch): the autotuner's search space
+RASTER_CONFIGS = [(t, p, b) for t, ps in ((8, (1, 2)), (16, (2, 4)), (32, (4, 8))) for p in ps
+                  for b in (32, 64, 128, 256)]
 
 
 class RepairBatch(C.Structure):
@@ -85,6 +109,8 @@ EXPORTS = {
     "gs_context_set_counting": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_context_set_raster": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig)]),
+    "gs_context_get_raster": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig)]),
     "gs_context_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "gs_context_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t),
                                     C.POINTER(C.c_int64)]),
@@ -96,6 +122,30 @@ EXPORTS = {
                                      C.POINTER(Intrinsics), C.POINTER(Outputs)]),
     "gs_warp_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Pose), C.POINTER(Pose),
                                   C.POINTER(Intrinsics), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int, C.c_void_p]),
+    "gs_batch_destroy": (C.c_int, [C.c_void_p]),
+    "gs_batch_set_raster": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig)]),
+    "gs_batch_get_raster": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig)]),
+    "gs_batch_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_batch_set_counting": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_batch_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
+    "gs_batch_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
+    "gs_batch_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "gs_render_stereo_batch": (C.c_int, [C.c_void_p, C.POINTER(Frame), C.c_int, C.c_int, C.POINTER(RoiParams)]),
+    "gs_render_two_pass_batch": (C.c_int, [C.c_void_p, C.POINTER(Frame), C.c_int]),
+    "gs_autotune_batch": (C.c_int, [C.c_void_p, C.POINTER(Frame), C.c_int, C.c_int, C.POINTER(RoiParams), C.c_int,
+                                    C.c_int, C.POINTER(TuneResult), C.c_int, C.POINTER(C.c_int),
+                                    C.POINTER(RasterConfig), C.POINTER(C.c_float)]),
+    "gs_autotune_stereo": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Pose),
+                                     C.POINTER(Intrinsics), C.c_int, C.POINTER(RoiParams), C.POINTER(Outputs), C.c_int,
+                                     C.c_int, C.POINTER(TuneResult), C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(RasterConfig), C.POINTER(C.c_float)]),
+    "gs_tune_cache_save": (C.c_int, [C.c_char_p]),
+    "gs_tune_cache_load": (C.c_int, [C.c_char_p]),
+    "gs_tune_cache_clear": (C.c_int, []),
+    "gs_tune_cache_size": (C.c_int, [C.POINTER(C.c_int)]),
+    "gs_tune_cache_put": (C.c_int, [C.c_char_p, C.POINTER(RasterConfig), C.c_float]),
+    "gs_tune_cache_get": (C.c_int, [C.c_char_p, C.POINTER(RasterConfig), C.POINTER(C.c_float)]),
     "gs_repair_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "gs_repair_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "gs_repair_features": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
@@ -182,9 +232,9 @@ class Context:
     """A renderer context: owns its workspace tensor, runs on a torch stream."""
 
     def __init__(self, max_surfels, max_width, max_height, max_instances=1 << 24, max_rects=1 << 16,
-                 keep_intermediates=False, device="cuda", stream=None):
+                 keep_intermediates=False, device="cuda", stream=None, min_tile=16):
         self.lim = Limits(int(max_surfels), int(max_width), int(max_height), int(max_instances),
-                          int(max_rects), int(bool(keep_intermediates)))
+                          int(max_rects), int(bool(keep_intermediates)), int(min_tile))
         nbytes = C.c_size_t()
         _check(lib().gs_workspace_size(C.byref(self.lim), C.byref(nbytes)), "gs_workspace_size")
         self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=device)
@@ -219,6 +269,15 @@ class Context:
 
     def set_graphs(self, on: bool):
         _check(lib().gs_context_set_graphs(self.h, int(bool(on))), "gs_context_set_graphs")
+
+    def set_raster(self, tile, pix, batch):
+        rc = RasterConfig(int(tile), int(pix), int(batch))
+        _check(lib().gs_context_set_raster(self.h, C.byref(rc)), "gs_context_set_raster")
+
+    def raster(self):
+        rc = RasterConfig()
+        _check(lib().gs_context_get_raster(self.h, C.byref(rc)), "gs_context_get_raster")
+        return rc.astuple()
 
     def set_profiling(self, on: bool):
         _check(lib().gs_context_set_profiling(self.h, int(bool(on))), "gs_context_set_profiling")
@@ -370,6 +429,157 @@ class Context:
                                         C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), C.byref(os_)),
                "gs_render_two_pass")
         return out
+
+
+def _tune_out(n, res, best, ms):
+    results = [(res[i].rc.astuple(), float(res[i].ms)) for i in range(n.value)]
+    return best.astuple(), float(ms.value), results
+
+
+def autotune_stereo(ctx, scene, pose_dom, pose_aff, cam, gap_thresh=2, roi=None, out=None, reps=5, use_cache=True,
+                    two_pass=False):
+    """Times every rasterizer configuration the context allows on this frame
+    (gs_render_stereo, or gs_render_two_pass with two_pass=True) and keeps the
+    fastest on the context: returns (best (tile, pix, batch), its median ms,
+    [(config, ms), ...]); with use_cache a cached shape is applied untimed."""
+    if out is None:
+        out = ctx.alloc_outputs(cam)
+    roi = None if two_pass else (roi if roi is not None else roi_params())
+    res = (TuneResult * 32)()
+    n, best, ms = C.c_int(), RasterConfig(), C.c_float()
+    _check(lib().gs_autotune_stereo(ctx.h, C.byref(scene.c), C.byref(pose_struct(pose_dom)),
+                                    C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), int(gap_thresh),
+                                    C.byref(roi) if roi is not None else None,
+                                    C.byref(Context._outputs_struct(out)), int(reps),
+                                    int(bool(use_cache)), res, 32, C.byref(n), C.byref(best), C.byref(ms)),
+           "gs_autotune_stereo")
+    return _tune_out(n, res, best, ms)
+
+
+class Batch:
+    """Many stereo frames per call (gs_render_stereo_batch): frame f runs in
+    slot f, a Context sized for it; each rasterizer pass is one persistent
+    launch over all frames."""
+
+    def __init__(self, contexts, stream=None):
+        self.slots = list(contexts)
+        dev = self.slots[0].device
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        arr = (C.c_void_p * len(self.slots))(*[c.h.value if isinstance(c.h, C.c_void_p) else c.h for c in self.slots])
+        h = C.c_void_p()
+        _check(lib().gs_batch_create(C.byref(h), arr, len(self.slots), C.c_void_p(self.stream.cuda_stream)),
+               "gs_batch_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().gs_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_raster(self, tile, pix, batch):
+        rc = RasterConfig(int(tile), int(pix), int(batch))
+        _check(lib().gs_batch_set_raster(self.h, C.byref(rc)), "gs_batch_set_raster")
+
+    def raster(self):
+        rc = RasterConfig()
+        _check(lib().gs_batch_get_raster(self.h, C.byref(rc)), "gs_batch_get_raster")
+        return rc.astuple()
+
+    def set_graphs(self, on: bool):
+        _check(lib().gs_batch_set_graphs(self.h, int(bool(on))), "gs_batch_set_graphs")
+
+    def set_counting(self, on: bool):
+        _check(lib().gs_batch_set_counting(self.h, int(bool(on))), "gs_batch_set_counting")
+
+    def set_profiling(self, on: bool):
+        _check(lib().gs_batch_set_profiling(self.h, int(bool(on))), "gs_batch_set_profiling")
+
+    def stage_times(self):
+        buf = (C.c_float * 8)()
+        n = C.c_int()
+        _check(lib().gs_batch_stage_times(self.h, buf, 8, C.byref(n)), "gs_batch_stage_times")
+        return [buf[i] for i in range(n.value)]
+
+    def check(self) -> int:
+        st = C.c_int()
+        _check(lib().gs_batch_check(self.h, C.byref(st)), "gs_batch_check")
+        return st.value
+
+    def check_ok(self):
+        st = self.check()
+        if st != GS_OK:
+            raise GsError(st, "device status")
+
+    @staticmethod
+    def frames_struct(frames):
+        """frames: [(DeviceScene, pose_dom, pose_aff, cam, outputs dict)]"""
+        arr = (Frame * len(frames))()
+        for i, (ds, d, a, cam, out) in enumerate(frames):
+            arr[i] = Frame(C.cast(C.pointer(ds.c), C.c_void_p), pose_struct(d), pose_struct(a), intr_struct(cam),
+                           Context._outputs_struct(out))
+        return arr
+
+    def render_stereo(self, frames, gap_thresh=2, roi=None):
+        roi = roi if roi is not None else roi_params()
+        arr = self.frames_struct(frames)
+        _check(lib().gs_render_stereo_batch(self.h, arr, len(frames), int(gap_thresh), C.byref(roi)),
+               "gs_render_stereo_batch")
+
+    def render_two_pass(self, frames):
+        arr = self.frames_struct(frames)
+        _check(lib().gs_render_two_pass_batch(self.h, arr, len(frames)), "gs_render_two_pass_batch")
+
+    def autotune(self, frames, gap_thresh=2, roi=None, reps=5, use_cache=True, two_pass=False):
+        """(best (tile, pix, batch), its median ms per call, [(config, ms), ...]);
+        two_pass=True tunes the two-pass comparator."""
+        roi = None if two_pass else (roi if roi is not None else roi_params())
+        arr = self.frames_struct(frames)
+        res = (TuneResult * 32)()
+        n, best, ms = C.c_int(), RasterConfig(), C.c_float()
+        _check(lib().gs_autotune_batch(self.h, arr, len(frames), int(gap_thresh),
+                                       C.byref(roi) if roi is not None else None, int(reps),
+                                       int(bool(use_cache)), res, 32, C.byref(n), C.byref(best), C.byref(ms)),
+               "gs_autotune_batch")
+        return _tune_out(n, res, best, ms)
+
+
+def tune_cache_save(path):
+    _check(lib().gs_tune_cache_save(os.fsencode(path)), "gs_tune_cache_save")
+
+
+def tune_cache_load(path):
+    _check(lib().gs_tune_cache_load(os.fsencode(path)), "gs_tune_cache_load")
+
+
+def tune_cache_clear():
+    _check(lib().gs_tune_cache_clear(), "gs_tune_cache_clear")
+
+
+def tune_cache_size() -> int:
+    n = C.c_int()
+    _check(lib().gs_tune_cache_size(C.byref(n)), "gs_tune_cache_size")
+    return n.value
+
+
+def tune_cache_put(key, config, ms):
+    rc = RasterConfig(*[int(v) for v in config])
+    _check(lib().gs_tune_cache_put(key.encode(), C.byref(rc), float(ms)), "gs_tune_cache_put")
+
+
+def tune_cache_get(key):
+    """(config, ms) or None"""
+    rc, ms = RasterConfig(), C.c_float()
+    s = lib().gs_tune_cache_get(key.encode(), C.byref(rc), C.byref(ms))
+    if s == GS_ERR_NOT_LOADED:
+        return None
+    _check(s, "gs_tune_cache_get")
+    return rc.astuple(), float(ms.value)
 
 
 def warp_noalloc(rgb_dom, depth_dom, trans_dom, pose_dom, pose_aff, cam, rgb_warp, depth_warp=None, hole=None,

@@ -101,8 +101,12 @@ def make_ctx(gs, scene, cam, **kw):
 # ----------------------------------------------------------------------------- Stage 1
 
 
-@pytest.mark.parametrize("which", ["small", "small_ragged", "random_sh3"])
+@pytest.mark.parametrize("which", ["small", "small_ragged", "random_sh3", "small_ragged@8,1,32",
+                                   "small_ragged@32,8,256", "random_sh3@8,2,64", "random_sh3@32,4,128"])
 def test_mono_render_matches_oracle(gs, orc, which):
+    """Default rasterizer configuration, and a few others (tile edge, pixels per
+    thread, records per stage) after '@'."""
+    which, _, cfg = which.partition("@")
     if which == "small":
         scene, cam, dom, _ = synth.workload_small()
     elif which == "small_ragged":
@@ -112,7 +116,9 @@ def test_mono_render_matches_oracle(gs, orc, which):
         scene = synth.random_scene(17, 3000, sh_degree=3, z_range=(1.0, 5.0), scale_mu=math.log(0.04))
         cam = synth.centred_camera(200, 136, 180.0)
         dom = synth.look_at((0.2, -0.1, -0.3), (0.0, 0.0, 3.0))
-    ctx = make_ctx(gs, scene, cam)
+    ctx = make_ctx(gs, scene, cam, min_tile=8)
+    if cfg:
+        ctx.set_raster(*(int(v) for v in cfg.split(",")))
     ds = gs.DeviceScene(scene)
     rgb, dep, tr = ctx.render_mono(ds, dom, cam, bg=(0.1, 0.2, 0.3))
     ctx.check_ok()

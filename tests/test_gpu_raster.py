@@ -1,0 +1,121 @@
+"""The persistent rasterizer's configurations - tile edge 8, 16 or 32 pixels,
+pixels per thread (block shape) and surfel records per shared-memory stage -
+produce the same images bit for bit. A tile's list holds every surfel that can
+reach one of its pixel centres, in depth order, so the tiling never changes
+which surfels a pixel blends or their order, and a pixel's arithmetic depends
+on its position only (the homogeneous plane point is evaluated per pixel). The
+contributed-pair count, a sum over pixels, is equal too; the evaluated-pair
+count grows with the tile edge."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2609_30741_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_30741_gb300 import build
+    build.build()
+    from paper_2609_30741_gb300 import gs as gsmod
+    return gsmod
+
+
+def _case(name):
+    if name == "small":
+        scene, cam, dom, aff = synth.workload_small()
+        return scene, cam, dom, aff
+    if name == "object_ragged":  # ragged tiles on both axes at every tile edge
+        scene = synth.scene_object_ground(1301, n=80_000)
+        cam = synth.centred_camera(650, 490, 640.0)
+        dom, aff = synth.eye_pair(synth.arc_poses()[2])
+        return scene, cam, dom, aff
+    # toed-in eyes: not a parallel rig, each eye sorts by its own depth keys
+    scene = synth.scene_object_ground(1302, n=50_000)
+    cam = synth.centred_camera(480, 360, 480.0)
+    dom = synth.look_at((-0.032, 0.0, 0.0), (0.0, 0.0, 2.0))
+    aff = synth.look_at((0.032, 0.0, 0.0), (0.0, 0.0, 2.0))
+    return scene, cam, dom, aff
+
+
+def _run(ctx, ds, dom, aff, cam):
+    ctx.set_counting(True)
+    o = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
+    ev, co = ctx.pair_counts()
+    t = ctx.render_two_pass(ds, dom, aff, cam)
+    m = ctx.render_mono(ds, aff, cam, bg=(0.1, 0.2, 0.3))
+    ctx.check_ok()
+    ctx.set_counting(False)
+    imgs = {k: v.clone() for k, v in o.items() if k in ("rgb_dom", "depth_dom", "trans_dom", "rgb_aff", "cls_aff",
+                                                         "edge_widths", "roi_count")}
+    imgs.update(tp_dom=t["rgb_dom"].clone(), tp_aff=t["rgb_aff"].clone(), mono=m[0].clone(), mono_d=m[1].clone(),
+                mono_t=m[2].clone())
+    return imgs, ev, co
+
+
+@pytest.mark.parametrize("case", ["small", "object_ragged", "toed_in"])
+def test_every_raster_config_is_bit_identical(gs, case):
+    scene, cam, dom, aff = _case(case)
+    ds = gs.DeviceScene(scene)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24, min_tile=8)
+    assert ctx.raster() == (16, 4, 128)
+    ref, ev_ref, co_ref = _run(ctx, ds, dom, aff, cam)
+    assert co_ref[0] > 0 and co_ref[1] > 0
+    for cfg in gs.RASTER_CONFIGS:
+        ctx.set_raster(*cfg)
+        assert ctx.raster() == cfg
+        got, ev, co = _run(ctx, ds, dom, aff, cam)
+        for k in ref:
+            assert torch.equal(ref[k], got[k]), (cfg, k)
+        assert co == co_ref, (cfg, co, co_ref)
+        assert ev[0] >= co[0] and ev[1] >= co[1]
+
+
+def test_tile_edge_orders_the_evaluated_pairs(gs):
+    scene, cam, dom, aff = _case("object_ragged")
+    ds = gs.DeviceScene(scene)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24, min_tile=8)
+    ev = {}
+    for t, p in ((8, 2), (16, 4), (32, 8)):
+        ctx.set_raster(t, p, 128)
+        _, e, _ = _run(ctx, ds, dom, aff, cam)
+        ev[t] = e[0]
+    assert ev[8] < ev[16] < ev[32], ev
+
+
+def test_invalid_raster_configs_are_rejected(gs):
+    ctx = gs.Context(1000, 128, 96, max_instances=1 << 16)  # min_tile 16
+    for bad in ((8, 2, 128), (16, 3, 128), (16, 4, 100), (32, 2, 64), (12, 4, 128), (16, 4, 512)):
+        with pytest.raises(gs.GsError):
+            ctx.set_raster(*bad)
+    ctx.set_raster(32, 4, 64)
+    assert ctx.raster() == (32, 4, 64)
+    with pytest.raises(gs.GsError):  # a context sized for 32-pixel tiles cannot run smaller ones
+        gs.Context(1000, 128, 96, max_instances=1 << 16, min_tile=32).set_raster(16, 4, 128)
+    with pytest.raises(gs.GsError):  # 8-pixel tiles: at most 512 tile columns
+        gs.Context(1000, 4104, 96, max_instances=1 << 16, min_tile=8)
+
+
+def test_masked_pass_at_tile_32_writes_only_roi_tiles(gs):
+    """With 32-pixel tiles the ROI pass renders whole 32-pixel tiles but writes
+    only the pixels of the ROI's 16-pixel tiles; the re-rendered class bit marks
+    exactly the 16-pixel ROI tiles."""
+    scene, cam, dom, aff = _case("object_ragged")
+    ds = gs.DeviceScene(scene)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24, min_tile=8)
+    ctx.set_raster(32, 8, 128)
+    o = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
+    ctx.check_ok()
+    mask, _ = ctx.buffer(gs.BUF_TILE_MASK, torch.uint8)
+    tx, ty = math.ceil(cam.width / 16), math.ceil(cam.height / 16)
+    m = mask[:tx * ty].view(ty, tx).bool()
+    rendered = (o["cls_aff"] & gs.CLS_RENDER) > 0
+    expect = m.repeat_interleave(16, 0).repeat_interleave(16, 1)[:cam.height, :cam.width]
+    assert 0 < int(m.sum()) < tx * ty
+    assert torch.equal(rendered, expect)
