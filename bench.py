@@ -58,7 +58,17 @@ def parse():
                     help="skip training and timing the learned-repair variant")
     ap.add_argument("--profile-once", action="store_true",
                     help="for profilers: one warm-up then one stereo and one two-pass frame, no timing")
+    ap.add_argument("--raster-stereo", default="auto",
+                    help="rasterizer tile,pix,batch of the method, or 'auto' (the autotuner's pick)")
+    ap.add_argument("--raster-two-pass", default="auto",
+                    help="rasterizer tile,pix,batch of the two-pass comparator, or 'auto'")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched 16-frame workload (4 scenes x 4 poses, one call)")
     return ap.parse_args()
+
+
+def parse_raster(text):
+    return None if text == "auto" else tuple(int(v) for v in text.split(","))
 
 
 def dist_info():
@@ -272,18 +282,35 @@ def run_ours(args):
     poses = poses[rank % len(poses):] + poses[: rank % len(poses)]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 27, device=dev)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 27, device=dev, min_tile=8)
     ds = gs.DeviceScene(scene, device=dev)
     out = ctx.alloc_outputs(cam)
     out2 = ctx.alloc_outputs(cam, with_cls=False)
     roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
+    # rasterizer configuration of each arm: the autotuner's pick on the first
+    # pose (untimed; every configuration renders the same images), unless given
+    rc = {"stereo": parse_raster(args.raster_stereo), "two_pass": parse_raster(args.raster_two_pass)}
+    tuning = {}
+    for arm in ("stereo", "two_pass"):
+        if rc[arm] is None:
+            d, a = poses[0]
+            best, ms, res = gs.autotune_stereo(ctx, ds, d, a, cam, gap_thresh=2, roi=roi,
+                                               out=out if arm == "stereo" else out2, reps=5, use_cache=False,
+                                               two_pass=arm == "two_pass")
+            rc[arm] = best
+            tuning[arm] = {"best": list(best), "best_ms": ms,
+                           "default_ms": dict((tuple(c), t) for c, t in res).get((16, 4, 128)),
+                           "all_ms": {",".join(map(str, c)): round(t, 4) for c, t in res}}
+
     def stereo(k):
+        ctx.set_raster(*rc["stereo"])
         d, a = poses[k % len(poses)]
         ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
 
     def two_pass(k):
+        ctx.set_raster(*rc["two_pass"])
         d, a = poses[k % len(poses)]
         ctx.render_two_pass(ds, d, a, cam, out=out2)
 
@@ -378,13 +405,13 @@ def run_ours(args):
     pk, pk_kind = peaks()
     sm_mhz_peak = float(pk.get("sm_max_mhz", 2070.0))
     blend_ms = st_stereo[2]
-    pix = ctx.raster()[1]
+    pix = rc["stereo"][1]
     ops = (OPS_EVAL_PIXEL + OPS_EVAL_COLUMN / pix) * float(np.mean(pairs_eval)) + \
         OPS_CONTRIB * float(np.mean(pairs_contrib))
     achieved = ops / (blend_ms * 1e-3) / 1e9
     peak_gops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz_peak * 1e6 / 1e9
     prof_traffic = None
-    pf = os.path.join(ROOT, "profiles", "blend_object500k.md")
+    pf = os.path.join(ROOT, "profiles", "raster_" + "x".join(map(str, rc["stereo"])) + "_object500k.md")
     if os.path.exists(pf):  # dram read + write bytes of one ncu-captured launch of this blend kernel
         for ln in open(pf):
             if ln.startswith("traffic_bytes_per_launch ="):
@@ -403,9 +430,14 @@ def run_ours(args):
         except Exception as ex:  # the CPU baseline is reported, not required
             cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
 
-    learned = None
+    learned, weights = None, None
     if not args.no_learned:
-        learned = run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev)
+        learned, weights = run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc)
+    batched = None
+    if not args.no_batched and ws_ == 1:
+        del ds, out, out2
+        torch.cuda.empty_cache()
+        batched = run_batched(args, dev, flush, weights)
 
     line = {
         "metric": METRIC, "value": ms_job, "unit": "ms", "n_gpus": ws_, "steps": args.steps,
@@ -423,12 +455,16 @@ def run_ours(args):
         "clocks": clocks,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches_stereo),
-        "roofline": {"bound": "alu", "kernel": "blend (dominant eye)", "achieved": achieved, "peak": peak_gops,
+        "raster": {"stereo": list(rc["stereo"]), "two_pass": list(rc["two_pass"]),
+                   "chosen_by": "autotuner" if tuning else "command line", "tuning": tuning},
+        "roofline": {"bound": "alu", "kernel": "raster_kernel<" + ",".join(map(str, rc["stereo"])) + "> (dominant eye)",
+                     "achieved": achieved, "peak": peak_gops,
                      "unit": "Gop/s", "frac": achieved / peak_gops, "traffic": prof_traffic,
                      "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz_peak:.0f} MHz ({pk_kind} max clock)",
                      "ops_per_launch": ops, "launch_ms": blend_ms},
         "cpu_baseline": cpu,
         "learned": learned,
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -436,10 +472,11 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev):
+def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
     """The learned-repair variant: the network is trained by the library's own
     kernels on pairs from other seeds of the same scene distribution, then the
-    stereo frame runs with repair_mode = 1 (gate threshold 0.5)."""
+    stereo frame runs with repair_mode = 1 (gate threshold 0.5). Returns the
+    report and the trained weights."""
     import torch
     from paper_2609_30741_gb300 import gs, repair_train as T
     t0 = time.time()
@@ -457,6 +494,7 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev):
         roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1, repair_mode=mode, gate_tau=0.5)
 
         def stereo(k):
+            ctx.set_raster(*rc["stereo"])
             d, a = poses[k % len(poses)]
             ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
 
@@ -465,6 +503,7 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev):
             stereo(k)
             cls = out["cls_aff"].clone()
             d, a = poses[k]
+            ctx.set_raster(*rc["two_pass"])
             ctx.render_two_pass(ds, d, a, cam, out=out2)
             ctx.check_ok()
             ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
@@ -487,6 +526,112 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev):
                        "loss_first_last": [hist[0][1], hist[-1][1]],
                        "data": "object-scene seeds 7000-7003, 6 random head poses each (held out from "
                                "the bench scene and poses)"}
+    return res, w
+
+
+def run_batched(args, dev, flush, weights):
+    """The batched workload: 16 stereo frames (4 scenes of 200k-3M surfels x 4
+    poses, 1280x720 to 2048x1536) in one gs_render_stereo_batch call, against the
+    two-pass comparator in the same batched mode; plain and learned repair side
+    by side. Each arm runs with the autotuner's pick for it."""
+    import torch
+    from paper_2609_30741_gb300 import gs, synth
+    t0 = time.time()
+    spec = synth.workload_batched()
+    scenes = [gs.DeviceScene(sc, device=dev) for sc, _, _ in spec]
+    ctxs, frames, frames2 = [], [], []
+    ws_bytes = 0
+    for k, (sc, cam, pairs) in enumerate(spec):
+        inst = 1 << (27 if sc.n > 2_000_000 else 26 if sc.n > 600_000 else 25)
+        for d, a in pairs:
+            ctx = gs.Context(sc.n, cam.width, cam.height, max_instances=inst, device=dev, min_tile=16)
+            ws_bytes += ctx.workspace.numel()
+            ctxs.append(ctx)
+            frames.append((scenes[k], d, a, cam, ctx.alloc_outputs(cam)))
+            frames2.append((scenes[k], d, a, cam, ctx.alloc_outputs(cam, with_cls=False)))
+    b = gs.Batch(ctxs)
+    setup_s = time.time() - t0
+    roi_plain = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1)
+    roi_learned = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1, repair_mode=1, gate_tau=0.5)
+    if weights is not None:
+        for c in ctxs:
+            c.repair_load(weights)
+    stream = torch.cuda.current_stream(dev)
+
+    tuned = {}
+    t1 = time.time()
+    tuned["stereo"] = b.autotune(frames, gap_thresh=2, roi=roi_plain, reps=3, use_cache=False)
+    tuned["two_pass"] = b.autotune(frames2, reps=3, use_cache=False, two_pass=True)
+    tune_s = time.time() - t1
+
+    def timed(fn, rc, steps, warmup, profile=False):
+        b.set_raster(*rc)
+        for k in range(warmup):
+            fn()
+        b.check_ok()
+        b.set_profiling(profile)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        st = []
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush.fill_(k & 255)
+            ev[k][0].record(stream)
+            fn()
+            ev[k][1].record(stream)
+            if profile:
+                st.append(b.stage_times())
+        torch.cuda.synchronize(dev)
+        b.set_profiling(False)
+        b.check_ok()
+        return float(np.mean([x.elapsed_time(y) for x, y in ev])), st
+
+    n = len(frames)
+    rs, rt = tuned["stereo"][0], tuned["two_pass"][0]
+    plain = lambda: b.render_stereo(frames, gap_thresh=2, roi=roi_plain)
+    learned = lambda: b.render_stereo(frames, gap_thresh=2, roi=roi_learned)
+    two = lambda: b.render_two_pass(frames2)
+    l0 = gs.kernel_launches()
+    ms_plain, _ = timed(plain, rs, args.steps, args.warmup)
+    launches = (gs.kernel_launches() - l0) // (args.steps + args.warmup)
+    ms_two, _ = timed(two, rt, args.steps, args.warmup)
+    _, st = timed(plain, rs, 4, 1, profile=True)
+    stage = np.mean(np.array(st), 0).tolist()
+    # quality per frame against the two-pass render of the same frame
+    timed(plain, rs, 1, 0)
+    timed(two, rt, 1, 0)
+    ps_plain = [psnr(f[4]["rgb_aff"], g[4]["rgb_aff"]) for f, g in zip(frames, frames2)]
+    res = {
+        "workload": "16 stereo frames in one call: 200k slab+ball (1280x720), 500k object (1600x1200), "
+                    "1.2M object (1920x1080), 3M unbounded (2048x1536), SH3, 4 head poses each",
+        "frames": n, "surfels": [sc.n for sc, _, _ in spec],
+        "raster": {"stereo": list(rs), "two_pass": list(rt), "chosen_by": "autotuner",
+                   "tuned_ms_per_call": {"stereo": tuned["stereo"][1], "two_pass": tuned["two_pass"][1]}},
+        "ms_per_call": {"stereo_plain": ms_plain, "two_pass": ms_two},
+        "ms_per_stereo_frame": {"stereo_plain": ms_plain / n, "two_pass": ms_two / n},
+        "fps": {"stereo_plain": 1e3 * n / ms_plain, "two_pass": 1e3 * n / ms_two},
+        "speedup_vs_two_pass": {"stereo_plain": ms_two / ms_plain},
+        "psnr_aff_vs_full_db": {"plain_mean": float(np.mean(ps_plain)), "plain_min": float(np.min(ps_plain))},
+        "stage_ms_stereo_plain": dict(zip(["per_frame_setup_preprocess_bin_dom", "raster_dom_all_frames",
+                                           "per_frame_warp_rois_bin_roi", "raster_roi_all_frames", "outputs"],
+                                          stage)),
+        "launches_per_call": int(launches), "raster_launches_per_call": 2,
+        "workspace_gb": ws_bytes / 2**30,
+        "l2": "flushed (256 MB write) before every timed call; the 16 frames' data exceed L2",
+        "setup_seconds": round(setup_s, 1), "tune_seconds": round(tune_s, 1),
+    }
+    if weights is not None:
+        ms_learned, _ = timed(learned, rs, args.steps, args.warmup)
+        timed(learned, rs, 1, 0)
+        ps_learned = [psnr(f[4]["rgb_aff"], g[4]["rgb_aff"]) for f, g in zip(frames, frames2)]
+        net = float(np.mean([((f[4]["cls_aff"] & gs.CLS_NET) > 0).float().mean().item() for f in frames]))
+        res["ms_per_call"]["stereo_learned"] = ms_learned
+        res["ms_per_stereo_frame"]["stereo_learned"] = ms_learned / n
+        res["fps"]["stereo_learned"] = 1e3 * n / ms_learned
+        res["speedup_vs_two_pass"]["stereo_learned"] = ms_two / ms_learned
+        res["psnr_aff_vs_full_db"].update(learned_mean=float(np.mean(ps_learned)),
+                                          learned_min=float(np.min(ps_learned)))
+        res["net_filled_pixel_share"] = net
+    b.close()
     return res
 
 

@@ -551,16 +551,17 @@ static gs_status tune_loop(cudaStream_t s, int reps, int min_tshift, Apply &&app
       if (st == GS_OK) st = call();
       int dev = GS_OK;
       if (st == GS_OK) st = check(&dev);
-      for (int r = 0; r < reps && st == GS_OK && dev == GS_OK; ++r) {
+      const bool ran = st == GS_OK && dev == GS_OK;  // (check clears the status it reports)
+      for (int r = 0; r < reps && ran && st == GS_OK; ++r) {
         if (cudaEventRecord(e0, s) != cudaSuccess) st = BFAIL(cudaGetLastError());
         if (st == GS_OK) st = call();
         if (st == GS_OK && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
                             cudaEventElapsedTime(&t[r], e0, e1) != cudaSuccess))
           st = BFAIL(cudaGetLastError());
       }
-      if (st == GS_OK) st = check(&dev);
+      if (ran && st == GS_OK) st = check(&dev);
       if (st == GS_ERR_CUDA) err = st;  // the context is unusable: stop
-      if (st == GS_OK && dev == GS_OK && reps > 0) {
+      if (ran && st == GS_OK && dev == GS_OK) {
         std::sort(t.begin(), t.end());
         ms = t[reps / 2];
         if (ms < win_ms) {

@@ -109,11 +109,13 @@ def _uniform_ball(rng, n, radius, centre):
     return d * r[:, None] + np.asarray(centre)[None, :]
 
 
-def scene_slab_ball(seed: int, n_bg: int = 16000, n_fg: int = 4000) -> Scene:
+def scene_slab_ball(seed: int, n_bg: int = 16000, n_fg: int = 4000, sh_degree: int = 0) -> Scene:
     """Small scene: a background slab of surfels (x in [-2,2], y in [-1.5,1.5],
     z in [3,4] m) and a foreground ball (radius 0.5 m at z = 1.5 m) that creates
     disocclusions. SH degree 0, RGB uniform in [0,1], opacity U(0.3, 0.99),
-    log-normal scales (mu = ln 0.02, sigma = 0.5), Gaussian-random rotations."""
+    log-normal scales (mu = ln 0.02, sigma = 0.5), Gaussian-random rotations.
+    With sh_degree > 0 the higher bands get N(0, 0.2) coefficients (as in the
+    object scene) on top of the same DC colour."""
     rng = np.random.default_rng(seed)
     bg = np.stack([rng.uniform(-2, 2, n_bg), rng.uniform(-1.5, 1.5, n_bg),
                    rng.uniform(3, 4, n_bg)], axis=1)
@@ -124,7 +126,10 @@ def scene_slab_ball(seed: int, n_bg: int = 16000, n_fg: int = 4000) -> Scene:
     scale = _lognormal_scales(rng, n)
     opacity = rng.uniform(0.3, 0.99, n)
     sh = _sh_from_uniform_rgb(rng, n)
-    return _pack(pos, quat, scale, opacity, sh, 0)
+    if sh_degree > 0:
+        K = (sh_degree + 1) ** 2
+        sh = np.concatenate([sh.reshape(n, 1, 3), rng.normal(0.0, 0.2, (n, K - 1, 3))], 1)
+    return _pack(pos, quat, scale, opacity, sh, sh_degree)
 
 
 def _plane_quats(rng, n):
@@ -253,6 +258,33 @@ def workload_object(seed: int = 1200, n: int = 500_000, pose_index: int = 0,
     cam = centred_camera(width, height, f)
     dom, aff = eye_pair(arc_poses()[pose_index])
     return scene_object_ground(seed, n), cam, dom, aff
+
+
+def workload_batched(seed: int = 1500, scale: float = 1.0):
+    """Four scenes of uneven size, each with four head poses (16 stereo frames),
+    SH degree 3, 0.064 m baseline; per scene (scene, camera, [4 pose pairs]):
+      200k slab + ball (small-scene distribution), 1280x720, f = 1500 (the small
+          camera's field of view), the head 0.1 m around the origin looking +z;
+      500k object + ground, 1600x1200, f = 1600, poses 0, 2, 5, 7 of the arc;
+      1.2M object + ground, 1920x1080, f = 1920, poses 1, 3, 4, 6 of the arc;
+      3M unbounded, 2048x1536, f = 1506 (the 2448-pixel, f = 1800 field of
+          view), orbiting at 3 m with yaw 0, 10, 20, 30 degrees.
+    `scale` shrinks every surfel count (tests)."""
+    n = lambda k: max(int(round(k * scale)), 1000)
+    fwd = [look_at((x, 0.0, 0.0), (0.0, 0.0, 3.5)) for x in (-0.1, -0.033, 0.033, 0.1)]
+    arc = arc_poses()
+    orbit = [look_at(3.0 * np.array([math.sin(math.radians(y)), 0.0, -math.cos(math.radians(y))]), (0.0, 0.0, 0.0))
+             for y in (0.0, 10.0, 20.0, 30.0)]
+    return [
+        (scene_slab_ball(seed, n(160_000), n(40_000), sh_degree=3), centred_camera(1280, 720, 1500.0),
+         [eye_pair(p) for p in fwd]),
+        (scene_object_ground(seed + 1, n(500_000)), centred_camera(1600, 1200, 1600.0),
+         [eye_pair(arc[k]) for k in (0, 2, 5, 7)]),
+        (scene_object_ground(seed + 2, n(1_200_000)), centred_camera(1920, 1080, 1920.0),
+         [eye_pair(arc[k]) for k in (1, 3, 4, 6)]),
+        (scene_unbounded(seed + 3, n(3_000_000)), centred_camera(2048, 1536, 1506.0),
+         [eye_pair(p) for p in orbit]),
+    ]
 
 
 def random_scene(seed: int, n: int, sh_degree: int = 0, z_range=(1.0, 4.0),

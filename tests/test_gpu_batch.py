@@ -224,3 +224,33 @@ def test_batch_argument_errors(gs, setup):
         b2.set_raster(8, 2, 64)  # below the slot's min_tile
     b.close()
     b2.close()
+
+
+def test_autotune_skips_configs_that_overflow(gs):
+    """A context whose instance capacity lies between the 32-pixel and the
+    16-pixel tile counts: the 16-pixel configurations overflow, are reported
+    with ms = -1, and the tuner picks a 32-pixel one."""
+    gs.tune_cache_clear()
+    scene, cam, dom, aff = synth.workload_small()
+    ds = gs.DeviceScene(scene)
+    probe = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 22)
+    counts = {}
+    for t, p in ((16, 4), (32, 8)):
+        probe.set_raster(t, p, 128)
+        probe.render_mono(ds, dom, cam)
+        probe.check_ok()
+        counts[t] = probe.buffer(gs.BUF_INST_VALS, torch.int32)[1]
+    assert counts[32] < counts[16]
+    cap = (counts[32] + counts[16]) // 2
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=cap)
+    best, ms, results = gs.autotune_stereo(ctx, ds, dom, aff, cam, reps=2, use_cache=False)
+    assert best[0] == 32 and ms > 0
+    for c, t in results:
+        assert (t > 0) == (c[0] == 32), (c, t)
+    ctx.check_ok()
+    # nothing fits: the tuner reports the overflow and keeps the old configuration
+    tiny = gs.Context(scene.n, cam.width, cam.height, max_instances=256)
+    with pytest.raises(gs.GsError) as e:
+        gs.autotune_stereo(tiny, ds, dom, aff, cam, reps=2, use_cache=False)
+    assert e.value.status == gs.GS_ERR_CAPACITY
+    assert tiny.raster() == (16, 4, 128)
