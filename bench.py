@@ -199,22 +199,32 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- oracle arm
 
 
-def oracle_sample(scene, cam, pose, k, win=48):
-    """One bounded oracle sample: the per-pixel render of a win x win window of
-    the dominant eye plus the fixed per-frame preparation, timed on the host."""
+def oracle_sample(scene, cam, pose, k, seconds=10.0):
+    """One bounded oracle sample: the per-pixel render of a square window of the
+    dominant eye (sized from a 48x48 probe so that the sample takes about
+    `seconds` of host time) plus the fixed per-frame preparation."""
     import oracle
     rng = np.random.default_rng(100 + k)
-    x0 = int(rng.integers(cam.width // 4, 3 * cam.width // 4 - win))
-    y0 = int(rng.integers(cam.height // 4, 3 * cam.height // 4 - win))
+    probe = 48
+    x0 = int(rng.integers(cam.width // 4, 3 * cam.width // 4 - probe))
+    y0 = int(rng.integers(cam.height // 4, 3 * cam.height // 4 - probe))
     t0 = time.perf_counter()
     oracle.render(scene, pose, cam, window=(x0, y0, 4, 4))
     t_small = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.render(scene, pose, cam, window=(x0, y0, probe, probe))
+    t_probe = time.perf_counter() - t0
+    per_px0 = max(t_probe - t_small, 1e-9) / (probe * probe - 16)
+    win = int(math.sqrt(max(seconds - t_small - t_probe, 0.0) / per_px0))
+    win = max(probe, min(win, cam.width // 2, cam.height // 2))
+    x0 = int(rng.integers(cam.width // 4, 3 * cam.width // 4 - win + 1))
+    y0 = int(rng.integers(cam.height // 4, 3 * cam.height // 4 - win + 1))
     t0 = time.perf_counter()
     oracle.render(scene, pose, cam, window=(x0, y0, win, win))
     t_big = time.perf_counter() - t0
     per_px = max(t_big - t_small, 1e-9) / (win * win - 16)
     prep = max(t_small - 16 * per_px, 0.0)
-    return prep, per_px, t_small + t_big
+    return prep, per_px, t_small + t_probe + t_big, win
 
 
 def oracle_frame_ms(prep, per_px, npix, roi_frac):
@@ -240,7 +250,7 @@ def run_reference(args):
     t_all = 0.0
     for k in range(args.warmup + args.steps):
         d, _ = synth.eye_pair(poses[k % len(poses)])
-        prep, per_px, t = oracle_sample(scene, cam, d, k)
+        prep, per_px, t, win = oracle_sample(scene, cam, d, k, seconds=4.0)
         t_all += t
         if k >= args.warmup:
             vals.append(oracle_frame_ms(prep, per_px, npix, roi_frac))
@@ -250,8 +260,9 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": "per step: oracle render of a 48x48 dominant-eye window plus the per-frame "
-                                       "surfel preparation, extrapolated to both eyes (dominant frame + ROI share)"},
+                             "sample": f"per step: oracle render of a {win}x{win} dominant-eye window (about 4 s "
+                                       f"of host time) plus the per-frame surfel preparation, extrapolated to both "
+                                       f"eyes (dominant frame + ROI share)"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -282,7 +293,10 @@ def run_ours(args):
     poses = poses[rank % len(poses):] + poses[: rank % len(poses)]
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 27, device=dev, min_tile=8)
+    # a profiler run keeps the device footprint small (its passes save and
+    # restore device memory): 32-pixel tiles at most 2^25 instances per eye
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << (25 if args.profile_once else 27),
+                     device=dev, min_tile=16 if args.profile_once else 8)
     ds = gs.DeviceScene(scene, device=dev)
     out = ctx.alloc_outputs(cam)
     out2 = ctx.alloc_outputs(cam, with_cls=False)
@@ -421,10 +435,10 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         try:
             import oracle
-            prep, per_px, t = oracle_sample(scene, cam, poses[0][0], 0)
+            prep, per_px, t, win = oracle_sample(scene, cam, poses[0][0], 0, seconds=10.0)
             cpu = {"value": oracle_frame_ms(prep, per_px, W * H, float(np.mean(roi_fracs))), "unit": "ms",
                    "cores": oracle.num_threads(), "kind": "oracle",
-                   "sample": f"oracle render of a 48x48 dominant-eye window + per-frame surfel preparation "
+                   "sample": f"oracle render of a {win}x{win} dominant-eye window + per-frame surfel preparation "
                              f"({t:.1f} s of CPU work), extrapolated to the dominant frame plus the measured "
                              f"ROI share of the affiliated eye"}
         except Exception as ex:  # the CPU baseline is reported, not required
