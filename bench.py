@@ -64,6 +64,10 @@ def parse():
                     help="rasterizer tile,pix,batch of the two-pass comparator, or 'auto'")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 16-frame workload (4 scenes x 4 poses, one call)")
+    ap.add_argument("--no-unbounded", action="store_true",
+                    help="skip the unbounded-scene learned-repair workload (1.5M surfels, 1920x1080)")
+    ap.add_argument("--no-hmd", action="store_true",
+                    help="skip the headset FP8 workload (3M surfels, 2448x2448, 120-frame trajectory)")
     return ap.parse_args()
 
 
@@ -447,11 +451,17 @@ def run_ours(args):
     learned, weights = None, None
     if not args.no_learned:
         learned, weights = run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc)
-    batched = None
-    if not args.no_batched and ws_ == 1:
+    batched = unbounded = hmd = None
+    if ws_ == 1:
         del ds, out, out2
         torch.cuda.empty_cache()
-        batched = run_batched(args, dev, flush, weights)
+        if not args.no_batched:
+            batched = run_batched(args, dev, flush, weights)
+        if not args.no_unbounded and not args.no_learned:
+            unbounded, w_unb, calib = run_unbounded(args, dev, flush)
+            if not args.no_hmd:
+                hmd = run_hmd(args, dev, flush, w_unb, calib)
+            del calib
 
     line = {
         "metric": METRIC, "value": ms_job, "unit": "ms", "n_gpus": ws_, "steps": args.steps,
@@ -479,6 +489,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "learned": learned,
         "batched": batched,
+        "unbounded_learned": unbounded,
+        "hmd_fp8": hmd,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -646,6 +658,148 @@ def run_batched(args, dev, flush, weights):
                                           learned_min=float(np.min(ps_learned)))
         res["net_filled_pixel_share"] = net
     b.close()
+    return res
+
+
+def run_unbounded(args, dev, flush):
+    """The unbounded-scene learned repair (BF16): 1.5M surfels (60 % in a 1 m
+    ball, 40 % on a 10-30 m shell), 1920x1080, f = 1600, 0.064 m baseline, eight
+    head poses on a 30 degree orbit at 3 m. The network is trained by the
+    library's kernels on 24 pairs from other seeds of the same distribution.
+    Returns the report, the weights and a calibration sample (features, tiles)."""
+    import torch
+    from paper_2609_30741_gb300 import gs, synth, repair_train as T
+    t0 = time.time()
+    tctx, pairs = T.build_pairs("unbounded", 4, 6, 7100, dev)
+    w, hist, secs = T.train(tctx, pairs, 1500, 512, 1e-3, 7100, gate_weight=1.0)
+    tiles = pairs.tile_tensor()
+    calib = (pairs.feat[:8].clone(), tiles[tiles < (8 << 24)][::4].contiguous())
+    n_frames, n_tiles = pairs.n, int(tiles.numel())
+    del tctx, pairs
+    torch.cuda.empty_cache()
+    train_s = time.time() - t0
+
+    scene = synth.scene_unbounded(1300, 1_500_000)
+    cam = synth.centred_camera(1920, 1080, 1600.0)
+    poses = [synth.eye_pair(synth.look_at(3.0 * np.array([math.sin(math.radians(y)), 0.0, -math.cos(math.radians(y))]),
+                                          (0.0, 0.0, 0.0))) for y in np.linspace(-15.0, 15.0, 8)]
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 27, device=dev)
+    ds = gs.DeviceScene(scene, device=dev)
+    out, out2 = ctx.alloc_outputs(cam), ctx.alloc_outputs(cam, with_cls=False)
+    ctx.repair_load(w)
+    ctx.repair_calibrate_fp8(*calib)
+    stream = torch.cuda.current_stream(dev)
+    rois = {"plain": gs.roi_params(), "learned_bf16": gs.roi_params(repair_mode=1, gate_tau=0.5),
+            "learned_fp8": gs.roi_params(repair_mode=2, gate_tau=0.5)}
+    d0, a0 = poses[0]
+    rc_s = gs.autotune_stereo(ctx, ds, d0, a0, cam, roi=rois["plain"], out=out, reps=5, use_cache=False)[0]
+    rc_t = gs.autotune_stereo(ctx, ds, d0, a0, cam, out=out2, reps=5, use_cache=False, two_pass=True)[0]
+
+    def run(fn, steps, warmup):
+        for k in range(warmup):
+            fn(k)
+        ctx.check_ok()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        for k in range(steps):
+            flush.fill_(k & 255)
+            ev[k][0].record(stream)
+            fn(warmup + k)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ctx.check_ok()
+        return float(np.mean([x.elapsed_time(y) for x, y in ev]))
+
+    def two(k):
+        ctx.set_raster(*rc_t)
+        d, a = poses[k % 8]
+        ctx.render_two_pass(ds, d, a, cam, out=out2)
+
+    res = {"workload": "unbounded 1.5M surfels (1 m ball + 10-30 m shell), SH3, 1920x1080, f=1600, 0.064 m "
+                       "baseline, 8 poses on a 30 deg orbit at 3 m",
+           "raster": {"stereo": list(rc_s), "two_pass": list(rc_t), "chosen_by": "autotuner"},
+           "two_pass_ms": run(two, args.steps, args.warmup)}
+    for name, roi in rois.items():
+        def stereo(k, roi=roi):
+            ctx.set_raster(*rc_s)
+            d, a = poses[k % 8]
+            ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+        ms = run(stereo, args.steps, args.warmup)
+        ps, roi_fr, net_fr = [], [], []
+        for k in range(8):
+            stereo(k)
+            cls = out["cls_aff"].clone()
+            two(k)
+            ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
+            roi_fr.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
+            net_fr.append(((cls & gs.CLS_NET) > 0).float().mean().item())
+        ctx.check_ok()
+        res[name] = {"ms_per_stereo_frame": ms, "speedup_vs_two_pass": res["two_pass_ms"] / ms,
+                     "psnr_aff_vs_full_db": float(np.mean(ps)), "psnr_min_db": float(np.min(ps)),
+                     "roi_pixel_share": float(np.mean(roi_fr)), "net_filled_pixel_share": float(np.mean(net_fr))}
+    res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "seconds": round(train_s, 1),
+                       "loss_first_last": [hist[0][1], hist[-1][1]],
+                       "data": "unbounded-distribution seeds 7100-7103 (1.5M surfels each), 6 random head poses "
+                               "each, 1920x1080"}
+    return res, w, calib
+
+
+def run_hmd(args, dev, flush, weights, calib):
+    """The headset workload: 3M surfels of the unbounded distribution, 2448x2448
+    per eye, f = 1800, 0.064 m baseline, a 120-frame head trajectory (yaw 60
+    deg/s sampled at 90 Hz, orbit of 3 m). Every frame runs the plain method, the
+    BF16 and the FP8 repair network and the two-pass comparator; per frame the
+    affiliated eye's PSNR against the full render is recorded."""
+    import torch
+    from paper_2609_30741_gb300 import gs, synth
+    scene = synth.scene_unbounded(1500, 3_000_000)
+    cam = synth.centred_camera(2448, 2448, 1800.0)
+    poses = [synth.eye_pair(p) for p in synth.yaw_trajectory(120, 60.0, 90.0, 3.0)]
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 28, device=dev)
+    ds = gs.DeviceScene(scene, device=dev)
+    ctx.repair_load(weights)
+    ctx.repair_calibrate_fp8(*calib)
+    outs = {m: ctx.alloc_outputs(cam) for m in ("plain", "bf16", "fp8")}
+    out2 = ctx.alloc_outputs(cam, with_cls=False)
+    rois = {"plain": gs.roi_params(), "bf16": gs.roi_params(repair_mode=1, gate_tau=0.5),
+            "fp8": gs.roi_params(repair_mode=2, gate_tau=0.5)}
+    d0, a0 = poses[0]
+    rc_s = gs.autotune_stereo(ctx, ds, d0, a0, cam, roi=rois["plain"], out=outs["plain"], reps=3, use_cache=False)[0]
+    rc_t = gs.autotune_stereo(ctx, ds, d0, a0, cam, out=out2, reps=3, use_cache=False, two_pass=True)[0]
+    stream = torch.cuda.current_stream(dev)
+    ms = {m: [] for m in ("plain", "bf16", "fp8", "two_pass")}
+    ps = {m: [] for m in ("plain", "bf16", "fp8")}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        flush.fill_(1)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    for k, (d, a) in enumerate(poses):
+        ctx.set_raster(*rc_t)
+        ms["two_pass"].append(timed(lambda: ctx.render_two_pass(ds, d, a, cam, out=out2)))
+        ctx.set_raster(*rc_s)
+        for m, roi in rois.items():
+            ms[m].append(timed(lambda: ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=outs[m])))
+            ps[m].append(psnr(outs[m]["rgb_aff"], out2["rgb_aff"]))
+    ctx.check_ok()
+    tp = float(np.mean(ms["two_pass"][3:]))
+    res = {"workload": "unbounded 3M surfels, SH3, 2448x2448, f=1800, 0.064 m baseline, 120 frames of a 60 deg/s "
+                       "yaw trajectory at 90 Hz (orbit 3 m)",
+           "raster": {"stereo": list(rc_s), "two_pass": list(rc_t), "chosen_by": "autotuner"},
+           "two_pass_ms": tp,
+           "note": "mean over frames 3-119 (the first three frames of each arm warm its graphs)"}
+    for m in ("plain", "bf16", "fp8"):
+        v = float(np.mean(ms[m][3:]))
+        res[m] = {"ms_per_stereo_frame": v, "speedup_vs_two_pass": tp / v,
+                  "psnr_aff_vs_full_db": {"mean": float(np.mean(ps[m])), "min": float(np.min(ps[m])),
+                                          "max": float(np.max(ps[m]))},
+                  "psnr_per_frame_db": [round(x, 3) for x in ps[m]]}
+    res["fp8_vs_bf16_psnr_gap_db"] = float(np.mean(np.array(ps["fp8"]) - np.array(ps["bf16"])))
     return res
 
 

@@ -39,7 +39,7 @@ constexpr int kHalo = 6;                // receptive-field radius of six 3x3 lay
 constexpr int kGW = kRT + 2 * kHalo;    // 28: width of the position grid
 constexpr int kNPos = 832;              // positions per activation buffer (6 M tiles + tap reach)
 constexpr int kQ = 26 * kGW;            // gradient grid: rows < 26 of any layer >= 1 output
-constexpr int kNetThreads = 128;
+constexpr int kNetThreads = 256;  // two warpgroups take alternate M tiles of the epilogue
 constexpr int kTmemCols = 256;
 
 __host__ __device__ constexpr int cin(int l) { return l == 0 ? 6 : 32; }
@@ -73,12 +73,13 @@ constexpr int kWPack8Bytes = woff8(6);
 static_assert(kWPack8Bytes == 50688, "packed FP8 weight image size");
 static_assert(poff(6) == kRepairParams, "parameter count");
 static_assert(mtiles(0) <= kMaxMT, "M tiles per layer");
+static_assert(kMaxMT <= kNetThreads / 32, "one issuing warp per M tile");
 static_assert(kMaxMT * 128 + 2 * kGW + 2 <= kNPos, "activation buffer reach");
 // shared memory of the network kernel: two activation buffers, the weight image,
 // bias, FP8 scales, barriers, reductions and calibration maxima
 __host__ __device__ constexpr size_t net_smem(bool fp8) {
   return 128 + 2 * (size_t)((fp8 ? 2 : 4) * kNPos * 16) + (fp8 ? kWPack8Bytes : kWPackBytes) + 3 * 6 * 32 * 4 +
-         8 * kMaxMT + 4 + 8 * 4 + 6 * 32 * 4 + 64;
+         8 * kMaxMT + 4 + 16 * 4 + 6 * 32 * 4 + 64;
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -119,28 +120,48 @@ __global__ void repair_pack_kernel(const float *__restrict__ master, uint16_t *_
 // at a hole outside the edge strips the method's own fill (gap interpolation,
 // else the row/column fill), 0 inside the strips.
 __global__ void __launch_bounds__(256) repair_features_kernel(const unsigned long long *__restrict__ warp,
+                                                              const uint8_t *__restrict__ cls,
                                                               const float *__restrict__ rgb_aff, int W, int H,
                                                               uint4 *__restrict__ feat) {
-  __shared__ uint8_t s_hole[32][33];
+  // The distance to the nearest hole, capped at 8, is exact and separable:
+  // d^2 = min over rows dy in [-8, 8] of dy^2 + g(dy)^2, with g the distance
+  // along that row to its nearest hole within 8 columns. The 32x32 window
+  // (tile + 8-pixel halo) is kept as one 32-bit hole mask per row; g comes
+  // from the nearest set bit on either side of the column.
+  __shared__ uint32_t s_row[32];
+  __shared__ uint8_t s_g[32][kRT];  // 9: no hole within 8 columns
   const int tx0 = blockIdx.x * kRT, ty0 = blockIdx.y * kRT;
-  for (int i = threadIdx.x; i < 32 * 32; i += 256) {
-    const int yy = ty0 - 8 + i / 32, xx = tx0 - 8 + i % 32;
-    uint8_t h = 0;
-    if (yy >= 0 && yy < H && xx >= 0 && xx < W) h = warp[(size_t)yy * W + xx] == ~0ull ? 1 : 0;
-    s_hole[i / 32][i % 32] = h;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r = wid; r < 32; r += 8) {
+    const int yy = ty0 - 8 + r, xx = tx0 - 8 + lane;
+    const bool h = yy >= 0 && yy < H && xx >= 0 && xx < W && (cls[(size_t)yy * W + xx] & kClsHole);
+    const uint32_t m = __ballot_sync(0xffffffffu, h);
+    if (lane == 0) s_row[r] = m;
   }
   __syncthreads();
-  const int x = tx0 + (threadIdx.x & 15), y = ty0 + (threadIdx.x >> 4);
+  for (int i = threadIdx.x; i < 32 * kRT; i += 256) {
+    const int r = i / kRT, c = i % kRT, bit = c + 8;
+    const uint32_t m = s_row[r];
+    const uint32_t left = m & (0xffffffffu >> (31 - bit));  // columns up to this one
+    const uint32_t right = m >> bit;                       // this column and those to the right
+    int g = 9;
+    if (left) g = min(g, bit - (31 - __clz(left)));
+    if (right) g = min(g, __ffs(right) - 1);
+    s_g[r][c] = (uint8_t)g;
+  }
+  __syncthreads();
+  const int lx = threadIdx.x & 15, ly = threadIdx.x >> 4;
+  const int x = tx0 + lx, y = ty0 + ly;
   if (x >= W || y >= H) return;
   const size_t p = (size_t)y * W + x;
   const unsigned long long k = warp[p];
   const bool hole = k == ~0ull;
   int best = 65;
-  for (int dy = -8; dy <= 8; ++dy)
-    for (int dx = -8; dx <= 8; ++dx) {
-      const int d2 = dy * dy + dx * dx;
-      if (d2 < best && s_hole[(threadIdx.x >> 4) + 8 + dy][(threadIdx.x & 15) + 8 + dx]) best = d2;
-    }
+#pragma unroll
+  for (int dy = -8; dy <= 8; ++dy) {
+    const int g = s_g[ly + 8 + dy][lx];
+    if (g <= 8) best = min(best, dy * dy + g * g);
+  }
   const float dist = fminf(sqrtf((float)best), 8.f) * 0.125f;
   const size_t hw = (size_t)W * H;
   const float r = rgb_aff[p], g = rgb_aff[hw + p], b = rgb_aff[2 * hw + p];
@@ -178,7 +199,7 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 }
 
 template <bool FP8>
-__global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
+__global__ void __launch_bounds__(kNetThreads, FP8 ? 2 : 1) repair_net_kernel(NetArgs a) {
   // BF16: 8 channels per 16-byte group, 4 groups, K = 16 per MMA (two per tap);
   // FP8: 16 channels per group, 2 groups, K = 32 per MMA (one per tap)
   constexpr int kChPerGroup = FP8 ? 16 : 8;
@@ -195,9 +216,10 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
   float *s_isx = s_sw + 6 * 32;         // FP8: reciprocal input scales
   uint64_t *mbar = (uint64_t *)(s_isx + 6 * 32);  // one per M tile of a layer
   uint32_t *s_taddr = (uint32_t *)(mbar + kMaxMT);
-  float *s_red = (float *)(s_taddr + 1);          // [4 warps][2]
-  uint32_t *s_amax = (uint32_t *)(s_red + 8);     // [6][32] calibration maxima
+  float *s_red = (float *)(s_taddr + 1);          // [8 warps][2]
+  uint32_t *s_amax = (uint32_t *)(s_red + 16);    // [6][32] calibration maxima
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int wq = wid & 3, wg = wid >> 2;  // TMEM lane quarter of the warp; its warpgroup
   const uint32_t n = load_n(a.n_tiles, a.n_max);
   if (blockIdx.x >= n) return;
 
@@ -273,43 +295,49 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
         const uint4 *srcb = (const uint4 *)in;
         for (int i = tid; i < kg * kNPos; i += kNetThreads) dst[i] = srcb[i];
       }
-      // one thread issues every MMA of the layer, committing each M tile to its
-      // own barrier, so the epilogue of tile mt overlaps the MMAs of mt + 1
-      if (tid == 0) {
+      // lane 0 of warp mt issues the MMAs of M tile mt (the M tiles are issued
+      // in parallel) and commits them to barrier mt, so every M tile's epilogue
+      // starts as soon as its own accumulator is complete
+      if (lane == 0 && wid < MT) {
+        const int mt = wid;
         const uint32_t idesc = FP8 ? umma::idesc_e4m3(128, N) : umma::idesc_bf16(128, N);
         const uint32_t wl = sW + (uint32_t)(FP8 ? woff8(l) : woff(l));
-        for (int mt = 0; mt < MT; ++mt) {
-          for (int tap = 0; tap < 9; ++tap) {
-            const int shift = (tap / 3) * kGW + (tap % 3);
-            for (int kp = 0; kp < kg / 2; ++kp) {  // two 16-byte groups per MMA
-              const uint64_t ad =
-                  umma::desc(sin + (uint32_t)(((2 * kp) * kNPos + mt * 128 + shift) * 16), kNPos * 16, 128);
-              const uint64_t bd = umma::desc(wl + (uint32_t)((tap * kg + 2 * kp) * ng * 128), ng * 128, 128);
-              if (FP8) umma::mma_e4m3(taddr + (uint32_t)(mt * N), ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
-              else umma::mma_bf16(taddr + (uint32_t)(mt * N), ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
-            }
+        const uint64_t a0 = umma::desc(sin + (uint32_t)(mt * 128 * 16), kNPos * 16, 128);
+        const uint64_t b0 = umma::desc(wl, ng * 128, 128);
+        const uint32_t d = taddr + (uint32_t)(mt * N);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int shift = (tap / 3) * kGW + (tap % 3);
+          for (int kp = 0; kp < kg / 2; ++kp) {  // two 16-byte groups per MMA
+            const uint64_t ad = umma::desc_add(a0, (uint32_t)(((2 * kp) * kNPos + shift) * 16));
+            const uint64_t bd = umma::desc_add(b0, (uint32_t)((tap * kg + 2 * kp) * ng * 128));
+            if (FP8) umma::mma_e4m3(d, ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
+            else umma::mma_bf16(d, ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
           }
-          umma::mma_commit(mbar + mt);
         }
+        umma::mma_commit(mbar + mt);
       }
       __syncwarp();
       // epilogue: accumulator rows -> scale, bias, ReLU, border zeroing -> next buffer
       const int shiftL = l + 1;  // this layer's output grid starts (l + 1) pixels in
       bool layer_ok = true;
       for (int mt = 0; mt < MT; ++mt) {
-        // the same decision on every lane of the warp (tcgen05.ld is warp-wide)
-        const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(mbar + mt, (phases >> mt) & 1u));
+        // warpgroup mt % 2 reads M tile mt; every thread tracks every barrier's phase
+        const uint32_t par = (phases >> mt) & 1u;
         phases ^= 1u << mt;
+        if ((mt & 1) != wg) continue;
+        // the same decision on every lane of the warp (tcgen05.ld is warp-wide)
+        const bool ok = __all_sync(0xffffffffu, umma::mbar_wait(mbar + mt, par));
         if (!ok) {
           layer_ok = false;
           break;
         }
         umma::fence_after_sync();
-        const int q = mt * 128 + wid * 32 + lane;
+        const int q = mt * 128 + wq * 32 + lane;
         const int r = q / kGW, c = q % kGW;
         const int y = ty0 - kHalo + shiftL + r, x = tx0 - kHalo + shiftL + c;
         const bool inside = y >= 0 && y < a.H && x >= 0 && x < a.W;
-        const uint32_t tl = taddr + ((uint32_t)(wid * 32) << 16) + (uint32_t)(mt * N);
+        const uint32_t tl = taddr + ((uint32_t)(wq * 32) << 16) + (uint32_t)(mt * N);
         const float *bl = s_bias + l * 32;
         const float *swl = s_sw + l * 32;
         if (l < 5) {
@@ -406,8 +434,11 @@ __global__ void __launch_bounds__(kNetThreads, 1) repair_net_kernel(NetArgs a) {
     }
     __syncthreads();
     if (tid == 0) {
-      const float sm = s_red[0] + s_red[2] + s_red[4] + s_red[6];
-      const float cn = s_red[1] + s_red[3] + s_red[5] + s_red[7];
+      float sm = 0.f, cn = 0.f;
+      for (int w = 0; w < kNetThreads / 32; ++w) {
+        sm += s_red[2 * w];
+        cn += s_red[2 * w + 1];
+      }
       a.gate[t] = cn > 0.f ? sm / cn : 0.f;
     }
     __syncthreads();
@@ -726,7 +757,7 @@ cudaError_t repair_pack(const Workspace &ws, cudaStream_t s) {
 
 cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_aff, uint4 *feat, cudaStream_t s) {
   const dim3 grid((W + kRT - 1) / kRT, (H + kRT - 1) / kRT);
-  repair_features_kernel<<<grid, 256, 0, s>>>(ws.warpbuf, rgb_aff, W, H, feat);
+  repair_features_kernel<<<grid, 256, 0, s>>>(ws.warpbuf, ws.cls, rgb_aff, W, H, feat);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -33,6 +33,11 @@ __device__ __forceinline__ uint64_t desc(uint32_t saddr, uint32_t lbo_bytes, uin
   return d;
 }
 
+// The same descriptor with its start address moved by `bytes` (a multiple of
+// 16): the address field holds addr >> 4 in 14 bits, and every shared-memory
+// address of a CTA (< 228 KB) fits, so the move never carries out of the field.
+__device__ __forceinline__ uint64_t desc_add(uint64_t d, uint32_t bytes) { return d + (uint64_t)(bytes >> 4); }
+
 // ---- instruction descriptor, kind::f16 (BF16 inputs, FP32 accumulate) ----
 // bits 4-5 D format (1: F32), 7-9 A format (1: BF16), 10-12 B format (1: BF16),
 // 15/16 A/B major (0: K-major), 17-22 N >> 3, 24-28 M >> 4.
