@@ -449,6 +449,14 @@ const char *gs_status_str(gs_status s);
  * calling host thread. */
 const char *gs_last_cuda_error(void);
 
+/* 1 (the default): the library launches its kernels with programmatic dependent
+ * launch, so a kernel is set up while its predecessor in the stream (or graph)
+ * drains; every kernel waits for its predecessor's completion before touching
+ * memory, so results do not depend on this switch. 0: plain launches.
+ * Process-wide; affects graphs captured afterwards. */
+void gs_set_programmatic_launch(int enable);
+int gs_programmatic_launch(void);
+
 /* Number of CUDA kernels this library has enqueued since it was loaded, over all
  * contexts and threads (diagnostics; host-side count, no synchronisation). */
 unsigned long long gs_kernel_launches(void);

@@ -7,11 +7,13 @@
 #include <new>
 
 #include "gs_context.cuh"
+#include "gs_launch.cuh"
 #include "gs_sort.cuh"
 
 namespace gs {
 
 unsigned long long g_launches = 0;
+int g_pdl = 1;
 
 namespace {
 
@@ -136,6 +138,7 @@ bool limits_ok(const gs_limits *lim) {
 }
 
 __global__ void reset_counters_kernel(Counters *c) {
+  griddep_wait();
   if (threadIdx.x == 0) {
     c->n_vis[0] = c->n_vis[1] = 0;
     c->n_inst[0] = c->n_inst[1] = 0;
@@ -279,7 +282,7 @@ cudaError_t copy_optional(gs_context *ctx, const gs_outputs *out, int W, int H) 
 }
 
 cudaError_t launch_reset_counters(Counters *c, cudaStream_t s) {
-  reset_counters_kernel<<<1, 32, 0, s>>>(c);
+  launch_k(reset_counters_kernel, 1, 32, 0, s, c);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -302,6 +305,9 @@ const char *gs_status_str(gs_status s) {
 }
 
 unsigned long long gs_kernel_launches(void) { return g_launches; }
+
+void gs_set_programmatic_launch(int enable) { g_pdl = enable ? 1 : 0; }
+int gs_programmatic_launch(void) { return g_pdl; }
 
 const char *gs_last_cuda_error(void) {
   snprintf(g_last_cuda_text, sizeof(g_last_cuda_text), "%s (%s:%d)", cudaGetErrorString(g_last_cuda_error),

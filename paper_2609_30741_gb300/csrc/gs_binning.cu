@@ -36,6 +36,7 @@
 
 #include "gs_conic.cuh"
 #include "gs_internal.cuh"
+#include "gs_launch.cuh"
 #include "gs_scan.cuh"
 #include "gs_sort.cuh"
 
@@ -84,6 +85,7 @@ __device__ __forceinline__ void row_ranges(const Conic &q, const float4 r0, int 
 // thread adds one column down the rows.
 __global__ void __launch_bounds__(1024) mask_sat_kernel(const uint8_t *__restrict__ mask, int tiles_x, int tiles_y,
                                                         uint32_t *__restrict__ sat) {
+  griddep_wait();
   const int sx = tiles_x + 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int y = wid; y <= tiles_y; y += nw) {
@@ -131,6 +133,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
                                                    uint32_t *__restrict__ row_off, uint2 *__restrict__ spans,
                                                    uint32_t cap, uint32_t *__restrict__ n_rows,
                                                    uint32_t *__restrict__ status) {
+  griddep_wait();
   const int lane = threadIdx.x & 31;
   const uint32_t n = load_n(n_ptr, n_max);
   const uint32_t j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
@@ -230,13 +233,18 @@ struct CompactApply {
   const uint32_t *zkey;
   uint32_t *key_out, *val_out;
   uint32_t *n_out;
+  uint32_t *n_rows, *n_band;  // cleared here for the row spans and band lists that follow
   __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
     if (v) {
       key_out[prefix] = zkey[i];
       val_out[prefix] = i;
     }
   }
-  __device__ void end(uint32_t, uint32_t total) const { *n_out = total; }
+  __device__ void end(uint32_t, uint32_t total) const {
+    *n_out = total;
+    *n_rows = 0u;
+    *n_band = 0u;
+  }
 };
 
 // The affiliated eye's surfels in the dominant eye's depth order: a stable filter
@@ -263,6 +271,7 @@ struct ReuseApply {
   const uint32_t *uval, *zkey;
   uint32_t *key_out, *val_out;
   uint32_t *n_out;
+  uint32_t *n_rows, *n_band;  // cleared here for the row spans and band lists that follow
   __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
     if (v) {
       const uint32_t id = uval[i];
@@ -270,8 +279,22 @@ struct ReuseApply {
       val_out[prefix] = id;
     }
   }
-  __device__ void end(uint32_t, uint32_t total) const { *n_out = total; }
+  __device__ void end(uint32_t, uint32_t total) const {
+    *n_out = total;
+    *n_rows = 0u;
+    *n_band = 0u;
+  }
 };
+
+// Keeps the dominant eye's depth order of the union for the affiliated eye.
+__global__ void keep_union_kernel(const uint32_t *__restrict__ src, const uint32_t *__restrict__ n_ptr, uint32_t n_max,
+                                  uint32_t *__restrict__ dst, uint32_t *__restrict__ n_union) {
+  griddep_wait();
+  const uint32_t n = load_n(n_ptr, n_max);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *n_union = n;
+}
 
 // ---------------------------------------------------------------- counting sort by tile
 //
@@ -330,6 +353,7 @@ struct BandArgs {
 constexpr int kListWarps = 2;
 
 __global__ void __launch_bounds__(32 * kListWarps) band_list_kernel(BandArgs a) {
+  griddep_wait();
   __shared__ uint32_t s_cnt[kListWarps][kMaxBands];
   const int lane = threadIdx.x & 31;
   const int w = (int)(blockIdx.x % (kBinWarps / kListWarps)) * kListWarps + (int)(threadIdx.x >> 5);
@@ -432,6 +456,7 @@ __device__ __forceinline__ uint32_t half16(const uint4 &v, int w) {
 }
 
 __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(BinArgs a, int mode) {
+  griddep_wait();
   extern __shared__ uint32_t s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
@@ -626,6 +651,7 @@ __global__ void bin_ranges_kernel(const uint32_t *__restrict__ offs, uint32_t nc
                                   const uint32_t *__restrict__ n_inst, uint32_t cap, uint2 *__restrict__ ranges,
                                   const uint8_t *__restrict__ mask, uint32_t *__restrict__ items,
                                   uint32_t *__restrict__ n_items) {
+  griddep_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < ntiles) {
     const uint32_t s0 = offs[(size_t)t * nch];
@@ -687,26 +713,28 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   const uint32_t cap = (uint32_t)ws.max_instances;
   const RadixScratch rs{ws.rs_table, ws.rs_offs, ws.rs_n, ws.rs_sums, ws.scan_ticket};
   if (tile_mask) {
-    mask_sat_kernel<<<1, 1024, 0, s>>>(tile_mask, tiles_x, tiles_y, ws.mask_sat);
+    launch_k(mask_sat_kernel, 1, 1024, 0, s, tile_mask, tiles_x, tiles_y, ws.mask_sat);
     GS_LAUNCHED(1);
   }
   // 1. compact the binned surfels: (depth bits, surfel id)
   const uint32_t *sat = tile_mask ? ws.mask_sat : nullptr;
   if (order == kOrderReuse) {  // the dominant order, filtered: already depth-ordered
     err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, ws.cnt[eye], ws.rect[eye], sat, tiles_x},
-                      ReuseApply{ws.uval, ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
+                      ReuseApply{ws.uval, ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
+                                 &ctr->n_band[eye]},
                       (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
   } else {
     err = scan_launch(VisibleLoad{ws.cnt[eye], order == kOrderUnion ? ws.cnt[1 - eye] : nullptr, ws.rect[eye], sat,
                                   tiles_x},
-                      CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye]},
+                      CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
+                                   &ctr->n_band[eye]},
                       (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
   }
   if (err != cudaSuccess) return err;
-  // 2. tile ranges of every rectangle row of those surfels
-  if ((err = cudaMemsetAsync(&ctr->n_rows[eye], 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
+  // 2. tile ranges of every rectangle row of those surfels (n_rows and n_band
+  // were cleared by the compaction)
   if (n > 0) {
-    rows_kernel<<<(n + 255) / 256, 256, 0, s>>>(ws.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
+    launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, ws.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
                                                 ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.row_off[eye],
                                                 ws.spans[eye], (uint32_t)ws.max_instances, &ctr->n_rows[eye],
                                                 &ctr->status);
@@ -718,12 +746,11 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
       (err = radix_sort(ws.dkey, ws.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
     return err;
   if (order == kOrderUnion && n > 0) {  // kept for the affiliated eye
-    if ((err = cudaMemcpyAsync(ws.uval, ws.dval[which], sizeof(uint32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s)) !=
-        cudaSuccess)
+    const int g = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+    if ((err = launch_k(keep_union_kernel, g, 256, 0, s, ws.dval[which], &ctr->n_vis[eye], (uint32_t)n, ws.uval,
+                        &ctr->n_union)) != cudaSuccess)
       return err;
-    if ((err = cudaMemcpyAsync(&ctr->n_union, &ctr->n_vis[eye], sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) !=
-        cudaSuccess)
-      return err;
+    GS_LAUNCHED(1);
   }
   const int nbands = (tiles_y + kBandRows - 1) / kBandRows;
   // 4. per chunk: each warp's depth-ordered (surfel, band) lists
@@ -743,8 +770,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   ba.pool_n = &ctr->n_band[eye];
   ba.lists = ws.band_lists;
   ba.status = &ctr->status;
-  if ((err = cudaMemsetAsync(&ctr->n_band[eye], 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
-  band_list_kernel<<<ws.bin_nch * (kBinWarps / kListWarps), 32 * kListWarps, 0, s>>>(ba);
+  launch_k(band_list_kernel, ws.bin_nch * (kBinWarps / kListWarps), 32 * kListWarps, 0, s, ba);
   GS_LAUNCHED(1);
   BinArgs a;
   a.n_vis = &ctr->n_vis[eye];
@@ -768,7 +794,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
     return err;
   const dim3 grid(ws.bin_nch, (unsigned)nbands);
   // 5. per-warp counts per (tile, chunk)
-  bin_kernel<<<grid, kBinThreads, bin_smem_bytes(tiles_x) / 2, s>>>(a, 0);
+  launch_k(bin_kernel, grid, kBinThreads, bin_smem_bytes(tiles_x) / 2, s, a, 0);
   GS_LAUNCHED(1);
   // 6. tile-major scan: where every (tile, chunk) run starts
   err = scan_launch(BinTableLoad{ws.bin_table, &ctr->n_vis[eye], (uint32_t)n, ws.bin_nch,
@@ -778,10 +804,10 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
                     (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, ws.scan_sums, ws.scan_ticket,
                     nullptr, s);
   if (err != cudaSuccess) return err;
-  bin_ranges_kernel<<<(ntiles + 255) / 256, 256, 0, s>>>(ws.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
+  launch_k(bin_ranges_kernel, (ntiles + 255) / 256, 256, 0, s, ws.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
                                                          ws.ranges, tile_mask, ws.items, &ctr->n_items);
   // 7. every surfel id to its slot
-  bin_kernel<<<grid, kBinThreads, bin_smem_bytes(tiles_x), s>>>(a, 1);
+  launch_k(bin_kernel, grid, kBinThreads, bin_smem_bytes(tiles_x), s, a, 1);
   GS_LAUNCHED(2);
   return cudaGetLastError();
 }

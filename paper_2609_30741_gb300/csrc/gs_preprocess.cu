@@ -3,6 +3,7 @@
 // Paper: Sec. 3.3 (2D Gaussian surfels, Eq. 1-2, ray-splat intersection),
 // Sec. 3.4 (pinhole projection, Eq. 3; poses, Eq. 4-5), Sec. 3.1 Stage 1.
 #include "gs_internal.cuh"
+#include "gs_launch.cuh"
 
 namespace gs {
 
@@ -12,6 +13,7 @@ namespace gs {
 // poses (world -> camera) and composing the relative pose between the eyes,
 // X_aff = R_aff^T R_dom X_dom + R_aff^T (t_dom - t_aff) (Eq. 4 followed by Eq. 5).
 __global__ void setup_cams_kernel(PoseArgs pa, CamBlock *cams) {
+  griddep_wait();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   CamBlock cb;
   for (int e = 0; e < 2; ++e) {
@@ -56,7 +58,7 @@ __global__ void setup_cams_kernel(PoseArgs pa, CamBlock *cams) {
 const void *setup_cams_kernel_ptr() { return (const void *)setup_cams_kernel; }
 
 cudaError_t launch_setup_cams(const PoseArgs &pa, CamBlock *cams, cudaStream_t s) {
-  setup_cams_kernel<<<1, 32, 0, s>>>(pa, cams);
+  launch_k(setup_cams_kernel, 1, 32, 0, s, pa, cams);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -130,6 +132,7 @@ __device__ __forceinline__ void sh_rgb(const float *__restrict__ c, int deg, flo
 // The intersection depth is z = M20 u + M21 v + p_z.
 __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamBlock *__restrict__ cams,
                                                          Workspace ws, int neyes) {
+  griddep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= sc.n) return;
   const float4 p4 = reinterpret_cast<const float4 *>(sc.pos)[i];
@@ -238,7 +241,7 @@ cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes
                               cudaStream_t s) {
   (void)W; (void)H;
   if (sc.n == 0) return cudaSuccess;
-  preprocess_kernel<<<(sc.n + 255) / 256, 256, 0, s>>>(sc, ws.cams, ws, neyes);
+  launch_k(preprocess_kernel, (sc.n + 255) / 256, 256, 0, s, sc, ws.cams, ws, neyes);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }

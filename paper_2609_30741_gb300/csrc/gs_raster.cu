@@ -28,6 +28,7 @@
 // support reaches any pixel centre of the tile, in depth order, and the others
 // contribute nothing to its pixels.
 #include "gs_internal.cuh"
+#include "gs_launch.cuh"
 
 namespace gs {
 
@@ -56,6 +57,7 @@ constexpr float kHalfLog2e = 0.72134752044448170f;
 template <int TS, int PIX, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_constant__ RasterTable tab,
                                                                uint32_t *__restrict__ queue) {
+  griddep_wait();
   constexpr int NT = TS * TS / PIX;  // threads
   constexpr int RS = TS / PIX;       // rows between a thread's pixels
   static_assert(NT % 32 == 0 && PIX <= 8, "block shape");
@@ -258,6 +260,7 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
 // ROI mask (16-pixel grid) -> rasterizer grid of tile edge 1 << tshift.
 __global__ void raster_mask_kernel(const uint8_t *__restrict__ roi, int rtx, int rty, int tx, int ty, int tshift,
                                    uint8_t *__restrict__ out) {
+  griddep_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= tx * ty) return;
   const int x = t % tx, y = t / tx;
@@ -359,8 +362,16 @@ cudaError_t launch_raster(const RasterTable &t, const RasterConfig &c, bool coun
   if (sms <= 0) return cudaErrorNoDevice;
   RasterTable arg = t;
   void *args[2] = {(void *)&arg, (void *)&queue};
-  const cudaError_t e = cudaLaunchKernel(v.fn, dim3((unsigned)(sms * v.occupancy)), dim3((unsigned)v.threads), args,
-                                         0, s);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.gridDim = dim3((unsigned)(sms * v.occupancy));
+  cfg.blockDim = dim3((unsigned)v.threads);
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = g_pdl ? 1 : 0;
+  const cudaError_t e = cudaLaunchKernelExC(&cfg, v.fn, args);
   GS_LAUNCHED(1);
   return e;
 }
@@ -399,7 +410,7 @@ cudaError_t launch_raster_mask(const uint8_t *roi, int W, int H, int tshift, uin
   const int rtx = (W + kTile - 1) / kTile, rty = (H + kTile - 1) / kTile;
   const int tx = (W + ts - 1) >> tshift, ty = (H + ts - 1) >> tshift;
   if (tx * ty == 0) return cudaSuccess;
-  raster_mask_kernel<<<(tx * ty + 255) / 256, 256, 0, s>>>(roi, rtx, rty, tx, ty, tshift, rmask);
+  launch_k(raster_mask_kernel, (tx * ty + 255) / 256, 256, 0, s, roi, rtx, rty, tx, ty, tshift, rmask);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -28,6 +28,7 @@
 #include <cuda_fp8.h>
 
 #include "gs_internal.cuh"
+#include "gs_launch.cuh"
 #include "gs_scan.cuh"
 #include "gs_umma.cuh"
 
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(256) repair_features_kernel(const unsigned lon
                                                               const uint8_t *__restrict__ cls,
                                                               const float *__restrict__ rgb_aff, int W, int H,
                                                               uint4 *__restrict__ feat) {
+  griddep_wait();
   // The distance to the nearest hole, capped at 8, is exact and separable:
   // d^2 = min over rows dy in [-8, 8] of dy^2 + g(dy)^2, with g the distance
   // along that row to its nearest hole within 8 columns. The 32x32 window
@@ -200,6 +202,7 @@ __device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
 
 template <bool FP8>
 __global__ void __launch_bounds__(kNetThreads, FP8 ? 2 : 1) repair_net_kernel(NetArgs a) {
+  griddep_wait();
   // BF16: 8 channels per 16-byte group, 4 groups, K = 16 per MMA (two per tap);
   // FP8: 16 channels per group, 2 groups, K = 32 per MMA (one per tap)
   constexpr int kChPerGroup = FP8 ? 16 : 8;
@@ -504,6 +507,7 @@ __global__ void __launch_bounds__(256) repair_pack8_kernel(const float *__restri
 // never saw.
 __global__ void repair_tile_flags_kernel(const uint8_t *__restrict__ cls, const uint8_t *__restrict__ tile_mask,
                                          int W, int H, uint8_t *__restrict__ flags) {
+  griddep_wait();
   const int t = blockIdx.y * gridDim.x + blockIdx.x;
   if (!tile_mask[t]) {
     if (threadIdx.x == 0) flags[t] = 0;
@@ -540,6 +544,7 @@ __global__ void repair_merge_kernel(const uint32_t *__restrict__ list, const uin
                                     const unsigned long long *__restrict__ warp, const float *__restrict__ fill,
                                     int W, int H, int tiles_x, float *__restrict__ rgb_aff,
                                     uint8_t *__restrict__ cls, uint8_t *__restrict__ tile_mask) {
+  griddep_wait();
   const uint32_t t = blockIdx.x;
   if (t >= *n_list || !(gate[t] >= logit_tau)) return;
   const uint32_t te = list[t];
@@ -757,7 +762,7 @@ cudaError_t repair_pack(const Workspace &ws, cudaStream_t s) {
 
 cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_aff, uint4 *feat, cudaStream_t s) {
   const dim3 grid((W + kRT - 1) / kRT, (H + kRT - 1) / kRT);
-  repair_features_kernel<<<grid, 256, 0, s>>>(ws.warpbuf, ws.cls, rgb_aff, W, H, feat);
+  launch_k(repair_features_kernel, grid, 256, 0, s, ws.warpbuf, ws.cls, rgb_aff, W, H, feat);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }
@@ -787,9 +792,9 @@ cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H,
   a.status = &ws.ctr->status;
   if (fp8) {  // two CTAs per SM fit the FP8 kernel's shared memory
     const uint32_t g = n_max < 304u ? (n_max < 1u ? 1u : n_max) : 304u;
-    repair_net_kernel<true><<<g, kNetThreads, net_smem(true), s>>>(a);
+    launch_k(repair_net_kernel<true>, g, kNetThreads, net_smem(true), s, a);
   } else {
-    repair_net_kernel<false><<<net_grid(n_max), kNetThreads, net_smem(false), s>>>(a);
+    launch_k(repair_net_kernel<false>, net_grid(n_max), kNetThreads, net_smem(false), s, a);
   }
   GS_LAUNCHED(1);
   return cudaGetLastError();
@@ -812,7 +817,7 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
                           bool fp8) {
   cudaError_t e;
   const int tx = (W + kRT - 1) / kRT, ty = (H + kRT - 1) / kRT, nt = tx * ty;
-  repair_tile_flags_kernel<<<dim3(tx, ty), 256, 0, s>>>(ws.cls, ws.tile_mask, W, H, ws.rp_flags);
+  launch_k(repair_tile_flags_kernel, dim3(tx, ty), 256, 0, s, ws.cls, ws.tile_mask, W, H, ws.rp_flags);
   GS_LAUNCHED(1);
   if ((e = scan_launch(TileFlagLoad{ws.rp_flags}, TileListApply{ws.rp_list, ws.rp_nlist, tx},
                        (const uint32_t *)nullptr, (uint32_t)nt, ws.scan_sums, ws.scan_ticket, nullptr, s)) !=
@@ -824,7 +829,7 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
   // sigmoid(g) >= tau  <=>  g >= log(tau / (1 - tau))
   const float tau = fminf(fmaxf(gate_tau, 1e-6f), 1.f - 1e-6f);
   const float logit_tau = logf(tau / (1.f - tau));
-  repair_merge_kernel<<<nt, 256, 0, s>>>(ws.rp_list, ws.rp_nlist, ws.rp_gate, logit_tau, ws.warpbuf, ws.rp_fill, W, H,
+  launch_k(repair_merge_kernel, nt, 256, 0, s, ws.rp_list, ws.rp_nlist, ws.rp_gate, logit_tau, ws.warpbuf, ws.rp_fill, W, H,
                                          tx, rgb_aff, ws.cls, ws.tile_mask);
   GS_LAUNCHED(1);
   return cudaGetLastError();

@@ -18,6 +18,7 @@
 //    interpolation along the shorter such run (horizontal on ties); the other
 //    holes are centre holes (4-connected components -> ROIs).
 #include "gs_internal.cuh"
+#include "gs_launch.cuh"
 #include "gs_scan.cuh"
 
 namespace gs {
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(256) warp_scatter_kernel(const CamBlock *__res
                                                            const float *__restrict__ depth,
                                                            const float *__restrict__ trans,
                                                            unsigned long long *__restrict__ buf, int W, int H) {
+  griddep_wait();
   const CamBlock &cb = *cams;
   const int64_t npix = (int64_t)W * H;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
@@ -76,6 +78,7 @@ __global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restric
                                                        float fixed_max, int32_t *__restrict__ strips,
                                                        int32_t *__restrict__ widths, float *__restrict__ drange,
                                                        uint8_t *__restrict__ tile_mask) {
+  griddep_wait();
   const CamBlock &cb = *cams;
   const int W = cb.eye[1].W, H = cb.eye[1].H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;  // the ROI grid
@@ -173,6 +176,7 @@ struct WarpView {
 __global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_t *__restrict__ strips, int gap,
                                                        int center_enabled, float *__restrict__ rgb_aff,
                                                        float *__restrict__ warp_depth, uint8_t *__restrict__ cls) {
+  griddep_wait();
   const int W = wv.W, H = wv.H;
   const int64_t npix = (int64_t)W * H;
   __shared__ int s[16];
@@ -302,11 +306,13 @@ __device__ void unite(int32_t *L, int a, int b, uint32_t *status) {
 }
 
 __global__ void cc_init_kernel(const uint8_t *__restrict__ cls, int32_t *__restrict__ L, int64_t npix) {
+  griddep_wait();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
     L[p] = (cls[p] & kClsCentre) ? (int32_t)p : -1;
 }
 
 __global__ void cc_merge_kernel(const uint8_t *__restrict__ cls, int32_t *L, int W, int H, uint32_t *status) {
+  griddep_wait();
   const int64_t npix = (int64_t)W * H;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
     if (!(cls[p] & kClsCentre)) continue;
@@ -317,6 +323,7 @@ __global__ void cc_merge_kernel(const uint8_t *__restrict__ cls, int32_t *L, int
 }
 
 __global__ void cc_flatten_kernel(int32_t *L, int64_t npix) {
+  griddep_wait();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
     if (L[p] >= 0) L[p] = find_root(L, (int)p);
 }
@@ -345,6 +352,7 @@ struct RootApply {
 
 __global__ void cc_bbox_kernel(const int32_t *__restrict__ L, const uint32_t *__restrict__ slots, int4 *rects,
                                uint32_t cap, int W, int64_t npix) {
+  griddep_wait();
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
     const int r = L[p];
     if (r < 0) continue;
@@ -362,6 +370,7 @@ __global__ void cc_bbox_kernel(const int32_t *__restrict__ L, const uint32_t *__
 // expand by m, align outward to tiles, clip; mark the tiles
 __global__ void cc_finalize_kernel(int4 *rects, const Counters *__restrict__ ctr, uint32_t cap, int W, int H, int m,
                                    int tiles_x, int tiles_y, uint8_t *__restrict__ tile_mask) {
+  griddep_wait();
   const uint32_t n = min(ctr->n_rects, cap);
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
     const int4 b = rects[s];
@@ -371,6 +380,15 @@ __global__ void cc_finalize_kernel(int4 *rects, const Counters *__restrict__ ctr
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) tile_mask[ty * tiles_x + tx] = 1;
   }
+}
+
+// Clears the warp buffer (no sample) and the ROI tile mask.
+__global__ void warp_init_kernel(unsigned long long *__restrict__ warpbuf, int64_t npix, uint8_t *__restrict__ mask,
+                                 int ntiles) {
+  griddep_wait();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride) warpbuf[i] = kNoSample;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ntiles; i += stride) mask[i] = 0;
 }
 
 static int grid_for(int64_t n, int per_block = 256) {
@@ -384,35 +402,35 @@ cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thre
   cudaError_t err;
   const int64_t npix = (int64_t)W * H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-  if ((err = cudaMemsetAsync(ws.tile_mask, 0, (size_t)tiles_x * tiles_y, s)) != cudaSuccess) return err;
-  if ((err = cudaMemsetAsync(ws.warpbuf, 0xff, sizeof(unsigned long long) * (size_t)npix, s)) != cudaSuccess)
+  if ((err = launch_k(warp_init_kernel, grid_for(npix), 256, 0, s, ws.warpbuf, npix, ws.tile_mask,
+                      tiles_x * tiles_y)) != cudaSuccess)
     return err;
-  edge_roi_kernel<<<1, 256, 0, s>>>(ws.cams, ws.ctr, roi.samples_per_edge, roi.margin, roi.depth_mode, roi.d_min,
+  launch_k(edge_roi_kernel, 1, 256, 0, s, ws.cams, ws.ctr, roi.samples_per_edge, roi.margin, roi.depth_mode, roi.d_min,
                                     roi.d_max, ws.strips, ws.widths, ws.drange, ws.tile_mask);
-  warp_scatter_kernel<<<grid_for(npix), 256, 0, s>>>(ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H);
+  launch_k(warp_scatter_kernel, grid_for(npix), 256, 0, s, ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H);
   WarpView wv{ws.warpbuf, rgb_dom, W, H, (size_t)npix};
   // the row/column fill of the remaining holes is the output when the centre step
   // is off, and the repair network's starting point in the repair modes (there
   // the ROI re-render or the network overwrites those pixels)
   const int fill_all = !roi.enable_center || roi.repair_mode != 0;
-  classify_kernel<<<grid_for(npix), 256, 0, s>>>(wv, ws.strips, gap_thresh, fill_all ? 0 : 1, rgb_aff,
+  launch_k(classify_kernel, grid_for(npix), 256, 0, s, wv, ws.strips, gap_thresh, fill_all ? 0 : 1, rgb_aff,
                                                   ws.warp_depth, ws.cls);
-  GS_LAUNCHED(3);
+  GS_LAUNCHED(4);
   return cudaGetLastError();
 }
 
 cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cudaStream_t s) {
   const int64_t npix = (int64_t)W * H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-  cc_init_kernel<<<grid_for(npix), 256, 0, s>>>(ws.cls, ws.labels, npix);
-  cc_merge_kernel<<<grid_for(npix), 256, 0, s>>>(ws.cls, ws.labels, W, H, &ws.ctr->status);
-  cc_flatten_kernel<<<grid_for(npix), 256, 0, s>>>(ws.labels, npix);
+  launch_k(cc_init_kernel, grid_for(npix), 256, 0, s, ws.cls, ws.labels, npix);
+  launch_k(cc_merge_kernel, grid_for(npix), 256, 0, s, ws.cls, ws.labels, W, H, &ws.ctr->status);
+  launch_k(cc_flatten_kernel, grid_for(npix), 256, 0, s, ws.labels, npix);
   const uint32_t cap = (uint32_t)ws.max_rects;
   cudaError_t err = scan_launch(RootLoad{ws.labels}, RootApply{ws.slots, ws.rects, cap, ws.ctr, W, H},
                                 (const uint32_t *)nullptr, (uint32_t)npix, ws.scan_sums, ws.scan_ticket, nullptr, s);
   if (err != cudaSuccess) return err;
-  cc_bbox_kernel<<<grid_for(npix), 256, 0, s>>>(ws.labels, ws.slots, ws.rects, cap, W, npix);
-  cc_finalize_kernel<<<grid_for(ws.max_rects), 256, 0, s>>>(ws.rects, ws.ctr, cap, W, H, margin, tiles_x, tiles_y,
+  launch_k(cc_bbox_kernel, grid_for(npix), 256, 0, s, ws.labels, ws.slots, ws.rects, cap, W, npix);
+  launch_k(cc_finalize_kernel, grid_for(ws.max_rects), 256, 0, s, ws.rects, ws.ctr, cap, W, H, margin, tiles_x, tiles_y,
                                                              ws.tile_mask);
   GS_LAUNCHED(5);
   return cudaGetLastError();

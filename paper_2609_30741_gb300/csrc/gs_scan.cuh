@@ -3,6 +3,7 @@
 #pragma once
 
 #include "gs_internal.cuh"
+#include "gs_launch.cuh"
 
 namespace gs {
 
@@ -49,6 +50,7 @@ template <class Load>
 __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load ld, const uint32_t *n_ptr,
                                                                    uint32_t n_max, uint32_t *sums,
                                                                    uint32_t *ticket, uint32_t *total_out) {
+  griddep_wait();
   __shared__ uint32_t smem[32];
   __shared__ uint32_t s_last;
   const uint32_t n = load_n(n_ptr, n_max);
@@ -97,6 +99,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load ld, cons
 template <class Load, class Apply>
 __global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(Load ld, Apply ap, const uint32_t *n_ptr,
                                                                   uint32_t n_max, const uint32_t *sums) {
+  griddep_wait();
   __shared__ uint32_t smem[32];
   __shared__ uint32_t vals[kScanTile];
   const uint32_t n = load_n(n_ptr, n_max);
@@ -138,12 +141,12 @@ cudaError_t scan_launch(Load ld, Apply ap, const uint32_t *n_ptr, uint32_t n_max
   const int nblocks = (int)((n_max + kScanTile - 1) / kScanTile);
   if (nblocks <= 1) {
     // one tile (or an empty result): its prefix starts at 0
-    scan_apply_kernel<<<1, kScanThreads, 0, s>>>(ld, ap, n_ptr, n_max, (const uint32_t *)nullptr);
+    launch_k(scan_apply_kernel<Load, Apply>, 1, kScanThreads, 0, s, ld, ap, n_ptr, n_max, (const uint32_t *)nullptr);
     GS_LAUNCHED(1);
     return cudaGetLastError();
   }
-  scan_reduce_kernel<<<nblocks, kScanThreads, 0, s>>>(ld, n_ptr, n_max, block_sums, ticket, total_out);
-  scan_apply_kernel<<<nblocks, kScanThreads, 0, s>>>(ld, ap, n_ptr, n_max, block_sums);
+  launch_k(scan_reduce_kernel<Load>, nblocks, kScanThreads, 0, s, ld, n_ptr, n_max, block_sums, ticket, total_out);
+  launch_k(scan_apply_kernel<Load, Apply>, nblocks, kScanThreads, 0, s, ld, ap, n_ptr, n_max, block_sums);
   GS_LAUNCHED(2);
   return cudaGetLastError();
 }

@@ -13,6 +13,7 @@
 #pragma once
 
 #include "gs_internal.cuh"
+#include "gs_launch.cuh"
 #include "gs_scan.cuh"
 
 namespace gs {
@@ -29,6 +30,7 @@ static __global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint32
                                                                      uint32_t *__restrict__ table,
                                                                      uint32_t *__restrict__ n_table,
                                                                      uint32_t *__restrict__ offs, uint32_t *ticket) {
+  griddep_wait();
   __shared__ uint32_t h[kRsThreads / 32][256];
   __shared__ uint32_t s_last, s_scan[32];
   const uint32_t n = load_n(n_ptr, n_max);
@@ -91,6 +93,7 @@ static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const 
                                                                            const uint32_t *n_ptr, uint32_t n_max,
                                                                            int shift,
                                                                            const uint32_t *__restrict__ offs) {
+  griddep_wait();
   constexpr int NW = kRsThreads / 32;
   __shared__ uint32_t s_warp[NW][256];
   __shared__ uint32_t s_local_base[256], s_global[256];
@@ -197,7 +200,7 @@ inline cudaError_t radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], 
   const bool fused = (n_max + kRsTile - 1) / kRsTile <= 32;
   int cur = 0;
   for (int p = 0; p < npass; ++p) {
-    rs_hist_kernel<<<grid, kRsThreads, 0, s>>>(keys[cur], n_ptr, n_max, 8 * p, sc.table, sc.n_table,
+    launch_k(rs_hist_kernel, grid, kRsThreads, 0, s, keys[cur], n_ptr, n_max, 8 * p, sc.table, sc.n_table,
                                                fused ? sc.offs : nullptr, sc.ticket);
     GS_LAUNCHED(1);
     if (!fused) {
@@ -205,7 +208,7 @@ inline cudaError_t radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], 
                                   sc.ticket, nullptr, s);
       if (e != cudaSuccess) return e;
     }
-    rs_scatter_kernel<<<grid, kRsThreads, 0, s>>>(keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_ptr, n_max,
+    launch_k(rs_scatter_kernel, grid, kRsThreads, 0, s, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_ptr, n_max,
                                                   8 * p, sc.offs);
     GS_LAUNCHED(1);
     cur ^= 1;

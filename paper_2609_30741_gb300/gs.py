@@ -102,6 +102,8 @@ EXPORTS = {
     "gs_kernel_launches": (C.c_ulonglong, []),
     "gs_last_cuda_error": (C.c_char_p, []),
     "gs_workspace_size": (C.c_int, [C.POINTER(Limits), C.POINTER(C.c_size_t)]),
+    "gs_set_programmatic_launch": (None, [C.c_int]),
+    "gs_programmatic_launch": (C.c_int, []),
     "gs_context_create": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(Limits), C.c_void_p, C.c_size_t, C.c_void_p]),
     "gs_context_destroy": (C.c_int, [C.c_void_p]),
     "gs_context_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
@@ -182,6 +184,15 @@ def lib():
 def kernel_launches() -> int:
     """Kernels libgs.so has enqueued since it was loaded."""
     return int(lib().gs_kernel_launches())
+
+
+def set_programmatic_launch(on: bool):
+    """Programmatic dependent launch of the library's kernels (default on)."""
+    lib().gs_set_programmatic_launch(int(bool(on)))
+
+
+def programmatic_launch() -> bool:
+    return bool(lib().gs_programmatic_launch())
 
 
 def status_str(s: int) -> str:

@@ -119,3 +119,23 @@ def test_masked_pass_at_tile_32_writes_only_roi_tiles(gs):
     expect = m.repeat_interleave(16, 0).repeat_interleave(16, 1)[:cam.height, :cam.width]
     assert 0 < int(m.sum()) < tx * ty
     assert torch.equal(rendered, expect)
+
+
+def test_programmatic_launch_changes_nothing(gs):
+    """Programmatic dependent launch only lets a kernel start its set-up early:
+    every kernel waits for its predecessor before touching memory, so frames
+    are identical with it on and off (direct launches and graph replays)."""
+    scene, cam, dom, aff = _case("object_ragged")
+    ds = gs.DeviceScene(scene)
+    res = {}
+    for on in (False, True):
+        gs.set_programmatic_launch(on)
+        assert gs.programmatic_launch() == on
+        ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24)
+        ctx.set_raster(32, 4, 64)
+        for _ in range(3):  # direct, capture, replay
+            got, _, _ = _run(ctx, ds, dom, aff, cam)
+        res[on] = got
+    gs.set_programmatic_launch(True)
+    for k in res[True]:
+        assert torch.equal(res[True][k], res[False][k]), k
