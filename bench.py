@@ -343,7 +343,7 @@ def run_ours(args):
 
     # quality and work counts (untimed): every pose once
     ctx.set_counting(True)
-    ps, roi_fracs, pairs_eval, pairs_contrib = [], [], [], []
+    ps, ss, roi_fracs, pairs_eval, pairs_contrib = [], [], [], [], []
     for k in range(len(poses)):
         stereo(k)
         e, c = ctx.pair_counts()
@@ -353,6 +353,7 @@ def run_ours(args):
         two_pass(k)
         ctx.check_ok()
         ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
+        ss.append(float(ctx.ssim(out["rgb_aff"], out2["rgb_aff"])))
         roi_fracs.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
     ctx.set_counting(False)
 
@@ -471,7 +472,8 @@ def run_ours(args):
                    "margin": 32, "samples_per_edge": 32, "enable_center": 1, "repair": "plain",
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{ws_}"},
         "two_pass_ms": ms_two, "speedup_vs_two_pass": ms_two / ms_stereo, "fps": 1e3 / ms_job,
-        "psnr_aff_vs_full_db": float(np.mean(ps)), "psnr_gate_db": PSNR_GATE,
+        "psnr_aff_vs_full_db": float(np.mean(ps)), "ssim_aff_vs_full": float(np.mean(ss)),
+        "psnr_gate_db": PSNR_GATE,
         "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
         "stage_ms_stereo": dict(zip(["preprocess", "bin_dom", "blend_dom", "warp_edge_gaps", "centre_rois",
                                      "bin_roi", "blend_roi", "outputs"], st_stereo)),
@@ -524,7 +526,7 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
             d, a = poses[k % len(poses)]
             ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
 
-        ps, roi_fracs, net_fracs = [], [], []
+        ps, ss, roi_fracs, net_fracs = [], [], [], []
         for k in range(len(poses)):
             stereo(k)
             cls = out["cls_aff"].clone()
@@ -533,12 +535,14 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
             ctx.render_two_pass(ds, d, a, cam, out=out2)
             ctx.check_ok()
             ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
+            ss.append(float(ctx.ssim(out["rgb_aff"], out2["rgb_aff"])))
             roi_fracs.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
             net_fracs.append(((cls & gs.CLS_NET) > 0).float().mean().item())
         ms, _, _ = timed(stereo, args.steps, args.warmup)
         _, _, st = timed(stereo, len(poses), 1, profile=True)
         st = np.mean(np.array(st), 0).tolist()
         return {"ms_per_stereo_frame": ms, "gate_tau": 0.5, "psnr_aff_vs_full_db": float(np.mean(ps)),
+                "ssim_aff_vs_full": float(np.mean(ss)),
                 "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
                 "net_filled_pixel_share": float(np.mean(net_fracs)),
                 "dtype": ("fp8 e4m3" if mode == 2 else "bf16") + " network, f32 rendering",
@@ -626,6 +630,7 @@ def run_batched(args, dev, flush, weights):
     timed(plain, rs, 1, 0)
     timed(two, rt, 1, 0)
     ps_plain = [psnr(f[4]["rgb_aff"], g[4]["rgb_aff"]) for f, g in zip(frames, frames2)]
+    ss_plain = [float(c.ssim(f[4]["rgb_aff"], g[4]["rgb_aff"])) for c, f, g in zip(ctxs, frames, frames2)]
     res = {
         "workload": "16 stereo frames in one call: 200k slab+ball (1280x720), 500k object (1600x1200), "
                     "1.2M object (1920x1080), 3M unbounded (2048x1536), SH3, 4 head poses each",
@@ -637,6 +642,7 @@ def run_batched(args, dev, flush, weights):
         "fps": {"stereo_plain": 1e3 * n / ms_plain, "two_pass": 1e3 * n / ms_two},
         "speedup_vs_two_pass": {"stereo_plain": ms_two / ms_plain},
         "psnr_aff_vs_full_db": {"plain_mean": float(np.mean(ps_plain)), "plain_min": float(np.min(ps_plain))},
+        "ssim_aff_vs_full": {"plain_mean": float(np.mean(ss_plain)), "plain_min": float(np.min(ss_plain))},
         "stage_ms_stereo_plain": dict(zip(["per_frame_setup_preprocess_bin_dom", "raster_dom_all_frames",
                                            "per_frame_warp_rois_bin_roi", "raster_roi_all_frames", "outputs"],
                                           stage)),
@@ -649,11 +655,14 @@ def run_batched(args, dev, flush, weights):
         ms_learned, _ = timed(learned, rs, args.steps, args.warmup)
         timed(learned, rs, 1, 0)
         ps_learned = [psnr(f[4]["rgb_aff"], g[4]["rgb_aff"]) for f, g in zip(frames, frames2)]
+        ss_learned = [float(c.ssim(f[4]["rgb_aff"], g[4]["rgb_aff"])) for c, f, g in zip(ctxs, frames, frames2)]
         net = float(np.mean([((f[4]["cls_aff"] & gs.CLS_NET) > 0).float().mean().item() for f in frames]))
         res["ms_per_call"]["stereo_learned"] = ms_learned
         res["ms_per_stereo_frame"]["stereo_learned"] = ms_learned / n
         res["fps"]["stereo_learned"] = 1e3 * n / ms_learned
         res["speedup_vs_two_pass"]["stereo_learned"] = ms_two / ms_learned
+        res["ssim_aff_vs_full"].update(learned_mean=float(np.mean(ss_learned)),
+                                       learned_min=float(np.min(ss_learned)))
         res["psnr_aff_vs_full_db"].update(learned_mean=float(np.mean(ps_learned)),
                                           learned_min=float(np.min(ps_learned)))
         res["net_filled_pixel_share"] = net
@@ -725,17 +734,19 @@ def run_unbounded(args, dev, flush):
             d, a = poses[k % 8]
             ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
         ms = run(stereo, args.steps, args.warmup)
-        ps, roi_fr, net_fr = [], [], []
+        ps, ss, roi_fr, net_fr = [], [], [], []
         for k in range(8):
             stereo(k)
             cls = out["cls_aff"].clone()
             two(k)
             ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
+            ss.append(float(ctx.ssim(out["rgb_aff"], out2["rgb_aff"])))
             roi_fr.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
             net_fr.append(((cls & gs.CLS_NET) > 0).float().mean().item())
         ctx.check_ok()
         res[name] = {"ms_per_stereo_frame": ms, "speedup_vs_two_pass": res["two_pass_ms"] / ms,
                      "psnr_aff_vs_full_db": float(np.mean(ps)), "psnr_min_db": float(np.min(ps)),
+                     "ssim_aff_vs_full": float(np.mean(ss)),
                      "roi_pixel_share": float(np.mean(roi_fr)), "net_filled_pixel_share": float(np.mean(net_fr))}
     res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "seconds": round(train_s, 1),
                        "loss_first_last": [hist[0][1], hist[-1][1]],
@@ -769,6 +780,7 @@ def run_hmd(args, dev, flush, weights, calib):
     stream = torch.cuda.current_stream(dev)
     ms = {m: [] for m in ("plain", "bf16", "fp8", "two_pass")}
     ps = {m: [] for m in ("plain", "bf16", "fp8")}
+    ss = {m: [] for m in ("plain", "bf16", "fp8")}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def timed(fn):
@@ -786,6 +798,7 @@ def run_hmd(args, dev, flush, weights, calib):
         for m, roi in rois.items():
             ms[m].append(timed(lambda: ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=outs[m])))
             ps[m].append(psnr(outs[m]["rgb_aff"], out2["rgb_aff"]))
+            ss[m].append(float(ctx.ssim(outs[m]["rgb_aff"], out2["rgb_aff"])))
     ctx.check_ok()
     tp = float(np.mean(ms["two_pass"][3:]))
     res = {"workload": "unbounded 3M surfels, SH3, 2448x2448, f=1800, 0.064 m baseline, 120 frames of a 60 deg/s "
@@ -798,6 +811,7 @@ def run_hmd(args, dev, flush, weights, calib):
         res[m] = {"ms_per_stereo_frame": v, "speedup_vs_two_pass": tp / v,
                   "psnr_aff_vs_full_db": {"mean": float(np.mean(ps[m])), "min": float(np.min(ps[m])),
                                           "max": float(np.max(ps[m]))},
+                  "ssim_aff_vs_full": {"mean": float(np.mean(ss[m])), "min": float(np.min(ss[m]))},
                   "psnr_per_frame_db": [round(x, 3) for x in ps[m]]}
     res["fp8_vs_bf16_psnr_gap_db"] = float(np.mean(np.array(ps["fp8"]) - np.array(ps["bf16"])))
     return res

@@ -317,6 +317,17 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
  * contributed, into GS_BUF_PAIRS (uint64 evaluated[2], contributed[2]). */
 gs_status gs_context_set_counting(gs_context *ctx, int enable);
 
+/* SSIM of an image against a reference (the structural similarity that Table 2
+ * reports beside PSNR), in the convention of the 2DGS/3DGS evaluation code:
+ * 11 x 11 Gaussian window with sigma 1.5, same-size filtering with zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2 (dynamic range 1), averaged over every
+ * pixel of every channel. img, ref: device [channels][height][width] float32
+ * (channels 1..3), within the context's size limits; *ssim: device float,
+ * written on the context's stream (float32 arithmetic, double-precision sum
+ * in a fixed order). */
+gs_status gs_ssim(gs_context *ctx, const float *img, const float *ref, int width, int height, int channels,
+                  float *ssim);
+
 /* Rasterizer configuration (no counterpart in the paper, which fixes 16x16
  * tiles for the ROI grid, Sec. 3.5; the tile edge of the rasterizer itself is a
  * free choice of the 2DGS/3DGS tile rasterizer it builds on).

@@ -114,6 +114,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.rp_flags = c.take<uint8_t>(tiles);
   ws.rp_list = c.take<uint32_t>(tiles);
   ws.rp_nlist = c.take<uint32_t>(1);
+  ws.ssim_part = c.take<double>(ssim_partials(lim.max_width, lim.max_height));
   ws.strips = c.take<int32_t>(16);
   ws.drange = c.take<float>(2);
   ws.widths = c.take<int32_t>(4);
@@ -691,6 +692,14 @@ gs_status gs_context_get_raster(gs_context *ctx, gs_raster_config *rc) {
   rc->pix = ctx->rc.pix;
   rc->batch = ctx->rc.batch;
   return GS_OK;
+}
+
+gs_status gs_ssim(gs_context *ctx, const float *img, const float *ref, int width, int height, int channels,
+                  float *ssim) {
+  if (!ctx || !img || !ref || !ssim || width <= 0 || height <= 0 || width > ctx->lim.max_width ||
+      height > ctx->lim.max_height || channels < 1 || channels > 3)
+    return GS_ERR_BAD_ARG;
+  return cuda_status(launch_ssim(img, ref, width, height, channels, ctx->ws.ssim_part, ssim, ctx->stream));
 }
 
 gs_status gs_context_set_graphs(gs_context *ctx, int enable) {

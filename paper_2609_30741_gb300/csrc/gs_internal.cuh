@@ -133,6 +133,7 @@ struct Workspace {
   float *rp_gate;               // [tiles] gate logit per listed tile
   uint8_t *rp_flags;            // [tiles] tile has a hole
   uint32_t *rp_list, *rp_nlist; // listed tiles and their number
+  double *ssim_part;            // per-(tile, channel) SSIM sums
   // limits
   int max_surfels, max_w, max_h, max_rects, max_tiles;  // max_tiles: rasterizer tiles at min_tshift
   int min_tshift;               // smallest rasterizer tile edge the buffers hold (log2)
@@ -258,6 +259,11 @@ RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift,
 // ROI mask (16-pixel grid) -> rasterizer grid of tile edge 1 << tshift (a tile is
 // masked when it holds a masked pixel).
 cudaError_t launch_raster_mask(const uint8_t *roi, int W, int H, int tshift, uint8_t *rmask, cudaStream_t s);
+// Mean SSIM of a [C][H][W] image against a reference (11 x 11 Gaussian window,
+// zero padding) into *out (device); part: ssim_partials() doubles.
+size_t ssim_partials(int max_w, int max_h);
+cudaError_t launch_ssim(const float *a, const float *b, int W, int H, int C, double *part, float *out,
+                        cudaStream_t s);
 // Warp, edge ROIs, hole classification and gap filling (writes rgb_aff and cls).
 cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
                                  const float *rgb_dom, const float *depth_dom, const float *trans_dom,

@@ -148,6 +148,7 @@ EXPORTS = {
     "gs_tune_cache_size": (C.c_int, [C.POINTER(C.c_int)]),
     "gs_tune_cache_put": (C.c_int, [C.c_char_p, C.POINTER(RasterConfig), C.c_float]),
     "gs_tune_cache_get": (C.c_int, [C.c_char_p, C.POINTER(RasterConfig), C.POINTER(C.c_float)]),
+    "gs_ssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "gs_repair_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "gs_repair_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "gs_repair_features": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
@@ -367,6 +368,17 @@ class Context:
         _check(lib().gs_render_stereo(self.h, C.byref(scene.c), C.byref(pose_struct(pose_dom)),
                                       C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), int(gap_thresh),
                                       C.byref(roi), C.byref(os_)), "gs_render_stereo")
+        return out
+
+    def ssim(self, img, ref, out=None):
+        """Mean SSIM of img against ref ([C, H, W] float32 CUDA tensors), as a
+        device scalar tensor (gs_ssim)."""
+        if img.shape != ref.shape or img.dim() != 3 or not img.is_contiguous() or not ref.is_contiguous():
+            raise ValueError("ssim takes two contiguous [C, H, W] tensors of one shape")
+        if out is None:
+            out = torch.empty((), dtype=torch.float32, device=img.device)
+        C_, H, W = img.shape
+        _check(lib().gs_ssim(self.h, _ptr(img), _ptr(ref), W, H, C_, _ptr(out)), "gs_ssim")
         return out
 
     # ---- learned repair ----
