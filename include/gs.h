@@ -399,6 +399,21 @@ gs_status gs_render_stereo_batch(gs_batch *b, const gs_frame *frames, int n_fram
  * every frame rendered in full (rgb_dom, depth_dom, trans_dom, rgb_aff). */
 gs_status gs_render_two_pass_batch(gs_batch *b, const gs_frame *frames, int n_frames);
 
+/* Full renders of single eyes in one call (as gs_render_mono, frame f in slot
+ * f): pose set-up, preprocessing and binning of every frame side by side, then
+ * one rasterizer launch over all of them. With a stereo pair's two eyes as two
+ * frames this is the concurrent two-eye comparator (the paper names a
+ * concurrent or multiview reference as future work, Sec. 4.3): the two-pass
+ * render without its sequential order. rgb is required; depth, trans optional. */
+typedef struct {
+  const gs_scene *scene;
+  gs_pose pose;
+  gs_intrinsics intr;
+  float bg[3];
+  float *rgb, *depth, *trans; /* device [3][H][W], [H][W], [H][W] */
+} gs_mono_frame;
+gs_status gs_render_mono_batch(gs_batch *b, const gs_mono_frame *frames, int n_frames);
+
 /* ---------------------------------------------------------------------------
  * Rasterizer autotuner. Runs the call - gs_render_stereo(_batch) with `roi`, or
  * the two-pass comparator gs_render_two_pass(_batch) when roi is NULL (gap

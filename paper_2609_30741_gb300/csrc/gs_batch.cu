@@ -69,7 +69,7 @@ struct gs_batch {
   int use_graphs, counting, profiling, nmarks;
   cudaStream_t cur;                    // where the call's main-line work goes
   int capturing;
-  BatchGraph graphs[2];                // stereo, two-pass
+  BatchGraph graphs[3];                // stereo, two-pass, mono
 };
 
 static gs_status bfail(int line, cudaError_t e) {
@@ -200,6 +200,33 @@ static gs_status enqueue_batch(gs_batch *b, const gs_frame *frames, int n, const
     }
   }
   bmark(b, 5);
+  return GS_OK;
+}
+
+// One eye per frame in full (gs_render_mono_batch): per frame pose set-up,
+// preprocessing and binning on the frame's stream, then one rasterizer launch.
+static gs_status enqueue_mono(gs_batch *b, const gs_mono_frame *frames, int n, const FrameGeom *g) {
+  bmark(b, 0);
+  BTRY(fork_frames(b, n, 0));
+  for (int f = 0; f < n; ++f) {
+    gs_context *ctx = b->slot[f];
+    cudaStream_t s = ctx->stream;
+    BTRY(launch_reset_counters(ctx->ws.ctr, s));
+    BTRY(launch_setup_cams(g[f].pa, ctx->ws.cams, s));
+    BTRY(launch_preprocess(*frames[f].scene, ctx->ws, 1, g[f].W, g[f].H, s));
+    BTRY(launch_binning(ctx->ws, 0, frames[f].scene->n, g[f].tx, g[f].ty, nullptr, s, kOrderOwn));
+  }
+  BTRY(join_frames(b, n));
+  bmark(b, 1);
+  RasterTable t;
+  t.n = n;
+  for (int f = 0; f < n; ++f) {
+    const gs_mono_frame &fr = frames[f];
+    t.f[f] = raster_frame(b->slot[f]->ws, 0, g[f].W, g[f].H, g[f].sh, nullptr,
+                          make_float3(fr.bg[0], fr.bg[1], fr.bg[2]), fr.rgb, fr.depth, fr.trans, nullptr, false);
+  }
+  BTRY(launch_raster(t, b->rc, b->counting != 0, b->slot[0]->ws.rqueue, b->cur));
+  bmark(b, 2);
   return GS_OK;
 }
 
@@ -411,7 +438,7 @@ gs_status gs_batch_create(gs_batch **out, gs_context *const *slots, int n_slots,
 
 gs_status gs_batch_destroy(gs_batch *b) {
   if (!b) return GS_ERR_BAD_ARG;
-  for (int k = 0; k < 2; ++k) release(b->graphs[k]);
+  for (int k = 0; k < 3; ++k) release(b->graphs[k]);
   for (int f = 0; f < kRasterFrames; ++f) {
     if (b->side[f]) cudaStreamDestroy(b->side[f]);
     if (b->join[f]) cudaEventDestroy(b->join[f]);
@@ -506,6 +533,39 @@ gs_status gs_render_stereo_batch(gs_batch *b, const gs_frame *frames, int n_fram
   kb.add(*roi);
   return batch_run(b, 0, kb, g, n_frames,
                    [&]() { return enqueue_batch(b, frames, n_frames, g, gap_thresh, roi, false); });
+}
+
+gs_status gs_render_mono_batch(gs_batch *b, const gs_mono_frame *frames, int n_frames) {
+  if (!b || !frames || n_frames <= 0 || n_frames > b->n_slots) return GS_ERR_BAD_ARG;
+  FrameGeom g[kRasterFrames];
+  for (int f = 0; f < n_frames; ++f) {
+    gs_context *ctx = b->slot[f];
+    const gs_mono_frame &fr = frames[f];
+    if (!scene_ok(ctx, fr.scene) || !intr_ok(ctx, &fr.intr) || !fr.rgb) return GS_ERR_BAD_ARG;
+    if (raster_tshift(b->rc) < ctx->ws.min_tshift) return GS_ERR_BAD_ARG;
+    g[f].W = fr.intr.width;
+    g[f].H = fr.intr.height;
+    g[f].sh = raster_tshift(b->rc);
+    g[f].tx = (g[f].W + (1 << g[f].sh) - 1) >> g[f].sh;
+    g[f].ty = (g[f].H + (1 << g[f].sh) - 1) >> g[f].sh;
+    g[f].pa = pose_args(&fr.pose, nullptr, &fr.intr, b->rc);
+  }
+  KeyBuilder kb;
+  kb.add(2);
+  kb.add(n_frames);
+  kb.add(b->rc);
+  kb.add(b->counting);
+  kb.add(b->profiling);
+  for (int f = 0; f < n_frames; ++f) {
+    kb.add(*frames[f].scene);
+    kb.add(frames[f].intr.width);
+    kb.add(frames[f].intr.height);
+    kb.add(frames[f].bg);
+    kb.add(frames[f].rgb);
+    kb.add(frames[f].depth);
+    kb.add(frames[f].trans);
+  }
+  return batch_run(b, 2, kb, g, n_frames, [&]() { return enqueue_mono(b, frames, n_frames, g); });
 }
 
 gs_status gs_render_two_pass_batch(gs_batch *b, const gs_frame *frames, int n_frames) {

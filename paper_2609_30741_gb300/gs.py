@@ -77,6 +77,12 @@ class Frame(C.Structure):
                 ("out", Outputs)]
 
 
+class MonoFrame(C.Structure):
+    """One eye of gs_render_mono_batch (gs_mono_frame)."""
+    _fields_ = [("scene", C.c_void_p), ("pose", Pose), ("intr", Intrinsics), ("bg", C.c_float * 3),
+                ("rgb", C.c_void_p), ("depth", C.c_void_p), ("trans", C.c_void_p)]
+
+
 class TuneResult(C.Structure):
     _fields_ = [("rc", RasterConfig), ("ms", C.c_float)]
 
@@ -135,6 +141,7 @@ EXPORTS = {
     "gs_batch_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "gs_render_stereo_batch": (C.c_int, [C.c_void_p, C.POINTER(Frame), C.c_int, C.c_int, C.POINTER(RoiParams)]),
     "gs_render_two_pass_batch": (C.c_int, [C.c_void_p, C.POINTER(Frame), C.c_int]),
+    "gs_render_mono_batch": (C.c_int, [C.c_void_p, C.POINTER(MonoFrame), C.c_int]),
     "gs_autotune_batch": (C.c_int, [C.c_void_p, C.POINTER(Frame), C.c_int, C.c_int, C.POINTER(RoiParams), C.c_int,
                                     C.c_int, C.POINTER(TuneResult), C.c_int, C.POINTER(C.c_int),
                                     C.POINTER(RasterConfig), C.POINTER(C.c_float)]),
@@ -557,6 +564,16 @@ class Batch:
     def render_two_pass(self, frames):
         arr = self.frames_struct(frames)
         _check(lib().gs_render_two_pass_batch(self.h, arr, len(frames)), "gs_render_two_pass_batch")
+
+    def render_mono(self, frames):
+        """frames: [(DeviceScene, pose, cam, (rgb, depth, trans) tensors, bg or None)]"""
+        arr = (MonoFrame * len(frames))()
+        for i, (ds, pose, cam, out, bg) in enumerate(frames):
+            rgb, dep, tr = out
+            arr[i] = MonoFrame(C.cast(C.pointer(ds.c), C.c_void_p), pose_struct(pose), intr_struct(cam),
+                               (C.c_float * 3)(*(bg if bg is not None else (0.0, 0.0, 0.0))), rgb.data_ptr(),
+                               dep.data_ptr() if dep is not None else None, tr.data_ptr() if tr is not None else None)
+        _check(lib().gs_render_mono_batch(self.h, arr, len(frames)), "gs_render_mono_batch")
 
     def autotune(self, frames, gap_thresh=2, roi=None, reps=5, use_cache=True, two_pass=False):
         """(best (tile, pix, batch), its median ms per call, [(config, ms), ...]);

@@ -254,3 +254,30 @@ def test_autotune_skips_configs_that_overflow(gs):
         gs.autotune_stereo(tiny, ds, dom, aff, cam, reps=2, use_cache=False)
     assert e.value.status == gs.GS_ERR_CAPACITY
     assert tiny.raster() == (16, 4, 128)
+
+
+def test_mono_batch_is_the_concurrent_two_eye_render(gs, setup):
+    """gs_render_mono_batch with a stereo pair's two eyes as two frames renders
+    both eyes in full side by side: each equals gs_render_mono of its pose, and
+    the pair equals the sequential two-pass render."""
+    spec = setup["spec"]
+    sc, cam, poses = spec[1]  # the object scene
+    ds = setup["scenes"][1]
+    d, a = poses[0]
+    slots = [gs.Context(sc.n, cam.width, cam.height, max_instances=1 << 24) for _ in range(2)]
+    b = gs.Batch(slots)
+    outs = [(torch.empty(3, cam.height, cam.width, device="cuda"), torch.empty(cam.height, cam.width, device="cuda"),
+             torch.empty(cam.height, cam.width, device="cuda")) for _ in range(2)]
+    for _ in range(3):  # direct, capture, replay
+        b.render_mono([(ds, d, cam, outs[0], None), (ds, a, cam, outs[1], None)])
+    b.check_ok()
+    got = [[t.clone() for t in o] for o in outs]
+    ref_ctx = gs.Context(sc.n, cam.width, cam.height, max_instances=1 << 24)
+    for pose, g in zip((d, a), got):
+        r = ref_ctx.render_mono(ds, pose, cam)
+        for x, y in zip(g, r):
+            assert torch.equal(x, y)
+    tp = ref_ctx.render_two_pass(ds, d, a, cam)
+    assert torch.equal(got[0][0], tp["rgb_dom"]) and torch.equal(got[0][1], tp["depth_dom"])
+    assert torch.equal(got[1][0], tp["rgb_aff"])
+    b.close()
