@@ -60,38 +60,44 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     ws.bounds[e] = c.take<float4>(lim.keep_intermediates ? N : 1);
     ws.cnt[e] = c.take<uint32_t>(N);
     ws.zkey[e] = c.take<uint32_t>(N);
-    ws.dkey[e] = c.take<uint32_t>(N);
-    ws.dval[e] = c.take<uint32_t>(N);
   }
   ws.uval = c.take<uint32_t>(N);
   ws.bin_warp_surfels = bin_warp_surfels(lim.max_surfels);
   ws.bin_nch = bin_chunks(lim.max_surfels);
   const size_t table = tiles * ws.bin_nch;
-  ws.ival = c.take<uint32_t>(I);
-  ws.ikey = c.take<uint32_t>(lim.keep_intermediates ? I : 1);
   ws.cnt_bin = c.take<uint32_t>(lim.keep_intermediates ? N : 1);
-  ws.bin_table = c.take<uint4>(table);
   ws.band_pool_cap = (uint32_t)(8 * N + 1024);
-  ws.band_pool = reinterpret_cast<BandEntry *>(c.take<char>(kBandEntryBytes * ws.band_pool_cap));
-  ws.band_lists = c.take<uint2>(band_list_words(lim.max_surfels, (int)rty));  // the binning runs on the raster grid
-  ws.bin_offs = c.take<uint32_t>(table);
-  ws.ranges = c.take<uint2>(tiles);
+  const size_t rs_words = radix_table_words(N);
+  for (int e = 0; e < 2; ++e) {  // one binning scratch per eye
+    BinScratch &b = ws.bin[e];
+    for (int k = 0; k < 2; ++k) {
+      b.dkey[k] = c.take<uint32_t>(N);
+      b.dval[k] = c.take<uint32_t>(N);
+    }
+    b.ival = c.take<uint32_t>(I);
+    b.ikey = c.take<uint32_t>(lim.keep_intermediates ? I : 1);
+    b.bin_table = c.take<uint4>(table);
+    b.band_pool = reinterpret_cast<BandEntry *>(c.take<char>(kBandEntryBytes * ws.band_pool_cap));
+    b.band_lists = c.take<uint2>(band_list_words(lim.max_surfels, (int)rty));  // the binning runs on the raster grid
+    b.bin_offs = c.take<uint32_t>(table);
+    b.ranges = c.take<uint2>(tiles);
+    b.rmask = c.take<uint8_t>(tiles);
+    b.items = c.take<uint32_t>(tiles);
+    b.rqueue = c.take<uint32_t>(2);
+    b.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
+    b.rs_table = c.take<uint32_t>(rs_words);
+    b.rs_offs = c.take<uint32_t>(rs_words);
+    b.rs_n = c.take<uint32_t>(1);
+    b.rs_sums = c.take<uint32_t>(rs_words / kScanTile + 2);
+    b.scan_sums = c.take<uint32_t>(scan_blocks);
+    b.scan_ticket = c.take<uint32_t>(1);
+  }
   ws.tile_mask = c.take<uint8_t>(tiles);
-  ws.rmask = c.take<uint8_t>(tiles);
-  ws.items = c.take<uint32_t>(tiles);
-  ws.rqueue = c.take<uint32_t>(2);
-  ws.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
+  ws.strip_mask = c.take<uint8_t>(tiles);
   for (int e = 0; e < 2; ++e) {
     ws.row_off[e] = c.take<uint32_t>(N);
     ws.spans[e] = c.take<uint2>(I);
   }
-  const size_t rs_words = radix_table_words(N);
-  ws.rs_table = c.take<uint32_t>(rs_words);
-  ws.rs_offs = c.take<uint32_t>(rs_words);
-  ws.rs_n = c.take<uint32_t>(1);
-  ws.rs_sums = c.take<uint32_t>(rs_words / kScanTile + 2);
-  ws.scan_sums = c.take<uint32_t>(scan_blocks);
-  ws.scan_ticket = c.take<uint32_t>(1);
   ws.warpbuf = c.take<unsigned long long>(P);
   ws.warp_depth = c.take<float>(P);
   ws.cls = c.take<uint8_t>(P);
@@ -147,7 +153,7 @@ __global__ void reset_counters_kernel(Counters *c) {
     c->n_rows[0] = c->n_rows[1] = 0;
     c->n_band[0] = c->n_band[1] = 0;
     c->n_union = 0;
-    c->n_items = 0;
+    c->n_items[0] = c->n_items[1] = 0;
     c->dmin_bits = 0x7f800000u;
     c->dmax_bits = 0u;
     c->n_rects = 0;
@@ -341,9 +347,11 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
   const int msh = min_tshift(*lim);
   cudaError_t e = prepare_binning((lim->max_width + (1 << msh) - 1) >> msh);
   if (e == cudaSuccess) e = prepare_repair();
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.rqueue, 0, 2 * sizeof(uint32_t), ctx->stream);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMemsetAsync(ctx->ws.bin[k].rqueue, 0, 2 * sizeof(uint32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.bin[k].scan_ticket, 0, sizeof(uint32_t), ctx->stream);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.scan_ticket, 0, sizeof(uint32_t), ctx->stream);
   if (e != cudaSuccess) {
     delete ctx;
     return cuda_fail(e);
@@ -426,7 +434,7 @@ static cudaError_t raster_one(gs_context *ctx, const RasterFrame &f) {
   RasterTable t;
   t.n = 1;
   t.f[0] = f;
-  return launch_raster(t, ctx->rc, ctx->counting != 0, ctx->ws.rqueue, ctx->stream);
+  return launch_raster(t, ctx->rc, ctx->counting != 0, ctx->ws.bin[f.eye].rqueue, ctx->stream);
 }
 
 static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye, int W, int H, float3 bg,
@@ -639,9 +647,9 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     ctx->last_tiles = tx * ty;
     const uint8_t *bmask = ctx->ws.tile_mask;
     if (sh != 4) {
-      if ((e = launch_raster_mask(ctx->ws.tile_mask, W, H, sh, ctx->ws.rmask, ctx->stream)) != cudaSuccess)
+      if ((e = launch_raster_mask(ctx->ws.tile_mask, W, H, sh, ctx->ws.bin[1].rmask, ctx->stream)) != cudaSuccess)
         return cuda_fail(e);
-      bmask = ctx->ws.rmask;
+      bmask = ctx->ws.bin[1].rmask;
     }
     e = launch_binning(ctx->ws, 1, scene->n, tx, ty, bmask, ctx->stream, p.parallel ? kOrderReuse : kOrderOwn);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -727,12 +735,12 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
     case GS_BUF_RECTS: p = ws.rect[eye]; b = 8 * N; n = (int64_t)N; break;
     case GS_BUF_BOUNDS: p = ws.bounds[eye]; b = ws.keep_intermediates ? 16 * N : 0; n = (int64_t)N; break;
     case GS_BUF_COUNTS: p = ws.cnt[eye]; b = 4 * N; n = (int64_t)N; break;
-    case GS_BUF_DEPTH_ORDER: p = ws.dval[0]; b = 4 * N; n = c.n_vis[last]; break;
+    case GS_BUF_DEPTH_ORDER: p = ws.bin[last].dval[0]; b = 4 * N; n = c.n_vis[last]; break;
     case GS_BUF_INST_KEYS:
       if (!ws.keep_intermediates) return GS_ERR_BAD_ARG;
-      p = ws.ikey; b = 4 * I; n = c.n_sort[last]; break;
-    case GS_BUF_INST_VALS: p = ws.ival; b = 4 * I; n = c.n_sort[last]; break;
-    case GS_BUF_RANGES: p = ws.ranges; b = 8 * (size_t)nt; n = nt; break;
+      p = ws.bin[last].ikey; b = 4 * I; n = c.n_sort[last]; break;
+    case GS_BUF_INST_VALS: p = ws.bin[last].ival; b = 4 * I; n = c.n_sort[last]; break;
+    case GS_BUF_RANGES: p = ws.bin[last].ranges; b = 8 * (size_t)nt; n = nt; break;
     case GS_BUF_WARP: p = ws.warpbuf; b = 8 * P; n = (int64_t)P; break;
     case GS_BUF_TILE_MASK: p = ws.tile_mask; b = (size_t)nt; n = nt; break;
     case GS_BUF_DEPTH_RANGE: p = ws.drange; b = 8; n = 2; break;

@@ -152,7 +152,7 @@ static gs_status enqueue_batch(gs_batch *b, const gs_frame *frames, int n, const
     t.f[f] = raster_frame(b->slot[f]->ws, 0, g[f].W, g[f].H, g[f].sh, nullptr, black, o.rgb_dom, o.depth_dom,
                           o.trans_dom, nullptr, !two_pass);
   }
-  BTRY(launch_raster(t, b->rc, b->counting != 0, b->slot[0]->ws.rqueue, b->cur));
+  BTRY(launch_raster(t, b->rc, b->counting != 0, b->slot[0]->ws.bin[0].rqueue, b->cur));
   bmark(b, 2);
   // per frame: warp, edge ROIs, gaps, centre ROIs, repair, ROI binning (or the
   // affiliated eye's full binning for the comparator)
@@ -174,8 +174,8 @@ static gs_status enqueue_batch(gs_batch *b, const gs_frame *frames, int n, const
       BTRY(repair_stereo(ctx->ws, g[f].W, g[f].H, roi->gate_tau, o.rgb_aff, s, roi->repair_mode == 2));
     const uint8_t *bmask = ctx->ws.tile_mask;
     if (g[f].sh != 4) {
-      BTRY(launch_raster_mask(ctx->ws.tile_mask, g[f].W, g[f].H, g[f].sh, ctx->ws.rmask, s));
-      bmask = ctx->ws.rmask;
+      BTRY(launch_raster_mask(ctx->ws.tile_mask, g[f].W, g[f].H, g[f].sh, ctx->ws.bin[1].rmask, s));
+      bmask = ctx->ws.bin[1].rmask;
     }
     BTRY(launch_binning(ctx->ws, 1, frames[f].scene->n, g[f].tx, g[f].ty, bmask, s, order));
   }
@@ -190,7 +190,7 @@ static gs_status enqueue_batch(gs_batch *b, const gs_frame *frames, int n, const
                       : raster_frame(ws, 1, g[f].W, g[f].H, g[f].sh, ws.tile_mask, black, frames[f].out.rgb_aff,
                                      nullptr, nullptr, ws.cls, false);
   }
-  BTRY(launch_raster(t, b->rc, b->counting != 0, b->slot[0]->ws.rqueue, b->cur));
+  BTRY(launch_raster(t, b->rc, b->counting != 0, b->slot[0]->ws.bin[1].rqueue, b->cur));
   bmark(b, 4);
   if (!two_pass) {
     for (int f = 0; f < n; ++f) {
@@ -225,7 +225,7 @@ static gs_status enqueue_mono(gs_batch *b, const gs_mono_frame *frames, int n, c
     t.f[f] = raster_frame(b->slot[f]->ws, 0, g[f].W, g[f].H, g[f].sh, nullptr,
                           make_float3(fr.bg[0], fr.bg[1], fr.bg[2]), fr.rgb, fr.depth, fr.trans, nullptr, false);
   }
-  BTRY(launch_raster(t, b->rc, b->counting != 0, b->slot[0]->ws.rqueue, b->cur));
+  BTRY(launch_raster(t, b->rc, b->counting != 0, b->slot[0]->ws.bin[0].rqueue, b->cur));
   bmark(b, 2);
   return GS_OK;
 }

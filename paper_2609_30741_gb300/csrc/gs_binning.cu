@@ -707,34 +707,35 @@ cudaError_t prepare_binning(int max_tiles_x) {
 
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
                            const uint8_t *tile_mask, cudaStream_t s, int order) {
+  const BinScratch &b = ws.bin[eye];
   cudaError_t err;
   Counters *ctr = ws.ctr;
   const int ntiles = tiles_x * tiles_y;
   const uint32_t cap = (uint32_t)ws.max_instances;
-  const RadixScratch rs{ws.rs_table, ws.rs_offs, ws.rs_n, ws.rs_sums, ws.scan_ticket};
+  const RadixScratch rs{b.rs_table, b.rs_offs, b.rs_n, b.rs_sums, b.scan_ticket};
   if (tile_mask) {
-    launch_k(mask_sat_kernel, 1, 1024, 0, s, tile_mask, tiles_x, tiles_y, ws.mask_sat);
+    launch_k(mask_sat_kernel, 1, 1024, 0, s, tile_mask, tiles_x, tiles_y, b.mask_sat);
     GS_LAUNCHED(1);
   }
   // 1. compact the binned surfels: (depth bits, surfel id)
-  const uint32_t *sat = tile_mask ? ws.mask_sat : nullptr;
+  const uint32_t *sat = tile_mask ? b.mask_sat : nullptr;
   if (order == kOrderReuse) {  // the dominant order, filtered: already depth-ordered
     err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, ws.cnt[eye], ws.rect[eye], sat, tiles_x},
-                      ReuseApply{ws.uval, ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
+                      ReuseApply{ws.uval, ws.zkey[eye], b.dkey[0], b.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
                                  &ctr->n_band[eye]},
-                      (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
+                      (const uint32_t *)nullptr, (uint32_t)n, b.scan_sums, b.scan_ticket, nullptr, s);
   } else {
     err = scan_launch(VisibleLoad{ws.cnt[eye], order == kOrderUnion ? ws.cnt[1 - eye] : nullptr, ws.rect[eye], sat,
                                   tiles_x},
-                      CompactApply{ws.zkey[eye], ws.dkey[0], ws.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
+                      CompactApply{ws.zkey[eye], b.dkey[0], b.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
                                    &ctr->n_band[eye]},
-                      (const uint32_t *)nullptr, (uint32_t)n, ws.scan_sums, ws.scan_ticket, nullptr, s);
+                      (const uint32_t *)nullptr, (uint32_t)n, b.scan_sums, b.scan_ticket, nullptr, s);
   }
   if (err != cudaSuccess) return err;
   // 2. tile ranges of every rectangle row of those surfels (n_rows and n_band
   // were cleared by the compaction)
   if (n > 0) {
-    launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, ws.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
+    launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, b.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
                                                 ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.row_off[eye],
                                                 ws.spans[eye], (uint32_t)ws.max_instances, &ctr->n_rows[eye],
                                                 &ctr->status);
@@ -743,11 +744,11 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   // 3. depth order (the low 32 bits of the packed key; stable, so ties keep id order)
   int which = 0;
   if (order != kOrderReuse &&
-      (err = radix_sort(ws.dkey, ws.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
+      (err = radix_sort(b.dkey, b.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
     return err;
   if (order == kOrderUnion && n > 0) {  // kept for the affiliated eye
     const int g = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
-    if ((err = launch_k(keep_union_kernel, g, 256, 0, s, ws.dval[which], &ctr->n_vis[eye], (uint32_t)n, ws.uval,
+    if ((err = launch_k(keep_union_kernel, g, 256, 0, s, b.dval[which], &ctr->n_vis[eye], (uint32_t)n, ws.uval,
                         &ctr->n_union)) != cudaSuccess)
       return err;
     GS_LAUNCHED(1);
@@ -755,28 +756,28 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   const int nbands = (tiles_y + kBandRows - 1) / kBandRows;
   // 4. per chunk: each warp's depth-ordered (surfel, band) lists
   BandArgs ba;
-  ba.ids = ws.dval[which];
+  ba.ids = b.dval[which];
   ba.n_vis = &ctr->n_vis[eye];
   ba.n_max = (uint32_t)n;
   ba.cnt = ws.cnt[eye];
   ba.rect = ws.rect[eye];
   ba.row_off = ws.row_off[eye];
-  ba.sat = tile_mask ? ws.mask_sat : nullptr;
+  ba.sat = tile_mask ? b.mask_sat : nullptr;
   ba.tiles_x = tiles_x;
   ba.tiles_y = tiles_y;
   ba.warp_surfels = ws.bin_warp_surfels;
-  ba.pool = ws.band_pool;
+  ba.pool = b.band_pool;
   ba.pool_cap = ws.band_pool_cap;
   ba.pool_n = &ctr->n_band[eye];
-  ba.lists = ws.band_lists;
+  ba.lists = b.band_lists;
   ba.status = &ctr->status;
   launch_k(band_list_kernel, ws.bin_nch * (kBinWarps / kListWarps), 32 * kListWarps, 0, s, ba);
   GS_LAUNCHED(1);
   BinArgs a;
   a.n_vis = &ctr->n_vis[eye];
   a.n_max = (uint32_t)n;
-  a.pool = ws.band_pool;
-  a.lists = ws.band_lists;
+  a.pool = b.band_pool;
+  a.lists = b.band_lists;
   a.spans = ws.spans[eye];
   a.span_cap = (uint32_t)ws.max_instances;
   a.mask = tile_mask;
@@ -784,11 +785,11 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   a.tiles_y = tiles_y;
   a.warp_surfels = ws.bin_warp_surfels;
   a.nch = ws.bin_nch;
-  a.table = ws.bin_table;
-  a.offs = ws.bin_offs;
+  a.table = b.bin_table;
+  a.offs = b.bin_offs;
   a.cap = cap;
-  a.ival = ws.ival;
-  a.ikey = ws.keep_intermediates ? ws.ikey : nullptr;
+  a.ival = b.ival;
+  a.ikey = ws.keep_intermediates ? b.ikey : nullptr;
   a.cnt_bin = ws.keep_intermediates ? ws.cnt_bin : nullptr;
   if (a.cnt_bin && n > 0 && (err = cudaMemsetAsync(a.cnt_bin, 0, sizeof(uint32_t) * (size_t)n, s)) != cudaSuccess)
     return err;
@@ -797,15 +798,15 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   launch_k(bin_kernel, grid, kBinThreads, bin_smem_bytes(tiles_x) / 2, s, a, 0);
   GS_LAUNCHED(1);
   // 6. tile-major scan: where every (tile, chunk) run starts
-  err = scan_launch(BinTableLoad{ws.bin_table, &ctr->n_vis[eye], (uint32_t)n, ws.bin_nch,
+  err = scan_launch(BinTableLoad{b.bin_table, &ctr->n_vis[eye], (uint32_t)n, ws.bin_nch,
                                  kBinWarps * ws.bin_warp_surfels},
-                    BinOffsetApply{ws.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status,
-                                   tile_mask ? &ctr->n_items : nullptr},
-                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, ws.scan_sums, ws.scan_ticket,
+                    BinOffsetApply{b.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status,
+                                   tile_mask ? &ctr->n_items[eye] : nullptr},
+                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, b.scan_sums, b.scan_ticket,
                     nullptr, s);
   if (err != cudaSuccess) return err;
-  launch_k(bin_ranges_kernel, (ntiles + 255) / 256, 256, 0, s, ws.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
-                                                         ws.ranges, tile_mask, ws.items, &ctr->n_items);
+  launch_k(bin_ranges_kernel, (ntiles + 255) / 256, 256, 0, s, b.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
+                                                         b.ranges, tile_mask, b.items, &ctr->n_items[eye]);
   // 7. every surfel id to its slot
   launch_k(bin_kernel, grid, kBinThreads, bin_smem_bytes(tiles_x), s, a, 1);
   GS_LAUNCHED(2);

@@ -64,8 +64,9 @@ struct Counters {
   uint32_t n_rows[2];    // (surfel, tile row) spans per eye
   uint32_t n_band[2];    // (surfel, band) list entries of the last binning per eye
   uint32_t n_union;      // surfels in the dominant binning's depth order (both eyes' visible set)
-  uint32_t n_items;      // rasterizer tiles listed by the last masked binning
-  uint32_t pad[4];
+  uint32_t n_items[2];   // rasterizer tiles listed by the last masked binning per eye
+  uint32_t prev_range[2];// float bits of the last measured depth range (reused by depth_mode 2)
+  uint32_t pad[1];
   unsigned long long pairs[2];    // evaluated (pixel, surfel) pairs per eye (counting mode)
   unsigned long long contrib[2];  // of which contributed (alpha >= 1/255, before termination)
 };
@@ -81,6 +82,28 @@ struct Record {
   float4 r0, r1, r2, r3;
 };
 
+// Scratch of one eye's binning and rasterization. Each eye has its own, so the
+// affiliated eye can be binned and rasterized while the dominant eye's binning
+// and rasterizer run on another stream.
+struct BinScratch {
+  uint32_t *dkey[2], *dval[2];  // depth sort double buffers
+  uint4 *bin_table;             // [tile][chunk] per-warp instance counts (8 x 16 bits)
+  struct BandEntry *band_pool;  // (surfel, band) entries of every warp's lists
+  uint2 *band_lists;            // [chunk][band][warp]: first entry, entries
+  uint32_t *bin_offs;           // their tile-major exclusive scan
+  uint32_t *ival;               // surfel id per instance, grouped by tile, depth order inside
+  uint32_t *ikey;               // tile id per instance (keep_intermediates)
+  uint2 *ranges;                // per rasterizer tile: [first, end) of its instances
+  uint8_t *rmask;               // the binning's mask on the rasterizer grid (tile edge 8 or 32)
+  uint32_t *items;              // rasterizer tiles of the last masked binning
+  uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
+  uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
+  uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
+  uint32_t *rs_n, *rs_sums;     // length of the table, scan block sums
+  uint32_t *scan_sums;          // scan block sums
+  uint32_t *scan_ticket;        // scan completion counter, 0 between scans
+};
+
 // Views of the caller-owned workspace.
 struct Workspace {
   CamBlock *cams;
@@ -91,27 +114,14 @@ struct Workspace {
   uint32_t *cnt[2];             // tiles of each surfel's bounding rectangle (0 = culled)
   uint32_t *zkey[2];            // float bits of the centre depth per surfel and eye
   uint32_t *cnt_bin;            // tiles each surfel reaches in the last binning (keep_intermediates)
-  uint32_t *dkey[2], *dval[2];  // depth sort double buffers
   uint32_t *uval;               // depth-ordered union of both eyes' binned surfels (dominant keys)
-  uint4 *bin_table;             // [tile][chunk] per-warp instance counts (8 x 16 bits)
-  struct BandEntry *band_pool;  // (surfel, band) entries of every warp's lists
   uint32_t band_pool_cap;
-  uint2 *band_lists;            // [chunk][band][warp]: first entry, entries
-  uint32_t *bin_offs;           // their tile-major exclusive scan
-  uint32_t *ival;               // surfel id per instance, grouped by tile, depth order inside
-  uint32_t *ikey;               // tile id per instance (keep_intermediates)
-  uint2 *ranges;                // per rasterizer tile: [first, end) of its instances
+  BinScratch bin[2];            // per eye
   uint8_t *tile_mask;           // ROI mask on the 16-pixel grid
-  uint8_t *rmask;               // the ROI mask on the rasterizer grid (tile edge 8 or 32)
-  uint32_t *items;              // rasterizer tiles of the last masked binning
-  uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
-  uint32_t *mask_sat;           // summed-area table of the tile mask [tiles_y + 1][tiles_x + 1]
+  uint8_t *strip_mask;          // edge-strip tiles of a reused depth range (16-pixel grid)
   uint32_t *row_off[2];         // per surfel and eye: slot of its first rectangle row in spans
   uint2 *spans[2];              // per (surfel, tile row): tile ranges [a0, a1] u [c0, c1], 4 x 16 bits
-  uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
-  uint32_t *rs_n, *rs_sums;     // length of the table, scan block sums
-  uint32_t *scan_sums;          // scan block sums
-  uint32_t *scan_ticket;        // scan completion counter, 0 between scans
+  // scans outside the binning (centre ROIs, repair tile lists) use bin[0]'s scratch
   unsigned long long *warpbuf;
   float *warp_depth;
   uint8_t *cls;

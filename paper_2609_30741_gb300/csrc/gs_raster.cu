@@ -380,12 +380,12 @@ RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift,
                          float *rgb, float *depth, float *trans, uint8_t *cls, bool stats) {
   RasterFrame f;
   const int ts = 1 << tshift;
-  f.ranges = ws.ranges;
-  f.ids = ws.ival;
+  f.ranges = ws.bin[eye].ranges;
+  f.ids = ws.bin[eye].ival;
   f.rec = ws.rec[eye];
   f.roi = (mask && tshift > 4) ? mask : nullptr;  // a 32-pixel tile may hold unmasked 16-pixel tiles
-  f.items = mask ? ws.items : nullptr;
-  f.n_items = mask ? &ws.ctr->n_items : nullptr;
+  f.items = mask ? ws.bin[eye].items : nullptr;
+  f.n_items = mask ? &ws.ctr->n_items[eye] : nullptr;
   f.rgb = rgb;
   f.depth = depth;
   f.trans = trans;
