@@ -85,7 +85,16 @@ typedef struct {
   int samples_per_edge; /* N boundary samples per image edge (>= 2) */
   int enable_center;    /* Step 2 (centre ROIs) on/off, chosen before rendering */
   int depth_mode;       /* 0: d_min/d_max = per-frame range of the normalised depth
-                           D/(1-T) over pixels with coverage 1-T >= 0.5; 1: fixed */
+                           D/(1-T) over pixels with coverage 1-T >= 0.5; 1: fixed;
+                           2: the range the previous stereo call of this context
+                           measured (temporal reuse along a head trajectory; the
+                           paper leaves continuous head motion to future work,
+                           Sec. 4.6 and Sec. 5): the edge strips are then
+                           known before the dominant eye is rendered, and
+                           gs_render_stereo renders the affiliated eye's strip
+                           tiles on a second stream meanwhile. The result equals
+                           mode 1 with that range. A context's first call, with
+                           no previous range, measures it (mode 0). */
   float d_min, d_max;   /* the two depth hypotheses when depth_mode = 1 */
   int repair_mode;      /* 0: plain interpolation + ROI re-render; 1: learned repair
                            in BF16; 2: learned repair in FP8 (both need
@@ -402,8 +411,8 @@ gs_status gs_render_two_pass_batch(gs_batch *b, const gs_frame *frames, int n_fr
 /* Full renders of single eyes in one call (as gs_render_mono, frame f in slot
  * f): pose set-up, preprocessing and binning of every frame side by side, then
  * one rasterizer launch over all of them. With a stereo pair's two eyes as two
- * frames this is the concurrent two-eye comparator (the paper names a
- * concurrent or multiview reference as future work, Sec. 4.3): the two-pass
+ * frames this is the concurrent two-eye comparator (the paper leaves concurrent
+ * and multiview references to future work, Sec. 4.6 and Sec. 5): the two-pass
  * render without its sequential order. rgb is required; depth, trans optional. */
 typedef struct {
   const gs_scene *scene;

@@ -94,6 +94,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   }
   ws.tile_mask = c.take<uint8_t>(tiles);
   ws.strip_mask = c.take<uint8_t>(tiles);
+  ws.strip_rgb = c.take<float>(3 * P);
   for (int e = 0; e < 2; ++e) {
     ws.row_off[e] = c.take<uint32_t>(N);
     ws.spans[e] = c.take<uint2>(I);
@@ -269,7 +270,7 @@ bool outputs_ok(const gs_outputs *o) { return o && o->rgb_dom && o->depth_dom &&
 
 bool roi_ok(int gap_thresh, const gs_roi_params *roi) {
   if (!roi || gap_thresh < 0 || roi->margin < 0 || roi->samples_per_edge < 2 || roi->samples_per_edge > 1 << 20 ||
-      (roi->depth_mode != 0 && roi->depth_mode != 1))
+      roi->depth_mode < 0 || roi->depth_mode > 2)
     return false;
   return roi->repair_mode >= 0 && roi->repair_mode <= 3 && roi->gate_tau > 0.f && roi->gate_tau < 1.f;
 }
@@ -366,6 +367,10 @@ gs_status gs_context_destroy(gs_context *ctx) {
     if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
   for (int k = 0; k < 3; ++k) release_slot(ctx->graphs[k]);
   if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_edge) cudaEventDestroy(ctx->ev_edge);
+  if (ctx->ev_strip) cudaEventDestroy(ctx->ev_strip);
   delete ctx;
   return GS_OK;
 }
@@ -595,6 +600,16 @@ gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *
   });
 }
 
+// The second stream and events of depth_mode 2 (created on first use).
+static gs_status ensure_side(gs_context *ctx) {
+  if (ctx->side) return GS_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_edge, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_strip, cudaEventDisableTiming);
+  return cuda_status(e);
+}
+
 gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom, const gs_pose *pose_aff,
                            const gs_intrinsics *intr, int gap_thresh, const gs_roi_params *roi,
                            const gs_outputs *out) {
@@ -606,62 +621,110 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
   const int sh = raster_tshift(ctx->rc), ts = 1 << sh;
   const int tx = (W + ts - 1) >> sh, ty = (H + ts - 1) >> sh;
   const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc);
+  // depth_mode 2 reuses the depth range the previous stereo call measured; the
+  // first call measures it (mode 0)
+  gs_roi_params r = *roi;
+  const bool reuse = roi->depth_mode == 2 && ctx->have_range;
+  if (roi->depth_mode == 2 && !reuse) r.depth_mode = 0;
+  if (reuse) {
+    const gs_status st = ensure_side(ctx);
+    if (st != GS_OK) return st;
+  }
   KeyBuilder kb;
   key_common(kb, ctx, 1, scene, intr);
   kb.add(gap_thresh);
-  kb.add(*roi);
+  kb.add(r);
   kb.add(*out);
   kb.add(pa.parallel);  // selects the depth-order path of the affiliated eye
-  return run_graph(ctx, 1, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
+  const gs_status res = run_graph(ctx, 1, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
     gs_status st = begin_call(ctx, scene, p);
     if (st != GS_OK) return st;
     const float3 black = make_float3(0.f, 0.f, 0.f);
+    const Workspace &ws = ctx->ws;
+    cudaError_t e = cudaSuccess;
+    if (reuse) {
+      // With the previous frame's depth range the edge strips (Eq. 6-8) are known
+      // before the dominant eye is rendered: a second stream bins and renders the
+      // affiliated eye's strip tiles (into a scratch image) while the dominant
+      // eye is binned and rendered.
+      cudaStream_t sd = ctx->side;
+      if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) == cudaSuccess) e = cudaStreamWaitEvent(sd, ctx->ev_fork, 0);
+      if (e == cudaSuccess) e = launch_edge_roi(ws, r, ws.strip_mask, true, sd);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_edge, sd);
+      const uint8_t *smask = ws.strip_mask;
+      if (e == cudaSuccess && sh != 4) {
+        e = launch_raster_mask(ws.strip_mask, W, H, sh, ws.bin[1].rmask, sd);
+        smask = ws.bin[1].rmask;
+      }
+      if (e == cudaSuccess) e = launch_binning(ws, 1, scene->n, tx, ty, smask, sd, kOrderOwn);
+      if (e == cudaSuccess) {
+        RasterTable t;
+        t.n = 1;
+        t.f[0] = raster_frame(ws, 1, W, H, sh, ws.strip_mask, black, ws.strip_rgb, nullptr, nullptr, nullptr, false);
+        e = launch_raster(t, ctx->rc, ctx->counting != 0, ws.bin[1].rqueue, sd);
+      }
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_strip, sd);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
     // Stage 1: dominant eye, RGB + depth proxy (+ the per-frame depth range)
     st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2,
                          p.parallel ? kOrderUnion : kOrderOwn);
     if (st != GS_OK) return st;
     // Stages 2-3: warp, edge ROIs, gaps
-    cudaError_t e = launch_warp_classify(ctx->ws, W, H, gap_thresh, *roi, out->rgb_dom, out->depth_dom,
-                                         out->trans_dom, out->rgb_aff, ctx->stream);
+    if (reuse) {
+      e = launch_warp(ws, W, H, out->depth_dom, out->trans_dom, ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_edge, 0);
+      if (e == cudaSuccess) e = launch_classify(ws, W, H, gap_thresh, r, out->rgb_dom, out->rgb_aff, ctx->stream);
+    } else {
+      e = launch_warp_classify(ws, W, H, gap_thresh, r, out->rgb_dom, out->depth_dom, out->trans_dom, out->rgb_aff,
+                               ctx->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e);
-    if (roi->repair_mode != 0) {  // the repair network's inputs, kept for gs_repair_features
-      if ((e = repair_features(ctx->ws, W, H, out->rgb_aff, ctx->ws.rp_feat, ctx->stream)) != cudaSuccess)
-        return cuda_fail(e);
+    if (r.repair_mode != 0) {  // the repair network's inputs, kept for gs_repair_features
+      if ((e = repair_features(ws, W, H, out->rgb_aff, ws.rp_feat, ctx->stream)) != cudaSuccess) return cuda_fail(e);
     }
     mark(ctx, 4);
     // Step 2: connected centre holes -> ROIs
-    if (roi->enable_center) {
-      if ((e = launch_centre_rois(ctx->ws, W, H, roi->margin, ctx->stream)) != cudaSuccess) return cuda_fail(e);
+    if (r.enable_center) {
+      if ((e = launch_centre_rois(ws, W, H, r.margin, ctx->stream)) != cudaSuccess) return cuda_fail(e);
     }
     // learned repair: tiles with holes whose gate passes take the network fill
     // and leave the ROI tile mask
-    if (roi->repair_mode == 1 || roi->repair_mode == 2) {
-      if ((e = repair_stereo(ctx->ws, W, H, roi->gate_tau, out->rgb_aff, ctx->stream, roi->repair_mode == 2)) !=
-          cudaSuccess)
+    if (r.repair_mode == 1 || r.repair_mode == 2) {
+      if ((e = repair_stereo(ws, W, H, r.gate_tau, out->rgb_aff, ctx->stream, r.repair_mode == 2)) != cudaSuccess)
         return cuda_fail(e);
+    }
+    if (reuse) {  // the strip tiles are rendered already
+      const int rtiles = ((W + kTile - 1) / kTile) * ((H + kTile - 1) / kTile);
+      if ((e = cudaStreamWaitEvent(ctx->stream, ctx->ev_strip, 0)) == cudaSuccess)
+        e = launch_mask_minus(ws.tile_mask, ws.strip_mask, rtiles, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(e);
     }
     mark(ctx, 5);
     // Stage 4: targeted re-rasterisation of the ROI tiles of the affiliated eye
     // (the ROI mask lives on the 16-pixel grid; other tile edges bin on a copy
     // on their own grid)
     ctx->last_tiles = tx * ty;
-    const uint8_t *bmask = ctx->ws.tile_mask;
+    const uint8_t *bmask = ws.tile_mask;
     if (sh != 4) {
-      if ((e = launch_raster_mask(ctx->ws.tile_mask, W, H, sh, ctx->ws.bin[1].rmask, ctx->stream)) != cudaSuccess)
+      if ((e = launch_raster_mask(ws.tile_mask, W, H, sh, ws.bin[1].rmask, ctx->stream)) != cudaSuccess)
         return cuda_fail(e);
-      bmask = ctx->ws.bin[1].rmask;
+      bmask = ws.bin[1].rmask;
     }
-    e = launch_binning(ctx->ws, 1, scene->n, tx, ty, bmask, ctx->stream, p.parallel ? kOrderReuse : kOrderOwn);
+    e = launch_binning(ws, 1, scene->n, tx, ty, bmask, ctx->stream, p.parallel ? kOrderReuse : kOrderOwn);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
-    e = raster_one(ctx, raster_frame(ctx->ws, 1, W, H, sh, ctx->ws.tile_mask, black, out->rgb_aff, nullptr, nullptr,
-                                     ctx->ws.cls, false));
+    e = raster_one(ctx, raster_frame(ws, 1, W, H, sh, ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ws.cls,
+                                     false));
+    if (e == cudaSuccess && reuse) e = launch_strip_composite(ws, W, H, ws.strip_rgb, out->rgb_aff, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 7);
     e = copy_optional(ctx, out, W, H);
     mark(ctx, 8);
     return cuda_status(e);
   });
+  if (res == GS_OK) ctx->have_range = 1;
+  return res;
 }
 
 gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,

@@ -521,18 +521,28 @@ gs_status gs_batch_check(gs_batch *b, int *device_status) {
 }
 
 gs_status gs_render_stereo_batch(gs_batch *b, const gs_frame *frames, int n_frames, int gap_thresh,
-                                 const gs_roi_params *roi) {
-  if (!b || !roi_ok(gap_thresh, roi)) return GS_ERR_BAD_ARG;
-  const gs_status cs = check_frames(b, frames, n_frames, roi);
+                                 const gs_roi_params *roi_in) {
+  if (!b || !roi_ok(gap_thresh, roi_in)) return GS_ERR_BAD_ARG;
+  const gs_status cs = check_frames(b, frames, n_frames, roi_in);
   if (cs != GS_OK) return cs;
+  // depth_mode 2 (the previous call's range) needs a previous call on every
+  // slot; until then every frame measures its own (mode 0)
+  gs_roi_params rr = *roi_in;
+  if (rr.depth_mode == 2)
+    for (int f = 0; f < n_frames; ++f)
+      if (!b->slot[f]->have_range) rr.depth_mode = 0;
+  const gs_roi_params *roi = &rr;
   FrameGeom g[kRasterFrames];
   for (int f = 0; f < n_frames; ++f) g[f] = geom(b, frames[f]);
   KeyBuilder kb;
   key_frames(kb, b, 0, frames, n_frames, g);
   kb.add(gap_thresh);
   kb.add(*roi);
-  return batch_run(b, 0, kb, g, n_frames,
-                   [&]() { return enqueue_batch(b, frames, n_frames, g, gap_thresh, roi, false); });
+  const gs_status res = batch_run(b, 0, kb, g, n_frames,
+                                  [&]() { return enqueue_batch(b, frames, n_frames, g, gap_thresh, roi, false); });
+  if (res == GS_OK)
+    for (int f = 0; f < n_frames; ++f) b->slot[f]->have_range = 1;
+  return res;
 }
 
 gs_status gs_render_mono_batch(gs_batch *b, const gs_mono_frame *frames, int n_frames) {

@@ -35,6 +35,9 @@ struct gs_context {
   int rp_loaded;        // repair network weights present
   int rp_fp8;           // FP8 scales and weights calibrated for the current weights
   int rp_step;          // AdamW steps taken
+  int have_range;       // a stereo call has measured a depth range (depth_mode 2 can reuse it)
+  cudaStream_t side;    // second stream of a stereo call with depth_mode 2
+  cudaEvent_t ev_fork, ev_edge, ev_strip;
 };
 
 namespace gs {

@@ -119,6 +119,7 @@ struct Workspace {
   BinScratch bin[2];            // per eye
   uint8_t *tile_mask;           // ROI mask on the 16-pixel grid
   uint8_t *strip_mask;          // edge-strip tiles of a reused depth range (16-pixel grid)
+  float *strip_rgb;             // [3][pixels] the affiliated eye's strip tiles, rendered ahead
   uint32_t *row_off[2];         // per surfel and eye: slot of its first rectangle row in spans
   uint2 *spans[2];              // per (surfel, tile row): tile ranges [a0, a1] u [c0, c1], 4 x 16 bits
   // scans outside the binning (centre ROIs, repair tile lists) use bin[0]'s scratch
@@ -274,6 +275,21 @@ cudaError_t launch_raster_mask(const uint8_t *roi, int W, int H, int tshift, uin
 size_t ssim_partials(int max_w, int max_h);
 cudaError_t launch_ssim(const float *a, const float *b, int W, int H, int C, double *part, float *out,
                         cudaStream_t s);
+// The stages of launch_warp_classify one by one: the warp (clears the warp
+// buffer and the ROI mask first), the edge ROI (into `mask`: ORed into the
+// cleared ROI mask, or every tile assigned when `assign`), and the
+// classification (which also keeps this frame's measured depth range for the
+// next frame's depth_mode 2).
+cudaError_t launch_warp(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,
+                        cudaStream_t s);
+cudaError_t launch_edge_roi(const Workspace &ws, const gs_roi_params &roi, uint8_t *mask, bool assign,
+                            cudaStream_t s);
+cudaError_t launch_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
+                            const float *rgb_dom, float *rgb_aff, cudaStream_t s);
+// Strip tiles of an image rendered ahead -> the affiliated image (and class bits).
+cudaError_t launch_strip_composite(const Workspace &ws, int W, int H, const float *src, float *rgb_aff,
+                                   cudaStream_t s);
+cudaError_t launch_mask_minus(uint8_t *mask, const uint8_t *minus, int n, cudaStream_t s);
 // Warp, edge ROIs, hole classification and gap filling (writes rgb_aff and cls).
 cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
                                  const float *rgb_dom, const float *depth_dom, const float *trans_dom,

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restric
                                                        int N, int m, int depth_mode, float fixed_min,
                                                        float fixed_max, int32_t *__restrict__ strips,
                                                        int32_t *__restrict__ widths, float *__restrict__ drange,
-                                                       uint8_t *__restrict__ tile_mask) {
+                                                       uint8_t *__restrict__ tile_mask, int assign) {
   griddep_wait();
   const CamBlock &cb = *cams;
   const int W = cb.eye[1].W, H = cb.eye[1].H;
@@ -85,10 +85,12 @@ __global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restric
   __shared__ int sxmin, sxmax, symin, symax, sany;
   __shared__ int sstrip[16];
   float dmin = fixed_min, dmax = fixed_max;
-  if (depth_mode == 0) {
-    dmin = __uint_as_float(ctr->dmin_bits);
-    dmax = __uint_as_float(ctr->dmax_bits);
-    if (ctr->dmax_bits == 0u) dmin = dmax = 0.f;  // no valid pixel
+  if (depth_mode == 0 || depth_mode == 2) {  // this frame's range, or the previous frame's
+    const uint32_t lo = depth_mode == 0 ? ctr->dmin_bits : ctr->prev_range[0];
+    const uint32_t hi = depth_mode == 0 ? ctr->dmax_bits : ctr->prev_range[1];
+    dmin = __uint_as_float(lo);
+    dmax = __uint_as_float(hi);
+    if (hi == 0u) dmin = dmax = 0.f;  // no valid pixel
   }
   if (threadIdx.x == 0) {
     sxmin = symin = 0x7fffffff;
@@ -149,7 +151,8 @@ __global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restric
       const int *r = sstrip + 4 * k;
       in |= x0 < r[2] && x0 + kTile > r[0] && y0 < r[3] && y0 + kTile > r[1];
     }
-    if (in) tile_mask[t] = 1;
+    if (assign) tile_mask[t] = in ? 1 : 0;  // a mask of its own
+    else if (in) tile_mask[t] = 1;         // into the cleared ROI mask
   }
 }
 
@@ -175,8 +178,15 @@ struct WarpView {
 
 __global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_t *__restrict__ strips, int gap,
                                                        int center_enabled, float *__restrict__ rgb_aff,
-                                                       float *__restrict__ warp_depth, uint8_t *__restrict__ cls) {
+                                                       float *__restrict__ warp_depth, uint8_t *__restrict__ cls,
+                                                       Counters *__restrict__ ctr) {
   griddep_wait();
+  // this frame's measured depth range, kept for the next frame's edge ROI
+  // (depth_mode 2); the edge ROI of this frame has read the previous one
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctr->prev_range[0] = ctr->dmin_bits;
+    ctr->prev_range[1] = ctr->dmax_bits;
+  }
   const int W = wv.W, H = wv.H;
   const int64_t npix = (int64_t)W * H;
   __shared__ int s[16];
@@ -396,27 +406,88 @@ static int grid_for(int64_t n, int per_block = 256) {
   return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
 }
 
-cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
-                                 const float *rgb_dom, const float *depth_dom, const float *trans_dom,
-                                 float *rgb_aff, cudaStream_t s) {
-  cudaError_t err;
+cudaError_t launch_warp(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,
+                        cudaStream_t s) {
   const int64_t npix = (int64_t)W * H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-  if ((err = launch_k(warp_init_kernel, grid_for(npix), 256, 0, s, ws.warpbuf, npix, ws.tile_mask,
-                      tiles_x * tiles_y)) != cudaSuccess)
-    return err;
-  launch_k(edge_roi_kernel, 1, 256, 0, s, ws.cams, ws.ctr, roi.samples_per_edge, roi.margin, roi.depth_mode, roi.d_min,
-                                    roi.d_max, ws.strips, ws.widths, ws.drange, ws.tile_mask);
-  launch_k(warp_scatter_kernel, grid_for(npix), 256, 0, s, ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H);
+  cudaError_t err = launch_k(warp_init_kernel, grid_for(npix), 256, 0, s, ws.warpbuf, npix, ws.tile_mask,
+                             tiles_x * tiles_y);
+  if (err == cudaSuccess)
+    err = launch_k(warp_scatter_kernel, grid_for(npix), 256, 0, s, ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H);
+  GS_LAUNCHED(2);
+  return err;
+}
+
+cudaError_t launch_edge_roi(const Workspace &ws, const gs_roi_params &roi, uint8_t *mask, bool assign,
+                            cudaStream_t s) {
+  const cudaError_t err = launch_k(edge_roi_kernel, 1, 256, 0, s, ws.cams, ws.ctr, roi.samples_per_edge, roi.margin,
+                                   roi.depth_mode, roi.d_min, roi.d_max, ws.strips, ws.widths, ws.drange, mask,
+                                   assign ? 1 : 0);
+  GS_LAUNCHED(1);
+  return err;
+}
+
+cudaError_t launch_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
+                            const float *rgb_dom, float *rgb_aff, cudaStream_t s) {
+  const int64_t npix = (int64_t)W * H;
   WarpView wv{ws.warpbuf, rgb_dom, W, H, (size_t)npix};
   // the row/column fill of the remaining holes is the output when the centre step
   // is off, and the repair network's starting point in the repair modes (there
   // the ROI re-render or the network overwrites those pixels)
   const int fill_all = !roi.enable_center || roi.repair_mode != 0;
-  launch_k(classify_kernel, grid_for(npix), 256, 0, s, wv, ws.strips, gap_thresh, fill_all ? 0 : 1, rgb_aff,
-                                                  ws.warp_depth, ws.cls);
-  GS_LAUNCHED(4);
-  return cudaGetLastError();
+  const cudaError_t err = launch_k(classify_kernel, grid_for(npix), 256, 0, s, wv, ws.strips, gap_thresh,
+                                   fill_all ? 0 : 1, rgb_aff, ws.warp_depth, ws.cls, ws.ctr);
+  GS_LAUNCHED(1);
+  return err;
+}
+
+cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
+                                 const float *rgb_dom, const float *depth_dom, const float *trans_dom,
+                                 float *rgb_aff, cudaStream_t s) {
+  cudaError_t err = launch_warp(ws, W, H, depth_dom, trans_dom, s);
+  if (err == cudaSuccess) err = launch_edge_roi(ws, roi, ws.tile_mask, false, s);
+  if (err == cudaSuccess) err = launch_classify(ws, W, H, gap_thresh, roi, rgb_dom, rgb_aff, s);
+  return err;
+}
+
+// Copies the strip tiles' pixels of an image rendered ahead (the edge strips of a
+// reused depth range) into the affiliated image and marks them re-rendered.
+__global__ void strip_composite_kernel(const uint8_t *__restrict__ strip_mask, int W, int H,
+                                       const float *__restrict__ src, float *__restrict__ dst,
+                                       uint8_t *__restrict__ cls) {
+  griddep_wait();
+  const int64_t npix = (int64_t)W * H;
+  const int tiles_x = (W + kTile - 1) / kTile;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(p % W), y = (int)(p / W);
+    if (!strip_mask[(y / kTile) * tiles_x + x / kTile]) continue;
+    dst[p] = src[p];
+    dst[npix + p] = src[npix + p];
+    dst[2 * npix + p] = src[2 * npix + p];
+    cls[p] |= (uint8_t)kClsRender;
+  }
+}
+
+// mask &= ~minus (tiles already rendered elsewhere leave the mask)
+__global__ void mask_minus_kernel(uint8_t *__restrict__ mask, const uint8_t *__restrict__ minus, int n) {
+  griddep_wait();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if (minus[i]) mask[i] = 0;
+}
+
+cudaError_t launch_strip_composite(const Workspace &ws, int W, int H, const float *src, float *rgb_aff,
+                                   cudaStream_t s) {
+  const int64_t npix = (int64_t)W * H;
+  const cudaError_t err = launch_k(strip_composite_kernel, grid_for(npix), 256, 0, s, (const uint8_t *)ws.strip_mask,
+                                   W, H, src, rgb_aff, ws.cls);
+  GS_LAUNCHED(1);
+  return err;
+}
+
+cudaError_t launch_mask_minus(uint8_t *mask, const uint8_t *minus, int n, cudaStream_t s) {
+  const cudaError_t err = launch_k(mask_minus_kernel, grid_for(n), 256, 0, s, mask, minus, n);
+  GS_LAUNCHED(1);
+  return err;
 }
 
 cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cudaStream_t s) {
