@@ -19,7 +19,7 @@ _lib = None
 
 class OrScene(C.Structure):
     _fields_ = [("n", C.c_int), ("sh_degree", C.c_int), ("pos", C.c_void_p), ("quat", C.c_void_p),
-                ("scale", C.c_void_p), ("opacity", C.c_void_p), ("sh", C.c_void_p)]
+                ("scale", C.c_void_p), ("opacity", C.c_void_p), ("sh", C.c_void_p), ("primitive", C.c_int)]
 
 
 class OrPose(C.Structure):
@@ -67,7 +67,7 @@ class _SceneRef:
     def __init__(self, scene):
         self.arrays = [np.ascontiguousarray(a, dtype=np.float32) for a in
                        (scene.pos, scene.quat, scene.scale, scene.opacity, scene.sh)]
-        self.s = OrScene(scene.n, scene.sh_degree, *[_p(a) for a in self.arrays])
+        self.s = OrScene(scene.n, scene.sh_degree, *[_p(a) for a in self.arrays], int(getattr(scene, "primitive", 0)))
 
 
 def pose_struct(pose):

@@ -31,6 +31,7 @@ typedef struct {
   int n;
   int sh_degree;
   const float *pos, *quat, *scale, *opacity, *sh;
+  int primitive; /* 0: 2D surfels (scale [n][2]); 1: 3D ellipsoids (scale [n][4]: sx, sy, sz, unused) */
 } or_scene;
 
 typedef struct {
@@ -55,6 +56,8 @@ typedef struct {
   double rgb[3];
   float key;        /* float32(p_c.z): the depth-order key */
   double box[4];    /* xmin, xmax, ymin, ymax enclosing the whole support (a cheap exact reject) */
+  int prim;         /* 0: surfel; 1: ellipsoid */
+  double conic[3];  /* ellipsoid: inverse of the 2-D screen covariance (xx, xy, yy) */
 } or_splat;
 
 /* ---- constants of the blending rule (3DGS/2DGS rasterizer conventions) ---- */

@@ -94,9 +94,83 @@ static void project(const or_cam *cam, const double X[3], double *u, double *v) 
   *v = cam->fy * X[1] / X[2] + cam->cy;
 }
 
+/* 3D Gaussian (ellipsoid) variant, the 3DGS backbone the method also accepts
+ * (Sec. 3.2: any Gaussian splatting variant with per-pixel depth), in the EWA
+ * splatting convention of the 3DGS rasterizer: world covariance
+ * Sigma = Rq diag(s^2) Rq^T; camera covariance W Sigma W^T with W = R^T (the
+ * world-to-camera rotation); screen covariance J (W Sigma W^T) J^T + 0.3 I with
+ * the perspective Jacobian J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]] at
+ * the centre (not clamped); alpha = o exp(-d^T Sigma2D^-1 d / 2); the depth of a
+ * contribution is the centre depth. */
+static void prepare_ellipsoid(const or_scene *sc, const or_pose *pose, const or_cam *cam, int i, or_splat *s) {
+  double Rq[9];
+  if (!or_quat_to_rot(sc->quat + 4 * (size_t)i, Rq)) return;
+  const double o = sc->opacity[i];
+  if (!(255.0 * o >= 1.0)) return;
+  const double *R = pose->R, *t = pose->t;
+  const double p[3] = {sc->pos[4 * (size_t)i], sc->pos[4 * (size_t)i + 1], sc->pos[4 * (size_t)i + 2]};
+  const double dp[3] = {p[0] - t[0], p[1] - t[1], p[2] - t[2]};
+  double pc[3];
+  for (int k = 0; k < 3; ++k) pc[k] = R[0 * 3 + k] * dp[0] + R[1 * 3 + k] * dp[1] + R[2 * 3 + k] * dp[2];
+  if (!(pc[2] > OR_Z_NEAR)) return;
+  const float *sv = sc->scale + 4 * (size_t)i;
+  const double s2[3] = {(double)sv[0] * sv[0], (double)sv[1] * sv[1], (double)sv[2] * sv[2]};
+  /* camera-frame axes of the ellipsoid: A = R^T Rq, covariance A diag(s^2) A^T */
+  double A[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) A[r * 3 + c] = R[0 * 3 + r] * Rq[0 * 3 + c] + R[1 * 3 + r] * Rq[1 * 3 + c] +
+                                            R[2 * 3 + r] * Rq[2 * 3 + c];
+  double V[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      V[r * 3 + c] = A[r * 3 + 0] * s2[0] * A[c * 3 + 0] + A[r * 3 + 1] * s2[1] * A[c * 3 + 1] +
+                     A[r * 3 + 2] * s2[2] * A[c * 3 + 2];
+  const double z = pc[2];
+  const double J[6] = {cam->fx / z, 0.0, -cam->fx * pc[0] / (z * z), 0.0, cam->fy / z, -cam->fy * pc[1] / (z * z)};
+  double JV[6];
+  for (int r = 0; r < 2; ++r)
+    for (int c = 0; c < 3; ++c) JV[r * 3 + c] = J[r * 3 + 0] * V[0 * 3 + c] + J[r * 3 + 1] * V[1 * 3 + c] +
+                                             J[r * 3 + 2] * V[2 * 3 + c];
+  const double cxx = JV[0] * J[0] + JV[1] * J[1] + JV[2] * J[2] + 0.3;
+  const double cxy = JV[0] * J[3] + JV[1] * J[4] + JV[2] * J[5];
+  const double cyy = JV[3] * J[3] + JV[4] * J[4] + JV[5] * J[5] + 0.3;
+  const double det = cxx * cyy - cxy * cxy;
+  if (!(det > 0.0)) return;
+  s->prim = 1;
+  s->conic[0] = cyy / det;
+  s->conic[1] = -cxy / det;
+  s->conic[2] = cxx / det;
+  s->opacity = o;
+  s->rc2 = 2.0 * log(255.0 * o); /* d^T conic d <= rc2  <=>  alpha >= 1/255 */
+  project(cam, pc, &s->cx, &s->cy);
+  const double ex = sqrt(s->rc2 * cxx), ey = sqrt(s->rc2 * cyy); /* the support ellipse's half extents */
+  const double eps = 1e-6;
+  s->box[0] = s->cx - ex - eps; s->box[1] = s->cx + ex + eps;
+  s->box[2] = s->cy - ey - eps; s->box[3] = s->cy + ey + eps;
+  for (int k = 0; k < 3; ++k) s->pc[k] = pc[k];
+  double dir[3] = {dp[0], dp[1], dp[2]};
+  const double dn = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+  for (int k = 0; k < 3; ++k) dir[k] /= dn;
+  double Y[16];
+  const int deg = sc->sh_degree, K = (deg + 1) * (deg + 1);
+  or_sh_basis(deg, dir, Y);
+  const float *c = sc->sh + (size_t)i * K * 3;
+  for (int ch = 0; ch < 3; ++ch) {
+    double acc = 0.5;
+    for (int k = 0; k < K; ++k) acc += Y[k] * c[k * 3 + ch];
+    s->rgb[ch] = acc > 0.0 ? acc : 0.0;
+  }
+  s->key = (float)pc[2];
+  s->visible = 1;
+}
+
 static void prepare_one(const or_scene *sc, const or_pose *pose, const or_cam *cam, int i,
                         or_splat *s) {
   memset(s, 0, sizeof(*s));
+  if (sc->primitive == 1) {
+    prepare_ellipsoid(sc, pose, cam, i, s);
+    return;
+  }
   double Rq[9];
   if (!or_quat_to_rot(sc->quat + 4 * (size_t)i, Rq)) return;
   const double o = sc->opacity[i];
@@ -174,6 +248,14 @@ double or_eval(const or_splat *s, const or_cam *cam, double x, double y, double 
    * coordinates (u, v) is M (u, v, 1); it lies on the ray at depth lambda when
    * M (u, v, 1) = lambda r, i.e. (a, b, g) = M^{-1} r with u = a/g, v = b/g,
    * lambda = 1/g. Solved by Cramer's rule. */
+  if (s->prim == 1) { /* ellipsoid: the screen-space Gaussian, centre depth */
+    const double dx = x - s->cx, dy = y - s->cy;
+    const double rho = s->conic[0] * dx * dx + 2.0 * s->conic[1] * dx * dy + s->conic[2] * dy * dy;
+    if (depth) *depth = s->pc[2];
+    if (rho3_out) *rho3_out = rho;
+    if (rho2_out) *rho2_out = INFINITY;
+    return s->opacity * exp(-0.5 * rho);
+  }
   const double r[3] = {(x - cam->cx) / cam->fx, (y - cam->cy) / cam->fy, 1.0};
   const double c0[3] = {s->M[0], s->M[3], s->M[6]};
   const double c1[3] = {s->M[1], s->M[4], s->M[7]};

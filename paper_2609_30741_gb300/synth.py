@@ -39,6 +39,7 @@ class Scene:
     opacity: np.ndarray
     sh: np.ndarray
     sh_degree: int
+    primitive: int = 0  # 0: 2D surfels, scale [n][2]; 1: 3D ellipsoids, scale [n][4] (sx, sy, sz, 0)
 
     @property
     def n(self) -> int:
@@ -47,7 +48,7 @@ class Scene:
     def subset(self, idx) -> "Scene":
         idx = np.asarray(idx)
         return Scene(self.pos[idx].copy(), self.quat[idx].copy(), self.scale[idx].copy(),
-                     self.opacity[idx].copy(), self.sh[idx].copy(), self.sh_degree)
+                     self.opacity[idx].copy(), self.sh[idx].copy(), self.sh_degree, self.primitive)
 
     def nbytes(self) -> int:
         return sum(a.nbytes for a in (self.pos, self.quat, self.scale, self.opacity, self.sh))
@@ -258,6 +259,17 @@ def workload_object(seed: int = 1200, n: int = 500_000, pose_index: int = 0,
     cam = centred_camera(width, height, f)
     dom, aff = eye_pair(arc_poses()[pose_index])
     return scene_object_ground(seed, n), cam, dom, aff
+
+
+def to_ellipsoids(scene: Scene, thickness: float = 0.1) -> Scene:
+    """The same primitives as 3D Gaussians (the 3DGS backbone): tangent scales
+    kept, a third axis along the surfel normal of `thickness` times the smaller
+    tangent scale."""
+    s = np.asarray(scene.scale, np.float32)
+    sz = thickness * np.minimum(s[:, 0], s[:, 1])
+    scale = np.stack([s[:, 0], s[:, 1], sz, np.zeros_like(sz)], 1).astype(np.float32)
+    return Scene(scene.pos.copy(), scene.quat.copy(), scale, scene.opacity.copy(), scene.sh.copy(),
+                 scene.sh_degree, 1)
 
 
 def workload_batched(seed: int = 1500, scale: float = 1.0):

@@ -619,3 +619,88 @@ def test_tile_test_matches_dense_sampling(orc):
         assert orc.tile_test(rec, k, x0, x1, y0, y1) == (mn <= k)
         checked += 1
     assert checked > 200
+
+
+# ----------------------------------------------------------------------------- 3D Gaussian (ellipsoid) backbone
+
+def _one_ellipsoid(pos, quat, scales, o, rgb_coeff):
+    return synth.Scene(np.array([[*pos, 1.0]], np.float32), np.array([quat], np.float32),
+                       np.array([[*scales, 0.0]], np.float32), np.array([o], np.float32),
+                       np.array([[[c] for c in rgb_coeff]], np.float32).reshape(1, 1, 3), 0, 1)
+
+
+def test_ellipsoid_on_axis_closed_form(orc):
+    """An ellipsoid centred on the optical axis, rotated by theta about it: the
+    Jacobian's depth column vanishes there, so the screen covariance is
+    (f/z)^2 R2 diag(sa^2, sb^2) R2^T + 0.3 I, whatever the third scale."""
+    f, z, th = 300.0, 3.0, 0.6
+    sa, sb, sc_, o = 0.02, 0.008, 0.05, 0.8
+    cam = synth.Camera(f, f, 64.0, 48.0, 129, 97)
+    q = (math.cos(th / 2), 0.0, 0.0, math.sin(th / 2))
+    coeff = (0.4, -0.2, 0.9)
+    scene = _one_ellipsoid((0.0, 0.0, z), q, (sa, sb, sc_), o, coeff)
+    rgb, dep, tr, _, _ = orc.render(scene, synth.identity_pose(), cam)
+    # the values the float32 scene arrays hold
+    R2 = rot_from_quat_scipy(np.asarray(scene.quat[0], np.float64))[:2, :2]
+    sa, sb, o, z = f32(sa), f32(sb), f32(o), f32(z)
+    S = (f / z) ** 2 * R2 @ np.diag([sa * sa, sb * sb]) @ R2.T + 0.3 * np.eye(2)
+    Si = np.linalg.inv(S)
+    col = np.maximum(0.0, 0.5 + 0.5 * math.sqrt(1.0 / math.pi) * np.array([f32(c) for c in coeff]))
+    for (x, y) in ((64, 48), (66, 47), (61, 52), (70, 44)):
+        d = np.array([x - 64.0, y - 48.0])
+        a = o * math.exp(-0.5 * d @ Si @ d)
+        if a < 1.0 / 255:
+            assert tr[y, x] == 1.0
+            continue
+        a = min(a, 0.99)
+        np.testing.assert_allclose(rgb[:, y, x], a * col, rtol=1e-12, atol=1e-15)
+        assert abs(tr[y, x] - (1 - a)) < 1e-14 and abs(dep[y, x] - a * z) < 1e-12
+
+
+def test_ellipsoid_off_axis_matches_numeric_jacobian(orc):
+    """Off the axis the screen covariance is J V J^T + 0.3 I with J the
+    projection's Jacobian at the centre: compare with central differences of the
+    pinhole projection itself."""
+    f = 250.0
+    cam = synth.Camera(f, f, 80.0, 60.0, 161, 121)
+    pos = np.array([0.4, -0.3, 2.5])
+    q = np.array([0.8, 0.3, -0.4, 0.33])
+    q /= np.linalg.norm(q)
+    s = np.array([0.03, 0.012, 0.02])
+    o = 0.9
+    scene = _one_ellipsoid(tuple(pos), tuple(q), tuple(s), o, (1.0, 1.0, 1.0))
+    rgb, _, tr, _, _ = orc.render(scene, synth.identity_pose(), cam)
+    Rq = rot_from_quat_scipy(np.asarray(scene.quat[0], np.float64))
+    V = Rq @ np.diag(s.astype(np.float32).astype(np.float64) ** 2) @ Rq.T
+
+    def proj(X):
+        return np.array([f * X[0] / X[2] + cam.cx, f * X[1] / X[2] + cam.cy])
+    h = 1e-6
+    J = np.stack([(proj(pos.astype(np.float32).astype(np.float64) + h * e) -
+                   proj(pos.astype(np.float32).astype(np.float64) - h * e)) / (2 * h) for e in np.eye(3)], 1)
+    S = J @ V @ J.T + 0.3 * np.eye(2)
+    c = proj(pos.astype(np.float32).astype(np.float64))
+    Si = np.linalg.inv(S)
+    o = f32(o)
+    checked = 0
+    for y in range(121):
+        for x in range(161):
+            d = np.array([x, y]) - c
+            a = o * math.exp(-0.5 * d @ Si @ d)
+            if a < 2.0 / 255:
+                continue
+            assert abs((1.0 - tr[y, x]) - min(a, 0.99)) < 1e-8, (x, y)
+            checked += 1
+    assert checked > 20
+
+
+def test_ellipsoid_weights_and_transmittance_sum_to_one(orc):
+    # white colour, black background: the image is the sum of the weights
+    rng = np.random.default_rng(41)
+    base = synth.random_scene(42, 60, sh_degree=0, z_range=(1.5, 3.0), scale_mu=math.log(0.05))
+    base.sh[:] = (0.5 / (0.5 * math.sqrt(1.0 / math.pi)))  # 0.5 + Y00 c = 1
+    scene = synth.to_ellipsoids(base, thickness=0.5)
+    cam = synth.centred_camera(64, 48, 60.0)
+    rgb, _, tr, _, _ = orc.render(scene, synth.identity_pose(), cam)
+    np.testing.assert_allclose(rgb[0] + tr, 1.0, atol=1e-12)
+    assert (tr < 0.999).mean() > 0.3
