@@ -41,7 +41,7 @@ class OrSplat(C.Structure):
     _fields_ = [("visible", C.c_int), ("pc", C.c_double * 3), ("M", C.c_double * 9),
                 ("opacity", C.c_double), ("rc2", C.c_double), ("lp2", C.c_double),
                 ("cx", C.c_double), ("cy", C.c_double), ("rgb", C.c_double * 3),
-                ("key", C.c_float), ("box", C.c_double * 4)]
+                ("key", C.c_float), ("box", C.c_double * 4), ("prim", C.c_int), ("conic", C.c_double * 3)]
 
 
 CLS_HOLE, CLS_GAP, CLS_CENTRE, CLS_STRIP, CLS_RENDER = 1, 2, 4, 8, 16
