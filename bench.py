@@ -66,6 +66,8 @@ def parse():
                     help="skip the batched 16-frame workload (4 scenes x 4 poses, one call)")
     ap.add_argument("--no-unbounded", action="store_true",
                     help="skip the unbounded-scene learned-repair workload (1.5M surfels, 1920x1080)")
+    ap.add_argument("--no-backbone3d", action="store_true",
+                    help="skip the 2DGS vs 3DGS backbone comparison on the object scene")
     ap.add_argument("--no-hmd", action="store_true",
                     help="skip the headset FP8 workload (3M surfels, 2448x2448, 120-frame trajectory)")
     return ap.parse_args()
@@ -482,10 +484,12 @@ def run_ours(args):
     learned, weights = None, None
     if not args.no_learned:
         learned, weights = run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc)
-    batched = unbounded = hmd = None
+    batched = unbounded = hmd = backbone3d = None
     if ws_ == 1:
         del ds, out, out2
         torch.cuda.empty_cache()
+        if not args.no_backbone3d:
+            backbone3d = run_backbone3d(args, dev, flush)
         if not args.no_batched:
             batched = run_batched(args, dev, flush, weights)
         if not args.no_unbounded and not args.no_learned:
@@ -527,6 +531,7 @@ def run_ours(args):
         "batched": batched,
         "unbounded_learned": unbounded,
         "hmd_fp8": hmd,
+        "backbone_3dgs": backbone3d,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -787,6 +792,83 @@ def run_unbounded(args, dev, flush):
                        "data": "unbounded-distribution seeds 7100-7103 (1.5M surfels each), 6 random head poses "
                                "each, 1920x1080"}
     return res, w, calib
+
+
+def run_backbone3d(args, dev, flush):
+    """The 3DGS backbone beside 2DGS (Sec. 3.2): the C2 object scene as 2D
+    surfels and as 3D ellipsoids with the same centres, rotations, tangent
+    scales, opacities and colours (third axis 0.3 x the smaller tangent scale),
+    same poses and ROI parameters. Per backbone: ms per stereo frame and two-pass
+    frame (each arm autotuned), quality of the affiliated eye against its own full
+    render, and the shares of warp holes, interpolated gaps, centre holes and
+    re-rendered (ROI) pixels of the affiliated eye."""
+    import torch
+    from paper_2609_30741_gb300 import gs, synth
+    scene2d, cam, _, _ = synth.workload_object(n=args.n)
+    poses = [synth.eye_pair(p) for p in synth.arc_poses()]
+    stream = torch.cuda.current_stream(dev)
+    roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1)
+    res = {"workload": "C2 object scene (500k) as surfels and as ellipsoids (third axis 0.3 x the smaller "
+                       "tangent scale), 1600x1200, 8 poses on a 30 deg arc",
+           "ellipsoid_thickness": 0.3}
+    for name, scene in (("2dgs", scene2d), ("3dgs", synth.to_ellipsoids(scene2d, 0.3))):
+        ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 27, device=dev)
+        ds = gs.DeviceScene(scene, device=dev)
+        out, out2 = ctx.alloc_outputs(cam), ctx.alloc_outputs(cam, with_cls=False)
+        d0, a0 = poses[0]
+        rc_s = gs.autotune_stereo(ctx, ds, d0, a0, cam, roi=roi, out=out, reps=3, use_cache=False)[0]
+        rc_t = gs.autotune_stereo(ctx, ds, d0, a0, cam, out=out2, reps=3, use_cache=False, two_pass=True)[0]
+
+        def stereo(k):
+            ctx.set_raster(*rc_s)
+            d, a = poses[k % 8]
+            ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+
+        def two(k):
+            ctx.set_raster(*rc_t)
+            d, a = poses[k % 8]
+            ctx.render_two_pass(ds, d, a, cam, out=out2)
+
+        def run(fn):
+            for k in range(args.warmup):
+                fn(k)
+            ctx.check_ok()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            torch.cuda.synchronize(dev)
+            for k in range(args.steps):
+                flush.fill_(k & 255)
+                ev[k][0].record(stream)
+                fn(args.warmup + k)
+                ev[k][1].record(stream)
+            torch.cuda.synchronize(dev)
+            ctx.check_ok()
+            return float(np.mean([x.elapsed_time(y) for x, y in ev]))
+
+        ms_s, ms_t = run(stereo), run(two)
+        ps, ss, shares = [], [], {"hole": [], "gap": [], "centre_hole": [], "roi": []}
+        ctx.set_counting(True)
+        pairs = []
+        for k in range(8):
+            stereo(k)
+            pairs.append(ctx.pair_counts()[0][0])
+            cls = out["cls_aff"].clone()
+            two(k)
+            ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
+            ss.append(float(ctx.ssim(out["rgb_aff"], out2["rgb_aff"])))
+            for key, bit in (("hole", gs.CLS_HOLE), ("gap", gs.CLS_GAP), ("centre_hole", gs.CLS_CENTRE),
+                             ("roi", gs.CLS_RENDER)):
+                shares[key].append(((cls & bit) > 0).float().mean().item())
+        ctx.set_counting(False)
+        ctx.check_ok()
+        res[name] = {"ms_per_stereo_frame": ms_s, "two_pass_ms": ms_t, "speedup_vs_two_pass": ms_t / ms_s,
+                     "psnr_aff_vs_full_db": float(np.mean(ps)), "ssim_aff_vs_full": float(np.mean(ss)),
+                     "pixel_share": {k: float(np.mean(v)) for k, v in shares.items()},
+                     "dominant_pairs_per_pixel": float(np.mean(pairs)) / (cam.width * cam.height),
+                     "raster": {"stereo": list(rc_s), "two_pass": list(rc_t)}}
+        del ctx, ds, out, out2
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_hmd(args, dev, flush, weights, calib):

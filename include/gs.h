@@ -17,7 +17,9 @@
  *   - Scene arrays, float32, structure of arrays:
  *       pos[n][4] surfel centre p_k (x, y, z, unused pad), 16-byte aligned
  *       quat[n][4] rotation (w, x, y, z), any non-zero norm (Sec. 3.3, Eq. 1)
- *       scale[n][2] in-plane scales (s_u, s_v) (Eq. 1)
+ *       scale[n][2] in-plane scales (s_u, s_v) (Eq. 1) of a surfel scene, or
+ *       scale[n][4] axis scales (s_x, s_y, s_z, unused pad) of an ellipsoid
+ *       scene (primitive 1, below), 16-byte aligned
  *       opacity[n]
  *       sh[n][(sh_degree+1)^2][3] real SH colour coefficients, degree 0..3
  *   - Poses are camera-to-world, double precision: P_world = R X_cam + t with
@@ -40,6 +42,17 @@
  * 1e-4; surfels are ordered by their float32 camera depth, ties by index.
  * A surfel is culled when its quaternion is zero, 255 o < 1, its centre is
  * within 0.2 m of the camera plane, or its support square reaches that plane.
+ *
+ * Ellipsoid scenes (gs_scene.primitive = 1): the 3D Gaussians of 3DGS, the
+ * other backbone the method accepts (Sec. 3.2: any Gaussian splatting variant
+ * with per-pixel depth), in the EWA splatting convention of the 3DGS
+ * rasterizer. Covariance Sigma = Rq diag(s^2) Rq^T; screen covariance
+ * Sigma2D = J W Sigma W^T J^T + 0.3 I with W the world-to-camera rotation and
+ * J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]] at the centre (unclamped);
+ * alpha = min(0.99, o exp(-d^T Sigma2D^-1 d / 2)), d the pixel offset from the
+ * projected centre, with no further low-pass term; the depth d_i of every
+ * contribution is the centre's camera depth. Ordering, the 1/255 and 1e-4
+ * rules and the z_near cull of the centre are those of surfels.
  */
 #ifndef GS_H
 #define GS_H
@@ -67,6 +80,7 @@ typedef struct {
   const float *pos, *quat, *scale, *opacity, *sh;
   int n;
   int sh_degree;
+  int primitive; /* 0: 2D surfels (scale[n][2]); 1: 3D ellipsoids (scale[n][4]) */
 } gs_scene;
 
 typedef struct {

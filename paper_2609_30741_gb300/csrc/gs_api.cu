@@ -223,10 +223,13 @@ namespace gs {
 
 bool scene_ok(const gs_context *ctx, const gs_scene *sc) {
   if (!sc || sc->n < 0 || sc->n > ctx->lim.max_surfels || sc->sh_degree < 0 || sc->sh_degree > 3) return false;
+  if (sc->primitive != 0 && sc->primitive != 1) return false;
   if (sc->n == 0) return true;
   if (!sc->pos || !sc->quat || !sc->scale || !sc->opacity || !sc->sh) return false;
-  // float4 loads need 16-byte alignment; scales are read as float2
-  if (((uintptr_t)sc->pos & 15) || ((uintptr_t)sc->quat & 15) || ((uintptr_t)sc->scale & 7) ||
+  // float4 loads need 16-byte alignment; surfel scales are read as float2,
+  // ellipsoid scales as float4
+  const uintptr_t scale_align = sc->primitive ? 15 : 7;
+  if (((uintptr_t)sc->pos & 15) || ((uintptr_t)sc->quat & 15) || ((uintptr_t)sc->scale & scale_align) ||
       ((uintptr_t)sc->opacity & 3))
     return false;
   if (sc->sh_degree == 3 && ((uintptr_t)sc->sh & 15)) return false;
@@ -572,7 +575,7 @@ static gs_status run_graph(gs_context *ctx, int kind, const void *key, size_t ke
 
 static void key_common(KeyBuilder &kb, gs_context *ctx, int kind, const gs_scene *scene, const gs_intrinsics *intr) {
   kb.add(kind);
-  kb.add(*scene);
+  kb.add_scene(*scene);
   kb.add(intr->width);
   kb.add(intr->height);
   kb.add(ctx->counting);

@@ -348,7 +348,7 @@ static void key_frames(KeyBuilder &kb, gs_batch *b, int kind, const gs_frame *fr
   kb.add(b->counting);
   kb.add(b->profiling);
   for (int f = 0; f < n; ++f) {
-    kb.add(*frames[f].scene);
+    kb.add_scene(*frames[f].scene);
     kb.add(frames[f].intr.width);
     kb.add(frames[f].intr.height);
     kb.add(frames[f].out);
@@ -567,7 +567,7 @@ gs_status gs_render_mono_batch(gs_batch *b, const gs_mono_frame *frames, int n_f
   kb.add(b->counting);
   kb.add(b->profiling);
   for (int f = 0; f < n_frames; ++f) {
-    kb.add(*frames[f].scene);
+    kb.add_scene(*frames[f].scene);
     kb.add(frames[f].intr.width);
     kb.add(frames[f].intr.height);
     kb.add(frames[f].bg);

@@ -129,7 +129,7 @@ __device__ __forceinline__ bool sat_any(const uint32_t *sat, int tiles_x, int y0
 __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ ids, const uint32_t *n_ptr,
                                                    uint32_t n_max, const float4 *__restrict__ rec,
                                                    const ushort4 *__restrict__ rect, const uint32_t *__restrict__ cnt,
-                                                   const CamBlock *__restrict__ cams, int eye,
+                                                   const CamBlock *__restrict__ cams, int eye, int prim,
                                                    uint32_t *__restrict__ row_off, uint2 *__restrict__ spans,
                                                    uint32_t cap, uint32_t *__restrict__ n_rows,
                                                    uint32_t *__restrict__ status) {
@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
     const float4 *r = rec + 4 * (size_t)i;
     const float4 r0 = r[0], r1 = r[1], r2 = r[2];
     q = make_conic(r0, r1, r2);
+    if (prim) q.rl2 = -1.f;  // ellipsoids have no low-pass disc
     cx = r0.x;
     cy = r0.y;
   }
@@ -736,7 +737,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   // were cleared by the compaction)
   if (n > 0) {
     launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, b.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
-                                                ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.row_off[eye],
+                                                ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.prim, ws.row_off[eye],
                                                 ws.spans[eye], (uint32_t)ws.max_instances, &ctr->n_rows[eye],
                                                 &ctr->status);
     GS_LAUNCHED(1);

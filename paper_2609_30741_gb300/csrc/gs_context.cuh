@@ -51,6 +51,11 @@ struct KeyBuilder {
     if (len + sizeof(T) <= sizeof(buf)) memcpy(buf + len, &v, sizeof(T));
     len += sizeof(T);
   }
+  // field by field: the struct's tail padding is not part of the key
+  void add_scene(const gs_scene &s) {
+    add(s.pos); add(s.quat); add(s.scale); add(s.opacity); add(s.sh);
+    add(s.n); add(s.sh_degree); add(s.primitive);
+  }
 };
 
 bool scene_ok(const gs_context *ctx, const gs_scene *sc);

@@ -21,6 +21,9 @@ constexpr float kNegHalfLog2e = -0.72134752044448170f;
 // the bounds of a surfel's support are grown by this many pixels so that the
 // float32 blend never evaluates a contributing pair outside its tile rectangle
 constexpr float kBoundPad = 1.0e-2f;
+// Low-pass factor that switches the surfel low-pass term off (ellipsoids): any
+// non-zero pixel offset gives a term above every record's support radius.
+constexpr float kNoLowpass = 3.0e38f;
 
 constexpr uint32_t kClsHole = 1, kClsGap = 2, kClsCentre = 4, kClsStrip = 8, kClsRender = 16,
                    kClsNet = 32;
@@ -151,6 +154,7 @@ struct Workspace {
   int64_t max_instances, max_pixels;
   int keep_intermediates;
   uint32_t bin_warp_surfels, bin_nch;  // binning chunk geometry (see launch_binning)
+  int prim;                     // primitive of the prepared records (gs_scene.primitive), set by launch_preprocess
 };
 
 constexpr int kScanThreads = 512;
@@ -172,7 +176,7 @@ bool carve_workspace(const gs_limits &lim, void *base, size_t bytes, Workspace *
 cudaError_t launch_setup_cams(const PoseArgs &pa, CamBlock *cams, cudaStream_t s);
 // Address of the set-up kernel (its graph node carries the per-frame poses).
 const void *setup_cams_kernel_ptr();
-cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes, int W, int H,
+cudaError_t launch_preprocess(const gs_scene &sc, Workspace &ws, int neyes, int W, int H,
                               cudaStream_t s);
 // Bins the visible surfels of `eye` (restricted to tile_mask when given) into
 // sorted per-tile instance lists and their ranges. Depth order:
@@ -246,6 +250,7 @@ struct RasterFrame {
   int W, H, tiles_x, ntiles, tshift;
   int eye;
   int stats;                // 1: record the range of D / (1 - T) over pixels with coverage >= 0.5
+  float lowpass;            // rho2 = lowpass |x - c|^2: 2 for surfels, kNoLowpass for ellipsoids
   uint32_t n_rec;           // records available (ids beyond are ignored)
 };
 struct RasterTable {

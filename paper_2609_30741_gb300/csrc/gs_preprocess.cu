@@ -1,7 +1,9 @@
 // Camera set-up (FP64) and per-surfel preprocessing for one or both eyes.
 //
 // Paper: Sec. 3.3 (2D Gaussian surfels, Eq. 1-2, ray-splat intersection),
-// Sec. 3.4 (pinhole projection, Eq. 3; poses, Eq. 4-5), Sec. 3.1 Stage 1.
+// Sec. 3.4 (pinhole projection, Eq. 3; poses, Eq. 4-5), Sec. 3.1 Stage 1;
+// Sec. 3.2 (the pipeline accepts any Gaussian splatting variant with per-pixel
+// depth: the 3D ellipsoids of 3DGS are prepared below as well).
 #include "gs_internal.cuh"
 #include "gs_launch.cuh"
 
@@ -114,6 +116,44 @@ __device__ __forceinline__ void sh_rgb(const float *__restrict__ c, int deg, flo
   out[2] = fmaxf(bl, 0.f);
 }
 
+// The SH coefficients of primitive i into registers (float4 loads at degree 3).
+__device__ __forceinline__ void load_sh(const gs_scene &sc, int i, float shc[48]) {
+  const int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
+  const float *src = sc.sh + (size_t)i * K * 3;
+  if (sc.sh_degree == 3) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const float4 v = s4[k];
+      shc[4 * k] = v.x; shc[4 * k + 1] = v.y; shc[4 * k + 2] = v.z; shc[4 * k + 3] = v.w;
+    }
+  } else {
+    for (int k = 0; k < 3 * K; ++k) shc[k] = src[k];
+  }
+}
+
+// Colour of a primitive centred at p seen from the eye's centre.
+__device__ __forceinline__ void view_rgb(const float *shc, int deg, const EyeCam &c, float4 p, float rgb[3]) {
+  float dx = p.x - c.centre[0], dy = p.y - c.centre[1], dz = p.z - c.centre[2];
+  const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+  sh_rgb(shc, deg, dx * dn, dy * dn, dz * dn, rgb);
+}
+
+// Tile rectangle of the pixels whose centres lie inside [xmin, xmax] x
+// [ymin, ymax]; the count is 0 when none does.
+__device__ __forceinline__ uint32_t tile_rect(const EyeCam &c, float xmin, float xmax, float ymin, float ymax,
+                                              ushort4 &rect) {
+  rect = make_ushort4(0, 0, 0, 0);
+  if (!(xmax >= 0.f && ymax >= 0.f && xmin <= c.W - 1.f && ymin <= c.H - 1.f)) return 0;
+  const int px0 = xmin <= 0.f ? 0 : (int)ceilf(xmin);
+  const int px1 = xmax >= c.W - 1.f ? c.W - 1 : (int)floorf(xmax);
+  const int py0 = ymin <= 0.f ? 0 : (int)ceilf(ymin);
+  const int py1 = ymax >= c.H - 1.f ? c.H - 1 : (int)floorf(ymax);
+  if (px0 > px1 || py0 > py1) return 0;
+  rect = make_ushort4(px0 >> c.tshift, py0 >> c.tshift, px1 >> c.tshift, py1 >> c.tshift);
+  return (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
+}
+
 // ---------------------------------------------------------------- preprocess
 //
 // One thread per surfel; the attributes are read once (coalesced float4 loads)
@@ -150,21 +190,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
   const float rc2 = alive ? 2.f * logf(255.f * o) : 0.f;
   const float rc = sqrtf(fmaxf(rc2, 0.f));
   const float lp = sqrtf(fmaxf(0.5f * rc2, 0.f));  // low-pass support radius, pixels
-  const int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
   float shc[48];
-  if (alive) {
-    const float *src = sc.sh + (size_t)i * K * 3;
-    if (sc.sh_degree == 3) {
-      const float4 *s4 = reinterpret_cast<const float4 *>(src);
-#pragma unroll
-      for (int k = 0; k < 12; ++k) {
-        const float4 v = s4[k];
-        shc[4 * k] = v.x; shc[4 * k + 1] = v.y; shc[4 * k + 2] = v.z; shc[4 * k + 3] = v.w;
-      }
-    } else {
-      for (int k = 0; k < 3 * K; ++k) shc[k] = src[k];
-    }
-  }
+  if (alive) load_sh(sc, i, shc);
   for (int e = 0; e < neyes; ++e) {
     const EyeCam &c = cams->eye[e];
     bool vis = alive;
@@ -200,19 +227,12 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
     xmin = fminf(xmin, cxp - lp) - kBoundPad; xmax = fmaxf(xmax, cxp + lp) + kBoundPad;
     ymin = fminf(ymin, cyp - lp) - kBoundPad; ymax = fmaxf(ymax, cyp + lp) + kBoundPad;
     // tile rectangle of the pixels whose centres lie inside the bounds
-    uint32_t count = 0;
-    ushort4 rect = make_ushort4(0, 0, 0, 0);
-    if (vis && xmax >= 0.f && ymax >= 0.f && xmin <= c.W - 1.f && ymin <= c.H - 1.f) {
-      const int px0 = xmin <= 0.f ? 0 : (int)ceilf(xmin);
-      const int px1 = xmax >= c.W - 1.f ? c.W - 1 : (int)floorf(xmax);
-      const int py0 = ymin <= 0.f ? 0 : (int)ceilf(ymin);
-      const int py1 = ymax >= c.H - 1.f ? c.H - 1 : (int)floorf(ymax);
-      if (px0 <= px1 && py0 <= py1) {
-        rect = make_ushort4(px0 >> c.tshift, py0 >> c.tshift, px1 >> c.tshift, py1 >> c.tshift);
-        count = (uint32_t)(rect.z - rect.x + 1) * (uint32_t)(rect.w - rect.y + 1);
-      }
+    ushort4 rect;
+    uint32_t count = tile_rect(c, xmin, xmax, ymin, ymax, rect);
+    if (!vis) {
+      count = 0;
+      rect = make_ushort4(0, 0, 0, 0);
     }
-    if (!vis) count = 0;
     ws.cnt[e][i] = count;
     ws.rect[e][i] = rect;
     ws.zkey[e][i] = __float_as_uint(pc[2]);
@@ -224,11 +244,8 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
     const float Bz = fmaf(V0, M2[1], -V1 * M2[0]) * izc;
     const float Cz = fmaf(M2[0], U1, -M2[1] * U0) * izc;
     // view-dependent colour from this eye's centre
-    float dx = p4.x - c.centre[0], dy = p4.y - c.centre[1], dz = p4.z - c.centre[2];
-    const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-    dx *= dn; dy *= dn; dz *= dn;
     float rgb[3];
-    sh_rgb(shc, sc.sh_degree, dx, dy, dz, rgb);
+    view_rgb(shc, sc.sh_degree, c, p4, rgb);
     float4 *r = ws.rec[e] + 4 * (size_t)i;
     r[0] = make_float4(cxp, cyp, rc2, pc[2]);
     r[1] = make_float4(V1, -V0, -U1, U0);
@@ -237,11 +254,105 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
   }
 }
 
-cudaError_t launch_preprocess(const gs_scene &sc, const Workspace &ws, int neyes, int W, int H,
-                              cudaStream_t s) {
+// Ellipsoids (3DGS backbone), EWA splatting. With the camera-frame axes
+// m_k = s_k W r_k (r_k the columns of Rq) the camera covariance is
+// sum_k m_k m_k^T, and with j_k = J m_k the screen covariance is
+// Sigma2D = sum_k j_k j_k^T + 0.3 I. Its determinant is assembled from
+// non-negative terms (Cauchy-Binet plus the dilation), so it keeps its relative
+// accuracy for elongated splats:
+//   det = sum_{k<l} (j_k x j_l)^2 + 0.3 (|j_0|^2 + |j_1|^2 + |j_2|^2) + 0.09.
+// The conic Q = Sigma2D^-1 = [[A, B], [B, C]] is stored as its upper Cholesky
+// factor L = [[l00, l01], [0, l11]], Q = L^T L, in closed form:
+// l00 = sqrt(cyy / det), l01 = -cxy / sqrt(det cyy), l11 = 1 / sqrt(cyy). The
+// record keeps the surfel layout: r1 = (l00, 0, l01, l11) for the plane point's
+// (x, y) rows, r2 = (1, 0, 0, 0) for a constant third coordinate and zero depth
+// slopes, so the rasterizer's u^2 + v^2 is d^T Q d and its depth the centre's.
+// The support d^T Q d <= 2 ln(255 o) has the half extents sqrt(k cxx) and
+// sqrt(k cyy).
+__global__ void __launch_bounds__(256) preprocess_ellipsoid_kernel(gs_scene sc, const CamBlock *__restrict__ cams,
+                                                                   Workspace ws, int neyes) {
+  griddep_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= sc.n) return;
+  const float4 p4 = reinterpret_cast<const float4 *>(sc.pos)[i];
+  const float4 q = reinterpret_cast<const float4 *>(sc.quat)[i];
+  const float4 s4 = reinterpret_cast<const float4 *>(sc.scale)[i];
+  const float o = sc.opacity[i];
+  const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  const bool alive = qn2 > 0.f && 255.f * o >= 1.f;
+  const float qi = alive ? rsqrtf(qn2) : 0.f;
+  const float w = q.x * qi, x = q.y * qi, y = q.z * qi, z = q.w * qi;
+  // the three columns of Rq, scaled by the axis lengths
+  const float ax[3][3] = {
+      {s4.x * (1.f - 2.f * (y * y + z * z)), s4.x * 2.f * (x * y + w * z), s4.x * 2.f * (x * z - w * y)},
+      {s4.y * 2.f * (x * y - w * z), s4.y * (1.f - 2.f * (x * x + z * z)), s4.y * 2.f * (y * z + w * x)},
+      {s4.z * 2.f * (x * z + w * y), s4.z * 2.f * (y * z - w * x), s4.z * (1.f - 2.f * (x * x + y * y))}};
+  const float rc2 = alive ? 2.f * logf(255.f * o) : 0.f;
+  float shc[48];
+  if (alive) load_sh(sc, i, shc);
+  for (int e = 0; e < neyes; ++e) {
+    const EyeCam &c = cams->eye[e];
+    float pc[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+      pc[r] = fmaf(c.R[r * 3 + 0], p4.x, fmaf(c.R[r * 3 + 1], p4.y, fmaf(c.R[r * 3 + 2], p4.z, c.t[r])));
+    const bool vis = alive && pc[2] > kZNear;
+    const float izc = 1.f / fmaxf(pc[2], kZNear);
+    const float rx = pc[0] * izc, ry = pc[1] * izc;
+    const float gx = c.fx * izc, gy = c.fy * izc;
+    float jx[3], jy[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float mx = fmaf(c.R[0], ax[k][0], fmaf(c.R[1], ax[k][1], c.R[2] * ax[k][2]));
+      const float my = fmaf(c.R[3], ax[k][0], fmaf(c.R[4], ax[k][1], c.R[5] * ax[k][2]));
+      const float mz = fmaf(c.R[6], ax[k][0], fmaf(c.R[7], ax[k][1], c.R[8] * ax[k][2]));
+      jx[k] = gx * fmaf(-rx, mz, mx);
+      jy[k] = gy * fmaf(-ry, mz, my);
+    }
+    const float txx = fmaf(jx[0], jx[0], fmaf(jx[1], jx[1], jx[2] * jx[2]));
+    const float tyy = fmaf(jy[0], jy[0], fmaf(jy[1], jy[1], jy[2] * jy[2]));
+    const float cxy = fmaf(jx[0], jy[0], fmaf(jx[1], jy[1], jx[2] * jy[2]));
+    const float cxx = txx + 0.3f, cyy = tyy + 0.3f;
+    const float k01 = fmaf(jx[0], jy[1], -jy[0] * jx[1]);
+    const float k02 = fmaf(jx[0], jy[2], -jy[0] * jx[2]);
+    const float k12 = fmaf(jx[1], jy[2], -jy[1] * jx[2]);
+    const float det = fmaf(k01, k01, fmaf(k02, k02, fmaf(k12, k12, fmaf(0.3f, txx + tyy, 0.09f))));
+    const float cxp = fmaf(c.fx, rx, c.cx), cyp = fmaf(c.fy, ry, c.cy);
+    const float ex = sqrtf(rc2 * cxx), ey = sqrtf(rc2 * cyy);
+    const float xmin = cxp - ex - kBoundPad, xmax = cxp + ex + kBoundPad;
+    const float ymin = cyp - ey - kBoundPad, ymax = cyp + ey + kBoundPad;
+    ushort4 rect;
+    uint32_t count = tile_rect(c, xmin, xmax, ymin, ymax, rect);
+    if (!vis) {
+      count = 0;
+      rect = make_ushort4(0, 0, 0, 0);
+    }
+    ws.cnt[e][i] = count;
+    ws.rect[e][i] = rect;
+    ws.zkey[e][i] = __float_as_uint(pc[2]);
+    if (ws.keep_intermediates) ws.bounds[e][i] = make_float4(xmin, xmax, ymin, ymax);
+    if (count == 0) continue;
+    const float l00 = sqrtf(cyy / det);
+    const float l01 = -cxy / sqrtf(det * cyy);
+    const float l11 = rsqrtf(cyy);
+    float rgb[3];
+    view_rgb(shc, sc.sh_degree, c, p4, rgb);
+    float4 *r = ws.rec[e] + 4 * (size_t)i;
+    r[0] = make_float4(cxp, cyp, rc2, pc[2]);
+    r[1] = make_float4(l00, 0.f, l01, l11);
+    r[2] = make_float4(1.f, 0.f, 0.f, 0.f);
+    r[3] = make_float4(0.f, rgb[0], rgb[1], rgb[2]);
+  }
+}
+
+cudaError_t launch_preprocess(const gs_scene &sc, Workspace &ws, int neyes, int W, int H, cudaStream_t s) {
   (void)W; (void)H;
+  ws.prim = sc.primitive;
   if (sc.n == 0) return cudaSuccess;
-  launch_k(preprocess_kernel, (sc.n + 255) / 256, 256, 0, s, sc, ws.cams, ws, neyes);
+  if (sc.primitive == 1)
+    launch_k(preprocess_ellipsoid_kernel, (sc.n + 255) / 256, 256, 0, s, sc, ws.cams, ws, neyes);
+  else
+    launch_k(preprocess_kernel, (sc.n + 255) / 256, 256, 0, s, sc, ws.cams, ws, neyes);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }

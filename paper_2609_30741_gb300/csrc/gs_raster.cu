@@ -27,6 +27,14 @@
 // does not depend on TS, PIX or BATCH: a tile's list holds every surfel whose
 // support reaches any pixel centre of the tile, in depth order, and the others
 // contribute nothing to its pixels.
+//
+// Ellipsoids (the 3DGS backbone) use the same loop: their record holds a
+// Cholesky factor L of the screen conic Sigma2D^-1 = L^T L in place of the
+// plane coefficients and a constant third coordinate, so the plane point is
+// (L d, 1) and u^2 + v^2 = d^T Sigma2D^-1 d, the EWA exponent; the frame's
+// low-pass factor is kNoLowpass (the EWA kernel already carries its 0.3 px^2
+// filter) and the depth terms are zero, so every contribution has the centre
+// depth.
 #include "gs_internal.cuh"
 #include "gs_launch.cuh"
 
@@ -103,6 +111,7 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
     const int rtx = (W + kTile - 1) / kTile;
 
     const float fx = (float)px;
+    const float lowpass = fr.lowpass;
     float fy[PIX];  // the thread's pixel rows
     float T[PIX], C0[PIX], C1[PIX], C2[PIX], D[PIX];
     unsigned live = 0;  // bit k: pixel k still blending
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
             const float u = qx * iq, v = qy * iq;
             const float rho3 = fmaf(u, u, v * v);
             const float h = fmaf(dyk, dyk, dx2);
-            const float rho2 = h + h;  // low-pass term 2 |x - c|^2, same exponent units
+            const float rho2 = h * lowpass;  // low-pass term 2 |x - c|^2, same exponent units
             const float rho = fminf(rho3, rho2);
             if (COUNT) ++npairs;
             if (rho <= a.z) {  // alpha >= 1/255
@@ -401,6 +410,7 @@ RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift,
   f.tshift = tshift;
   f.eye = eye;
   f.stats = stats ? 1 : 0;
+  f.lowpass = ws.prim ? kNoLowpass : 2.f;
   f.n_rec = (uint32_t)ws.max_surfels;
   return f;
 }

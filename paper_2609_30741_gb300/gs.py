@@ -33,7 +33,7 @@ class GsError(RuntimeError):
 
 class Scene(C.Structure):
     _fields_ = [("pos", C.c_void_p), ("quat", C.c_void_p), ("scale", C.c_void_p), ("opacity", C.c_void_p),
-                ("sh", C.c_void_p), ("n", C.c_int), ("sh_degree", C.c_int)]
+                ("sh", C.c_void_p), ("n", C.c_int), ("sh_degree", C.c_int), ("primitive", C.c_int)]
 
 
 class Pose(C.Structure):
@@ -232,7 +232,9 @@ def roi_params(margin=32, samples_per_edge=32, enable_center=1, depth_mode=0, d_
 
 
 class DeviceScene:
-    """Surfel attributes resident on the GPU (torch tensors) + the C struct."""
+    """Primitive attributes resident on the GPU (torch tensors) + the C struct.
+    `scene.primitive` (default 0) selects 2D surfels (scale [n, 2]) or 3D
+    ellipsoids (scale [n, 4]: s_x, s_y, s_z, pad)."""
 
     def __init__(self, scene, device="cuda"):
         def t(a):
@@ -240,8 +242,12 @@ class DeviceScene:
         self.pos, self.quat, self.scale = t(scene.pos), t(scene.quat), t(scene.scale)
         self.opacity, self.sh = t(scene.opacity), t(scene.sh)
         self.n, self.sh_degree = int(scene.n), int(scene.sh_degree)
+        self.primitive = int(getattr(scene, "primitive", 0))
+        want = 4 if self.primitive == 1 else 2
+        if self.n and tuple(self.scale.shape) != (self.n, want):
+            raise ValueError(f"scale must be [{self.n}, {want}] for primitive {self.primitive}")
         self.c = Scene(self.pos.data_ptr(), self.quat.data_ptr(), self.scale.data_ptr(),
-                       self.opacity.data_ptr(), self.sh.data_ptr(), self.n, self.sh_degree)
+                       self.opacity.data_ptr(), self.sh.data_ptr(), self.n, self.sh_degree, self.primitive)
 
     def nbytes(self):
         return sum(x.numel() * 4 for x in (self.pos, self.quat, self.scale, self.opacity, self.sh))
