@@ -848,10 +848,11 @@ def run_backbone3d(args, dev, flush):
         ms_s, ms_t = run(stereo), run(two)
         ps, ss, shares = [], [], {"hole": [], "gap": [], "centre_hole": [], "roi": []}
         ctx.set_counting(True)
-        pairs = []
+        pairs, widths = [], []
         for k in range(8):
             stereo(k)
             pairs.append(ctx.pair_counts()[0][0])
+            widths.append(out["edge_widths"].cpu().numpy().astype(np.float64))
             cls = out["cls_aff"].clone()
             two(k)
             ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
@@ -864,6 +865,7 @@ def run_backbone3d(args, dev, flush):
         res[name] = {"ms_per_stereo_frame": ms_s, "two_pass_ms": ms_t, "speedup_vs_two_pass": ms_t / ms_s,
                      "psnr_aff_vs_full_db": float(np.mean(ps)), "ssim_aff_vs_full": float(np.mean(ss)),
                      "pixel_share": {k: float(np.mean(v)) for k, v in shares.items()},
+                     "edge_widths_mean": np.mean(widths, 0).round(1).tolist(),
                      "dominant_pairs_per_pixel": float(np.mean(pairs)) / (cam.width * cam.height),
                      "raster": {"stereo": list(rc_s), "two_pass": list(rc_t)}}
         del ctx, ds, out, out2

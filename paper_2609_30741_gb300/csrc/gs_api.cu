@@ -85,6 +85,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     b.items = c.take<uint32_t>(tiles);
     b.rqueue = c.take<uint32_t>(2);
     b.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
+    b.roi_flag = c.take<uint8_t>(N);
     b.rs_table = c.take<uint32_t>(rs_words);
     b.rs_offs = c.take<uint32_t>(rs_words);
     b.rs_n = c.take<uint32_t>(1);

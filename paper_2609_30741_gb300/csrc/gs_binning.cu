@@ -248,23 +248,33 @@ struct CompactApply {
   }
 };
 
+// Per surfel id (coalesced): binned by this eye and, for an ROI binning, with a
+// masked tile in its rectangle. The filters below read one byte per surfel
+// instead of repeating the rectangle and summed-area lookups in both scan passes.
+__global__ void roi_flag_kernel(const uint32_t *__restrict__ cnt, const ushort4 *__restrict__ rect,
+                                const uint32_t *__restrict__ sat, int tiles_x, uint32_t n,
+                                uint8_t *__restrict__ flag) {
+  griddep_wait();
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  bool f = cnt[i] > 0u;
+  if (f && sat) {
+    const ushort4 rc = rect[i];
+    f = sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z);
+  }
+  flag[i] = f ? 1 : 0;
+}
+
 // The affiliated eye's surfels in the dominant eye's depth order: a stable filter
 // of that order. For a parallel rig both eyes' keys are identical, so the
 // filtered order is exactly the affiliated (depth, index) order.
 struct ReuseLoad {
   const uint32_t *uval, *n_union;
   uint32_t n_max;
-  const uint32_t *cnt;
-  const ushort4 *rect;
-  const uint32_t *sat;
-  int tiles_x;
+  const uint8_t *flag;  // roi_flag_kernel's flags
   __device__ uint32_t operator()(uint32_t i) const {
     if (i >= load_n(n_union, n_max)) return 0u;
-    const uint32_t id = uval[i];
-    if (cnt[id] == 0u) return 0u;
-    if (!sat) return 1u;
-    const ushort4 rc = rect[id];
-    return sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z) ? 1u : 0u;
+    return flag[uval[i]];
   }
 };
 
@@ -349,55 +359,76 @@ struct BandArgs {
   uint32_t *status;
 };
 
-// Band lists are built by small CTAs (kListWarps warps each) for parallelism;
-// CTA b of a chunk handles warps [b * kListWarps, (b + 1) * kListWarps).
-constexpr int kListWarps = 2;
-
-__global__ void __launch_bounds__(32 * kListWarps) band_list_kernel(BandArgs a) {
+// Band lists: one CTA of kBinWarps warps per sub-chunk (the surfels of one
+// bin_kernel warp). The sub-chunk's 32-surfel groups are split into kBinWarps
+// consecutive ranges, one per warp. Pass 0 counts each warp's (surfel, band)
+// entries per band; a CTA-wide scan turns the counts into the band lists'
+// places (bands in order, warps in order inside a band, so every list stays in
+// depth order) with one pool reservation per sub-chunk; pass 1 walks the same
+// groups again and writes the entries.
+__global__ void __launch_bounds__(kBinThreads) band_list_kernel(BandArgs a) {
   griddep_wait();
-  __shared__ uint32_t s_cnt[kListWarps][kMaxBands];
-  const int lane = threadIdx.x & 31;
-  const int w = (int)(blockIdx.x % (kBinWarps / kListWarps)) * kListWarps + (int)(threadIdx.x >> 5);
+  __shared__ uint32_t s_cnt[kBinWarps][kMaxBands];  // pass 0 counts, then each warp's write position
+  __shared__ uint32_t s_scan[32];
+  __shared__ uint32_t s_base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   const uint32_t nv = load_n(a.n_vis, a.n_max);
-  const uint32_t c = blockIdx.x / (kBinWarps / kListWarps);
-  const uint32_t chunk = kBinWarps * a.warp_surfels;
+  const uint32_t sub = blockIdx.x;                  // sub-chunk: chunk sub / kBinWarps, warp sub % kBinWarps
+  const uint32_t c = sub / kBinWarps;
+  if (c * kBinWarps * a.warp_surfels >= nv) return;  // bin_kernel skips the whole chunk
   const int nb = (a.tiles_y + kBandRows - 1) / kBandRows;
-  uint2 *my_lists = a.lists + ((size_t)c * nb) * kBinWarps + w;  // stride kBinWarps per band
-  uint32_t *cnt = s_cnt[threadIdx.x >> 5];
-  const uint32_t j0 = c * chunk + (uint32_t)w * a.warp_surfels;
-  const uint32_t j1 = min(j0 + a.warp_surfels, nv);
+  uint2 *my_lists = a.lists + ((size_t)c * nb) * kBinWarps + (sub % kBinWarps);  // stride kBinWarps per band
+  const uint32_t s0 = sub * a.warp_surfels;
+  const uint32_t s1 = min(s0 + a.warp_surfels, nv);
+  // this warp's groups of 32 surfels: [g0, g1) of the sub-chunk's ng groups
+  const uint32_t ng = s1 > s0 ? (s1 - s0 + 31) / 32 : 0u;
+  const uint32_t g0 = ng * (uint32_t)w / kBinWarps, g1 = ng * (uint32_t)(w + 1) / kBinWarps;
+  uint32_t *cnt = s_cnt[w];
   for (int b = lane; b < nb; b += 32) cnt[b] = 0u;
   __syncwarp();
-  // pass 0 counts the entries per band, pass 1 writes them
 #pragma unroll 1
   for (int pass = 0; pass < 2; ++pass) {
     if (pass == 1) {
-      uint32_t total = 0;
-      for (int b = 0; b < nb; ++b) total += cnt[b];
-      uint32_t base = 0;
-      if (lane == 0 && total > 0) base = atomicAdd(a.pool_n, total);
-      base = __shfl_sync(0xffffffffu, base, 0);
-      if (lane == 0 && total > 0 && (uint64_t)base + total > a.pool_cap) atomicOr(a.status, kStCapacity);
-      __syncwarp();
-      if (lane == 0) {  // lists and their running write positions
-        uint32_t at = base;
-        for (int b = 0; b < nb; ++b) {
-          const uint32_t n = cnt[b];
-          const uint32_t keep = at >= a.pool_cap ? 0u : min(n, a.pool_cap - at);
-          my_lists[(size_t)b * kBinWarps] = make_uint2(at, keep);
-          cnt[b] = at;
-          at += n;
+      // per band: the warps' exclusive offsets inside the band and the band's
+      // total; then the bands' places in the sub-chunk's pool range
+      __syncthreads();
+      uint32_t tot = 0;
+      static_assert(kMaxBands <= kBinThreads, "one thread per band");
+      if (threadIdx.x < nb) {
+        const int b = threadIdx.x;
+#pragma unroll
+        for (int ww = 0; ww < kBinWarps; ++ww) {
+          const uint32_t v = s_cnt[ww][b];
+          s_cnt[ww][b] = tot;
+          tot += v;
         }
       }
-      __syncwarp();
+      uint32_t band_off;
+      const uint32_t all = block_exclusive_scan<kBinThreads>(threadIdx.x < nb ? tot : 0u, &band_off, s_scan);
+      if (threadIdx.x == 0) {
+        uint32_t base = 0;
+        if (all > 0) base = atomicAdd(a.pool_n, all);
+        if (all > 0 && (uint64_t)base + all > a.pool_cap) atomicOr(a.status, kStCapacity);
+        s_base = base;
+      }
+      __syncthreads();
+      if (threadIdx.x < nb) {
+        const int b = threadIdx.x;
+        const uint32_t at = s_base + band_off;
+        const uint32_t keep = at >= a.pool_cap ? 0u : min(tot, a.pool_cap - at);
+        my_lists[(size_t)b * kBinWarps] = make_uint2(at, keep);
+#pragma unroll
+        for (int ww = 0; ww < kBinWarps; ++ww) s_cnt[ww][b] += at;
+      }
+      __syncthreads();
     }
-    for (uint32_t sub = j0; sub < j1; sub += 32) {  // warp-uniform
-      const uint32_t j = sub + (uint32_t)lane;
+    for (uint32_t g = g0; g < g1; ++g) {  // warp-uniform
+      const uint32_t j = s0 + g * 32u + (uint32_t)lane;
       int b0 = 1, b1 = 0, y0 = 0, y1 = -1, x0 = 0, x1 = -1;
       uint32_t id = 0, ro = 0;
-      if (j < j1) id = a.ids[j];
-      if (j < j1 && a.cnt[id] > 0u) {
+      if (j < s1) id = a.ids[j];
+      if (j < s1 && a.cnt[id] > 0u) {
         const ushort4 rc = a.rect[id];
         y0 = rc.y; y1 = rc.w; x0 = rc.x; x1 = rc.z;
         b0 = y0 / kBandRows;
@@ -415,15 +446,13 @@ __global__ void __launch_bounds__(32 * kListWarps) band_list_kernel(BandArgs a) 
         bool in = b >= b0 && b <= b1 && lo <= hi;
         if (in && a.sat) in = sat_any(a.sat, a.tiles_x, lo, hi, x0, x1);
         const uint32_t ball = __ballot_sync(0xffffffffu, in);
-        if (pass == 0) {
-          if (lane == 0) cnt[b] += (uint32_t)__popc(ball);
-        } else {
+        if (pass == 1) {
           const uint32_t at = cnt[b] + (uint32_t)__popc(ball & lt);
           if (in && at < a.pool_cap)
             a.pool[at] = BandEntry{id, ro + (uint32_t)(lo - y0), ((uint32_t)lo << 4) | (uint32_t)(hi - lo + 1)};
-          __syncwarp();
-          if (lane == 0) cnt[b] += (uint32_t)__popc(ball);
         }
+        __syncwarp();
+        if (lane == 0) cnt[b] += (uint32_t)__popc(ball);
         __syncwarp();
       }
     }
@@ -721,7 +750,12 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   // 1. compact the binned surfels: (depth bits, surfel id)
   const uint32_t *sat = tile_mask ? b.mask_sat : nullptr;
   if (order == kOrderReuse) {  // the dominant order, filtered: already depth-ordered
-    err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, ws.cnt[eye], ws.rect[eye], sat, tiles_x},
+    if (n > 0) {
+      launch_k(roi_flag_kernel, (n + 255) / 256, 256, 0, s, (const uint32_t *)ws.cnt[eye],
+               (const ushort4 *)ws.rect[eye], sat, tiles_x, (uint32_t)n, b.roi_flag);
+      GS_LAUNCHED(1);
+    }
+    err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, b.roi_flag},
                       ReuseApply{ws.uval, ws.zkey[eye], b.dkey[0], b.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
                                  &ctr->n_band[eye]},
                       (const uint32_t *)nullptr, (uint32_t)n, b.scan_sums, b.scan_ticket, nullptr, s);
@@ -772,7 +806,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   ba.pool_n = &ctr->n_band[eye];
   ba.lists = b.band_lists;
   ba.status = &ctr->status;
-  launch_k(band_list_kernel, ws.bin_nch * (kBinWarps / kListWarps), 32 * kListWarps, 0, s, ba);
+  launch_k(band_list_kernel, ws.bin_nch * kBinWarps, kBinThreads, 0, s, ba);
   GS_LAUNCHED(1);
   BinArgs a;
   a.n_vis = &ctr->n_vis[eye];

@@ -101,6 +101,7 @@ struct BinScratch {
   uint32_t *items;              // rasterizer tiles of the last masked binning
   uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
   uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
+  uint8_t *roi_flag;            // per surfel: binned and its rectangle holds a masked tile
   uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
   uint32_t *rs_n, *rs_sums;     // length of the table, scan block sums
   uint32_t *scan_sums;          // scan block sums

@@ -61,6 +61,53 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 // 1 / (2 ln 2): log2(o Ghat) = (r_c^2 - rho) / (2 ln 2) + log2(1/255)
 constexpr float kHalfLog2e = 0.72134752044448170f;
+// the row of a pixel that takes no more contributions
+#define kNaN __int_as_float(0x7fffffff)
+
+// The per-pixel part of one record's evaluation for a thread's PIX pixels of
+// one column: dy = y - c_y, the plane point (qx, qy, qz) = (px0, py0, pz0) +
+// dy (bz, bw, cz), u = qx / qz, v = qy / qz, rho3 = u^2 + v^2 and the low-pass
+// term rho2 = lowpass (dx^2 + dy^2). Pixel pairs go through the packed FP32x2
+// pipe (add/mul/fma .f32x2: one issue slot for two lanes' worth of work);
+// every component is rounded exactly as the scalar operation, so the result
+// does not depend on PIX.
+template <int PIX>
+__device__ __forceinline__ void eval_pixels(const float (&fy)[PIX], float ay, float bz, float bw, float cz,
+                                            float px0, float py0, float pz0, float dx2, float lowpass,
+                                            float (&uq)[PIX], float (&vq)[PIX], float (&r3q)[PIX],
+                                            float (&r2q)[PIX]) {
+  if constexpr (PIX % 2 == 0) {
+    const float2 nay = make_float2(-ay, -ay), bz2 = make_float2(bz, bz), bw2 = make_float2(bw, bw);
+    const float2 cz2 = make_float2(cz, cz), px2 = make_float2(px0, px0), py2 = make_float2(py0, py0);
+    const float2 pz2 = make_float2(pz0, pz0), dx22 = make_float2(dx2, dx2), lp2 = make_float2(lowpass, lowpass);
+#pragma unroll
+    for (int p = 0; p < PIX / 2; ++p) {
+      const float2 dy = __fadd2_rn(make_float2(fy[2 * p], fy[2 * p + 1]), nay);
+      const float2 qx = __ffma2_rn(dy, bz2, px2);
+      const float2 qy = __ffma2_rn(dy, bw2, py2);
+      const float2 qz = __ffma2_rn(dy, cz2, pz2);
+      const float2 iq = make_float2(rcp_approx(qz.x), rcp_approx(qz.y));
+      const float2 u = __fmul2_rn(qx, iq), v = __fmul2_rn(qy, iq);
+      const float2 r3 = __ffma2_rn(u, u, __fmul2_rn(v, v));
+      const float2 r2 = __fmul2_rn(__ffma2_rn(dy, dy, dx22), lp2);
+      uq[2 * p] = u.x; uq[2 * p + 1] = u.y;
+      vq[2 * p] = v.x; vq[2 * p + 1] = v.y;
+      r3q[2 * p] = r3.x; r3q[2 * p + 1] = r3.y;
+      r2q[2 * p] = r2.x; r2q[2 * p + 1] = r2.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < PIX; ++q) {
+      const float dy = fy[q] - ay;
+      const float qx = fmaf(dy, bz, px0), qy = fmaf(dy, bw, py0), qz = fmaf(dy, cz, pz0);
+      const float iq = rcp_approx(qz);
+      uq[q] = qx * iq;
+      vq[q] = qy * iq;
+      r3q[q] = fmaf(uq[q], uq[q], vq[q] * vq[q]);
+      r2q[q] = fmaf(dy, dy, dx2) * lowpass;
+    }
+  }
+}
 
 template <int TS, int PIX, int BATCH, bool COUNT>
 __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_constant__ RasterTable tab,
@@ -112,16 +159,18 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
 
     const float fx = (float)px;
     const float lowpass = fr.lowpass;
-    float fy[PIX];  // the thread's pixel rows
+    // the thread's pixel rows; a pixel that is not blending (outside the image
+    // or the ROI, or finished) has a NaN row, so every test on it fails
+    float fy[PIX];
     float T[PIX], C0[PIX], C1[PIX], C2[PIX], D[PIX];
     unsigned live = 0;  // bit k: pixel k still blending
 #pragma unroll
     for (int q = 0; q < PIX; ++q) {
       T[q] = 1.f; C0[q] = C1[q] = C2[q] = D[q] = 0.f;
       const int y = py + RS * q;
-      fy[q] = (float)y;
       bool on = px < W && y < H;
       if (on && fr.roi) on = fr.roi[(y / kTile) * rtx + px / kTile] != 0;
+      fy[q] = on ? (float)y : kNaN;
       if (on) live |= 1u << q;
     }
     const unsigned wmask = live;  // pixels this thread writes
@@ -167,41 +216,30 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
         const float dx = fx - a.x;
         const float px0 = dx * b.x, py0 = dx * b.y, pz0 = fmaf(dx, c.y, c.x);
         const float dx2 = dx * dx;
-        float dyv[PIX], qxv[PIX], qyv[PIX], qzv[PIX];  // independent per pixel: issued back to back
+        // per pixel: u, v, rho3 and the low-pass term rho2 = lowpass |x - c|^2
+        float uq[PIX], vq[PIX], r3q[PIX], r2q[PIX];
+        eval_pixels<PIX>(fy, a.y, b.z, b.w, c.z, px0, py0, pz0, dx2, lowpass, uq, vq, r3q, r2q);
 #pragma unroll
         for (int q = 0; q < PIX; ++q) {
-          dyv[q] = fy[q] - a.y;
-          qxv[q] = fmaf(dyv[q], b.z, px0);
-          qyv[q] = fmaf(dyv[q], b.w, py0);
-          qzv[q] = fmaf(dyv[q], c.z, pz0);
-        }
-#pragma unroll
-        for (int q = 0; q < PIX; ++q) {
-          if (live & (1u << q)) {
-            const float dyk = dyv[q], qx = qxv[q], qy = qyv[q];
-            const float iq = rcp_approx(qzv[q]);
-            const float u = qx * iq, v = qy * iq;
-            const float rho3 = fmaf(u, u, v * v);
-            const float h = fmaf(dyk, dyk, dx2);
-            const float rho2 = h * lowpass;  // low-pass term 2 |x - c|^2, same exponent units
-            const float rho = fminf(rho3, rho2);
-            if (COUNT) ++npairs;
-            if (rho <= a.z) {  // alpha >= 1/255
-              const float alpha = fminf(kAlphaMax, ex2_approx(fmaf(a.z - rho, kHalfLog2e, kLog2AlphaMin)));
-              const float Tn = fmaf(-T[q], alpha, T[q]);
-              if (Tn < kTMin) {
-                live &= ~(1u << q);
-              } else {
-                const float4 d = s3[buf][j];
-                const float z = rho3 <= rho2 ? fmaf(c.w, u, fmaf(d.x, v, a.w)) : a.w;
-                const float w = alpha * T[q];
-                if (COUNT) ++ncontrib;
-                C0[q] = fmaf(w, d.y, C0[q]);
-                C1[q] = fmaf(w, d.z, C1[q]);
-                C2[q] = fmaf(w, d.w, C2[q]);
-                D[q] = fmaf(w, z, D[q]);
-                T[q] = Tn;
-              }
+          const float rho3 = r3q[q], rho2 = r2q[q];
+          const float rho = fminf(rho3, rho2);
+          if (COUNT && (live & (1u << q))) ++npairs;
+          if (rho <= a.z) {  // alpha >= 1/255 (false for a NaN row)
+            const float alpha = fminf(kAlphaMax, ex2_approx(fmaf(a.z - rho, kHalfLog2e, kLog2AlphaMin)));
+            const float Tn = fmaf(-T[q], alpha, T[q]);
+            if (Tn < kTMin) {
+              live &= ~(1u << q);
+              fy[q] = kNaN;
+            } else {
+              const float4 d = s3[buf][j];
+              const float z = rho3 <= rho2 ? fmaf(c.w, uq[q], fmaf(d.x, vq[q], a.w)) : a.w;
+              const float w = alpha * T[q];
+              if (COUNT) ++ncontrib;
+              C0[q] = fmaf(w, d.y, C0[q]);
+              C1[q] = fmaf(w, d.z, C1[q]);
+              C2[q] = fmaf(w, d.w, C2[q]);
+              D[q] = fmaf(w, z, D[q]);
+              T[q] = Tn;
             }
           }
         }

@@ -16,6 +16,14 @@ pytestmark = pytest.mark.gpu
 KEYS = ("rgb_dom", "depth_dom", "trans_dom", "rgb_aff", "cls_aff", "roi_rects", "roi_count", "edge_widths")
 
 
+def _same(kk, got, ref):
+    """Outputs agree; of roi_rects only the roi_count entries written are defined."""
+    if kk == "roi_rects":
+        n = int(ref["roi_count"].item())
+        return int(got["roi_count"].item()) == n and torch.equal(got[kk][:n], ref[kk][:n])
+    return torch.equal(got[kk], ref[kk])
+
+
 @pytest.fixture(scope="module")
 def gs():
     if not torch.cuda.is_available():
@@ -75,7 +83,7 @@ def test_reuse_equals_fixed_range_of_previous_frame(gs, kind, cfg, repair):
                                                     gate_tau=0.4))
         b.check_ok()
         for kk in KEYS:
-            assert torch.equal(got[kk], ref[kk]), (k, kk)
+            assert _same(kk, got, ref), (k, kk)
         # the range this frame measured, for the next one
         prev, _ = _measured_range(gs, b, ds, (d, f), cam, gs.roi_params(repair_mode=repair, gate_tau=0.4))
 
@@ -95,5 +103,5 @@ def test_reuse_in_batches(gs):
         for j in range(2):
             r = refs[j].render_stereo(ds, *pairs[(k + j) % len(pairs)], cam, gap_thresh=2, roi=roi)
             for kk in KEYS:
-                assert torch.equal(frames[j][4][kk], r[kk]), (k, j, kk)
+                assert _same(kk, frames[j][4], r), (k, j, kk)
     bt.close()
