@@ -358,7 +358,7 @@ gs_status gs_ssim(gs_context *ctx, const float *img, const float *ref, int width
  *         the context's min_tile. The ROI generator keeps the 16-pixel grid:
  *         with 32-pixel tiles only the pixels of ROI 16-pixel tiles are written.
  *   pix   pixels per thread, i.e. the block shape (tile^2 / pix threads): 1 or 2
- *         at tile 8, 2 or 4 at tile 16, 4 or 8 at tile 32.
+ *         at tile 8, 2 or 4 at tile 16, 2, 4 or 8 at tile 32.
  *   batch 32, 64, 128 or 256 surfel records per shared-memory stage.
  * Every configuration produces the same images bit for bit; they differ in
  * speed only. The default is {16, 4, 128} ({32, 8, 128} when min_tile = 32).

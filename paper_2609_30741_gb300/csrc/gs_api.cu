@@ -51,7 +51,6 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   const size_t table_max = tiles * bin_chunks(lim.max_surfels);
   size_t scan_n = N > P ? N : P;
   if (table_max > scan_n) scan_n = table_max;
-  const size_t scan_blocks = (scan_n + kScanTile - 1) / kScanTile + 2;
   ws.cams = c.take<CamBlock>(1);
   ws.ctr = c.take<Counters>(1);
   for (int e = 0; e < 2; ++e) {
@@ -89,9 +88,11 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     b.rs_table = c.take<uint32_t>(rs_words);
     b.rs_offs = c.take<uint32_t>(rs_words);
     b.rs_n = c.take<uint32_t>(1);
-    b.rs_sums = c.take<uint32_t>(rs_words / kScanTile + 2);
-    b.scan_sums = c.take<uint32_t>(scan_blocks);
-    b.scan_ticket = c.take<uint32_t>(1);
+    b.rs_tiles = c.take<unsigned long long>(scan_tiles(rs_words));
+    b.scan_tiles = c.take<unsigned long long>(scan_tiles(scan_n));
+    ws.n_rs_tiles = scan_tiles(rs_words);
+    ws.n_scan_tiles = scan_tiles(scan_n);
+    b.scan_ticket = c.take<uint32_t>(4);
   }
   ws.tile_mask = c.take<uint8_t>(tiles);
   ws.strip_mask = c.take<uint8_t>(tiles);
@@ -354,7 +355,11 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
   if (e == cudaSuccess) e = prepare_repair();
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaMemsetAsync(ctx->ws.bin[k].rqueue, 0, 2 * sizeof(uint32_t), ctx->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.bin[k].scan_ticket, 0, sizeof(uint32_t), ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.bin[k].scan_ticket, 0, 4 * sizeof(uint32_t), ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(ctx->ws.bin[k].scan_tiles, 0, sizeof(unsigned long long) * ctx->ws.n_scan_tiles, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(ctx->ws.bin[k].rs_tiles, 0, sizeof(unsigned long long) * ctx->ws.n_rs_tiles, ctx->stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
   if (e != cudaSuccess) {

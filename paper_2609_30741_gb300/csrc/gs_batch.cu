@@ -602,7 +602,7 @@ template <class Apply, class Call, class Check>
 static gs_status tune_loop(cudaStream_t s, int reps, int min_tshift, Apply &&apply, Call &&call, Check &&check,
                            gs_tune_result *results, int max_results, int *n_results, gs_raster_config *best,
                            float *best_ms) {
-  static const int shapes[6][2] = {{8, 1}, {8, 2}, {16, 2}, {16, 4}, {32, 4}, {32, 8}};
+  static const int shapes[7][2] = {{8, 1}, {8, 2}, {16, 2}, {16, 4}, {32, 2}, {32, 4}, {32, 8}};
   static const int batches[4] = {32, 64, 128, 256};
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return BFAIL(cudaGetLastError());
@@ -611,7 +611,7 @@ static gs_status tune_loop(cudaStream_t s, int reps, int min_tshift, Apply &&app
   gs_raster_config win{0, 0, 0};
   float win_ms = INFINITY;
   gs_status err = GS_OK;
-  for (int si = 0; si < 6 && err == GS_OK; ++si) {
+  for (int si = 0; si < 7 && err == GS_OK; ++si) {
     for (int bi = 0; bi < 4 && err == GS_OK; ++bi) {
       const gs_raster_config rc{shapes[si][0], shapes[si][1], batches[bi]};
       if (raster_tshift(RasterConfig{rc.tile, rc.pix, rc.batch}) < min_tshift) continue;

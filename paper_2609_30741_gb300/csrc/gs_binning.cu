@@ -742,7 +742,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   Counters *ctr = ws.ctr;
   const int ntiles = tiles_x * tiles_y;
   const uint32_t cap = (uint32_t)ws.max_instances;
-  const RadixScratch rs{b.rs_table, b.rs_offs, b.rs_n, b.rs_sums, b.scan_ticket};
+  const RadixScratch rs{b.rs_table, b.rs_offs, b.rs_n, b.rs_tiles, b.scan_ticket, &ctr->status};
   if (tile_mask) {
     launch_k(mask_sat_kernel, 1, 1024, 0, s, tile_mask, tiles_x, tiles_y, b.mask_sat);
     GS_LAUNCHED(1);
@@ -758,13 +758,13 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
     err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, b.roi_flag},
                       ReuseApply{ws.uval, ws.zkey[eye], b.dkey[0], b.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
                                  &ctr->n_band[eye]},
-                      (const uint32_t *)nullptr, (uint32_t)n, b.scan_sums, b.scan_ticket, nullptr, s);
+                      (const uint32_t *)nullptr, (uint32_t)n, b.scan_tiles, b.scan_ticket, &ctr->status, s);
   } else {
     err = scan_launch(VisibleLoad{ws.cnt[eye], order == kOrderUnion ? ws.cnt[1 - eye] : nullptr, ws.rect[eye], sat,
                                   tiles_x},
                       CompactApply{ws.zkey[eye], b.dkey[0], b.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
                                    &ctr->n_band[eye]},
-                      (const uint32_t *)nullptr, (uint32_t)n, b.scan_sums, b.scan_ticket, nullptr, s);
+                      (const uint32_t *)nullptr, (uint32_t)n, b.scan_tiles, b.scan_ticket, &ctr->status, s);
   }
   if (err != cudaSuccess) return err;
   // 2. tile ranges of every rectangle row of those surfels (n_rows and n_band
@@ -837,8 +837,8 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
                                  kBinWarps * ws.bin_warp_surfels},
                     BinOffsetApply{b.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status,
                                    tile_mask ? &ctr->n_items[eye] : nullptr},
-                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, b.scan_sums, b.scan_ticket,
-                    nullptr, s);
+                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, b.scan_tiles, b.scan_ticket,
+                    &ctr->status, s);
   if (err != cudaSuccess) return err;
   launch_k(bin_ranges_kernel, (ntiles + 255) / 256, 256, 0, s, b.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
                                                          b.ranges, tile_mask, b.items, &ctr->n_items[eye]);

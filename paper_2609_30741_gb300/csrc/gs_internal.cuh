@@ -103,9 +103,10 @@ struct BinScratch {
   uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
   uint8_t *roi_flag;            // per surfel: binned and its rectangle holds a masked tile
   uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
-  uint32_t *rs_n, *rs_sums;     // length of the table, scan block sums
-  uint32_t *scan_sums;          // scan block sums
-  uint32_t *scan_ticket;        // scan completion counter, 0 between scans
+  uint32_t *rs_n;               // length of the radix table
+  unsigned long long *rs_tiles; // look-back tile words of the radix table scans
+  unsigned long long *scan_tiles;  // look-back tile words of the other scans
+  uint32_t *scan_ticket;        // scan control words {tile counter, exit counter, epoch}
 };
 
 // Views of the caller-owned workspace.
@@ -156,6 +157,7 @@ struct Workspace {
   int keep_intermediates;
   uint32_t bin_warp_surfels, bin_nch;  // binning chunk geometry (see launch_binning)
   int prim;                     // primitive of the prepared records (gs_scene.primitive), set by launch_preprocess
+  size_t n_scan_tiles, n_rs_tiles;  // look-back words of scan_tiles and rs_tiles
 };
 
 constexpr int kScanThreads = 512;

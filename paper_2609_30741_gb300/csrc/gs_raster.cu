@@ -335,7 +335,7 @@ struct Variant {
   int occupancy;  // resident CTAs per SM, 0 until queried
 };
 
-constexpr int kShapes = 6;  // (tile, pix): (8,1) (8,2) (16,2) (16,4) (32,4) (32,8)
+constexpr int kShapes = 7;  // (tile, pix): (8,1) (8,2) (16,2) (16,4) (32,4) (32,8) (32,2)
 constexpr int kBatches = 4; // 32 64 128 256
 
 template <int TS, int PIX, bool C>
@@ -355,12 +355,14 @@ struct VariantTable {
     fill_batches<16, 4, false>(v[0][3]);
     fill_batches<32, 4, false>(v[0][4]);
     fill_batches<32, 8, false>(v[0][5]);
+    fill_batches<32, 2, false>(v[0][6]);
     fill_batches<8, 1, true>(v[1][0]);
     fill_batches<8, 2, true>(v[1][1]);
     fill_batches<16, 2, true>(v[1][2]);
     fill_batches<16, 4, true>(v[1][3]);
     fill_batches<32, 4, true>(v[1][4]);
     fill_batches<32, 8, true>(v[1][5]);
+    fill_batches<32, 2, true>(v[1][6]);
   }
 };
 
@@ -370,7 +372,7 @@ int shape_index(const RasterConfig &c) {
   switch (c.tile) {
     case 8: return c.pix == 1 ? 0 : c.pix == 2 ? 1 : -1;
     case 16: return c.pix == 2 ? 2 : c.pix == 4 ? 3 : -1;
-    case 32: return c.pix == 4 ? 4 : c.pix == 8 ? 5 : -1;
+    case 32: return c.pix == 4 ? 4 : c.pix == 8 ? 5 : c.pix == 2 ? 6 : -1;
   }
   return -1;
 }

@@ -820,7 +820,7 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
   launch_k(repair_tile_flags_kernel, dim3(tx, ty), 256, 0, s, ws.cls, ws.tile_mask, W, H, ws.rp_flags);
   GS_LAUNCHED(1);
   if ((e = scan_launch(TileFlagLoad{ws.rp_flags}, TileListApply{ws.rp_list, ws.rp_nlist, tx},
-                       (const uint32_t *)nullptr, (uint32_t)nt, ws.bin[0].scan_sums, ws.bin[0].scan_ticket, nullptr, s)) !=
+                       (const uint32_t *)nullptr, (uint32_t)nt, ws.bin[0].scan_tiles, ws.bin[0].scan_ticket, &ws.ctr->status, s)) !=
       cudaSuccess)
     return e;
   if ((e = repair_forward(ws, ws.rp_feat, W, H, ws.rp_list, ws.rp_nlist, (uint32_t)nt, ws.rp_fill, ws.rp_gate,

@@ -498,7 +498,7 @@ cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cu
   launch_k(cc_flatten_kernel, grid_for(npix), 256, 0, s, ws.labels, npix);
   const uint32_t cap = (uint32_t)ws.max_rects;
   cudaError_t err = scan_launch(RootLoad{ws.labels}, RootApply{ws.slots, ws.rects, cap, ws.ctr, W, H},
-                                (const uint32_t *)nullptr, (uint32_t)npix, ws.bin[0].scan_sums, ws.bin[0].scan_ticket, nullptr, s);
+                                (const uint32_t *)nullptr, (uint32_t)npix, ws.bin[0].scan_tiles, ws.bin[0].scan_ticket, &ws.ctr->status, s);
   if (err != cudaSuccess) return err;
   launch_k(cc_bbox_kernel, grid_for(npix), 256, 0, s, ws.labels, ws.slots, ws.rects, cap, W, npix);
   launch_k(cc_finalize_kernel, grid_for(ws.max_rects), 256, 0, s, ws.rects, ws.ctr, cap, W, H, margin, tiles_x, tiles_y,

@@ -43,111 +43,144 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *e
   return total;
 }
 
-// Pass 1: per-tile sums. The last block to finish (counted on *ticket, which
-// it resets to 0) then scans the tile sums in place, so no block ever waits on
-// another.
-template <class Load>
-__global__ void __launch_bounds__(kScanThreads) scan_reduce_kernel(Load ld, const uint32_t *n_ptr,
-                                                                   uint32_t n_max, uint32_t *sums,
-                                                                   uint32_t *ticket, uint32_t *total_out) {
-  griddep_wait();
-  __shared__ uint32_t smem[32];
-  __shared__ uint32_t s_last;
-  const uint32_t n = load_n(n_ptr, n_max);
-  const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
-  uint32_t acc = 0;
-  if (base < n) {
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-      const uint32_t i = base + k * kScanThreads + threadIdx.x;  // coalesced
-      if (i < n) acc += ld(i);
-    }
-  }
-  uint32_t ex;
-  const uint32_t tot = block_exclusive_scan<kScanThreads>(acc, &ex, smem);
-  if (threadIdx.x == 0) {
-    sums[blockIdx.x] = tot;
-    __threadfence();
-    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  const int nb = (int)gridDim.x;
-  const int per = (nb + kScanThreads - 1) / kScanThreads;
-  const int b0 = threadIdx.x * per;
-  uint32_t a2 = 0;
-  for (int k = 0; k < per; ++k)
-    if (b0 + k < nb) a2 += __ldcg(sums + b0 + k);
-  uint32_t ex2;
-  const uint32_t all = block_exclusive_scan<kScanThreads>(a2, &ex2, smem);
-  for (int k = 0; k < per; ++k) {
-    if (b0 + k < nb) {
-      const uint32_t v = __ldcg(sums + b0 + k);
-      sums[b0 + k] = ex2;
-      ex2 += v;
-    }
-  }
-  if (threadIdx.x == 0) {
-    if (total_out) *total_out = all;
-    *ticket = 0u;
-  }
+// Single-pass exclusive scan with decoupled look-back. A CTA takes its tile of
+// kScanTile elements from a device counter (so every tile it waits on belongs
+// to a CTA that is already running), scans the tile in shared memory and
+// publishes the tile total in a 64-bit status word: (epoch << 34) | (flag << 32)
+// | value, flag 1 = the tile's own total, 2 = inclusive prefix through the tile.
+// Warp 0 then walks back over the predecessors 32 at a time, adding totals up to
+// the nearest inclusive prefix, and publishes its own. A word only counts when
+// its epoch is this launch's; the last CTA out advances the epoch and clears the
+// counters, so no status word needs clearing between launches (graph replays
+// included). Every wait is bounded: after kLbSpinLimit reads a tile that has
+// not published is taken as 0 and kStTimeout is raised in the status word.
+//
+// Scratch (per workspace, used by one scan at a time): `tiles`, one 64-bit
+// word per tile, zero at context creation; `ctl` = {tile counter, exit
+// counter, epoch}, zero at context creation.
+constexpr uint32_t kLbAgg = 1u, kLbIncl = 2u;
+constexpr uint32_t kLbSpinLimit = 1u << 20;
+
+__device__ __forceinline__ unsigned long long lb_load(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void lb_store(unsigned long long *p, uint32_t epoch, uint32_t flag, uint32_t v) {
+  const unsigned long long w = ((unsigned long long)((epoch << 2) | flag) << 32) | v;
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
 }
 
-// Pass 2: per-element exclusive prefix; ap(i, prefix, value) for every i < n and
-// ap.end(n, total) once.
+// Warp-collective: the sum of the totals of tiles [0, t) (t > 0).
+__device__ __forceinline__ uint32_t lb_prefix(const unsigned long long *tiles, uint32_t t, uint32_t epoch,
+                                              uint32_t *status) {
+  const int lane = threadIdx.x & 31;
+  uint32_t prefix = 0;
+  for (int j = (int)t - 1; j >= 0; j -= 32) {  // warp-uniform
+    const int idx = j - lane;  // lane 0: the nearest predecessor
+    uint32_t flag = kLbIncl, v = 0;  // before tile 0: an inclusive zero
+    if (idx >= 0) {
+      for (uint32_t spin = 0;; ++spin) {
+        const unsigned long long w = lb_load(tiles + idx);
+        const uint32_t hi = (uint32_t)(w >> 32);
+        if ((hi >> 2) == epoch && (hi & 3u) != 0u) {
+          flag = hi & 3u;
+          v = (uint32_t)w;
+          break;
+        }
+        if (spin >= kLbSpinLimit) {  // never expected: give up on this tile, flag it
+          atomicOr(status, kStTimeout);
+          break;
+        }
+      }
+    }
+    const uint32_t incl = __ballot_sync(0xffffffffu, flag == kLbIncl);
+    const int stop = incl ? __ffs(incl) - 1 : 31;
+    uint32_t x = lane <= stop ? v : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    prefix += x;
+    if (incl) break;
+  }
+  return prefix;
+}
+
+// ap(i, prefix, value) for every i < n, and ap.end(n, total) once.
 template <class Load, class Apply>
-__global__ void __launch_bounds__(kScanThreads) scan_apply_kernel(Load ld, Apply ap, const uint32_t *n_ptr,
-                                                                  uint32_t n_max, const uint32_t *sums) {
+__global__ void __launch_bounds__(kScanThreads) scan_kernel(Load ld, Apply ap, const uint32_t *n_ptr, uint32_t n_max,
+                                                            unsigned long long *tiles, uint32_t *ctl,
+                                                            uint32_t *status) {
   griddep_wait();
   __shared__ uint32_t smem[32];
   __shared__ uint32_t vals[kScanTile];
+  __shared__ uint32_t s_tile, s_prefix;
   const uint32_t n = load_n(n_ptr, n_max);
-  const uint32_t base = blockIdx.x * (uint32_t)kScanTile;
-  if (base >= n) {
-    if (blockIdx.x == 0) ap.end(n, 0u);
-    return;
-  }
-#pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const uint32_t i = base + k * kScanThreads + threadIdx.x;
-    vals[k * kScanThreads + threadIdx.x] = i < n ? ld(i) : 0u;
-  }
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl[0], 1u);
   __syncthreads();
-  // each thread owns kScanItems consecutive elements
-  uint32_t loc[kScanItems], acc = 0;
+  const uint32_t t = s_tile;
+  const uint32_t epoch = (*(volatile uint32_t *)(ctl + 2)) & 0x3fffffffu;
+  const uint32_t base = t * (uint32_t)kScanTile;
+  if (base < n) {
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    loc[k] = vals[threadIdx.x * kScanItems + k];
-    acc += loc[k];
-  }
-  uint32_t ex;
-  const uint32_t tot = block_exclusive_scan<kScanThreads>(acc, &ex, smem);
-  if (sums) ex += sums[blockIdx.x];
+    for (int k = 0; k < kScanItems; ++k) {  // coalesced loads
+      const uint32_t i = base + k * kScanThreads + threadIdx.x;
+      vals[k * kScanThreads + threadIdx.x] = i < n ? ld(i) : 0u;
+    }
+    __syncthreads();
+    // each thread owns kScanItems consecutive elements
+    uint32_t loc[kScanItems], acc = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    const uint32_t i = base + threadIdx.x * kScanItems + k;
-    if (i < n) ap(i, ex, loc[k]);
-    ex += loc[k];
+    for (int k = 0; k < kScanItems; ++k) {
+      loc[k] = vals[threadIdx.x * kScanItems + k];
+      acc += loc[k];
+    }
+    uint32_t ex;
+    const uint32_t tot = block_exclusive_scan<kScanThreads>(acc, &ex, smem);
+    if (threadIdx.x < 32) {
+      uint32_t prefix = 0;
+      if (t == 0) {
+        if (threadIdx.x == 0) lb_store(tiles, epoch, kLbIncl, tot);
+      } else {
+        if (threadIdx.x == 0) lb_store(tiles + t, epoch, kLbAgg, tot);
+        prefix = lb_prefix(tiles, t, epoch, status);
+        if (threadIdx.x == 0) lb_store(tiles + t, epoch, kLbIncl, prefix + tot);
+      }
+      if (threadIdx.x == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    ex += s_prefix;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const uint32_t i = base + threadIdx.x * kScanItems + k;
+      if (i < n) ap(i, ex, loc[k]);
+      ex += loc[k];
+    }
+    if (base + kScanTile >= n && threadIdx.x == 0) ap.end(n, s_prefix + tot);
+  } else if (t == 0 && threadIdx.x == 0) {
+    ap.end(n, 0u);
   }
-  if (base + kScanTile >= n && threadIdx.x == 0) ap.end(n, (sums ? sums[blockIdx.x] : 0u) + tot);
+  // the last CTA out clears the counters and advances the epoch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ctl[1], 1u) == gridDim.x - 1) {
+      ctl[0] = 0u;
+      ctl[1] = 0u;
+      ctl[2] = (epoch + 1u) & 0x3fffffffu;
+      __threadfence();
+    }
+  }
 }
 
-// block_sums: one word per tile of kScanTile elements (+1); ticket: one word that
-// is 0 between scans (the scans of one workspace run one after another).
+// Scratch words: scan_tiles(n_max) 64-bit tile words, and 3 control words.
+inline size_t scan_tiles(size_t n_max) { return (n_max + kScanTile - 1) / kScanTile + 1; }
+
 template <class Load, class Apply>
-cudaError_t scan_launch(Load ld, Apply ap, const uint32_t *n_ptr, uint32_t n_max, uint32_t *block_sums,
-                        uint32_t *ticket, uint32_t *total_out, cudaStream_t s) {
+cudaError_t scan_launch(Load ld, Apply ap, const uint32_t *n_ptr, uint32_t n_max, unsigned long long *tiles,
+                        uint32_t *ctl, uint32_t *status, cudaStream_t s) {
   const int nblocks = (int)((n_max + kScanTile - 1) / kScanTile);
-  if (nblocks <= 1) {
-    // one tile (or an empty result): its prefix starts at 0
-    launch_k(scan_apply_kernel<Load, Apply>, 1, kScanThreads, 0, s, ld, ap, n_ptr, n_max, (const uint32_t *)nullptr);
-    GS_LAUNCHED(1);
-    return cudaGetLastError();
-  }
-  launch_k(scan_reduce_kernel<Load>, nblocks, kScanThreads, 0, s, ld, n_ptr, n_max, block_sums, ticket, total_out);
-  launch_k(scan_apply_kernel<Load, Apply>, nblocks, kScanThreads, 0, s, ld, ap, n_ptr, n_max, block_sums);
-  GS_LAUNCHED(2);
+  launch_k(scan_kernel<Load, Apply>, nblocks < 1 ? 1 : nblocks, kScanThreads, 0, s, ld, ap, n_ptr, n_max, tiles, ctl,
+           status);
+  GS_LAUNCHED(1);
   return cudaGetLastError();
 }
 

@@ -175,11 +175,12 @@ static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const 
 }
 
 struct RadixScratch {
-  uint32_t *table;   // [256][tiles]
-  uint32_t *offs;    // [256][tiles]
-  uint32_t *n_table; // one word
-  uint32_t *sums;    // scan block sums
-  uint32_t *ticket;  // scan completion counter (0 between scans)
+  uint32_t *table;            // [256][tiles]
+  uint32_t *offs;             // [256][tiles]
+  uint32_t *n_table;          // one word
+  unsigned long long *tiles;  // look-back words of the table scan
+  uint32_t *ticket;           // scan control words (the first is 0 between scans)
+  uint32_t *status;           // device status word
 };
 
 inline size_t radix_table_words(size_t n_max) { return 256 * ((n_max + kRsTile - 1) / kRsTile + 1); }
@@ -204,8 +205,8 @@ inline cudaError_t radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], 
                                                fused ? sc.offs : nullptr, sc.ticket);
     GS_LAUNCHED(1);
     if (!fused) {
-      cudaError_t e = scan_launch(TableLoad{sc.table}, TableApply{sc.offs}, sc.n_table, table_max, sc.sums,
-                                  sc.ticket, nullptr, s);
+      cudaError_t e = scan_launch(TableLoad{sc.table}, TableApply{sc.offs}, sc.n_table, table_max, sc.tiles,
+                                  sc.ticket, sc.status, s);
       if (e != cudaSuccess) return e;
     }
     launch_k(rs_scatter_kernel, grid, kRsThreads, 0, s, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_ptr, n_max,

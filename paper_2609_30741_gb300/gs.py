@@ -88,7 +88,7 @@ class TuneResult(C.Structure):
 
 
 # every valid (tile, pix, batch): the autotuner's search space
-RASTER_CONFIGS = [(t, p, b) for t, ps in ((8, (1, 2)), (16, (2, 4)), (32, (4, 8))) for p in ps
+RASTER_CONFIGS = [(t, p, b) for t, ps in ((8, (1, 2)), (16, (2, 4)), (32, (2, 4, 8))) for p in ps
                   for b in (32, 64, 128, 256)]
 
 

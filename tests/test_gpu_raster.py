@@ -91,7 +91,7 @@ def test_tile_edge_orders_the_evaluated_pairs(gs):
 
 def test_invalid_raster_configs_are_rejected(gs):
     ctx = gs.Context(1000, 128, 96, max_instances=1 << 16)  # min_tile 16
-    for bad in ((8, 2, 128), (16, 3, 128), (16, 4, 100), (32, 2, 64), (12, 4, 128), (16, 4, 512)):
+    for bad in ((8, 2, 128), (16, 3, 128), (16, 4, 100), (32, 1, 64), (12, 4, 128), (16, 4, 512)):
         with pytest.raises(gs.GsError):
             ctx.set_raster(*bad)
     ctx.set_raster(32, 4, 64)
