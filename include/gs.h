@@ -142,6 +142,8 @@ typedef struct {
                             ids and per-surfel tile counts for inspection */
   int min_tile;          /* smallest rasterizer tile edge the context will run: 8, 16
                             or 32 (0 = 16); max_width / min_tile <= 512 */
+  int host_outputs;      /* 1: the workspace also holds the device images that
+                            gs_render_stereo_host renders into (32 B per pixel) */
 } gs_limits;
 
 /* Bytes of device workspace a context with these limits needs. */
@@ -173,6 +175,22 @@ gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *
 gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
                            const gs_pose *pose_aff, const gs_intrinsics *intr, int gap_thresh,
                            const gs_roi_params *roi, const gs_outputs *out);
+
+/* gs_render_stereo with both eyes' RGB images delivered to HOST memory, for a
+ * frame loop that ends on the host (a display or an encoder). The pipeline
+ * renders into the context's own device images (gs_limits.host_outputs = 1).
+ * The dominant eye is final after Stage 1, so its image is copied out on a
+ * second stream while Stages 2-4 run; the affiliated eye's image follows
+ * Stage 4.
+ *   host_rgb_dom, host_rgb_aff: [3][H][W] float32 in page-locked host memory
+ *     (cudaHostAlloc, cudaMallocHost or cudaHostRegister); other host memory,
+ *     device memory or NULL gives GS_ERR_BAD_ARG.
+ * Asynchronous like gs_render_stereo: the host images are complete once the
+ * context's stream is synchronised (gs_context_check does that). The depth,
+ * transmittance and class images stay in the workspace (gs_context_buffer). */
+gs_status gs_render_stereo_host(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                                const gs_pose *pose_aff, const gs_intrinsics *intr, int gap_thresh,
+                                const gs_roi_params *roi, float *host_rgb_dom, float *host_rgb_aff);
 
 /* The sequential two-pass reference of Sec. 4.3: full dominant render, then a
  * full affiliated render, built from the same kernels. Black background. */

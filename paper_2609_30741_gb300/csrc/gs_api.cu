@@ -136,6 +136,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.max_instances = (int64_t)I;
   ws.max_pixels = (int64_t)P;
   ws.keep_intermediates = lim.keep_intermediates;
+  ws.host_img = c.take<float>(lim.host_outputs ? 8 * P : 1);
 }
 
 bool limits_ok(const gs_limits *lim) {
@@ -380,6 +381,9 @@ gs_status gs_context_destroy(gs_context *ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_edge) cudaEventDestroy(ctx->ev_edge);
   if (ctx->ev_strip) cudaEventDestroy(ctx->ev_strip);
+  if (ctx->copy) cudaStreamDestroy(ctx->copy);
+  if (ctx->ev_hfork) cudaEventDestroy(ctx->ev_hfork);
+  if (ctx->ev_hjoin) cudaEventDestroy(ctx->ev_hjoin);
   delete ctx;
   return GS_OK;
 }
@@ -619,9 +623,61 @@ static gs_status ensure_side(gs_context *ctx) {
   return cuda_status(e);
 }
 
+// The copy stream and events of gs_render_stereo_host (created on first use).
+static gs_status ensure_copy(gs_context *ctx) {
+  if (ctx->copy) return GS_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_hfork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_hjoin, cudaEventDisableTiming);
+  return cuda_status(e);
+}
+
+// Host destinations of the two RGB images (gs_render_stereo_host), or none.
+struct HostCopy {
+  float *dom, *aff;
+};
+
+static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                             const gs_pose *pose_aff, const gs_intrinsics *intr, int gap_thresh,
+                             const gs_roi_params *roi, const gs_outputs *out, const HostCopy *hc);
+
 gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom, const gs_pose *pose_aff,
                            const gs_intrinsics *intr, int gap_thresh, const gs_roi_params *roi,
                            const gs_outputs *out) {
+  return stereo_impl(ctx, scene, pose_dom, pose_aff, intr, gap_thresh, roi, out, nullptr);
+}
+
+static bool page_locked(const void *p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear a sticky-free error from an unknown pointer
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
+
+gs_status gs_render_stereo_host(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                                const gs_pose *pose_aff, const gs_intrinsics *intr, int gap_thresh,
+                                const gs_roi_params *roi, float *host_rgb_dom, float *host_rgb_aff) {
+  if (!ctx || !ctx->lim.host_outputs || !intr_ok(ctx, intr)) return GS_ERR_BAD_ARG;
+  if (!page_locked(host_rgb_dom) || !page_locked(host_rgb_aff)) return GS_ERR_BAD_ARG;
+  const gs_status st = ensure_copy(ctx);
+  if (st != GS_OK) return st;
+  const size_t P = (size_t)intr->width * intr->height;
+  float *img = ctx->ws.host_img;
+  gs_outputs out{};
+  out.rgb_dom = img;
+  out.depth_dom = img + 3 * P;
+  out.trans_dom = img + 4 * P;
+  out.rgb_aff = img + 5 * P;
+  const HostCopy hc{host_rgb_dom, host_rgb_aff};
+  return stereo_impl(ctx, scene, pose_dom, pose_aff, intr, gap_thresh, roi, &out, &hc);
+}
+
+static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_pose *pose_dom,
+                             const gs_pose *pose_aff, const gs_intrinsics *intr, int gap_thresh,
+                             const gs_roi_params *roi, const gs_outputs *out, const HostCopy *hc) {
   if (!ctx || !pose_dom || !pose_aff || !roi || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
     return GS_ERR_BAD_ARG;
   if (!roi_ok(gap_thresh, roi)) return GS_ERR_BAD_ARG;
@@ -645,6 +701,8 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
   kb.add(r);
   kb.add(*out);
   kb.add(pa.parallel);  // selects the depth-order path of the affiliated eye
+  kb.add(hc ? hc->dom : nullptr);  // host copies are nodes of the captured graph
+  kb.add(hc ? hc->aff : nullptr);
   const gs_status res = run_graph(ctx, 1, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
     gs_status st = begin_call(ctx, scene, p);
     if (st != GS_OK) return st;
@@ -679,6 +737,15 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2,
                          p.parallel ? kOrderUnion : kOrderOwn);
     if (st != GS_OK) return st;
+    if (hc) {  // the dominant eye is final: copy it out beside Stages 2-4
+      if ((e = cudaEventRecord(ctx->ev_hfork, ctx->stream)) == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->copy, ctx->ev_hfork, 0);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hc->dom, out->rgb_dom, sizeof(float) * 3 * (size_t)W * H, cudaMemcpyDeviceToHost,
+                            ctx->copy);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_hjoin, ctx->copy);
+      if (e != cudaSuccess) return cuda_fail(e);
+    }
     // Stages 2-3: warp, edge ROIs, gaps
     if (reuse) {
       e = launch_warp(ws, W, H, out->depth_dom, out->trans_dom, ctx->stream);
@@ -729,6 +796,11 @@ gs_status gs_render_stereo(gs_context *ctx, const gs_scene *scene, const gs_pose
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 7);
     e = copy_optional(ctx, out, W, H);
+    if (e == cudaSuccess && hc) {  // the affiliated eye, then join the dominant eye's copy
+      e = cudaMemcpyAsync(hc->aff, out->rgb_aff, sizeof(float) * 3 * (size_t)W * H, cudaMemcpyDeviceToHost,
+                          ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->stream, ctx->ev_hjoin, 0);
+    }
     mark(ctx, 8);
     return cuda_status(e);
   });

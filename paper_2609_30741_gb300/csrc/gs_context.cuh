@@ -38,6 +38,8 @@ struct gs_context {
   int have_range;       // a stereo call has measured a depth range (depth_mode 2 can reuse it)
   cudaStream_t side;    // second stream of a stereo call with depth_mode 2
   cudaEvent_t ev_fork, ev_edge, ev_strip;
+  cudaStream_t copy;    // gs_render_stereo_host: the dominant eye's copy to the host
+  cudaEvent_t ev_hfork, ev_hjoin;
 };
 
 namespace gs {

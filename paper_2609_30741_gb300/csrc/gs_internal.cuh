@@ -157,6 +157,7 @@ struct Workspace {
   int keep_intermediates;
   uint32_t bin_warp_surfels, bin_nch;  // binning chunk geometry (see launch_binning)
   int prim;                     // primitive of the prepared records (gs_scene.primitive), set by launch_preprocess
+  float *host_img;              // gs_render_stereo_host's device images: rgb_dom, depth, trans, rgb_aff [8][pixels]
   size_t n_scan_tiles, n_rs_tiles;  // look-back words of scan_tiles and rs_tiles
 };
 

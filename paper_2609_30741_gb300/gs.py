@@ -60,7 +60,7 @@ class Outputs(C.Structure):
 class Limits(C.Structure):
     _fields_ = [("max_surfels", C.c_int), ("max_width", C.c_int), ("max_height", C.c_int),
                 ("max_instances", C.c_int64), ("max_rects", C.c_int), ("keep_intermediates", C.c_int),
-                ("min_tile", C.c_int)]
+                ("min_tile", C.c_int), ("host_outputs", C.c_int)]
 
 
 class RasterConfig(C.Structure):
@@ -126,6 +126,9 @@ EXPORTS = {
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_render_stereo": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Pose),
                                    C.POINTER(Intrinsics), C.c_int, C.POINTER(RoiParams), C.POINTER(Outputs)]),
+    "gs_render_stereo_host": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Pose),
+                                        C.POINTER(Intrinsics), C.c_int, C.POINTER(RoiParams), C.c_void_p,
+                                        C.c_void_p]),
     "gs_render_two_pass": (C.c_int, [C.c_void_p, C.POINTER(Scene), C.POINTER(Pose), C.POINTER(Pose),
                                      C.POINTER(Intrinsics), C.POINTER(Outputs)]),
     "gs_warp_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Pose), C.POINTER(Pose),
@@ -257,9 +260,9 @@ class Context:
     """A renderer context: owns its workspace tensor, runs on a torch stream."""
 
     def __init__(self, max_surfels, max_width, max_height, max_instances=1 << 24, max_rects=1 << 16,
-                 keep_intermediates=False, device="cuda", stream=None, min_tile=16):
+                 keep_intermediates=False, device="cuda", stream=None, min_tile=16, host_outputs=False):
         self.lim = Limits(int(max_surfels), int(max_width), int(max_height), int(max_instances),
-                          int(max_rects), int(bool(keep_intermediates)), int(min_tile))
+                          int(max_rects), int(bool(keep_intermediates)), int(min_tile), int(bool(host_outputs)))
         nbytes = C.c_size_t()
         _check(lib().gs_workspace_size(C.byref(self.lim), C.byref(nbytes)), "gs_workspace_size")
         self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=device)
@@ -382,6 +385,20 @@ class Context:
                                       C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), int(gap_thresh),
                                       C.byref(roi), C.byref(os_)), "gs_render_stereo")
         return out
+
+    def render_stereo_host(self, scene: DeviceScene, pose_dom, pose_aff, cam, host_rgb_dom, host_rgb_aff,
+                           gap_thresh=2, roi=None):
+        """gs_render_stereo_host: both eyes' RGB into page-locked host tensors
+        ([3, H, W] float32, pin_memory=True); complete after the stream syncs."""
+        for t in (host_rgb_dom, host_rgb_aff):
+            if t.device.type != "cpu" or t.dtype != torch.float32 or not t.is_contiguous() or \
+                    tuple(t.shape) != (3, cam.height, cam.width):
+                raise ValueError("host images must be contiguous [3, H, W] float32 CPU tensors")
+        roi = roi if roi is not None else roi_params()
+        _check(lib().gs_render_stereo_host(self.h, C.byref(scene.c), C.byref(pose_struct(pose_dom)),
+                                           C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)),
+                                           int(gap_thresh), C.byref(roi), C.c_void_p(host_rgb_dom.data_ptr()),
+                                           C.c_void_p(host_rgb_aff.data_ptr())), "gs_render_stereo_host")
 
     def ssim(self, img, ref, out=None):
         """Mean SSIM of img against ref ([C, H, W] float32 CUDA tensors), as a
