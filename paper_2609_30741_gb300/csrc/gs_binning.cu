@@ -324,12 +324,14 @@ __global__ void keep_union_kernel(const uint32_t *__restrict__ src, const uint32
 //     it and writes every surfel id to its slot.
 //
 // In modes 0 and 1 every warp keeps private per-tile counters for the band in
-// shared memory and walks its list's rows 32 at a time, one (surfel, tile row)
-// per lane, reading the row's tile ranges from the spans. The lanes of one step
-// hold rows of surfels in depth order; lanes that reach the same tile are ranked
-// by a per-tile bit mask of lanes, so every tile's list comes out in depth
-// order. Both modes run the same walk code in one kernel, so the counts of mode
-// 0 and the slots written in mode 1 always agree.
+// shared memory and walks its list's instances 32 at a time, one (surfel, tile)
+// per lane: a warp scan over the entries' instance counts (read from the row
+// spans) gives each lane its entry, row and tile, so no lane loops over a span
+// while others idle. The lanes of one step hold instances in depth order;
+// lanes that reach the same tile are ranked by a per-tile bit mask of lanes, so
+// every tile's list comes out in depth order. Both modes run the same walk code
+// in one kernel, so the counts of mode 0 and the slots written in mode 1 always
+// agree.
 constexpr int kBinWarps = 8;
 constexpr int kBinThreads = kBinWarps * 32;
 constexpr int kBandRows = 4;
@@ -529,110 +531,109 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(BinArgs a, int mode
   const uint2 li = lists[w];
   const BandEntry *q = a.pool + li.x;
   const int qn = (int)li.y;
-  // all loops below are warp-uniform: qn, qpos and total agree on all lanes
-  int qpos = 0, rdone = 0;  // list cursor; rows of entry qpos already taken
-  while (qpos < qn) {
+  // All loops below are warp-uniform. A step loads 32 entries (one per lane)
+  // and the instance counts of their rows from the row spans; a warp scan of
+  // those counts then maps instance g of the step to its entry, row and tile,
+  // and the step's instances are taken 32 at a time, one per lane, so no lane
+  // loops over a span while others idle.
+  for (int qpos = 0; qpos < qn; qpos += 32) {
     const int e = qpos + lane;
     uint32_t id = 0, sp = 0;
-    int lo = 0, nr = 0;
+    int lo = 0;
+    int rc[kBandRows];  // instances per row of the entry
+    int pk[kBandRows];  // the row's ranges: a0 | na << 10 | c0 << 20 (na = a1 - a0 + 1 or 0)
+#pragma unroll
+    for (int r = 0; r < kBandRows; ++r) rc[r] = pk[r] = 0;
     if (e < qn) {
       const BandEntry en = q[e];
       id = en.id;
       sp = en.sp;
       lo = (int)(en.rows >> 4);
-      nr = (int)(en.rows & 15u);
-      if (lane == 0) {
-        lo += rdone;
-        sp += (uint32_t)rdone;
-        nr -= rdone;
+      const int nr = (int)(en.rows & 15u);
+#pragma unroll
+      for (int r = 0; r < kBandRows; ++r) {
+        if (r < nr && sp + (uint32_t)r < a.span_cap) {
+          const uint2 v = a.spans[sp + (uint32_t)r];
+          const int a0 = (int)(v.x & 0xffffu), a1 = (int)(v.x >> 16);
+          const int c0 = (int)(v.y & 0xffffu), c1 = (int)(v.y >> 16);
+          const int na = max(a1 - a0 + 1, 0);
+          rc[r] = na + max(c1 - c0 + 1, 0);
+          pk[r] = (a0 & 1023) | (na << 10) | ((c0 & 1023) << 20);
+        }
       }
     }
-    int incl = nr;
+    int nt = 0;
+#pragma unroll
+    for (int r = 0; r < kBandRows; ++r) nt += rc[r];
+    int incl = nt;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, incl, o);
       if (lane >= o) incl += y;
     }
     const int total = shi(incl, 31);
-    int kl = 0, kh = 31;  // entry of row `lane`: first lane whose inclusive prefix exceeds it
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-      const int mid = (kl + kh) >> 1;
-      if (shi(incl, mid) > lane) kh = mid; else kl = mid + 1;
-    }
-    const int k = kl;
-    const bool act = lane < total;
-    const uint32_t sid = (uint32_t)shi((int)id, k);
-    const int excl_k = shi(incl, k) - shi(nr, k);
-    const int ty = shi(lo, k) + (lane - excl_k);
-    const uint32_t spk = (uint32_t)shi((int)sp, k) + (uint32_t)(lane - excl_k);
-    // advance past the rows taken in this step
-    if (total <= 32) {
-      qpos += 32;
-      rdone = 0;
-    } else {
-      int ml = 0, mh = 31;  // entry holding row 31
+    for (int g0 = 0; g0 < total; g0 += 32) {
+      const int g = g0 + lane;
+      const bool act = g < total;
+      int kl = 0, kh = 31;  // entry of instance g: first lane whose inclusive prefix exceeds it
 #pragma unroll
       for (int it = 0; it < 5; ++it) {
-        const int mid = (ml + mh) >> 1;
-        if (shi(incl, mid) > 31) mh = mid; else ml = mid + 1;
+        const int mid = (kl + kh) >> 1;
+        if (shi(incl, mid) > g) kh = mid; else kl = mid + 1;
       }
-      const int taken = 32 - (shi(incl, ml) - shi(nr, ml));
-      if (taken == shi(nr, ml)) {
-        qpos += ml + 1;
-        rdone = 0;
+      const int k = kl;
+      const uint32_t sid = (uint32_t)shi((int)id, k);
+      // index of the instance among entry k's instances, then its row r and
+      // the row's ranges (all from lane k's registers: independent shuffles)
+      int t = g - (shi(incl, k) - shi(nt, k));
+      int rcs[kBandRows], pks[kBandRows];
+#pragma unroll
+      for (int rr = 0; rr < kBandRows; ++rr) {
+        rcs[rr] = shi(rc[rr], k);
+        pks[rr] = shi(pk[rr], k);
+      }
+      int r = 0, w = pks[0];
+#pragma unroll
+      for (int rr = 0; rr < kBandRows - 1; ++rr) {
+        if (r == rr && t >= rcs[rr]) {
+          t -= rcs[rr];
+          r = rr + 1;
+          w = pks[rr + 1];
+        }
+      }
+      const int ty = shi(lo, k) + r;
+      // the lane's tile: the t-th of the row's ranges [a0, a1] u [c0, c1]
+      const int a0 = w & 1023, na = (w >> 10) & 1023, c0 = (w >> 20) & 1023;
+      const int tx = t < na ? a0 + t : c0 + (t - na);
+      const bool valid = act && (!a.mask || a.mask[(size_t)ty * tx_n + tx] != 0);
+      const int bt = (ty - by0) * tx_n + tx;
+      if (mode == 0) {
+        if (valid) {
+          atomicAdd(&my_cnt[bt], 1u);
+          if (a.cnt_bin) atomicAdd(&a.cnt_bin[sid], 1u);
+        }
       } else {
-        rdone = (ml == 0 ? rdone : 0) + taken;
-        qpos += ml;
+        // lanes on one tile are ranked by lane (depth order); the highest of
+        // them advances the tile's counter
+        if (valid) atomicOr(&my_msk[bt], 1u << lane);
+        __syncwarp();
+        uint32_t m = 0, base = 0;
+        if (valid) {
+          m = my_msk[bt];
+          base = my_cnt[bt];
+          const uint32_t pos = base + (uint32_t)__popc(m & lt);
+          if (pos < a.cap) {
+            a.ival[pos] = sid;
+            if (a.ikey) a.ikey[pos] = (uint32_t)(ty * tx_n + tx);
+          }
+        }
+        __syncwarp();
+        if (valid && lane == 31 - __clz(m)) {
+          my_cnt[bt] = base + (uint32_t)__popc(m);
+          my_msk[bt] = 0u;
+        }
+        __syncwarp();
       }
-    }
-    int a0 = 1, a1 = 0, c0 = 1, c1 = 0;
-    if (act && spk < a.span_cap) {
-      const uint2 v = a.spans[spk];
-      a0 = (int)(v.x & 0xffffu);
-      a1 = (int)(v.x >> 16);
-      c0 = (int)(v.y & 0xffffu);
-      c1 = (int)(v.y >> 16);
-    }
-    const int rowb = (ty - by0) * tx_n;
-    const uint8_t *mrow = a.mask ? a.mask + (size_t)ty * tx_n : nullptr;
-    if (mode == 0) {
-      uint32_t nrow = 0;
-      for (int s2 = 0; s2 < 2; ++s2)
-        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
-          if (!mrow || mrow[tx]) {
-            atomicAdd(&my_cnt[rowb + tx], 1u);
-            ++nrow;
-          }
-      if (a.cnt_bin && nrow) atomicAdd(&a.cnt_bin[sid], nrow);
-    } else {
-      for (int s2 = 0; s2 < 2; ++s2)
-        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
-          if (!mrow || mrow[tx]) atomicOr(&my_msk[rowb + tx], 1u << lane);
-      __syncwarp();
-      for (int s2 = 0; s2 < 2; ++s2)
-        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
-          if (!mrow || mrow[tx]) {
-            const int bt = rowb + tx;
-            const uint32_t pos = my_cnt[bt] + (uint32_t)__popc(my_msk[bt] & lt);
-            if (pos < a.cap) {
-              a.ival[pos] = sid;
-              if (a.ikey) a.ikey[pos] = (uint32_t)(ty * tx_n + tx);
-            }
-          }
-      __syncwarp();
-      // the highest lane on a tile advances its counter and clears its mask
-      for (int s2 = 0; s2 < 2; ++s2)
-        for (int tx = s2 ? c0 : a0; tx <= (s2 ? c1 : a1); ++tx)
-          if (!mrow || mrow[tx]) {
-            const int bt = rowb + tx;
-            const uint32_t m = my_msk[bt];
-            if (m != 0u && lane == 31 - __clz(m)) {
-              my_cnt[bt] += (uint32_t)__popc(m);
-              my_msk[bt] = 0u;
-            }
-          }
-      __syncwarp();
     }
   }
   if (mode == 0) {

@@ -478,6 +478,25 @@ def test_full_size_sampled_pixels_match_oracle(object_scene, orc):
                        o_rgb, o_dep, o_tr, mrg, f"window {win}")
 
 
+def test_full_size_bench_configuration(gs, object_scene, orc):
+    """The launch configuration the bench times (the autotuner's pick on this
+    workload: 32-pixel tiles, 2 pixels per thread, 256 records per stage) gives
+    the full-size frame bit for bit like the default configuration, and a window
+    of it matches the oracle directly."""
+    s = object_scene
+    ctx = gs.Context(s["scene"].n, s["cam"].width, s["cam"].height, max_instances=1 << 26)
+    ctx.set_raster(32, 2, 256)
+    out = ctx.render_stereo(s["ds"], s["dom"], s["aff"], s["cam"], gap_thresh=2)
+    ctx.check_ok()
+    for k in ("rgb_dom", "depth_dom", "trans_dom", "rgb_aff", "cls_aff", "edge_widths", "roi_count"):
+        assert torch.equal(out[k], s["out"][k]), k
+    x0, y0 = 1000, 600
+    o_rgb, o_dep, o_tr, mrg, _ = orc.render(s["scene"], s["dom"], s["cam"], window=(x0, y0, 64, 64))
+    sl = (slice(y0, y0 + 64), slice(x0, x0 + 64))
+    compare_render(_np(out["rgb_dom"][:, sl[0], sl[1]]), _np(out["depth_dom"][sl]), _np(out["trans_dom"][sl]),
+                   o_rgb, o_dep, o_tr, mrg, "bench configuration")
+
+
 def test_full_size_two_pass_agrees_on_roi_tiles(gs, object_scene):
     s = object_scene
     ctx2 = gs.Context(s["scene"].n, s["cam"].width, s["cam"].height, max_instances=1 << 26)
