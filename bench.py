@@ -206,9 +206,10 @@ class ClockSampler:
 
 
 def oracle_sample(scene, cam, pose, k, seconds=10.0):
-    """One bounded oracle sample: the per-pixel render of a square window of the
+    """One bounded oracle sample: the per-pixel render of a window of the
     dominant eye (sized from a 48x48 probe so that the sample takes about
-    `seconds` of host time) plus the fixed per-frame preparation."""
+    `seconds` of host time, up to the whole frame) plus the fixed per-frame
+    preparation. Returns (prep, per_px, seconds spent, "w x h")."""
     import oracle
     rng = np.random.default_rng(100 + k)
     probe = 48
@@ -221,16 +222,17 @@ def oracle_sample(scene, cam, pose, k, seconds=10.0):
     oracle.render(scene, pose, cam, window=(x0, y0, probe, probe))
     t_probe = time.perf_counter() - t0
     per_px0 = max(t_probe - t_small, 1e-9) / (probe * probe - 16)
-    win = int(math.sqrt(max(seconds - t_small - t_probe, 0.0) / per_px0))
-    win = max(probe, min(win, cam.width // 2, cam.height // 2))
-    x0 = int(rng.integers(cam.width // 4, 3 * cam.width // 4 - win + 1))
-    y0 = int(rng.integers(cam.height // 4, 3 * cam.height // 4 - win + 1))
+    area = max(seconds - t_small - t_probe, 0.0) / per_px0
+    h = max(probe, min(int(math.sqrt(area)), cam.height))
+    w = max(probe, min(int(area / h), cam.width))
+    # centred on the frame (the dense part of the object workloads)
+    x0, y0 = (cam.width - w) // 2, (cam.height - h) // 2
     t0 = time.perf_counter()
-    oracle.render(scene, pose, cam, window=(x0, y0, win, win))
+    oracle.render(scene, pose, cam, window=(x0, y0, w, h))
     t_big = time.perf_counter() - t0
-    per_px = max(t_big - t_small, 1e-9) / (win * win - 16)
+    per_px = max(t_big - t_small, 1e-9) / (w * h - 16)
     prep = max(t_small - 16 * per_px, 0.0)
-    return prep, per_px, t_small + t_probe + t_big, win
+    return prep, per_px, t_small + t_probe + t_big, f"{w}x{h}"
 
 
 def oracle_frame_ms(prep, per_px, npix, roi_frac):
@@ -266,7 +268,7 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"per step: oracle render of a {win}x{win} dominant-eye window (about 4 s "
+                             "sample": f"per step: oracle render of a {win} dominant-eye window (about 4 s "
                                        f"of host time) plus the per-frame surfel preparation, extrapolated to both "
                                        f"eyes (dominant frame + ROI share)"},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -476,7 +478,7 @@ def run_ours(args):
             prep, per_px, t, win = oracle_sample(scene, cam, poses[0][0], 0, seconds=10.0)
             cpu = {"value": oracle_frame_ms(prep, per_px, W * H, float(np.mean(roi_fracs))), "unit": "ms",
                    "cores": oracle.num_threads(), "kind": "oracle",
-                   "sample": f"oracle render of a {win}x{win} dominant-eye window + per-frame surfel preparation "
+                   "sample": f"oracle render of a {win} dominant-eye window + per-frame surfel preparation "
                              f"({t:.1f} s of CPU work), extrapolated to the dominant frame plus the measured "
                              f"ROI share of the affiliated eye"}
         except Exception as ex:  # the CPU baseline is reported, not required
