@@ -580,7 +580,7 @@ struct TrainArgs {
 // per tile: squared errors at the tile's hole pixels of the network fill and of
 // the plain image, hole and pixel counts (the loss normalisers and the gate
 // labels; the warped pixels carry view-dependent colour the features cannot
-// see, so the label judges the fill alone)
+// see, so the label rates the fill alone)
 __global__ void __launch_bounds__(256) repair_stats_kernel(TrainArgs a) {
   const int t = blockIdx.x;
   const uint32_t te = a.tiles[t];

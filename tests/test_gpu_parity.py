@@ -39,7 +39,7 @@ def _np(t):
 def compare_render(g_rgb, g_dep, g_tr, o_rgb, o_dep, o_tr, margin, what=""):
     """Depth is compared relative to max(|D|, 1e-3 * d_max): the float32 sum of
     weighted depths carries an absolute error of about 1e-7 of the depth range,
-    so pixels with almost no coverage (D -> 0) are judged on that floor."""
+    so pixels with almost no coverage (D -> 0) are measured against that floor."""
     ok = margin >= MARGIN
     frac = 1.0 - ok.mean()
     assert frac <= MAX_MARGINAL, f"{what}: {frac:.4%} marginal pixels"
