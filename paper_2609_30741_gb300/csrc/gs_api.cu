@@ -66,7 +66,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   const size_t table = tiles * ws.bin_nch;
   ws.cnt_bin = c.take<uint32_t>(lim.keep_intermediates ? N : 1);
   ws.band_pool_cap = (uint32_t)(8 * N + 1024);
-  const size_t rs_words = radix_table_words(N);
+  const size_t rs_words = radix_status_words(N);
   for (int e = 0; e < 2; ++e) {  // one binning scratch per eye
     BinScratch &b = ws.bin[e];
     for (int k = 0; k < 2; ++k) {
@@ -85,12 +85,11 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     b.rqueue = c.take<uint32_t>(2);
     b.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
     b.roi_flag = c.take<uint8_t>(N);
-    b.rs_table = c.take<uint32_t>(rs_words);
-    b.rs_offs = c.take<uint32_t>(rs_words);
-    b.rs_n = c.take<uint32_t>(1);
-    b.rs_tiles = c.take<unsigned long long>(scan_tiles(rs_words));
+    b.rs_hist = c.take<uint32_t>(2 * kRsPasses * 256);
+    b.rs_status = c.take<unsigned long long>(rs_words);
+    b.rs_ctl = c.take<uint32_t>(4);
     b.scan_tiles = c.take<unsigned long long>(scan_tiles(scan_n));
-    ws.n_rs_tiles = scan_tiles(rs_words);
+    ws.n_rs_status = rs_words;
     ws.n_scan_tiles = scan_tiles(scan_n);
     b.scan_ticket = c.take<uint32_t>(4);
   }
@@ -360,7 +359,9 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
     if (e == cudaSuccess)
       e = cudaMemsetAsync(ctx->ws.bin[k].scan_tiles, 0, sizeof(unsigned long long) * ctx->ws.n_scan_tiles, ctx->stream);
     if (e == cudaSuccess)
-      e = cudaMemsetAsync(ctx->ws.bin[k].rs_tiles, 0, sizeof(unsigned long long) * ctx->ws.n_rs_tiles, ctx->stream);
+      e = cudaMemsetAsync(ctx->ws.bin[k].rs_status, 0, sizeof(unsigned long long) * ctx->ws.n_rs_status, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.bin[k].rs_hist, 0, sizeof(uint32_t) * kRsPasses * 256, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.bin[k].rs_ctl, 0, sizeof(uint32_t) * 4, ctx->stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.ctr, 0, sizeof(Counters), ctx->stream);
   if (e != cudaSuccess) {

@@ -743,7 +743,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   Counters *ctr = ws.ctr;
   const int ntiles = tiles_x * tiles_y;
   const uint32_t cap = (uint32_t)ws.max_instances;
-  const RadixScratch rs{b.rs_table, b.rs_offs, b.rs_n, b.rs_tiles, b.scan_ticket, &ctr->status};
+  const RadixScratch rs{b.rs_hist, b.rs_hist + kRsPasses * 256, b.rs_status, b.rs_ctl, &ctr->status};
   if (tile_mask) {
     launch_k(mask_sat_kernel, 1, 1024, 0, s, tile_mask, tiles_x, tiles_y, b.mask_sat);
     GS_LAUNCHED(1);

@@ -102,9 +102,9 @@ struct BinScratch {
   uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
   uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
   uint8_t *roi_flag;            // per surfel: binned and its rectangle holds a masked tile
-  uint32_t *rs_table, *rs_offs; // radix sort [digit][tile] counts and their scan
-  uint32_t *rs_n;               // length of the radix table
-  unsigned long long *rs_tiles; // look-back tile words of the radix table scans
+  uint32_t *rs_hist;            // radix sort: [4][256] digit counts, then [4][256] digit bases
+  unsigned long long *rs_status;// radix sort look-back words [tiles][256]
+  uint32_t *rs_ctl;             // radix sort control words (zero at creation)
   unsigned long long *scan_tiles;  // look-back tile words of the other scans
   uint32_t *scan_ticket;        // scan control words {tile counter, exit counter, epoch}
 };
@@ -158,7 +158,7 @@ struct Workspace {
   uint32_t bin_warp_surfels, bin_nch;  // binning chunk geometry (see launch_binning)
   int prim;                     // primitive of the prepared records (gs_scene.primitive), set by launch_preprocess
   float *host_img;              // gs_render_stereo_host's device images: rgb_dom, depth, trans, rgb_aff [8][pixels]
-  size_t n_scan_tiles, n_rs_tiles;  // look-back words of scan_tiles and rs_tiles
+  size_t n_scan_tiles, n_rs_status;  // look-back words of scan_tiles and rs_status
 };
 
 constexpr int kScanThreads = 512;

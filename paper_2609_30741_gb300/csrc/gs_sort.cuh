@@ -1,15 +1,21 @@
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs, 8 bits per pass,
-// with a device-resident element count.
+// with a device-resident element count ("one sweep" per pass).
 //
-// Each pass has three phases with no waiting between CTAs:
-//   1. every tile of 2048 pairs counts its digits into a [digit][tile] table;
-//   2. one device-wide exclusive scan of that table in digit-major order gives,
-//      for every (digit, tile), where the tile's run of that digit starts;
-//   3. every tile ranks its pairs stably (per warp with bit ballots, then across
-//      warps), sorts them locally in shared memory and writes each digit run to
-//      its place with coalesced stores.
-// Tiles are independent in phases 1 and 3, so the passes scale with the number
-// of SMs instead of waiting on a chain of predecessor tiles.
+//   1. One histogram kernel counts every pass's digits over all keys at once
+//      (the digit counts of a pass do not depend on the order the earlier
+//      passes leave); the last CTA out turns them into each pass's digit bases.
+//   2. Per pass, one kernel: a CTA takes the next tile of 2048 pairs from a
+//      device counter, ranks its pairs stably (per warp with bit ballots, then
+//      across warps), publishes its per-digit counts, and finds every digit's
+//      offset among the earlier tiles by decoupled look-back: it adds the
+//      published counts of its predecessors, 8 tiles per step, down to the
+//      nearest tile that has published an inclusive prefix, then publishes its
+//      own. The tile is sorted in shared memory and each digit run is written
+//      to its place with coalesced stores.
+// Tiles are taken in counter order, so a CTA only ever waits for tiles that
+// CTAs already running hold; every wait is bounded (kLbSpinLimit reads of a
+// word, then kStTimeout is raised in the status word and the tile's count is
+// taken as zero).
 #pragma once
 
 #include "gs_internal.cuh"
@@ -21,92 +27,116 @@ namespace gs {
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 pairs per tile
+constexpr int kRsPasses = 4;                    // 32-bit keys
+constexpr int kRsWindow = 8;                    // predecessor tiles read per look-back step
 
-// n_table = 256 * number of tiles, written by phase 1 for the scan of phase 2.
-// With `offs` given (small tables), the last block to finish (counted on
-// *ticket, which it resets) also runs phase 2: thread d scans digit d's row.
+struct RadixScratch {
+  uint32_t *hist;              // [kRsPasses][256] digit counts (0 between sorts)
+  uint32_t *base;              // [kRsPasses][256] exclusive digit bases
+  unsigned long long *status;  // [tiles][256] look-back words (zero at context creation)
+  uint32_t *ctl;               // {tile counter, exit counter, epoch, histogram exit counter}, zero at creation
+  uint32_t *status_word;       // device status word
+};
+
+inline size_t radix_status_words(size_t n_max) { return 256 * ((n_max + kRsTile - 1) / kRsTile + 1); }
+
+inline int radix_hist_grid(uint32_t n_max) {
+  const uint32_t tiles = (n_max + kRsTile - 1) / kRsTile;
+  return (int)(tiles < 1 ? 1 : (tiles > 152 * 4 ? 152 * 4 : tiles));
+}
+
+// Digit counts of all passes; the last CTA out writes the bases and clears the
+// counts and its ticket.
 static __global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint32_t *__restrict__ keys,
-                                                                     const uint32_t *n_ptr, uint32_t n_max, int shift,
-                                                                     uint32_t *__restrict__ table,
-                                                                     uint32_t *__restrict__ n_table,
-                                                                     uint32_t *__restrict__ offs, uint32_t *ticket) {
+                                                                     const uint32_t *n_ptr, uint32_t n_max,
+                                                                     int npass, RadixScratch sc) {
   griddep_wait();
-  __shared__ uint32_t h[kRsThreads / 32][256];
+  __shared__ uint32_t h[kRsPasses][256];
   __shared__ uint32_t s_last, s_scan[32];
+  for (int i = threadIdx.x; i < kRsPasses * 256; i += kRsThreads) (&h[0][0])[i] = 0u;
+  __syncthreads();
   const uint32_t n = load_n(n_ptr, n_max);
-  const uint32_t ntiles = (n + kRsTile - 1) / kRsTile;
-  if (blockIdx.x == 0 && threadIdx.x == 0) *n_table = 256u * ntiles;
-  uint32_t(*hw) = h[threadIdx.x >> 5];
-  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    for (int i = threadIdx.x; i < (kRsThreads / 32) * 256; i += kRsThreads) (&h[0][0])[i] = 0;
-    __syncthreads();
-    const uint32_t base = t * (uint32_t)kRsTile;
-#pragma unroll
-    for (int j = 0; j < kRsItems; ++j) {
-      const uint32_t i = base + (uint32_t)(j * kRsThreads + threadIdx.x);
-      if (i < n) atomicAdd(&hw[(keys[i] >> shift) & 255u], 1u);
-    }
-    __syncthreads();
-    uint32_t c = 0;
-#pragma unroll
-    for (int w = 0; w < kRsThreads / 32; ++w) c += h[w][threadIdx.x];
-    table[(size_t)threadIdx.x * ntiles + t] = c;
-    __syncthreads();
+  for (uint32_t i = blockIdx.x * kRsThreads + threadIdx.x; i < n; i += gridDim.x * kRsThreads) {
+    const uint32_t k = keys[i];
+    for (int p = 0; p < npass; ++p) atomicAdd(&h[p][(k >> (8 * p)) & 255u], 1u);
   }
-  if (!offs) return;
+  __syncthreads();
+  for (int p = 0; p < npass; ++p) {
+    const uint32_t v = h[p][threadIdx.x];
+    if (v) atomicAdd(&sc.hist[p * 256 + threadIdx.x], v);
+  }
   if (threadIdx.x == 0) {
     __threadfence();
-    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1 ? 1u : 0u;
+    s_last = atomicAdd(&sc.ctl[3], 1u) == gridDim.x - 1 ? 1u : 0u;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  const uint32_t *row = table + (size_t)threadIdx.x * ntiles;
-  uint32_t tot = 0;
-  for (uint32_t t = 0; t < ntiles; ++t) tot += __ldcg(row + t);
-  uint32_t base;
-  block_exclusive_scan<kRsThreads>(tot, &base, s_scan);
-  uint32_t *orow = offs + (size_t)threadIdx.x * ntiles;
-  for (uint32_t t = 0; t < ntiles; ++t) {
-    const uint32_t v = __ldcg(row + t);
-    orow[t] = base;
-    base += v;
+  for (int p = 0; p < npass; ++p) {
+    const uint32_t v = __ldcg(&sc.hist[p * 256 + threadIdx.x]);
+    uint32_t ex;
+    block_exclusive_scan<kRsThreads>(v, &ex, s_scan);
+    sc.base[p * 256 + threadIdx.x] = ex;
+    sc.hist[p * 256 + threadIdx.x] = 0u;
   }
-  if (threadIdx.x == 0) *ticket = 0u;
+  if (threadIdx.x == 0) sc.ctl[3] = 0u;
 }
 
-struct TableLoad {
-  const uint32_t *table;
-  __device__ uint32_t operator()(uint32_t i) const { return table[i]; }
-};
+// Sum of digit d's counts over tiles [0, t) (t > 0) by decoupled look-back.
+__device__ __forceinline__ uint32_t rs_lookback(const unsigned long long *status, uint32_t t, int d, uint32_t epoch,
+                                                uint32_t *status_word) {
+  uint32_t prefix = 0;
+  for (int j = (int)t - 1; j >= 0; j -= kRsWindow) {
+    unsigned long long w[kRsWindow];
+#pragma unroll
+    for (int k = 0; k < kRsWindow; ++k)  // independent loads: one round trip per window
+      w[k] = j - k >= 0 ? lb_load(status + (size_t)(j - k) * 256 + d) : 0ull;
+#pragma unroll
+    for (int k = 0; k < kRsWindow; ++k) {
+      if (j - k < 0) return prefix;
+      unsigned long long x = w[k];
+      uint32_t spin = 0;
+      for (;;) {
+        const uint32_t hi = (uint32_t)(x >> 32);
+        if ((hi >> 2) == epoch && (hi & 3u) != 0u) break;
+        if (++spin > kLbSpinLimit) {  // never expected: flag it and take the tile as empty, inclusive
+          atomicOr(status_word, kStTimeout);
+          x = ((unsigned long long)((epoch << 2) | kLbIncl) << 32);
+          break;
+        }
+        x = lb_load(status + (size_t)(j - k) * 256 + d);
+      }
+      prefix += (uint32_t)x;
+      if (((uint32_t)(x >> 32) & 3u) == kLbIncl) return prefix;
+    }
+  }
+  return prefix;
+}
 
-struct TableApply {
-  uint32_t *offs;
-  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const { offs[i] = prefix; }
-  __device__ void end(uint32_t, uint32_t) const {}
-};
-
-static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const uint32_t *__restrict__ kin,
-                                                                           const uint32_t *__restrict__ vin,
-                                                                           uint32_t *__restrict__ kout,
-                                                                           uint32_t *__restrict__ vout,
-                                                                           const uint32_t *n_ptr, uint32_t n_max,
-                                                                           int shift,
-                                                                           const uint32_t *__restrict__ offs) {
+static __global__ void __launch_bounds__(kRsThreads) rs_sweep_kernel(const uint32_t *__restrict__ kin,
+                                                                      const uint32_t *__restrict__ vin,
+                                                                      uint32_t *__restrict__ kout,
+                                                                      uint32_t *__restrict__ vout,
+                                                                      const uint32_t *n_ptr, uint32_t n_max, int pass,
+                                                                      RadixScratch sc) {
   griddep_wait();
   constexpr int NW = kRsThreads / 32;
   __shared__ uint32_t s_warp[NW][256];
   __shared__ uint32_t s_local_base[256], s_global[256];
   __shared__ uint32_t s_keys[kRsTile], s_vals[kRsTile];
   __shared__ uint32_t s_scan[32];
+  __shared__ uint32_t s_tile;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
+  const int shift = 8 * pass;
+  if (tid == 0) s_tile = atomicAdd(&sc.ctl[0], 1u);
+  __syncthreads();
+  const uint32_t t = s_tile;
+  const uint32_t epoch = (*(volatile uint32_t *)(sc.ctl + 2)) & 0x3fffffffu;
   const uint32_t n = load_n(n_ptr, n_max);
-  const uint32_t ntiles = (n + kRsTile - 1) / kRsTile;
-  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const uint32_t base = t * (uint32_t)kRsTile;
+  const uint32_t base = t * (uint32_t)kRsTile;
+  if (base < n) {
     for (int i = tid; i < NW * 256; i += kRsThreads) (&s_warp[0][0])[i] = 0;
-    s_global[tid] = offs[(size_t)tid * ntiles + t];
     __syncthreads();
     // warp w owns pairs [w * 32 * kRsItems, (w + 1) * 32 * kRsItems) of the tile
     uint32_t k[kRsItems], r[kRsItems], v[kRsItems];
@@ -137,7 +167,8 @@ static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const 
       r[j] = before + __popc(peers & lt);
     }
     __syncthreads();
-    // digit d = tid: the tile's count and each warp's offset inside the digit run
+    // digit d = tid: the tile's count, each warp's offset inside the digit run,
+    // the run's place among the earlier tiles (look-back) and in the output
     uint32_t cnt = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) {
@@ -145,6 +176,16 @@ static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const 
       s_warp[w][tid] = cnt;
       cnt += c;
     }
+    unsigned long long *my = sc.status + (size_t)t * 256 + tid;
+    uint32_t prefix = 0;
+    if (t == 0) {
+      lb_store(my, epoch, kLbIncl, cnt);
+    } else {
+      lb_store(my, epoch, kLbAgg, cnt);
+      prefix = rs_lookback(sc.status, t, tid, epoch, sc.status_word);
+      lb_store(my, epoch, kLbIncl, prefix + cnt);
+    }
+    s_global[tid] = __ldg(&sc.base[pass * 256 + tid]) + prefix;
     {
       uint32_t ex;
       block_exclusive_scan<kRsThreads>(cnt, &ex, s_scan);
@@ -170,47 +211,31 @@ static __global__ void __launch_bounds__(kRsThreads, 4) rs_scatter_kernel(const 
       kout[gp] = key;
       vout[gp] = s_vals[i];
     }
-    __syncthreads();
+  }
+  // the last CTA out clears the tile counter and advances the epoch
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&sc.ctl[1], 1u) == gridDim.x - 1) {
+      sc.ctl[0] = 0u;
+      sc.ctl[1] = 0u;
+      sc.ctl[2] = (epoch + 1u) & 0x3fffffffu;
+      __threadfence();
+    }
   }
 }
 
-struct RadixScratch {
-  uint32_t *table;            // [256][tiles]
-  uint32_t *offs;             // [256][tiles]
-  uint32_t *n_table;          // one word
-  unsigned long long *tiles;  // look-back words of the table scan
-  uint32_t *ticket;           // scan control words (the first is 0 between scans)
-  uint32_t *status;           // device status word
-};
-
-inline size_t radix_table_words(size_t n_max) { return 256 * ((n_max + kRsTile - 1) / kRsTile + 1); }
-
-inline int radix_grid(uint32_t n_max) {
-  const uint32_t tiles = (n_max + kRsTile - 1) / kRsTile;
-  return (int)(tiles < 1 ? 1 : (tiles > 152 * 8 ? 152 * 8 : tiles));
-}
-
-// Sorts on bits [0, bits); the result lands in buffer index *which.
+// Sorts on bits [0, bits) (bits <= 32); the result lands in buffer index *which.
 inline cudaError_t radix_sort(uint32_t *const keys[2], uint32_t *const vals[2], const uint32_t *n_ptr, uint32_t n_max,
                               int bits, const RadixScratch &sc, int *which, cudaStream_t s) {
   const int npass = (bits + 7) / 8;
-  const int grid = radix_grid(n_max);
-  const uint32_t table_max = (uint32_t)radix_table_words(n_max);
-  // small tables (<= 32 tiles per digit row) are scanned by the histogram
-  // kernel's last block: one launch fewer; larger rows scan faster in parallel
-  const bool fused = (n_max + kRsTile - 1) / kRsTile <= 32;
+  const int tiles = (int)((n_max + kRsTile - 1) / kRsTile);
+  launch_k(rs_hist_kernel, radix_hist_grid(n_max), kRsThreads, 0, s, (const uint32_t *)keys[0], n_ptr, n_max, npass,
+           sc);
+  GS_LAUNCHED(1);
   int cur = 0;
   for (int p = 0; p < npass; ++p) {
-    launch_k(rs_hist_kernel, grid, kRsThreads, 0, s, keys[cur], n_ptr, n_max, 8 * p, sc.table, sc.n_table,
-                                               fused ? sc.offs : nullptr, sc.ticket);
-    GS_LAUNCHED(1);
-    if (!fused) {
-      cudaError_t e = scan_launch(TableLoad{sc.table}, TableApply{sc.offs}, sc.n_table, table_max, sc.tiles,
-                                  sc.ticket, sc.status, s);
-      if (e != cudaSuccess) return e;
-    }
-    launch_k(rs_scatter_kernel, grid, kRsThreads, 0, s, keys[cur], vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_ptr, n_max,
-                                                  8 * p, sc.offs);
+    launch_k(rs_sweep_kernel, tiles < 1 ? 1 : tiles, kRsThreads, 0, s, (const uint32_t *)keys[cur],
+             (const uint32_t *)vals[cur], keys[cur ^ 1], vals[cur ^ 1], n_ptr, n_max, p, sc);
     GS_LAUNCHED(1);
     cur ^= 1;
   }
