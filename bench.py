@@ -464,12 +464,17 @@ def run_ours(args):
         OPS_CONTRIB * float(np.mean(pairs_contrib))
     achieved = ops / (blend_ms * 1e-3) / 1e9
     peak_gops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz_peak * 1e6 / 1e9
+    # dram read + write bytes of one ncu-captured launch of this blend kernel in
+    # this configuration ("traffic_bytes_per_launch <tile>x<pix>x<batch> = N" in
+    # a profiles/raster_*_object500k.md summary), or none
     prof_traffic = None
-    pf = os.path.join(ROOT, "profiles", "raster_" + "x".join(map(str, rc["stereo"])) + "_object500k.md")
-    if os.path.exists(pf):  # dram read + write bytes of one ncu-captured launch of this blend kernel
-        for ln in open(pf):
-            if ln.startswith("traffic_bytes_per_launch ="):
-                prof_traffic = int(ln.split("=")[1])
+    key = "traffic_bytes_per_launch " + "x".join(map(str, rc["stereo"])) + " ="
+    pdir = os.path.join(ROOT, "profiles")
+    for name in sorted(os.listdir(pdir)) if os.path.isdir(pdir) else []:
+        if name.startswith("raster_") and name.endswith("_object500k.md"):
+            for ln in open(os.path.join(pdir, name)):
+                if ln.startswith(key):
+                    prof_traffic = int(ln.split("=")[1])
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
