@@ -229,6 +229,39 @@ def test_sorted_instances_bit_exact(gs, orc):
     assert np.all(rg[~nonempty, 0] == rg[~nonempty, 1])
 
 
+@pytest.mark.parametrize("case", ["equal_depth_2049", "one", "three_depths_4097"])
+def test_depth_order_and_instances_with_ties(gs, case):
+    """The depth sort at its edges: every centre at one depth (all keys equal:
+    the order is the surfel index), one surfel, and three depths over a count
+    that leaves one pair in the last 2048-pair sort tile. The depth order is the
+    stable sort by (float32 depth bits, index) of the binned surfels, and the
+    instance list the unique sort by (tile, depth bits, index)."""
+    n, seed = {"equal_depth_2049": (2049, 31), "one": (1, 32), "three_depths_4097": (4097, 33)}[case]
+    scene = synth.random_scene(seed, n, z_range=(2.0, 3.0))
+    if case == "three_depths_4097":
+        scene.pos[:, 2] = np.array([2.0, 2.5, 3.0], np.float32)[np.arange(n) % 3]
+    else:
+        scene.pos[:, 2] = 2.5
+    cam = synth.centred_camera(256, 192, 300.0)
+    ctx = make_ctx(gs, scene, cam, keep_intermediates=True, max_instances=1 << 20)
+    ctx.render_mono(gs.DeviceScene(scene), synth.identity_pose(), cam)
+    ctx.check_ok()
+    counts, _ = ctx.buffer(gs.BUF_COUNTS, torch.int32, None)
+    recs, _ = ctx.buffer(gs.BUF_RECORDS, torch.float32, (-1, 16))
+    order, nv = ctx.buffer(gs.BUF_DEPTH_ORDER, torch.int32, None)
+    keys, nk = ctx.buffer(gs.BUF_INST_KEYS, torch.int32, None)
+    vals, _ = ctx.buffer(gs.BUF_INST_VALS, torch.int32, None)
+    c = counts[:n].cpu().numpy()
+    zbits = recs[:n, 3].contiguous().view(torch.int32).cpu().numpy().astype(np.uint32)
+    binned = np.where(c > 0)[0]
+    assert nv == len(binned) and nv > 0
+    expect = binned[np.lexsort((binned, zbits[binned]))]
+    assert np.array_equal(order[:nv].cpu().numpy(), expect)
+    gk = keys[:nk].cpu().numpy().astype(np.uint32)
+    gv = vals[:nk].cpu().numpy().astype(np.uint32)
+    assert nk > 0 and np.array_equal(np.lexsort((gv, zbits[gv], gk)), np.arange(nk))
+
+
 def test_empty_and_culled_scenes(gs):
     cam = synth.centred_camera(64, 48, 100.0)
     ctx = gs.Context(16, 64, 48, max_instances=1 << 12)
