@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
       if (__syncthreads_count(live == 0u) == NT) break;
       if (b0 + BATCH < rg.y) stage(buf ^ 1, b0 + BATCH);
       const int nb = (int)min((uint32_t)BATCH, rg.y - b0);
+#pragma unroll 4
       for (int j = 0; j < nb && live; ++j) {
         const float4 a = s0[buf][j];
         const float4 b = s1[buf][j];
