@@ -1,8 +1,7 @@
-// The screen-space support of a surfel, shared by the binning (which tiles a
-// surfel reaches) and the rasterizer (which warp regions of a tile it reaches).
-// Both ask the same question - can the support meet a pixel centre inside a
-// rectangle - with the same float32 arithmetic and slack, so a pair one of them
-// rules out never has alpha >= 1/255 in the other.
+// The screen-space support of a surfel (or an ellipsoid, whose record has the
+// same form), as the binning uses it: which tiles of a tile row the support can
+// reach at a pixel centre. The support is grown by a float32 slack, so a pair
+// it rules out never has alpha >= 1/255 in the rasterizer.
 #pragma once
 
 #include "gs_internal.cuh"
