@@ -21,7 +21,9 @@
 // projected centre. The test is exact for the continuous tile rectangle (so it
 // keeps every contributing pair) with the radius grown by 1e-3 for float32
 // safety; the few surfels whose ellipse is too thin and oblique to solve in
-// float32 keep their whole bounding rectangle.
+// float32 keep their whole bounding rectangle. An ellipsoid's record has the
+// same form (its screen conic in place of the plane coefficients) and no
+// low-pass disc.
 //
 // Pipeline per eye (all counts stay on the device):
 //   1. compact the surfels with a non-empty rectangle (reaching an ROI tile when
