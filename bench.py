@@ -84,6 +84,24 @@ def dist_info():
     return ws, rank, local
 
 
+def rank_poses(poses, rank, world):
+    """The frames of one replica: rank r renders poses r, r + N, r + 2N, ...
+    (mod the pose count), so N ranks cover the arc without rendering the same
+    pose at the same step."""
+    n = len(poses)
+    return [poses[(rank + k * world) % n] for k in range(n)]
+
+
+def job_ms_per_frame(ms_per_step, steps, world, reduce_max=None):
+    """Whole-job ms per frame of N replicas: the slowest rank's total time
+    (reduce_max: the max over ranks of a float, e.g. an all-reduce) over the
+    frames all ranks rendered."""
+    total = ms_per_step * steps
+    if world > 1:
+        total = reduce_max(total)
+    return total / (steps * world)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -297,8 +315,7 @@ def run_ours(args):
 
     scene, cam, _, _ = synth.workload_object(n=args.n)
     poses = [synth.eye_pair(p) for p in synth.arc_poses()]
-    # replicas: rank r renders poses r, r + N, ... (independent frames)
-    poses = poses[rank % len(poses):] + poses[: rank % len(poses)]
+    poses = rank_poses(poses, rank, ws_)  # replicas: independent frames
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     # a profiler run keeps the device footprint small (its passes save and
@@ -434,12 +451,13 @@ def run_ours(args):
     e2e_ms = float(np.mean(e2e_t))
 
     # replicas: whole-job ms per frame = max rank time / frames of all ranks
-    ms_job = ms_stereo
-    if ws_ > 1:
+    def all_reduce_max(x):
         import torch.distributed as dist
-        t = torch.tensor([ms_stereo * args.steps], device=dev)
+        t = torch.tensor([x], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_job = t.item() / (args.steps * ws_)
+        return t.item()
+
+    ms_job = job_ms_per_frame(ms_stereo, args.steps, ws_, all_reduce_max)
 
     # temporal reuse of the depth range along the arc (depth_mode 2)
     roi_reuse = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1, depth_mode=2)
