@@ -145,9 +145,10 @@ def sigmoid(x):
     return 1.0 / (1.0 + np.exp(-x))
 
 
-def loss(out, target, hole, label, lam=0.1, tile=TILE, base=None):
+def loss(out, target, hole, label, lam=1.0, tile=TILE, base=None):
     """L1 of the fill (base + out[:3], base = features 0-2) on hole pixels +
-    lam * gate BCE; returns (L, dL/dout)."""
+    lam * gate BCE (lam = 1, the weight the training uses); returns (L,
+    dL/dout)."""
     hole = np.asarray(hole, bool)
     nh = max(int(hole.sum()), 1)
     fill = out[:3] if base is None else np.asarray(base, np.float64) + out[:3]

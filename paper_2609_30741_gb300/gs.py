@@ -645,19 +645,48 @@ def tune_cache_get(key):
     return rc.astuple(), float(ms.value)
 
 
+def check_warp_noalloc_args(cam, device, rgb_dom, depth_dom, trans_dom, rgb_warp, depth_warp=None, hole=None):
+    """Argument checks of warp_noalloc, before anything reaches the device: every
+    tensor contiguous, on `device`, of the dtype and element count the C entry
+    point reads or writes for a cam.height x cam.width frame (rgb 3*H*W float32,
+    depth and transmittance H*W float32, hole H*W uint8). The C entry point
+    takes plain pointers and cannot see a short buffer, so a mis-sized output
+    would be written out of bounds. Raises ValueError."""
+    npix = int(cam.width) * int(cam.height)
+    spec = (("rgb_dom", rgb_dom, torch.float32, 3), ("depth_dom", depth_dom, torch.float32, 1),
+            ("trans_dom", trans_dom, torch.float32, 1), ("rgb_warp", rgb_warp, torch.float32, 3),
+            ("depth_warp", depth_warp, torch.float32, 1), ("hole", hole, torch.uint8, 1))
+    for name, t, dtype, planes in spec:
+        if t is None:
+            if name in ("depth_warp", "hole"):
+                continue
+            raise ValueError(f"warp_noalloc: {name} is required")
+        if not isinstance(t, torch.Tensor) or not t.is_contiguous():
+            raise ValueError(f"warp_noalloc: {name} must be a contiguous tensor")
+        if t.device != torch.device(device):
+            raise ValueError(f"warp_noalloc: {name} is on {t.device}, expected {device}")
+        if t.dtype != dtype:
+            raise ValueError(f"warp_noalloc: {name} is {t.dtype}, expected {dtype}")
+        if t.numel() != planes * npix:
+            raise ValueError(f"warp_noalloc: {name} has {t.numel()} elements, expected {planes} x {cam.height} x "
+                             f"{cam.width} = {planes * npix}")
+
+
 def warp_noalloc(rgb_dom, depth_dom, trans_dom, pose_dom, pose_aff, cam, rgb_warp, depth_warp=None, hole=None,
                  stream=None):
     """Depth-tested forward warp of a dominant-eye render into the affiliated eye
     through gs_warp_noalloc, which allocates no device memory (for callers inside
     a host application that owns the GPU memory pool). All tensors are caller-
-    owned CUDA tensors: rgb_dom (3, H, W), depth_dom and trans_dom (H, W) float32
-    in; rgb_warp (3, H, W) float32, optional depth_warp (H, W) float32 and hole
-    (H, W) uint8 out. Calls that overlap on the GPU share one static scratch
-    array and race: serialise them."""
-    for t in (rgb_dom, depth_dom, trans_dom, rgb_warp, depth_warp, hole):
-        if t is not None and (not t.is_cuda or not t.is_contiguous()):
-            raise ValueError("warp_noalloc takes contiguous CUDA tensors")
-    st = stream if stream is not None else torch.cuda.current_stream(rgb_dom.device)
+    owned CUDA tensors on the current device: rgb_dom (3, H, W), depth_dom and
+    trans_dom (H, W) float32 in; rgb_warp (3, H, W) float32, optional depth_warp
+    (H, W) float32 and hole (H, W) uint8 out (checked by check_warp_noalloc_args).
+    Calls that overlap on the GPU share one static scratch array and race:
+    serialise them."""
+    if not isinstance(rgb_dom, torch.Tensor) or not rgb_dom.is_cuda:
+        raise ValueError("warp_noalloc takes CUDA tensors")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    check_warp_noalloc_args(cam, dev, rgb_dom, depth_dom, trans_dom, rgb_warp, depth_warp, hole)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
     _check(lib().gs_warp_noalloc(_ptr(rgb_dom), _ptr(depth_dom), _ptr(trans_dom), C.byref(pose_struct(pose_dom)),
                                  C.byref(pose_struct(pose_aff)), C.byref(intr_struct(cam)), _ptr(rgb_warp),
                                  _ptr(depth_warp), _ptr(hole), C.c_void_p(st.cuda_stream)),

@@ -78,3 +78,34 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "oracle.h" not in txt, f
+
+
+def test_warp_noalloc_rejects_mis_sized_tensors_before_any_launch():
+    """gs_warp_noalloc takes plain pointers, so the binding checks element counts,
+    dtypes and devices first: a short, mistyped or misplaced tensor raises
+    ValueError and nothing reaches the device (CPU tensors stand in here)."""
+    import torch
+    from paper_2609_30741_gb300 import gs, synth
+    cam = synth.centred_camera(40, 24, 50.0)
+    H, W = cam.height, cam.width
+    cpu = torch.device("cpu")
+    rgb, plane = torch.zeros(3, H, W), torch.zeros(H, W)
+    hole = torch.zeros(H, W, dtype=torch.uint8)
+    gs.check_warp_noalloc_args(cam, cpu, rgb, plane, plane, rgb.clone(), plane.clone(), hole)  # well-formed
+    bad = [
+        dict(rgb_warp=torch.zeros(3, H, W - 1)),                # one column short
+        dict(depth_warp=torch.zeros(H * W + 1)),                # one element long
+        dict(hole=torch.zeros(H, W, dtype=torch.int32)),        # wrong dtype
+        dict(trans_dom=torch.zeros(H, W, dtype=torch.float64)),
+        dict(rgb_dom=torch.zeros(3, W, H).transpose(1, 2)),     # not contiguous
+        dict(depth_dom=torch.zeros(H, W, device="meta")),       # another device
+        dict(rgb_warp=None),                                    # a required output missing
+    ]
+    for change in bad:
+        args = dict(rgb_dom=rgb, depth_dom=plane, trans_dom=plane, rgb_warp=rgb.clone(), depth_warp=plane.clone(),
+                    hole=hole)
+        args.update(change)
+        with pytest.raises(ValueError):
+            gs.check_warp_noalloc_args(cam, cpu, **args)
+    with pytest.raises(ValueError):
+        gs.warp_noalloc(rgb, plane, plane, *synth.eye_pair(synth.identity_pose()), cam, rgb.clone())

@@ -306,6 +306,22 @@ def test_bad_arguments_are_rejected(gs):
 # ----------------------------------------------------------------------------- Stages 2-4
 
 
+def _stage_snapshot(gs, ctx, out, cam):
+    """The GPU's Stage 2-4 intermediates after a stereo call: packed warp keys,
+    edge strips, measured depth range, ROI tile mask and warped depth."""
+    npix = cam.width * cam.height
+    warp, _ = ctx.buffer(gs.BUF_WARP, torch.int64, None)
+    strips, _ = ctx.buffer(gs.BUF_STRIPS, torch.int32, (4, 4))
+    drange, _ = ctx.buffer(gs.BUF_DEPTH_RANGE, torch.float32, None)
+    tmask, _ = ctx.buffer(gs.BUF_TILE_MASK, torch.uint8, None)
+    wd, _ = ctx.buffer(gs.BUF_WARP_DEPTH, torch.float32, None)
+    return dict(out={k: v.clone() for k, v in out.items()},
+                warp=warp[:npix].clone().cpu().numpy().view(np.uint64).reshape(cam.height, cam.width),
+                strips=strips.cpu().numpy().copy(), drange=drange[:2].cpu().numpy().copy(),
+                tmask=tmask[: ((cam.width + 15) // 16) * ((cam.height + 15) // 16)].cpu().numpy().copy(),
+                warp_depth=wd[:npix].cpu().numpy().reshape(cam.height, cam.width).copy())
+
+
 @pytest.fixture(scope="module")
 def stereo_small(gs):
     scene, cam, dom, aff = synth.workload_small()
@@ -313,18 +329,24 @@ def stereo_small(gs):
     ds = gs.DeviceScene(scene)
     out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
     ctx.check_ok()
-    warp, _ = ctx.buffer(gs.BUF_WARP, torch.int64, None)
-    npix = cam.width * cam.height
-    strips, _ = ctx.buffer(gs.BUF_STRIPS, torch.int32, (4, 4))
-    drange, _ = ctx.buffer(gs.BUF_DEPTH_RANGE, torch.float32, None)
-    tmask, _ = ctx.buffer(gs.BUF_TILE_MASK, torch.uint8, None)
-    wd, _ = ctx.buffer(gs.BUF_WARP_DEPTH, torch.float32, None)
-    snap = dict(out={k: v.clone() for k, v in out.items()},
-                warp=warp[:npix].clone().cpu().numpy().view(np.uint64).reshape(cam.height, cam.width),
-                strips=strips.cpu().numpy().copy(), drange=drange[:2].cpu().numpy().copy(),
-                tmask=tmask[: ((cam.width + 15) // 16) * ((cam.height + 15) // 16)].cpu().numpy().copy(),
-                warp_depth=wd[:npix].cpu().numpy().reshape(cam.height, cam.width).copy())
-    return dict(scene=scene, cam=cam, dom=dom, aff=aff, ctx=ctx, ds=ds, **snap)
+    return dict(scene=scene, cam=cam, dom=dom, aff=aff, ctx=ctx, ds=ds, **_stage_snapshot(gs, ctx, out, cam))
+
+
+@pytest.fixture(scope="module")
+def stereo_object(gs):
+    """The 500k-surfel object workload at 1600x1200 (first arc pose) in the
+    rasterizer configuration the bench times (32-pixel tiles, 2 pixels per
+    thread, 256 records per stage)."""
+    scene, cam, dom, aff = synth.workload_object()
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 26)
+    ctx.set_raster(32, 2, 256)
+    ds = gs.DeviceScene(scene)
+    out = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
+    ctx.check_ok()
+    return dict(scene=scene, cam=cam, dom=dom, aff=aff, ctx=ctx, ds=ds, **_stage_snapshot(gs, ctx, out, cam))
+
+
+STAGE_CASES = ["stereo_small", "stereo_object"]
 
 
 def test_stereo_dominant_eye_matches_oracle(stereo_small, orc):
@@ -334,35 +356,42 @@ def test_stereo_dominant_eye_matches_oracle(stereo_small, orc):
     compare_render(_np(o["rgb_dom"]), _np(o["depth_dom"]), _np(o["trans_dom"]), o_rgb, o_dep, o_tr, mrg, "dom")
 
 
-def test_warp_matches_oracle_on_gpu_depth(stereo_small, orc):
+def _warp_marginal(w, W, H):
+    """Destinations touched (3x3 neighbourhood) by a source within 1e-4 px of a
+    rounding boundary, or holding near-equal (<= 4 ulp) depth keys."""
+    marg = np.zeros((H, W), bool)
+    tg, tm, zk = w["tgt"], w["tmargin"], w["zkey"]
+    bad = np.where((tg >= 0) & (tm < 1e-4))[0]
+    bx, by = tg[bad] % W, tg[bad] // W
+    for dx in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            xx, yy = bx + dx, by + dy
+            inb = (xx >= 0) & (xx < W) & (yy >= 0) & (yy < H)
+            marg[yy[inb], xx[inb]] = True
+    zbits = zk.view(np.uint32).astype(np.int64)
+    order = np.lexsort((zbits, tg))
+    tg_s, zb_s = tg[order], zbits[order]
+    same = (tg_s[1:] == tg_s[:-1]) & (tg_s[1:] >= 0)
+    near = same & (np.abs(zb_s[1:] - zb_s[:-1]) <= 4)
+    t = tg_s[1:][near]
+    marg[t // W, t % W] = True
+    return marg
+
+
+@pytest.mark.parametrize("case", STAGE_CASES)
+def test_warp_matches_oracle_on_gpu_depth(case, request, orc):
     """The oracle warp fed the GPU's dominant RGB, depth proxy and transmittance
     gives the same winner at every destination pixel whose sources are not within
     1e-4 px of a rounding boundary and whose depth keys are not within 4 ulp."""
-    s = stereo_small
+    s = request.getfixturevalue(case)
     cam, o = s["cam"], s["out"]
     W, H = cam.width, cam.height
     w = orc.warp(cam, s["dom"], s["aff"], _np(o["rgb_dom"]), _np(o["depth_dom"]), _np(o["trans_dom"]))
     g = s["warp"]
     g_hole = g == np.uint64(0xFFFFFFFFFFFFFFFF)
     g_src = np.where(g_hole, -1, (g & np.uint64(0xFFFFFFFF)).astype(np.int64))
-    # destinations touched by a marginal source, or with a near-tie in depth
-    marg = np.zeros(W * H, bool)
-    tg, tm, zk = w["tgt"], w["tmargin"], w["zkey"]
-    bad_src = (tg >= 0) & (tm < 1e-4)
-    for sidx in np.where(bad_src)[0]:
-        x, y = sidx % W, sidx // W
-        for dx in (-1, 0, 1):
-            for dy in (-1, 0, 1):
-                xx, yy = int(tg[sidx] % W) + dx, int(tg[sidx] // W) + dy
-                if 0 <= xx < W and 0 <= yy < H:
-                    marg[yy * W + xx] = True
-    zbits = zk.view(np.uint32).astype(np.int64)
-    order = np.lexsort((zbits, tg))
-    tg_s, zb_s = tg[order], zbits[order]
-    same = (tg_s[1:] == tg_s[:-1]) & (tg_s[1:] >= 0)
-    near = same & (np.abs(zb_s[1:] - zb_s[:-1]) <= 4)
-    marg[tg_s[1:][near]] = True
-    marg = marg.reshape(H, W)
+    marg = _warp_marginal(w, W, H)
+    print({"case": case, "marginal_share": float(marg.mean())})
     assert marg.mean() < 0.01
     ok = ~marg
     assert np.array_equal(g_hole[ok], w["hole"].astype(bool)[ok])
@@ -375,8 +404,9 @@ def test_warp_matches_oracle_on_gpu_depth(stereo_small, orc):
     assert np.array_equal(np.isinf(wz[valid]), np.isinf(w["zdst"][valid]))
 
 
-def test_edge_roi_bit_exact_given_depth_range(stereo_small, orc):
-    s = stereo_small
+@pytest.mark.parametrize("case", STAGE_CASES)
+def test_edge_roi_bit_exact_given_depth_range(case, request, orc):
+    s = request.getfixturevalue(case)
     cam = s["cam"]
     dmin, dmax = float(s["drange"][0]), float(s["drange"][1])
     o = s["out"]
@@ -388,8 +418,9 @@ def test_edge_roi_bit_exact_given_depth_range(stereo_small, orc):
     assert np.array_equal(strips, s["strips"])
 
 
-def test_classification_bit_exact_given_warp(stereo_small, orc):
-    s = stereo_small
+@pytest.mark.parametrize("case", STAGE_CASES)
+def test_classification_bit_exact_given_warp(case, request, orc):
+    s = request.getfixturevalue(case)
     cam, o = s["cam"], s["out"]
     g = s["warp"]
     hole = (g == np.uint64(0xFFFFFFFFFFFFFFFF)).astype(np.uint8)
@@ -406,8 +437,9 @@ def test_classification_bit_exact_given_warp(stereo_small, orc):
     assert (cls & 2).any() and (cls & 4).any()
 
 
-def test_centre_rois_bit_exact_given_classes(stereo_small, orc):
-    s = stereo_small
+@pytest.mark.parametrize("case", STAGE_CASES)
+def test_centre_rois_bit_exact_given_classes(case, request, orc):
+    s = request.getfixturevalue(case)
     o = s["out"]
     g_cls = o["cls_aff"].cpu().numpy()
     rects, n = orc.center_rois(g_cls & 15, m=32, tile=16)
@@ -448,18 +480,83 @@ def test_roi_render_matches_oracle(stereo_small, orc):
     assert err <= RGB_TOL
 
 
-def test_stereo_end_to_end_against_oracle(stereo_small, orc):
-    """Whole method vs the oracle's own pipeline: images agree within tolerance on
-    every pixel whose class (and tile) agrees; almost all pixels agree."""
+def _nearest_valid(valid, axis):
+    """Index of the nearest valid pixel before (lo) and after (hi) every pixel
+    along an axis (-1 / L when there is none)."""
+    v = valid if axis == 1 else valid.T
+    L = v.shape[1]
+    idx = np.broadcast_to(np.arange(L), v.shape)
+    lo = np.maximum.accumulate(np.where(v, idx, -1), axis=1)
+    hi = np.minimum.accumulate(np.where(v, idx, L)[:, ::-1], axis=1)[:, ::-1]
+    return (lo, hi) if axis == 1 else (lo.T, hi.T)
+
+
+def trusted_pixels(g_cls, ref_cls, g_src, o_src, dom_margin, aff_margin, gap_thresh):
+    """Affiliated-eye pixels whose value both pipelines derive from the same
+    inputs, so that they must agree within the image tolerance:
+    - the class agrees;
+    - a re-rendered pixel has no blend decision within MARGIN of a threshold in
+      the oracle's full render of the affiliated eye;
+    - a warped pixel has the same winner (source pixel) on both sides, and that
+      source pixel has no marginal blend decision in the dominant render;
+    - a filled hole pixel (gap interpolation, or the row/column fill with the
+      centre step off) has a trusted warped pixel or an agreeing hole at each of
+      the nearest non-hole pixels along its row and column, the only pixels the
+      fill reads."""
+    H, W = g_cls.shape
+    hole = g_src < 0
+    src_ok = (dom_margin.ravel() >= MARGIN)[np.maximum(g_src, 0)]
+    tw = (g_src == o_src) & (hole | src_ok)
+    ok = g_cls == ref_cls
+    rend = (g_cls & 16) > 0
+    ok &= ~rend | (aff_margin >= MARGIN)
+    ok &= rend | hole | tw
+    ends_ok = np.ones((H, W), bool)
+    ys, xs = np.mgrid[0:H, 0:W]
+    for axis in (0, 1):
+        lo, hi = _nearest_valid(~hole, axis)
+        for e in (lo, hi):
+            L = W if axis == 1 else H
+            has = (e >= 0) & (e < L)
+            ec = np.clip(e, 0, L - 1)
+            t = tw[ys, ec] if axis == 1 else tw[ec, xs]
+            ends_ok &= ~has | t
+    ok &= rend | ~hole | (tw & ends_ok)
+    return ok
+
+
+def _end_to_end(gs, orc, s, ctx, out, enable_center):
+    cam = s["cam"]
+    W, H = cam.width, cam.height
+    ref = orc.stereo(s["scene"], s["dom"], s["aff"], cam, gap_thresh=2, enable_center=enable_center)
+    o_rgb, o_dep, o_tr, dmrg, _ = orc.render(s["scene"], s["dom"], cam)
+    w = orc.warp(cam, s["dom"], s["aff"], o_rgb, o_dep, o_tr)
+    _, _, _, amrg, _ = orc.render(s["scene"], s["aff"], cam)
+    warp, _ = ctx.buffer(gs.BUF_WARP, torch.int64, None)
+    g = warp[: W * H].cpu().numpy().view(np.uint64).reshape(H, W)
+    g_hole = g == np.uint64(0xFFFFFFFFFFFFFFFF)
+    g_src = np.where(g_hole, -1, (g & np.uint64(0xFFFFFFFF)).astype(np.int64))
+    g_cls = out["cls_aff"].cpu().numpy()
+    assert (g_cls == ref["cls"]).mean() > 0.99
+    ok = trusted_pixels(g_cls, ref["cls"], g_src, w["winner"], dmrg, amrg, 2)
+    excluded = 1.0 - ok.mean()
+    err_map = np.abs(_np(out["rgb_aff"]) - ref["rgb_aff"]).max(0)
+    err = err_map[ok].max()
+    print({"enable_center": enable_center, "excluded_share": float(excluded), "max_abs": float(err),
+           "max_abs_untrusted": float(err_map[~ok].max(initial=0.0))})
+    assert excluded <= 0.01
+    assert err <= RGB_TOL
+    return ref
+
+
+def test_stereo_end_to_end_against_oracle(gs, stereo_small, orc):
+    """Whole method vs the oracle's own pipeline (each side renders its own
+    dominant eye): max-abs error within the image tolerance on every pixel that
+    both sides derive from the same inputs (trusted_pixels); the excluded share
+    is bounded."""
     s = stereo_small
-    ref = orc.stereo(s["scene"], s["dom"], s["aff"], s["cam"], gap_thresh=2)
-    o = s["out"]
-    g_cls = o["cls_aff"].cpu().numpy()
-    same = g_cls == ref["cls"]
-    assert same.mean() > 0.99
-    assert np.array_equal(ref["widths"], o["edge_widths"].cpu().numpy())
-    err = np.abs(_np(o["rgb_aff"]) - ref["rgb_aff"])[:, same]
-    assert np.quantile(err, 0.999) <= RGB_TOL
+    ref = _end_to_end(gs, orc, s, s["ctx"], s["out"], 1)
+    assert np.array_equal(ref["widths"], s["out"]["edge_widths"].cpu().numpy())
 
 
 def test_identity_pose_stereo_is_identity(gs):
@@ -477,12 +574,7 @@ def test_centre_step_off_fills_every_hole(gs, orc, stereo_small):
     ctx = make_ctx(gs, s["scene"], s["cam"])
     out = ctx.render_stereo(s["ds"], s["dom"], s["aff"], s["cam"], roi=gs.roi_params(enable_center=0))
     ctx.check_ok()
-    ref = orc.stereo(s["scene"], s["dom"], s["aff"], s["cam"], enable_center=0)
-    g_cls = out["cls_aff"].cpu().numpy()
-    same = g_cls == ref["cls"]
-    assert same.mean() > 0.99
-    err = np.abs(_np(out["rgb_aff"]) - ref["rgb_aff"])[:, same]
-    assert np.quantile(err, 0.999) <= RGB_TOL
+    _end_to_end(gs, orc, s, ctx, out, 0)
 
 
 # ----------------------------------------------------------------------------- full size

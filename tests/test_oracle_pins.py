@@ -704,3 +704,62 @@ def test_ellipsoid_weights_and_transmittance_sum_to_one(orc):
     rgb, _, tr, _, _ = orc.render(scene, synth.identity_pose(), cam)
     np.testing.assert_allclose(rgb[0] + tr, 1.0, atol=1e-12)
     assert (tr < 0.999).mean() > 0.3
+
+
+def _brute_support_pairs(orc, scene, pose, cam, tile):
+    """Every (surfel, tile) pair found by evaluating each visible surfel at every
+    pixel centre of the whole image (no box, no early exit): the pair is kept when
+    some pixel of the tile has min(0.99, o G) >= 1/255 (the skip rule of Stage 1)."""
+    sp = orc.prepare(scene, pose, cam)
+    ntx = (cam.width + tile - 1) // tile
+    pairs = []
+    for i in range(scene.n):
+        s = sp[i]
+        if not s.visible:
+            continue
+        hit = set()
+        for y in range(cam.height):
+            for x in range(cam.width):
+                oG = orc.eval_pair(s, cam, float(x), float(y))[0]
+                if min(oG, 0.99) >= 1 / 255:
+                    hit.add((y // tile) * ntx + x // tile)
+        pairs += [(i, t) for t in sorted(hit)]
+    return pairs
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_support_pairs_match_whole_image_sweep(orc, tile):
+    """or_support_pairs (which sweeps only each surfel's support box) against a
+    sweep of or_eval over every pixel of the image, on a ragged image (37 x 29:
+    neither side a multiple of the tile) with surfels whose boxes cross the
+    left, right, top and bottom borders and corners, and under a tilted pose."""
+    cam = synth.centred_camera(37, 29, 40.0)
+    base = synth.random_scene(21, 10, z_range=(1.0, 2.5), scale_mu=math.log(0.15), scale_sigma=0.4)
+    # surfels centred on or beyond the borders (x, y in camera units at z = 1.5:
+    # the half field of view is 18 px / 40 * 1.5 = 0.675 m across, 0.525 m down)
+    edge = []
+    for k, (px, py) in enumerate([(-0.68, 0.0), (0.70, 0.1), (0.0, -0.55), (0.1, 0.56), (-0.7, -0.55),
+                                  (0.66, 0.52), (-0.75, 0.3), (0.2, 0.6)]):
+        q = np.array([1.0, 0.3 * (k % 3), -0.2 * (k % 2), 0.1 * k])
+        edge.append(_one_surfel((px, py, 1.5), q / np.linalg.norm(q), (0.12, 0.08), 0.9, (0.0, 0.0, 0.0)))
+    # small surfels centred one to three pixels outside a border (or on a tile
+    # boundary), whose support reaches only the first or last pixel row or column
+    # of the tiles it touches
+    z, f = 1.5, 40.0
+    for k, (u, v) in enumerate([(-2.0, 14.0), (38.5, 9.0), (20.0, -1.6), (11.0, 30.2), (-1.5, -1.5),
+                                (39.0, 30.5), (7.5, 5.0), (15.5, 23.5), (24.0, 7.6)]):
+        s = 0.02 + 0.006 * (k % 3)
+        edge.append(_one_surfel(((u - cam.cx) * z / f, (v - cam.cy) * z / f, z), (1, 0, 0, 0), (s, s), 0.95,
+                                (0.0, 0.0, 0.0)))
+    sc = synth.concat(base, *edge)
+    for pose in (synth.identity_pose(), synth.look_at((0.05, -0.03, -0.1), (0.02, 0.01, 1.8))):
+        ids, tiles = orc.support_pairs(sc, pose, cam, tile=tile)
+        got = list(zip(ids.tolist(), tiles.tolist()))
+        want = _brute_support_pairs(orc, sc, pose, cam, tile)
+        assert got == want
+        # the scene does reach every border, and the ragged last column and row
+        ntx, nty = (37 + tile - 1) // tile, (29 + tile - 1) // tile
+        hit_tiles = {t for _, t in want}
+        assert any(t % ntx == ntx - 1 for t in hit_tiles) and any(t // ntx == nty - 1 for t in hit_tiles)
+        assert any(t % ntx == 0 for t in hit_tiles) and any(t // ntx == 0 for t in hit_tiles)
+        assert len(want) > 30

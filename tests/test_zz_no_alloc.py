@@ -77,7 +77,9 @@ def test_noalloc_warp_matches_stereo_warp_two_calls(gs):
 def test_noalloc_warp_rejects_frames_above_its_scratch(gs):
     cam = synth.centred_camera(2049, 2048, 1000.0)
     dom, aff = synth.eye_pair(synth.identity_pose())
-    small = torch.zeros(4, device="cuda")
+    H, W = cam.height, cam.width
+    rgb = torch.zeros(3, H, W, device="cuda")
+    plane = torch.zeros(H, W, device="cuda")
     with pytest.raises(gs.GsError) as e:
-        gs.warp_noalloc(small, small, small, dom, aff, cam, small)
+        gs.warp_noalloc(rgb, plane, plane, dom, aff, cam, rgb)
     assert e.value.status == gs.GS_ERR_CAPACITY
