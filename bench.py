@@ -35,7 +35,29 @@ WORKLOAD = "object-centric 500k surfels (450k Gaussian cluster + 50k ground plan
 # 10 log10(1 + MSE/s^2) <= 1.3  <=>  PSNR_vs_full >= 28.83 - 10 log10(10^0.13 - 1)
 PSNR_FLOOR_DTU = 28.83
 PSNR_GATE = PSNR_FLOOR_DTU - 10 * math.log10(10 ** 0.13 - 1)
-# FP32 lane operations the rasterizer spends per evaluated (pixel, surfel) pair:
+# Mip-NeRF 360 two-pass PSNR (Table 2): the floor of the unbounded workloads
+PSNR_FLOOR_MIP = 26.14
+PSNR_GATE_MIP = PSNR_FLOOR_MIP - 10 * math.log10(10 ** 0.13 - 1)
+# Algorithmic work per unit of each kernel class of the hot path (the roofline
+# denominators' numerators):
+# - blend: about 40 FP32 instructions and 2 MUFU (ex2, rcp) per evaluated
+#   (pixel, surfel) pair, counted against the FP32 lane rate;
+# - preprocess: 232 B of SH3 attributes read, two 64 B blend records and 8 B of
+#   tile counts written per surfel;
+# - binning: 12 B emitted, 6 sort passes of 24 B and 8 B of histogram per
+#   (surfel, tile) instance (the duplicate-and-sort binning of the tile
+#   rasterizer; the counting sort here moves fewer bytes than that);
+# - warp + classification: 84 B per pixel (read 20, clear 8, atomic 8, resolve
+#   8 + 20 gather + 20 write);
+# - repair network: 79,488 FLOP per pixel over each candidate tile and its
+#   6-pixel halo (28 x 28 positions).
+OPS_PER_PAIR = 42
+PREPROCESS_BYTES_PER_SURFEL = 232 + 2 * 64 + 8
+BIN_BYTES_PER_INSTANCE = 12 + 6 * 24 + 8
+WARP_BYTES_PER_PIXEL = 84
+REPAIR_FLOP_PER_PIXEL = 79488
+REPAIR_WINDOW_PX = 28 * 28
+# The rasterizer's own instruction count (for comparison): per evaluated pair
 # the row offset and the three plane-point FMAs (4), reciprocal, u and v (3),
 # rho3 (2), rho2 (2), min and the threshold compare (2) = 13, the live-bit test
 # (3) and a 1/pix share of the per-surfel column set-up (dx, its three plane
@@ -43,7 +65,9 @@ PSNR_GATE = PSNR_FLOOR_DTU - 10 * math.log10(10 ** 0.13 - 1)
 # pair: exponent fma, ex2, alpha clamp, T update, stop compare, depth (2 fma +
 # select), weight, RGB and depth accumulation (4) = 12.
 OPS_EVAL_PIXEL, OPS_EVAL_COLUMN, OPS_CONTRIB = 16, 5, 12
-SM_COUNT, FP32_LANES_PER_SM = 152, 128
+FP32_LANES_PER_SM = 128
+# the oracle's bounded sample: a centred window of the dominant eye
+ORACLE_WINDOW = (640, 480)
 
 
 def parse():
@@ -223,72 +247,89 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- oracle arm
 
 
-def oracle_sample(scene, cam, pose, k, seconds=10.0):
-    """One bounded oracle sample: the per-pixel render of a window of the
-    dominant eye (sized from a 48x48 probe so that the sample takes about
-    `seconds` of host time, up to the whole frame) plus the fixed per-frame
-    preparation. Returns (prep, per_px, seconds spent, "w x h")."""
+def oracle_roi_share(scene, cam, dom, aff):
+    """The affiliated eye's re-rendered (ROI) pixel share of the oracle's own
+    pipeline on one pose (gap 2 px, margin 32, 32 samples per edge, centre ROIs
+    on), and the seconds it took."""
     import oracle
-    rng = np.random.default_rng(100 + k)
-    probe = 48
-    x0 = int(rng.integers(cam.width // 4, 3 * cam.width // 4 - probe))
-    y0 = int(rng.integers(cam.height // 4, 3 * cam.height // 4 - probe))
     t0 = time.perf_counter()
-    oracle.render(scene, pose, cam, window=(x0, y0, 4, 4))
-    t_small = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.render(scene, pose, cam, window=(x0, y0, probe, probe))
-    t_probe = time.perf_counter() - t0
-    per_px0 = max(t_probe - t_small, 1e-9) / (probe * probe - 16)
-    area = max(seconds - t_small - t_probe, 0.0) / per_px0
-    h = max(probe, min(int(math.sqrt(area)), cam.height))
-    w = max(probe, min(int(area / h), cam.width))
-    # centred on the frame (the dense part of the object workloads)
+    ref = oracle.stereo(scene, dom, aff, cam, gap_thresh=2, margin=32, nsamples=32, enable_center=1)
+    return float(((ref["cls"] & oracle.CLS_RENDER) > 0).mean()), time.perf_counter() - t0
+
+
+def oracle_leg(n_surfels, steps, warmup, roi_frac=None):
+    """The FP64 oracle's ms per stereo frame on the object workload, from bounded
+    samples: per step, for the arc pose of that step, the per-pixel render of a
+    centred ORACLE_WINDOW window of the dominant eye and the fixed per-frame
+    preparation (every surfel projected, coloured and depth-sorted), measured
+    as the difference of that render and a 4 x 4 one; extrapolated to a stereo
+    frame as two preparations plus the dominant eye's pixels plus the affiliated
+    eye's ROI pixels (the oracle re-renders only those; its reprojection, gap and
+    component stages are per pixel and cheap). roi_frac: the ROI pixel share,
+    else measured by the oracle's own pipeline on the first pose.
+
+    Both arms of the bench call this in a process of its own (the GPU arm spawns
+    one), so that no thread of a CUDA process competes with the oracle's."""
+    import oracle
+    from paper_2609_30741_gb300 import synth
+    scene, cam, _, _ = synth.workload_object(n=n_surfels)
+    poses = [synth.eye_pair(p) for p in synth.arc_poses()]
+    roi_s = 0.0
+    src = "given (measured by the GPU arm over the arc)"
+    if roi_frac is None:
+        roi_frac, roi_s = oracle_roi_share(scene, cam, *poses[0])
+        src = "measured by the oracle's pipeline on the first arc pose"
+    w, h = ORACLE_WINDOW
     x0, y0 = (cam.width - w) // 2, (cam.height - h) // 2
-    t0 = time.perf_counter()
-    oracle.render(scene, pose, cam, window=(x0, y0, w, h))
-    t_big = time.perf_counter() - t0
-    per_px = max(t_big - t_small, 1e-9) / (w * h - 16)
-    prep = max(t_small - 16 * per_px, 0.0)
-    return prep, per_px, t_small + t_probe + t_big, f"{w}x{h}"
+    npix = cam.width * cam.height
+    vals, preps, per_pxs = [], [], []
+    t_all = time.perf_counter()
+    for k in range(warmup + steps):
+        d = poses[k % len(poses)][0]
+        t0 = time.perf_counter()
+        oracle.render(scene, d, cam, window=(x0, y0, 4, 4))
+        t_small = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.render(scene, d, cam, window=(x0, y0, w, h))
+        t_big = time.perf_counter() - t0
+        per_px = max(t_big - t_small, 1e-9) / (w * h - 16)
+        prep = max(t_small - 16 * per_px, 0.0)
+        if k >= warmup:
+            vals.append(1e3 * (2 * prep + per_px * npix * (1.0 + roi_frac)))
+            preps.append(prep)
+            per_pxs.append(per_px)
+    return {"value": float(np.mean(vals)), "values": vals, "cores": oracle.num_threads(),
+            "window": f"{w}x{h}", "roi_frac": roi_frac, "roi_frac_source": src, "roi_seconds": round(roi_s, 1),
+            "prep_s": float(np.mean(preps)), "per_px_us": 1e6 * float(np.mean(per_pxs)),
+            "seconds": round(time.perf_counter() - t_all, 1)}
 
 
-def oracle_frame_ms(prep, per_px, npix, roi_frac):
-    # dominant eye: preparation + every pixel; affiliated eye: preparation + the
-    # ROI pixels (reprojection, gaps and components are per-pixel and cheap)
-    return 1e3 * (2 * prep + per_px * npix * (1.0 + roi_frac))
+def oracle_leg_spawned(n_surfels, steps, warmup, roi_frac):
+    """oracle_leg in a fresh spawned interpreter (no CUDA context, no torch
+    threads)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(1) as pool:
+        return pool.apply(oracle_leg, (n_surfels, steps, warmup, roi_frac))
 
 
 def run_reference(args):
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    import oracle
-    from paper_2609_30741_gb300 import synth
-    scene, cam, dom, aff = synth.workload_object(n=args.n)
-    poses = synth.arc_poses()
-    npix = cam.width * cam.height
-    # ROI pixel share of the affiliated eye on this workload, as the GPU arm measures
-    # it over the eight poses (cls_aff render bit); the oracle arm does not run the
-    # whole pipeline per step, so it takes the measured share
-    roi_frac = 0.18
-    vals = []
-    t_all = 0.0
-    for k in range(args.warmup + args.steps):
-        d, _ = synth.eye_pair(poses[k % len(poses)])
-        prep, per_px, t, win = oracle_sample(scene, cam, d, k, seconds=4.0)
-        t_all += t
-        if k >= args.warmup:
-            vals.append(oracle_frame_ms(prep, per_px, npix, roi_frac))
-    v = float(np.mean(vals))
+    leg = oracle_leg(args.n, args.steps, args.warmup)
+    v = leg["value"]
+    sample = (f"per step: the oracle's render of a centred {leg['window']} dominant-eye window plus the per-frame "
+              f"surfel preparation of that step's arc pose ({leg['per_px_us']:.2f} us per pixel, "
+              f"{leg['prep_s']:.2f} s preparation), extrapolated to a stereo frame: two preparations, the "
+              f"dominant eye's pixels and the ROI share {leg['roi_frac']:.4f} of the "
+              f"affiliated eye ({leg['roi_frac_source']})")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle"},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"per step: oracle render of a {win} dominant-eye window (about 4 s "
-                                       f"of host time) plus the per-frame surfel preparation, extrapolated to both "
-                                       f"eyes (dominant frame + ROI share)"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": leg["cores"], "kind": "oracle", "sample": sample,
+                             "per_step_ms": [round(x, 1) for x in leg["values"]],
+                             "roi_frac": leg["roi_frac"], "roi_seconds": leg["roi_seconds"]},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -300,6 +341,45 @@ def psnr(a, b):
     import torch
     mse = torch.mean((a - b) ** 2).item()
     return 10 * math.log10(1.0 / max(mse, 1e-20))
+
+
+def stats(times):
+    t = np.asarray(times, np.float64)
+    return {"mean": float(t.mean()), "median": float(np.median(t)), "p90": float(np.percentile(t, 90)),
+            "n": int(t.size)}
+
+
+def error_split(gs, ctx, out, out2):
+    """Where the affiliated eye's squared error against the full render sits:
+    shares of the total on warped pixels (and, among them, on pixels whose
+    dominant-eye source was only partly covered, 0.5 <= 1 - T < 0.99: the
+    silhouette fringe of the coverage threshold), on interpolated gaps, on other
+    filled holes and on re-rendered (ROI) pixels (zero by construction)."""
+    import torch
+    e2 = ((out["rgb_aff"] - out2["rgb_aff"]) ** 2).sum(0)
+    c = out["cls_aff"]
+    rend = (c & gs.CLS_RENDER) > 0
+    hole = (c & gs.CLS_HOLE) > 0
+    gap = ((c & gs.CLS_GAP) > 0) & ~rend
+    warped = ~hole & ~rend
+    H, W = e2.shape
+    key, _ = ctx.buffer(gs.BUF_WARP, torch.int64, None)
+    src = (key[: H * W] & 0xFFFFFFFF).view(H, W)
+    cov = 1.0 - out["trans_dom"].reshape(-1)[torch.where(warped, src, torch.zeros_like(src)).reshape(-1)].view(H, W)
+    fringe = warped & (cov < 0.99)
+    tot = max(float(e2.sum()), 1e-30)
+    return {"warped": float(e2[warped].sum()) / tot, "warped_fringe": float(e2[fringe].sum()) / tot,
+            "gap": float(e2[gap].sum()) / tot, "other_hole": float(e2[hole & ~rend & ~gap].sum()) / tot,
+            "roi": float(e2[rend].sum()) / tot,
+            "pixel_share": {"warped": float(warped.float().mean()), "warped_fringe": float(fringe.float().mean()),
+                            "gap": float(gap.float().mean()), "roi": float(rend.float().mean())}}
+
+
+def mean_dicts(ds):
+    out = {}
+    for k, v in ds[0].items():
+        out[k] = mean_dicts([d[k] for d in ds]) if isinstance(v, dict) else float(np.mean([d[k] for d in ds]))
+    return out
 
 
 def run_ours(args):
@@ -318,6 +398,7 @@ def run_ours(args):
     poses = rank_poses(poses, rank, ws_)  # replicas: independent frames
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     # a profiler run keeps the device footprint small (its passes save and
     # restore device memory): 32-pixel tiles at most 2^25 instances per eye
     ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << (25 if args.profile_once else 27),
@@ -343,15 +424,15 @@ def run_ours(args):
                            "default_ms": dict((tuple(c), t) for c, t in res).get((16, 4, 128)),
                            "all_ms": {",".join(map(str, c)): round(t, 4) for c, t in res}}
 
-    def stereo(k):
+    def stereo(k, scn=None):
         ctx.set_raster(*rc["stereo"])
         d, a = poses[k % len(poses)]
-        ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+        ctx.render_stereo(scn or ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
 
-    def two_pass(k):
+    def two_pass(k, scn=None):
         ctx.set_raster(*rc["two_pass"])
         d, a = poses[k % len(poses)]
-        ctx.render_two_pass(ds, d, a, cam, out=out2)
+        ctx.render_two_pass(scn or ds, d, a, cam, out=out2)
 
     if args.profile_once:
         for k in range(2):
@@ -362,20 +443,27 @@ def run_ours(args):
         print(json.dumps({"profile_once": "ok", "launches_per_stereo_and_two_pass": gs.kernel_launches() // 2}))
         return
 
-    # quality and work counts (untimed): every pose once
+    # quality, error split and work counts (untimed): every pose once
     ctx.set_counting(True)
-    ps, ss, roi_fracs, pairs_eval, pairs_contrib = [], [], [], [], []
+    ps, ss, roi_fracs, pairs_eval, pairs_contrib, splits, use_s, use_t = [], [], [], [], [], [], [], []
     for k in range(len(poses)):
         stereo(k)
         e, c = ctx.pair_counts()
+        use_s.append(ctx.usage())
         pairs_eval.append(e[0])
         pairs_contrib.append(c[0])
-        cls = out["cls_aff"].clone()
+        keep = {"rgb_aff": out["rgb_aff"].clone(), "cls_aff": out["cls_aff"].clone(),
+                "trans_dom": out["trans_dom"].clone()}
+        warp_keys = ctx.buffer(gs.BUF_WARP, torch.int64, None)[0][: cam.width * cam.height].clone()
         two_pass(k)
+        use_t.append(ctx.usage())
         ctx.check_ok()
-        ps.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
-        ss.append(float(ctx.ssim(out["rgb_aff"], out2["rgb_aff"])))
-        roi_fracs.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
+        ps.append(psnr(keep["rgb_aff"], out2["rgb_aff"]))
+        ss.append(float(ctx.ssim(keep["rgb_aff"], out2["rgb_aff"])))
+        roi_fracs.append(((keep["cls_aff"] & gs.CLS_RENDER) > 0).float().mean().item())
+        # the split reads the warp keys from the workspace: put this pose's back
+        ctx.buffer(gs.BUF_WARP, torch.int64, None)[0][: cam.width * cam.height].copy_(warp_keys)
+        splits.append(error_split(gs, ctx, keep, out2))
     ctx.set_counting(False)
 
     def timed(fn, steps, warmup, profile=False):
@@ -424,6 +512,10 @@ def run_ours(args):
     pair.check_ok()
     pair.close()
     del pair, pair_ctx
+    # the timing protocol of the measurement plan: median and p90 of 60
+    # repetitions of each arm (L2 flushed before each)
+    _, t60_s, _ = timed(stereo, 60, 3)
+    _, t60_t, _ = timed(two_pass, 60, 3)
     # per-stage times (events at the stage boundaries; a separate pass)
     _, _, st_stereo = timed(stereo, len(poses), 1, profile=True)
     _, _, st_two = timed(two_pass, len(poses), 1, profile=True)
@@ -474,14 +566,78 @@ def run_ours(args):
         two_pass(k)
         ps_reuse.append(psnr(out["rgb_aff"], out2["rgb_aff"]))
 
+    # view-independent colour: the same geometry and poses with every SH band
+    # above degree 0 zeroed (isolates what reprojection cannot carry)
+    sc0 = synth.Scene(scene.pos, scene.quat, scene.scale, scene.opacity, scene.sh.copy(), scene.sh_degree,
+                      scene.primitive)
+    sc0.sh[:, 1:, :] = 0.0
+    ds0 = gs.DeviceScene(sc0, device=dev)
+    ps0, splits0 = [], []
+    for k in range(len(poses)):
+        stereo(k, ds0)
+        keep = {"rgb_aff": out["rgb_aff"].clone(), "cls_aff": out["cls_aff"].clone(),
+                "trans_dom": out["trans_dom"].clone()}
+        warp_keys = ctx.buffer(gs.BUF_WARP, torch.int64, None)[0][: W * H].clone()
+        two_pass(k, ds0)
+        ctx.check_ok()
+        ps0.append(psnr(keep["rgb_aff"], out2["rgb_aff"]))
+        ctx.buffer(gs.BUF_WARP, torch.int64, None)[0][: W * H].copy_(warp_keys)
+        splits0.append(error_split(gs, ctx, keep, out2))
+    del ds0
+
+    # peak memory per path (Table 2's memory column): the scene, a workspace
+    # sized to what the path used on these frames (instances, spans and list
+    # entries per eye, buffers of other paths left out) and the output images;
+    # each size is verified by rendering every pose in a context of exactly that
+    # size and comparing with the large context's images
+    def caps(us):
+        return [max(max(u["instances"][e], u["spans"][e]) for u in us) for e in (0, 1)]
+
+    cap_s, cap_t = caps(use_s), caps(use_t)
+    ref_imgs = []
+    for k in range(len(poses)):
+        stereo(k)
+        a = out["rgb_aff"].clone()
+        two_pass(k)
+        ref_imgs.append((a, out2["rgb_aff"].clone()))
+    mem = {}
+    for arm, paths, cp in (("stereo", gs.PATH_STEREO, cap_s), ("two_pass", gs.PATH_MONO, cap_t)):
+        mctx = gs.Context(scene.n, W, H, max_instances=cp[0], max_instances_aff=cp[1], device=dev,
+                          min_tile=rc[arm][0], paths=paths)
+        mctx.set_raster(*rc[arm])
+        mo = mctx.alloc_outputs(cam, with_cls=False)
+        same = True
+        for k, (d, a) in enumerate(poses):
+            if arm == "stereo":
+                mctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=mo)
+            else:
+                mctx.render_two_pass(ds, d, a, cam, out=mo)
+            mctx.check_ok()
+            same &= bool(torch.equal(mo["rgb_aff"], ref_imgs[k][0 if arm == "stereo" else 1]))
+        mem[arm] = {"workspace_mb": mctx.workspace.numel() / 2**20, "instance_capacity": cp, "verified": same}
+        del mctx, mo
+    scene_mb = ds.nbytes() / 2**20
+    out_mb = 32 * W * H / 2**20  # rgb_dom, depth_dom, trans_dom, rgb_aff
+    for arm in mem:
+        mem[arm]["peak_mb"] = scene_mb + out_mb + mem[arm]["workspace_mb"]
+    peak_mb = {"stereo": mem["stereo"]["peak_mb"], "two_pass": mem["two_pass"]["peak_mb"],
+               "reduction": 1.0 - mem["stereo"]["peak_mb"] / mem["two_pass"]["peak_mb"],
+               "scene_mb": scene_mb, "outputs_mb": out_mb, "paths": mem,
+               "note": "scene + a workspace sized to the path's measured instances/spans/list entries per eye over "
+                       "the 8 poses with other paths' buffers left out + the four output images; each size "
+                       "verified by rendering all poses in a context of exactly that size"}
+
+    # rooflines: algorithmic work per unit x units / event-timed stage duration
     pk, pk_kind = peaks()
     sm_mhz_peak = float(pk.get("sm_max_mhz", 2070.0))
+    hbm = float(pk["hbm_gbs"])
+    peak_gops = sms * FP32_LANES_PER_SM * sm_mhz_peak * 1e6 / 1e9
     blend_ms = st_stereo[2]
     pix = rc["stereo"][1]
-    ops = (OPS_EVAL_PIXEL + OPS_EVAL_COLUMN / pix) * float(np.mean(pairs_eval)) + \
+    ops = OPS_PER_PAIR * float(np.mean(pairs_eval))
+    own_ops = (OPS_EVAL_PIXEL + OPS_EVAL_COLUMN / pix) * float(np.mean(pairs_eval)) + \
         OPS_CONTRIB * float(np.mean(pairs_contrib))
     achieved = ops / (blend_ms * 1e-3) / 1e9
-    peak_gops = SM_COUNT * FP32_LANES_PER_SM * sm_mhz_peak * 1e6 / 1e9
     # dram read + write bytes of one ncu-captured launch of this blend kernel in
     # this configuration ("traffic_bytes_per_launch <tile>x<pix>x<batch> = N" in
     # a profiles/raster_*_object500k.md summary), or none
@@ -493,23 +649,47 @@ def run_ours(args):
             for ln in open(os.path.join(pdir, name)):
                 if ln.startswith(key):
                     prof_traffic = int(ln.split("=")[1])
+    inst_dom = float(np.mean([u["instances"][0] for u in use_s]))
+
+    def hbm_line(kernel, nbytes, ms, unit_note):
+        a = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "kernel": kernel, "achieved": a, "peak": hbm, "unit": "GB/s", "frac": a / hbm,
+                "bytes": nbytes, "ms": ms, "work": unit_note, "peak_source": f"{pk_kind} copy bandwidth"}
+
+    rooflines = {
+        "blend_dominant": {"bound": "alu", "kernel": "raster_kernel<" + ",".join(map(str, rc["stereo"])) + ">",
+                           "achieved": achieved, "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops,
+                           "ms": blend_ms, "work": f"{OPS_PER_PAIR} ops x {np.mean(pairs_eval):.4g} evaluated pairs",
+                           "own_count_frac": own_ops / (blend_ms * 1e-3) / 1e9 / peak_gops},
+        "preprocess": hbm_line("preprocess_kernel (stage: counters, FP64 set-up, both eyes' records)",
+                               PREPROCESS_BYTES_PER_SURFEL * scene.n, st_stereo[0],
+                               f"{PREPROCESS_BYTES_PER_SURFEL} B x {scene.n} surfels"),
+        "binning_dominant": hbm_line("dominant-eye binning (compaction, row spans, depth sort, band lists, "
+                                     "counting sort by tile)", BIN_BYTES_PER_INSTANCE * inst_dom, st_stereo[1],
+                                     f"{BIN_BYTES_PER_INSTANCE} B x {inst_dom:.4g} instances"),
+        "warp_classify": hbm_line("warp, edge ROIs, gap classification", WARP_BYTES_PER_PIXEL * W * H, st_stereo[3],
+                                  f"{WARP_BYTES_PER_PIXEL} B x {W * H} pixels"),
+    }
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         try:
-            import oracle
-            prep, per_px, t, win = oracle_sample(scene, cam, poses[0][0], 0, seconds=10.0)
-            cpu = {"value": oracle_frame_ms(prep, per_px, W * H, float(np.mean(roi_fracs))), "unit": "ms",
-                   "cores": oracle.num_threads(), "kind": "oracle",
-                   "sample": f"oracle render of a {win} dominant-eye window + per-frame surfel preparation "
-                             f"({t:.1f} s of CPU work), extrapolated to the dominant frame plus the measured "
-                             f"ROI share of the affiliated eye"}
+            leg = oracle_leg_spawned(args.n, 2, 0, float(np.mean(roi_fracs)))
+            cpu = {"value": leg["value"], "unit": "ms", "cores": leg["cores"], "kind": "oracle",
+                   "sample": f"the reference arm's oracle leg in a spawned process: per step the oracle's render "
+                             f"of a centred {leg['window']} dominant-eye window plus the per-frame surfel "
+                             f"preparation ({leg['per_px_us']:.2f} us per pixel, {leg['prep_s']:.2f} s), 2 steps "
+                             f"({leg['seconds']} s), extrapolated to two preparations, the dominant frame and the "
+                             f"measured ROI share of the affiliated eye",
+                   "per_step_ms": [round(x, 1) for x in leg["values"]]}
         except Exception as ex:  # the CPU baseline is reported, not required
             cpu = {"value": None, "unit": "ms", "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
 
     learned, weights = None, None
     if not args.no_learned:
         learned, weights = run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc)
+        rooflines["repair_net"] = learned.pop("roofline")
+        rooflines["repair_net_fp8"] = learned["fp8"].pop("roofline")
     batched = unbounded = hmd = backbone3d = None
     if ws_ == 1:
         del ds, out, out2
@@ -524,6 +704,7 @@ def run_ours(args):
                 hmd = run_hmd(args, dev, flush, w_unb, calib)
             del calib
 
+    split = mean_dicts(splits)
     line = {
         "metric": METRIC, "value": ms_job, "unit": "ms", "n_gpus": ws_, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_stereo, "higher_is_better": False, "scaling": "weak",
@@ -532,16 +713,32 @@ def run_ours(args):
                    "margin": 32, "samples_per_edge": 32, "enable_center": 1, "repair": "plain",
                    "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{ws_}"},
         "two_pass_ms": ms_two, "speedup_vs_two_pass": ms_two / ms_stereo, "fps": 1e3 / ms_job,
+        "ms_stats": {"stereo": stats(t60_s), "two_pass": stats(t60_t),
+                     "speedup_by_median": float(np.median(t60_t) / np.median(t60_s)),
+                     "timed_steps": {"stereo": stats(t_stereo), "two_pass": stats(t_two)},
+                     "note": "60 repetitions per arm after 3 warm-up frames, L2 flushed before each"},
         "two_pass_concurrent_ms": ms_two_conc, "speedup_vs_two_pass_concurrent": ms_two_conc / ms_stereo,
         "depth_reuse": {"ms_per_stereo_frame": ms_reuse, "psnr_aff_vs_full_db": float(np.mean(ps_reuse)),
                         "note": "depth_mode 2: each frame reuses the previous pose's measured depth range; edge "
                                 "strips rendered on a second stream beside the dominant eye"},
-        "psnr_aff_vs_full_db": float(np.mean(ps)), "ssim_aff_vs_full": float(np.mean(ss)),
+        "psnr_aff_vs_full_db": float(np.mean(ps)), "psnr_min_db": float(np.min(ps)),
+        "ssim_aff_vs_full": float(np.mean(ss)),
         "psnr_gate_db": PSNR_GATE,
-        "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
+        "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE),
+        "quality_gate": {"floor": "DTU two-pass PSNR 28.83 dB (Table 2)", "gate_db": PSNR_GATE,
+                         "psnr_min_db": float(np.min(ps)), "pass": bool(np.min(ps) >= PSNR_GATE)},
+        "error_split": split,
+        "sh0_variant": {"psnr_aff_vs_full_db": float(np.mean(ps0)), "psnr_min_db": float(np.min(ps0)),
+                        "quality_gate_pass": bool(np.min(ps0) >= PSNR_GATE), "error_split": mean_dicts(splits0),
+                        "note": "same geometry, opacities and poses with the SH bands above degree 0 zeroed "
+                                "(view-independent colour)"},
+        "roi_pixel_share": float(np.mean(roi_fracs)),
+        "peak_mb": peak_mb,
         "stage_ms_stereo": dict(zip(["preprocess", "bin_dom", "blend_dom", "warp_edge_gaps", "centre_rois",
                                      "bin_roi", "blend_roi", "outputs"], st_stereo)),
         "stage_ms_two_pass": dict(zip(["preprocess", "bin_dom", "blend_dom", "bin_aff", "blend_aff"], st_two)),
+        "usage": {"stereo_instances_per_eye": [float(np.mean([u["instances"][e] for u in use_s])) for e in (0, 1)],
+                  "two_pass_instances_per_eye": [float(np.mean([u["instances"][e] for u in use_t])) for e in (0, 1)]},
         "clocks": clocks,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches_stereo),
@@ -550,8 +747,10 @@ def run_ours(args):
         "roofline": {"bound": "alu", "kernel": "raster_kernel<" + ",".join(map(str, rc["stereo"])) + "> (dominant eye)",
                      "achieved": achieved, "peak": peak_gops,
                      "unit": "Gop/s", "frac": achieved / peak_gops, "traffic": prof_traffic,
-                     "peak_source": f"152 SMs x 128 FP32 lanes x {sm_mhz_peak:.0f} MHz ({pk_kind} max clock)",
-                     "ops_per_launch": ops, "launch_ms": blend_ms},
+                     "peak_source": f"{sms} SMs x 128 FP32 lanes x {sm_mhz_peak:.0f} MHz ({pk_kind} max clock)",
+                     "ops_per_launch": ops, "launch_ms": blend_ms,
+                     "work": f"{OPS_PER_PAIR} ops (40 FP32 + 2 MUFU) per evaluated (pixel, surfel) pair"},
+        "rooflines": rooflines,
         "cpu_baseline": cpu,
         "learned": learned,
         "batched": batched,
@@ -580,6 +779,33 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
     # FP8 scales from the BF16 network over an even sample of the training tiles
     tiles = pairs.tile_tensor()
     ctx.repair_calibrate_fp8(pairs.feat, tiles[::max(1, tiles.numel() // 8192)].contiguous())
+    # the network kernel alone (gs_repair_infer) on 8192 of the training frames'
+    # hole tiles: tensor roofline of the implicit-GEMM convolutions
+    sample = tiles[::max(1, tiles.numel() // 8192)][:8192].contiguous()
+    gate = torch.empty(sample.numel(), dtype=torch.float32, device=dev)
+    pk, pk_kind = peaks()
+
+    def time_net(fp8):
+        for _ in range(3):
+            ctx.repair_infer(pairs.feat, sample, gate=gate, fp8=fp8)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream(dev)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(10):
+            ctx.repair_infer(pairs.feat, sample, gate=gate, fp8=fp8)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / 10
+        flop = REPAIR_FLOP_PER_PIXEL * REPAIR_WINDOW_PX * sample.numel()
+        tf = flop / (ms * 1e-3) / 1e12
+        peak = float(pk["bf16_tflops"]) * (2.0 if fp8 else 1.0)
+        return {"bound": "tensor", "kernel": f"repair_net_kernel<{'FP8' if fp8 else 'BF16'}>", "achieved": tf,
+                "peak": peak, "unit": "TFLOP/s", "frac": tf / peak, "ms": ms, "tiles": int(sample.numel()),
+                "work": f"{REPAIR_FLOP_PER_PIXEL} FLOP x 28x28 positions per tile",
+                "peak_source": f"{pk_kind} bf16 burst" + (" x 2 (nominal e4m3/bf16 ratio)" if fp8 else "")}
+
+    net_rl = {False: time_net(False), True: time_net(True)}
     del tctx, pairs
     torch.cuda.empty_cache()
 
@@ -607,6 +833,7 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
         _, _, st = timed(stereo, len(poses), 1, profile=True)
         st = np.mean(np.array(st), 0).tolist()
         return {"ms_per_stereo_frame": ms, "gate_tau": 0.5, "psnr_aff_vs_full_db": float(np.mean(ps)),
+                "psnr_min_db": float(np.min(ps)),
                 "ssim_aff_vs_full": float(np.mean(ss)),
                 "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
                 "net_filled_pixel_share": float(np.mean(net_fracs)),
@@ -616,6 +843,8 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
 
     res = variant(1)
     res["fp8"] = variant(2)
+    res["roofline"] = net_rl[False]
+    res["fp8"]["roofline"] = net_rl[True]
     res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "batch_tiles": 512,
                        "seconds": round(secs, 2), "setup_seconds": round(time.time() - t0 - secs, 2),
                        "loss_first_last": [hist[0][1], hist[-1][1]],
@@ -791,6 +1020,7 @@ def run_unbounded(args, dev, flush):
 
     res = {"workload": "unbounded 1.5M surfels (1 m ball + 10-30 m shell), SH3, 1920x1080, f=1600, 0.064 m "
                        "baseline, 8 poses on a 30 deg orbit at 3 m",
+           "quality_gate": {"floor": "Mip-NeRF 360 two-pass PSNR 26.14 dB (Table 2)", "gate_db": PSNR_GATE_MIP},
            "raster": {"stereo": list(rc_s), "two_pass": list(rc_t), "chosen_by": "autotuner"},
            "two_pass_ms": run(two, args.steps, args.warmup)}
     for name, roi in rois.items():
@@ -811,6 +1041,7 @@ def run_unbounded(args, dev, flush):
         ctx.check_ok()
         res[name] = {"ms_per_stereo_frame": ms, "speedup_vs_two_pass": res["two_pass_ms"] / ms,
                      "psnr_aff_vs_full_db": float(np.mean(ps)), "psnr_min_db": float(np.min(ps)),
+                     "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE_MIP),
                      "ssim_aff_vs_full": float(np.mean(ss)),
                      "roi_pixel_share": float(np.mean(roi_fr)), "net_filled_pixel_share": float(np.mean(net_fr))}
     res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "seconds": round(train_s, 1),
@@ -960,6 +1191,7 @@ def run_hmd(args, dev, flush, weights, calib):
                        "yaw trajectory at 90 Hz (orbit 3 m)",
            "raster": {"stereo": list(rc_s), "two_pass": list(rc_t), "chosen_by": "autotuner"},
            "two_pass_ms": tp,
+           "quality_gate": {"floor": "Mip-NeRF 360 two-pass PSNR 26.14 dB (Table 2)", "gate_db": PSNR_GATE_MIP},
            "note": "mean over frames 3-119 (the first three frames of each arm warm its graphs)"}
     for m in ("plain", "bf16", "fp8", "reuse"):
         v = float(np.mean(ms[m][3:]))
@@ -967,6 +1199,7 @@ def run_hmd(args, dev, flush, weights, calib):
                   "psnr_aff_vs_full_db": {"mean": float(np.mean(ps[m])), "min": float(np.min(ps[m])),
                                           "max": float(np.max(ps[m]))},
                   "ssim_aff_vs_full": {"mean": float(np.mean(ss[m])), "min": float(np.min(ss[m]))},
+                  "quality_gate_pass": bool(np.min(ps[m]) >= PSNR_GATE_MIP),
                   "psnr_per_frame_db": [round(x, 3) for x in ps[m]]}
     res["fp8_vs_bf16_psnr_gap_db"] = float(np.mean(np.array(ps["fp8"]) - np.array(ps["bf16"])))
     res["reuse"]["note"] = ("depth_mode 2: the previous frame's measured depth range; the edge strips are rendered "

@@ -144,7 +144,38 @@ typedef struct {
                             or 32 (0 = 16); max_width / min_tile <= 512 */
   int host_outputs;      /* 1: the workspace also holds the device images that
                             gs_render_stereo_host renders into (32 B per pixel) */
+  int64_t max_instances_aff; /* (surfel, tile) pairs and (surfel, tile row) spans
+                            of the affiliated eye (0 = max_instances). A context
+                            that serves only gs_render_stereo needs room for the
+                            ROI tiles alone (Stage 4 re-renders only them) */
+  int paths;             /* which entry points the context serves, GS_PATH_* bits
+                            (0 = all); buffers only other paths use are left
+                            out of the workspace, and a call on a path the
+                            context was not sized for returns GS_ERR_BAD_ARG */
 } gs_limits;
+
+/* gs_limits.paths bits. MONO: gs_render_mono and gs_render_two_pass (full
+ * renders of one or both eyes). STEREO: gs_render_stereo(_host) with
+ * depth_mode 0 or 1 and repair_mode 0: the warp, class, component and ROI
+ * buffers (21 B per pixel). REUSE: depth_mode 2 (the affiliated eye's strip
+ * image, 12 B per pixel). REPAIR: the learned repair (repair_mode 1-3, the
+ * gs_repair_* calls): features and fill (28 B per pixel). */
+#define GS_PATH_MONO 1
+#define GS_PATH_STEREO 2
+#define GS_PATH_REUSE 4
+#define GS_PATH_REPAIR 8
+#define GS_PATH_ALL 15
+
+/* Work counts of a context's last call, for sizing a context to a workload:
+ * per eye the binned surfels, the (surfel, tile) instances, the (surfel, tile
+ * row) spans and the (surfel, band of 4 tile rows) list entries the binning
+ * produced (counted also when they overflowed a capacity). */
+typedef struct {
+  int64_t binned[2], instances[2], spans[2], band_entries[2];
+} gs_usage;
+
+/* Synchronises the context's stream and reads the counts of its last call. */
+gs_status gs_context_usage(gs_context *ctx, gs_usage *usage);
 
 /* Bytes of device workspace a context with these limits needs. */
 gs_status gs_workspace_size(const gs_limits *lim, size_t *bytes);

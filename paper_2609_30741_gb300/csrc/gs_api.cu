@@ -48,6 +48,9 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   const size_t rtx = (size_t)((lim.max_width + mts - 1) >> msh), rty = (size_t)((lim.max_height + mts - 1) >> msh);
   const size_t tiles = rtx * rty > roi_tiles ? rtx * rty : roi_tiles;
   const size_t I = (size_t)lim.max_instances;
+  const size_t Ie[2] = {I, lim.max_instances_aff > 0 ? (size_t)lim.max_instances_aff : I};
+  const int paths = lim.paths ? lim.paths : GS_PATH_ALL;
+  const bool stereo = paths & GS_PATH_STEREO, reuse = paths & GS_PATH_REUSE, repair = paths & GS_PATH_REPAIR;
   const size_t table_max = tiles * bin_chunks(lim.max_surfels);
   size_t scan_n = N > P ? N : P;
   if (table_max > scan_n) scan_n = table_max;
@@ -65,7 +68,9 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.bin_nch = bin_chunks(lim.max_surfels);
   const size_t table = tiles * ws.bin_nch;
   ws.cnt_bin = c.take<uint32_t>(lim.keep_intermediates ? N : 1);
-  ws.band_pool_cap = (uint32_t)(8 * N + 1024);
+  // a band-list entry covers at least one span of its surfel, so the spans'
+  // capacity bounds the entries too
+  for (int e = 0; e < 2; ++e) ws.band_pool_cap[e] = (uint32_t)(Ie[e] < 8 * N ? Ie[e] + 1024 : 8 * N + 1024);
   const size_t rs_words = radix_status_words(N);
   for (int e = 0; e < 2; ++e) {  // one binning scratch per eye
     BinScratch &b = ws.bin[e];
@@ -73,10 +78,10 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
       b.dkey[k] = c.take<uint32_t>(N);
       b.dval[k] = c.take<uint32_t>(N);
     }
-    b.ival = c.take<uint32_t>(I);
-    b.ikey = c.take<uint32_t>(lim.keep_intermediates ? I : 1);
+    b.ival = c.take<uint32_t>(Ie[e]);
+    b.ikey = c.take<uint32_t>(lim.keep_intermediates ? Ie[e] : 1);
     b.bin_table = c.take<uint4>(table);
-    b.band_pool = reinterpret_cast<BandEntry *>(c.take<char>(kBandEntryBytes * ws.band_pool_cap));
+    b.band_pool = reinterpret_cast<BandEntry *>(c.take<char>(kBandEntryBytes * ws.band_pool_cap[e]));
     b.band_lists = c.take<uint2>(band_list_words(lim.max_surfels, (int)rty));  // the binning runs on the raster grid
     b.bin_offs = c.take<uint32_t>(table);
     b.ranges = c.take<uint2>(tiles);
@@ -95,16 +100,16 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   }
   ws.tile_mask = c.take<uint8_t>(tiles);
   ws.strip_mask = c.take<uint8_t>(tiles);
-  ws.strip_rgb = c.take<float>(3 * P);
+  ws.strip_rgb = c.take<float>(reuse ? 3 * P : 1);
   for (int e = 0; e < 2; ++e) {
     ws.row_off[e] = c.take<uint32_t>(N);
-    ws.spans[e] = c.take<uint2>(I);
+    ws.spans[e] = c.take<uint2>(Ie[e]);
   }
-  ws.warpbuf = c.take<unsigned long long>(P);
-  ws.warp_depth = c.take<float>(P);
-  ws.cls = c.take<uint8_t>(P);
-  ws.labels = c.take<int32_t>(P);
-  ws.slots = c.take<uint32_t>(P + 1);
+  ws.warpbuf = c.take<unsigned long long>(stereo ? P : 1);
+  ws.warp_depth = c.take<float>(stereo ? P : 1);
+  ws.cls = c.take<uint8_t>(stereo ? P : 1);
+  ws.labels = c.take<int32_t>(stereo ? P : 1);
+  ws.slots = c.take<uint32_t>(stereo ? P + 1 : 1);
   ws.rects = c.take<int4>((size_t)lim.max_rects);
   ws.rp_master = c.take<float>(kRepairParams);
   ws.rp_grad = c.take<float>(kRepairParams);
@@ -116,8 +121,8 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.rp_sx = c.take<float>(6 * 32);
   ws.rp_sw = c.take<float>(6 * 32);
   ws.rp_amax = c.take<uint32_t>(6 * 32);
-  ws.rp_feat = c.take<uint4>(P);
-  ws.rp_fill = c.take<float>(3 * P);
+  ws.rp_feat = c.take<uint4>(repair ? P : 1);
+  ws.rp_fill = c.take<float>(repair ? 3 * P : 1);
   ws.rp_gate = c.take<float>(tiles);
   ws.rp_flags = c.take<uint8_t>(tiles);
   ws.rp_list = c.take<uint32_t>(tiles);
@@ -133,6 +138,9 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.max_tiles = (int)tiles;
   ws.min_tshift = msh;
   ws.max_instances = (int64_t)I;
+  ws.max_inst[0] = (int64_t)Ie[0];
+  ws.max_inst[1] = (int64_t)Ie[1];
+  ws.paths = paths;
   ws.max_pixels = (int64_t)P;
   ws.keep_intermediates = lim.keep_intermediates;
   ws.host_img = c.take<float>(lim.host_outputs ? 8 * P : 1);
@@ -140,7 +148,9 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
 
 bool limits_ok(const gs_limits *lim) {
   return lim && lim->max_surfels >= 0 && lim->max_width > 0 && lim->max_height > 0 && lim->max_instances > 0 &&
-         lim->max_instances < (int64_t(1) << 30) && lim->max_rects > 0 &&
+         lim->max_instances < (int64_t(1) << 30) && lim->max_instances_aff >= 0 &&
+         lim->max_instances_aff < (int64_t(1) << 30) && lim->paths >= 0 && lim->paths <= GS_PATH_ALL &&
+         lim->max_rects > 0 &&
          (int64_t)lim->max_width * lim->max_height < (int64_t(1) << 31) && lim->max_surfels < (1 << 30) &&
          lim->max_width <= kMaxWidth && lim->max_height <= kMaxWidth &&
          (lim->min_tile == 0 || lim->min_tile == 8 || lim->min_tile == 16 || lim->min_tile == 32) &&
@@ -269,6 +279,14 @@ PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in, 
   pa.fx = in->fx; pa.fy = in->fy; pa.cx = in->cx; pa.cy = in->cy;
   pa.W = in->width; pa.H = in->height;
   return pa;
+}
+
+// The buffers a stereo call with these parameters needs are in the workspace.
+bool paths_ok(const gs_context *ctx, const gs_roi_params *roi) {
+  const int p = ctx->ws.paths;
+  if (!(p & GS_PATH_STEREO)) return false;
+  if (roi->depth_mode == 2 && !(p & GS_PATH_REUSE)) return false;
+  return roi->repair_mode == 0 || (p & GS_PATH_REPAIR);
 }
 
 bool outputs_ok(const gs_outputs *o) { return o && o->rgb_dom && o->depth_dom && o->trans_dom && o->rgb_aff; }
@@ -418,6 +436,21 @@ gs_status gs_context_set_stream(gs_context *ctx, void *stream) {
 gs_status gs_context_set_counting(gs_context *ctx, int enable) {
   if (!ctx) return GS_ERR_BAD_ARG;
   ctx->counting = enable ? 1 : 0;
+  return GS_OK;
+}
+
+gs_status gs_context_usage(gs_context *ctx, gs_usage *u) {
+  if (!ctx || !u) return GS_ERR_BAD_ARG;
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  Counters c;
+  if ((e = cudaMemcpy(&c, ctx->ws.ctr, sizeof(c), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e);
+  for (int k = 0; k < 2; ++k) {
+    u->binned[k] = c.n_vis[k];
+    u->instances[k] = c.n_inst[k];
+    u->spans[k] = c.n_rows[k];
+    u->band_entries[k] = c.n_band[k];
+  }
   return GS_OK;
 }
 
@@ -599,6 +632,7 @@ extern "C" {
 gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *pose, const gs_intrinsics *intr,
                          const float *bg, float *rgb, float *depth, float *trans) {
   if (!ctx || !pose || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !rgb) return GS_ERR_BAD_ARG;
+  if (!(ctx->ws.paths & GS_PATH_MONO)) return GS_ERR_BAD_ARG;
   const float3 b = bg ? make_float3(bg[0], bg[1], bg[2]) : make_float3(0.f, 0.f, 0.f);
   const PoseArgs pa = pose_args(pose, nullptr, intr, ctx->rc);
   KeyBuilder kb;
@@ -681,7 +715,7 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
                              const gs_roi_params *roi, const gs_outputs *out, const HostCopy *hc) {
   if (!ctx || !pose_dom || !pose_aff || !roi || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
     return GS_ERR_BAD_ARG;
-  if (!roi_ok(gap_thresh, roi)) return GS_ERR_BAD_ARG;
+  if (!roi_ok(gap_thresh, roi) || !paths_ok(ctx, roi)) return GS_ERR_BAD_ARG;
   if ((roi->repair_mode == 1 && !ctx->rp_loaded) || (roi->repair_mode == 2 && !ctx->rp_fp8)) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
   const int sh = raster_tshift(ctx->rc), ts = 1 << sh;
@@ -813,6 +847,7 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
                              const gs_pose *pose_aff, const gs_intrinsics *intr, const gs_outputs *out) {
   if (!ctx || !pose_dom || !pose_aff || !scene_ok(ctx, scene) || !intr_ok(ctx, intr) || !outputs_ok(out))
     return GS_ERR_BAD_ARG;
+  if (!(ctx->ws.paths & GS_PATH_MONO)) return GS_ERR_BAD_ARG;
   const int W = intr->width, H = intr->height;
   const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc);
   KeyBuilder kb;
@@ -864,7 +899,7 @@ gs_status gs_context_set_graphs(gs_context *ctx, int enable) {
 gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *bytes, int64_t *count) {
   if (!ctx || !dev_ptr) return GS_ERR_BAD_ARG;
   const Workspace &ws = ctx->ws;
-  const size_t N = (size_t)ws.max_surfels, P = (size_t)ws.max_pixels, I = (size_t)ws.max_instances;
+  const size_t N = (size_t)ws.max_surfels, P = (size_t)ws.max_pixels;
   Counters c;
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_fail(cudaGetLastError());
   if (cudaMemcpy(&c, ws.ctr, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return cuda_fail(cudaGetLastError());
@@ -875,6 +910,7 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
   const int eye = (which & GS_BUF_EYE1) ? 1 : 0;
   // the last binning is the affiliated eye's when it ran, else the dominant eye's
   const int last = c.n_vis[1] || c.n_inst[1] ? 1 : 0;
+  const size_t I = (size_t)ws.max_inst[last];
   switch (which & ~GS_BUF_EYE1) {
     case GS_BUF_RECORDS: p = ws.rec[eye]; b = 64 * N; n = (int64_t)N; break;
     case GS_BUF_RECTS: p = ws.rect[eye]; b = 8 * N; n = (int64_t)N; break;
@@ -886,11 +922,15 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
       p = ws.bin[last].ikey; b = 4 * I; n = c.n_sort[last]; break;
     case GS_BUF_INST_VALS: p = ws.bin[last].ival; b = 4 * I; n = c.n_sort[last]; break;
     case GS_BUF_RANGES: p = ws.bin[last].ranges; b = 8 * (size_t)nt; n = nt; break;
-    case GS_BUF_WARP: p = ws.warpbuf; b = 8 * P; n = (int64_t)P; break;
+    case GS_BUF_WARP:
+      if (!(ws.paths & GS_PATH_STEREO)) return GS_ERR_BAD_ARG;
+      p = ws.warpbuf; b = 8 * P; n = (int64_t)P; break;
     case GS_BUF_TILE_MASK: p = ws.tile_mask; b = (size_t)nt; n = nt; break;
     case GS_BUF_DEPTH_RANGE: p = ws.drange; b = 8; n = 2; break;
     case GS_BUF_STRIPS: p = ws.strips; b = 64; n = 16; break;
-    case GS_BUF_WARP_DEPTH: p = ws.warp_depth; b = 4 * P; n = (int64_t)P; break;
+    case GS_BUF_WARP_DEPTH:
+      if (!(ws.paths & GS_PATH_STEREO)) return GS_ERR_BAD_ARG;
+      p = ws.warp_depth; b = 4 * P; n = (int64_t)P; break;
     case GS_BUF_PAIRS: p = &ws.ctr->pairs[0]; b = 32; n = 4; break;
     case GS_BUF_BIN_COUNTS:
       if (!ws.keep_intermediates) return GS_ERR_BAD_ARG;
@@ -935,7 +975,7 @@ gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count) 
 
 gs_status gs_repair_features(gs_context *ctx, int width, int height, uint16_t *feat) {
   if (!ctx || !feat || width <= 0 || height <= 0 || width > ctx->lim.max_width || height > ctx->lim.max_height ||
-      ((uintptr_t)feat & 15))
+      ((uintptr_t)feat & 15) || !(ctx->ws.paths & GS_PATH_REPAIR))
     return GS_ERR_BAD_ARG;
   return cuda_status(cudaMemcpyAsync(feat, ctx->ws.rp_feat, (size_t)width * height * 16, cudaMemcpyDeviceToDevice,
                                      ctx->stream));
@@ -954,7 +994,8 @@ gs_status gs_repair_infer(gs_context *ctx, const uint16_t *feat, int frames, int
 gs_status gs_repair_calibrate_fp8(gs_context *ctx, const uint16_t *feat, int frames, int width, int height,
                                   const uint32_t *tiles, int n_tiles) {
   if (!ctx || !feat || !tiles || frames <= 0 || frames > 255 || width <= 0 || height <= 0 || width > 4095 * 16 ||
-      height > 4095 * 16 || n_tiles <= 0 || ((uintptr_t)feat & 15) || (int64_t)n_tiles > 3 * ctx->ws.max_pixels)
+      height > 4095 * 16 || n_tiles <= 0 || ((uintptr_t)feat & 15) || (int64_t)n_tiles > 3 * ctx->ws.max_pixels ||
+      !(ctx->ws.paths & GS_PATH_REPAIR))
     return GS_ERR_BAD_ARG;
   if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
   cudaError_t e = repair_calibrate_fp8(ctx->ws, (const uint4 *)feat, width, height, tiles, (uint32_t)n_tiles,

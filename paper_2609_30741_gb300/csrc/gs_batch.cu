@@ -335,6 +335,7 @@ static gs_status check_frames(gs_batch *b, const gs_frame *frames, int n, const 
     const gs_frame &fr = frames[f];
     if (!scene_ok(ctx, fr.scene) || !intr_ok(ctx, &fr.intr) || !outputs_ok(&fr.out)) return GS_ERR_BAD_ARG;
     if (raster_tshift(b->rc) < ctx->ws.min_tshift) return GS_ERR_BAD_ARG;
+    if (roi ? !paths_ok(ctx, roi) : !(ctx->ws.paths & GS_PATH_MONO)) return GS_ERR_BAD_ARG;
     if (roi && ((roi->repair_mode == 1 && !ctx->rp_loaded) || (roi->repair_mode == 2 && !ctx->rp_fp8)))
       return GS_ERR_NOT_LOADED;
   }
@@ -552,7 +553,7 @@ gs_status gs_render_mono_batch(gs_batch *b, const gs_mono_frame *frames, int n_f
     gs_context *ctx = b->slot[f];
     const gs_mono_frame &fr = frames[f];
     if (!scene_ok(ctx, fr.scene) || !intr_ok(ctx, &fr.intr) || !fr.rgb) return GS_ERR_BAD_ARG;
-    if (raster_tshift(b->rc) < ctx->ws.min_tshift) return GS_ERR_BAD_ARG;
+    if (raster_tshift(b->rc) < ctx->ws.min_tshift || !(ctx->ws.paths & GS_PATH_MONO)) return GS_ERR_BAD_ARG;
     g[f].W = fr.intr.width;
     g[f].H = fr.intr.height;
     g[f].sh = raster_tshift(b->rc);
@@ -716,6 +717,7 @@ gs_status gs_autotune_stereo(gs_context *ctx, const gs_scene *scene, const gs_po
   if (!ctx || !pose_dom || !pose_aff || (roi && !roi_ok(gap_thresh, roi)) || !scene_ok(ctx, scene) ||
       !intr_ok(ctx, intr) || !outputs_ok(out) || reps <= 0 || reps > 1000 || max_results < 0)
     return GS_ERR_BAD_ARG;
+  if (roi ? !paths_ok(ctx, roi) : !(ctx->ws.paths & GS_PATH_MONO)) return GS_ERR_BAD_ARG;
   if (n_results) *n_results = 0;
   gs_frame fr;
   fr.scene = scene;

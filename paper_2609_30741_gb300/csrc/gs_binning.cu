@@ -744,7 +744,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   cudaError_t err;
   Counters *ctr = ws.ctr;
   const int ntiles = tiles_x * tiles_y;
-  const uint32_t cap = (uint32_t)ws.max_instances;
+  const uint32_t cap = (uint32_t)ws.max_inst[eye];
   const RadixScratch rs{b.rs_hist, b.rs_hist + kRsPasses * 256, b.rs_status, b.rs_ctl, &ctr->status};
   if (tile_mask) {
     launch_k(mask_sat_kernel, 1, 1024, 0, s, tile_mask, tiles_x, tiles_y, b.mask_sat);
@@ -775,7 +775,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   if (n > 0) {
     launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, b.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
                                                 ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.prim, ws.row_off[eye],
-                                                ws.spans[eye], (uint32_t)ws.max_instances, &ctr->n_rows[eye],
+                                                ws.spans[eye], cap, &ctr->n_rows[eye],
                                                 &ctr->status);
     GS_LAUNCHED(1);
   }
@@ -785,7 +785,8 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
       (err = radix_sort(b.dkey, b.dval, &ctr->n_vis[eye], (uint32_t)n, 32, rs, &which, s)) != cudaSuccess)
     return err;
   if (order == kOrderUnion && n > 0) {  // kept for the affiliated eye
-    const int g = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+    const int cap = sm_grid_cap(8);
+    const int g = (int)((n + 255) / 256 < cap ? (n + 255) / 256 : cap);
     if ((err = launch_k(keep_union_kernel, g, 256, 0, s, b.dval[which], &ctr->n_vis[eye], (uint32_t)n, ws.uval,
                         &ctr->n_union)) != cudaSuccess)
       return err;
@@ -805,7 +806,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   ba.tiles_y = tiles_y;
   ba.warp_surfels = ws.bin_warp_surfels;
   ba.pool = b.band_pool;
-  ba.pool_cap = ws.band_pool_cap;
+  ba.pool_cap = ws.band_pool_cap[eye];
   ba.pool_n = &ctr->n_band[eye];
   ba.lists = b.band_lists;
   ba.status = &ctr->status;
@@ -817,7 +818,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   a.pool = b.band_pool;
   a.lists = b.band_lists;
   a.spans = ws.spans[eye];
-  a.span_cap = (uint32_t)ws.max_instances;
+  a.span_cap = cap;
   a.mask = tile_mask;
   a.tiles_x = tiles_x;
   a.tiles_y = tiles_y;

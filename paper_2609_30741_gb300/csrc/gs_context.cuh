@@ -65,6 +65,7 @@ bool intr_ok(const gs_context *ctx, const gs_intrinsics *in);
 bool outputs_ok(const gs_outputs *o);
 // gs_roi_params and gap threshold of a stereo call (not the repair weights)
 bool roi_ok(int gap_thresh, const gs_roi_params *roi);
+bool paths_ok(const gs_context *ctx, const gs_roi_params *roi);
 PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in, const RasterConfig &rc);
 cudaError_t launch_reset_counters(Counters *c, cudaStream_t s);
 // Copies the optional stereo outputs (class map, ROI rectangles, counts) on ctx->stream.

@@ -120,7 +120,7 @@ struct Workspace {
   uint32_t *zkey[2];            // float bits of the centre depth per surfel and eye
   uint32_t *cnt_bin;            // tiles each surfel reaches in the last binning (keep_intermediates)
   uint32_t *uval;               // depth-ordered union of both eyes' binned surfels (dominant keys)
-  uint32_t band_pool_cap;
+  uint32_t band_pool_cap[2];     // per eye
   BinScratch bin[2];            // per eye
   uint8_t *tile_mask;           // ROI mask on the 16-pixel grid
   uint8_t *strip_mask;          // edge-strip tiles of a reused depth range (16-pixel grid)
@@ -153,7 +153,9 @@ struct Workspace {
   // limits
   int max_surfels, max_w, max_h, max_rects, max_tiles;  // max_tiles: rasterizer tiles at min_tshift
   int min_tshift;               // smallest rasterizer tile edge the buffers hold (log2)
-  int64_t max_instances, max_pixels;
+  int64_t max_instances, max_pixels;  // max_instances: the dominant eye's
+  int64_t max_inst[2];          // instance and span capacity per eye
+  int paths;                    // GS_PATH_* bits the buffers serve
   int keep_intermediates;
   uint32_t bin_warp_surfels, bin_nch;  // binning chunk geometry (see launch_binning)
   int prim;                     // primitive of the prepared records (gs_scene.primitive), set by launch_preprocess
@@ -266,6 +268,14 @@ struct RasterTable {
 struct RasterConfig {
   int tile, pix, batch;
 };
+// Streaming multiprocessors of the current device (cached per device; 0 on error).
+int sm_count();
+// Grid cap for grid-stride kernels: `per_sm` CTAs per multiprocessor (152 SMs
+// when the device cannot be queried).
+inline int sm_grid_cap(int per_sm) {
+  const int n = sm_count();
+  return (n > 0 ? n : 152) * per_sm;
+}
 bool raster_config_ok(const RasterConfig &c);
 int raster_tshift(const RasterConfig &c);
 // `queue` holds two words that are zero between launches (the launch's last CTA

@@ -137,7 +137,8 @@ cudaError_t scratch_on_current_device(unsigned long long **keys, WarpCams **cams
 
 int grid_for_pixels(int64_t n) {
   const int64_t b = (n + 255) / 256;
-  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+  const int64_t cap = sm_grid_cap(16);
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 }  // namespace

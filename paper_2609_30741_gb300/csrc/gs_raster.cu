@@ -380,6 +380,8 @@ int shape_index(const RasterConfig &c) {
 
 int batch_index(int b) { return b == 32 ? 0 : b == 64 ? 1 : b == 128 ? 2 : b == 256 ? 3 : -1; }
 
+}  // namespace
+
 int sm_count() {
   static int cached[64];
   int dev = 0;
@@ -390,8 +392,6 @@ int sm_count() {
   if (dev < 64) cached[dev] = n;
   return n;
 }
-
-}  // namespace
 
 bool raster_config_ok(const RasterConfig &c) { return shape_index(c) >= 0 && batch_index(c.batch) >= 0; }
 

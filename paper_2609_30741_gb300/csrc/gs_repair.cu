@@ -767,7 +767,10 @@ cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_
   return cudaGetLastError();
 }
 
-static int net_grid(uint32_t n_max) { return (int)(n_max < 152u ? (n_max < 1u ? 1u : n_max) : 152u); }
+static int net_grid(uint32_t n_max) {
+  const uint32_t sms = (uint32_t)sm_grid_cap(1);
+  return (int)(n_max < sms ? (n_max < 1u ? 1u : n_max) : sms);
+}
 
 cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
                            const uint32_t *n_ptr, uint32_t n_max, float *fill, float *gate, float *out4,

@@ -403,7 +403,8 @@ __global__ void warp_init_kernel(unsigned long long *__restrict__ warpbuf, int64
 
 static int grid_for(int64_t n, int per_block = 256) {
   const int64_t b = (n + per_block - 1) / per_block;
-  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+  const int64_t cap = sm_grid_cap(16);
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
 cudaError_t launch_warp(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,

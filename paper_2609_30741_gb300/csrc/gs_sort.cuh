@@ -42,7 +42,8 @@ inline size_t radix_status_words(size_t n_max) { return 256 * ((n_max + kRsTile 
 
 inline int radix_hist_grid(uint32_t n_max) {
   const uint32_t tiles = (n_max + kRsTile - 1) / kRsTile;
-  return (int)(tiles < 1 ? 1 : (tiles > 152 * 4 ? 152 * 4 : tiles));
+  const uint32_t cap = (uint32_t)sm_grid_cap(4);
+  return (int)(tiles < 1 ? 1 : (tiles > cap ? cap : tiles));
 }
 
 // Digit counts of all passes; the last CTA out writes the bases and clears the

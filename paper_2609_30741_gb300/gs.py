@@ -20,6 +20,7 @@ GS_OK, GS_ERR_BAD_ARG, GS_ERR_CAPACITY, GS_ERR_TIMEOUT, GS_ERR_CUDA, GS_ERR_WORK
  BUF_WARP, BUF_TILE_MASK, BUF_DEPTH_RANGE, BUF_STRIPS, BUF_WARP_DEPTH, BUF_PAIRS, BUF_BIN_COUNTS) = range(15)
 BUF_EYE1 = 0x100
 CLS_HOLE, CLS_GAP, CLS_CENTRE, CLS_STRIP, CLS_RENDER, CLS_NET = 1, 2, 4, 8, 16, 32
+PATH_MONO, PATH_STEREO, PATH_REUSE, PATH_REPAIR, PATH_ALL = 1, 2, 4, 8, 15
 
 
 class GsError(RuntimeError):
@@ -60,7 +61,17 @@ class Outputs(C.Structure):
 class Limits(C.Structure):
     _fields_ = [("max_surfels", C.c_int), ("max_width", C.c_int), ("max_height", C.c_int),
                 ("max_instances", C.c_int64), ("max_rects", C.c_int), ("keep_intermediates", C.c_int),
-                ("min_tile", C.c_int), ("host_outputs", C.c_int)]
+                ("min_tile", C.c_int), ("host_outputs", C.c_int), ("max_instances_aff", C.c_int64),
+                ("paths", C.c_int)]
+
+
+class Usage(C.Structure):
+    """Work counts of a context's last call (gs_usage), per eye."""
+    _fields_ = [("binned", C.c_int64 * 2), ("instances", C.c_int64 * 2), ("spans", C.c_int64 * 2),
+                ("band_entries", C.c_int64 * 2)]
+
+    def asdict(self):
+        return {k: [int(v) for v in getattr(self, k)] for k, _ in self._fields_}
 
 
 class RasterConfig(C.Structure):
@@ -114,6 +125,7 @@ EXPORTS = {
     "gs_context_destroy": (C.c_int, [C.c_void_p]),
     "gs_context_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "gs_context_check": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "gs_context_usage": (C.c_int, [C.c_void_p, C.POINTER(Usage)]),
     "gs_context_set_counting": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
@@ -260,9 +272,14 @@ class Context:
     """A renderer context: owns its workspace tensor, runs on a torch stream."""
 
     def __init__(self, max_surfels, max_width, max_height, max_instances=1 << 24, max_rects=1 << 16,
-                 keep_intermediates=False, device="cuda", stream=None, min_tile=16, host_outputs=False):
+                 keep_intermediates=False, device="cuda", stream=None, min_tile=16, host_outputs=False,
+                 max_instances_aff=0, paths=0):
+        """max_instances_aff: instance capacity of the affiliated eye (0: as the
+        dominant eye); paths: PATH_* bits of the entry points the context serves
+        (0: all), which leaves other paths' buffers out of the workspace."""
         self.lim = Limits(int(max_surfels), int(max_width), int(max_height), int(max_instances),
-                          int(max_rects), int(bool(keep_intermediates)), int(min_tile), int(bool(host_outputs)))
+                          int(max_rects), int(bool(keep_intermediates)), int(min_tile), int(bool(host_outputs)),
+                          int(max_instances_aff), int(paths))
         nbytes = C.c_size_t()
         _check(lib().gs_workspace_size(C.byref(self.lim), C.byref(nbytes)), "gs_workspace_size")
         self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=device)
@@ -291,6 +308,13 @@ class Context:
     def set_stream(self, stream):
         self.stream = stream
         _check(lib().gs_context_set_stream(self.h, C.c_void_p(stream.cuda_stream)), "gs_context_set_stream")
+
+    def usage(self):
+        """Per-eye binned surfels, instances, spans and band-list entries of the
+        last call (synchronises the context's stream)."""
+        u = Usage()
+        _check(lib().gs_context_usage(self.h, C.byref(u)), "gs_context_usage")
+        return u.asdict()
 
     def set_counting(self, on: bool):
         _check(lib().gs_context_set_counting(self.h, int(bool(on))), "gs_context_set_counting")

@@ -109,3 +109,37 @@ def test_warp_noalloc_rejects_mis_sized_tensors_before_any_launch():
             gs.check_warp_noalloc_args(cam, cpu, **args)
     with pytest.raises(ValueError):
         gs.warp_noalloc(rgb, plane, plane, *synth.eye_pair(synth.identity_pose()), cam, rgb.clone())
+
+
+def test_workspace_follows_paths_and_per_eye_capacity(gslib):
+    """The workspace holds only what the served paths use: leaving the stereo
+    path out drops its per-pixel buffers (8 + 4 + 1 + 4 + 4 = 21 B per pixel),
+    the repair path its features and fill (16 + 12 B per pixel), the reuse path
+    its strip image (12 B per pixel); a smaller affiliated-eye instance capacity
+    shrinks that eye's instance, span and band-list buffers."""
+    from paper_2609_30741_gb300 import gs
+
+    def size(**kw):
+        args = dict(max_surfels=20000, max_width=320, max_height=240, max_instances=1 << 20, max_rects=1024,
+                    keep_intermediates=0, min_tile=16, host_outputs=0, max_instances_aff=0, paths=0)
+        args.update(kw)
+        n = C.c_size_t()
+        st = gs.lib().gs_workspace_size(C.byref(gs.Limits(*args.values())), C.byref(n))
+        return st, n.value
+
+    P = 320 * 240
+    full = size()[1]
+    assert size(paths=gs.PATH_ALL)[1] == full
+    no_stereo = size(paths=gs.PATH_ALL & ~gs.PATH_STEREO)[1]
+    assert abs((full - no_stereo) - 21 * P) <= 256 * 6
+    no_repair = size(paths=gs.PATH_ALL & ~gs.PATH_REPAIR)[1]
+    assert abs((full - no_repair) - 28 * P) <= 256 * 3
+    no_reuse = size(paths=gs.PATH_ALL & ~gs.PATH_REUSE)[1]
+    assert abs((full - no_reuse) - 12 * P) <= 256 * 2
+    small_aff = size(max_instances_aff=1 << 16)[1]
+    # per instance: surfel id 4 B + span 8 B; band entries (12 B) are capped at
+    # the smaller of the span capacity and 8 per surfel
+    band = 12 * (min(1 << 20, 8 * 20000) - min(1 << 16, 8 * 20000))
+    assert abs((full - small_aff) - 12 * ((1 << 20) - (1 << 16)) - band) <= 256 * 4
+    assert size(paths=16)[0] == gs.GS_ERR_BAD_ARG
+    assert size(max_instances_aff=-1)[0] == gs.GS_ERR_BAD_ARG

@@ -27,12 +27,17 @@ RGB_TOL = 2e-4
 # Pixels with a blend decision within MARGIN (relative) of its threshold, or with
 # near-equal depth keys among their contributors, are excluded from the
 # tolerance. The smaller parity workloads use 1e-5. Here a pixel evaluates about
-# 400 surfels, and float32 rounding of the running transmittance accumulates to
-# about 400 * 2^-24 = 2.4e-5 relative, so decisions within 1e-4 may flip; and the
-# 1.8M surfels of the 1 m ball give many near-equal depth keys. The excluded
-# share of every crop is printed and bounded by MAX_MARGINAL, a bound set a
-# little above the largest share measured on the sampled frames.
-MARGIN = 1e-4
+# 400 surfels. The float32 running transmittance carries a relative error of
+# about 2^-24 per factor (1 - alpha), plus alpha's own relative error amplified
+# by alpha / (1 - alpha) (up to ~50 for the alpha ~ 0.98 layers of the dense
+# ball), so over a few hundred factors the transmittance at the stop test
+# T (1 - alpha) < 1e-4 can be off by ~1e-4 relative: a stop decision within
+# 1e-4 of its threshold flipped on one frame (a 2.02e-4 error, one contribution
+# of weight ~1e-4 times a colour ~2). Decisions within MARGIN = 1e-3 are
+# therefore excluded at this size. The excluded share of every crop is printed
+# and bounded by MAX_MARGINAL, set a little above the largest share measured on
+# the sampled frames.
+MARGIN = 1e-3
 MAX_MARGINAL = 0.5
 N_FRAMES = 16
 
@@ -116,11 +121,15 @@ def test_hmd_frames_against_oracle_crops(hmd, orc):
         o_rgb, _, _, mrg, _ = orc.render(hmd["scene"], a, cam, window=(x0, y0, 256, 256))
         ok = mrg >= MARGIN
         excluded = float(1.0 - ok.mean())
-        e_full = np.abs(_crop(full["rgb_aff"], x0, y0) - o_rgb).max(0)[ok].max()
+        e_map = np.abs(_crop(full["rgb_aff"], x0, y0) - o_rgb).max(0)
+        e_full = e_map[ok].max()
+        worst = np.unravel_index(np.argmax(np.where(ok, e_map, -1.0)), e_map.shape)
         rend = (_crop(outs["plain"]["cls_aff"], x0, y0).astype(np.int64) & gs.CLS_RENDER) > 0
         e_roi = np.abs(_crop(outs["plain"]["rgb_aff"], x0, y0) - o_rgb).max(0)[rend & ok].max(initial=0.0)
         row = {"frame": frame, "crop": (x0, y0), "excluded_share": round(excluded, 4),
-               "comparator_max_abs": float(e_full), "plain_roi_max_abs": float(e_roi)}
+               "comparator_max_abs": float(e_full), "plain_roi_max_abs": float(e_roi),
+               "worst": {"yx": [int(worst[0]), int(worst[1])], "margin": float(mrg[worst]),
+                         "share_margin_below_1e-4": round(float((mrg < 1e-4).mean()), 4)}}
         f_ref = full["rgb_aff"].double().cpu().numpy()
         for k, v in outs.items():
             c = _crop(v["rgb_aff"], x0, y0)
