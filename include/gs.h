@@ -157,7 +157,7 @@ typedef struct {
 /* gs_limits.paths bits. MONO: gs_render_mono and gs_render_two_pass (full
  * renders of one or both eyes). STEREO: gs_render_stereo(_host) with
  * depth_mode 0 or 1 and repair_mode 0: the warp, class, component and ROI
- * buffers (21 B per pixel). REUSE: depth_mode 2 (the affiliated eye's strip
+ * buffers (25 B per pixel). REUSE: depth_mode 2 (the affiliated eye's strip
  * image, 12 B per pixel). REPAIR: the learned repair (repair_mode 1-3, the
  * gs_repair_* calls): features and fill (28 B per pixel). */
 #define GS_PATH_MONO 1
@@ -258,9 +258,22 @@ gs_status gs_render_two_pass(gs_context *ctx, const gs_scene *scene, const gs_po
  * stream), resets the AdamW state and packs the BF16 weights. */
 gs_status gs_repair_load(gs_context *ctx, const float *weights, int64_t count);
 
-/* Reads back the FP32 parameters (which = 0) or the gradients of the last
- * training step (which = 1) into a host array; synchronises the stream. */
+/* Reads back the FP32 parameters (which = 0), the gradients of the last
+ * training step (which = 1), or the AdamW first (which = 2) and second (which =
+ * 3) moments into a host array of GS_REPAIR_PARAMS floats; synchronises the
+ * stream. */
 gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count);
+
+/* Training checkpoints: the AdamW steps taken since the last gs_repair_load
+ * (the bias correction's step count), and the restore of a saved state: the
+ * parameters, both moments (host arrays of GS_REPAIR_PARAMS floats) and the
+ * step count; packs the BF16 weights and synchronises the stream. A training
+ * run resumed from a state read with gs_repair_read (which = 0, 2, 3) and
+ * gs_repair_steps continues exactly as the uninterrupted run (the training
+ * step is deterministic). */
+gs_status gs_repair_steps(gs_context *ctx, int *steps);
+gs_status gs_repair_load_state(gs_context *ctx, const float *weights, const float *m, const float *v,
+                               int64_t count, int steps);
 
 /* The features of the last gs_render_stereo call on this context made with
  * repair_mode != 0 (same width and height), copied to feat: device [H][W][8]

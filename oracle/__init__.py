@@ -110,9 +110,11 @@ def eval_pair(splat, cam, x, y):
     return oG, d.value, r3.value, r2.value
 
 
-def render(scene, pose, cam, bg=(0.0, 0.0, 0.0), window=None):
+def render(scene, pose, cam, bg=(0.0, 0.0, 0.0), window=None, fp32_bound=False):
     """Full render of `window` = (x0, y0, w, h) (default: the whole image).
-    Returns rgb [3,h,w], depth [h,w], trans [h,w], margin [h,w], pairs."""
+    Returns rgb [3,h,w], depth [h,w], trans [h,w], margin [h,w], pairs, and with
+    fp32_bound=True also the per-pixel bound [h,w] on the error of a float32
+    evaluation of the same sum."""
     x0, y0, w, h = window if window is not None else (0, 0, cam.width, cam.height)
     rgb = np.zeros((3, h, w))
     dep = np.zeros((h, w))
@@ -121,10 +123,13 @@ def render(scene, pose, cam, bg=(0.0, 0.0, 0.0), window=None):
     pairs = C.c_int64()
     ref = _SceneRef(scene)
     bgv = np.asarray(bg, np.float64)
+    bound = np.zeros((h, w)) if fp32_bound else None
     r = lib().or_render(C.byref(ref.s), C.byref(pose_struct(pose)), C.byref(cam_struct(cam)), _p(bgv),
-                        x0, y0, w, h, _p(rgb), _p(dep), _p(tr), _p(mrg), C.byref(pairs))
+                        x0, y0, w, h, _p(rgb), _p(dep), _p(tr), _p(mrg), C.byref(pairs), _p(bound))
     if r < 0:
         raise ValueError("oracle render: bad arguments")
+    if fp32_bound:
+        return rgb, dep, tr, mrg, pairs.value, bound
     return rgb, dep, tr, mrg, pairs.value
 
 
@@ -145,6 +150,13 @@ def tile_rect(bounds, W, H, tile=16):
     b = np.ascontiguousarray(bounds, np.float32)
     cnt = lib().or_tile_rect(_p(b), W, H, tile, _p(r))
     return r, cnt
+
+
+def depth_key(pose, p):
+    """The oracle's depth-order key of a centre p (3 floats) for a pose."""
+    lib().or_depth_key.restype = C.c_float
+    pp = np.ascontiguousarray(p, np.float32)
+    return float(lib().or_depth_key(C.byref(pose_struct(pose)), _p(pp)))
 
 
 def sort_pairs(keys, vals):

@@ -54,7 +54,7 @@ typedef struct {
   double lp2;       /* pixel radius^2 of the low-pass support: ln(255 o) */
   double cx, cy;    /* projected centre pi(p_c) (Eq. 3) */
   double rgb[3];
-  float key;        /* float32(p_c.z): the depth-order key */
+  float key;        /* the depth-order key: p_c.z in float32 arithmetic (or_depth_key) */
   double box[4];    /* xmin, xmax, ymin, ymax enclosing the whole support (a cheap exact reject) */
   int prim;         /* 0: surfel; 1: ellipsoid */
   double conic[3];  /* ellipsoid: inverse of the 2-D screen covariance (xx, xy, yy) */
@@ -95,10 +95,12 @@ double or_eval(const or_splat *s, const or_cam *cam, double x, double y, double 
  * margin (optional) receives, per pixel, the smallest relative distance of a
  * decision that can move the result by more than 1e-5 to its threshold.
  * pairs (optional) receives the number of in-support evaluations.
+ * fp32_bound (optional) receives, per pixel, a first-order bound on the error
+ * of a float32 evaluation of the same blending sum (see render.c).
  * Returns the number of visible surfels, or -1 on bad arguments. */
 int or_render(const or_scene *sc, const or_pose *pose, const or_cam *cam, const double bg[3],
               int x0, int y0, int w, int h, double *rgb, double *depth, double *trans,
-              double *margin, int64_t *pairs);
+              double *margin, int64_t *pairs, double *fp32_bound);
 
 /* Render only the pixels whose tile (tile x tile) is set in tile_mask, writing
  * full-frame planar buffers (other pixels untouched). */
@@ -120,6 +122,8 @@ int64_t or_support_pairs(const or_scene *sc, const or_pose *pose, const or_cam *
  * with squared radius k (FP64 evaluation of float inputs). */
 int or_tile_test(const float rec[12], double k, double x0, double x1, double y0, double y1);
 
+/* The depth-order key of a centre p (float32 scene position) for a pose. */
+float or_depth_key(const or_pose *pose, const float p[3]);
 /* Stable sort of (key, value) pairs by key (merge sort). */
 void or_sort_pairs(int64_t n, uint64_t *keys, uint32_t *vals);
 

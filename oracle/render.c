@@ -19,7 +19,8 @@
  *     sigma^2 = 1/2 px^2 around the projected centre c; where it wins, the
  *     contribution's depth is the centre depth p_c.z, otherwise the depth of the
  *     ray-plane intersection.
- *   - order: visible surfels sorted by (float32(p_c.z), index).
+ *   - order: visible surfels sorted by (key, index), the key being p_c.z as the
+ *     tile rasterizer computes it in float32 (or_depth_key).
  *   - a surfel is culled when its quaternion is zero, when 255 o < 1 (it can never
  *     reach alpha = 1/255), when p_c.z <= 0.2 m, or when a corner of the square
  *     |u|, |v| <= r_c around its support is not in front of that near plane.
@@ -160,8 +161,23 @@ static void prepare_ellipsoid(const or_scene *sc, const or_pose *pose, const or_
     for (int k = 0; k < K; ++k) acc += Y[k] * c[k * 3 + ch];
     s->rgb[ch] = acc > 0.0 ? acc : 0.0;
   }
-  s->key = (float)pc[2];
+  s->key = or_depth_key(pose, sc->pos + 4 * (size_t)i);
   s->visible = 1;
+}
+
+/* The depth-order key (the 2DGS ordering the method keeps, Sec. 2.2 and
+ * Sec. 3.1): the camera depth of the centre as the tile rasterizer computes it,
+ * in float32: the world -> camera rotation's last row and offset are rounded to
+ * float32 from their FP64 values, and z = r20 x + r21 y + r22 z + t2 is
+ * evaluated with one fused multiply-add per term. Evaluating it in float64
+ * instead would order surfels whose depths lie a few float32 ulps apart
+ * differently from the rasterizer whose order the method defines. */
+float or_depth_key(const or_pose *pose, const float p[3]) {
+  const double *R = pose->R, *t = pose->t;
+  double t2 = 0.0;
+  for (int j = 0; j < 3; ++j) t2 = fma(-R[j * 3 + 2], t[j], t2);
+  const float r0 = (float)R[0 * 3 + 2], r1 = (float)R[1 * 3 + 2], r2 = (float)R[2 * 3 + 2];
+  return fmaf(r0, p[0], fmaf(r1, p[1], fmaf(r2, p[2], (float)t2)));
 }
 
 static void prepare_one(const or_scene *sc, const or_pose *pose, const or_cam *cam, int i,
@@ -227,7 +243,7 @@ static void prepare_one(const or_scene *sc, const or_pose *pose, const or_cam *c
     for (int k = 0; k < K; ++k) acc += Y[k] * c[k * 3 + ch];
     s->rgb[ch] = acc > 0.0 ? acc : 0.0;
   }
-  s->key = (float)pc[2];
+  s->key = or_depth_key(pose, sc->pos + 4 * (size_t)i);
   s->visible = 1;
 }
 
@@ -313,10 +329,24 @@ static uint32_t fbits(float f) {
 }
 
 /* Front-to-back blend of one pixel over all visible surfels in depth order. */
+/* A first-order bound on how far a float32 evaluation of the same blending sum
+ * can be from the exact one at this pixel (u = 2^-24): alpha carries a relative
+ * error of about 3u + 4u rho (the exponential and its argument; none once
+ * clamped at 0.99), and through (1 - alpha) each factor of the running
+ * transmittance adds 2u + alpha / (1 - alpha) times that error; every weight
+ * alpha T then carries the errors of its alpha and of its T, each colour about
+ * 20u of its magnitude (at least 0.5), and the n-term sum nu of the total.
+ * Used by the tests to tell pixels whose float32 value cannot meet an absolute
+ * tolerance by construction from pixels that must. */
+#define OR_U (1.0 / 16777216.0)
+
 static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_cam *cam,
                          const double bg[3], double x, double y, double out_rgb[3],
-                         double *out_d, double *out_t, double *out_margin, int64_t *out_pairs) {
+                         double *out_d, double *out_t, double *out_margin, int64_t *out_pairs,
+                         double *out_bound) {
   double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, mrg = INFINITY;
+  double eT = 0.0, bnd = 0.0, cabs = 0.0;
+  int ncontrib = 0;
   int64_t pairs = 0;
   int have_prev = 0;
   float prev_key = 0.f;
@@ -348,17 +378,27 @@ static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_
     D += w * dep;
     T = Tn;
     have_prev = 1; prev_key = s->key; prev_w = w;
+    if (out_bound) {
+      const double rho = isfinite(rho3) ? fmin(rho3, rho2) : rho2;
+      const double ea = a < OR_ALPHA_MAX ? OR_U * (3.0 + 4.0 * rho) : 0.0;
+      const double cm = fmax(fmax(fabs(s->rgb[0]), fabs(s->rgb[1])), fabs(s->rgb[2]));
+      bnd += w * (cm * (eT + ea + OR_U) + 20.0 * OR_U * fmax(cm, 0.5));
+      cabs += w * cm;
+      eT += 2.0 * OR_U + a / (1.0 - a) * ea;
+      ++ncontrib;
+    }
   }
   for (int ch = 0; ch < 3; ++ch) out_rgb[ch] = C[ch] + T * (bg ? bg[ch] : 0.0);
   *out_d = D;
   *out_t = T;
   if (out_margin) *out_margin = mrg;
   if (out_pairs) *out_pairs = pairs;
+  if (out_bound) *out_bound = bnd + ncontrib * OR_U * cabs;
 }
 
 int or_render(const or_scene *sc, const or_pose *pose, const or_cam *cam, const double bg[3],
               int x0, int y0, int w, int h, double *rgb, double *depth, double *trans,
-              double *margin, int64_t *pairs) {
+              double *margin, int64_t *pairs, double *fp32_bound) {
   if (!sc || !pose || !cam || w < 0 || h < 0 || sc->n < 0) return -1;
   or_splat *sp = (or_splat *)malloc(sizeof(or_splat) * (size_t)(sc->n > 0 ? sc->n : 1));
   or_prepare(sc, pose, cam, sp);
@@ -373,7 +413,7 @@ int or_render(const or_scene *sc, const or_pose *pose, const or_cam *cam, const 
       double c3[3], m;
       int64_t np;
       render_pixel(sp, ord, nvis, cam, bg, (double)(x0 + i), (double)(y0 + j), c3, &depth[p],
-                   &trans[p], &m, &np);
+                   &trans[p], &m, &np, fp32_bound ? &fp32_bound[p] : NULL);
       for (int ch = 0; ch < 3; ++ch) rgb[ch * npix + p] = c3[ch];
       if (margin) margin[p] = m;
       total += np;
@@ -401,7 +441,7 @@ int or_render_tiles(const or_scene *sc, const or_pose *pose, const or_cam *cam, 
       const size_t p = (size_t)y * W + x;
       double c3[3];
       render_pixel(sp, ord, nvis, cam, bg, (double)x, (double)y, c3, &depth[p], &trans[p], NULL,
-                   NULL);
+                   NULL, NULL);
       for (int ch = 0; ch < 3; ++ch) rgb[ch * npix + p] = c3[ch];
     }
   }

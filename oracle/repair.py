@@ -186,15 +186,20 @@ def conv3x3_backward(x, W, dy):
     return dxp[:, 1:-1, 1:-1], dW, dy.sum((1, 2))
 
 
-def backward(acts, W, dout):
+def backward(acts, W, dout, bf16=False):
     """Gradients (dW[l], db[l]) of the network for dL/dout, from the stored
-    activations of forward()."""
+    activations of forward(). With bf16=True the gradient entering each layer
+    (dL/dy of its output) and the weights its input gradient is formed with are
+    rounded to bfloat16, the points where the GPU's tensor-core backward stores
+    them as operands (the network computes in BF16 with FP32 accumulation); the
+    sums stay in float64."""
+    r = round_bf16 if bf16 else (lambda a: np.asarray(a, np.float64))
     dW, db = [None] * 6, [None] * 6
-    dy = dout
+    dy = r(dout)
     for l in range(5, -1, -1):
-        dx, dW[l], db[l] = conv3x3_backward(acts[l], W[l], dy)
+        dx, dW[l], db[l] = conv3x3_backward(acts[l], r(W[l]), dy)
         if l > 0:
-            dy = dx * (acts[l] > 0)
+            dy = r(dx * (acts[l] > 0))
     return dW, db
 
 

@@ -319,7 +319,7 @@ int or_stereo(const or_scene *sc, const or_pose *dom, const or_pose *aff, const 
   const int64_t npix = (int64_t)W * H;
   if (W <= 0 || H <= 0 || tile <= 0 || p->nsamples < 2) return -1;
   /* Stage 1 */
-  or_render(sc, dom, cam, bg, 0, 0, W, H, rgb_dom, depth_dom, trans_dom, NULL, NULL);
+  or_render(sc, dom, cam, bg, 0, 0, W, H, rgb_dom, depth_dom, trans_dom, NULL, NULL, NULL);
   /* Stage 2 */
   int64_t *tgt = (int64_t *)malloc(sizeof(int64_t) * npix), *win = (int64_t *)malloc(sizeof(int64_t) * npix);
   float *zk = (float *)malloc(sizeof(float) * npix), *zd = (float *)malloc(sizeof(float) * npix);

@@ -89,7 +89,6 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     b.items = c.take<uint32_t>(tiles);
     b.rqueue = c.take<uint32_t>(2);
     b.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
-    b.roi_flag = c.take<uint8_t>(N);
     b.rs_hist = c.take<uint32_t>(2 * kRsPasses * 256);
     b.rs_status = c.take<unsigned long long>(rs_words);
     b.rs_ctl = c.take<uint32_t>(4);
@@ -109,6 +108,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.warp_depth = c.take<float>(stereo ? P : 1);
   ws.cls = c.take<uint8_t>(stereo ? P : 1);
   ws.labels = c.take<int32_t>(stereo ? P : 1);
+  ws.cc_list = c.take<uint32_t>(stereo ? P : 1);
   ws.slots = c.take<uint32_t>(stereo ? P + 1 : 1);
   ws.rects = c.take<int4>((size_t)lim.max_rects);
   ws.rp_master = c.take<float>(kRepairParams);
@@ -118,6 +118,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.rp_wpack = c.take<uint8_t>(92160);
   ws.rp_bias = c.take<float>(6 * 32);
   ws.rp_wpack8 = c.take<uint8_t>(50688);
+  ws.rp_wpackT = c.take<uint8_t>(82944);
   ws.rp_sx = c.take<float>(6 * 32);
   ws.rp_sw = c.take<float>(6 * 32);
   ws.rp_amax = c.take<uint32_t>(6 * 32);
@@ -170,6 +171,7 @@ __global__ void reset_counters_kernel(Counters *c) {
     c->dmin_bits = 0x7f800000u;
     c->dmax_bits = 0u;
     c->n_rects = 0;
+    c->n_centre = 0;
     c->pairs[0] = c->pairs[1] = 0ull;
     c->contrib[0] = c->contrib[1] = 0ull;
   }
@@ -371,6 +373,7 @@ gs_status gs_context_create(gs_context **out, const gs_limits *lim, void *worksp
   const int msh = min_tshift(*lim);
   cudaError_t e = prepare_binning((lim->max_width + (1 << msh) - 1) >> msh);
   if (e == cudaSuccess) e = prepare_repair();
+  if (e == cudaSuccess) e = prepare_reproject();
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = cudaMemsetAsync(ctx->ws.bin[k].rqueue, 0, 2 * sizeof(uint32_t), ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->ws.bin[k].scan_ticket, 0, 4 * sizeof(uint32_t), ctx->stream);
@@ -753,12 +756,9 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
       if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) == cudaSuccess) e = cudaStreamWaitEvent(sd, ctx->ev_fork, 0);
       if (e == cudaSuccess) e = launch_edge_roi(ws, r, ws.strip_mask, true, sd);
       if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_edge, sd);
-      const uint8_t *smask = ws.strip_mask;
-      if (e == cudaSuccess && sh != 4) {
-        e = launch_raster_mask(ws.strip_mask, W, H, sh, ws.bin[1].rmask, sd);
-        smask = ws.bin[1].rmask;
-      }
-      if (e == cudaSuccess) e = launch_binning(ws, 1, scene->n, tx, ty, smask, sd, kOrderOwn);
+      if (e == cudaSuccess)
+        e = sh != 4 ? launch_binning(ws, 1, scene->n, tx, ty, ws.bin[1].rmask, sd, kOrderOwn, ws.strip_mask, W, H, sh)
+                    : launch_binning(ws, 1, scene->n, tx, ty, ws.strip_mask, sd, kOrderOwn);
       if (e == cudaSuccess) {
         RasterTable t;
         t.n = 1;
@@ -816,13 +816,9 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
     // (the ROI mask lives on the 16-pixel grid; other tile edges bin on a copy
     // on their own grid)
     ctx->last_tiles = tx * ty;
-    const uint8_t *bmask = ws.tile_mask;
-    if (sh != 4) {
-      if ((e = launch_raster_mask(ws.tile_mask, W, H, sh, ws.bin[1].rmask, ctx->stream)) != cudaSuccess)
-        return cuda_fail(e);
-      bmask = ws.bin[1].rmask;
-    }
-    e = launch_binning(ws, 1, scene->n, tx, ty, bmask, ctx->stream, p.parallel ? kOrderReuse : kOrderOwn);
+    const int aorder = p.parallel ? kOrderReuse : kOrderOwn;
+    e = sh != 4 ? launch_binning(ws, 1, scene->n, tx, ty, ws.bin[1].rmask, ctx->stream, aorder, ws.tile_mask, W, H, sh)
+                : launch_binning(ws, 1, scene->n, tx, ty, ws.tile_mask, ctx->stream, aorder);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
     e = raster_one(ctx, raster_frame(ws, 1, W, H, sh, ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ws.cls,
@@ -964,10 +960,36 @@ gs_status gs_repair_load(gs_context *ctx, const float *weights, int64_t count) {
   return GS_OK;
 }
 
-gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count) {
-  if (!ctx || !out || count != kRepairParams || (which != 0 && which != 1)) return GS_ERR_BAD_ARG;
+gs_status gs_repair_steps(gs_context *ctx, int *steps) {
+  if (!ctx || !steps) return GS_ERR_BAD_ARG;
   if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
-  const float *src = which == 0 ? ctx->ws.rp_master : ctx->ws.rp_grad;
+  *steps = ctx->rp_step;
+  return GS_OK;
+}
+
+gs_status gs_repair_load_state(gs_context *ctx, const float *weights, const float *m, const float *v, int64_t count,
+                               int steps) {
+  if (!ctx || !weights || !m || !v || count != kRepairParams || steps < 0) return GS_ERR_BAD_ARG;
+  const Workspace &ws = ctx->ws;
+  cudaStream_t s = ctx->stream;
+  const size_t bytes = sizeof(float) * kRepairParams;
+  cudaError_t e = cudaMemcpyAsync(ws.rp_master, weights, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws.rp_m, m, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(ws.rp_v, v, bytes, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = repair_pack(ws, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host arrays may go away after the call
+  if (e != cudaSuccess) return cuda_fail(e);
+  ctx->rp_loaded = 1;
+  ctx->rp_fp8 = 0;
+  ctx->rp_step = steps;
+  return GS_OK;
+}
+
+gs_status gs_repair_read(gs_context *ctx, int which, float *out, int64_t count) {
+  if (!ctx || !out || count != kRepairParams || which < 0 || which > 3) return GS_ERR_BAD_ARG;
+  if (!ctx->rp_loaded) return GS_ERR_NOT_LOADED;
+  const float *src = which == 0 ? ctx->ws.rp_master : which == 1 ? ctx->ws.rp_grad : which == 2 ? ctx->ws.rp_m
+                                                                                                : ctx->ws.rp_v;
   cudaError_t e = cudaMemcpyAsync(out, src, sizeof(float) * kRepairParams, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   return cuda_status(e);

@@ -172,12 +172,11 @@ static gs_status enqueue_batch(gs_batch *b, const gs_frame *frames, int n, const
     if (roi->enable_center) BTRY(launch_centre_rois(ctx->ws, g[f].W, g[f].H, roi->margin, s));
     if (roi->repair_mode == 1 || roi->repair_mode == 2)
       BTRY(repair_stereo(ctx->ws, g[f].W, g[f].H, roi->gate_tau, o.rgb_aff, s, roi->repair_mode == 2));
-    const uint8_t *bmask = ctx->ws.tile_mask;
-    if (g[f].sh != 4) {
-      BTRY(launch_raster_mask(ctx->ws.tile_mask, g[f].W, g[f].H, g[f].sh, ctx->ws.bin[1].rmask, s));
-      bmask = ctx->ws.bin[1].rmask;
-    }
-    BTRY(launch_binning(ctx->ws, 1, frames[f].scene->n, g[f].tx, g[f].ty, bmask, s, order));
+    if (g[f].sh != 4)
+      BTRY(launch_binning(ctx->ws, 1, frames[f].scene->n, g[f].tx, g[f].ty, ctx->ws.bin[1].rmask, s, order,
+                          ctx->ws.tile_mask, g[f].W, g[f].H, g[f].sh));
+    else
+      BTRY(launch_binning(ctx->ws, 1, frames[f].scene->n, g[f].tx, g[f].ty, ctx->ws.tile_mask, s, order));
   }
   BTRY(join_frames(b, n));
   bmark(b, 3);

@@ -85,9 +85,31 @@ __device__ __forceinline__ void row_ranges(const Conic &q, const float4 r0, int 
 // and column < x, (tiles_y + 1) x (tiles_x + 1) entries. One block: each warp
 // takes whole rows (prefix counts by ballot, 32 columns at a time), then each
 // thread adds one column down the rows.
-__global__ void __launch_bounds__(1024) mask_sat_kernel(const uint8_t *__restrict__ mask, int tiles_x, int tiles_y,
-                                                        uint32_t *__restrict__ sat) {
+// With roi16 given, the mask is first derived from the ROI mask on the 16-pixel
+// grid (rtx x rty tiles): a tile of edge 1 << tshift is masked when it holds a
+// masked pixel.
+__global__ void __launch_bounds__(1024) mask_sat_kernel(uint8_t *mask, int tiles_x, int tiles_y,
+                                                        uint32_t *__restrict__ sat, const uint8_t *__restrict__ roi16,
+                                                        int rtx, int rty, int tshift) {
   griddep_wait();
+  if (roi16) {
+    for (int t = threadIdx.x; t < tiles_x * tiles_y; t += blockDim.x) {
+      const int x = t % tiles_x, y = t / tiles_x;
+      uint8_t v = 0;
+      if (tshift <= 4) {
+        v = roi16[(y >> (4 - tshift)) * rtx + (x >> (4 - tshift))];
+      } else {
+        const int sc = 1 << (tshift - 4);
+        for (int dy = 0; dy < sc; ++dy)
+          for (int dx = 0; dx < sc; ++dx) {
+            const int yy = y * sc + dy, xx = x * sc + dx;
+            if (yy < rty && xx < rtx) v |= roi16[yy * rtx + xx];
+          }
+      }
+      mask[t] = v ? 1 : 0;
+    }
+    __syncthreads();
+  }
   const int sx = tiles_x + 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int y = wid; y <= tiles_y; y += nw) {
@@ -120,6 +142,32 @@ __device__ __forceinline__ bool sat_any(const uint32_t *sat, int tiles_x, int y0
   return v != 0u;
 }
 
+// The masked tiles of tile row ty between columns [x0, x1]: the span clipped to
+// its first and last masked tile (empty, lo > hi, when it has none). The tiles
+// in between may still be unmasked; the counting sort skips those one by one.
+__device__ __forceinline__ void clip_to_mask(const uint32_t *sat, int tiles_x, int ty, int &x0, int &x1) {
+  if (x0 > x1) return;
+  if (!sat_any(sat, tiles_x, ty, ty, x0, x1)) {
+    x0 = 1;
+    x1 = 0;
+    return;
+  }
+  int lo = x0, hi = x1;  // first masked: smallest c with a masked tile in [x0, c]
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (sat_any(sat, tiles_x, ty, ty, x0, mid)) hi = mid; else lo = mid + 1;
+  }
+  const int first = lo;
+  lo = first;
+  hi = x1;  // last masked: largest c with a masked tile in [c, x1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sat_any(sat, tiles_x, ty, ty, mid, x1)) lo = mid; else hi = mid - 1;
+  }
+  x0 = first;
+  x1 = lo;
+}
+
 // ---------------------------------------------------------------- row spans
 // Once per eye and frame, every tile row of every surfel's bounding rectangle
 // gets its tile ranges [a0, a1] u [c0, c1] (row_ranges; an ill-conditioned
@@ -127,14 +175,16 @@ __device__ __forceinline__ bool sat_any(const uint32_t *sat, int tiles_x, int y0
 // takes 32 consecutive surfels (one per lane), reserves slots for all their rows
 // with one atomic, and then computes the rows 32 at a time, one per lane, so no
 // lane idles while another walks a large surfel. row_off[i] is the slot of
-// surfel i's first rectangle row.
+// surfel i's first rectangle row. An ROI binning keeps of each range only the
+// part from its first to its last masked tile.
 __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ ids, const uint32_t *n_ptr,
                                                    uint32_t n_max, const float4 *__restrict__ rec,
                                                    const ushort4 *__restrict__ rect, const uint32_t *__restrict__ cnt,
                                                    const CamBlock *__restrict__ cams, int eye, int prim,
                                                    uint32_t *__restrict__ row_off, uint2 *__restrict__ spans,
                                                    uint32_t cap, uint32_t *__restrict__ n_rows,
-                                                   uint32_t *__restrict__ status) {
+                                                   uint32_t *__restrict__ status, const uint32_t *__restrict__ sat,
+                                                   int sat_tiles_x) {
   griddep_wait();
   const int lane = threadIdx.x & 31;
   const uint32_t n = load_n(n_ptr, n_max);
@@ -203,6 +253,11 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
     if (qq < total && slot < cap) {
       int a0 = sx0, a1 = sx1, c0 = 1, c1 = 0;
       if (qk.ok) row_ranges(qk, ck, ty, W, H, sx0, sx1, tshift, a0, a1, c0, c1);
+      if (sat) {  // an ROI binning: only the masked part of each range
+        clip_to_mask(sat, sat_tiles_x, ty, a0, a1);
+        clip_to_mask(sat, sat_tiles_x, ty, c0, c1);
+        if (a0 > a1) { a0 = c0; a1 = c1; c0 = 1; c1 = 0; }
+      }
       // empty ranges are stored as [1, 0]
       if (a0 > a1) { a0 = 1; a1 = 0; }
       if (c0 > c1) { c0 = 1; c1 = 0; }
@@ -232,40 +287,36 @@ struct VisibleLoad {
   }
 };
 
+// What the compaction's last CTA sets up for the rest of a binning: the binned
+// count, cleared row-span, list and tile-list counters, the chunks holding
+// binned surfels and the size of the (tile, chunk) table scan over them.
+struct BinCounts {
+  uint32_t *n_out, *n_rows, *n_band, *n_items, *n_chunks, *n_table;
+  uint32_t chunk, ntiles;
+  __device__ void set(uint32_t total) const {
+    *n_out = total;
+    *n_rows = 0u;
+    *n_band = 0u;
+    *n_items = 0u;
+    // at least one chunk, so that every tile's range is written
+    const uint32_t nc = total > 0u ? (total + chunk - 1) / chunk : 1u;
+    *n_chunks = nc;
+    *n_table = nc * ntiles;
+  }
+};
+
 struct CompactApply {
   const uint32_t *zkey;
   uint32_t *key_out, *val_out;
-  uint32_t *n_out;
-  uint32_t *n_rows, *n_band;  // cleared here for the row spans and band lists that follow
+  BinCounts bc;
   __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
     if (v) {
       key_out[prefix] = zkey[i];
       val_out[prefix] = i;
     }
   }
-  __device__ void end(uint32_t, uint32_t total) const {
-    *n_out = total;
-    *n_rows = 0u;
-    *n_band = 0u;
-  }
+  __device__ void end(uint32_t, uint32_t total) const { bc.set(total); }
 };
-
-// Per surfel id (coalesced): binned by this eye and, for an ROI binning, with a
-// masked tile in its rectangle. The filters below read one byte per surfel
-// instead of repeating the rectangle and summed-area lookups in both scan passes.
-__global__ void roi_flag_kernel(const uint32_t *__restrict__ cnt, const ushort4 *__restrict__ rect,
-                                const uint32_t *__restrict__ sat, int tiles_x, uint32_t n,
-                                uint8_t *__restrict__ flag) {
-  griddep_wait();
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  bool f = cnt[i] > 0u;
-  if (f && sat) {
-    const ushort4 rc = rect[i];
-    f = sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z);
-  }
-  flag[i] = f ? 1 : 0;
-}
 
 // The affiliated eye's surfels in the dominant eye's depth order: a stable filter
 // of that order. For a parallel rig both eyes' keys are identical, so the
@@ -273,18 +324,24 @@ __global__ void roi_flag_kernel(const uint32_t *__restrict__ cnt, const ushort4 
 struct ReuseLoad {
   const uint32_t *uval, *n_union;
   uint32_t n_max;
-  const uint8_t *flag;  // roi_flag_kernel's flags
+  const uint32_t *cnt;   // this eye's tile counts
+  const ushort4 *rect;
+  const uint32_t *sat;   // summed-area table of the ROI mask, or null
+  int tiles_x;
   __device__ uint32_t operator()(uint32_t i) const {
     if (i >= load_n(n_union, n_max)) return 0u;
-    return flag[uval[i]];
+    const uint32_t id = uval[i];
+    if (cnt[id] == 0u) return 0u;
+    if (!sat) return 1u;
+    const ushort4 rc = rect[id];
+    return sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z) ? 1u : 0u;
   }
 };
 
 struct ReuseApply {
   const uint32_t *uval, *zkey;
   uint32_t *key_out, *val_out;
-  uint32_t *n_out;
-  uint32_t *n_rows, *n_band;  // cleared here for the row spans and band lists that follow
+  BinCounts bc;
   __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
     if (v) {
       const uint32_t id = uval[i];
@@ -292,11 +349,7 @@ struct ReuseApply {
       val_out[prefix] = id;
     }
   }
-  __device__ void end(uint32_t, uint32_t total) const {
-    *n_out = total;
-    *n_rows = 0u;
-    *n_band = 0u;
-  }
+  __device__ void end(uint32_t, uint32_t total) const { bc.set(total); }
 };
 
 // Keeps the dominant eye's depth order of the union for the affiliated eye.
@@ -650,56 +703,54 @@ __global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(BinArgs a, int mode
   }
 }
 
-// Sum of a (tile, chunk)'s per-warp counts; chunks past the binned surfels read as 0.
+// The tile-major scan runs over the (tile, chunk) entries of the chunks that
+// hold binned surfels only (one chunk when none does): element i is tile
+// i / n_chunks, chunk i % n_chunks (the table rows keep their full length nch).
 struct BinTableLoad {
   const uint4 *table;
-  const uint32_t *n_vis;
-  uint32_t n_max, nch, chunk;
+  const uint32_t *n_chunks, *n_vis;
+  uint32_t nch, chunk;
   __device__ uint32_t operator()(uint32_t i) const {
-    if ((i % nch) * chunk >= load_n(n_vis, n_max)) return 0u;
-    const uint4 v = table[i];
+    const uint32_t na = *n_chunks, c = i % na;
+    if (c * chunk >= *n_vis) return 0u;  // only with no binned surfel: bin_kernel wrote nothing
+    const uint4 v = table[(size_t)(i / na) * nch + c];
     const uint32_t lo = (v.x & 0xffffu) + (v.y & 0xffffu) + (v.z & 0xffffu) + (v.w & 0xffffu);
     return lo + (v.x >> 16) + (v.y >> 16) + (v.z >> 16) + (v.w >> 16);
   }
 };
 
+// Offsets of every (tile, chunk) run; the first chunk's entry of a tile also
+// gives the tile's range (its start, and the end of the tile before it), and a
+// masked binning lists its masked tiles for the persistent rasterizer (in any
+// order: the rasterizer's tiles are independent).
 struct BinOffsetApply {
   uint32_t *offs;
+  const uint32_t *n_chunks;
+  uint32_t nch;
   uint32_t *n_inst, *n_sort;
   uint32_t cap;
   uint32_t *status;
-  uint32_t *n_items;  // cleared for the tile list of a masked binning, or null
-  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const { offs[i] = prefix; }
+  uint2 *ranges;
+  int ntiles;
+  const uint8_t *mask;  // null for a full binning
+  uint32_t *items, *n_items;
+  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const {
+    const uint32_t na = *n_chunks;
+    const uint32_t t = i / na, c = i % na;
+    offs[(size_t)t * nch + c] = prefix;
+    if (c != 0u) return;
+    const uint32_t p = min(prefix, cap);
+    ranges[t].x = p;
+    if (t > 0u) ranges[t - 1].y = p;
+    if (mask && mask[t]) items[atomicAdd(n_items, 1u)] = t;
+  }
   __device__ void end(uint32_t, uint32_t total) const {
     *n_inst = total;
     *n_sort = total < cap ? total : cap;
     if (total > cap) atomicOr(status, kStCapacity);
-    if (n_items) *n_items = 0u;
+    if (ntiles > 0) ranges[ntiles - 1].y = min(total, cap);
   }
 };
-
-// Tile ranges; a masked binning also lists its masked tiles (in any order: the
-// rasterizer's tiles are independent) for the persistent rasterizer.
-__global__ void bin_ranges_kernel(const uint32_t *__restrict__ offs, uint32_t nch, int ntiles,
-                                  const uint32_t *__restrict__ n_inst, uint32_t cap, uint2 *__restrict__ ranges,
-                                  const uint8_t *__restrict__ mask, uint32_t *__restrict__ items,
-                                  uint32_t *__restrict__ n_items) {
-  griddep_wait();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < ntiles) {
-    const uint32_t s0 = offs[(size_t)t * nch];
-    const uint32_t s1 = t + 1 < ntiles ? offs[(size_t)(t + 1) * nch] : *n_inst;
-    ranges[t] = make_uint2(min(s0, cap), min(s1, cap));
-  }
-  if (!mask) return;
-  const bool on = t < ntiles && mask[t] != 0;
-  const uint32_t ball = __ballot_sync(0xffffffffu, on);
-  const int lane = threadIdx.x & 31;
-  uint32_t base = 0;
-  if (lane == 0 && ball) base = atomicAdd(n_items, (uint32_t)__popc(ball));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (on) items[base + (uint32_t)__popc(ball & ((1u << lane) - 1u))] = (uint32_t)t;
-}
 
 uint32_t bin_warp_surfels(int max_surfels) {
   const uint32_t per = ((uint32_t)max_surfels + kBinWarps * 256 - 1) / (kBinWarps * 256);
@@ -739,34 +790,32 @@ cudaError_t prepare_binning(int max_tiles_x) {
 }
 
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
-                           const uint8_t *tile_mask, cudaStream_t s, int order) {
+                           const uint8_t *tile_mask, cudaStream_t s, int order, const uint8_t *roi16, int W,
+                           int H, int tshift) {
   const BinScratch &b = ws.bin[eye];
   cudaError_t err;
   Counters *ctr = ws.ctr;
   const int ntiles = tiles_x * tiles_y;
   const uint32_t cap = (uint32_t)ws.max_inst[eye];
   const RadixScratch rs{b.rs_hist, b.rs_hist + kRsPasses * 256, b.rs_status, b.rs_ctl, &ctr->status};
-  if (tile_mask) {
-    launch_k(mask_sat_kernel, 1, 1024, 0, s, tile_mask, tiles_x, tiles_y, b.mask_sat);
+  if (tile_mask) {  // (the rasterizer-grid mask and) its summed-area table
+    launch_k(mask_sat_kernel, 1, 1024, 0, s, const_cast<uint8_t *>(tile_mask), tiles_x, tiles_y, b.mask_sat, roi16,
+             (W + kTile - 1) / kTile, (H + kTile - 1) / kTile, roi16 ? tshift : 4);
     GS_LAUNCHED(1);
   }
+  const uint32_t chunk = kBinWarps * ws.bin_warp_surfels;
+  const BinCounts bc{&ctr->n_vis[eye], &ctr->n_rows[eye], &ctr->n_band[eye], &ctr->n_items[eye],
+                     &ctr->n_chunks[eye], &ctr->n_table[eye], chunk, (uint32_t)ntiles};
   // 1. compact the binned surfels: (depth bits, surfel id)
   const uint32_t *sat = tile_mask ? b.mask_sat : nullptr;
   if (order == kOrderReuse) {  // the dominant order, filtered: already depth-ordered
-    if (n > 0) {
-      launch_k(roi_flag_kernel, (n + 255) / 256, 256, 0, s, (const uint32_t *)ws.cnt[eye],
-               (const ushort4 *)ws.rect[eye], sat, tiles_x, (uint32_t)n, b.roi_flag);
-      GS_LAUNCHED(1);
-    }
-    err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, b.roi_flag},
-                      ReuseApply{ws.uval, ws.zkey[eye], b.dkey[0], b.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
-                                 &ctr->n_band[eye]},
+    err = scan_launch(ReuseLoad{ws.uval, &ctr->n_union, (uint32_t)n, ws.cnt[eye], ws.rect[eye], sat, tiles_x},
+                      ReuseApply{ws.uval, ws.zkey[eye], b.dkey[0], b.dval[0], bc},
                       (const uint32_t *)nullptr, (uint32_t)n, b.scan_tiles, b.scan_ticket, &ctr->status, s);
   } else {
     err = scan_launch(VisibleLoad{ws.cnt[eye], order == kOrderUnion ? ws.cnt[1 - eye] : nullptr, ws.rect[eye], sat,
                                   tiles_x},
-                      CompactApply{ws.zkey[eye], b.dkey[0], b.dval[0], &ctr->n_vis[eye], &ctr->n_rows[eye],
-                                   &ctr->n_band[eye]},
+                      CompactApply{ws.zkey[eye], b.dkey[0], b.dval[0], bc},
                       (const uint32_t *)nullptr, (uint32_t)n, b.scan_tiles, b.scan_ticket, &ctr->status, s);
   }
   if (err != cudaSuccess) return err;
@@ -776,7 +825,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
     launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, b.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
                                                 ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.prim, ws.row_off[eye],
                                                 ws.spans[eye], cap, &ctr->n_rows[eye],
-                                                &ctr->status);
+                                                &ctr->status, sat, tiles_x);
     GS_LAUNCHED(1);
   }
   // 3. depth order (the low 32 bits of the packed key; stable, so ties keep id order)
@@ -836,19 +885,16 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   // 5. per-warp counts per (tile, chunk)
   launch_k(bin_kernel, grid, kBinThreads, bin_smem_bytes(tiles_x) / 2, s, a, 0);
   GS_LAUNCHED(1);
-  // 6. tile-major scan: where every (tile, chunk) run starts
-  err = scan_launch(BinTableLoad{b.bin_table, &ctr->n_vis[eye], (uint32_t)n, ws.bin_nch,
-                                 kBinWarps * ws.bin_warp_surfels},
-                    BinOffsetApply{b.bin_offs, &ctr->n_inst[eye], &ctr->n_sort[eye], cap, &ctr->status,
-                                   tile_mask ? &ctr->n_items[eye] : nullptr},
-                    (const uint32_t *)nullptr, (uint32_t)ntiles * ws.bin_nch, b.scan_tiles, b.scan_ticket,
-                    &ctr->status, s);
+  // 6. tile-major scan over the chunks that hold binned surfels: where every
+  // (tile, chunk) run starts, every tile's range and, for a mask, the tile list
+  err = scan_launch(BinTableLoad{b.bin_table, &ctr->n_chunks[eye], &ctr->n_vis[eye], ws.bin_nch, chunk},
+                    BinOffsetApply{b.bin_offs, &ctr->n_chunks[eye], ws.bin_nch, &ctr->n_inst[eye], &ctr->n_sort[eye],
+                                   cap, &ctr->status, b.ranges, ntiles, tile_mask, b.items, &ctr->n_items[eye]},
+                    &ctr->n_table[eye], (uint32_t)ntiles * ws.bin_nch, b.scan_tiles, b.scan_ticket, &ctr->status, s);
   if (err != cudaSuccess) return err;
-  launch_k(bin_ranges_kernel, (ntiles + 255) / 256, 256, 0, s, b.bin_offs, ws.bin_nch, ntiles, &ctr->n_inst[eye], cap,
-                                                         b.ranges, tile_mask, b.items, &ctr->n_items[eye]);
   // 7. every surfel id to its slot
   launch_k(bin_kernel, grid, kBinThreads, bin_smem_bytes(tiles_x), s, a, 1);
-  GS_LAUNCHED(2);
+  GS_LAUNCHED(1);
   return cudaGetLastError();
 }
 

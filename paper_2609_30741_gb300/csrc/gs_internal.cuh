@@ -69,7 +69,9 @@ struct Counters {
   uint32_t n_union;      // surfels in the dominant binning's depth order (both eyes' visible set)
   uint32_t n_items[2];   // rasterizer tiles listed by the last masked binning per eye
   uint32_t prev_range[2];// float bits of the last measured depth range (reused by depth_mode 2)
-  uint32_t pad[1];
+  uint32_t n_chunks[2];  // binning chunks holding binned surfels, per eye (at least 1)
+  uint32_t n_table[2];   // (tile, chunk) entries the binning's table scan covers, per eye
+  uint32_t n_centre;     // centre-hole pixels listed by the classification
   unsigned long long pairs[2];    // evaluated (pixel, surfel) pairs per eye (counting mode)
   unsigned long long contrib[2];  // of which contributed (alpha >= 1/255, before termination)
 };
@@ -101,7 +103,6 @@ struct BinScratch {
   uint32_t *items;              // rasterizer tiles of the last masked binning
   uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
   uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
-  uint8_t *roi_flag;            // per surfel: binned and its rectangle holds a masked tile
   uint32_t *rs_hist;            // radix sort: [4][256] digit counts, then [4][256] digit bases
   unsigned long long *rs_status;// radix sort look-back words [tiles][256]
   uint32_t *rs_ctl;             // radix sort control words (zero at creation)
@@ -132,6 +133,7 @@ struct Workspace {
   float *warp_depth;
   uint8_t *cls;
   int32_t *labels;
+  uint32_t *cc_list;            // the frame's centre-hole pixels (classification order)
   uint32_t *slots;              // scan of component roots (+1)
   int4 *rects;                  // centre ROI rectangles
   int32_t *strips;              // [4][4]
@@ -141,6 +143,7 @@ struct Workspace {
   float *rp_master, *rp_grad, *rp_m, *rp_v;  // FP32 parameters, gradients, AdamW moments
   uint8_t *rp_wpack;            // BF16 B-operand images of the six layers
   uint8_t *rp_wpack8;           // FP8 (e4m3) B-operand images
+  uint8_t *rp_wpackT;           // BF16 flipped, transposed images of layers 1-5 (input gradients)
   float *rp_sx, *rp_sw;         // FP8 input scales and output-channel weight scales, [6][32] each
   uint32_t *rp_amax;            // calibration maxima of the layer inputs [6][32]
   float *rp_bias;               // [6][32]
@@ -194,8 +197,13 @@ cudaError_t launch_preprocess(const gs_scene &sc, Workspace &ws, int neyes, int 
 //                 a parallel rig both eyes' depth keys are identical, so the
 //                 filtered order is the affiliated (depth, index) order.
 enum BinOrder { kOrderOwn = 0, kOrderUnion = 1, kOrderReuse = 2 };
+// roi16 (with W x H the image and tshift the rasterizer's log2 tile edge): the
+// ROI mask on the 16-pixel grid from which the binning derives its own mask on
+// the rasterizer grid into tile_mask (then ws.bin[eye].rmask); null when
+// tile_mask is given directly (or no mask).
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
-                           const uint8_t *tile_mask, cudaStream_t s, int order = kOrderOwn);
+                           const uint8_t *tile_mask, cudaStream_t s, int order = kOrderOwn,
+                           const uint8_t *roi16 = nullptr, int W = 0, int H = 0, int tshift = 4);
 // Chunk geometry of the binning for a surfel capacity, and the one-time
 // shared-memory opt-in of its kernel for the widest image.
 uint32_t bin_warp_surfels(int max_surfels);
@@ -219,6 +227,7 @@ struct RepairOpt {
   int step;
 };
 cudaError_t prepare_repair();
+cudaError_t prepare_reproject();
 size_t repair_train_scratch_bytes(int n_tiles);
 cudaError_t repair_pack(const Workspace &ws, cudaStream_t s);
 // Features from the warp buffer and the affiliated image after hole
@@ -286,9 +295,6 @@ cudaError_t launch_raster(const RasterTable &t, const RasterConfig &c, bool coun
 // masked pass (the listed tiles of the last masked binning), or null.
 RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift, const uint8_t *mask, float3 bg,
                          float *rgb, float *depth, float *trans, uint8_t *cls, bool stats);
-// ROI mask (16-pixel grid) -> rasterizer grid of tile edge 1 << tshift (a tile is
-// masked when it holds a masked pixel).
-cudaError_t launch_raster_mask(const uint8_t *roi, int W, int H, int tshift, uint8_t *rmask, cudaStream_t s);
 // Mean SSIM of a [C][H][W] image against a reference (11 x 11 Gaussian window,
 // zero padding) into *out (device); part: ssim_partials() doubles.
 size_t ssim_partials(int max_w, int max_h);

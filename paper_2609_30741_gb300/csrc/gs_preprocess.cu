@@ -70,8 +70,8 @@ cudaError_t launch_setup_cams(const PoseArgs &pa, CamBlock *cams, cudaStream_t s
 // Real spherical harmonics up to degree 3 (3DGS sign convention). Constants are
 // the closed forms sqrt((2l+1)/(4 pi) (l-|m|)!/(l+|m|)!) times each polynomial's
 // normalisation, written out to float precision.
-__device__ __forceinline__ void sh_rgb(const float *__restrict__ c, int deg, float x, float y, float z,
-                                       float out[3]) {
+template <int DEG>
+__device__ __forceinline__ void sh_basis(float x, float y, float z, float b[16]) {
   const float Y00 = 0.28209479177387814f;        // 1 / (2 sqrt(pi))
   const float Y1 = 0.48860251190291992f;         // sqrt(3 / (4 pi))
   const float Y2a = 1.0925484305920792f;         // sqrt(15 / pi) / 2
@@ -82,19 +82,15 @@ __device__ __forceinline__ void sh_rgb(const float *__restrict__ c, int deg, flo
   const float Y3c = 0.45704579946446572f;        // sqrt(21 / (2 pi)) / 4
   const float Y3d = 0.37317633259011540f;        // sqrt(7 / pi) / 4
   const float Y3e = 1.4453057213202769f;         // sqrt(105 / pi) / 4
-  float b[16];
   b[0] = Y00;
-  int K = 1;
-  if (deg >= 1) {
+  if (DEG >= 1) {
     b[1] = -Y1 * y; b[2] = Y1 * z; b[3] = -Y1 * x;
-    K = 4;
   }
-  if (deg >= 2) {
+  if (DEG >= 2) {
     const float xx = x * x, yy = y * y, zz = z * z;
     b[4] = Y2a * x * y; b[5] = -Y2a * y * z; b[6] = Y2b * (2.f * zz - xx - yy);
     b[7] = -Y2a * x * z; b[8] = Y2c * (xx - yy);
-    K = 9;
-    if (deg >= 3) {
+    if (DEG >= 3) {
       b[9] = -Y3a * y * (3.f * xx - yy);
       b[10] = Y3b * x * y * z;
       b[11] = -Y3c * y * (4.f * zz - xx - yy);
@@ -102,41 +98,58 @@ __device__ __forceinline__ void sh_rgb(const float *__restrict__ c, int deg, flo
       b[13] = -Y3c * x * (4.f * zz - xx - yy);
       b[14] = Y3e * z * (xx - yy);
       b[15] = -Y3a * x * (xx - 3.f * yy);
-      K = 16;
     }
   }
-  float r = 0.5f, g = 0.5f, bl = 0.5f;
-  for (int k = 0; k < K; ++k) {
-    r = fmaf(b[k], c[3 * k + 0], r);
-    g = fmaf(b[k], c[3 * k + 1], g);
-    bl = fmaf(b[k], c[3 * k + 2], bl);
-  }
-  out[0] = fmaxf(r, 0.f);
-  out[1] = fmaxf(g, 0.f);
-  out[2] = fmaxf(bl, 0.f);
 }
 
-// The SH coefficients of primitive i into registers (float4 loads at degree 3).
-__device__ __forceinline__ void load_sh(const gs_scene &sc, int i, float shc[48]) {
-  const int K = (sc.sh_degree + 1) * (sc.sh_degree + 1);
-  const float *src = sc.sh + (size_t)i * K * 3;
-  if (sc.sh_degree == 3) {
-    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+// Both eyes' colours of primitive i centred at p: max(0, 0.5 + sum_k Y_k(dir)
+// c_k) with dir the unit vector from the eye's centre to p. The coefficients
+// are streamed once from memory (float4 loads at degree 3, whose 48 floats per
+// primitive keep the alignment the scene check demands) and every index is a
+// compile-time constant, so
+// nothing goes through local memory; each channel's sum runs in the order k = 0,
+// 1, ... for both eyes.
+template <int DEG>
+__device__ __forceinline__ void sh_colours(const gs_scene &sc, int i, bool load, const CamBlock *cams, int neyes,
+                                           float4 p, float rgb[2][3]) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  float b[2][16];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      const float4 v = s4[k];
-      shc[4 * k] = v.x; shc[4 * k + 1] = v.y; shc[4 * k + 2] = v.z; shc[4 * k + 3] = v.w;
-    }
-  } else {
-    for (int k = 0; k < 3 * K; ++k) shc[k] = src[k];
+  for (int e = 0; e < 2; ++e) {
+    const EyeCam &c = cams->eye[e < neyes ? e : 0];
+    const float dx = p.x - c.centre[0], dy = p.y - c.centre[1], dz = p.z - c.centre[2];
+    const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+    sh_basis<DEG>(dx * dn, dy * dn, dz * dn, b[e]);
   }
-}
-
-// Colour of a primitive centred at p seen from the eye's centre.
-__device__ __forceinline__ void view_rgb(const float *shc, int deg, const EyeCam &c, float4 p, float rgb[3]) {
-  float dx = p.x - c.centre[0], dy = p.y - c.centre[1], dz = p.z - c.centre[2];
-  const float dn = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-  sh_rgb(shc, deg, dx * dn, dy * dn, dz * dn, rgb);
+  float acc[2][3] = {{0.5f, 0.5f, 0.5f}, {0.5f, 0.5f, 0.5f}};
+  const float *src = sc.sh + (size_t)i * K * 3;
+  if (load) {
+    if (DEG == 3) {  // 48 floats: the scene's SH array is 16-byte aligned at degree 3
+      const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+      for (int m = 0; m < 3 * K / 4; ++m) {
+        const float4 v = s4[m];
+        const float cf[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int j = 4 * m + u;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) acc[e][j % 3] = fmaf(b[e][j / 3], cf[u], acc[e][j % 3]);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3 * K; ++j) {
+        const float cf = src[j];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) acc[e][j % 3] = fmaf(b[e][j / 3], cf, acc[e][j % 3]);
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 2; ++e)
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) rgb[e][ch] = fmaxf(acc[e][ch], 0.f);
 }
 
 // Tile rectangle of the pixels whose centres lie inside [xmin, xmax] x
@@ -170,6 +183,7 @@ __device__ __forceinline__ uint32_t tile_rect(const EyeCam &c, float xmin, float
 // Bz = (V0 M21 - V1 M20)/p_z, Cz = (M20 U1 - M21 U0)/p_z, so u = p.x/p.z,
 // v = p.y/p.z. Expanding around c keeps the terms small (well conditioned).
 // The intersection depth is z = M20 u + M21 v + p_z.
+template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamBlock *__restrict__ cams,
                                                          Workspace ws, int neyes) {
   griddep_wait();
@@ -190,9 +204,11 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
   const float rc2 = alive ? 2.f * logf(255.f * o) : 0.f;
   const float rc = sqrtf(fmaxf(rc2, 0.f));
   const float lp = sqrtf(fmaxf(0.5f * rc2, 0.f));  // low-pass support radius, pixels
-  float shc[48];
-  if (alive) load_sh(sc, i, shc);
-  for (int e = 0; e < neyes; ++e) {
+  float rgbs[2][3];
+  sh_colours<DEG>(sc, i, alive, cams, neyes, p4, rgbs);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    if (e >= neyes) break;
     const EyeCam &c = cams->eye[e];
     bool vis = alive;
     float pc[3], tuc[3], tvc[3];
@@ -244,8 +260,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
     const float Bz = fmaf(V0, M2[1], -V1 * M2[0]) * izc;
     const float Cz = fmaf(M2[0], U1, -M2[1] * U0) * izc;
     // view-dependent colour from this eye's centre
-    float rgb[3];
-    view_rgb(shc, sc.sh_degree, c, p4, rgb);
+    const float *rgb = rgbs[e];
     float4 *r = ws.rec[e] + 4 * (size_t)i;
     r[0] = make_float4(cxp, cyp, rc2, pc[2]);
     r[1] = make_float4(V1, -V0, -U1, U0);
@@ -269,6 +284,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
 // slopes, so the rasterizer's u^2 + v^2 is d^T Q d and its depth the centre's.
 // The support d^T Q d <= 2 ln(255 o) has the half extents sqrt(k cxx) and
 // sqrt(k cyy).
+template <int DEG>
 __global__ void __launch_bounds__(256) preprocess_ellipsoid_kernel(gs_scene sc, const CamBlock *__restrict__ cams,
                                                                    Workspace ws, int neyes) {
   griddep_wait();
@@ -288,9 +304,11 @@ __global__ void __launch_bounds__(256) preprocess_ellipsoid_kernel(gs_scene sc, 
       {s4.y * 2.f * (x * y - w * z), s4.y * (1.f - 2.f * (x * x + z * z)), s4.y * 2.f * (y * z + w * x)},
       {s4.z * 2.f * (x * z + w * y), s4.z * 2.f * (y * z - w * x), s4.z * (1.f - 2.f * (x * x + y * y))}};
   const float rc2 = alive ? 2.f * logf(255.f * o) : 0.f;
-  float shc[48];
-  if (alive) load_sh(sc, i, shc);
-  for (int e = 0; e < neyes; ++e) {
+  float rgbs[2][3];
+  sh_colours<DEG>(sc, i, alive, cams, neyes, p4, rgbs);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    if (e >= neyes) break;
     const EyeCam &c = cams->eye[e];
     float pc[3];
 #pragma unroll
@@ -335,8 +353,7 @@ __global__ void __launch_bounds__(256) preprocess_ellipsoid_kernel(gs_scene sc, 
     const float l00 = sqrtf(cyy / det);
     const float l01 = -cxy / sqrtf(det * cyy);
     const float l11 = rsqrtf(cyy);
-    float rgb[3];
-    view_rgb(shc, sc.sh_degree, c, p4, rgb);
+    const float *rgb = rgbs[e];
     float4 *r = ws.rec[e] + 4 * (size_t)i;
     r[0] = make_float4(cxp, cyp, rc2, pc[2]);
     r[1] = make_float4(l00, 0.f, l01, l11);
@@ -349,10 +366,17 @@ cudaError_t launch_preprocess(const gs_scene &sc, Workspace &ws, int neyes, int 
   (void)W; (void)H;
   ws.prim = sc.primitive;
   if (sc.n == 0) return cudaSuccess;
-  if (sc.primitive == 1)
-    launch_k(preprocess_ellipsoid_kernel, (sc.n + 255) / 256, 256, 0, s, sc, ws.cams, ws, neyes);
-  else
-    launch_k(preprocess_kernel, (sc.n + 255) / 256, 256, 0, s, sc, ws.cams, ws, neyes);
+  const int g = (sc.n + 255) / 256;
+  switch (sc.sh_degree + 4 * (sc.primitive == 1)) {
+    case 0: launch_k(preprocess_kernel<0>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+    case 1: launch_k(preprocess_kernel<1>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+    case 2: launch_k(preprocess_kernel<2>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+    case 3: launch_k(preprocess_kernel<3>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+    case 4: launch_k(preprocess_ellipsoid_kernel<0>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+    case 5: launch_k(preprocess_ellipsoid_kernel<1>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+    case 6: launch_k(preprocess_ellipsoid_kernel<2>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+    default: launch_k(preprocess_ellipsoid_kernel<3>, g, 256, 0, s, sc, ws.cams, ws, neyes); break;
+  }
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }

@@ -305,27 +305,6 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
   }
 }
 
-// ROI mask (16-pixel grid) -> rasterizer grid of tile edge 1 << tshift.
-__global__ void raster_mask_kernel(const uint8_t *__restrict__ roi, int rtx, int rty, int tx, int ty, int tshift,
-                                   uint8_t *__restrict__ out) {
-  griddep_wait();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= tx * ty) return;
-  const int x = t % tx, y = t / tx;
-  uint8_t v = 0;
-  if (tshift <= 4) {
-    v = roi[(y >> (4 - tshift)) * rtx + (x >> (4 - tshift))];
-  } else {
-    const int s = 1 << (tshift - 4);
-    for (int dy = 0; dy < s; ++dy)
-      for (int dx = 0; dx < s; ++dx) {
-        const int yy = y * s + dy, xx = x * s + dx;
-        if (yy < rty && xx < rtx) v |= roi[yy * rtx + xx];
-      }
-  }
-  out[t] = v ? 1 : 0;
-}
-
 // ---------------------------------------------------------------- host side
 
 namespace {
@@ -456,14 +435,5 @@ RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift,
   return f;
 }
 
-cudaError_t launch_raster_mask(const uint8_t *roi, int W, int H, int tshift, uint8_t *rmask, cudaStream_t s) {
-  const int ts = 1 << tshift;
-  const int rtx = (W + kTile - 1) / kTile, rty = (H + kTile - 1) / kTile;
-  const int tx = (W + ts - 1) >> tshift, ty = (H + ts - 1) >> tshift;
-  if (tx * ty == 0) return cudaSuccess;
-  launch_k(raster_mask_kernel, (tx * ty + 255) / 256, 256, 0, s, roi, rtx, rty, tx, ty, tshift, rmask);
-  GS_LAUNCHED(1);
-  return cudaGetLastError();
-}
 
 }  // namespace gs

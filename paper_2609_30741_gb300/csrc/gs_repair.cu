@@ -22,8 +22,15 @@
 // apply ReLU and the image-border zeroing, and store BF16 for the next layer.
 //
 // Training runs the same forward kernel (keeping every layer's input), then a
-// loss kernel, data-parallel FP32 weight- and input-gradient kernels and AdamW
-// on FP32 master weights.
+// loss kernel, and per layer (last to first) one backward kernel on the tensor
+// cores: the input gradient is the full convolution of the output gradient with
+// the flipped, transposed weights (the forward's implicit GEMM with another
+// weight image and the ReLU derivative in the epilogue), and the weight
+// gradient is a GEMM over positions per 3x3 tap (M = c_out, N = c_in, K = the
+// tile's positions, the tap again a shift of an operand's start address),
+// accumulated in tensor memory over all tiles a CTA takes; the CTAs' partial
+// sums are reduced in a fixed order (no atomics, so a step is deterministic).
+// AdamW updates the FP32 master weights.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
@@ -39,7 +46,6 @@ constexpr int kRT = 16;                 // output tile edge
 constexpr int kHalo = 6;                // receptive-field radius of six 3x3 layers
 constexpr int kGW = kRT + 2 * kHalo;    // 28: width of the position grid
 constexpr int kNPos = 832;              // positions per activation buffer (6 M tiles + tap reach)
-constexpr int kQ = 26 * kGW;            // gradient grid: rows < 26 of any layer >= 1 output
 constexpr int kNetThreads = 256;  // two warpgroups take alternate M tiles of the epilogue
 constexpr int kTmemCols = 256;
 
@@ -75,6 +81,31 @@ static_assert(kWPack8Bytes == 50688, "packed FP8 weight image size");
 static_assert(poff(6) == kRepairParams, "parameter count");
 static_assert(mtiles(0) <= kMaxMT, "M tiles per layer");
 static_assert(kMaxMT <= kNetThreads / 32, "one issuing warp per M tile");
+// backward: the input gradient of layer l (l >= 1) convolves dY_l, stored kDPad
+// positions later in shared memory, with the flipped transposed weights
+// W'[tap'][c_out group][c_in group][8 c_in][8 c_out] (W' at tap' = W at 8 - tap')
+constexpr int kDPad = 2 * kGW + 2;
+__host__ __device__ constexpr int kgd(int l) { return l == 5 ? 2 : 4; }  // c_out groups, padded to K = 16
+__host__ __device__ constexpr int wbytesT(int l) { return l == 0 ? 0 : 9 * kgd(l) * 4 * 128; }
+__host__ __device__ constexpr int woffT(int l) {
+  int o = 0;
+  for (int i = 1; i < l; ++i) o += wbytesT(i);
+  return o;
+}
+constexpr int kWPackTBytes = woffT(6);
+static_assert(kWPackTBytes == 82944, "packed transposed weight image size");
+__host__ __device__ constexpr int vrows(int l) { return kGW - 2 * (l + 1); }            // layer l's output edge
+__host__ __device__ constexpr int kchunks(int l) { return (vrows(l) * kGW + 15) / 16; }  // weight-gradient K = 16 steps
+constexpr int kBwdThreads = 256;
+constexpr int kBwdTmemCols = 512;   // 9 taps x 32 (weight gradient) + 6 M tiles x 32 (input gradient)
+constexpr int kBufT = (kchunks(0) + 2) * 1024;  // dY^T, plus the reach of the padded A rows
+constexpr int kBwdParts = 32 * 9 * 32 + 32;     // largest layer: weight and bias gradients
+static_assert(9 * 32 + kMaxMT * 32 <= kBwdTmemCols, "tensor memory of the backward");
+static_assert(kchunks(0) * 16 + 2 * kGW + 2 <= kNPos && kMaxMT * 128 + 2 * kGW + 2 <= kNPos,
+              "backward operand reach");
+__host__ __device__ constexpr size_t bwd_smem() {
+  return 128 + 2 * (size_t)(4 * kNPos * 16) + kBufT + wbytesT(1) + (8 * 32 + 32) * 4 + 2 * 8 + 16;
+}
 static_assert(kMaxMT * 128 + 2 * kGW + 2 <= kNPos, "activation buffer reach");
 // shared memory of the network kernel: two activation buffers, the weight image,
 // bias, FP8 scales, barriers, reductions and calibration maxima
@@ -112,6 +143,23 @@ __global__ void repair_pack_kernel(const float *__restrict__ master, uint16_t *_
   if (co < cout(l) && ci < cin(l)) v = master[poff(l) + (co * 9 + tap) * cin(l) + ci];
   const __nv_bfloat16 h = __float2bfloat16_rn(v);
   wpack[e] = *reinterpret_cast<const uint16_t *>(&h);
+}
+
+// FP32 master -> the backward's BF16 images of layers 1-5 (see kDPad): element
+// [tap'][c_out group][c_in group][8 c_in][8 c_out] = W[c_out][8 - tap'][c_in].
+__global__ void repair_packT_kernel(const float *__restrict__ master, uint16_t *__restrict__ wpackT) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= kWPackTBytes / 2) return;
+  int l = 1;
+  while (l < 5 && e >= woffT(l + 1) / 2) ++l;
+  const int r = e - woffT(l) / 2;
+  const int kg = kgd(l);
+  const int co8 = r % 8, ci8 = (r / 8) % 8, ngi = (r / 64) % 4, kgi = (r / 256) % kg, tp = r / (256 * kg);
+  const int co = kgi * 8 + co8, ci = ngi * 8 + ci8, tap = 8 - tp;
+  float v = 0.f;
+  if (co < cout(l) && ci < cin(l)) v = master[poff(l) + (co * 9 + tap) * cin(l) + ci];
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  wpackT[e] = *reinterpret_cast<const uint16_t *>(&h);
 }
 
 // ---------------------------------------------------------------- features
@@ -570,9 +618,8 @@ struct TrainArgs {
   int n;
   const float *out4;       // [n][4][16][16]
   const float *gate;       // [n]
-  float *dy;               // [n][32][kQ] gradient of the current layer's output
-  float *dx;               // [n][32][kQ]
-  float *tile_stats;       // [n][4]: net MSE, plain MSE, holes, pixels
+  uint4 *dy;               // [n][4 groups][kNPos] BF16 gradient of the last layer's output
+  float *tile_stats;       // [n][8]: net MSE, plain MSE, holes, pixels, L1 sum, BCE, label
   float *sums;             // [8]: holes, L1 sum, BCE sum, labels, ...
   float lam;
 };
@@ -620,107 +667,316 @@ __global__ void __launch_bounds__(256) repair_stats_kernel(TrainArgs a) {
     float s[5] = {0, 0, 0, 0, 0};
     for (int ww = 0; ww < 8; ++ww)
       for (int k = 0; k < 5; ++k) s[k] += wred[ww][k];
-    a.tile_stats[t * 4 + 0] = s[2] > 0.f ? s[0] / (3.f * s[2]) : 1.f;  // a tile without holes never passes
-    a.tile_stats[t * 4 + 1] = s[2] > 0.f ? s[1] / (3.f * s[2]) : 0.f;
-    a.tile_stats[t * 4 + 2] = s[2];
-    a.tile_stats[t * 4 + 3] = s[3];
-    atomicAdd(&a.sums[0], s[2]);
-    atomicAdd(&a.sums[1], s[4]);
+    a.tile_stats[t * 8 + 0] = s[2] > 0.f ? s[0] / (3.f * s[2]) : 1.f;  // a tile without holes never passes
+    a.tile_stats[t * 8 + 1] = s[2] > 0.f ? s[1] / (3.f * s[2]) : 0.f;
+    a.tile_stats[t * 8 + 2] = s[2];
+    a.tile_stats[t * 8 + 3] = s[3];
+    a.tile_stats[t * 8 + 4] = s[4];
+  }
+}
+
+// sums[s0] and sums[s0 + 1] = the sums over tiles of tile_stats[t][fa] and
+// [t][fb], in a fixed order (one block: thread i takes tiles i, i + 1024, ...,
+// then a tree), so a training step's loss terms do not depend on scheduling.
+__global__ void __launch_bounds__(1024) repair_sums_kernel(const float *__restrict__ tile_stats, int n, int fa, int fb,
+                                                           float *__restrict__ sums, int s0) {
+  __shared__ float red[1024];
+  for (int k = 0; k < 2; ++k) {
+    const int f = k ? fb : fa;
+    float v = 0.f;
+    for (int t = threadIdx.x; t < n; t += 1024) v += tile_stats[t * 8 + f];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+      if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[s0 + k] = red[0];
+    __syncthreads();
   }
 }
 
 __device__ __forceinline__ float psnr_of(float mse) { return mse > 0.f ? -10.f * log10f(mse) : 1e9f; }
 
-// dL/d(output) of the last layer on its 28-wide grid (rows < 16, cols < 16)
+// dL/d(output) of the last layer on its 28-wide grid (rows < 16, cols < 16), as
+// the BF16 operand of the backward: channel group 0 holds the 4 outputs, the
+// other groups and every other position are zero
 __global__ void __launch_bounds__(256) repair_dout_kernel(TrainArgs a) {
   const int t = blockIdx.x;
   const uint32_t te = a.tiles[t];
   const int frame = (int)(te >> 24), ty0 = (int)((te >> 12) & 0xfffu) * kRT, tx0 = (int)(te & 0xfffu) * kRT;
-  float *dy = a.dy + (size_t)t * 32 * kQ;
-  for (int i = threadIdx.x; i < 32 * kQ; i += 256) dy[i] = 0.f;
-  __syncthreads();
-  const float net_psnr = psnr_of(a.tile_stats[t * 4 + 0]), plain_psnr = psnr_of(a.tile_stats[t * 4 + 1]);
+  uint4 *dy = a.dy + (size_t)t * 4 * kNPos;
+  const float net_psnr = psnr_of(a.tile_stats[t * 8 + 0]), plain_psnr = psnr_of(a.tile_stats[t * 8 + 1]);
   // positive: the fill reaches 30 dB at the tile's holes and loses at most 0.5 dB
   // against the plain image there (exactly the re-render inside the edge strips,
   // so strip tiles stay negative)
   const float label = (net_psnr >= plain_psnr - 0.5f && net_psnr >= 30.f) ? 1.f : 0.f;
   const float p = 1.f / (1.f + expf(-a.gate[t]));
-  const float npx = a.tile_stats[t * 4 + 3];
+  const float npx = a.tile_stats[t * 8 + 3];
   const float nh_total = fmaxf(a.sums[0], 1.f);
-  const int r = threadIdx.x >> 4, c = threadIdx.x & 15, y = ty0 + r, x = tx0 + c;
   if (threadIdx.x == 0) {
-    atomicAdd(&a.sums[2], -(label * logf(p + 1e-12f) + (1.f - label) * logf(1.f - p + 1e-12f)));
-    atomicAdd(&a.sums[3], label);
+    a.tile_stats[t * 8 + 5] = -(label * logf(p + 1e-12f) + (1.f - label) * logf(1.f - p + 1e-12f));
+    a.tile_stats[t * 8 + 6] = label;
   }
-  if (y >= a.H || x >= a.W) return;
-  const size_t hw = (size_t)a.W * a.H, pix = (size_t)y * a.W + x;
-  const uint4 f = a.feat[(size_t)frame * hw + pix];
-  const bool hole = bf16_lo(f.z) > 0.5f;
-  const int q = r * kGW + c;
-  const float base[3] = {bf16_lo(f.x), bf16_hi(f.x), bf16_lo(f.y)};
-  for (int ch = 0; ch < 3; ++ch) {
-    const float o = base[ch] + a.out4[(size_t)t * 4 * kRT * kRT + ch * kRT * kRT + r * kRT + c];
-    const float tg = a.target[(size_t)frame * 3 * hw + ch * hw + pix];
-    const float d = o - tg;
-    dy[ch * kQ + q] = hole ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (3.f * nh_total) : 0.f;
-  }
-  dy[3 * kQ + q] = a.lam * (p - label) / ((float)a.n * npx);
-}
-
-// X_l[ci][p] of tile t from the stored BF16 layer input
-__device__ __forceinline__ float act_at(const uint4 *acts, size_t t, int l, int ci, int p) {
-  const uint16_t *v = (const uint16_t *)(acts + ((t * 6 + l) * 4 + ci / 8) * kNPos + p);
-  return __uint_as_float((uint32_t)v[ci % 8] << 16);
-}
-
-// dW[l][co][tap][ci] and db: one block per (tile, co); threads over (tap, ci)
-__global__ void __launch_bounds__(288) repair_wgrad_kernel(const uint4 *__restrict__ acts,
-                                                           const float *__restrict__ dy, int l, int rows,
-                                                           float *__restrict__ grad) {
-  const size_t t = blockIdx.x / 32;
-  const int co = blockIdx.x % 32;
-  if (co >= cout(l)) return;
-  const int tap = threadIdx.x / 32, ci = threadIdx.x % 32;
-  const float *g = dy + (t * 32 + co) * kQ;
-  const int shift = (tap / 3) * kGW + (tap % 3);
-  float acc = 0.f, bacc = 0.f;
-  if (ci < cin(l)) {
-    for (int q = 0; q < rows * kGW; ++q) {
-      const float d = g[q];
-      if (d != 0.f) acc = fmaf(d, act_at(acts, t, l, ci, q + shift), acc);
+  const size_t hw = (size_t)a.W * a.H;
+  for (int q = threadIdx.x; q < kNPos; q += blockDim.x) {
+    float g[4] = {0.f, 0.f, 0.f, 0.f};
+    const int r = q / kGW, c = q % kGW, y = ty0 + r, x = tx0 + c;
+    if (r < kRT && c < kRT && y < a.H && x < a.W) {
+      const size_t pix = (size_t)y * a.W + x;
+      const uint4 f = a.feat[(size_t)frame * hw + pix];
+      const bool hole = bf16_lo(f.z) > 0.5f;
+      const float base[3] = {bf16_lo(f.x), bf16_hi(f.x), bf16_lo(f.y)};
+      for (int ch = 0; ch < 3; ++ch) {
+        const float o = base[ch] + a.out4[(size_t)t * 4 * kRT * kRT + ch * kRT * kRT + r * kRT + c];
+        const float d = o - a.target[(size_t)frame * 3 * hw + ch * hw + pix];
+        g[ch] = hole ? (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) / (3.f * nh_total) : 0.f;
+      }
+      g[3] = a.lam * (p - label) / ((float)a.n * npx);
     }
-    atomicAdd(&grad[poff(l) + (co * 9 + tap) * cin(l) + ci], acc);
-  }
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < rows * kGW; ++q) bacc += g[q];
-    atomicAdd(&grad[poff(l) + cout(l) * 9 * cin(l) + co], bacc);
+    dy[q] = make_uint4(pack_bf16(g[0], g[1]), pack_bf16(g[2], g[3]), 0u, 0u);
+    for (int grp = 1; grp < 4; ++grp) dy[grp * kNPos + q] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
-// dX of layer l's input (= layer l-1's output) on its valid window, times the
-// ReLU derivative (the stored activation is 0 where ReLU or the border cut it)
-__global__ void __launch_bounds__(256) repair_dgrad_kernel(const uint4 *__restrict__ acts,
-                                                           const float *__restrict__ dy,
-                                                           const float *__restrict__ master, int l, int rows_out,
-                                                           int n, float *__restrict__ dx) {
-  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t total = (size_t)n * 32 * kQ;
-  if (i >= total) return;
-  const size_t t = i / (32 * kQ);
-  const int ci = (int)((i / kQ) % 32), p = (int)(i % kQ);
-  const int valid = kGW - 2 * l;  // layer l's input window edge
-  const int r = p / kGW, c = p % kGW;
-  float s = 0.f;
-  if (ci < cin(l) && r < valid && c < valid && act_at(acts, t, l, ci, p) > 0.f) {
-    const float *w = master + poff(l);
+// ---------------------------------------------------------------- backward
+struct BwdArgs {
+  const uint4 *acts;       // [n][6][4 groups][kNPos]: every layer's BF16 input (forward)
+  const uint4 *dy;         // [n][4][kNPos]: BF16 dL/d(output of layer l), zero outside its window
+  uint4 *dyo;              // [n][4][kNPos]: BF16 dL/d(output of layer l - 1) (l >= 1)
+  const uint8_t *wpackT;   // the transposed image of layer l
+  float *part;             // [gridDim][cout(l) * 9 * cin(l) + cout(l)] weight and bias gradients per CTA
+  int l, n;
+  uint32_t *status;
+};
+
+// One layer of the backward pass on the tensor cores; a CTA takes tiles
+// blockIdx.x, + gridDim.x, ... Per tile:
+//   weight gradient: for each tap, D_tap[c_out][c_in] += sum over positions q of
+//     dY[c_out][q] x[c_in][q + shift(tap)]: A = dY^T (K-major, K = positions,
+//     M = 128 rows of which the first c_out are real; the other rows read the next
+//     positions' data and are never used), B = x shifted (MN-major: the 8 c_in of a
+//     position are contiguous), 16 positions per MMA. D_tap stays in tensor
+//     memory across the CTA's tiles and goes to the CTA's partial sums at the end.
+//   input gradient (l >= 1): dX[p][c_in] = sum over tap', c_out of dY[c_out]
+//     [p + shift(tap') - kDPad] W[c_out][8 - tap'][c_in] (the forward's implicit
+//     GEMM on dY stored kDPad positions later), times the ReLU derivative (the
+//     stored input x > 0) inside layer l's input window, stored as BF16 dY of
+//     layer l - 1.
+// Warp 0 issues the weight-gradient MMAs, warp 1 the input-gradient MMAs, each
+// committing to its own barrier; every wait is bounded.
+__global__ void __launch_bounds__(kBwdThreads, 1) repair_bwd_kernel(BwdArgs a) {
+  extern __shared__ uint8_t s_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)s_raw + 127) & ~(uintptr_t)127);
+  constexpr int kBuf = 4 * kNPos * 16;
+  uint8_t *bufD = smem;              // dY at positions + kDPad: input-gradient A
+  uint8_t *bufX = smem + kBuf;       // x_l: weight-gradient B, ReLU derivative
+  uint8_t *bufT = smem + 2 * kBuf;   // dY^T [8-position group][c_out group][8 c_out][8 positions]
+  uint8_t *wsm = bufT + kBufT;
+  float *s_part = (float *)(wsm + wbytesT(1));  // [8 warps][32]
+  float *s_db = s_part + 8 * 32;                // [32] bias gradient over the CTA's tiles
+  uint64_t *mbar = (uint64_t *)(s_db + 32);     // weight gradient, input gradient
+  uint32_t *s_taddr = (uint32_t *)(mbar + 2);
+  const int l = a.l;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int wq = wid & 3, wg = wid >> 2;
+  const int ci_n = cin(l), co_n = cout(l);
+  const int NW = l == 0 ? 16 : 32;            // weight-gradient N: c_in padded to 16
+  const int nK = kchunks(l);
+  const int MT = l > 0 ? mtiles(l - 1) : 0;   // input-gradient M tiles: layer l's input window
+  const int vin = kGW - 2 * l, vout = vrows(l);
+  const int kg = kgd(l);
+  constexpr uint32_t kColG = 9 * 32;          // first input-gradient column
+  {
+    if (l > 0) {
+      const uint4 *src = (const uint4 *)(a.wpackT + woffT(l));
+      for (int i = tid; i < wbytesT(l) / 16; i += kBwdThreads) ((uint4 *)wsm)[i] = src[i];
+    }
+    for (int i = tid; i < kBuf / 16; i += kBwdThreads) ((uint4 *)bufD)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < kBufT / 16; i += kBwdThreads) ((uint4 *)bufT)[i] = make_uint4(0, 0, 0, 0);
+    if (tid < 32) s_db[tid] = 0.f;
+    if (tid < 2) umma::mbar_init(mbar + tid, 1);
+    if (wid == 0) {
+      umma::tmem_alloc(s_taddr, kBwdTmemCols);
+      umma::tmem_relinquish();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+  }
+  const uint32_t taddr = *s_taddr;
+  const uint32_t sD = umma::smem_u32(bufD), sX = umma::smem_u32(bufX), sT = umma::smem_u32(bufT),
+                 sW = umma::smem_u32(wsm);
+  uint32_t ph_w = 0, ph_g = 0;
+  bool failed = false, any = false;
+  for (int t = blockIdx.x; t < a.n && !failed; t += gridDim.x) {
+    // operands of this tile (the previous tile's MMAs have completed)
+    const uint4 *xs = a.acts + ((size_t)t * 6 + l) * 4 * kNPos;
+    for (int i = tid; i < 4 * kNPos; i += kBwdThreads) ((uint4 *)bufX)[i] = xs[i];
+    const uint4 *ds = a.dy + (size_t)t * 4 * kNPos;
+    for (int i = tid; i < 4 * nK * 16; i += kBwdThreads) {
+      const int g = i / (nK * 16), q = i % (nK * 16);
+      ((uint4 *)bufD)[g * kNPos + kDPad + q] = ds[g * kNPos + q];
+    }
+    // dY^T: every 8-position x 8-channel block transposed through registers
+    for (int i = tid; i < 2 * nK * 4; i += kBwdThreads) {
+      const int pg = i >> 2, g = i & 3;
+      uint32_t m[8][4];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const uint4 v = ds[g * kNPos + pg * 8 + j];
+        m[j][0] = v.x; m[j][1] = v.y; m[j][2] = v.z; m[j][3] = v.w;
+      }
+      uint4 *dst = (uint4 *)(bufT + pg * 512 + g * 128);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {  // row c: channel c at the 8 positions
+        uint32_t w[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t lo = (m[2 * j][c >> 1] >> ((c & 1) * 16)) & 0xffffu;
+          const uint32_t hi = (m[2 * j + 1][c >> 1] >> ((c & 1) * 16)) & 0xffffu;
+          w[j] = lo | (hi << 16);
+        }
+        dst[c] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+    }
+    umma::fence_proxy_async();
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (lane == 0 && wid == 0) {  // weight gradient: 9 taps x nK MMAs
+      const uint32_t idesc = umma::idesc_bf16(128, NW) | (1u << 16);  // B MN-major
+#pragma unroll 1
+      for (int tap = 0; tap < 9; ++tap) {
+        const int shift = (tap / 3) * kGW + (tap % 3);
+        for (int kc = 0; kc < nK; ++kc) {
+          const uint64_t ad = umma::desc(sT + (uint32_t)(kc * 1024), 512, 128);
+          const uint64_t bd = umma::desc(sX + (uint32_t)((kc * 16 + shift) * 16), 128, kNPos * 16);
+          umma::mma_bf16(taddr + (uint32_t)(tap * NW), ad, bd, idesc, (any || kc > 0) ? 1u : 0u);
+        }
+      }
+      umma::mma_commit(mbar + 0);
+    }
+    if (lane == 0 && wid == 1 && l > 0) {  // input gradient: MT tiles x 9 taps x kg / 2 MMAs
+      const uint32_t idesc = umma::idesc_bf16(128, 32);
+      const uint64_t b0 = umma::desc(sW, 4 * 128, 128);
+      for (int mt = 0; mt < MT; ++mt) {
+        const uint64_t a0 = umma::desc(sD + (uint32_t)(mt * 128 * 16), kNPos * 16, 128);
+        const uint32_t d = taddr + kColG + (uint32_t)(mt * 32);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int shift = (tap / 3) * kGW + (tap % 3);
+          for (int kp = 0; kp < kg / 2; ++kp) {
+            const uint64_t ad = umma::desc_add(a0, (uint32_t)(((2 * kp) * kNPos + shift) * 16));
+            const uint64_t bd = umma::desc_add(b0, (uint32_t)((tap * kg + 2 * kp) * 4 * 128));
+            umma::mma_bf16(d, ad, bd, idesc, (tap | kp) != 0 ? 1u : 0u);
+          }
+        }
+      }
+      umma::mma_commit(mbar + 1);
+    }
+    __syncwarp();
+    any = true;
+    // bias gradient: sum of dY over the output window (fixed order per tile)
+    {
+      const int co = lane;
+      float sum = 0.f;
+      if (co < co_n) {
+        const uint16_t *col = (const uint16_t *)(bufD + (co >> 3) * kNPos * 16) + (co & 7);
+        for (int q = wid; q < vout * kGW; q += 8) sum += __uint_as_float((uint32_t)col[(kDPad + q) * 8] << 16);
+      }
+      s_part[wid * 32 + co] = sum;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      float sum = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) sum += s_part[w * 32 + tid];
+      s_db[tid] += sum;
+    }
+    bool ok = true;
+    if (l > 0) {
+      ok = __all_sync(0xffffffffu, umma::mbar_wait(mbar + 1, ph_g));
+      ph_g ^= 1u;
+      umma::fence_after_sync();
+      uint4 *dout = a.dyo + (size_t)t * 4 * kNPos;
+      for (int mt = wg; mt < MT && ok; mt += 2) {
+        const int q = mt * 128 + wq * 32 + lane;
+        const int r = q / kGW, c = q % kGW;
+        const bool win = r < vin && c < vin;
+        const uint32_t tl = taddr + ((uint32_t)(wq * 32) << 16) + kColG + (uint32_t)(mt * 32);
+        float v[32], h[16];
+        umma::tmem_ld16(tl, h);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = h[i];
+        umma::tmem_ld16(tl + 16, h);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[16 + i] = h[i];
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+          const uint4 xv = ((const uint4 *)bufX)[g * kNPos + q];
+          const uint32_t xw[4] = {xv.x, xv.y, xv.z, xv.w};
+          uint32_t w4[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float m0 = (win && bf16_lo(xw[j]) > 0.f) ? 1.f : 0.f;
+            const float m1 = (win && bf16_hi(xw[j]) > 0.f) ? 1.f : 0.f;
+            w4[j] = pack_bf16(v[g * 8 + 2 * j] * m0, v[g * 8 + 2 * j + 1] * m1);
+          }
+          dout[g * kNPos + q] = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+      }
+      for (int i = tid; i < 4 * (kNPos - MT * 128); i += kBwdThreads) {
+        const int g = i / (kNPos - MT * 128), q = MT * 128 + i % (kNPos - MT * 128);
+        dout[g * kNPos + q] = make_uint4(0, 0, 0, 0);
+      }
+    }
+    // the weight-gradient MMAs read bufT and bufX: wait before the next tile
+    ok = __all_sync(0xffffffffu, umma::mbar_wait(mbar + 0, ph_w)) && ok;
+    ph_w ^= 1u;
+    umma::fence_before_sync();
+    failed = __syncthreads_or(!ok) != 0;
+    umma::fence_after_sync();
+  }
+  if (failed) {
+    if (tid == 0) atomicOr(a.status, kStTimeout);
+    for (int k = 0; k < 2; ++k) umma::mbar_wait(mbar + k, k ? ph_g : ph_w, 1u << 18);
+  } else if (wid == 0) {
+    // weight gradient of the CTA's tiles: TMEM lane = c_out, column = tap * NW + c_in
+    const int npar = co_n * 9 * ci_n;
+    float *part = a.part + (size_t)blockIdx.x * (npar + co_n);
+    const int co = lane;
+#pragma unroll 1
     for (int tap = 0; tap < 9; ++tap) {
-      const int qr = r - tap / 3, qc = c - tap % 3;
-      if (qr < 0 || qc < 0 || qr >= rows_out || qc >= kGW - 2 * (l + 1)) continue;
-      const int q = qr * kGW + qc;
-      for (int co = 0; co < cout(l); ++co) s = fmaf(w[(co * 9 + tap) * cin(l) + ci], dy[(t * 32 + co) * kQ + q], s);
+      for (int c16 = 0; c16 < NW / 16; ++c16) {
+        float h[16];
+        if (any) {
+          umma::tmem_ld16(taddr + (uint32_t)(tap * NW + c16 * 16), h);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) h[i] = 0.f;
+        }
+        if (co < co_n)
+          for (int i = 0; i < 16; ++i) {
+            const int ci = c16 * 16 + i;
+            if (ci < ci_n) part[(co * 9 + tap) * ci_n + ci] = h[i];
+          }
+      }
     }
+    if (co < co_n) part[npar + co] = s_db[co];
   }
-  dx[i] = s;
+  umma::fence_before_sync();
+  __syncthreads();
+  if (wid == 0) umma::tmem_dealloc(taddr, kBwdTmemCols);
+}
+
+// grad[i] = sum over CTAs (in order) of the partials: deterministic
+__global__ void repair_reduce_kernel(const float *__restrict__ part, int n_parts, int count, float *__restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float sum = 0.f;
+  for (int k = 0; k < n_parts; ++k) sum += part[(size_t)k * count + i];
+  grad[i] = sum;
 }
 
 __global__ void repair_adamw_kernel(float *__restrict__ w, const float *__restrict__ g, float *__restrict__ m,
@@ -739,9 +995,16 @@ __global__ void repair_adamw_kernel(float *__restrict__ w, const float *__restri
 }  // namespace
 
 size_t repair_act_bytes_per_tile() { return (size_t)6 * 4 * kNPos * 16; }
+static int bwd_grid(int n) {
+  const int sms = sm_grid_cap(1);
+  return n < sms ? (n < 1 ? 1 : n) : sms;
+}
 size_t repair_train_scratch_bytes(int n_tiles) {
   const size_t n = (size_t)(n_tiles > 0 ? n_tiles : 1);
-  return n * (repair_act_bytes_per_tile() + 4 * kRT * kRT * 4 + 4 + 2 * 32 * kQ * 4 + 16) + 64 + 1024;
+  // activations, raw outputs, gate, two BF16 gradient buffers, tile stats, the
+  // loss sums and the CTAs' partial gradients of one layer
+  return n * (repair_act_bytes_per_tile() + 4 * kRT * kRT * 4 + 4 + 2 * 4 * kNPos * 16 + 32) +
+         (size_t)bwd_grid((int)n) * kBwdParts * 4 + 10 * 256;  // + alignment of the 8 buffers
 }
 
 cudaError_t prepare_repair() {
@@ -750,13 +1013,16 @@ cudaError_t prepare_repair() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(repair_net_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)net_smem(true));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(repair_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem());
   return e;
 }
 
 cudaError_t repair_pack(const Workspace &ws, cudaStream_t s) {
   repair_pack_kernel<<<(kWPackBytes / 2 + 255) / 256, 256, 0, s>>>(ws.rp_master, (uint16_t *)ws.rp_wpack,
                                                                    ws.rp_bias);
-  GS_LAUNCHED(1);
+  repair_packT_kernel<<<(kWPackTBytes / 2 + 255) / 256, 256, 0, s>>>(ws.rp_master, (uint16_t *)ws.rp_wpackT);
+  GS_LAUNCHED(2);
   return cudaGetLastError();
 }
 
@@ -843,21 +1109,21 @@ cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const R
   cudaError_t e;
   const int n = b.n_tiles;
   uint8_t *p = (uint8_t *)(((uintptr_t)b.scratch + 255) & ~(uintptr_t)255);
-  uint4 *acts = (uint4 *)p;
-  p += (size_t)n * repair_act_bytes_per_tile();
-  float *out4 = (float *)p;
-  p += (size_t)n * 4 * kRT * kRT * 4;
-  float *gate = (float *)p;
-  p += ((size_t)n * 4 + 255) / 256 * 256;
-  float *dy = (float *)p;
-  p += (size_t)n * 32 * kQ * 4;
-  float *dx = (float *)p;
-  p += (size_t)n * 32 * kQ * 4;
-  float *stats = (float *)p;
-  p += ((size_t)n * 16 + 255) / 256 * 256;
-  float *sums = (float *)p;
+  auto take = [&p](size_t bytes) {
+    uint8_t *q = p;
+    p += (bytes + 255) / 256 * 256;
+    return q;
+  };
+  uint4 *acts = (uint4 *)take((size_t)n * repair_act_bytes_per_tile());
+  float *out4 = (float *)take((size_t)n * 4 * kRT * kRT * 4);
+  float *gate = (float *)take((size_t)n * 4);
+  uint4 *dy = (uint4 *)take((size_t)n * 4 * kNPos * 16);
+  uint4 *dx = (uint4 *)take((size_t)n * 4 * kNPos * 16);
+  float *stats = (float *)take((size_t)n * 32);
+  float *sums = (float *)take(8 * sizeof(float));
+  const int G = bwd_grid(n);
+  float *part = (float *)take((size_t)G * kBwdParts * 4);
   if ((e = cudaMemsetAsync(sums, 0, 8 * sizeof(float), s)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(ws.rp_grad, 0, kRepairParams * sizeof(float), s)) != cudaSuccess) return e;
   if ((e = repair_forward(ws, b.feat, b.W, b.H, b.tiles, nullptr, (uint32_t)n, nullptr, gate, out4, acts, s, false,
                           nullptr)) != cudaSuccess)
     return e;
@@ -872,27 +1138,35 @@ cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const R
   a.out4 = out4;
   a.gate = gate;
   a.dy = dy;
-  a.dx = dx;
   a.tile_stats = stats;
   a.sums = sums;
   a.lam = o.gate_weight;
   repair_stats_kernel<<<n, 256, 0, s>>>(a);
+  repair_sums_kernel<<<1, 1024, 0, s>>>(stats, n, 2, 4, sums, 0);  // holes, L1 sum
   repair_dout_kernel<<<n, 256, 0, s>>>(a);
-  GS_LAUNCHED(2);
-  float *cur = dy, *nxt = dx;
+  repair_sums_kernel<<<1, 1024, 0, s>>>(stats, n, 5, 6, sums, 2);  // BCE, positive labels
+  GS_LAUNCHED(4);
+  // backward, last layer first: per layer one tensor-core kernel (weight
+  // gradient into per-CTA partials, input gradient into the other buffer) and
+  // the fixed-order reduction of the partials into this layer's gradient
+  uint4 *cur = dy, *nxt = dx;
   for (int l = 5; l >= 0; --l) {
-    const int rows_out = kGW - 2 * (l + 1);  // this layer's valid output rows
-    repair_wgrad_kernel<<<n * 32, 288, 0, s>>>(acts, cur, l, rows_out, ws.rp_grad);
-    GS_LAUNCHED(1);
-    if (l > 0) {
-      const size_t total = (size_t)n * 32 * kQ;
-      repair_dgrad_kernel<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(acts, cur, ws.rp_master, l, rows_out, n,
-                                                                          nxt);
-      GS_LAUNCHED(1);
-      float *tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-    }
+    BwdArgs ba;
+    ba.acts = acts;
+    ba.dy = cur;
+    ba.dyo = nxt;
+    ba.wpackT = ws.rp_wpackT;
+    ba.part = part;
+    ba.l = l;
+    ba.n = n;
+    ba.status = &ws.ctr->status;
+    repair_bwd_kernel<<<G, kBwdThreads, bwd_smem(), s>>>(ba);
+    const int count = cout(l) * 9 * cin(l) + cout(l);
+    repair_reduce_kernel<<<(count + 255) / 256, 256, 0, s>>>(part, G, count, ws.rp_grad + poff(l));
+    GS_LAUNCHED(2);
+    uint4 *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
   }
   if (o.lr > 0.f) {
     repair_adamw_kernel<<<(kRepairParams + 255) / 256, 256, 0, s>>>(

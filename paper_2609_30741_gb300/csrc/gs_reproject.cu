@@ -51,11 +51,27 @@ __device__ __forceinline__ bool transfer(const CamBlock &cb, float x, float y, f
 }
 
 // ---------------------------------------------------------------- forward warp
+struct EdgeArgs {
+  Counters *ctr;
+  int N, m, depth_mode;
+  float fixed_min, fixed_max;
+  int32_t *strips, *widths;
+  float *drange;
+  uint8_t *tile_mask;
+  int assign;  // 1: the strips are the mask's only tiles; 0: added to a cleared mask
+};
+__device__ void edge_roi_block(const CamBlock *__restrict__ cams, const EdgeArgs &ea);
+
+// The first block also computes the edge ROIs (Step 1) when `edge` is set: they
+// need only the depth range of Stage 1, and the classification that reads them
+// follows this kernel.
 __global__ void __launch_bounds__(256) warp_scatter_kernel(const CamBlock *__restrict__ cams,
                                                            const float *__restrict__ depth,
                                                            const float *__restrict__ trans,
-                                                           unsigned long long *__restrict__ buf, int W, int H) {
+                                                           unsigned long long *__restrict__ buf, int W, int H,
+                                                           int edge, EdgeArgs ea) {
   griddep_wait();
+  if (edge && blockIdx.x == 0) edge_roi_block(cams, ea);
   const CamBlock &cb = *cams;
   const int64_t npix = (int64_t)W * H;
   for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
@@ -73,18 +89,21 @@ __global__ void __launch_bounds__(256) warp_scatter_kernel(const CamBlock *__res
 }
 
 // ---------------------------------------------------------------- edge ROI (Step 1)
-__global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restrict__ cams, Counters *__restrict__ ctr,
-                                                       int N, int m, int depth_mode, float fixed_min,
-                                                       float fixed_max, int32_t *__restrict__ strips,
-                                                       int32_t *__restrict__ widths, float *__restrict__ drange,
-                                                       uint8_t *__restrict__ tile_mask, int assign) {
-  griddep_wait();
+// One block (any size) computes the edge ROIs: samples at the two depth
+// hypotheses, the extrema of Eq. 6, the widths of Eq. 7-8, the tile-aligned
+// strips and their tiles in the mask.
+__device__ void edge_roi_block(const CamBlock *__restrict__ cams, const EdgeArgs &ea) {
+  Counters *ctr = ea.ctr;
+  const int N = ea.N, m = ea.m, depth_mode = ea.depth_mode, assign = ea.assign;
+  int32_t *strips = ea.strips, *widths = ea.widths;
+  float *drange = ea.drange;
+  uint8_t *tile_mask = ea.tile_mask;
   const CamBlock &cb = *cams;
   const int W = cb.eye[1].W, H = cb.eye[1].H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;  // the ROI grid
   __shared__ int sxmin, sxmax, symin, symax, sany;
   __shared__ int sstrip[16];
-  float dmin = fixed_min, dmax = fixed_max;
+  float dmin = ea.fixed_min, dmax = ea.fixed_max;
   if (depth_mode == 0 || depth_mode == 2) {  // this frame's range, or the previous frame's
     const uint32_t lo = depth_mode == 0 ? ctr->dmin_bits : ctr->prev_range[0];
     const uint32_t hi = depth_mode == 0 ? ctr->dmax_bits : ctr->prev_range[1];
@@ -156,6 +175,11 @@ __global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restric
   }
 }
 
+__global__ void __launch_bounds__(256) edge_roi_kernel(const CamBlock *__restrict__ cams, EdgeArgs ea) {
+  griddep_wait();
+  edge_roi_block(cams, ea);
+}
+
 // ------------------------------------------------ resolve + classification + fill
 //
 // Per affiliated pixel: resolve the warp buffer, then (outside the edge strips)
@@ -179,7 +203,8 @@ struct WarpView {
 __global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_t *__restrict__ strips, int gap,
                                                        int center_enabled, float *__restrict__ rgb_aff,
                                                        float *__restrict__ warp_depth, uint8_t *__restrict__ cls,
-                                                       Counters *__restrict__ ctr) {
+                                                       Counters *__restrict__ ctr, uint32_t *__restrict__ cc_list,
+                                                       int32_t *__restrict__ labels) {
   griddep_wait();
   // this frame's measured depth range, kept for the next frame's edge ROI
   // (depth_mode 2); the edge ROI of this frame has read the previous one
@@ -276,6 +301,22 @@ __global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_
     rgb_aff[wv.hw + p] = out[1];
     rgb_aff[2 * wv.hw + p] = out[2];
     cls[p] = c;
+    // centre holes join the component labelling's list (one atomic per warp;
+    // the list order does not reach any output)
+    const bool cc = (c & kClsCentre) != 0;
+    const unsigned am = __activemask();
+    const unsigned bal = __ballot_sync(am, cc);
+    if (bal) {
+      const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(&ctr->n_centre, (uint32_t)__popc(bal));
+      base = __shfl_sync(am, base, leader);
+      if (cc) {
+        const uint32_t k = base + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+        cc_list[k] = (uint32_t)p;
+        labels[p] = (int32_t)k;  // the pixel's place in the list
+      }
+    }
   }
 }
 
@@ -315,78 +356,164 @@ __device__ void unite(int32_t *L, int a, int b, uint32_t *status) {
   atomicOr(status, kStTimeout);
 }
 
-__global__ void cc_init_kernel(const uint8_t *__restrict__ cls, int32_t *__restrict__ L, int64_t npix) {
-  griddep_wait();
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
-    L[p] = (cls[p] & kClsCentre) ? (int32_t)p : -1;
+// One CTA labels the components over the classification's list of centre-hole
+// pixels (about 0.1 % of the frame on the workloads here, so a full-image pass
+// per phase would cost more than the labelling). The list (up to kCcSmem
+// pixels) and the union-find parents live in shared memory, indexed by list
+// position; a pixel's neighbours are found through labels[] (its list
+// position, written by the classification). Phases, separated by block
+// barriers:
+//   1. union with the left and upper neighbours that are centre holes, always
+//      linking the root with the larger pixel index below the other, so every
+//      component's root is its smallest pixel (the canonical rectangle order);
+//   2. every entry's parent to its root;
+//   3. the roots in increasing pixel order (up to one root per thread: ranked by
+//      counting the smaller roots; up to kCcSortMax: a bitonic sort in shared
+//      memory);
+//   4. bounding boxes (shared-memory atomics);
+//   5. expand by m, align outward to tiles, clip, mark the tiles.
+// Longer lists take the same phases with the parents in global memory.
+constexpr int kCcThreads = 1024;
+constexpr int kCcSmem = 8192;
+constexpr int kCcSortMax = 4096;
+constexpr size_t kCcSmemBytes = sizeof(uint32_t) * (2 * kCcSmem + kCcSortMax);
+
+__device__ __forceinline__ uint32_t cc_find(volatile uint32_t *par, uint32_t x) {
+  uint32_t p = par[x];
+  for (int steps = 0; p != x && steps < kMaxUnionSteps; ++steps) {
+    x = p;
+    p = par[x];
+  }
+  return x;
 }
 
-__global__ void cc_merge_kernel(const uint8_t *__restrict__ cls, int32_t *L, int W, int H, uint32_t *status) {
-  griddep_wait();
-  const int64_t npix = (int64_t)W * H;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-    if (!(cls[p] & kClsCentre)) continue;
-    const int x = (int)(p % W);
-    if (x > 0 && (cls[p - 1] & kClsCentre)) unite(L, (int)p, (int)p - 1, status);
-    if (p >= W && (cls[p - W] & kClsCentre)) unite(L, (int)p, (int)(p - W), status);
+// Links the roots of list entries a and b (pix: their pixels) with a CAS on the
+// root with the larger pixel; bounded retries.
+__device__ void cc_unite(uint32_t *par, const uint32_t *pix, uint32_t a, uint32_t b, uint32_t *status) {
+  for (int it = 0; it < kMaxUnionSteps; ++it) {
+    a = cc_find(par, a);
+    b = cc_find(par, b);
+    if (a == b) return;
+    if (pix[a] < pix[b]) {
+      const uint32_t t = a;
+      a = b;
+      b = t;
+    }
+    if (atomicCAS(par + a, a, b) == a) return;
   }
+  atomicOr(status, kStTimeout);
 }
 
-__global__ void cc_flatten_kernel(int32_t *L, int64_t npix) {
+__global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__restrict__ cls,
+                                                              const uint32_t *__restrict__ list,
+                                                              const int32_t *__restrict__ lpos,
+                                                              uint32_t *__restrict__ gpar, int4 *rects,
+                                                              Counters *ctr, uint32_t cap, int W, int H, int m,
+                                                              int tiles_x, int tiles_y, uint8_t *__restrict__ tile_mask) {
   griddep_wait();
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x)
-    if (L[p] >= 0) L[p] = find_root(L, (int)p);
-}
-
-struct RootLoad {
-  const int32_t *L;
-  __device__ uint32_t operator()(uint32_t p) const { return L[p] == (int32_t)p ? 1u : 0u; }
-};
-
-struct RootApply {
-  uint32_t *slots;
-  int4 *rects;
-  uint32_t cap;
-  Counters *ctr;
-  int W, H;
-  __device__ void operator()(uint32_t p, uint32_t prefix, uint32_t v) const {
-    if (!v) return;
-    slots[p] = prefix;
-    if (prefix < cap) rects[prefix] = make_int4(W, H, -1, -1);
+  extern __shared__ uint32_t s_cc[];
+  uint32_t *s_pix = s_cc, *s_par = s_cc + kCcSmem, *s_roots = s_cc + 2 * kCcSmem;
+  __shared__ uint32_t s_nr;
+  const int tid = threadIdx.x;
+  const uint32_t n = min(ctr->n_centre, (uint32_t)W * (uint32_t)H);
+  const bool small = n <= (uint32_t)kCcSmem;
+  const uint32_t *pix = small ? s_pix : list;
+  uint32_t *par = small ? s_par : gpar;
+  if (tid == 0) s_nr = 0u;
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    if (small) s_pix[k] = list[k];
+    par[k] = k;
   }
-  __device__ void end(uint32_t, uint32_t total) const {
-    ctr->n_rects = total;
-    if (total > cap) atomicOr(&ctr->status, kStCapacity);
+  __syncthreads();
+  if (!small) __threadfence();
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    const int p = (int)pix[k];
+    const int x = p % W;
+    const bool l = x > 0 && (cls[p - 1] & kClsCentre), u = p >= W && (cls[p - W] & kClsCentre);
+    const uint32_t kl = l ? (uint32_t)lpos[p - 1] : 0u, ku = u ? (uint32_t)lpos[p - W] : 0u;
+    if (l) cc_unite(par, pix, k, kl, &ctr->status);
+    if (u) cc_unite(par, pix, k, ku, &ctr->status);
   }
-};
-
-__global__ void cc_bbox_kernel(const int32_t *__restrict__ L, const uint32_t *__restrict__ slots, int4 *rects,
-                               uint32_t cap, int W, int64_t npix) {
-  griddep_wait();
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-    const int r = L[p];
-    if (r < 0) continue;
-    const uint32_t s = slots[r];
-    if (s >= cap) continue;
-    const int x = (int)(p % W), y = (int)(p / W);
-    int *q = reinterpret_cast<int *>(rects + s);
+  __syncthreads();
+  if (!small) __threadfence();
+  for (uint32_t k = tid; k < n; k += kCcThreads) par[k] = cc_find(par, k);
+  __syncthreads();
+  if (!small) __threadfence();
+  // roots, and their rank by pixel (the rectangle slot) kept in the root's own
+  // parent entry's place in s_roots order
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    if (par[k] == k) {
+      const uint32_t j = atomicAdd(&s_nr, 1u);
+      if (j < (uint32_t)kCcSortMax) s_roots[j] = pix[k];
+    }
+  }
+  __syncthreads();
+  const uint32_t nr = s_nr;
+  // slot of a root pixel: its rank among the roots' pixels
+  if (nr <= (uint32_t)kCcSortMax) {
+    if (nr > (uint32_t)kCcThreads) {
+      uint32_t np2 = 1;
+      while (np2 < nr) np2 <<= 1;
+      for (uint32_t j = nr + tid; j < np2; j += kCcThreads) s_roots[j] = 0xffffffffu;
+      __syncthreads();
+      for (uint32_t size = 2; size <= np2; size <<= 1) {
+        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+          for (uint32_t i = tid; i < np2 / 2; i += kCcThreads) {
+            const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+            const bool up = (lo & size) == 0;
+            const uint32_t a = s_roots[lo], b = s_roots[hi];
+            if ((a > b) == up) {
+              s_roots[lo] = b;
+              s_roots[hi] = a;
+            }
+          }
+          __syncthreads();
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (uint32_t j = tid; j < min(nr, cap); j += kCcThreads) rects[j] = make_int4(W, H, -1, -1);
+  if (tid == 0) {
+    ctr->n_rects = nr;
+    if (nr > cap) atomicOr(&ctr->status, kStCapacity);
+  }
+  __syncthreads();
+  __threadfence_block();
+  // bounding boxes: every entry adds its pixel to its root's rectangle
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    const uint32_t rp = pix[par[k]];
+    uint32_t sl;
+    if (nr <= (uint32_t)kCcThreads) {  // rank by counting the smaller roots
+      sl = 0;
+      for (uint32_t j = 0; j < nr; ++j) sl += s_roots[j] < rp ? 1u : 0u;
+    } else if (nr <= (uint32_t)kCcSortMax) {  // position in the sorted roots
+      uint32_t lo = 0, hi = nr;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_roots[mid] < rp) lo = mid + 1; else hi = mid;
+      }
+      sl = lo;
+    } else {  // many roots: count the smaller roots of the list
+      sl = 0;
+      for (uint32_t q = 0; q < n; ++q) sl += (par[q] == q && pix[q] < rp) ? 1u : 0u;
+    }
+    if (sl >= cap) continue;
+    const int p = (int)pix[k];
+    const int x = p % W, y = p / W;
+    int *q = reinterpret_cast<int *>(rects + sl);
     atomicMin(q + 0, x);
     atomicMin(q + 1, y);
     atomicMax(q + 2, x);
     atomicMax(q + 3, y);
   }
-}
-
-// expand by m, align outward to tiles, clip; mark the tiles
-__global__ void cc_finalize_kernel(int4 *rects, const Counters *__restrict__ ctr, uint32_t cap, int W, int H, int m,
-                                   int tiles_x, int tiles_y, uint8_t *__restrict__ tile_mask) {
-  griddep_wait();
-  const uint32_t n = min(ctr->n_rects, cap);
-  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-    const int4 b = rects[s];
-    const int tx0 = b.x - m <= 0 ? 0 : (b.x - m) / kTile, ty0 = b.y - m <= 0 ? 0 : (b.y - m) / kTile;
-    const int tx1 = min((b.z + m) / kTile, tiles_x - 1), ty1 = min((b.w + m) / kTile, tiles_y - 1);
-    rects[s] = make_int4(tx0 * kTile, ty0 * kTile, min((tx1 + 1) * kTile, W), min((ty1 + 1) * kTile, H));
+  __syncthreads();
+  __threadfence_block();
+  for (uint32_t sl = tid; sl < min(nr, cap); sl += kCcThreads) {
+    const int4 bx = rects[sl];
+    const int tx0 = bx.x - m <= 0 ? 0 : (bx.x - m) / kTile, ty0 = bx.y - m <= 0 ? 0 : (bx.y - m) / kTile;
+    const int tx1 = min((bx.z + m) / kTile, tiles_x - 1), ty1 = min((bx.w + m) / kTile, tiles_y - 1);
+    rects[sl] = make_int4(tx0 * kTile, ty0 * kTile, min((tx1 + 1) * kTile, W), min((ty1 + 1) * kTile, H));
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) tile_mask[ty * tiles_x + tx] = 1;
   }
@@ -407,23 +534,33 @@ static int grid_for(int64_t n, int per_block = 256) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-cudaError_t launch_warp(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,
-                        cudaStream_t s) {
+static EdgeArgs edge_args(const Workspace &ws, const gs_roi_params &roi, uint8_t *mask, bool assign) {
+  return EdgeArgs{ws.ctr, roi.samples_per_edge, roi.margin, roi.depth_mode, roi.d_min, roi.d_max, ws.strips,
+                  ws.widths, ws.drange, mask, assign ? 1 : 0};
+}
+
+static cudaError_t warp_launches(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,
+                                 const gs_roi_params *roi, cudaStream_t s) {
   const int64_t npix = (int64_t)W * H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
   cudaError_t err = launch_k(warp_init_kernel, grid_for(npix), 256, 0, s, ws.warpbuf, npix, ws.tile_mask,
                              tiles_x * tiles_y);
+  const EdgeArgs ea = roi ? edge_args(ws, *roi, ws.tile_mask, false) : EdgeArgs{};
   if (err == cudaSuccess)
-    err = launch_k(warp_scatter_kernel, grid_for(npix), 256, 0, s, ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H);
+    err = launch_k(warp_scatter_kernel, grid_for(npix), 256, 0, s, ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H,
+                   roi ? 1 : 0, ea);
   GS_LAUNCHED(2);
   return err;
 }
 
+cudaError_t launch_warp(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,
+                        cudaStream_t s) {
+  return warp_launches(ws, W, H, depth_dom, trans_dom, nullptr, s);
+}
+
 cudaError_t launch_edge_roi(const Workspace &ws, const gs_roi_params &roi, uint8_t *mask, bool assign,
                             cudaStream_t s) {
-  const cudaError_t err = launch_k(edge_roi_kernel, 1, 256, 0, s, ws.cams, ws.ctr, roi.samples_per_edge, roi.margin,
-                                   roi.depth_mode, roi.d_min, roi.d_max, ws.strips, ws.widths, ws.drange, mask,
-                                   assign ? 1 : 0);
+  const cudaError_t err = launch_k(edge_roi_kernel, 1, 256, 0, s, ws.cams, edge_args(ws, roi, mask, assign));
   GS_LAUNCHED(1);
   return err;
 }
@@ -437,7 +574,7 @@ cudaError_t launch_classify(const Workspace &ws, int W, int H, int gap_thresh, c
   // the ROI re-render or the network overwrites those pixels)
   const int fill_all = !roi.enable_center || roi.repair_mode != 0;
   const cudaError_t err = launch_k(classify_kernel, grid_for(npix), 256, 0, s, wv, ws.strips, gap_thresh,
-                                   fill_all ? 0 : 1, rgb_aff, ws.warp_depth, ws.cls, ws.ctr);
+                                   fill_all ? 0 : 1, rgb_aff, ws.warp_depth, ws.cls, ws.ctr, ws.cc_list, ws.labels);
   GS_LAUNCHED(1);
   return err;
 }
@@ -445,8 +582,8 @@ cudaError_t launch_classify(const Workspace &ws, int W, int H, int gap_thresh, c
 cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
                                  const float *rgb_dom, const float *depth_dom, const float *trans_dom,
                                  float *rgb_aff, cudaStream_t s) {
-  cudaError_t err = launch_warp(ws, W, H, depth_dom, trans_dom, s);
-  if (err == cudaSuccess) err = launch_edge_roi(ws, roi, ws.tile_mask, false, s);
+  // warp and edge ROIs in one kernel, then the classification
+  cudaError_t err = warp_launches(ws, W, H, depth_dom, trans_dom, &roi, s);
   if (err == cudaSuccess) err = launch_classify(ws, W, H, gap_thresh, roi, rgb_dom, rgb_aff, s);
   return err;
 }
@@ -492,20 +629,18 @@ cudaError_t launch_mask_minus(uint8_t *mask, const uint8_t *minus, int n, cudaSt
 }
 
 cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cudaStream_t s) {
-  const int64_t npix = (int64_t)W * H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-  launch_k(cc_init_kernel, grid_for(npix), 256, 0, s, ws.cls, ws.labels, npix);
-  launch_k(cc_merge_kernel, grid_for(npix), 256, 0, s, ws.cls, ws.labels, W, H, &ws.ctr->status);
-  launch_k(cc_flatten_kernel, grid_for(npix), 256, 0, s, ws.labels, npix);
-  const uint32_t cap = (uint32_t)ws.max_rects;
-  cudaError_t err = scan_launch(RootLoad{ws.labels}, RootApply{ws.slots, ws.rects, cap, ws.ctr, W, H},
-                                (const uint32_t *)nullptr, (uint32_t)npix, ws.bin[0].scan_tiles, ws.bin[0].scan_ticket, &ws.ctr->status, s);
-  if (err != cudaSuccess) return err;
-  launch_k(cc_bbox_kernel, grid_for(npix), 256, 0, s, ws.labels, ws.slots, ws.rects, cap, W, npix);
-  launch_k(cc_finalize_kernel, grid_for(ws.max_rects), 256, 0, s, ws.rects, ws.ctr, cap, W, H, margin, tiles_x, tiles_y,
-                                                             ws.tile_mask);
-  GS_LAUNCHED(5);
+  launch_k(cc_label_kernel, 1, kCcThreads, kCcSmemBytes, s, (const uint8_t *)ws.cls, (const uint32_t *)ws.cc_list,
+           (const int32_t *)ws.labels, ws.slots, ws.rects, ws.ctr, (uint32_t)ws.max_rects, W, H, margin, tiles_x,
+           tiles_y, ws.tile_mask);
+  GS_LAUNCHED(1);
   return cudaGetLastError();
+}
+
+// The component labelling's shared memory exceeds the default 48 KB: one opt-in
+// per device (the attribute belongs to the kernel).
+cudaError_t prepare_reproject() {
+  return cudaFuncSetAttribute(cc_label_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCcSmemBytes);
 }
 
 }  // namespace gs

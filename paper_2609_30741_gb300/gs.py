@@ -173,6 +173,8 @@ EXPORTS = {
     "gs_ssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
     "gs_repair_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "gs_repair_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "gs_repair_steps": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "gs_repair_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "gs_repair_features": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p]),
     "gs_repair_infer": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int,
                                   C.c_void_p, C.c_void_p, C.c_int]),
@@ -449,6 +451,25 @@ class Context:
         _check(lib().gs_repair_read(self.h, int(which), out.ctypes.data_as(C.c_void_p), C.c_int64(out.size)),
                "gs_repair_read")
         return out
+
+    def repair_steps(self) -> int:
+        """AdamW steps taken since the last repair_load (the bias-correction count)."""
+        n = C.c_int()
+        _check(lib().gs_repair_steps(self.h, C.byref(n)), "gs_repair_steps")
+        return n.value
+
+    def repair_state(self):
+        """(weights, m, v, steps): everything a training checkpoint needs from the
+        context."""
+        return self.repair_read(0), self.repair_read(2), self.repair_read(3), self.repair_steps()
+
+    def repair_load_state(self, weights, m, v, steps):
+        import numpy as np
+        arrs = [np.ascontiguousarray(np.asarray(a, np.float32).ravel()) for a in (weights, m, v)]
+        if any(a.size != REPAIR_PARAMS for a in arrs):
+            raise ValueError(f"repair state arrays need {REPAIR_PARAMS} floats")
+        _check(lib().gs_repair_load_state(self.h, *[a.ctypes.data_as(C.c_void_p) for a in arrs],
+                                          C.c_int64(REPAIR_PARAMS), int(steps)), "gs_repair_load_state")
 
     def repair_features(self, cam, out=None):
         """Features of the last gs_render_stereo call made with repair_mode != 0:

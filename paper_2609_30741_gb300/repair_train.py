@@ -11,12 +11,15 @@ network serves at inference) and runs gs_repair_train_step (forward on the
 tensor cores, FP32 gradients, AdamW) through the C ABI.
 
     python -m paper_2609_30741_gb300.repair_train --scene object --scenes 4 \\
-        --poses 6 --steps 1500 --out weights.npy
+        --poses 6 --steps 1500 --out weights.npy [--checkpoint ck.npz
+        --checkpoint-every 100] [--resume ck.npz]
 """
 from __future__ import annotations
 
 import argparse
+import json
 import math
+import os
 import time
 
 import numpy as np
@@ -131,17 +134,54 @@ def build_pairs(kind: str, scenes: int, poses_per_scene: int, seed: int, device,
     return ctx, pairs
 
 
+def save_checkpoint(path, ctx, next_step: int, generator: torch.Generator, meta: dict):
+    """Everything a training run needs to continue exactly: FP32 parameters, both
+    AdamW moments and their step count (from the context), the next step index,
+    the state of the tile sampler's generator (the data cursor) and the run's
+    settings (checked on resume)."""
+    w, m, v, adam_steps = ctx.repair_state()
+    tmp = f"{path}.tmp.npz"
+    np.savez(tmp, weights=w, m=m, v=v, adam_steps=np.int64(adam_steps), next_step=np.int64(next_step),
+             generator=generator.get_state().cpu().numpy(), meta=np.array(json.dumps(meta, sort_keys=True)))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path):
+    z = np.load(path, allow_pickle=False)
+    return {"weights": z["weights"], "m": z["m"], "v": z["v"], "adam_steps": int(z["adam_steps"]),
+            "next_step": int(z["next_step"]), "generator": torch.from_numpy(z["generator"].copy()),
+            "meta": json.loads(str(z["meta"]))}
+
+
 def train(ctx: gs.Context, pairs: PairSet, steps: int, batch_tiles: int, lr: float, seed: int,
-          weights: np.ndarray | None = None, log_every: int = 50, gate_weight: float = 1.0):
-    ctx.repair_load(weights if weights is not None else init_weights(seed))
+          weights: np.ndarray | None = None, log_every: int = 50, gate_weight: float = 1.0,
+          checkpoint: str | None = None, checkpoint_every: int = 0, resume: str | None = None):
+    """AdamW training on random batches of the pairs' hole tiles with a cosine
+    rate decay. checkpoint / checkpoint_every: save the state every so many
+    steps; resume: continue from a saved state (the same pairs and settings),
+    which reproduces the uninterrupted run's remaining losses and final weights
+    bit for bit ("{step}" in the checkpoint path is replaced by the step count).
+    Returns (weights, [(step, loss, l1, bce, positive share)], seconds)."""
     all_tiles = pairs.tile_tensor()
     g = torch.Generator(device=all_tiles.device)
     g.manual_seed(seed)
     nb = min(batch_tiles, all_tiles.numel())
+    meta = {"steps": steps, "batch_tiles": nb, "lr": lr, "seed": seed, "gate_weight": gate_weight,
+            "hole_tiles": int(all_tiles.numel()), "frames": int(pairs.n)}
+    start = 0
+    if resume is not None:
+        ck = load_checkpoint(resume)
+        if ck["meta"] != meta:
+            raise ValueError(f"checkpoint settings {ck['meta']} differ from this run's {meta}")
+        ctx.repair_load_state(ck["weights"], ck["m"], ck["v"], ck["adam_steps"])
+        g.set_state(ck["generator"])
+        start = ck["next_step"]
+    else:
+        ctx.repair_load(weights if weights is not None else init_weights(seed))
     scratch = ctx.repair_scratch(nb)
     history = []
     t0 = time.time()
-    for step in range(steps):
+    for step in range(start, steps):
         pick = torch.randperm(all_tiles.numel(), generator=g, device=all_tiles.device)[:nb]
         tiles = all_tiles[pick].contiguous()
         # cosine decay to 10% of the rate
@@ -150,6 +190,60 @@ def train(ctx: gs.Context, pairs: PairSet, steps: int, batch_tiles: int, lr: flo
                                      gate_weight=gate_weight, want_loss=(step % log_every == 0 or step == steps - 1))
         if step % log_every == 0 or step == steps - 1:
             history.append((step, float(loss[0]), float(loss[1]), float(loss[2]), float(loss[3])))
+        if checkpoint and checkpoint_every > 0 and (step + 1) % checkpoint_every == 0:
+            save_checkpoint(checkpoint.format(step=step + 1), ctx, step + 1, g, meta)
+    if all_tiles.is_cuda:
+        torch.cuda.synchronize()
+    return ctx.repair_read(0), history, time.time() - t0
+
+
+def train_streamed(kind: str, n_scenes: int, poses_per_scene: int, shard_frames: int, epochs: int,
+                   steps_per_shard: int, batch_tiles: int, lr: float, seed: int, device, n_surfels=None,
+                   gate_weight: float = 1.0, log=print):
+    """Training on more pairs than fit resident at once (the 2,000 pairs of 50
+    scenes x 40 poses at 1920x1080 would take ~166 GB of frames): every epoch
+    walks the pairs in shards of shard_frames frames, renders a shard (features,
+    full render, interpolation-only image), and takes steps_per_shard AdamW steps
+    on random batches of its hole tiles; the parameters and AdamW moments carry
+    over between shards. The scenes stay resident; pair k is scene k //
+    poses_per_scene at the k-th pose of a seeded sequence, the same in every
+    epoch. Returns (weights, history, seconds)."""
+    t0 = time.time()
+    scenes = []
+    for sidx in range(n_scenes):
+        scene, cam, centre, radius = scene_and_camera(kind, seed + sidx, n_surfels)
+        scenes.append(gs.DeviceScene(scene, device=device))
+    n_pairs = n_scenes * poses_per_scene
+    rng = np.random.default_rng(seed)
+    poses = [random_pose(rng, centre, radius, kind) for _ in range(n_pairs)]
+    ctx = gs.Context(max(sc.n for sc in scenes), cam.width, cam.height, max_instances=1 << 26, device=device)
+    ctx.repair_load(init_weights(seed))
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    history, step = [], 0
+    total_steps = epochs * ((n_pairs + shard_frames - 1) // shard_frames) * steps_per_shard
+    scratch = ctx.repair_scratch(batch_tiles)
+    for epoch in range(epochs):
+        for s0 in range(0, n_pairs, shard_frames):
+            pairs = PairSet(ctx, cam, min(shard_frames, n_pairs - s0), device)
+            for k in range(s0, s0 + pairs.feat.shape[0]):
+                pairs.add(scenes[k // poses_per_scene], *poses[k])
+            all_tiles = pairs.tile_tensor()
+            nb = min(batch_tiles, all_tiles.numel())
+            for _ in range(steps_per_shard):
+                pick = torch.randperm(all_tiles.numel(), generator=g, device=device)[:nb]
+                lr_s = lr * (0.1 + 0.9 * 0.5 * (1 + math.cos(math.pi * step / max(total_steps - 1, 1))))
+                want = step % 100 == 0 or step == total_steps - 1
+                loss = ctx.repair_train_step(pairs.feat, pairs.target, pairs.plain, all_tiles[pick].contiguous(),
+                                             scratch=scratch if nb == batch_tiles else None, lr=lr_s,
+                                             gate_weight=gate_weight, want_loss=want)
+                if want:
+                    history.append((step, float(loss[0]), float(loss[1]), float(loss[2]), float(loss[3])))
+                    log(f"epoch {epoch} pairs {s0}-{s0 + pairs.n - 1} step {step} loss {loss[0]:.5f} "
+                        f"hole tiles {all_tiles.numel()}")
+                step += 1
+            del pairs, all_tiles
+    ctx.check_ok()
     torch.cuda.synchronize()
     return ctx.repair_read(0), history, time.time() - t0
 
@@ -215,12 +309,28 @@ def main():
     ap.add_argument("--gate-weight", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=7000)
     ap.add_argument("--out", required=True)
+    ap.add_argument("--checkpoint", default=None, help="save the training state here every --checkpoint-every steps")
+    ap.add_argument("--checkpoint-every", type=int, default=0)
+    ap.add_argument("--resume", default=None, help="continue from a saved training state")
+    ap.add_argument("--shard", type=int, default=0,
+                    help="stream the pairs in shards of this many frames (rendered on the fly), for pair counts "
+                         "that do not fit resident; --steps is then per shard and --epochs passes are made")
+    ap.add_argument("--epochs", type=int, default=1)
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
     from . import build
     build.build()
+    if args.shard > 0:
+        w, hist, secs = train_streamed(args.scene, args.scenes, args.poses, args.shard, args.epochs, args.steps,
+                                       args.batch, args.lr, args.seed, dev, args.surfels,
+                                       gate_weight=args.gate_weight)
+        np.save(args.out, w)
+        print(f"trained on {args.scenes * args.poses} pairs in shards of {args.shard}, {args.epochs} epochs, "
+              f"{len(hist)} logged steps, {secs:.1f} s")
+        return
     ctx, pairs = build_pairs(args.scene, args.scenes, args.poses, args.seed, dev, args.surfels)
-    w, hist, secs = train(ctx, pairs, args.steps, args.batch, args.lr, args.seed, gate_weight=args.gate_weight)
+    w, hist, secs = train(ctx, pairs, args.steps, args.batch, args.lr, args.seed, gate_weight=args.gate_weight,
+                          checkpoint=args.checkpoint, checkpoint_every=args.checkpoint_every, resume=args.resume)
     np.save(args.out, w)
     for h in hist:
         print(f"step {h[0]:5d} loss {h[1]:.5f} l1 {h[2]:.5f} bce {h[3]:.5f} pos {h[4]:.3f}")

@@ -24,21 +24,22 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 RGB_TOL = 2e-4
-# Pixels with a blend decision within MARGIN (relative) of its threshold, or with
-# near-equal depth keys among their contributors, are excluded from the
-# tolerance. The smaller parity workloads use 1e-5. Here a pixel evaluates about
-# 400 surfels. The float32 running transmittance carries a relative error of
-# about 2^-24 per factor (1 - alpha), plus alpha's own relative error amplified
-# by alpha / (1 - alpha) (up to ~50 for the alpha ~ 0.98 layers of the dense
-# ball), so over a few hundred factors the transmittance at the stop test
-# T (1 - alpha) < 1e-4 can be off by ~1e-4 relative: a stop decision within
-# 1e-4 of its threshold flipped on one frame (a 2.02e-4 error, one contribution
-# of weight ~1e-4 times a colour ~2). Decisions within MARGIN = 1e-3 are
-# therefore excluded at this size. The excluded share of every crop is printed
-# and bounded by MAX_MARGINAL, set a little above the largest share measured on
-# the sampled frames.
-MARGIN = 1e-3
-MAX_MARGINAL = 0.5
+# Excluded from the tolerance: pixels with a blend decision within MARGIN
+# (relative) of its threshold or near-equal depth keys among their contributors
+# (as in the smaller parity workloads, where MARGIN is 1e-5), and pixels whose
+# float32 evaluation cannot meet the tolerance by construction: here a pixel
+# blends up to several hundred surfels, and alpha's float32 error is amplified
+# by alpha / (1 - alpha) in the running transmittance, so the oracle's
+# first-order bound on the float32 error of a pixel's blending sum
+# (or_render's fp32_bound) can exceed the 2e-4 tolerance; a pixel is excluded
+# when that bound exceeds half of it. A pixel evaluates about 400 surfels, so
+# decisions within MARGIN = 1e-4 may flip as well. (The depth order itself is
+# decided identically on both sides: the oracle's key is the float32 camera
+# depth the rasterizer computes.) The excluded shares of every crop are printed
+# and bounded.
+MARGIN = 1e-4
+FP32_BOUND_MAX = RGB_TOL / 2
+MAX_MARGINAL = 0.02
 N_FRAMES = 16
 
 
@@ -118,8 +119,8 @@ def test_hmd_frames_against_oracle_crops(hmd, orc):
     for frame in frames:
         a, full, outs = _render_arms(hmd, frame)
         x0, y0 = _roi_crop(gs, cam, outs, frame)
-        o_rgb, _, _, mrg, _ = orc.render(hmd["scene"], a, cam, window=(x0, y0, 256, 256))
-        ok = mrg >= MARGIN
+        o_rgb, _, _, mrg, _, bound = orc.render(hmd["scene"], a, cam, window=(x0, y0, 256, 256), fp32_bound=True)
+        ok = (mrg >= MARGIN) & (bound <= FP32_BOUND_MAX)
         excluded = float(1.0 - ok.mean())
         e_map = np.abs(_crop(full["rgb_aff"], x0, y0) - o_rgb).max(0)
         e_full = e_map[ok].max()
@@ -129,7 +130,10 @@ def test_hmd_frames_against_oracle_crops(hmd, orc):
         row = {"frame": frame, "crop": (x0, y0), "excluded_share": round(excluded, 4),
                "comparator_max_abs": float(e_full), "plain_roi_max_abs": float(e_roi),
                "worst": {"yx": [int(worst[0]), int(worst[1])], "margin": float(mrg[worst]),
-                         "share_margin_below_1e-4": round(float((mrg < 1e-4).mean()), 4)}}
+                         "fp32_bound": float(bound[worst])},
+               "share_marginal": round(float((mrg < MARGIN).mean()), 4),
+               "share_fp32_bound": round(float((bound > FP32_BOUND_MAX).mean()), 4),
+               "fp32_bound_max": float(bound.max())}
         f_ref = full["rgb_aff"].double().cpu().numpy()
         for k, v in outs.items():
             c = _crop(v["rgb_aff"], x0, y0)

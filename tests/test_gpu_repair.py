@@ -1,5 +1,5 @@
-"""The learned repair network on the GPU (tcgen05 forward, FP32 backward,
-AdamW) against the FP64 oracle in oracle/repair.py.
+"""The learned repair network on the GPU (tcgen05 forward and backward, AdamW)
+against the FP64 oracle in oracle/repair.py.
 
 Tolerances: the oracle rounds inputs, weights and stored activations to
 bfloat16 at the points where the GPU stores them and sums in float64; the GPU
@@ -113,9 +113,12 @@ def test_forward_is_tile_local_and_listed_only(gs):
     assert np.all(p[:, :, ~listed] == -7.0)
 
 
-def test_gradients_match_oracle(gs):
+@pytest.mark.parametrize("H,W", [(32, 48), (200, 216)])
+def test_gradients_match_oracle(gs, H, W):
+    """Weight and bias gradients of one training step against the oracle's
+    backward; 200 x 216 gives 13 x 14 = 182 tiles, more than the backward's CTAs,
+    so some CTAs accumulate several tiles in tensor memory."""
     rng = np.random.default_rng(11)
-    H, W = 32, 48
     x, hole = _features(rng, H, W, 0.3)
     Wt, b = _weights(5)
     flat = R.pack(Wt, b).astype(np.float32).astype(np.float64)
@@ -130,8 +133,11 @@ def test_gradients_match_oracle(gs):
     loss = ctx.repair_train_step(feat, tgt, tgt.clone(), _tiles(H, W), lr=0.0, gate_weight=0.1)
     g_gpu = ctx.repair_read(1).astype(np.float64)
     out, acts = R.forward(x, Wt, b, bf16=True)
-    L, dout = R.loss(out, target, hole, np.zeros((2, 3)), lam=0.1, base=x[:3])
-    dW, db = R.backward(acts, Wt, dout)
+    L, dout = R.loss(out, target, hole, np.zeros(((H + 15) // 16, (W + 15) // 16)), lam=0.1, base=x[:3])
+    # the tensor-core backward rounds each layer's output gradient and its
+    # weights to bfloat16 operands (FP32 accumulation); the oracle rounds at the
+    # same points and sums exactly
+    dW, db = R.backward(acts, Wt, dout, bf16=True)
     g_ref = R.pack(dW, db)
     assert abs(loss[0] - L) <= 1e-3 * abs(L)
     rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
@@ -146,6 +152,10 @@ def test_gradients_match_oracle(gs):
             o += n
     # lr = 0 leaves the parameters untouched
     assert np.array_equal(ctx.repair_read(0), flat.astype(np.float32))
+    # the gradient sums are reduced in a fixed order: a second step gives the
+    # same gradients bit for bit
+    ctx.repair_train_step(feat, tgt, tgt.clone(), _tiles(H, W), lr=0.0, gate_weight=0.1)
+    assert np.array_equal(ctx.repair_read(1), g_gpu.astype(np.float32))
 
 
 def test_adamw_steps_reduce_the_loss(gs):
@@ -342,3 +352,20 @@ def test_stereo_fp8_mode(gs):
     closed = _stereo(gs, ctx, ds, dom, aff, cam, 2)
     for k in ("rgb_aff", "cls_aff"):
         assert torch.equal(closed[k], plain[k]), k
+
+
+def test_training_resumes_bit_for_bit(gs, tmp_path):
+    """The training step is deterministic (fixed-order gradient reduction), so a
+    run resumed from a checkpoint in a fresh context reproduces the
+    uninterrupted run's remaining losses and final weights exactly."""
+    from paper_2609_30741_gb300 import repair_train as T
+    dev = torch.device("cuda", 0)
+    ctx, pairs = T.build_pairs("small", 2, 2, 41, dev)
+    w_full, h_full, _ = T.train(ctx, pairs, 12, 96, 2e-3, 41, log_every=1)
+    ck = str(tmp_path / "ck_{step}.npz")
+    T.train(ctx, pairs, 12, 96, 2e-3, 41, log_every=1, checkpoint=ck, checkpoint_every=6)
+    ctx2 = gs.Context(ctx.lim.max_surfels, ctx.lim.max_width, ctx.lim.max_height, max_instances=1 << 22)
+    w_res, h_res, _ = T.train(ctx2, pairs, 12, 96, 2e-3, 41, log_every=1, resume=ck.format(step=6))
+    assert [h[0] for h in h_res] == list(range(6, 12))
+    assert h_res == h_full[6:]
+    assert np.array_equal(w_res, w_full)

@@ -5,8 +5,7 @@ method generates from seeded object scenes (500k surfels, 1600x1200), then
 evaluated on two held-out scene seeds and poses. The gain is a smaller
 re-rendered area: tiles whose gate passes take the network's fill and leave
 the ROI re-render (on these workloads 4-21% of the plain method's re-rendered
-pixels at tau = 0.5, varying with the training run because the FP32 gradient
-sums are accumulated atomically in a run-dependent order). The cost is
+pixels at tau = 0.5). The cost is
 bounded: the PSNR of the affiliated eye against the full render may drop by at
 most 0.5 dB.
 """

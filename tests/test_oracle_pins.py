@@ -763,3 +763,75 @@ def test_support_pairs_match_whole_image_sweep(orc, tile):
         assert any(t % ntx == ntx - 1 for t in hit_tiles) and any(t // ntx == nty - 1 for t in hit_tiles)
         assert any(t % ntx == 0 for t in hit_tiles) and any(t // ntx == 0 for t in hit_tiles)
         assert len(want) > 30
+
+
+def _round_f32(x):
+    """Exact round-to-nearest-even of a Fraction to float32."""
+    from fractions import Fraction
+    c = np.float32(float(x))
+    best = c
+    for cand in (np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))):
+        d, db = abs(Fraction(float(cand)) - x), abs(Fraction(float(best)) - x)
+        if d < db or (d == db and int(np.float32(cand).view(np.uint32)) % 2 == 0):
+            best = cand
+    return np.float32(best)
+
+
+def test_depth_key_is_the_float32_camera_depth(orc):
+    """The depth-order key is z = r20 x + r21 y + r22 z + t2 evaluated in float32
+    with one rounding per fused multiply-add, the rotation row and offset rounded
+    to float32 from the FP64 pose: checked against an exact-arithmetic restatement
+    (fractions), and against the FP64 depth within a few float32 ulps."""
+    from fractions import Fraction as F
+    rng = np.random.default_rng(44)
+    for k in range(200):
+        pose = synth.look_at(rng.normal(0, 2, 3), rng.normal(0, 1, 3) + np.array([0.0, 0.0, 3.0]))
+        p = rng.normal(0, 2, 3).astype(np.float32)
+        R, t = np.asarray(pose.R, np.float64), np.asarray(pose.t, np.float64)
+        t2 = 0.0
+        for j in range(3):
+            t2 = float(F(-R[j, 2]) * F(t[j]) + F(t2))  # fma in float64: exact, then one rounding
+        r = [np.float32(R[j, 2]) for j in range(3)]
+        z = _round_f32(F(float(r[2])) * F(float(p[2])) + F(float(np.float32(t2))))
+        z = _round_f32(F(float(r[1])) * F(float(p[1])) + F(float(z)))
+        z = _round_f32(F(float(r[0])) * F(float(p[0])) + F(float(z)))
+        key = orc.depth_key(pose, p)
+        assert key == float(z), (k, key, float(z))
+        z64 = float(R[:, 2] @ (p.astype(np.float64) - t))
+        assert abs(key - z64) <= 8 * abs(float(np.spacing(np.float32(z64)))) + 1e-6
+
+
+def test_fp32_bound_covers_a_float32_blend(orc):
+    """The oracle's per-pixel float32 error bound against an actual float32
+    evaluation of the same blend: a stack of fronto-parallel surfels centred on
+    the optical axis (so G = 1 at the centre pixel and alpha = min(0.99, o)),
+    with low and high opacities mixed so that the stop rule is reached only after
+    many contributions; numpy float32 arithmetic for alpha, T and the colour sum
+    must stay within the bound of the FP64 result, and the bound must not be
+    vacuous."""
+    cam = synth.centred_camera(3, 3, 100.0)
+    k = f32(1.0 / (0.5 / math.sqrt(math.pi)))
+    for seed, hi_share in ((1, 0.0), (2, 0.15), (3, 0.4)):
+        rng = np.random.default_rng(seed)
+        n = 400
+        z = 1.0 + np.arange(n) * 0.01
+        o = np.where(rng.random(n) < hi_share, rng.uniform(0.85, 0.98, n), rng.uniform(0.005, 0.05, n))
+        col = rng.uniform(0.0, 1.0, (n, 3))
+        sc = synth.concat(*[_one_surfel((0, 0, z[i]), (1, 0, 0, 0), (1.0, 1.0), o[i],
+                                        tuple(k * (c - 0.5) for c in col[i])) for i in range(n)])
+        rgb, _, tr, _, _, bound = orc.render(sc, synth.identity_pose(), cam, window=(1, 1, 1, 1), fp32_bound=True)
+        # float32 restatement of the blend at this pixel (alpha = min(0.99, o), G = 1)
+        T, C = np.float32(1.0), np.zeros(3, np.float32)
+        cs = (0.5 + (0.5 / math.sqrt(math.pi)) * sc.sh[:, 0, :].astype(np.float64)).astype(np.float32)
+        for i in range(n):
+            a = min(np.float32(0.99), np.float32(sc.opacity[i]))
+            if a < np.float32(1 / 255):
+                continue
+            Tn = np.float32(T * np.float32(np.float32(1.0) - a))
+            if Tn < np.float32(1e-4):
+                break
+            C = (C + cs[i] * np.float32(a * T)).astype(np.float32)
+            T = Tn
+        err = np.abs(C.astype(np.float64) - rgb[:, 0, 0]).max()
+        assert err <= bound[0, 0], (seed, err, bound[0, 0])
+        assert bound[0, 0] < 1e-3

@@ -171,3 +171,35 @@ def test_fp8_network_with_exact_codes_is_the_fp64_network():
     out8 = R.forward_fp8(x, W, b, sx, sw)
     out, _ = R.forward(x, W, b)
     np.testing.assert_array_equal(out8, out)
+
+
+def test_bf16_backward_on_exact_operands_is_the_fp64_backward():
+    """The BF16 backward only rounds: with weights, input and every gradient that
+    enters a layer exactly representable in bfloat16 (small dyadic values, single
+    nonzero taps so that no sum needs more than 8 bits), it equals the float64
+    backward bit for bit; on general operands it stays within a few bfloat16
+    ulps (2^-8) of it."""
+    H, Wd = 12, 10
+    W = [np.zeros((R.CHANNELS[l + 1], 3, 3, R.CHANNELS[l])) for l in range(6)]
+    b = [np.zeros(R.CHANNELS[l + 1]) for l in range(6)]
+    for l in range(6):
+        W[l][0, 1, 1, 0] = 0.5      # centre tap passes channel 0 on, halved
+        W[l][0, 0, 1, 0] = 0.25     # and a quarter of the row above
+    x = np.zeros((6, H, Wd))
+    x[0, 3:9, 2:8] = 1.0
+    out, acts = R.forward(x, W, b, bf16=True)
+    dout = np.zeros_like(out)
+    dout[0, 6, 5] = 0.125
+    dout[3, 4, 4] = -0.5
+    g64 = R.pack(*R.backward(acts, W, dout))
+    g16 = R.pack(*R.backward(acts, W, dout, bf16=True))
+    assert np.array_equal(g64, g16) and np.abs(g64).max() > 0
+    rng = np.random.default_rng(8)
+    Wr, br = R.init_weights(9)
+    xr = rng.random((6, 20, 18))
+    out, acts = R.forward(xr, Wr, br, bf16=True)
+    dout = rng.normal(0.0, 1.0, out.shape)
+    g64 = R.pack(*R.backward(acts, Wr, dout))
+    g16 = R.pack(*R.backward(acts, Wr, dout, bf16=True))
+    rel = np.linalg.norm(g16 - g64) / np.linalg.norm(g64)
+    assert 0.0 < rel <= 2 ** -7, rel
