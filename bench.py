@@ -86,6 +86,9 @@ def parse():
                     help="rasterizer tile,pix,batch of the method, or 'auto' (the autotuner's pick)")
     ap.add_argument("--raster-two-pass", default="auto",
                     help="rasterizer tile,pix,batch of the two-pass comparator, or 'auto'")
+    ap.add_argument("--raster-roi", default="auto",
+                    help="rasterizer tile,pix,batch of the method's ROI re-render, 'same' (the dominant eye's) "
+                         "or 'auto' (the fastest stereo frame over a few candidates)")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched 16-frame workload (4 scenes x 4 poses, one call)")
     ap.add_argument("--no-unbounded", action="store_true",
@@ -424,6 +427,36 @@ def run_ours(args):
                            "default_ms": dict((tuple(c), t) for c, t in res).get((16, 4, 128)),
                            "all_ms": {",".join(map(str, c)): round(t, 4) for c, t in res}}
 
+    # the ROI re-render's own configuration (Stage 4 re-renders only ROI tiles,
+    # whose mask lives on 16-pixel tiles): the stereo frame timed with each
+    # candidate, the dominant eye's configuration fixed
+    roi_tuning = {}
+    if args.raster_roi == "same":
+        rc["roi"] = None
+    elif args.raster_roi != "auto":
+        rc["roi"] = parse_raster(args.raster_roi)
+    else:
+        ctx.set_raster(*rc["stereo"])
+        cands = [None, (16, 2, 64), (16, 2, 128), (16, 4, 64), (16, 4, 128), (8, 2, 64), (32, 2, 64), (32, 2, 128)]
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(7)]
+        for cand in cands:
+            ctx.set_raster_roi(cand)
+            d, a = poses[0]
+            for _ in range(3):
+                ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+            for e0, e1 in evs:
+                flush.fill_(1)
+                e0.record(stream)
+                ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
+                e1.record(stream)
+            torch.cuda.synchronize(dev)
+            roi_tuning["same" if cand is None else ",".join(map(str, cand))] = \
+                float(np.median([e0.elapsed_time(e1) for e0, e1 in evs]))
+        ctx.check_ok()
+        best = min(roi_tuning, key=roi_tuning.get)
+        rc["roi"] = None if best == "same" else parse_raster(best)
+    ctx.set_raster_roi(rc["roi"])
+
     def stereo(k, scn=None):
         ctx.set_raster(*rc["stereo"])
         d, a = poses[k % len(poses)]
@@ -602,9 +635,12 @@ def run_ours(args):
         ref_imgs.append((a, out2["rgb_aff"].clone()))
     mem = {}
     for arm, paths, cp in (("stereo", gs.PATH_STEREO, cap_s), ("two_pass", gs.PATH_MONO, cap_t)):
+        tile_min = min(rc[arm][0], rc["roi"][0]) if arm == "stereo" and rc["roi"] else rc[arm][0]
         mctx = gs.Context(scene.n, W, H, max_instances=cp[0], max_instances_aff=cp[1], device=dev,
-                          min_tile=rc[arm][0], paths=paths)
+                          min_tile=tile_min, paths=paths)
         mctx.set_raster(*rc[arm])
+        if arm == "stereo":
+            mctx.set_raster_roi(rc["roi"])
         mo = mctx.alloc_outputs(cam, with_cls=False)
         same = True
         for k, (d, a) in enumerate(poses):
@@ -690,6 +726,8 @@ def run_ours(args):
         learned, weights = run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc)
         rooflines["repair_net"] = learned.pop("roofline")
         rooflines["repair_net_fp8"] = learned["fp8"].pop("roofline")
+        learned["speedup_vs_two_pass"] = ms_two / learned["ms_per_stereo_frame"]
+        learned["fp8"]["speedup_vs_two_pass"] = ms_two / learned["fp8"]["ms_per_stereo_frame"]
     batched = unbounded = hmd = backbone3d = None
     if ws_ == 1:
         del ds, out, out2
@@ -743,7 +781,9 @@ def run_ours(args):
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches_stereo),
         "raster": {"stereo": list(rc["stereo"]), "two_pass": list(rc["two_pass"]),
-                   "chosen_by": "autotuner" if tuning else "command line", "tuning": tuning},
+                   "stereo_roi": list(rc["roi"]) if rc["roi"] else "same as stereo",
+                   "chosen_by": "autotuner" if tuning else "command line", "tuning": tuning,
+                   "roi_tuning_ms": roi_tuning},
         "roofline": {"bound": "alu", "kernel": "raster_kernel<" + ",".join(map(str, rc["stereo"])) + "> (dominant eye)",
                      "achieved": achieved, "peak": peak_gops,
                      "unit": "Gop/s", "frac": achieved / peak_gops, "traffic": prof_traffic,
@@ -809,15 +849,16 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
     del tctx, pairs
     torch.cuda.empty_cache()
 
-    def variant(mode):
-        roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=1, repair_mode=mode, gate_tau=0.5)
+    def variant(mode, enable_center=1):
+        roi = gs.roi_params(margin=32, samples_per_edge=32, enable_center=enable_center, repair_mode=mode,
+                            gate_tau=0.5)
 
         def stereo(k):
             ctx.set_raster(*rc["stereo"])
             d, a = poses[k % len(poses)]
             ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
 
-        ps, ss, roi_fracs, net_fracs = [], [], [], []
+        ps, ss, roi_fracs, net_fracs, centre_fracs, hole_fracs = [], [], [], [], [], []
         for k in range(len(poses)):
             stereo(k)
             cls = out["cls_aff"].clone()
@@ -829,6 +870,8 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
             ss.append(float(ctx.ssim(out["rgb_aff"], out2["rgb_aff"])))
             roi_fracs.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
             net_fracs.append(((cls & gs.CLS_NET) > 0).float().mean().item())
+            centre_fracs.append((((cls & gs.CLS_RENDER) > 0) & ((cls & gs.CLS_STRIP) == 0)).float().mean().item())
+            hole_fracs.append((((cls & gs.CLS_HOLE) > 0) & ((cls & gs.CLS_STRIP) == 0)).float().mean().item())
         ms, _, _ = timed(stereo, args.steps, args.warmup)
         _, _, st = timed(stereo, len(poses), 1, profile=True)
         st = np.mean(np.array(st), 0).tolist()
@@ -837,12 +880,17 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
                 "ssim_aff_vs_full": float(np.mean(ss)),
                 "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE), "roi_pixel_share": float(np.mean(roi_fracs)),
                 "net_filled_pixel_share": float(np.mean(net_fracs)),
+                "centre_roi_pixel_share": float(np.mean(centre_fracs)),
+                "non_strip_hole_pixel_share": float(np.mean(hole_fracs)),
                 "dtype": ("fp8 e4m3" if mode == 2 else "bf16") + " network, f32 rendering",
                 "stage_ms": dict(zip(["preprocess", "bin_dom", "blend_dom", "warp_edge_gaps_features",
-                                      "centre_rois_and_repair", "bin_roi", "blend_roi", "outputs"], st))}
+                                      "centre_rois" + ("_and_repair_fork" if mode else ""), "bin_roi",
+                                      "blend_roi", "outputs"], st))}
 
     res = variant(1)
     res["fp8"] = variant(2)
+    plain, floor = variant(0), variant(0, enable_center=0)
+    res["gain_bound"] = gain_bound(plain, floor, res, res["fp8"])
     res["roofline"] = net_rl[False]
     res["fp8"]["roofline"] = net_rl[True]
     res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "batch_tiles": 512,
@@ -851,6 +899,23 @@ def run_learned(args, ctx, ds, cam, poses, out, out2, timed, flush, dev, rc):
                        "data": "object-scene seeds 7000-7003, 6 random head poses each (held out from "
                                "the bench scene and poses)"}
     return res, w
+
+
+def gain_bound(plain, floor, bf16, fp8):
+    """What any hole filler can save on a workload: the network only serves the
+    holes outside the edge strips, so its best case replaces the centre-ROI
+    re-render by nothing. The plain method with the centre step off (those holes
+    interpolated, only the edge strips re-rendered) is that floor."""
+    keep = ("ms_per_stereo_frame", "psnr_aff_vs_full_db", "roi_pixel_share", "centre_roi_pixel_share",
+            "non_strip_hole_pixel_share")
+    out = {"plain": {k: plain[k] for k in keep if k in plain},
+           "centre_step_off": {k: floor[k] for k in keep if k in floor},
+           "max_saving_ms": plain["ms_per_stereo_frame"] - floor["ms_per_stereo_frame"],
+           "learned_bf16_extra_ms": bf16["ms_per_stereo_frame"] - plain["ms_per_stereo_frame"],
+           "learned_fp8_extra_ms": fp8["ms_per_stereo_frame"] - plain["ms_per_stereo_frame"],
+           "note": "the network serves only holes outside the edge strips; the most it can save is the centre-ROI "
+                   "re-render, i.e. plain minus the centre-step-off frame (max_saving_ms)"}
+    return out
 
 
 def run_batched(args, dev, flush, weights):
@@ -993,7 +1058,8 @@ def run_unbounded(args, dev, flush):
     ctx.repair_calibrate_fp8(*calib)
     stream = torch.cuda.current_stream(dev)
     rois = {"plain": gs.roi_params(), "learned_bf16": gs.roi_params(repair_mode=1, gate_tau=0.5),
-            "learned_fp8": gs.roi_params(repair_mode=2, gate_tau=0.5)}
+            "learned_fp8": gs.roi_params(repair_mode=2, gate_tau=0.5),
+            "centre_step_off": gs.roi_params(enable_center=0)}
     d0, a0 = poses[0]
     rc_s = gs.autotune_stereo(ctx, ds, d0, a0, cam, roi=rois["plain"], out=out, reps=5, use_cache=False)[0]
     rc_t = gs.autotune_stereo(ctx, ds, d0, a0, cam, out=out2, reps=5, use_cache=False, two_pass=True)[0]
@@ -1029,7 +1095,7 @@ def run_unbounded(args, dev, flush):
             d, a = poses[k % 8]
             ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
         ms = run(stereo, args.steps, args.warmup)
-        ps, ss, roi_fr, net_fr = [], [], [], []
+        ps, ss, roi_fr, net_fr, cen_fr, hole_fr = [], [], [], [], [], []
         for k in range(8):
             stereo(k)
             cls = out["cls_aff"].clone()
@@ -1038,12 +1104,17 @@ def run_unbounded(args, dev, flush):
             ss.append(float(ctx.ssim(out["rgb_aff"], out2["rgb_aff"])))
             roi_fr.append(((cls & gs.CLS_RENDER) > 0).float().mean().item())
             net_fr.append(((cls & gs.CLS_NET) > 0).float().mean().item())
+            cen_fr.append((((cls & gs.CLS_RENDER) > 0) & ((cls & gs.CLS_STRIP) == 0)).float().mean().item())
+            hole_fr.append((((cls & gs.CLS_HOLE) > 0) & ((cls & gs.CLS_STRIP) == 0)).float().mean().item())
         ctx.check_ok()
         res[name] = {"ms_per_stereo_frame": ms, "speedup_vs_two_pass": res["two_pass_ms"] / ms,
                      "psnr_aff_vs_full_db": float(np.mean(ps)), "psnr_min_db": float(np.min(ps)),
                      "quality_gate_pass": bool(np.min(ps) >= PSNR_GATE_MIP),
                      "ssim_aff_vs_full": float(np.mean(ss)),
-                     "roi_pixel_share": float(np.mean(roi_fr)), "net_filled_pixel_share": float(np.mean(net_fr))}
+                     "roi_pixel_share": float(np.mean(roi_fr)), "net_filled_pixel_share": float(np.mean(net_fr)),
+                     "centre_roi_pixel_share": float(np.mean(cen_fr)),
+                     "non_strip_hole_pixel_share": float(np.mean(hole_fr))}
+    res["gain_bound"] = gain_bound(res["plain"], res.pop("centre_step_off"), res["learned_bf16"], res["learned_fp8"])
     res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "seconds": round(train_s, 1),
                        "loss_first_last": [hist[0][1], hist[-1][1]],
                        "data": "unbounded-distribution seeds 7100-7103 (1.5M surfels each), 6 random head poses "

@@ -377,7 +377,7 @@ gs_status gs_warp_noalloc(const float *rgb_dom, const float *depth_dom, const fl
 typedef enum {
   GS_BUF_RECORDS = 0,     /* float4[eye][max_surfels][4]: per-surfel blend records */
   GS_BUF_RECTS = 1,       /* uint16x4[eye][max_surfels]: tile rect tx0, ty0, tx1, ty1 */
-  GS_BUF_BOUNDS = 2,      /* float4[eye][max_surfels]: xmin, xmax, ymin, ymax (keep_intermediates) */
+  GS_BUF_BOUNDS = 2,      /* float4[eye][max_surfels]: xmin, xmax, ymin, ymax (screen bounds) */
   GS_BUF_COUNTS = 3,      /* uint32[eye][max_surfels]: tiles touched per surfel (0 = culled) */
   GS_BUF_DEPTH_ORDER = 4, /* uint32[max_surfels]: surfel ids of the last binning in depth order */
   GS_BUF_INST_KEYS = 5,   /* uint32[max_instances]: tile id per instance, sorted (keep_intermediates) */
@@ -430,6 +430,16 @@ typedef struct {
 } gs_raster_config;
 gs_status gs_context_set_raster(gs_context *ctx, const gs_raster_config *rc);
 gs_status gs_context_get_raster(gs_context *ctx, gs_raster_config *rc);
+
+/* The configuration of gs_render_stereo's ROI re-render (Sec. 3.1 Stage 4): the
+ * affiliated eye's ROI tiles are binned and blended on its tile grid, which may
+ * differ from the dominant eye's (the ROI mask lives on 16-pixel tiles, so
+ * 16-pixel tiles render exactly the ROI tiles). NULL clears it: the ROI
+ * re-render then uses gs_context_set_raster's configuration. The images do not
+ * depend on it. get returns the configuration the ROI re-render uses and, in
+ * *is_set, whether one of its own is set. */
+gs_status gs_context_set_raster_roi(gs_context *ctx, const gs_raster_config *rc);
+gs_status gs_context_get_raster_roi(gs_context *ctx, gs_raster_config *rc, int *is_set);
 
 /* ---------------------------------------------------------------------------
  * Batched rendering (a serving mode; the paper renders one stereo frame at a

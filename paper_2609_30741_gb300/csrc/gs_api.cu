@@ -59,7 +59,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   for (int e = 0; e < 2; ++e) {
     ws.rec[e] = c.take<float4>(4 * N);
     ws.rect[e] = c.take<ushort4>(N);
-    ws.bounds[e] = c.take<float4>(lim.keep_intermediates ? N : 1);
+    ws.bounds[e] = c.take<float4>(N);  // the rasterizer's per-warp culling reads them
     ws.cnt[e] = c.take<uint32_t>(N);
     ws.zkey[e] = c.take<uint32_t>(N);
   }
@@ -125,7 +125,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
   ws.rp_feat = c.take<uint4>(repair ? P : 1);
   ws.rp_fill = c.take<float>(repair ? 3 * P : 1);
   ws.rp_gate = c.take<float>(tiles);
-  ws.rp_flags = c.take<uint8_t>(tiles);
+  ws.rp_skip = c.take<uint8_t>(tiles);
   ws.rp_list = c.take<uint32_t>(tiles);
   ws.rp_nlist = c.take<uint32_t>(1);
   ws.ssim_part = c.take<double>(ssim_partials(lim.max_width, lim.max_height));
@@ -256,10 +256,12 @@ bool intr_ok(const gs_context *ctx, const gs_intrinsics *in) {
          in->height < 65536 * kTile;
 }
 
-PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in, const RasterConfig &rc) {
+PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in, const RasterConfig &rc,
+                   const RasterConfig *rc1) {
   PoseArgs pa;
   memset(&pa, 0, sizeof(pa));
   pa.tshift = raster_tshift(rc);
+  pa.tshift1 = raster_tshift(rc1 ? *rc1 : rc);
   memcpy(pa.R[0], a->R, sizeof(double) * 9);
   memcpy(pa.t[0], a->t, sizeof(double) * 3);
   if (b) {
@@ -403,6 +405,7 @@ gs_status gs_context_destroy(gs_context *ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_edge) cudaEventDestroy(ctx->ev_edge);
   if (ctx->ev_strip) cudaEventDestroy(ctx->ev_strip);
+  if (ctx->ev_net) cudaEventDestroy(ctx->ev_net);
   if (ctx->copy) cudaStreamDestroy(ctx->copy);
   if (ctx->ev_hfork) cudaEventDestroy(ctx->ev_hfork);
   if (ctx->ev_hjoin) cudaEventDestroy(ctx->ev_hjoin);
@@ -485,11 +488,11 @@ static void mark(gs_context *ctx, int slot) {
 }
 
 // One eye through the persistent rasterizer (a table of one frame).
-static cudaError_t raster_one(gs_context *ctx, const RasterFrame &f) {
+static cudaError_t raster_one(gs_context *ctx, const RasterFrame &f, const RasterConfig *rc = nullptr) {
   RasterTable t;
   t.n = 1;
   t.f[0] = f;
-  return launch_raster(t, ctx->rc, ctx->counting != 0, ctx->ws.bin[f.eye].rqueue, ctx->stream);
+  return launch_raster(t, rc ? *rc : ctx->rc, ctx->counting != 0, ctx->ws.bin[f.eye].rqueue, ctx->stream);
 }
 
 static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye, int W, int H, float3 bg,
@@ -658,6 +661,7 @@ static gs_status ensure_side(gs_context *ctx) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_edge, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_strip, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_net, cudaEventDisableTiming);
   return cuda_status(e);
 }
 
@@ -721,15 +725,22 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
   if (!roi_ok(gap_thresh, roi) || !paths_ok(ctx, roi)) return GS_ERR_BAD_ARG;
   if ((roi->repair_mode == 1 && !ctx->rp_loaded) || (roi->repair_mode == 2 && !ctx->rp_fp8)) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
-  const int sh = raster_tshift(ctx->rc), ts = 1 << sh;
+  // the ROI re-render (Stage 4) runs in its own rasterizer configuration when
+  // one is set (its tile edge is also the affiliated eye's binning grid)
+  const RasterConfig rc1 = ctx->has_rc_roi ? ctx->rc_roi : ctx->rc;
+  const int sh = raster_tshift(rc1), ts = 1 << sh;
   const int tx = (W + ts - 1) >> sh, ty = (H + ts - 1) >> sh;
-  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc);
+  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc, &rc1);
   // depth_mode 2 reuses the depth range the previous stereo call measured; the
   // first call measures it (mode 0)
   gs_roi_params r = *roi;
   const bool reuse = roi->depth_mode == 2 && ctx->have_range;
   if (roi->depth_mode == 2 && !reuse) r.depth_mode = 0;
-  if (reuse) {
+  // learned repair without the depth-range reuse: the network runs on the second
+  // stream beside the ROI binning (which reads the ROI mask the network leaves
+  // unchanged); the rasterizer then skips the tiles whose gate passed
+  const bool net_side = (r.repair_mode == 1 || r.repair_mode == 2) && !reuse;
+  if (reuse || net_side) {
     const gs_status st = ensure_side(ctx);
     if (st != GS_OK) return st;
   }
@@ -739,6 +750,7 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
   kb.add(r);
   kb.add(*out);
   kb.add(pa.parallel);  // selects the depth-order path of the affiliated eye
+  kb.add(rc1);
   kb.add(hc ? hc->dom : nullptr);  // host copies are nodes of the captured graph
   kb.add(hc ? hc->aff : nullptr);
   const gs_status res = run_graph(ctx, 1, kb.buf, kb.len, pa, [&](const PoseArgs &p) -> gs_status {
@@ -763,7 +775,7 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
         RasterTable t;
         t.n = 1;
         t.f[0] = raster_frame(ws, 1, W, H, sh, ws.strip_mask, black, ws.strip_rgb, nullptr, nullptr, nullptr, false);
-        e = launch_raster(t, ctx->rc, ctx->counting != 0, ws.bin[1].rqueue, sd);
+        e = launch_raster(t, rc1, ctx->counting != 0, ws.bin[1].rqueue, sd);
       }
       if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_strip, sd);
       if (e != cudaSuccess) return cuda_fail(e);
@@ -801,7 +813,14 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
     }
     // learned repair: tiles with holes whose gate passes take the network fill
     // and leave the ROI tile mask
-    if (r.repair_mode == 1 || r.repair_mode == 2) {
+    if (net_side) {
+      if ((e = cudaEventRecord(ctx->ev_fork, ctx->stream)) == cudaSuccess)
+        e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+      if (e == cudaSuccess)
+        e = repair_stereo(ws, W, H, r.gate_tau, out->rgb_aff, ctx->side, r.repair_mode == 2, ws.rp_skip);
+      if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_net, ctx->side);
+      if (e != cudaSuccess) return cuda_fail(e);
+    } else if (r.repair_mode == 1 || r.repair_mode == 2) {
       if ((e = repair_stereo(ws, W, H, r.gate_tau, out->rgb_aff, ctx->stream, r.repair_mode == 2)) != cudaSuccess)
         return cuda_fail(e);
     }
@@ -821,8 +840,12 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
                 : launch_binning(ws, 1, scene->n, tx, ty, ws.tile_mask, ctx->stream, aorder);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
-    e = raster_one(ctx, raster_frame(ws, 1, W, H, sh, ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ws.cls,
-                                     false));
+    RasterFrame rf = raster_frame(ws, 1, W, H, sh, ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ws.cls, false);
+    if (net_side) {  // join the network; its gated tiles keep the fill
+      if ((e = cudaStreamWaitEvent(ctx->stream, ctx->ev_net, 0)) != cudaSuccess) return cuda_fail(e);
+      rf.skip = ws.rp_skip;
+    }
+    e = raster_one(ctx, rf, &rc1);
     if (e == cudaSuccess && reuse) e = launch_strip_composite(ws, W, H, ws.strip_rgb, out->rgb_aff, ctx->stream);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 7);
@@ -870,6 +893,29 @@ gs_status gs_context_set_raster(gs_context *ctx, const gs_raster_config *rc) {
   return GS_OK;
 }
 
+gs_status gs_context_set_raster_roi(gs_context *ctx, const gs_raster_config *rc) {
+  if (!ctx) return GS_ERR_BAD_ARG;
+  if (!rc) {
+    ctx->has_rc_roi = 0;
+    return GS_OK;
+  }
+  const RasterConfig c{rc->tile, rc->pix, rc->batch};
+  if (!raster_config_ok(c) || raster_tshift(c) < ctx->ws.min_tshift) return GS_ERR_BAD_ARG;
+  ctx->rc_roi = c;
+  ctx->has_rc_roi = 1;
+  return GS_OK;
+}
+
+gs_status gs_context_get_raster_roi(gs_context *ctx, gs_raster_config *rc, int *is_set) {
+  if (!ctx || !rc) return GS_ERR_BAD_ARG;
+  const RasterConfig &c = ctx->has_rc_roi ? ctx->rc_roi : ctx->rc;
+  rc->tile = c.tile;
+  rc->pix = c.pix;
+  rc->batch = c.batch;
+  if (is_set) *is_set = ctx->has_rc_roi;
+  return GS_OK;
+}
+
 gs_status gs_context_get_raster(gs_context *ctx, gs_raster_config *rc) {
   if (!ctx || !rc) return GS_ERR_BAD_ARG;
   rc->tile = ctx->rc.tile;
@@ -910,7 +956,7 @@ gs_status gs_context_buffer(gs_context *ctx, int which, void **dev_ptr, size_t *
   switch (which & ~GS_BUF_EYE1) {
     case GS_BUF_RECORDS: p = ws.rec[eye]; b = 64 * N; n = (int64_t)N; break;
     case GS_BUF_RECTS: p = ws.rect[eye]; b = 8 * N; n = (int64_t)N; break;
-    case GS_BUF_BOUNDS: p = ws.bounds[eye]; b = ws.keep_intermediates ? 16 * N : 0; n = (int64_t)N; break;
+    case GS_BUF_BOUNDS: p = ws.bounds[eye]; b = 16 * N; n = (int64_t)N; break;
     case GS_BUF_COUNTS: p = ws.cnt[eye]; b = 4 * N; n = (int64_t)N; break;
     case GS_BUF_DEPTH_ORDER: p = ws.bin[last].dval[0]; b = 4 * N; n = c.n_vis[last]; break;
     case GS_BUF_INST_KEYS:

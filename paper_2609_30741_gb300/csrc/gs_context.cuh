@@ -32,12 +32,15 @@ struct gs_context {
   cudaStream_t cap_stream;
   GraphSlot graphs[3];  // mono, stereo, two-pass
   gs::RasterConfig rc;  // persistent rasterizer: tile edge, pixels per thread, records per stage
+  gs::RasterConfig rc_roi;  // the ROI re-render's (Stage 4), when has_rc_roi
+  int has_rc_roi;
   int rp_loaded;        // repair network weights present
   int rp_fp8;           // FP8 scales and weights calibrated for the current weights
   int rp_step;          // AdamW steps taken
   int have_range;       // a stereo call has measured a depth range (depth_mode 2 can reuse it)
   cudaStream_t side;    // second stream of a stereo call with depth_mode 2
   cudaEvent_t ev_fork, ev_edge, ev_strip;
+  cudaEvent_t ev_net;    // learned repair on the second stream: the network is done
   cudaStream_t copy;    // gs_render_stereo_host: the dominant eye's copy to the host
   cudaEvent_t ev_hfork, ev_hjoin;
 };
@@ -66,7 +69,8 @@ bool outputs_ok(const gs_outputs *o);
 // gs_roi_params and gap threshold of a stereo call (not the repair weights)
 bool roi_ok(int gap_thresh, const gs_roi_params *roi);
 bool paths_ok(const gs_context *ctx, const gs_roi_params *roi);
-PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in, const RasterConfig &rc);
+PoseArgs pose_args(const gs_pose *a, const gs_pose *b, const gs_intrinsics *in, const RasterConfig &rc,
+                   const RasterConfig *rc1 = nullptr);
 cudaError_t launch_reset_counters(Counters *c, cudaStream_t s);
 // Copies the optional stereo outputs (class map, ROI rectangles, counts) on ctx->stream.
 cudaError_t copy_optional(gs_context *ctx, const gs_outputs *out, int W, int H);

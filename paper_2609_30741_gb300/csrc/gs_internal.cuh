@@ -54,7 +54,8 @@ struct PoseArgs {
   int W, H;
   int neyes;
   int parallel;  // the eyes share orientation and the baseline lies in the image plane
-  int tshift;    // rasterizer tile edge = 1 << tshift pixels
+  int tshift;    // rasterizer tile edge = 1 << tshift pixels (the dominant eye)
+  int tshift1;   // the affiliated eye's (its ROI re-render may use another tile edge)
 };
 
 struct Counters {
@@ -150,7 +151,7 @@ struct Workspace {
   uint4 *rp_feat;               // [pixels] 8 x bf16 features of the affiliated eye
   float *rp_fill;               // [3][pixels] network fill
   float *rp_gate;               // [tiles] gate logit per listed tile
-  uint8_t *rp_flags;            // [tiles] tile has a hole
+  uint8_t *rp_skip;             // [16-pixel tiles] the network's fill was taken
   uint32_t *rp_list, *rp_nlist; // listed tiles and their number
   double *ssim_part;            // per-(tile, channel) SSIM sums
   // limits
@@ -241,9 +242,11 @@ cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H,
 cudaError_t repair_calibrate_fp8(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
                                  uint32_t n_tiles, float *gate_scratch, cudaStream_t s);
 // Tile list, network and gated merge for the affiliated eye of the last warp
-// (features already in ws.rp_feat); gated tiles leave ws.tile_mask.
+// (features already in ws.rp_feat). Gated tiles leave ws.tile_mask, or, with
+// skip given, are flagged there instead (the ROI mask stays as it is, so the
+// ROI binning can read it while the network runs on another stream).
 cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s,
-                          bool fp8 = false);
+                          bool fp8 = false, uint8_t *skip = nullptr);
 cudaError_t repair_train_step(const Workspace &ws, const RepairBatch &b, const RepairOpt &o, float *host_loss,
                               cudaStream_t s);
 
@@ -255,7 +258,9 @@ struct RasterFrame {
   const uint2 *ranges;      // per rasterizer tile: [first, end) into ids
   const uint32_t *ids;      // surfel id per instance, grouped by tile, depth order inside
   const float4 *rec;        // this eye's blend records
+  const float4 *box;        // their screen bounds xmin, xmax, ymin, ymax (conservative)
   const uint8_t *roi;       // 16-pixel ROI mask: only its pixels are written, or null
+  const uint8_t *skip;      // 16-pixel tiles another step filled: not written, or null
   const uint32_t *items;    // listed tiles, or null: every tile in raster order
   const uint32_t *n_items;  // device count of the listed tiles
   float *rgb, *depth, *trans;  // [3][H][W], [H][W] (or null), [H][W] (or null)

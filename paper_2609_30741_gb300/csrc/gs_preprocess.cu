@@ -33,9 +33,9 @@ __global__ void setup_cams_kernel(PoseArgs pa, CamBlock *cams) {
     }
     c.fx = (float)pa.fx; c.fy = (float)pa.fy; c.cx = (float)pa.cx; c.cy = (float)pa.cy;
     c.W = pa.W; c.H = pa.H;
-    c.tshift = pa.tshift;
-    c.tiles_x = (pa.W + (1 << pa.tshift) - 1) >> pa.tshift;
-    c.tiles_y = (pa.H + (1 << pa.tshift) - 1) >> pa.tshift;
+    c.tshift = e == 0 ? pa.tshift : pa.tshift1;
+    c.tiles_x = (pa.W + (1 << c.tshift) - 1) >> c.tshift;
+    c.tiles_y = (pa.H + (1 << c.tshift) - 1) >> c.tshift;
   }
   // A parallel rig (equal orientation, baseline in the image plane, Sec. 4.2):
   // both cameras measure the same depth, z_aff = z_dom in exact arithmetic. The
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) preprocess_kernel(gs_scene sc, const CamB
     ws.cnt[e][i] = count;
     ws.rect[e][i] = rect;
     ws.zkey[e][i] = __float_as_uint(pc[2]);
-    if (ws.keep_intermediates) ws.bounds[e][i] = make_float4(xmin, xmax, ymin, ymax);
+    ws.bounds[e][i] = make_float4(xmin, xmax, ymin, ymax);
     if (count == 0) continue;
     const float U0 = c.fx * fmaf(-rx, M2[0], M0[0]), U1 = c.fx * fmaf(-rx, M2[1], M0[1]);
     const float V0 = c.fy * fmaf(-ry, M2[0], M1[0]), V1 = c.fy * fmaf(-ry, M2[1], M1[1]);
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256) preprocess_ellipsoid_kernel(gs_scene sc, 
     ws.cnt[e][i] = count;
     ws.rect[e][i] = rect;
     ws.zkey[e][i] = __float_as_uint(pc[2]);
-    if (ws.keep_intermediates) ws.bounds[e][i] = make_float4(xmin, xmax, ymin, ymax);
+    ws.bounds[e][i] = make_float4(xmin, xmax, ymin, ymax);
     if (count == 0) continue;
     const float l00 = sqrtf(cyy / det);
     const float l01 = -cxy / sqrtf(det * cyy);

@@ -13,8 +13,11 @@
 // the others and no CTA is launched per tile. A frame either offers every tile
 // of its grid or a device list of tiles (the ROI tiles of a masked binning).
 //
-// A CTA renders one TS x TS tile with TS^2 / PIX threads; every thread blends
-// PIX pixels of one column, TS / PIX rows apart. The homogeneous plane point p
+// A CTA renders one TS x TS tile with TS^2 / PIX threads. A warp covers a block
+// of 8 x (4 PIX) pixels (lane l: column l % 8, rows l / 8 + 4 q for q < PIX),
+// so it can skip, in one uniform branch, every record whose screen bounds miss
+// its block: those surfels cannot reach its pixels, and at 32-pixel tiles most
+// of a tile's surfels reach only a few of its blocks. The homogeneous plane point p
 // of a pixel is affine in the pixel offset (dx, dy) from the projected centre;
 // the thread forms the dx terms once per surfel and adds the dy terms per pixel
 // with three FMAs, so each surfel record read from shared memory serves PIX
@@ -114,9 +117,10 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
                                                                uint32_t *__restrict__ queue) {
   griddep_wait();
   constexpr int NT = TS * TS / PIX;  // threads
-  constexpr int RS = TS / PIX;       // rows between a thread's pixels
-  static_assert(NT % 32 == 0 && PIX <= 8, "block shape");
-  __shared__ float4 s0[2][BATCH], s1[2][BATCH], s2[2][BATCH], s3[2][BATCH];
+  constexpr int RS = 4;              // rows between a thread's pixels
+  constexpr int WBX = TS / 8;        // warp blocks per tile row
+  static_assert(NT % 32 == 0 && PIX <= 8 && TS % 8 == 0 && TS % (4 * PIX) == 0, "block shape");
+  __shared__ float4 s0[2][BATCH], s1[2][BATCH], s2[2][BATCH], s3[2][BATCH], s4[2][BATCH];
   __shared__ uint32_t s_first[kRasterFrames + 1];  // first work item of every frame
   __shared__ uint32_t s_item[2];                   // double-buffered: one barrier per item
 
@@ -136,7 +140,9 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
     s_first[f + 1] = c;
     if (f == 0) s_first[0] = 0u;
   }
-  const int lx = threadIdx.x % TS, ly = threadIdx.x / TS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int bx0 = (warp % WBX) * 8, by0 = (warp / WBX) * (4 * PIX);  // the warp's block in the tile
+  const int lx = bx0 + (lane & 7), ly = by0 + (lane >> 3);
 
   if (threadIdx.x == 0) s_item[0] = atomicAdd(queue, 1u);
   for (int it = 0;; it ^= 1) {
@@ -159,6 +165,9 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
 
     const float fx = (float)px;
     const float lowpass = fr.lowpass;
+    // the warp's pixel block (pixel centres), for the record culling
+    const float wx0 = (float)((tile % fr.tiles_x) * TS + bx0), wy0 = (float)((tile / fr.tiles_x) * TS + by0);
+    const float wx1 = wx0 + 7.f, wy1 = wy0 + (float)(4 * PIX - 1);
     // the thread's pixel rows; a pixel that is not blending (outside the image
     // or the ROI, or finished) has a NaN row, so every test on it fails
     float fy[PIX];
@@ -170,6 +179,7 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
       const int y = py + RS * q;
       bool on = px < W && y < H;
       if (on && fr.roi) on = fr.roi[(y / kTile) * rtx + px / kTile] != 0;
+      if (on && fr.skip) on = fr.skip[(y / kTile) * rtx + px / kTile] == 0;
       fy[q] = on ? (float)y : kNaN;
       if (on) live |= 1u << q;
     }
@@ -187,11 +197,13 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
             cp_async16(&s1[buf][slot], r + 1);
             cp_async16(&s2[buf][slot], r + 2);
             cp_async16(&s3[buf][slot], r + 3);
+            cp_async16(&s4[buf][slot], fr.box + id);
           } else {  // never expected; a record that cannot contribute keeps reads in bounds
             s0[buf][slot] = make_float4(0.f, 0.f, -1.f, 1.f);
             s1[buf][slot] = make_float4(0.f, 0.f, 0.f, 0.f);
             s2[buf][slot] = make_float4(1.f, 0.f, 0.f, 0.f);
             s3[buf][slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+            s4[buf][slot] = make_float4(1.f, 0.f, 1.f, 0.f);  // empty bounds
           }
         }
       }
@@ -209,6 +221,9 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
       const int nb = (int)min((uint32_t)BATCH, rg.y - b0);
 #pragma unroll 4
       for (int j = 0; j < nb && live; ++j) {
+        // warp-uniform: the record's bounds miss the warp's block
+        const float4 bb = s4[buf][j];
+        if (bb.y < wx0 || bb.x > wx1 || bb.w < wy0 || bb.z > wy1) continue;
         const float4 a = s0[buf][j];
         const float4 b = s1[buf][j];
         const float4 c = s2[buf][j];
@@ -412,7 +427,9 @@ RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift,
   f.ranges = ws.bin[eye].ranges;
   f.ids = ws.bin[eye].ival;
   f.rec = ws.rec[eye];
+  f.box = ws.bounds[eye];
   f.roi = (mask && tshift > 4) ? mask : nullptr;  // a 32-pixel tile may hold unmasked 16-pixel tiles
+  f.skip = nullptr;
   f.items = mask ? ws.bin[eye].items : nullptr;
   f.n_items = mask ? &ws.ctr->n_items[eye] : nullptr;
   f.rgb = rgb;

@@ -552,38 +552,25 @@ __global__ void __launch_bounds__(256) repair_pack8_kernel(const float *__restri
 // Candidate tiles (frame 0): tiles the ROI re-render would redraw that hold a hole
 // outside the edge strips. Only there can the gate save work; gap-only tiles
 // keep the cheap interpolation, and strip holes show content the dominant eye
-// never saw.
-__global__ void repair_tile_flags_kernel(const uint8_t *__restrict__ cls, const uint8_t *__restrict__ tile_mask,
-                                         int W, int H, uint8_t *__restrict__ flags) {
+// never saw. One CTA per 16x16 tile appends its tile to the list (in no fixed
+// order: a tile's network output and gate depend on that tile's pixels only)
+// and clears the tile's skip flag.
+__global__ void repair_tile_list_kernel(const uint8_t *__restrict__ cls, const uint8_t *__restrict__ tile_mask,
+                                        int W, int H, uint32_t *__restrict__ list, uint32_t *__restrict__ n_list,
+                                        uint8_t *__restrict__ skip) {
   griddep_wait();
   const int t = blockIdx.y * gridDim.x + blockIdx.x;
-  if (!tile_mask[t]) {
-    if (threadIdx.x == 0) flags[t] = 0;
-    return;
-  }
+  if (skip && threadIdx.x == 0) skip[t] = 0;
+  if (!tile_mask[t]) return;  // CTA-uniform
   const int x = blockIdx.x * kRT + (threadIdx.x & 15), y = blockIdx.y * kRT + (threadIdx.x >> 4);
   bool h = false;
   if (x < W && y < H) {
     const uint8_t c = cls[(size_t)y * W + x];
     h = (c & kClsHole) && !(c & kClsStrip);
   }
-  const int any = __syncthreads_or(h);
-  if (threadIdx.x == 0) flags[t] = any ? 1 : 0;
+  if (__syncthreads_or(h) && threadIdx.x == 0)
+    list[atomicAdd(n_list, 1u)] = ((uint32_t)blockIdx.y << 12) | (uint32_t)blockIdx.x;
 }
-
-struct TileFlagLoad {
-  const uint8_t *flags;
-  __device__ uint32_t operator()(uint32_t i) const { return flags[i]; }
-};
-struct TileListApply {
-  uint32_t *list;
-  uint32_t *n_out;
-  int tiles_x;
-  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
-    if (v) list[prefix] = ((i / (uint32_t)tiles_x) << 12) | (i % (uint32_t)tiles_x);
-  }
-  __device__ void end(uint32_t, uint32_t total) const { *n_out = total; }
-};
 
 // Gate >= tau: the tile's hole pixels take the (non-negative) fill, the tile
 // leaves the ROI re-render and its pixels are marked as repaired.
@@ -591,14 +578,18 @@ __global__ void repair_merge_kernel(const uint32_t *__restrict__ list, const uin
                                     const float *__restrict__ gate, float logit_tau,
                                     const unsigned long long *__restrict__ warp, const float *__restrict__ fill,
                                     int W, int H, int tiles_x, float *__restrict__ rgb_aff,
-                                    uint8_t *__restrict__ cls, uint8_t *__restrict__ tile_mask) {
+                                    uint8_t *__restrict__ cls, uint8_t *__restrict__ tile_mask,
+                                    uint8_t *__restrict__ skip) {
   griddep_wait();
   const uint32_t t = blockIdx.x;
   if (t >= *n_list || !(gate[t] >= logit_tau)) return;
   const uint32_t te = list[t];
   const int ty = (int)((te >> 12) & 0xfffu), tx = (int)(te & 0xfffu);
   const int x = tx * kRT + (threadIdx.x & 15), y = ty * kRT + (threadIdx.x >> 4);
-  if (threadIdx.x == 0) tile_mask[ty * tiles_x + tx] = 0;
+  if (threadIdx.x == 0) {
+    if (skip) skip[ty * tiles_x + tx] = 1;
+    else tile_mask[ty * tiles_x + tx] = 0;
+  }
   if (x >= W || y >= H) return;
   const size_t p = (size_t)y * W + x, hw = (size_t)W * H;
   if (warp[p] != ~0ull) return;
@@ -1083,15 +1074,13 @@ cudaError_t repair_calibrate_fp8(const Workspace &ws, const uint4 *feat, int W, 
 }
 
 cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, float *rgb_aff, cudaStream_t s,
-                          bool fp8) {
+                          bool fp8, uint8_t *skip) {
   cudaError_t e;
   const int tx = (W + kRT - 1) / kRT, ty = (H + kRT - 1) / kRT, nt = tx * ty;
-  launch_k(repair_tile_flags_kernel, dim3(tx, ty), 256, 0, s, ws.cls, ws.tile_mask, W, H, ws.rp_flags);
+  if ((e = cudaMemsetAsync(ws.rp_nlist, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+  launch_k(repair_tile_list_kernel, dim3(tx, ty), 256, 0, s, ws.cls, ws.tile_mask, W, H, ws.rp_list, ws.rp_nlist,
+           skip);
   GS_LAUNCHED(1);
-  if ((e = scan_launch(TileFlagLoad{ws.rp_flags}, TileListApply{ws.rp_list, ws.rp_nlist, tx},
-                       (const uint32_t *)nullptr, (uint32_t)nt, ws.bin[0].scan_tiles, ws.bin[0].scan_ticket, &ws.ctr->status, s)) !=
-      cudaSuccess)
-    return e;
   if ((e = repair_forward(ws, ws.rp_feat, W, H, ws.rp_list, ws.rp_nlist, (uint32_t)nt, ws.rp_fill, ws.rp_gate,
                           nullptr, nullptr, s, fp8, nullptr)) != cudaSuccess)
     return e;
@@ -1099,7 +1088,7 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
   const float tau = fminf(fmaxf(gate_tau, 1e-6f), 1.f - 1e-6f);
   const float logit_tau = logf(tau / (1.f - tau));
   launch_k(repair_merge_kernel, nt, 256, 0, s, ws.rp_list, ws.rp_nlist, ws.rp_gate, logit_tau, ws.warpbuf, ws.rp_fill, W, H,
-                                         tx, rgb_aff, ws.cls, ws.tile_mask);
+           tx, rgb_aff, ws.cls, ws.tile_mask, skip);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }

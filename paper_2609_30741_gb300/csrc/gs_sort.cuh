@@ -8,7 +8,7 @@
 //      device counter, ranks its pairs stably (per warp with bit ballots, then
 //      across warps), publishes its per-digit counts, and finds every digit's
 //      offset among the earlier tiles by decoupled look-back: it adds the
-//      published counts of its predecessors, 32 tiles per step, down to the
+//      published counts of its predecessors, 8 tiles per step, down to the
 //      nearest tile that has published an inclusive prefix, then publishes its
 //      own. The tile is sorted in shared memory and each digit run is written
 //      to its place with coalesced stores.
@@ -28,7 +28,7 @@ constexpr int kRsThreads = 256;
 constexpr int kRsItems = 8;
 constexpr int kRsTile = kRsThreads * kRsItems;  // 2048 pairs per tile
 constexpr int kRsPasses = 4;                    // 32-bit keys
-constexpr int kRsWindow = 32;                   // predecessor tiles read per look-back step
+constexpr int kRsWindow = 8;                    // predecessor tiles read per look-back step
 
 struct RadixScratch {
   uint32_t *hist;              // [kRsPasses][256] digit counts (0 between sorts)

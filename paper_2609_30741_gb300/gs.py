@@ -130,6 +130,8 @@ EXPORTS = {
     "gs_context_set_profiling": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_set_graphs": (C.c_int, [C.c_void_p, C.c_int]),
     "gs_context_set_raster": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig)]),
+    "gs_context_set_raster_roi": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig)]),
+    "gs_context_get_raster_roi": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig), C.POINTER(C.c_int)]),
     "gs_context_get_raster": (C.c_int, [C.c_void_p, C.POINTER(RasterConfig)]),
     "gs_context_stage_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)]),
     "gs_context_buffer": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t),
@@ -332,6 +334,18 @@ class Context:
         rc = RasterConfig()
         _check(lib().gs_context_get_raster(self.h, C.byref(rc)), "gs_context_get_raster")
         return rc.astuple()
+
+    def set_raster_roi(self, config=None):
+        """The ROI re-render's own (tile, pix, batch), or None to use set_raster's."""
+        rc = RasterConfig(*[int(v) for v in config]) if config is not None else None
+        _check(lib().gs_context_set_raster_roi(self.h, C.byref(rc) if rc is not None else None),
+               "gs_context_set_raster_roi")
+
+    def raster_roi(self):
+        """(the configuration the ROI re-render uses, whether one of its own is set)"""
+        rc, is_set = RasterConfig(), C.c_int()
+        _check(lib().gs_context_get_raster_roi(self.h, C.byref(rc), C.byref(is_set)), "gs_context_get_raster_roi")
+        return rc.astuple(), bool(is_set.value)
 
     def set_profiling(self, on: bool):
         _check(lib().gs_context_set_profiling(self.h, int(bool(on))), "gs_context_set_profiling")

@@ -316,6 +316,9 @@ def main():
                     help="stream the pairs in shards of this many frames (rendered on the fly), for pair counts "
                          "that do not fit resident; --steps is then per shard and --epochs passes are made")
     ap.add_argument("--epochs", type=int, default=1)
+    ap.add_argument("--eval-scenes", type=int, default=0,
+                    help="after training, evaluate on this many held-out scene seeds (3 poses each)")
+    ap.add_argument("--tau", type=float, default=0.5)
     args = ap.parse_args()
     dev = torch.device("cuda", 0)
     from . import build
@@ -327,6 +330,8 @@ def main():
         np.save(args.out, w)
         print(f"trained on {args.scenes * args.poses} pairs in shards of {args.shard}, {args.epochs} epochs, "
               f"{len(hist)} logged steps, {secs:.1f} s")
+        if args.eval_scenes:
+            _report_eval(args, w, dev)
         return
     ctx, pairs = build_pairs(args.scene, args.scenes, args.poses, args.seed, dev, args.surfels)
     w, hist, secs = train(ctx, pairs, args.steps, args.batch, args.lr, args.seed, gate_weight=args.gate_weight,
@@ -335,6 +340,18 @@ def main():
     for h in hist:
         print(f"step {h[0]:5d} loss {h[1]:.5f} l1 {h[2]:.5f} bce {h[3]:.5f} pos {h[4]:.3f}")
     print(f"trained {args.steps} steps in {secs:.1f} s on {pairs.n} frames, {pairs.tile_tensor().numel()} hole tiles")
+    if args.eval_scenes:
+        _report_eval(args, w, dev)
+
+
+def _report_eval(args, w, dev):
+    """Held-out scene seeds lie above every training seed."""
+    scene, cam, _, _ = scene_and_camera(args.scene, args.seed, args.surfels)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 26, device=dev)
+    ctx.repair_load(w)
+    seeds = [args.seed + 100000 + i for i in range(args.eval_scenes)]
+    ev = evaluate(ctx, args.scene, seeds, 3, args.seed + 1, args.tau, dev, args.surfels)
+    print("eval " + " ".join(f"{k}={v:.4f}" for k, v in ev.items()))
 
 
 if __name__ == "__main__":

@@ -139,3 +139,31 @@ def test_programmatic_launch_changes_nothing(gs):
     gs.set_programmatic_launch(True)
     for k in res[True]:
         assert torch.equal(res[True][k], res[False][k]), k
+
+
+@pytest.mark.parametrize("case", ["small", "object_ragged", "toed_in"])
+def test_roi_raster_config_is_bit_identical(gs, case):
+    """The ROI re-render in its own configuration (another tile edge than the
+    dominant eye's, also in depth_mode 2 where the strips render on a second
+    stream) gives the same stereo frame bit for bit."""
+    scene, cam, dom, aff = _case(case)
+    ds = gs.DeviceScene(scene)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24, min_tile=8)
+    for mode in (0, 2):
+        roi = gs.roi_params(depth_mode=mode)
+        for dom_cfg in ((32, 2, 64), (16, 4, 128)):
+            ctx.set_raster(*dom_cfg)
+            ctx.set_raster_roi(None)
+            for _ in range(2):  # depth_mode 2: the second call reuses the first one's range
+                ref = {k: v.clone() for k, v in ctx.render_stereo(ds, dom, aff, cam, roi=roi).items()}
+            ctx.check_ok()
+            for roi_cfg in ((16, 2, 64), (8, 2, 128), (32, 4, 256)):
+                ctx.set_raster_roi(roi_cfg)
+                assert ctx.raster_roi() == (roi_cfg, True)
+                for _ in range(2):
+                    got = ctx.render_stereo(ds, dom, aff, cam, roi=roi)
+                ctx.check_ok()
+                for k in ("rgb_dom", "rgb_aff", "cls_aff", "roi_count", "edge_widths"):
+                    assert torch.equal(ref[k], got[k]), (mode, dom_cfg, roi_cfg, k)
+    ctx.set_raster_roi(None)
+    assert ctx.raster_roi() == (ctx.raster(), False)
