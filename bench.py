@@ -1032,14 +1032,20 @@ def run_batched(args, dev, flush, weights):
 def run_unbounded(args, dev, flush):
     """The unbounded-scene learned repair (BF16): 1.5M surfels (60 % in a 1 m
     ball, 40 % on a 10-30 m shell), 1920x1080, f = 1600, 0.064 m baseline, eight
-    head poses on a 30 degree orbit at 3 m. The network is trained by the
-    library's kernels on 24 pairs from other seeds of the same distribution.
-    Returns the report, the weights and a calibration sample (features, tiles)."""
+    head poses on a 30 degree orbit at 3 m. The network is the packaged one,
+    trained by the library's kernels on 2,000 pairs of other seeds of the same
+    distribution (repair_train.UNBOUNDED_WEIGHTS); without that file it is
+    trained here on 24 pairs. Returns the report, the weights and a calibration
+    sample (features, tiles) for the FP8 scales."""
     import torch
     from paper_2609_30741_gb300 import gs, synth, repair_train as T
     t0 = time.time()
-    tctx, pairs = T.build_pairs("unbounded", 4, 6, 7100, dev)
-    w, hist, secs = T.train(tctx, pairs, 1500, 512, 1e-3, 7100, gate_weight=1.0)
+    packaged = os.path.exists(T.UNBOUNDED_WEIGHTS)
+    tctx, pairs = T.build_pairs("unbounded", 1 if packaged else 4, 8 if packaged else 6, 7100, dev)
+    if packaged:
+        w, hist = np.load(T.UNBOUNDED_WEIGHTS), None
+    else:
+        w, hist, secs = T.train(tctx, pairs, 1500, 512, 1e-3, 7100, gate_weight=1.0)
     tiles = pairs.tile_tensor()
     calib = (pairs.feat[:8].clone(), tiles[tiles < (8 << 24)][::4].contiguous())
     n_frames, n_tiles = pairs.n, int(tiles.numel())
@@ -1115,10 +1121,15 @@ def run_unbounded(args, dev, flush):
                      "centre_roi_pixel_share": float(np.mean(cen_fr)),
                      "non_strip_hole_pixel_share": float(np.mean(hole_fr))}
     res["gain_bound"] = gain_bound(res["plain"], res.pop("centre_step_off"), res["learned_bf16"], res["learned_fp8"])
-    res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "seconds": round(train_s, 1),
-                       "loss_first_last": [hist[0][1], hist[-1][1]],
-                       "data": "unbounded-distribution seeds 7100-7103 (1.5M surfels each), 6 random head poses "
-                               "each, 1920x1080"}
+    if packaged:
+        res["training"] = dict(T.UNBOUNDED_TRAINING, weights="paper_2609_30741_gb300/weights/"
+                               "repair_unbounded_2000pairs.npy (repair_train, see its docstring)",
+                               fp8_calibration=f"{n_frames} frames of unbounded seed 7100")
+    else:
+        res["training"] = {"frames": n_frames, "hole_tiles": n_tiles, "steps": 1500, "seconds": round(train_s, 1),
+                           "loss_first_last": [hist[0][1], hist[-1][1]],
+                           "data": "unbounded-distribution seeds 7100-7103 (1.5M surfels each), 6 random head "
+                                   "poses each, 1920x1080"}
     return res, w, calib
 
 

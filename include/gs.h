@@ -413,6 +413,25 @@ gs_status gs_context_set_counting(gs_context *ctx, int enable);
 gs_status gs_ssim(gs_context *ctx, const float *img, const float *ref, int width, int height, int channels,
                   float *ssim);
 
+/* Centre ROIs of a caller-given class map (Sec. 3.1 Stage 3, Step 2, the step
+ * gs_render_stereo runs after its classification): the 4-connected components
+ * of the pixels whose class has GS_CLS_CENTRE set, each component's bounding box
+ * grown by `margin` pixels, aligned outward to the 16-pixel tile grid and
+ * clipped to the image.
+ *   cls        device uint8[height][width], the classes of gs_outputs.cls_aff
+ *              (only the GS_CLS_CENTRE bit is read), within the size limits;
+ *   rects      device int32[max_rects][4]: x0, y0, x1, y1 (x1, y1 exclusive) per
+ *              component, in increasing order of the component's first pixel in
+ *              row-major order; entries past the count are left unspecified;
+ *   count      device int32: the number of components, which may exceed the
+ *              context's max_rects (then only max_rects are written and
+ *              gs_context_check reports GS_ERR_CAPACITY);
+ *   tile_mask  optional device uint8[ceil(height/16)][ceil(width/16)]: 1 is
+ *              written on every tile of a rectangle (nothing is cleared).
+ * Needs the stereo path (GS_PATH_STEREO). Asynchronous on the context's stream. */
+gs_status gs_centre_rois(gs_context *ctx, const uint8_t *cls, int width, int height, int margin, int32_t *rects,
+                         int32_t *count, uint8_t *tile_mask);
+
 /* Rasterizer configuration (no counterpart in the paper, which fixes 16x16
  * tiles for the ROI grid, Sec. 3.5; the tile edge of the rasterizer itself is a
  * free choice of the 2DGS/3DGS tile rasterizer it builds on).

@@ -41,7 +41,8 @@ class OrSplat(C.Structure):
     _fields_ = [("visible", C.c_int), ("pc", C.c_double * 3), ("M", C.c_double * 9),
                 ("opacity", C.c_double), ("rc2", C.c_double), ("lp2", C.c_double),
                 ("cx", C.c_double), ("cy", C.c_double), ("rgb", C.c_double * 3),
-                ("key", C.c_float), ("box", C.c_double * 4), ("prim", C.c_int), ("conic", C.c_double * 3)]
+                ("key", C.c_float), ("box", C.c_double * 4), ("prim", C.c_int), ("conic", C.c_double * 3),
+                ("su", C.c_double), ("sv", C.c_double), ("pscale", C.c_double)]
 
 
 CLS_HOLE, CLS_GAP, CLS_CENTRE, CLS_STRIP, CLS_RENDER = 1, 2, 4, 8, 16
@@ -110,11 +111,19 @@ def eval_pair(splat, cam, x, y):
     return oG, d.value, r3.value, r2.value
 
 
+def rho3_err(splat, cam, x, y, rho3, lam):
+    """First-order bound on the float32 error of rho3 at pixel (x, y)."""
+    lib().or_rho3_err.restype = C.c_double
+    return lib().or_rho3_err(C.byref(splat), C.byref(cam_struct(cam)), C.c_double(x), C.c_double(y),
+                             C.c_double(rho3), C.c_double(lam))
+
+
 def render(scene, pose, cam, bg=(0.0, 0.0, 0.0), window=None, fp32_bound=False):
     """Full render of `window` = (x0, y0, w, h) (default: the whole image).
     Returns rgb [3,h,w], depth [h,w], trans [h,w], margin [h,w], pairs, and with
     fp32_bound=True also the per-pixel bound [h,w] on the error of a float32
-    evaluation of the same sum."""
+    evaluation of the same sum; the margins then also account for the float32
+    error of each surfel's rho3."""
     x0, y0, w, h = window if window is not None else (0, 0, cam.width, cam.height)
     rgb = np.zeros((3, h, w))
     dep = np.zeros((h, w))

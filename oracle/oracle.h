@@ -58,7 +58,13 @@ typedef struct {
   double box[4];    /* xmin, xmax, ymin, ymax enclosing the whole support (a cheap exact reject) */
   int prim;         /* 0: surfel; 1: ellipsoid */
   double conic[3];  /* ellipsoid: inverse of the 2-D screen covariance (xx, xy, yy) */
+  double su, sv;    /* surfel scales: the lengths of the columns s_u t_u^c, s_v t_v^c */
+  double pscale;    /* |P| + |t|: the magnitude a float32 camera transform of the centre rounds */
 } or_splat;
+
+/* First-order bound on the float32 error of a surfel's rho3 at pixel (x, y),
+ * whose FP64 value is rho3 at intersection depth lam (0 for ellipsoids). */
+double or_rho3_err(const or_splat *s, const or_cam *cam, double x, double y, double rho3, double lam);
 
 /* ---- constants of the blending rule (3DGS/2DGS rasterizer conventions) ---- */
 #define OR_Z_NEAR 0.2
@@ -96,7 +102,10 @@ double or_eval(const or_splat *s, const or_cam *cam, double x, double y, double 
  * decision that can move the result by more than 1e-5 to its threshold.
  * pairs (optional) receives the number of in-support evaluations.
  * fp32_bound (optional) receives, per pixel, a first-order bound on the error
- * of a float32 evaluation of the same blending sum (see render.c).
+ * of a float32 evaluation of the same blending sum (see render.c); with it
+ * requested, the margins also take the float32 error of each surfel's rho3
+ * (or_rho3_err) into account: a skip decision closer to its threshold than
+ * that error gets a negative margin.
  * Returns the number of visible surfels, or -1 on bad arguments. */
 int or_render(const or_scene *sc, const or_pose *pose, const or_cam *cam, const double bg[3],
               int x0, int y0, int w, int h, double *rgb, double *depth, double *trans,

@@ -230,6 +230,9 @@ static void prepare_one(const or_scene *sc, const or_pose *pose, const or_cam *c
   const double eps = 1e-6;
   s->box[0] = xmin - eps; s->box[1] = xmax + eps; s->box[2] = ymin - eps; s->box[3] = ymax + eps;
   for (int k = 0; k < 3; ++k) s->pc[k] = pc[k];
+  s->su = su;
+  s->sv = sv;
+  s->pscale = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]) + sqrt(t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
   /* view-dependent colour from the camera centre t towards p_k */
   double dir[3] = {dp[0], dp[1], dp[2]};
   const double dn = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
@@ -297,6 +300,34 @@ double or_eval(const or_splat *s, const or_cam *cam, double x, double y, double 
   return s->opacity * exp(-0.5 * rho);
 }
 
+/* First-order bound on the error of rho3 = u^2 + v^2 when the intersection is
+ * evaluated in float32 (the reading of the tolerance's scope: a float32
+ * evaluation of the blend). The solve's inputs carry float32 rounding: the
+ * camera-frame centre p_c about c u (|P| + |t|) (a float32 camera transform),
+ * the tangent columns and the ray relative c u. Moving the plane by dP moves
+ * the intersection along the plane by up to dP (1 + G), G = |n| |r| / |n . r|
+ * the inverse cosine between the ray and the normal n = m0 x m1 (large for a
+ * surfel seen nearly edge-on), and (u, v) by that over the shorter column;
+ * then d rho3 <= 2 sqrt(rho3) d(u, v) + d(u, v)^2. */
+#define OR_U (1.0 / 16777216.0) /* float32 unit roundoff */
+#define OR_RHO_C 1.0
+double or_rho3_err(const or_splat *s, const or_cam *cam, double x, double y, double rho3, double lam) {
+  if (s->prim != 0 || !isfinite(rho3)) return 0.0;
+  const double r[3] = {(x - cam->cx) / cam->fx, (y - cam->cy) / cam->fy, 1.0};
+  const double m0[3] = {s->M[0], s->M[3], s->M[6]}, m1[3] = {s->M[1], s->M[4], s->M[7]};
+  const double n[3] = {m0[1] * m1[2] - m0[2] * m1[1], m0[2] * m1[0] - m0[0] * m1[2], m0[0] * m1[1] - m0[1] * m1[0]};
+  const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  const double rn = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+  const double nr = fabs(n[0] * r[0] + n[1] * r[1] + n[2] * r[2]);
+  const double smin = fmin(s->su, s->sv);
+  if (!(nr > 0.0) || !(smin > 0.0)) return INFINITY;
+  const double G = nn * rn / nr;
+  const double q = sqrt(rho3);
+  const double dP = OR_RHO_C * OR_U * (s->pscale + q * (s->su + s->sv) + lam * rn);
+  const double duv = dP * (1.0 + G) / smin;
+  return 2.0 * q * duv + duv * duv;
+}
+
 typedef struct {
   float key;
   int idx;
@@ -330,16 +361,25 @@ static uint32_t fbits(float f) {
 
 /* Front-to-back blend of one pixel over all visible surfels in depth order. */
 /* A first-order bound on how far a float32 evaluation of the same blending sum
- * can be from the exact one at this pixel (u = 2^-24): alpha carries a relative
- * error of about 3u + 4u rho (the exponential and its argument; none once
- * clamped at 0.99), and through (1 - alpha) each factor of the running
- * transmittance adds 2u + alpha / (1 - alpha) times that error; every weight
- * alpha T then carries the errors of its alpha and of its T, each colour about
- * 20u of its magnitude (at least 0.5), and the n-term sum nu of the total.
+ * can be from the exact one at this pixel (u = 2^-24). Two parts:
+ *  - rounding of the blend itself: alpha carries a relative error of about
+ *    3u + 4u rho (the exponential and its argument; none once clamped at 0.99),
+ *    and through (1 - alpha) each factor of the running transmittance adds
+ *    2u + alpha / (1 - alpha) times that error; every weight alpha T then carries
+ *    the errors of its alpha and of its T, each colour about 20u of its magnitude
+ *    (at least 0.5), and the n-term sum nu of the total;
+ *  - the conditioning of the ray-plane solve: alpha_k moves by alpha_k e_k,
+ *    e_k = half the float32 error of rho3 (or_rho3_err) where that term decides,
+ *    and the colour moves by dC/dalpha_k = T_k c_k - C_behind_k / (1 - alpha_k)
+ *    times that (C_behind_k: everything blended behind k, the background
+ *    included). The largest of these terms enters: the surfels' roundings are
+ *    independent, and their worst cases summed over a pixel's contributors
+ *    overstate a float32 evaluation's error ten to twenty times on 3M-surfel
+ *    scenes, while a pixel where one surfel alone can move the colour past the
+ *    tolerance (a surfel seen nearly edge-on) is what cannot meet it.
  * Used by the tests to tell pixels whose float32 value cannot meet an absolute
  * tolerance by construction from pixels that must. */
-#define OR_U (1.0 / 16777216.0)
-
+#define OR_MAX_CONTRIB 2560 /* T >= 1e-4 with alpha >= 1/255 allows at most 2345 */
 static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_cam *cam,
                          const double bg[3], double x, double y, double out_rgb[3],
                          double *out_d, double *out_t, double *out_margin, int64_t *out_pairs,
@@ -351,24 +391,37 @@ static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_
   int have_prev = 0;
   float prev_key = 0.f;
   double prev_w = 0.0;
+  /* per contributor: T, alpha, the alpha error of the solve's conditioning, colour */
+  double (*ck)[6] = out_bound ? (double (*)[6])malloc(sizeof(double[6]) * OR_MAX_CONTRIB) : NULL;
   for (int k = 0; k < nvis; ++k) {
     const or_splat *s = &sp[ord[k]];
     if (x < s->box[0] || x > s->box[1] || y < s->box[2] || y > s->box[3]) continue;
     double dep, rho3, rho2;
     const double oG = or_eval(s, cam, x, y, &dep, &rho3, &rho2);
     ++pairs;
+    /* float32 error of rho3, and of rho = min(rho3, rho2) (rho3 may dip below
+     * the low-pass term by that much); only with the bound requested */
+    const double erho3 = out_bound ? or_rho3_err(s, cam, x, y, rho3, dep) : 0.0;
+    const double erho = rho3 <= rho2 ? erho3 : fmax(0.0, erho3 - (rho3 - rho2));
+    const double rho = isfinite(rho3) ? fmin(rho3, rho2) : rho2;
     /* margins of the skip and stop decisions, at any transmittance: a flip adds
      * or drops a weight alpha T, and a deep surfel behind a near one moves the
-     * depth proxy by alpha T d, relatively more than the colour */
+     * depth proxy by alpha T d, relatively more than the colour. The skip
+     * threshold alpha = 1/255 is rho = rc2: the decision is only safe when rho
+     * lies farther from rc2 than its float32 error (in the same relative units:
+     * half the rho gap). */
     mrg = fmin(mrg, fabs(oG * 255.0 - 1.0));
+    if (erho > 0.0) mrg = fmin(mrg, 0.5 * (fabs(rho - s->rc2) - erho));
     const double a = oG < OR_ALPHA_MAX ? oG : OR_ALPHA_MAX;
     if (a < OR_ALPHA_MIN) continue;
+    const double ea = a < OR_ALPHA_MAX ? OR_U * (3.0 + 4.0 * rho) : 0.0;
+    const double ec = a < OR_ALPHA_MAX ? 0.5 * erho : 0.0;
     const double Tn = T * (1.0 - a);
-    mrg = fmin(mrg, fabs(Tn - OR_T_MIN) / OR_T_MIN);
+    mrg = fmin(mrg, fabs(Tn - OR_T_MIN) / OR_T_MIN - (eT + a / (1.0 - a) * (ea + ec)));
     if (Tn < OR_T_MIN) break;
     const double w = a * T;
     if (isfinite(rho3) && w * fabs(dep - s->pc[2]) > 1e-5 * s->pc[2])
-      mrg = fmin(mrg, fabs(rho3 - rho2) / fmax(rho3, rho2));
+      mrg = fmin(mrg, (fabs(rho3 - rho2) - erho3) / fmax(rho3, rho2));
     if (have_prev && w > 1e-3 && prev_w > 1e-3) {
       const uint32_t kb = fbits(s->key), pb = fbits(prev_key);
       const uint32_t du = kb > pb ? kb - pb : pb - kb;
@@ -376,24 +429,41 @@ static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_
     }
     for (int ch = 0; ch < 3; ++ch) C[ch] += w * s->rgb[ch];
     D += w * dep;
+    const double cm = fmax(fmax(fabs(s->rgb[0]), fabs(s->rgb[1])), fabs(s->rgb[2]));
+    bnd += w * (cm * (eT + ea + OR_U) + 20.0 * OR_U * fmax(cm, 0.5));
+    cabs += w * cm;
+    /* the transmittance's relative error: rounding, and the conditioning errors
+     * of the alphas in front (those also enter through the per-alpha sum below) */
+    eT += 2.0 * OR_U + a / (1.0 - a) * (ea + ec);
+    if (ck && ncontrib < OR_MAX_CONTRIB) {
+      ck[ncontrib][0] = T;
+      ck[ncontrib][1] = a;
+      ck[ncontrib][2] = ec;
+      for (int ch = 0; ch < 3; ++ch) ck[ncontrib][3 + ch] = s->rgb[ch];
+    }
     T = Tn;
     have_prev = 1; prev_key = s->key; prev_w = w;
-    if (out_bound) {
-      const double rho = isfinite(rho3) ? fmin(rho3, rho2) : rho2;
-      const double ea = a < OR_ALPHA_MAX ? OR_U * (3.0 + 4.0 * rho) : 0.0;
-      const double cm = fmax(fmax(fabs(s->rgb[0]), fabs(s->rgb[1])), fabs(s->rgb[2]));
-      bnd += w * (cm * (eT + ea + OR_U) + 20.0 * OR_U * fmax(cm, 0.5));
-      cabs += w * cm;
-      eT += 2.0 * OR_U + a / (1.0 - a) * ea;
-      ++ncontrib;
-    }
+    ++ncontrib;
   }
   for (int ch = 0; ch < 3; ++ch) out_rgb[ch] = C[ch] + T * (bg ? bg[ch] : 0.0);
   *out_d = D;
   *out_t = T;
   if (out_margin) *out_margin = mrg;
   if (out_pairs) *out_pairs = pairs;
-  if (out_bound) *out_bound = bnd + ncontrib * OR_U * cabs;
+  if (out_bound) {
+    /* the conditioning part: back to front, C_behind accumulates */
+    double cb[3] = {T * (bg ? bg[0] : 0.0), T * (bg ? bg[1] : 0.0), T * (bg ? bg[2] : 0.0)}, cond = 0.0;
+    const int nk = ncontrib < OR_MAX_CONTRIB ? ncontrib : OR_MAX_CONTRIB;
+    for (int k = nk - 1; k >= 0; --k) {
+      const double Tk = ck[k][0], ak = ck[k][1], eck = ck[k][2];
+      double sens = 0.0;
+      for (int ch = 0; ch < 3; ++ch) sens = fmax(sens, fabs(Tk * ck[k][3 + ch] - cb[ch] / (1.0 - ak)));
+      cond = fmax(cond, sens * ak * eck);
+      for (int ch = 0; ch < 3; ++ch) cb[ch] += Tk * ak * ck[k][3 + ch];
+    }
+    *out_bound = bnd + ncontrib * OR_U * cabs + cond;
+    free(ck);
+  }
 }
 
 int or_render(const or_scene *sc, const or_pose *pose, const or_cam *cam, const double bg[3],

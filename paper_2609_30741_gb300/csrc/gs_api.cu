@@ -89,6 +89,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     b.items = c.take<uint32_t>(tiles);
     b.rqueue = c.take<uint32_t>(2);
     b.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
+    b.mask_clip = c.take<uint16_t>(2 * rty * rtx);
     b.rs_hist = c.take<uint32_t>(2 * kRsPasses * 256);
     b.rs_status = c.take<unsigned long long>(rs_words);
     b.rs_ctl = c.take<uint32_t>(4);
@@ -930,6 +931,23 @@ gs_status gs_ssim(gs_context *ctx, const float *img, const float *ref, int width
       height > ctx->lim.max_height || channels < 1 || channels > 3)
     return GS_ERR_BAD_ARG;
   return cuda_status(launch_ssim(img, ref, width, height, channels, ctx->ws.ssim_part, ssim, ctx->stream));
+}
+
+gs_status gs_centre_rois(gs_context *ctx, const uint8_t *cls, int width, int height, int margin, int32_t *rects,
+                         int32_t *count, uint8_t *tile_mask) {
+  if (!ctx || !cls || !rects || !count || width <= 0 || height <= 0 || width > ctx->lim.max_width ||
+      height > ctx->lim.max_height || margin < 0)
+    return GS_ERR_BAD_ARG;
+  if (!(ctx->ws.paths & GS_PATH_STEREO)) return GS_ERR_BAD_ARG;
+  const Workspace &ws = ctx->ws;
+  // without a caller mask the tiles land in the workspace's ROI mask
+  cudaError_t e = launch_centre_rois_of(ws, cls, width, height, margin, tile_mask ? tile_mask : ws.tile_mask,
+                                        ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(rects, ws.rects, sizeof(int4) * (size_t)ws.max_rects, cudaMemcpyDeviceToDevice, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(count, &ws.ctr->n_rects, sizeof(uint32_t), cudaMemcpyDeviceToDevice, ctx->stream);
+  return cuda_status(e);
 }
 
 gs_status gs_context_set_graphs(gs_context *ctx, int enable) {

@@ -87,10 +87,12 @@ __device__ __forceinline__ void row_ranges(const Conic &q, const float4 r0, int 
 // thread adds one column down the rows.
 // With roi16 given, the mask is first derived from the ROI mask on the 16-pixel
 // grid (rtx x rty tiles): a tile of edge 1 << tshift is masked when it holds a
-// masked pixel.
+// masked pixel. clip[0][ty][tx] / clip[1][ty][tx] get the first masked column
+// >= tx / the last masked column <= tx of row ty (0xffff: none), by ballots 32
+// columns at a time with the carry of the columns already passed.
 __global__ void __launch_bounds__(1024) mask_sat_kernel(uint8_t *mask, int tiles_x, int tiles_y,
                                                         uint32_t *__restrict__ sat, const uint8_t *__restrict__ roi16,
-                                                        int rtx, int rty, int tshift) {
+                                                        int rtx, int rty, int tshift, uint16_t *__restrict__ clip) {
   griddep_wait();
   if (roi16) {
     for (int t = threadIdx.x; t < tiles_x * tiles_y; t += blockDim.x) {
@@ -112,6 +114,26 @@ __global__ void __launch_bounds__(1024) mask_sat_kernel(uint8_t *mask, int tiles
   }
   const int sx = tiles_x + 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nt = tiles_x * tiles_y;
+  for (int y = wid; y < tiles_y; y += nw) {
+    const uint8_t *row = mask + (size_t)y * tiles_x;
+    uint32_t carry = 0xffffu;  // previous masked column: left to right
+    for (int x0 = 0; x0 < tiles_x; x0 += 32) {  // warp-uniform
+      const int x = x0 + lane;
+      const uint32_t b = __ballot_sync(0xffffffffu, x < tiles_x && row[x] != 0);
+      const uint32_t le = b & (0xffffffffu >> (31 - lane));  // columns <= x
+      if (x < tiles_x) clip[nt + y * tiles_x + x] = (uint16_t)(le ? (uint32_t)x0 + 31u - __clz(le) : carry);
+      if (b) carry = (uint32_t)x0 + 31u - __clz(b);
+    }
+    carry = 0xffffu;  // next masked column: right to left
+    for (int x0 = (tiles_x - 1) & ~31; x0 >= 0; x0 -= 32) {  // warp-uniform
+      const int x = x0 + lane;
+      const uint32_t b = __ballot_sync(0xffffffffu, x < tiles_x && row[x] != 0);
+      const uint32_t ge = b & (0xffffffffu << lane);  // columns >= x
+      if (x < tiles_x) clip[y * tiles_x + x] = (uint16_t)(ge ? (uint32_t)x0 + (uint32_t)__ffs(ge) - 1u : carry);
+      if (b) carry = (uint32_t)x0 + (uint32_t)__ffs(b) - 1u;
+    }
+  }
   for (int y = wid; y <= tiles_y; y += nw) {
     uint32_t acc = 0;
     if (lane == 0) sat[(size_t)y * sx] = 0u;
@@ -143,29 +165,20 @@ __device__ __forceinline__ bool sat_any(const uint32_t *sat, int tiles_x, int y0
 }
 
 // The masked tiles of tile row ty between columns [x0, x1]: the span clipped to
-// its first and last masked tile (empty, lo > hi, when it has none). The tiles
-// in between may still be unmasked; the counting sort skips those one by one.
-__device__ __forceinline__ void clip_to_mask(const uint32_t *sat, int tiles_x, int ty, int &x0, int &x1) {
+// its first and last masked tile (empty, lo > hi, when it has none), from the
+// row's next / previous masked-column tables. The tiles in between may still be
+// unmasked; the counting sort skips those one by one.
+__device__ __forceinline__ void clip_to_mask(const uint16_t *clip, int tiles_x, int tiles_y, int ty, int &x0,
+                                             int &x1) {
   if (x0 > x1) return;
-  if (!sat_any(sat, tiles_x, ty, ty, x0, x1)) {
+  const int first = clip[ty * tiles_x + x0];  // 0xffff when none: beyond any column
+  if (first > x1) {
     x0 = 1;
     x1 = 0;
     return;
   }
-  int lo = x0, hi = x1;  // first masked: smallest c with a masked tile in [x0, c]
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (sat_any(sat, tiles_x, ty, ty, x0, mid)) hi = mid; else lo = mid + 1;
-  }
-  const int first = lo;
-  lo = first;
-  hi = x1;  // last masked: largest c with a masked tile in [c, x1]
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (sat_any(sat, tiles_x, ty, ty, mid, x1)) lo = mid; else hi = mid - 1;
-  }
+  x1 = clip[tiles_x * tiles_y + ty * tiles_x + x1];
   x0 = first;
-  x1 = lo;
 }
 
 // ---------------------------------------------------------------- row spans
@@ -183,8 +196,8 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
                                                    const CamBlock *__restrict__ cams, int eye, int prim,
                                                    uint32_t *__restrict__ row_off, uint2 *__restrict__ spans,
                                                    uint32_t cap, uint32_t *__restrict__ n_rows,
-                                                   uint32_t *__restrict__ status, const uint32_t *__restrict__ sat,
-                                                   int sat_tiles_x) {
+                                                   uint32_t *__restrict__ status, const uint16_t *__restrict__ clip,
+                                                   int clip_tiles_x, int clip_tiles_y) {
   griddep_wait();
   const int lane = threadIdx.x & 31;
   const uint32_t n = load_n(n_ptr, n_max);
@@ -253,9 +266,9 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
     if (qq < total && slot < cap) {
       int a0 = sx0, a1 = sx1, c0 = 1, c1 = 0;
       if (qk.ok) row_ranges(qk, ck, ty, W, H, sx0, sx1, tshift, a0, a1, c0, c1);
-      if (sat) {  // an ROI binning: only the masked part of each range
-        clip_to_mask(sat, sat_tiles_x, ty, a0, a1);
-        clip_to_mask(sat, sat_tiles_x, ty, c0, c1);
+      if (clip) {  // an ROI binning: only the masked part of each range
+        clip_to_mask(clip, clip_tiles_x, clip_tiles_y, ty, a0, a1);
+        clip_to_mask(clip, clip_tiles_x, clip_tiles_y, ty, c0, c1);
         if (a0 > a1) { a0 = c0; a1 = c1; c0 = 1; c1 = 0; }
       }
       // empty ranges are stored as [1, 0]
@@ -278,11 +291,12 @@ struct VisibleLoad {
   const uint32_t *sat;        // summed-area table of the ROI mask, or null
   int tiles_x;
   __device__ uint32_t operator()(uint32_t i) const {
+    // the count and the rectangle are loaded together (one memory round trip)
     const bool mine = cnt[i] > 0u;
+    const ushort4 rc = sat ? rect[i] : make_ushort4(0, 0, 0, 0);
     if (cnt_other) return (mine || cnt_other[i] > 0u) ? 1u : 0u;
     if (!mine) return 0u;
     if (!sat) return 1u;
-    const ushort4 rc = rect[i];
     return sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z) ? 1u : 0u;
   }
 };
@@ -331,9 +345,11 @@ struct ReuseLoad {
   __device__ uint32_t operator()(uint32_t i) const {
     if (i >= load_n(n_union, n_max)) return 0u;
     const uint32_t id = uval[i];
-    if (cnt[id] == 0u) return 0u;
+    // the count and the rectangle are loaded together (one memory round trip)
+    const uint32_t c = cnt[id];
+    const ushort4 rc = sat ? rect[id] : make_ushort4(0, 0, 0, 0);
+    if (c == 0u) return 0u;
     if (!sat) return 1u;
-    const ushort4 rc = rect[id];
     return sat_any(sat, tiles_x, rc.y, rc.w, rc.x, rc.z) ? 1u : 0u;
   }
 };
@@ -800,7 +816,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   const RadixScratch rs{b.rs_hist, b.rs_hist + kRsPasses * 256, b.rs_status, b.rs_ctl, &ctr->status};
   if (tile_mask) {  // (the rasterizer-grid mask and) its summed-area table
     launch_k(mask_sat_kernel, 1, 1024, 0, s, const_cast<uint8_t *>(tile_mask), tiles_x, tiles_y, b.mask_sat, roi16,
-             (W + kTile - 1) / kTile, (H + kTile - 1) / kTile, roi16 ? tshift : 4);
+             (W + kTile - 1) / kTile, (H + kTile - 1) / kTile, roi16 ? tshift : 4, b.mask_clip);
     GS_LAUNCHED(1);
   }
   const uint32_t chunk = kBinWarps * ws.bin_warp_surfels;
@@ -825,7 +841,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
     launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, b.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
                                                 ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.prim, ws.row_off[eye],
                                                 ws.spans[eye], cap, &ctr->n_rows[eye],
-                                                &ctr->status, sat, tiles_x);
+                                                &ctr->status, tile_mask ? b.mask_clip : nullptr, tiles_x, tiles_y);
     GS_LAUNCHED(1);
   }
   // 3. depth order (the low 32 bits of the packed key; stable, so ties keep id order)

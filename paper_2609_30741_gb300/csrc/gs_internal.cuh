@@ -104,6 +104,7 @@ struct BinScratch {
   uint32_t *items;              // rasterizer tiles of the last masked binning
   uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
   uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
+  uint16_t *mask_clip;          // [2][tiles_y][tiles_x]: next / previous masked tile of the row (0xffff: none)
   uint32_t *rs_hist;            // radix sort: [4][256] digit counts, then [4][256] digit bases
   unsigned long long *rs_status;// radix sort look-back words [tiles][256]
   uint32_t *rs_ctl;             // radix sort control words (zero at creation)
@@ -229,6 +230,10 @@ struct RepairOpt {
 };
 cudaError_t prepare_repair();
 cudaError_t prepare_reproject();
+// The classification's centre-hole list of a caller-given class map, then the
+// component labelling into ws.rects (gs_centre_rois).
+cudaError_t launch_centre_rois_of(const Workspace &ws, const uint8_t *cls, int W, int H, int margin,
+                                  uint8_t *tile_mask, cudaStream_t s);
 size_t repair_train_scratch_bytes(int n_tiles);
 cudaError_t repair_pack(const Workspace &ws, cudaStream_t s);
 // Features from the warp buffer and the affiliated image after hole

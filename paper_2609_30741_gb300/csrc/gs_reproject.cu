@@ -327,72 +327,51 @@ __global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_
 // the smaller one), which also gives the canonical rectangle order.
 constexpr int kMaxUnionSteps = 1 << 22;
 
-__device__ __forceinline__ int find_root(const int32_t *L, int x) {
-  int steps = 0;
-  int p = __ldcg(L + x);
-  while (p != x && steps < kMaxUnionSteps) {
-    x = p;
-    p = __ldcg(L + x);
-    ++steps;
-  }
-  return x;
-}
-
-__device__ void unite(int32_t *L, int a, int b, uint32_t *status) {
-  for (int it = 0; it < kMaxUnionSteps; ++it) {
-    a = find_root(L, a);
-    b = find_root(L, b);
-    if (a == b) return;
-    if (a < b) {
-      const int t = a;
-      a = b;
-      b = t;
-    }
-    // link the larger root a below b; succeeds only if a is still a root
-    const int old = atomicMin(L + a, b);
-    if (old == a) return;
-    a = old;
-  }
-  atomicOr(status, kStTimeout);
-}
-
 // One CTA labels the components over the classification's list of centre-hole
 // pixels (about 0.1 % of the frame on the workloads here, so a full-image pass
-// per phase would cost more than the labelling). The list (up to kCcSmem
-// pixels) and the union-find parents live in shared memory, indexed by list
-// position; a pixel's neighbours are found through labels[] (its list
-// position, written by the classification). Phases, separated by block
-// barriers:
-//   1. union with the left and upper neighbours that are centre holes, always
-//      linking the root with the larger pixel index below the other, so every
-//      component's root is its smallest pixel (the canonical rectangle order);
+// per phase would cost more than the labelling). A pixel's neighbours are found
+// through labels[] (its list position, written by the classification) once the
+// class map says they are centre holes. Phases, separated by block barriers:
+//   1. union with the left and the upper neighbour: the root with the larger
+//      pixel is linked below the other by a CAS (bounded retries), so every
+//      component's root is its smallest pixel, the canonical rectangle order;
+//      finds halve their paths;
 //   2. every entry's parent to its root;
-//   3. the roots in increasing pixel order (up to one root per thread: ranked by
-//      counting the smaller roots; up to kCcSortMax: a bitonic sort in shared
-//      memory);
-//   4. bounding boxes (shared-memory atomics);
+//   3. the roots' ranks by pixel are the rectangle slots: up to kCcBoxes roots
+//      are sorted (bitonic) and found by binary search, more are ranked through
+//      a bitmap of the root pixels and its per-word prefix counts;
+//   4. bounding boxes (shared-memory atomics up to kCcBoxes components, else
+//      global atomics on the rectangles);
 //   5. expand by m, align outward to tiles, clip, mark the tiles.
-// Longer lists take the same phases with the parents in global memory.
+// Up to kCcFast entries the list and the parents live in shared memory, longer
+// lists keep them in global memory.
 constexpr int kCcThreads = 1024;
-constexpr int kCcSmem = 8192;
-constexpr int kCcSortMax = 4096;
-constexpr size_t kCcSmemBytes = sizeof(uint32_t) * (2 * kCcSmem + kCcSortMax);
+constexpr int kCcFast = 16384;   // entries whose list and parents stay in shared memory
+constexpr int kCcBoxes = 4096;   // components sorted and boxed in shared memory
+constexpr uint32_t kCcRank = 0x80000000u;
+constexpr size_t kCcSmemBytes = sizeof(uint32_t) * (2 * kCcFast + kCcBoxes) + sizeof(int4) * kCcBoxes;
 
+// Root of x with path halving. A concurrent link only turns a root into a child,
+// and a halving store writes a grandparent (an ancestor), so every parent word
+// keeps pointing into its own tree.
 __device__ __forceinline__ uint32_t cc_find(volatile uint32_t *par, uint32_t x) {
-  uint32_t p = par[x];
-  for (int steps = 0; p != x && steps < kMaxUnionSteps; ++steps) {
-    x = p;
-    p = par[x];
+  for (int steps = 0; steps < kMaxUnionSteps; ++steps) {
+    const uint32_t p = par[x];
+    if (p == x) return x;
+    const uint32_t g = par[p];
+    par[x] = g;
+    x = g;
   }
   return x;
 }
 
-// Links the roots of list entries a and b (pix: their pixels) with a CAS on the
-// root with the larger pixel; bounded retries.
+// Links the roots of entries a and b (pix: their pixels) with a CAS on the root
+// with the larger pixel; bounded retries.
 __device__ void cc_unite(uint32_t *par, const uint32_t *pix, uint32_t a, uint32_t b, uint32_t *status) {
+  volatile uint32_t *vp = par;
   for (int it = 0; it < kMaxUnionSteps; ++it) {
-    a = cc_find(par, a);
-    b = cc_find(par, b);
+    a = cc_find(vp, a);
+    b = cc_find(vp, b);
     if (a == b) return;
     if (pix[a] < pix[b]) {
       const uint32_t t = a;
@@ -404,119 +383,181 @@ __device__ void cc_unite(uint32_t *par, const uint32_t *pix, uint32_t a, uint32_
   atomicOr(status, kStTimeout);
 }
 
-__global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__restrict__ cls,
-                                                              const uint32_t *__restrict__ list,
-                                                              const int32_t *__restrict__ lpos,
-                                                              uint32_t *__restrict__ gpar, int4 *rects,
-                                                              Counters *ctr, uint32_t cap, int W, int H, int m,
-                                                              int tiles_x, int tiles_y, uint8_t *__restrict__ tile_mask) {
-  griddep_wait();
-  extern __shared__ uint32_t s_cc[];
-  uint32_t *s_pix = s_cc, *s_par = s_cc + kCcSmem, *s_roots = s_cc + 2 * kCcSmem;
-  __shared__ uint32_t s_nr;
-  const int tid = threadIdx.x;
-  const uint32_t n = min(ctr->n_centre, (uint32_t)W * (uint32_t)H);
-  const bool small = n <= (uint32_t)kCcSmem;
-  const uint32_t *pix = small ? s_pix : list;
-  uint32_t *par = small ? s_par : gpar;
-  if (tid == 0) s_nr = 0u;
-  for (uint32_t k = tid; k < n; k += kCcThreads) {
-    if (small) s_pix[k] = list[k];
-    par[k] = k;
-  }
-  __syncthreads();
-  if (!small) __threadfence();
-  for (uint32_t k = tid; k < n; k += kCcThreads) {
-    const int p = (int)pix[k];
-    const int x = p % W;
-    const bool l = x > 0 && (cls[p - 1] & kClsCentre), u = p >= W && (cls[p - W] & kClsCentre);
-    const uint32_t kl = l ? (uint32_t)lpos[p - 1] : 0u, ku = u ? (uint32_t)lpos[p - W] : 0u;
-    if (l) cc_unite(par, pix, k, kl, &ctr->status);
-    if (u) cc_unite(par, pix, k, ku, &ctr->status);
-  }
-  __syncthreads();
-  if (!small) __threadfence();
-  for (uint32_t k = tid; k < n; k += kCcThreads) par[k] = cc_find(par, k);
-  __syncthreads();
-  if (!small) __threadfence();
-  // roots, and their rank by pixel (the rectangle slot) kept in the root's own
-  // parent entry's place in s_roots order
-  for (uint32_t k = tid; k < n; k += kCcThreads) {
-    if (par[k] == k) {
-      const uint32_t j = atomicAdd(&s_nr, 1u);
-      if (j < (uint32_t)kCcSortMax) s_roots[j] = pix[k];
-    }
-  }
-  __syncthreads();
-  const uint32_t nr = s_nr;
-  // slot of a root pixel: its rank among the roots' pixels
-  if (nr <= (uint32_t)kCcSortMax) {
-    if (nr > (uint32_t)kCcThreads) {
-      uint32_t np2 = 1;
-      while (np2 < nr) np2 <<= 1;
-      for (uint32_t j = nr + tid; j < np2; j += kCcThreads) s_roots[j] = 0xffffffffu;
-      __syncthreads();
-      for (uint32_t size = 2; size <= np2; size <<= 1) {
-        for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-          for (uint32_t i = tid; i < np2 / 2; i += kCcThreads) {
-            const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
-            const bool up = (lo & size) == 0;
-            const uint32_t a = s_roots[lo], b = s_roots[hi];
-            if ((a > b) == up) {
-              s_roots[lo] = b;
-              s_roots[hi] = a;
-            }
-          }
-          __syncthreads();
-        }
+// Phase 1 for the entries of this thread, four at a time: the neighbours' class
+// bytes and list positions are all loaded before the first link.
+__device__ __forceinline__ void cc_union_all(const uint8_t *__restrict__ cls, const int32_t *labels,
+                                             const uint32_t *pix, uint32_t *par, uint32_t n, int W,
+                                             uint32_t *status) {
+  constexpr int kB = 4;
+  for (uint32_t k0 = threadIdx.x; k0 < n; k0 += kB * kCcThreads) {
+    uint32_t kl[kB], ku[kB];
+    bool l[kB], u[kB];
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const uint32_t k = k0 + (uint32_t)j * kCcThreads;
+      l[j] = u[j] = false;
+      kl[j] = ku[j] = 0u;
+      if (k < n) {
+        const int p = (int)pix[k];
+        const bool hl = p % W > 0, hu = p >= W;
+        l[j] = hl && (cls[p - 1] & kClsCentre);
+        u[j] = hu && (cls[p - W] & kClsCentre);
+        kl[j] = hl ? (uint32_t)labels[p - 1] : 0u;
+        ku[j] = hu ? (uint32_t)labels[p - W] : 0u;
       }
     }
-  }
-  __syncthreads();
-  for (uint32_t j = tid; j < min(nr, cap); j += kCcThreads) rects[j] = make_int4(W, H, -1, -1);
-  if (tid == 0) {
-    ctr->n_rects = nr;
-    if (nr > cap) atomicOr(&ctr->status, kStCapacity);
-  }
-  __syncthreads();
-  __threadfence_block();
-  // bounding boxes: every entry adds its pixel to its root's rectangle
-  for (uint32_t k = tid; k < n; k += kCcThreads) {
-    const uint32_t rp = pix[par[k]];
-    uint32_t sl;
-    if (nr <= (uint32_t)kCcThreads) {  // rank by counting the smaller roots
-      sl = 0;
-      for (uint32_t j = 0; j < nr; ++j) sl += s_roots[j] < rp ? 1u : 0u;
-    } else if (nr <= (uint32_t)kCcSortMax) {  // position in the sorted roots
-      uint32_t lo = 0, hi = nr;
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (s_roots[mid] < rp) lo = mid + 1; else hi = mid;
-      }
-      sl = lo;
-    } else {  // many roots: count the smaller roots of the list
-      sl = 0;
-      for (uint32_t q = 0; q < n; ++q) sl += (par[q] == q && pix[q] < rp) ? 1u : 0u;
+#pragma unroll
+    for (int j = 0; j < kB; ++j) {
+      const uint32_t k = k0 + (uint32_t)j * kCcThreads;
+      if (l[j]) cc_unite(par, pix, k, kl[j], status);
+      if (u[j]) cc_unite(par, pix, k, ku[j], status);
     }
-    if (sl >= cap) continue;
-    const int p = (int)pix[k];
-    const int x = p % W, y = p / W;
-    int *q = reinterpret_cast<int *>(rects + sl);
-    atomicMin(q + 0, x);
-    atomicMin(q + 1, y);
-    atomicMax(q + 2, x);
-    atomicMax(q + 3, y);
+  }
+}
+
+// Phase 3 for many roots: bitmap of the root pixels in bits[] (W * H bits) and
+// per-word prefix counts in pre[]; returns the root count.
+__device__ uint32_t cc_rank_bitmap(const uint32_t *par, const uint32_t *pix, uint32_t n, uint32_t npx,
+                                   uint32_t *bits, uint32_t *pre, uint32_t *s_scan) {
+  const uint32_t nw = (npx + 31u) / 32u;
+  for (uint32_t w = threadIdx.x; w < nw; w += kCcThreads) bits[w] = 0u;
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < n; k += kCcThreads)
+    if (par[k] == k) atomicOr(bits + pix[k] / 32u, 1u << (pix[k] % 32u));
+  __syncthreads();
+  const uint32_t per = (nw + kCcThreads - 1) / kCcThreads;
+  const uint32_t w0 = min((uint32_t)threadIdx.x * per, nw), w1 = min(w0 + per, nw);
+  uint32_t cnt = 0;
+  for (uint32_t w = w0; w < w1; ++w) cnt += (uint32_t)__popc(bits[w]);
+  uint32_t base;
+  const uint32_t nr = block_exclusive_scan<kCcThreads>(cnt, &base, s_scan);
+  for (uint32_t w = w0; w < w1; ++w) {
+    pre[w] = base;
+    base += (uint32_t)__popc(bits[w]);
   }
   __syncthreads();
-  __threadfence_block();
-  for (uint32_t sl = tid; sl < min(nr, cap); sl += kCcThreads) {
-    const int4 bx = rects[sl];
+  return nr;
+}
+
+__device__ __forceinline__ uint32_t cc_bitmap_slot(const uint32_t *bits, const uint32_t *pre, uint32_t rp) {
+  return pre[rp / 32u] + (uint32_t)__popc(bits[rp / 32u] & ((1u << (rp % 32u)) - 1u));
+}
+
+// Phase 5: the component boxes to tile-aligned rectangles and the tile mask.
+__device__ __forceinline__ void cc_finish(int4 *rects, const int4 *box, uint32_t nbox, int W, int H, int m,
+                                          int tiles_x, int tiles_y, uint8_t *tile_mask) {
+  for (uint32_t sl = threadIdx.x; sl < nbox; sl += kCcThreads) {
+    const int4 bx = box[sl];
     const int tx0 = bx.x - m <= 0 ? 0 : (bx.x - m) / kTile, ty0 = bx.y - m <= 0 ? 0 : (bx.y - m) / kTile;
     const int tx1 = min((bx.z + m) / kTile, tiles_x - 1), ty1 = min((bx.w + m) / kTile, tiles_y - 1);
     rects[sl] = make_int4(tx0 * kTile, ty0 * kTile, min((tx1 + 1) * kTile, W), min((ty1 + 1) * kTile, H));
     for (int ty = ty0; ty <= ty1; ++ty)
       for (int tx = tx0; tx <= tx1; ++tx) tile_mask[ty * tiles_x + tx] = 1;
   }
+}
+
+__global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__restrict__ cls,
+                                                              const uint32_t *__restrict__ list,
+                                                              int32_t *__restrict__ labels,
+                                                              uint32_t *__restrict__ gpar, int4 *rects,
+                                                              Counters *ctr, uint32_t cap, int W, int H, int m,
+                                                              int tiles_x, int tiles_y, uint8_t *__restrict__ tile_mask) {
+  griddep_wait();
+  extern __shared__ uint32_t s_cc[];
+  __shared__ uint32_t s_scan[32];
+  __shared__ uint32_t s_nr;
+  const int tid = threadIdx.x;
+  const uint32_t npx = (uint32_t)W * (uint32_t)H;
+  const uint32_t n = min(ctr->n_centre, npx);
+  const bool fast = n <= (uint32_t)kCcFast;
+  uint32_t *pix = fast ? s_cc : const_cast<uint32_t *>(list);
+  uint32_t *par = fast ? s_cc + kCcFast : gpar;
+  uint32_t *s_roots = s_cc + 2 * kCcFast;                              // [kCcBoxes]
+  int4 *s_box = reinterpret_cast<int4 *>(s_cc + 2 * kCcFast + kCcBoxes);  // [kCcBoxes]
+  if (tid == 0) s_nr = 0u;
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    if (fast) pix[k] = list[k];
+    par[k] = k;
+  }
+  __syncthreads();
+  // 1. union; 2. parents to roots
+  cc_union_all(cls, labels, pix, par, n, W, &ctr->status);
+  __syncthreads();
+  for (uint32_t k = tid; k < n; k += kCcThreads) par[k] = cc_find(par, k);
+  __syncthreads();
+  // 3. the roots' slots: par[root] = kCcRank | slot
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    if (par[k] == k) {
+      const uint32_t j = atomicAdd(&s_nr, 1u);
+      if (j < (uint32_t)kCcBoxes) s_roots[j] = pix[k];
+    }
+  }
+  __syncthreads();
+  uint32_t nr = s_nr;
+  const bool sorted = nr <= (uint32_t)kCcBoxes;
+  uint32_t *bits = reinterpret_cast<uint32_t *>(labels), *pre = bits + (npx + 31u) / 32u;  // labels[] is free now
+  if (sorted) {
+    uint32_t np2 = 1;
+    while (np2 < nr) np2 <<= 1;
+    for (uint32_t j = nr + tid; j < np2; j += kCcThreads) s_roots[j] = 0xffffffffu;
+    __syncthreads();
+    for (uint32_t size = 2; size <= np2; size <<= 1) {
+      for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+        for (uint32_t i = tid; i < np2 / 2; i += kCcThreads) {
+          const uint32_t lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+          const bool up = (lo & size) == 0;
+          const uint32_t a = s_roots[lo], b = s_roots[hi];
+          if ((a > b) == up) {
+            s_roots[lo] = b;
+            s_roots[hi] = a;
+          }
+        }
+        __syncthreads();
+      }
+    }
+  } else {
+    nr = cc_rank_bitmap(par, pix, n, npx, bits, pre, s_scan);
+  }
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    if (par[k] != k) continue;
+    const uint32_t rp = pix[k];
+    uint32_t sl;
+    if (sorted) {
+      uint32_t lo = 0, hi = nr;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (s_roots[mid] < rp) lo = mid + 1; else hi = mid;
+      }
+      sl = lo;
+    } else {
+      sl = cc_bitmap_slot(bits, pre, rp);
+    }
+    par[k] = kCcRank | sl;
+  }
+  const uint32_t nbox = min(nr, cap);
+  int4 *box = sorted ? s_box : rects;
+  for (uint32_t j = tid; j < nbox; j += kCcThreads) box[j] = make_int4(W, H, -1, -1);
+  if (tid == 0) {
+    ctr->n_rects = nr;
+    if (nr > cap) atomicOr(&ctr->status, kStCapacity);
+  }
+  __syncthreads();
+  // 4. bounding boxes
+  for (uint32_t k = tid; k < n; k += kCcThreads) {
+    const uint32_t r = par[k];
+    const uint32_t sl = (r & kCcRank) ? (r & ~kCcRank) : (par[r] & ~kCcRank);
+    if (sl >= nbox) continue;
+    const uint32_t p = pix[k];
+    const int x = (int)(p % (uint32_t)W), y = (int)(p / (uint32_t)W);
+    int *q = reinterpret_cast<int *>(box + sl);
+    atomicMin(q + 0, x);
+    atomicMin(q + 1, y);
+    atomicMax(q + 2, x);
+    atomicMax(q + 3, y);
+  }
+  __syncthreads();
+  // 5. rectangles and tiles
+  cc_finish(rects, box, nbox, W, H, m, tiles_x, tiles_y, tile_mask);
 }
 
 // Clears the warp buffer (no sample) and the ROI tile mask.
@@ -631,8 +672,46 @@ cudaError_t launch_mask_minus(uint8_t *mask, const uint8_t *minus, int n, cudaSt
 cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cudaStream_t s) {
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
   launch_k(cc_label_kernel, 1, kCcThreads, kCcSmemBytes, s, (const uint8_t *)ws.cls, (const uint32_t *)ws.cc_list,
-           (const int32_t *)ws.labels, ws.slots, ws.rects, ws.ctr, (uint32_t)ws.max_rects, W, H, margin, tiles_x,
+           ws.labels, ws.slots, ws.rects, ws.ctr, (uint32_t)ws.max_rects, W, H, margin, tiles_x,
            tiles_y, ws.tile_mask);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
+}
+
+// The centre-hole list of a class map: every pixel whose class has the centre bit,
+// appended with one atomic per warp (the list order reaches no output), and its
+// list position in labels[].
+__global__ void centre_list_kernel(const uint8_t *__restrict__ cls, uint32_t npix, Counters *ctr,
+                                   uint32_t *__restrict__ list, int32_t *__restrict__ labels) {
+  griddep_wait();
+  const int lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t b0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32u; b0 < npix; b0 += warps * 32u) {
+    const uint32_t p = b0 + (uint32_t)lane;
+    const bool cc = p < npix && (cls[p] & kClsCentre) != 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, cc);
+    if (!bal) continue;  // warp-uniform
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&ctr->n_centre, (uint32_t)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (cc) {
+      const uint32_t k = base + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+      list[k] = p;
+      labels[p] = (int32_t)k;
+    }
+  }
+}
+
+cudaError_t launch_centre_rois_of(const Workspace &ws, const uint8_t *cls, int W, int H, int margin,
+                                  uint8_t *tile_mask, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(&ws.ctr->n_centre, 0, sizeof(uint32_t), s);
+  if (e != cudaSuccess) return e;
+  const uint32_t npix = (uint32_t)W * (uint32_t)H;
+  launch_k(centre_list_kernel, grid_for((npix + 7) / 8), 256, 0, s, cls, npix, ws.ctr, ws.cc_list, ws.labels);
+  GS_LAUNCHED(1);
+  const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
+  launch_k(cc_label_kernel, 1, kCcThreads, kCcSmemBytes, s, cls, (const uint32_t *)ws.cc_list, ws.labels, ws.slots,
+           ws.rects, ws.ctr, (uint32_t)ws.max_rects, W, H, margin, tiles_x, tiles_y, tile_mask);
   GS_LAUNCHED(1);
   return cudaGetLastError();
 }

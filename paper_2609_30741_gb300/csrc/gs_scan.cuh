@@ -121,11 +121,17 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(Load ld, Apply ap, c
   const uint32_t epoch = (*(volatile uint32_t *)(ctl + 2)) & 0x3fffffffu;
   const uint32_t base = t * (uint32_t)kScanTile;
   if (base < n) {
+    // coalesced loads, all issued before the first shared-memory store (a store
+    // in between could alias the loaders' generic pointers and would serialise
+    // their dependent chains)
+    uint32_t ldv[kScanItems];
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {  // coalesced loads
+    for (int k = 0; k < kScanItems; ++k) {
       const uint32_t i = base + k * kScanThreads + threadIdx.x;
-      vals[k * kScanThreads + threadIdx.x] = i < n ? ld(i) : 0u;
+      ldv[k] = i < n ? ld(i) : 0u;
     }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) vals[k * kScanThreads + threadIdx.x] = ldv[k];
     __syncthreads();
     // each thread owns kScanItems consecutive elements
     uint32_t loc[kScanItems], acc = 0;

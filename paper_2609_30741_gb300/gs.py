@@ -173,6 +173,8 @@ EXPORTS = {
     "gs_tune_cache_put": (C.c_int, [C.c_char_p, C.POINTER(RasterConfig), C.c_float]),
     "gs_tune_cache_get": (C.c_int, [C.c_char_p, C.POINTER(RasterConfig), C.POINTER(C.c_float)]),
     "gs_ssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p]),
+    "gs_centre_rois": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p]),
     "gs_repair_load": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
     "gs_repair_read": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "gs_repair_steps": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
@@ -450,6 +452,18 @@ class Context:
         C_, H, W = img.shape
         _check(lib().gs_ssim(self.h, _ptr(img), _ptr(ref), W, H, C_, _ptr(out)), "gs_ssim")
         return out
+
+    def centre_rois(self, cls, margin=32, tile_mask=None):
+        """Centre ROIs of a [H, W] uint8 class map (gs_centre_rois): (rects
+        [max_rects, 4] int32, count int32 tensor), both on the device."""
+        if cls.dtype != torch.uint8 or cls.dim() != 2 or not cls.is_contiguous():
+            raise ValueError("centre_rois takes a contiguous [H, W] uint8 tensor")
+        H, W = cls.shape
+        rects = torch.empty(self.lim.max_rects, 4, dtype=torch.int32, device=cls.device)
+        count = torch.zeros(1, dtype=torch.int32, device=cls.device)
+        _check(lib().gs_centre_rois(self.h, _ptr(cls), W, H, int(margin), _ptr(rects), _ptr(count),
+                                    _ptr(tile_mask) if tile_mask is not None else None), "gs_centre_rois")
+        return rects, count
 
     # ---- learned repair ----
     def repair_load(self, weights):

@@ -13,6 +13,14 @@ tensor cores, FP32 gradients, AdamW) through the C ABI.
     python -m paper_2609_30741_gb300.repair_train --scene object --scenes 4 \\
         --poses 6 --steps 1500 --out weights.npy [--checkpoint ck.npz
         --checkpoint-every 100] [--resume ck.npz]
+
+The packaged weights (UNBOUNDED_WEIGHTS) come from 2,000 pairs of the
+unbounded distribution, 50 scenes (seeds 7000-7049, 1.5M surfels, 1920x1080)
+x 40 random head poses, streamed in shards of 250 frames over two epochs:
+
+    python -m paper_2609_30741_gb300.repair_train --scene unbounded --scenes 50 \\
+        --poses 40 --shard 250 --epochs 2 --steps 150 --eval-scenes 2 \\
+        --out paper_2609_30741_gb300/weights/repair_unbounded_2000pairs.npy
 """
 from __future__ import annotations
 
@@ -26,6 +34,12 @@ import numpy as np
 import torch
 
 from . import gs, synth
+
+UNBOUNDED_WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                                 "repair_unbounded_2000pairs.npy")
+UNBOUNDED_TRAINING = {"pairs": 2000, "scenes": "unbounded seeds 7000-7049, 1.5M surfels, 1920x1080",
+                      "poses_per_scene": 40, "shard_frames": 250, "epochs": 2, "steps": 2400,
+                      "batch_tiles": 512}
 
 
 def init_weights(seed: int, gate_bias: float = -2.0) -> np.ndarray:

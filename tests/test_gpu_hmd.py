@@ -24,25 +24,23 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 RGB_TOL = 2e-4
-# Excluded from the tolerance: pixels with a blend decision within MARGIN
-# (relative) of its threshold or near-equal depth keys among their contributors,
-# and pixels whose float32 evaluation cannot meet the tolerance by construction
-# (the oracle's first-order bound on a float32 evaluation of the pixel's
-# blending sum, or_render's fp32_bound, above half the tolerance). The smaller
-# parity workloads use MARGIN = 1e-5. Here a pixel evaluates about 400 surfels,
-# many of them seen nearly edge-on from 3 m with f = 1800: the ray-plane
-# intersection of such a surfel is ill-conditioned, so float32 rho carries a
-# relative error up to ~1e-4, and a skip decision 4.4e-4 from its threshold did
-# flip (one alpha ~ 1/255 contribution at T c ~ 0.05: a 2.02e-4 error on frame
-# 14, while the bound there was 4e-6). Decisions within MARGIN = 1e-3 are
-# therefore excluded at this size. (The depth order is decided identically on
-# both sides: the oracle's key is the float32 camera depth the rasterizer
-# computes.) The excluded share grows in proportion to the margin, about 7 % of
-# the pixels of frame 0's crop at 1e-3 (0.9 % at 1e-4); it is printed for every
-# crop and bounded by MAX_MARGINAL.
-MARGIN = 1e-3
-FP32_BOUND_MAX = RGB_TOL / 2
-MAX_MARGINAL = 0.15
+# Excluded from the tolerance (the scope of the float32 reading of the
+# tolerance): pixels with a blend decision within MARGIN (relative) of its
+# threshold, near-equal depth keys among their contributors, and pixels whose
+# float32 evaluation cannot meet the tolerance by construction (the oracle's
+# first-order estimate, or_render's fp32_bound, above the tolerance). At this
+# size the float32 conditioning of the ray-plane solve decides: a pixel
+# evaluates about 400 surfels, 10-30 m away and a few cm large, many of them
+# seen nearly edge-on from 3 m with f = 1800, where float32 rho3 errs by up to
+# about 1 % (one surfel with the ray 0.3 degrees off its plane and weight 0.28
+# moved a pixel of frame 17 by 2.8e-4; a skip decision 4.4e-4 from its
+# threshold flipped on frame 14). With the bound requested the oracle's margins
+# subtract each surfel's rho3 error bound and fp32_bound includes the largest
+# single-surfel effect of it, so both pixels are excluded. The excluded shares
+# of every crop are printed and bounded by MAX_MARGINAL.
+MARGIN = 1e-4
+FP32_BOUND_MAX = RGB_TOL
+MAX_MARGINAL = 0.10
 N_FRAMES = 16
 
 
@@ -54,11 +52,11 @@ def hmd():
     build.build()
     from paper_2609_30741_gb300 import gs, repair_train as T
     dev = torch.device("cuda", 0)
-    # the network the bench uses on this distribution: trained by the library's
-    # kernels on 24 pairs of unbounded scenes (seeds 7100-7103), FP8 scales
-    # calibrated on their tiles
-    tctx, pairs = T.build_pairs("unbounded", 4, 6, 7100, dev)
-    w_trained, _, _ = T.train(tctx, pairs, 1500, 512, 1e-3, 7100, gate_weight=1.0)
+    # the network the bench uses on this distribution: the packaged one, trained
+    # by the library's kernels on 2,000 pairs of unbounded scenes (seeds
+    # 7000-7049); FP8 scales calibrated on 8 frames of another seed
+    w_trained = np.load(T.UNBOUNDED_WEIGHTS)
+    tctx, pairs = T.build_pairs("unbounded", 1, 8, 7100, dev)
     tiles = pairs.tile_tensor()
     calib = (pairs.feat[:8].clone(), tiles[tiles < (8 << 24)][::4].contiguous())
     del tctx, pairs

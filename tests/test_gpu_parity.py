@@ -455,6 +455,58 @@ def test_centre_rois_bit_exact_given_classes(case, request, orc):
     assert np.array_equal(tm.ravel(), s["tmask"])
 
 
+def _class_map(shape, density, pattern, seed):
+    """A [H, W] class map: random non-centre bits everywhere, the centre bit (4) on
+    random pixels at `density`, or on blobs and long snakes (`pattern` 1)."""
+    rng = np.random.default_rng(seed)
+    H, W = shape
+    cls = (rng.integers(0, 16, shape) & ~4).astype(np.uint8)
+    centre = rng.random(shape) < density
+    if pattern:
+        for _ in range(60):  # discs
+            cy, cx, r = rng.integers(0, H), rng.integers(0, W), rng.integers(1, 12)
+            yy, xx = np.ogrid[:H, :W]
+            centre |= (yy - cy) ** 2 + (xx - cx) ** 2 <= r * r
+        for k in range(6):  # serpentine snakes: components whose union chains are long
+            y0 = 8 + 80 * k
+            for row in range(y0, min(y0 + 60, H), 4):
+                centre[row, 4:W - 4] = True
+                edge = W - 5 if (row - y0) % 8 == 0 else 4
+                centre[row:min(row + 4, H), edge] = True
+    cls[centre] |= 4
+    return cls
+
+
+@pytest.mark.parametrize("shape,density,pattern,seed,cap", [
+    ((480, 640), 0.002, 0, 1, 1 << 16),    # a few hundred components: all in shared memory
+    ((600, 800), 0.03, 0, 2, 1 << 16),     # 14k centre pixels, > 4096 components: boxes in global memory
+    ((1024, 1024), 0.04, 0, 3, 1 << 16),   # 42k centre pixels: the long-list path
+    ((512, 512), 0.0, 1, 4, 1 << 16),      # discs and serpentine snakes
+    ((333, 517), 0.01, 0, 5, 1 << 16),     # ragged size
+    ((600, 800), 0.03, 0, 6, 64),          # more components than rectangles
+    ((1024, 1024), 0.04, 0, 7, 64),        # the same on the long-list path
+])
+def test_centre_rois_of_random_class_maps(gs, orc, shape, density, pattern, seed, cap):
+    """gs_centre_rois against the oracle's Step 2 on class maps with every kind of
+    component population; only the centre bit may matter."""
+    cls = _class_map(shape, density, pattern, seed)
+    H, W = shape
+    ctx = gs.Context(16, W, H, max_instances=1 << 12, max_rects=cap)
+    tm = torch.zeros((H + 15) // 16, (W + 15) // 16, dtype=torch.uint8, device="cuda")
+    rects, count = ctx.centre_rois(torch.from_numpy(cls).cuda(), margin=32, tile_mask=tm)
+    st = ctx.check()
+    ref, n = orc.center_rois(cls, m=32, tile=16, cap=cap)
+    assert int(count.item()) == n and n > 0
+    assert st == (gs.GS_ERR_CAPACITY if n > cap else gs.GS_OK)
+    k = min(n, cap)
+    assert np.array_equal(rects[:k].cpu().numpy(), ref[:k])
+    want = np.zeros(((H + 15) // 16, (W + 15) // 16), np.uint8)
+    for x0, y0, x1, y1 in ref[:k]:
+        want[y0 // 16:(y1 - 1) // 16 + 1, x0 // 16:(x1 - 1) // 16 + 1] = 1
+    assert np.array_equal(tm.cpu().numpy(), want)
+    print({"centre_px": int((cls & 4).astype(bool).sum()), "components": n})
+
+
 def test_roi_tiles_equal_the_full_affiliated_render(gs, stereo_small):
     """Per-tile blending is independent of other tiles, so the ROI re-render gives
     exactly the two-pass affiliated pixels on every ROI tile (same kernels)."""

@@ -1,14 +1,23 @@
 """What the trained repair network gains over the method without it.
 
-The network is trained on the GPU by the library's own kernels on pairs the
-method generates from seeded object scenes (500k surfels, 1600x1200), then
-evaluated on two held-out scene seeds and poses. The gain is a smaller
-re-rendered area: tiles whose gate passes take the network's fill and leave
-the ROI re-render (on these workloads 4-21% of the plain method's re-rendered
-pixels at tau = 0.5). The cost is
-bounded: the PSNR of the affiliated eye against the full render may drop by at
-most 0.5 dB.
+The network is the packaged one: trained on the GPU by the library's own
+kernels on 2,000 pairs of the unbounded distribution (50 scenes x 40 poses,
+seeds 7000-7049, 1.5M surfels, 1920x1080; repair_train.UNBOUNDED_WEIGHTS). It is
+evaluated here on two held-out scene seeds and three random head poses each.
+
+Measured per frame (CUDA events, median of repeated frames): the plain method,
+the learned repair (BF16, gate tau = 0.5), the plain method with the centre
+step off (the holes interpolated: the floor of any hole filler's time) and the
+two-pass render. The network replaces part of the ROI re-render: the test
+asserts fewer re-rendered pixels at a bounded PSNR cost, a learned frame
+faster than the two-pass render, and a network whose extra time over the plain
+frame stays below the most any hole filler could save (plain minus the
+centre-step-off frame). On these workloads the learned frame is not faster than
+the plain one: the network serves only hole pixels outside the edge strips and
+its gate keeps a part of the centre ROIs on the re-render.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -16,29 +25,75 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 
+def _psnr(a, b):
+    mse = torch.mean((a - b) ** 2).item()
+    return 10 * math.log10(1.0 / max(mse, 1e-20))
+
+
 @pytest.fixture(scope="module")
-def trained():
+def measured():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_2609_30741_gb300 import build
     build.build()
-    from paper_2609_30741_gb300 import repair_train as T
+    from paper_2609_30741_gb300 import gs, repair_train as T
     dev = torch.device("cuda", 0)
-    ctx, pairs = T.build_pairs("object", 4, 6, 7000, dev)
-    w, hist, secs = T.train(ctx, pairs, 1500, 512, 1e-3, 7000, gate_weight=1.0)
-    ev = T.evaluate(ctx, "object", [9100, 9101], 3, 123, 0.5, dev)
-    return dict(w=w, hist=hist, ev=ev)
+    w = np.load(T.UNBOUNDED_WEIGHTS)
+    rng = np.random.default_rng(4242)
+    arms = {"plain": gs.roi_params(), "learned": gs.roi_params(repair_mode=1, gate_tau=0.5),
+            "centre_off": gs.roi_params(enable_center=0)}
+    rows = []
+    stream = torch.cuda.current_stream(dev)
+    for seed in (107000, 107001):
+        scene, cam, centre, radius = T.scene_and_camera("unbounded", seed)
+        ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 27, device=dev)
+        ctx.repair_load(w)
+        ds = gs.DeviceScene(scene, device=dev)
+        out, out2 = ctx.alloc_outputs(cam), ctx.alloc_outputs(cam, with_cls=False)
+        for _ in range(3):
+            dom, aff = T.random_pose(rng, centre, radius, "unbounded")
+
+            def timed(fn, reps=7):
+                for _ in range(3):
+                    fn()
+                ms = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                    ms.append(e0.elapsed_time(e1))
+                return float(np.median(ms))
+
+            row = {"two_pass_ms": timed(lambda: ctx.render_two_pass(ds, dom, aff, cam, out=out2))}
+            full = out2["rgb_aff"].clone()
+            for name, roi in arms.items():
+                row[name + "_ms"] = timed(lambda roi=roi: ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2, roi=roi,
+                                                                           out=out))
+                row[name + "_psnr"] = _psnr(out["rgb_aff"], full)
+                row[name + "_roi"] = ((out["cls_aff"] & gs.CLS_RENDER) > 0).float().mean().item()
+                row[name + "_net"] = ((out["cls_aff"] & gs.CLS_NET) > 0).float().mean().item()
+            ctx.check_ok()
+            rows.append(row)
+        del ctx, ds
+        torch.cuda.empty_cache()
+    mean = {k: float(np.mean([r[k] for r in rows])) for k in rows[0]}
+    print({k: round(v, 4) for k, v in mean.items()})
+    return mean
 
 
-def test_training_lowers_the_loss(trained):
-    h = trained["hist"]
-    assert h[-1][1] < 0.7 * h[0][1], h
+def test_network_fills_holes_and_cuts_the_rerendered_area(measured):
+    m = measured
+    assert m["learned_net"] > 0.0                        # holes filled by the network
+    assert m["learned_roi"] <= 0.8 * m["plain_roi"]      # at least a fifth fewer re-rendered pixels
+    assert m["learned_psnr"] >= m["plain_psnr"] - 0.3    # at most 0.3 dB lost
+    assert m["learned_psnr"] > m["centre_off_psnr"]      # and better than no centre re-render
 
 
-def test_gate_cuts_the_rerendered_area_at_bounded_cost(trained):
-    ev = trained["ev"]
-    print({k: round(v, 4) for k, v in ev.items()})
-    assert ev["net_pixels"] > 0.0                         # holes filled by the network
-    assert ev["roi_learned"] <= 0.98 * ev["roi_plain"]    # fewer re-rendered pixels
-    assert ev["psnr_learned"] >= ev["psnr_plain"] - 0.5   # at most 0.5 dB lost
-    assert ev["psnr_learned"] > ev["psnr_interp"]         # and far better than no re-render
+def test_learned_frame_against_the_two_pass_render_and_the_best_case(measured):
+    m = measured
+    assert m["learned_ms"] < m["two_pass_ms"]
+    max_saving = m["plain_ms"] - m["centre_off_ms"]
+    assert max_saving > 0.0
+    assert m["learned_ms"] - m["plain_ms"] < max_saving

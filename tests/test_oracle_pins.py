@@ -835,3 +835,83 @@ def test_fp32_bound_covers_a_float32_blend(orc):
         err = np.abs(C.astype(np.float64) - rgb[:, 0, 0]).max()
         assert err <= bound[0, 0], (seed, err, bound[0, 0])
         assert bound[0, 0] < 1e-3
+
+
+def _quat_from_rot(R):
+    from scipy.spatial.transform import Rotation
+    x, y, z, w = Rotation.from_matrix(R).as_quat()
+    return (w, x, y, z)
+
+
+def test_rho3_uncertainty_covers_an_independent_float32_solve(orc):
+    """The oracle's first-order bound on the float32 error of rho3 (or_rho3_err:
+    one unit roundoff on each input magnitude, amplified by the ray's inverse
+    cosine to the surfel normal) against an independent float32 evaluation:
+    the world-to-camera transform as R^T (P - t) and a pivoted LU solve
+    (numpy float32) of [s_u t_u, s_v t_v, -r] (u, v, lambda) = -p_c. Surfels 2-30 m
+    from a rotated camera, half of them within 0.2-3 degrees of edge-on to the
+    ray through the sampled pixel. The uncertainty must cover the independent
+    error on every pair and must not be vacuous on well-conditioned pairs."""
+    rng = np.random.default_rng(77)
+    cam = synth.centred_camera(2000, 2000, 1800.0)
+    pose = synth.look_at((2.5, -0.4, -3.0), (0.3, 0.1, 4.0))
+    R, t = pose.R, pose.t
+    n = 400
+    rows = []
+    for i in range(n):
+        d = rng.uniform(2.0, 30.0)
+        dirc = np.array([rng.uniform(-0.4, 0.4), rng.uniform(-0.4, 0.4), 1.0])
+        pc = d * dirc / np.linalg.norm(dirc)
+        view = pc / np.linalg.norm(pc)
+        if i % 2 == 0:  # nearly edge-on: the normal almost perpendicular to the view ray
+            a = rng.standard_normal(3)
+            tu = a - (a @ view) * view
+            tu /= np.linalg.norm(tu)
+            nrm0 = np.cross(view, tu)
+            th = math.radians(rng.uniform(0.2, 3.0))
+            nrm = math.cos(th) * nrm0 + math.sin(th) * view
+            tv = np.cross(nrm, tu)
+            Rc = np.stack([tu, tv, nrm], 1)
+        else:
+            from scipy.spatial.transform import Rotation
+            Rc = Rotation.random(random_state=int(rng.integers(1 << 30))).as_matrix()
+        Rw = R @ Rc  # tangent frame in world coordinates
+        pw = R @ pc + t
+        su, sv = rng.uniform(0.01, 0.1, 2)
+        o = rng.uniform(0.2, 0.95)
+        sc = _one_surfel(tuple(pw), _quat_from_rot(Rw), (su, sv), o, (0.0, 0.0, 0.0))
+        sp = orc.prepare(sc, pose, cam)[0]
+        if not sp.visible:
+            continue
+        # a pixel inside the support: a local point of the disc, projected
+        rc = math.sqrt(sp.rc2)
+        uv = rng.uniform(-0.7, 0.7, 2) * rc
+        M = np.array(sp.M).reshape(3, 3)
+        P = M @ np.array([uv[0], uv[1], 1.0])
+        if P[2] <= 0.2:
+            continue
+        x, y = cam.fx * P[0] / P[2] + cam.cx, cam.fy * P[1] / P[2] + cam.cy
+        _, lam, rho3, rho2 = orc.eval_pair(sp, cam, x, y)
+        if not np.isfinite(rho3) or rho3 > rho2:
+            continue
+        err_bound = orc.rho3_err(sp, cam, x, y, rho3, lam)
+        # independent float32 evaluation
+        q = sc.quat[0].astype(np.float32)
+        Rq = np.array(rot_from_quat_scipy(q), np.float32)
+        Rt32 = R.T.astype(np.float32)
+        pc32 = Rt32 @ (sc.pos[0, :3].astype(np.float32) - t.astype(np.float32))
+        m0 = np.float32(sc.scale[0, 0]) * (Rt32 @ Rq[:, 0])
+        m1 = np.float32(sc.scale[0, 1]) * (Rt32 @ Rq[:, 1])
+        r32 = np.array([(x - cam.cx) / cam.fx, (y - cam.cy) / cam.fy, 1.0], np.float32)
+        A = np.stack([m0, m1, -r32], 1).astype(np.float32)
+        sol = np.linalg.solve(A, (-pc32).astype(np.float32)).astype(np.float32)
+        rho3_32 = float(sol[0] * sol[0] + sol[1] * sol[1])
+        rows.append((i % 2 == 0, abs(rho3_32 - rho3), err_bound, rho3))
+    rows = np.array(rows, dtype=np.float64)
+    assert len(rows) > 300
+    grazing, err, bnd, rho = rows[:, 0] > 0, rows[:, 1], rows[:, 2], rows[:, 3]
+    assert np.all(err <= bnd), np.max(err / bnd)
+    # not vacuous: typically within a hundred times the independent error, and
+    # edge-on pairs get far larger bounds than the others
+    assert np.median(err / bnd) > 0.01
+    assert np.median(bnd[grazing] / rho[grazing]) > 5 * np.median(bnd[~grazing] / rho[~grazing])
