@@ -697,7 +697,7 @@ def run_ours(args):
                            "achieved": achieved, "peak": peak_gops, "unit": "Gop/s", "frac": achieved / peak_gops,
                            "ms": blend_ms, "work": f"{OPS_PER_PAIR} ops x {np.mean(pairs_eval):.4g} evaluated pairs",
                            "own_count_frac": own_ops / (blend_ms * 1e-3) / 1e9 / peak_gops},
-        "preprocess": hbm_line("preprocess_kernel (stage: counters, FP64 set-up, both eyes' records)",
+        "preprocess": hbm_line("preprocess_kernel (stage: the kernel alone, both eyes' records)",
                                PREPROCESS_BYTES_PER_SURFEL * scene.n, st_stereo[0],
                                f"{PREPROCESS_BYTES_PER_SURFEL} B x {scene.n} surfels"),
         "binning_dominant": hbm_line("dominant-eye binning (compaction, row spans, depth sort, band lists, "
@@ -1101,6 +1101,17 @@ def run_unbounded(args, dev, flush):
             d, a = poses[k % 8]
             ctx.render_stereo(ds, d, a, cam, gap_thresh=2, roi=roi, out=out)
         ms = run(stereo, args.steps, args.warmup)
+        # stage events over the eight poses (a separate pass: events add a little time)
+        ctx.set_profiling(True)
+        st = []
+        for k in range(8):
+            flush.fill_(k & 255)
+            stereo(k)
+            st.append(ctx.stage_times())
+        ctx.set_profiling(False)
+        stage_ms = dict(zip(["preprocess", "bin_dom", "blend_dom", "warp_edge_gaps_features",
+                             "centre_rois" + ("_and_repair_fork" if roi.repair_mode else ""), "bin_roi", "blend_roi",
+                             "outputs"], np.mean(np.array(st), 0).tolist()))
         ps, ss, roi_fr, net_fr, cen_fr, hole_fr = [], [], [], [], [], []
         for k in range(8):
             stereo(k)
@@ -1119,7 +1130,7 @@ def run_unbounded(args, dev, flush):
                      "ssim_aff_vs_full": float(np.mean(ss)),
                      "roi_pixel_share": float(np.mean(roi_fr)), "net_filled_pixel_share": float(np.mean(net_fr)),
                      "centre_roi_pixel_share": float(np.mean(cen_fr)),
-                     "non_strip_hole_pixel_share": float(np.mean(hole_fr))}
+                     "non_strip_hole_pixel_share": float(np.mean(hole_fr)), "stage_ms": stage_ms}
     res["gain_bound"] = gain_bound(res["plain"], res.pop("centre_step_off"), res["learned_bf16"], res["learned_fp8"])
     if packaged:
         res["training"] = dict(T.UNBOUNDED_TRAINING, weights="paper_2609_30741_gb300/weights/"

@@ -580,7 +580,9 @@ gs_status gs_context_set_profiling(gs_context *ctx, int enable);
  *                       gaps, centre ROIs, bin ROI tiles, blend ROI tiles, outputs
  *   gs_render_two_pass: preprocess, bin dominant, blend dominant, bin affiliated,
  *                       blend affiliated
- *   gs_render_mono:     preprocess, bin, blend */
+ *   gs_render_mono:     preprocess, bin, blend
+ * "preprocess" is the preprocessing kernel alone: the counter reset and the FP64
+ * camera set-up before it belong to no stage. */
 gs_status gs_context_stage_times(gs_context *ctx, float *ms, int max_stages, int *n_stages);
 
 const char *gs_status_str(gs_status s);

@@ -383,7 +383,7 @@ static uint32_t fbits(float f) {
 static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_cam *cam,
                          const double bg[3], double x, double y, double out_rgb[3],
                          double *out_d, double *out_t, double *out_margin, int64_t *out_pairs,
-                         double *out_bound) {
+                         double *out_bound, double (*ck)[6]) {
   double T = 1.0, C[3] = {0, 0, 0}, D = 0.0, mrg = INFINITY;
   double eT = 0.0, bnd = 0.0, cabs = 0.0;
   int ncontrib = 0;
@@ -391,8 +391,9 @@ static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_
   int have_prev = 0;
   float prev_key = 0.f;
   double prev_w = 0.0;
-  /* per contributor: T, alpha, the alpha error of the solve's conditioning, colour */
-  double (*ck)[6] = out_bound ? (double (*)[6])malloc(sizeof(double[6]) * OR_MAX_CONTRIB) : NULL;
+  /* ck (scratch of OR_MAX_CONTRIB rows, with the bound): per contributor T, alpha,
+   * the alpha error of the solve's conditioning, colour */
+  if (!out_bound) ck = NULL;
   for (int k = 0; k < nvis; ++k) {
     const or_splat *s = &sp[ord[k]];
     if (x < s->box[0] || x > s->box[1] || y < s->box[2] || y > s->box[3]) continue;
@@ -417,7 +418,8 @@ static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_
     const double ea = a < OR_ALPHA_MAX ? OR_U * (3.0 + 4.0 * rho) : 0.0;
     const double ec = a < OR_ALPHA_MAX ? 0.5 * erho : 0.0;
     const double Tn = T * (1.0 - a);
-    mrg = fmin(mrg, fabs(Tn - OR_T_MIN) / OR_T_MIN - (eT + a / (1.0 - a) * (ea + ec)));
+    /* with the bound requested, T's own float32 error narrows the stop margin */
+    mrg = fmin(mrg, fabs(Tn - OR_T_MIN) / OR_T_MIN - (out_bound ? eT + a / (1.0 - a) * (ea + ec) : 0.0));
     if (Tn < OR_T_MIN) break;
     const double w = a * T;
     if (isfinite(rho3) && w * fabs(dep - s->pc[2]) > 1e-5 * s->pc[2])
@@ -462,7 +464,6 @@ static void render_pixel(const or_splat *sp, const int *ord, int nvis, const or_
       for (int ch = 0; ch < 3; ++ch) cb[ch] += Tk * ak * ck[k][3 + ch];
     }
     *out_bound = bnd + ncontrib * OR_U * cabs + cond;
-    free(ck);
   }
 }
 
@@ -474,20 +475,32 @@ int or_render(const or_scene *sc, const or_pose *pose, const or_cam *cam, const 
   or_prepare(sc, pose, cam, sp);
   int nvis = 0;
   int *ord = depth_order(sp, sc->n, &nvis);
+  /* only surfels whose box meets the window can pass a pixel's box test (the
+   * depth order is kept) */
+  int nwin = 0;
+  for (int k = 0; k < nvis; ++k) {
+    const double *b = sp[ord[k]].box;
+    if (b[1] >= x0 && b[0] <= x0 + w - 1 && b[3] >= y0 && b[2] <= y0 + h - 1) ord[nwin++] = ord[k];
+  }
   const size_t npix = (size_t)w * h;
   int64_t total = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : total)
-  for (int j = 0; j < h; ++j) {
-    for (int i = 0; i < w; ++i) {
-      const size_t p = (size_t)j * w + i;
-      double c3[3], m;
-      int64_t np;
-      render_pixel(sp, ord, nvis, cam, bg, (double)(x0 + i), (double)(y0 + j), c3, &depth[p],
-                   &trans[p], &m, &np, fp32_bound ? &fp32_bound[p] : NULL);
-      for (int ch = 0; ch < 3; ++ch) rgb[ch * npix + p] = c3[ch];
-      if (margin) margin[p] = m;
-      total += np;
+#pragma omp parallel reduction(+ : total)
+  {
+    double (*ck)[6] = fp32_bound ? (double (*)[6])malloc(sizeof(double[6]) * OR_MAX_CONTRIB) : NULL;
+#pragma omp for schedule(dynamic, 1)
+    for (int j = 0; j < h; ++j) {
+      for (int i = 0; i < w; ++i) {
+        const size_t p = (size_t)j * w + i;
+        double c3[3], m;
+        int64_t np;
+        render_pixel(sp, ord, nwin, cam, bg, (double)(x0 + i), (double)(y0 + j), c3, &depth[p],
+                     &trans[p], &m, &np, fp32_bound ? &fp32_bound[p] : NULL, ck);
+        for (int ch = 0; ch < 3; ++ch) rgb[ch * npix + p] = c3[ch];
+        if (margin) margin[p] = m;
+        total += np;
+      }
     }
+    free(ck);
   }
   if (pairs) *pairs = total;
   free(ord);
@@ -511,7 +524,7 @@ int or_render_tiles(const or_scene *sc, const or_pose *pose, const or_cam *cam, 
       const size_t p = (size_t)y * W + x;
       double c3[3];
       render_pixel(sp, ord, nvis, cam, bg, (double)x, (double)y, c3, &depth[p], &trans[p], NULL,
-                   NULL, NULL);
+                   NULL, NULL, NULL);
       for (int ch = 0; ch < 3; ++ch) rgb[ch * npix + p] = c3[ch];
     }
   }

@@ -87,6 +87,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     b.ranges = c.take<uint2>(tiles);
     b.rmask = c.take<uint8_t>(tiles);
     b.items = c.take<uint32_t>(tiles);
+    b.items16 = c.take<uint32_t>(1 + roi_tiles);
     b.rqueue = c.take<uint32_t>(2);
     b.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
     b.mask_clip = c.take<uint16_t>(2 * rty * rtx);
@@ -514,10 +515,10 @@ static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye
 static gs_status begin_call(gs_context *ctx, const gs_scene *scene, const PoseArgs &pa) {
   cudaStream_t s = ctx->stream;
   ctx->nmarks = 0;
-  mark(ctx, 0);
   cudaError_t e = launch_reset_counters(ctx->ws.ctr, s);
   if (e == cudaSuccess) e = launch_setup_cams(pa, ctx->ws.cams, s);
   if (e != cudaSuccess) return cuda_fail(e);
+  mark(ctx, 0);  // the first stage is the preprocessing kernel alone
   e = launch_preprocess(*scene, ctx->ws, pa.neyes, pa.W, pa.H, s);
   mark(ctx, 1);
   return cuda_status(e);
@@ -727,11 +728,18 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
   if ((roi->repair_mode == 1 && !ctx->rp_loaded) || (roi->repair_mode == 2 && !ctx->rp_fp8)) return GS_ERR_NOT_LOADED;
   const int W = intr->width, H = intr->height;
   // the ROI re-render (Stage 4) runs in its own rasterizer configuration when
-  // one is set (its tile edge is also the affiliated eye's binning grid)
+  // one is set. Its tile edge is also the affiliated eye's binning grid, except
+  // that 16-pixel ROI tiles under a coarser dominant grid are binned on the
+  // dominant grid and rendered from their parent tiles' lists (the masked
+  // 16-pixel tiles, without the unmasked pixels of a coarse tile)
   const RasterConfig rc1 = ctx->has_rc_roi ? ctx->rc_roi : ctx->rc;
-  const int sh = raster_tshift(rc1), ts = 1 << sh;
+  const int rsh = raster_tshift(rc1), dsh = raster_tshift(ctx->rc);
+  const bool parent = rsh == 4 && dsh > 4;
+  const int sh = parent ? dsh : rsh, ts = 1 << sh;
   const int tx = (W + ts - 1) >> sh, ty = (H + ts - 1) >> sh;
-  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc, &rc1);
+  RasterConfig rcb = rc1;  // the ROI binning grid
+  rcb.tile = ts;
+  const PoseArgs pa = pose_args(pose_dom, pose_aff, intr, ctx->rc, &rcb);
   // depth_mode 2 reuses the depth range the previous stereo call measured; the
   // first call measures it (mode 0)
   gs_roi_params r = *roi;
@@ -760,6 +768,23 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
     const float3 black = make_float3(0.f, 0.f, 0.f);
     const Workspace &ws = ctx->ws;
     cudaError_t e = cudaSuccess;
+    // the affiliated eye's masked re-render: the binning grid's masked tiles, or
+    // the masked 16-pixel tiles, each from its parent tile's list
+    auto roi_frame = [&](const uint8_t *mask, float *rgb, uint8_t *cls) {
+      RasterFrame f = raster_frame(ws, 1, W, H, sh, mask, black, rgb, nullptr, nullptr, cls, false);
+      if (parent) {
+        const RasterFrame fine = raster_frame(ws, 1, W, H, 4, mask, black, rgb, nullptr, nullptr, cls, false);
+        f.tiles_x = fine.tiles_x;
+        f.ntiles = fine.ntiles;
+        f.tshift = 4;
+        f.roi = nullptr;  // the listed tiles are masked whole
+        f.items = ws.bin[1].items16 + 1;
+        f.n_items = ws.bin[1].items16;
+        f.rshift = sh - 4;
+        f.rtiles_x = tx;
+      }
+      return f;
+    };
     if (reuse) {
       // With the previous frame's depth range the edge strips (Eq. 6-8) are known
       // before the dominant eye is rendered: a second stream bins and renders the
@@ -775,7 +800,7 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
       if (e == cudaSuccess) {
         RasterTable t;
         t.n = 1;
-        t.f[0] = raster_frame(ws, 1, W, H, sh, ws.strip_mask, black, ws.strip_rgb, nullptr, nullptr, nullptr, false);
+        t.f[0] = roi_frame(ws.strip_mask, ws.strip_rgb, nullptr);
         e = launch_raster(t, rc1, ctx->counting != 0, ws.bin[1].rqueue, sd);
       }
       if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_strip, sd);
@@ -841,7 +866,7 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
                 : launch_binning(ws, 1, scene->n, tx, ty, ws.tile_mask, ctx->stream, aorder);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
-    RasterFrame rf = raster_frame(ws, 1, W, H, sh, ws.tile_mask, black, out->rgb_aff, nullptr, nullptr, ws.cls, false);
+    RasterFrame rf = roi_frame(ws.tile_mask, out->rgb_aff, ws.cls);
     if (net_side) {  // join the network; its gated tiles keep the fill
       if ((e = cudaStreamWaitEvent(ctx->stream, ctx->ev_net, 0)) != cudaSuccess) return cuda_fail(e);
       rf.skip = ws.rp_skip;

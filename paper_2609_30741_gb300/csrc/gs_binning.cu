@@ -89,11 +89,32 @@ __device__ __forceinline__ void row_ranges(const Conic &q, const float4 r0, int 
 // grid (rtx x rty tiles): a tile of edge 1 << tshift is masked when it holds a
 // masked pixel. clip[0][ty][tx] / clip[1][ty][tx] get the first masked column
 // >= tx / the last masked column <= tx of row ty (0xffff: none), by ballots 32
-// columns at a time with the carry of the columns already passed.
+// columns at a time with the carry of the columns already passed. With list16
+// given, list16[0] gets the number of masked 16-pixel tiles and list16[1..] the
+// tiles (a rasterizer on the 16-pixel grid reading this grid's lists).
 __global__ void __launch_bounds__(1024) mask_sat_kernel(uint8_t *mask, int tiles_x, int tiles_y,
                                                         uint32_t *__restrict__ sat, const uint8_t *__restrict__ roi16,
-                                                        int rtx, int rty, int tshift, uint16_t *__restrict__ clip) {
+                                                        int rtx, int rty, int tshift, uint16_t *__restrict__ clip,
+                                                        uint32_t *__restrict__ list16) {
   griddep_wait();
+  __shared__ uint32_t s_n16;
+  if (list16 && roi16) {
+    if (threadIdx.x == 0) s_n16 = 0u;
+    __syncthreads();
+    const int n16 = rtx * rty;
+    for (int b0 = (threadIdx.x >> 5) * 32; b0 < n16; b0 += (int)blockDim.x) {  // warp-uniform
+      const int t = b0 + (int)(threadIdx.x & 31);
+      const bool on = t < n16 && roi16[t] != 0;
+      const unsigned bal = __ballot_sync(0xffffffffu, on);
+      if (!bal) continue;
+      uint32_t base = 0;
+      if ((threadIdx.x & 31) == 0) base = atomicAdd(&s_n16, (uint32_t)__popc(bal));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if (on) list16[1 + base + (uint32_t)__popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = (uint32_t)t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) list16[0] = s_n16;
+  }
   if (roi16) {
     for (int t = threadIdx.x; t < tiles_x * tiles_y; t += blockDim.x) {
       const int x = t % tiles_x, y = t / tiles_x;
@@ -816,7 +837,8 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   const RadixScratch rs{b.rs_hist, b.rs_hist + kRsPasses * 256, b.rs_status, b.rs_ctl, &ctr->status};
   if (tile_mask) {  // (the rasterizer-grid mask and) its summed-area table
     launch_k(mask_sat_kernel, 1, 1024, 0, s, const_cast<uint8_t *>(tile_mask), tiles_x, tiles_y, b.mask_sat, roi16,
-             (W + kTile - 1) / kTile, (H + kTile - 1) / kTile, roi16 ? tshift : 4, b.mask_clip);
+             (W + kTile - 1) / kTile, (H + kTile - 1) / kTile, roi16 ? tshift : 4, b.mask_clip,
+             roi16 ? b.items16 : nullptr);
     GS_LAUNCHED(1);
   }
   const uint32_t chunk = kBinWarps * ws.bin_warp_surfels;

@@ -102,6 +102,7 @@ struct BinScratch {
   uint2 *ranges;                // per rasterizer tile: [first, end) of its instances
   uint8_t *rmask;               // the binning's mask on the rasterizer grid (tile edge 8 or 32)
   uint32_t *items;              // rasterizer tiles of the last masked binning
+  uint32_t *items16;            // [1 + 16-pixel tiles]: count, then the masked 16-pixel tiles
   uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
   uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
   uint16_t *mask_clip;          // [2][tiles_y][tiles_x]: next / previous masked tile of the row (0xffff: none)
@@ -267,6 +268,8 @@ struct RasterFrame {
   const uint8_t *roi;       // 16-pixel ROI mask: only its pixels are written, or null
   const uint8_t *skip;      // 16-pixel tiles another step filled: not written, or null
   const uint32_t *items;    // listed tiles, or null: every tile in raster order
+  int rshift, rtiles_x;     // > 0: the tile lists are those of a grid 1 << rshift times coarser
+                            // (rtiles_x columns), each raster tile reads its parent's list
   const uint32_t *n_items;  // device count of the listed tiles
   float *rgb, *depth, *trans;  // [3][H][W], [H][W] (or null), [H][W] (or null)
   uint8_t *cls;             // class map: written pixels get kClsRender, or null

@@ -11,7 +11,10 @@
 // items, (frame, tile) pairs numbered frame by frame, from a device counter
 // until none is left, so the heavy tiles of one frame overlap the light tiles of
 // the others and no CTA is launched per tile. A frame either offers every tile
-// of its grid or a device list of tiles (the ROI tiles of a masked binning).
+// of its grid or a device list of tiles (the ROI tiles of a masked binning, or
+// the masked 16-pixel tiles rendered from the lists of a coarser binning: each
+// reads its parent tile's list, every surfel reaching the parent in depth
+// order, and the surfels that miss its pixels contribute nothing).
 //
 // A CTA renders one TS x TS tile with TS^2 / PIX threads. A warp covers a block
 // of 8 x (4 PIX) pixels (lane l: column l % 8, rows l / 8 + 4 q for q < PIX),
@@ -160,7 +163,11 @@ __global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_cons
     const int W = fr.W, H = fr.H;
     const int px = (tile % fr.tiles_x) * TS + lx;
     const int py = (tile / fr.tiles_x) * TS + ly;  // first of rows py, py + RS, ...
-    const uint2 rg = fr.ranges[tile];
+    // a tile of a finer grid than the binning's reads its parent tile's list
+    // (every surfel reaching the parent, a superset of the tile's own)
+    const int rt = fr.rshift ? ((tile / fr.tiles_x) >> fr.rshift) * fr.rtiles_x + ((tile % fr.tiles_x) >> fr.rshift)
+                             : tile;
+    const uint2 rg = fr.ranges[rt];
     const int rtx = (W + kTile - 1) / kTile;
 
     const float fx = (float)px;
@@ -430,6 +437,8 @@ RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift,
   f.box = ws.bounds[eye];
   f.roi = (mask && tshift > 4) ? mask : nullptr;  // a 32-pixel tile may hold unmasked 16-pixel tiles
   f.skip = nullptr;
+  f.rshift = 0;
+  f.rtiles_x = 0;
   f.items = mask ? ws.bin[eye].items : nullptr;
   f.n_items = mask ? &ws.ctr->n_items[eye] : nullptr;
   f.rgb = rgb;
