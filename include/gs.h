@@ -453,10 +453,13 @@ gs_status gs_context_get_raster(gs_context *ctx, gs_raster_config *rc);
 /* The configuration of gs_render_stereo's ROI re-render (Sec. 3.1 Stage 4): the
  * affiliated eye's ROI tiles are binned and blended on its tile grid, which may
  * differ from the dominant eye's (the ROI mask lives on 16-pixel tiles, so
- * 16-pixel tiles render exactly the ROI tiles). NULL clears it: the ROI
- * re-render then uses gs_context_set_raster's configuration. The images do not
- * depend on it. get returns the configuration the ROI re-render uses and, in
- * *is_set, whether one of its own is set. */
+ * 16-pixel tiles render exactly the ROI tiles). A 16-pixel ROI tile under a
+ * coarser dominant grid is binned on the dominant grid and blended from its
+ * parent tile's list (fewer, shorter binning passes; only the masked 16-pixel
+ * tiles blended). NULL clears it: the ROI re-render then uses
+ * gs_context_set_raster's configuration. The images do not depend on it. get
+ * returns the configuration the ROI re-render uses and, in *is_set, whether one
+ * of its own is set. */
 gs_status gs_context_set_raster_roi(gs_context *ctx, const gs_raster_config *rc);
 gs_status gs_context_get_raster_roi(gs_context *ctx, gs_raster_config *rc, int *is_set);
 

@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(1024) mask_sat_kernel(uint8_t *mask, int tiles
                                                         int rtx, int rty, int tshift, uint16_t *__restrict__ clip,
                                                         uint32_t *__restrict__ list16) {
   griddep_wait();
+  constexpr int kSatSmem = 12000;
+  __shared__ uint32_t s_sat[kSatSmem];
   __shared__ uint32_t s_n16;
   if (list16 && roi16) {
     if (threadIdx.x == 0) s_n16 = 0u;
@@ -155,14 +157,18 @@ __global__ void __launch_bounds__(1024) mask_sat_kernel(uint8_t *mask, int tiles
       if (b) carry = (uint32_t)x0 + (uint32_t)__ffs(b) - 1u;
     }
   }
+  // the table is built in shared memory when it fits (the column pass is a
+  // dependent chain down each column) and then copied out
+  const int nsat = (tiles_y + 1) * sx;
+  uint32_t *S = nsat <= kSatSmem ? s_sat : sat;
   for (int y = wid; y <= tiles_y; y += nw) {
     uint32_t acc = 0;
-    if (lane == 0) sat[(size_t)y * sx] = 0u;
+    if (lane == 0) S[(size_t)y * sx] = 0u;
     for (int x0 = 0; x0 < tiles_x; x0 += 32) {  // warp-uniform
       const int x = x0 + lane;
       const bool on = y > 0 && x < tiles_x && mask[(size_t)(y - 1) * tiles_x + x] != 0;
       const uint32_t b = __ballot_sync(0xffffffffu, on);
-      if (x < tiles_x) sat[(size_t)y * sx + x + 1] = acc + (uint32_t)__popc(b & (0xffffffffu >> (31 - lane)));
+      if (x < tiles_x) S[(size_t)y * sx + x + 1] = acc + (uint32_t)__popc(b & (0xffffffffu >> (31 - lane)));
       acc += (uint32_t)__popc(b);
     }
   }
@@ -170,9 +176,13 @@ __global__ void __launch_bounds__(1024) mask_sat_kernel(uint8_t *mask, int tiles
   for (int x = threadIdx.x; x <= tiles_x; x += blockDim.x) {
     uint32_t acc = 0;
     for (int y = 1; y <= tiles_y; ++y) {
-      acc += sat[(size_t)y * sx + x];
-      sat[(size_t)y * sx + x] = acc;
+      acc += S[(size_t)y * sx + x];
+      S[(size_t)y * sx + x] = acc;
     }
+  }
+  if (S != sat) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < nsat; i += blockDim.x) sat[i] = S[i];
   }
 }
 
@@ -344,9 +354,11 @@ struct CompactApply {
   const uint32_t *zkey;
   uint32_t *key_out, *val_out;
   BinCounts bc;
-  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
+  using Payload = uint32_t;  // the depth key
+  __device__ Payload fetch(uint32_t i, uint32_t v) const { return v ? zkey[i] : 0u; }
+  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v, Payload key) const {
     if (v) {
-      key_out[prefix] = zkey[i];
+      key_out[prefix] = key;
       val_out[prefix] = i;
     }
   }
@@ -379,11 +391,16 @@ struct ReuseApply {
   const uint32_t *uval, *zkey;
   uint32_t *key_out, *val_out;
   BinCounts bc;
-  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v) const {
+  using Payload = uint2;  // surfel id, depth key
+  __device__ Payload fetch(uint32_t i, uint32_t v) const {
+    if (!v) return make_uint2(0u, 0u);
+    const uint32_t id = uval[i];
+    return make_uint2(id, zkey[id]);
+  }
+  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t v, Payload p) const {
     if (v) {
-      const uint32_t id = uval[i];
-      key_out[prefix] = zkey[id];
-      val_out[prefix] = id;
+      key_out[prefix] = p.y;
+      val_out[prefix] = p.x;
     }
   }
   __device__ void end(uint32_t, uint32_t total) const { bc.set(total); }
@@ -771,15 +788,20 @@ struct BinOffsetApply {
   int ntiles;
   const uint8_t *mask;  // null for a full binning
   uint32_t *items, *n_items;
-  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t) const {
+  using Payload = uint2;  // chunks in use, the tile's mask byte (first chunk only)
+  __device__ Payload fetch(uint32_t i, uint32_t) const {
     const uint32_t na = *n_chunks;
+    return make_uint2(na, (mask && i % na == 0u) ? (uint32_t)mask[i / na] : 0u);
+  }
+  __device__ void operator()(uint32_t i, uint32_t prefix, uint32_t, Payload pl) const {
+    const uint32_t na = pl.x;
     const uint32_t t = i / na, c = i % na;
     offs[(size_t)t * nch + c] = prefix;
     if (c != 0u) return;
     const uint32_t p = min(prefix, cap);
     ranges[t].x = p;
     if (t > 0u) ranges[t - 1].y = p;
-    if (mask && mask[t]) items[atomicAdd(n_items, 1u)] = t;
+    if (pl.y) items[atomicAdd(n_items, 1u)] = t;
   }
   __device__ void end(uint32_t, uint32_t total) const {
     *n_inst = total;

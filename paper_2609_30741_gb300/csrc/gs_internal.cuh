@@ -240,9 +240,12 @@ cudaError_t repair_pack(const Workspace &ws, cudaStream_t s);
 // Features from the warp buffer and the affiliated image after hole
 // classification (rgb_aff before the ROI re-render).
 cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_aff, uint4 *feat, cudaStream_t s);
+// sm_share: the percentage of the multiprocessors the persistent grid may hold
+// (less when other work runs beside it).
 cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
                            const uint32_t *n_ptr, uint32_t n_max, float *fill, float *gate, float *out4,
-                           uint4 *acts, cudaStream_t s, bool fp8 = false, uint32_t *amax = nullptr);
+                           uint4 *acts, cudaStream_t s, bool fp8 = false, uint32_t *amax = nullptr,
+                           int sm_share = 100);
 // FP8 scales from the BF16 network's activation maxima over the listed tiles,
 // then the e4m3 weight images.
 cudaError_t repair_calibrate_fp8(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,

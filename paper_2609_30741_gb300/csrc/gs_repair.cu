@@ -1024,14 +1024,15 @@ cudaError_t repair_features(const Workspace &ws, int W, int H, const float *rgb_
   return cudaGetLastError();
 }
 
-static int net_grid(uint32_t n_max) {
-  const uint32_t sms = (uint32_t)sm_grid_cap(1);
-  return (int)(n_max < sms ? (n_max < 1u ? 1u : n_max) : sms);
+static int net_grid(uint32_t n_max, int per_sm = 1, int sm_share = 100) {
+  uint32_t cap = (uint32_t)sm_grid_cap(per_sm) * (uint32_t)sm_share / 100u;
+  if (cap < 1u) cap = 1u;
+  return (int)(n_max < cap ? (n_max < 1u ? 1u : n_max) : cap);
 }
 
 cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H, const uint32_t *tiles,
                            const uint32_t *n_ptr, uint32_t n_max, float *fill, float *gate, float *out4,
-                           uint4 *acts, cudaStream_t s, bool fp8, uint32_t *amax) {
+                           uint4 *acts, cudaStream_t s, bool fp8, uint32_t *amax, int sm_share) {
   if (n_max == 0) return cudaSuccess;
   NetArgs a;
   a.feat = feat;
@@ -1051,10 +1052,9 @@ cudaError_t repair_forward(const Workspace &ws, const uint4 *feat, int W, int H,
   a.amax = amax;
   a.status = &ws.ctr->status;
   if (fp8) {  // two CTAs per SM fit the FP8 kernel's shared memory
-    const uint32_t g = n_max < 304u ? (n_max < 1u ? 1u : n_max) : 304u;
-    launch_k(repair_net_kernel<true>, g, kNetThreads, net_smem(true), s, a);
+    launch_k(repair_net_kernel<true>, net_grid(n_max, 2, sm_share), kNetThreads, net_smem(true), s, a);
   } else {
-    launch_k(repair_net_kernel<false>, net_grid(n_max), kNetThreads, net_smem(false), s, a);
+    launch_k(repair_net_kernel<false>, net_grid(n_max, 1, sm_share), kNetThreads, net_smem(false), s, a);
   }
   GS_LAUNCHED(1);
   return cudaGetLastError();
@@ -1081,8 +1081,12 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
   launch_k(repair_tile_list_kernel, dim3(tx, ty), 256, 0, s, ws.cls, ws.tile_mask, W, H, ws.rp_list, ws.rp_nlist,
            skip);
   GS_LAUNCHED(1);
+  // beside the ROI binning (skip given) the network leaves a quarter of the
+  // multiprocessors to the binning's kernels (measured: with half, the network
+  // became the longer branch on the object workload; with all, the binning
+  // slowed by a third on the unbounded one)
   if ((e = repair_forward(ws, ws.rp_feat, W, H, ws.rp_list, ws.rp_nlist, (uint32_t)nt, ws.rp_fill, ws.rp_gate,
-                          nullptr, nullptr, s, fp8, nullptr)) != cudaSuccess)
+                          nullptr, nullptr, s, fp8, nullptr, skip ? 75 : 100)) != cudaSuccess)
     return e;
   // sigmoid(g) >= tau  <=>  g >= log(tau / (1 - tau))
   const float tau = fminf(fmaxf(gate_tau, 1e-6f), 1.f - 1e-6f);

@@ -332,7 +332,8 @@ constexpr int kMaxUnionSteps = 1 << 22;
 // per phase would cost more than the labelling). A pixel's neighbours are found
 // through labels[] (its list position, written by the classification) once the
 // class map says they are centre holes. Phases, separated by block barriers:
-//   1. union with the left and the upper neighbour: the root with the larger
+//   1. runs of consecutive entries point at their first entry, then links with
+//      the left and upper neighbours (cc_union_all): the root with the larger
 //      pixel is linked below the other by a CAS (bounded retries), so every
 //      component's root is its smallest pixel, the canonical rectangle order;
 //      finds halve their paths;
@@ -383,35 +384,45 @@ __device__ void cc_unite(uint32_t *par, const uint32_t *pix, uint32_t a, uint32_
   atomicOr(status, kStTimeout);
 }
 
-// Phase 1 for the entries of this thread, four at a time: the neighbours' class
-// bytes and list positions are all loaded before the first link.
+// Phase 1. The classification appends the centre holes of 32 consecutive pixels
+// together, so a horizontal run of them is mostly a run of consecutive list
+// entries. First, without links, every entry that continues its left neighbour
+// at the previous list position points straight at its run's first entry in
+// the warp's 32 entries (a smaller pixel, so roots stay the smallest pixels).
+// Then the links, all loads issued first: a run's first entry with its left
+// neighbour elsewhere in the list, a run continuing from the previous 32
+// entries, and an entry with its upper neighbour - skipped when its left
+// neighbour is in its run and that neighbour's upper pixel is a centre hole too
+// (the two upper pixels are then connected, and the left one's link covers
+// both), so a run links about once per run above it.
 __device__ __forceinline__ void cc_union_all(const uint8_t *__restrict__ cls, const int32_t *labels,
                                              const uint32_t *pix, uint32_t *par, uint32_t n, int W,
                                              uint32_t *status) {
-  constexpr int kB = 4;
-  for (uint32_t k0 = threadIdx.x; k0 < n; k0 += kB * kCcThreads) {
-    uint32_t kl[kB], ku[kB];
-    bool l[kB], u[kB];
-#pragma unroll
-    for (int j = 0; j < kB; ++j) {
-      const uint32_t k = k0 + (uint32_t)j * kCcThreads;
-      l[j] = u[j] = false;
-      kl[j] = ku[j] = 0u;
-      if (k < n) {
-        const int p = (int)pix[k];
-        const bool hl = p % W > 0, hu = p >= W;
-        l[j] = hl && (cls[p - 1] & kClsCentre);
-        u[j] = hu && (cls[p - W] & kClsCentre);
-        kl[j] = hl ? (uint32_t)labels[p - 1] : 0u;
-        ku[j] = hu ? (uint32_t)labels[p - W] : 0u;
-      }
+  const uint32_t lane = threadIdx.x & 31u, uW = (uint32_t)W;
+  for (uint32_t base = threadIdx.x & ~31u; base < n; base += kCcThreads) {  // warp-uniform
+    const uint32_t k = base + lane;
+    const bool valid = k < n;
+    const uint32_t p = valid ? pix[k] : 0u;
+    const bool cont = valid && k > 0u && p % uW != 0u && pix[k - 1] == p - 1u;
+    const uint32_t heads = __ballot_sync(0xffffffffu, valid && !cont);
+    if (cont) {
+      const uint32_t le = heads & (0xffffffffu >> (31u - lane));  // heads at or before this lane
+      if (le) par[k] = base + 31u - (uint32_t)__clz(le);
+      else if (lane > 0u) par[k] = base;  // the run came in from the previous 32 entries
     }
-#pragma unroll
-    for (int j = 0; j < kB; ++j) {
-      const uint32_t k = k0 + (uint32_t)j * kCcThreads;
-      if (l[j]) cc_unite(par, pix, k, kl[j], status);
-      if (u[j]) cc_unite(par, pix, k, ku[j], status);
-    }
+  }
+  __syncthreads();
+  for (uint32_t base = threadIdx.x & ~31u; base < n; base += kCcThreads) {  // warp-uniform
+    const uint32_t k = base + lane;
+    if (k >= n) continue;
+    const uint32_t p = pix[k];
+    const bool cont = k > 0u && p % uW != 0u && pix[k - 1] == p - 1u;
+    const bool need_l = !cont && p % uW != 0u, hu = p >= uW;
+    const uint8_t cl = need_l ? cls[p - 1] : 0, cu = hu ? cls[p - uW] : 0, cul = hu && cont ? cls[p - 1 - uW] : 0;
+    const uint32_t kl = need_l ? (uint32_t)labels[p - 1] : 0u, ku = hu ? (uint32_t)labels[p - uW] : 0u;
+    if (need_l && (cl & kClsCentre)) cc_unite(par, pix, k, kl, status);
+    if (cont && lane == 0u) cc_unite(par, pix, k, k - 1, status);
+    if ((cu & kClsCentre) && !(cont && (cul & kClsCentre))) cc_unite(par, pix, k, ku, status);
   }
 }
 

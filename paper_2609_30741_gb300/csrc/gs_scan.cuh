@@ -105,7 +105,9 @@ __device__ __forceinline__ uint32_t lb_prefix(const unsigned long long *tiles, u
   return prefix;
 }
 
-// ap(i, prefix, value) for every i < n, and ap.end(n, total) once.
+// ap(i, prefix, value, ap.fetch(i, value)) for every i < n, and ap.end(n, total)
+// once. fetch only loads (its payload is gathered before the tile's prefix is
+// known); the call with the prefix stores.
 template <class Load, class Apply>
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(Load ld, Apply ap, const uint32_t *n_ptr, uint32_t n_max,
                                                             unsigned long long *tiles, uint32_t *ctl,
@@ -140,6 +142,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(Load ld, Apply ap, c
       loc[k] = vals[threadIdx.x * kScanItems + k];
       acc += loc[k];
     }
+    // the apply step's gathers, issued now: they land while the block scan and
+    // the look-back run
+    typename Apply::Payload pl[kScanItems];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const uint32_t i = base + threadIdx.x * kScanItems + k;
+      pl[k] = i < n ? ap.fetch(i, loc[k]) : typename Apply::Payload{};
+    }
     uint32_t ex;
     const uint32_t tot = block_exclusive_scan<kScanThreads>(acc, &ex, smem);
     if (threadIdx.x < 32) {
@@ -158,7 +168,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(Load ld, Apply ap, c
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
       const uint32_t i = base + threadIdx.x * kScanItems + k;
-      if (i < n) ap(i, ex, loc[k]);
+      if (i < n) ap(i, ex, loc[k], pl[k]);
       ex += loc[k];
     }
     if (base + kScanTile >= n && threadIdx.x == 0) ap.end(n, s_prefix + tot);

@@ -665,8 +665,18 @@ def test_full_size_bench_configuration(gs, object_scene, orc):
     ctx.set_raster(32, 2, 256)
     out = ctx.render_stereo(s["ds"], s["dom"], s["aff"], s["cam"], gap_thresh=2)
     ctx.check_ok()
+
+    def where(k):  # a mismatch's extent, classes and rectangles, for the report
+        d = out[k] != s["out"][k]
+        d = d.any(0) if d.dim() == 3 else d
+        idx = d.nonzero()[:4].tolist() if d.dim() == 2 else []
+        n1, n2 = int(out["roi_count"].item()), int(s["out"]["roi_count"].item())
+        return dict(pixels=int(d.sum()), first=idx, roi_count=(n1, n2),
+                    cls=[(int(out["cls_aff"][i, j]), int(s["out"]["cls_aff"][i, j])) for i, j in idx],
+                    rects_equal=n1 == n2 and torch.equal(out["roi_rects"][:n1], s["out"]["roi_rects"][:n2]))
+
     for k in ("rgb_dom", "depth_dom", "trans_dom", "rgb_aff", "cls_aff", "edge_widths", "roi_count"):
-        assert torch.equal(out[k], s["out"][k]), k
+        assert torch.equal(out[k], s["out"][k]), (k, where(k))
     x0, y0 = 1000, 600
     o_rgb, o_dep, o_tr, mrg, _ = orc.render(s["scene"], s["dom"], s["cam"], window=(x0, y0, 64, 64))
     sl = (slice(y0, y0 + 64), slice(x0, x0 + 64))
