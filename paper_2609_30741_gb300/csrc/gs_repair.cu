@@ -1081,12 +1081,11 @@ cudaError_t repair_stereo(const Workspace &ws, int W, int H, float gate_tau, flo
   launch_k(repair_tile_list_kernel, dim3(tx, ty), 256, 0, s, ws.cls, ws.tile_mask, W, H, ws.rp_list, ws.rp_nlist,
            skip);
   GS_LAUNCHED(1);
-  // beside the ROI binning (skip given) the network leaves a quarter of the
-  // multiprocessors to the binning's kernels (measured: with half, the network
-  // became the longer branch on the object workload; with all, the binning
-  // slowed by a third on the unbounded one)
+  // beside the ROI binning (skip given) the network still takes every
+  // multiprocessor: with a half or three quarters it became the longer branch on
+  // the object workload
   if ((e = repair_forward(ws, ws.rp_feat, W, H, ws.rp_list, ws.rp_nlist, (uint32_t)nt, ws.rp_fill, ws.rp_gate,
-                          nullptr, nullptr, s, fp8, nullptr, skip ? 75 : 100)) != cudaSuccess)
+                          nullptr, nullptr, s, fp8, nullptr, 100)) != cudaSuccess)
     return e;
   // sigmoid(g) >= tau  <=>  g >= log(tau / (1 - tau))
   const float tau = fminf(fmaxf(gate_tau, 1e-6f), 1.f - 1e-6f);
