@@ -127,7 +127,8 @@ typedef struct {
                          16 re-rendered tile, 32 filled by the repair network */
   int32_t *roi_rects; /* optional [max_rects][4] centre ROIs x0, y0, x1, y1 (half-open
                          pixels, tile aligned), in the order of each component's
-                         smallest linear pixel index */
+                         smallest linear pixel index; only the first
+                         min(count, max_rects) entries are written */
   int32_t *roi_count; /* optional [1]: number of centre components found */
   int32_t *edge_widths; /* optional [4]: left, right, top, bottom widths (Eq. 7-8) */
 } gs_outputs;

@@ -304,18 +304,40 @@ bool roi_ok(int gap_thresh, const gs_roi_params *roi) {
   return roi->repair_mode >= 0 && roi->repair_mode <= 3 && roi->gate_tau > 0.f && roi->gate_tau < 1.f;
 }
 
+// The optional outputs in one kernel: the class map (16 bytes at a time when
+// both buffers allow it), the rectangles the frame found (not the whole
+// capacity), their count and the edge widths.
+__global__ void outputs_kernel(const uint8_t *__restrict__ cls, uint8_t *__restrict__ cls_out, size_t npix,
+                               const int4 *__restrict__ rects, int4 *__restrict__ rects_out, uint32_t cap,
+                               const Counters *__restrict__ ctr, int32_t *__restrict__ count_out,
+                               const int32_t *__restrict__ widths, int32_t *__restrict__ widths_out) {
+  griddep_wait();
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  if (cls_out) {
+    const bool vec = (((uintptr_t)cls | (uintptr_t)cls_out) & 15u) == 0;
+    const size_t nv = vec ? npix / 16 : 0;
+    for (size_t i = tid; i < nv; i += stride)
+      reinterpret_cast<uint4 *>(cls_out)[i] = reinterpret_cast<const uint4 *>(cls)[i];
+    for (size_t i = nv * 16 + tid; i < npix; i += stride) cls_out[i] = cls[i];
+  }
+  const uint32_t nr = min(ctr->n_rects, cap);
+  if (rects_out)
+    for (size_t i = tid; i < nr; i += stride) rects_out[i] = rects[i];
+  if (tid == 0 && count_out) *count_out = (int32_t)ctr->n_rects;
+  if (tid < 4 && widths_out) widths_out[tid] = widths[tid];
+}
+
 cudaError_t copy_optional(gs_context *ctx, const gs_outputs *out, int W, int H) {
-  cudaStream_t s = ctx->stream;
-  cudaError_t e = cudaSuccess;
-  if (out->cls_aff) e = cudaMemcpyAsync(out->cls_aff, ctx->ws.cls, (size_t)W * H, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && out->roi_rects)
-    e = cudaMemcpyAsync(out->roi_rects, ctx->ws.rects, sizeof(int4) * (size_t)ctx->lim.max_rects,
-                        cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && out->roi_count)
-    e = cudaMemcpyAsync(out->roi_count, &ctx->ws.ctr->n_rects, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess && out->edge_widths)
-    e = cudaMemcpyAsync(out->edge_widths, ctx->ws.widths, sizeof(int32_t) * 4, cudaMemcpyDeviceToDevice, s);
-  return e;
+  if (!out->cls_aff && !out->roi_rects && !out->roi_count && !out->edge_widths) return cudaSuccess;
+  const size_t npix = (size_t)W * H;
+  const int64_t grid = ((int64_t)npix / 16 + 255) / 256;
+  const int64_t cap = sm_grid_cap(4);
+  launch_k(outputs_kernel, (unsigned)(grid < 1 ? 1 : grid > cap ? cap : grid), 256, 0, ctx->stream,
+           (const uint8_t *)ctx->ws.cls, out->cls_aff, npix, (const int4 *)ctx->ws.rects,
+           reinterpret_cast<int4 *>(out->roi_rects), (uint32_t)ctx->lim.max_rects, (const Counters *)ctx->ws.ctr,
+           out->roi_count, (const int32_t *)ctx->ws.widths, out->edge_widths);
+  GS_LAUNCHED(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_reset_counters(Counters *c, cudaStream_t s) {

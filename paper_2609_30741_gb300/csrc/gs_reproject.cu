@@ -338,9 +338,10 @@ constexpr int kMaxUnionSteps = 1 << 22;
 //      component's root is its smallest pixel, the canonical rectangle order;
 //      finds halve their paths;
 //   2. every entry's parent to its root;
-//   3. the roots' ranks by pixel are the rectangle slots: up to kCcBoxes roots
-//      are sorted (bitonic) and found by binary search, more are ranked through
-//      a bitmap of the root pixels and its per-word prefix counts;
+//   3. the roots' ranks by pixel are the rectangle slots: up to one root per
+//      thread counts the roots with a smaller pixel, up to kCcBoxes roots are
+//      sorted (bitonic) and found by binary search, more are ranked through a
+//      bitmap of the root pixels and its per-word prefix counts;
 //   4. bounding boxes (shared-memory atomics up to kCcBoxes components, else
 //      global atomics on the rectangles);
 //   5. expand by m, align outward to tiles, clip, mark the tiles.
@@ -497,17 +498,32 @@ __global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__r
   for (uint32_t k = tid; k < n; k += kCcThreads) par[k] = cc_find(par, k);
   __syncthreads();
   // 3. the roots' slots: par[root] = kCcRank | slot
+  uint32_t *s_rootk = reinterpret_cast<uint32_t *>(s_box);  // the roots' list positions, until the boxes
   for (uint32_t k = tid; k < n; k += kCcThreads) {
     if (par[k] == k) {
       const uint32_t j = atomicAdd(&s_nr, 1u);
-      if (j < (uint32_t)kCcBoxes) s_roots[j] = pix[k];
+      if (j < (uint32_t)kCcBoxes) {
+        s_roots[j] = pix[k];
+        s_rootk[j] = k;
+      }
     }
   }
   __syncthreads();
   uint32_t nr = s_nr;
   const bool sorted = nr <= (uint32_t)kCcBoxes;
   uint32_t *bits = reinterpret_cast<uint32_t *>(labels), *pre = bits + (npx + 31u) / 32u;  // labels[] is free now
-  if (sorted) {
+  if (nr <= (uint32_t)kCcThreads) {
+    // up to one root per thread: its slot is the number of roots with a smaller
+    // pixel (every thread of a warp reads the same root at a time)
+    uint32_t sl = 0;
+    if ((uint32_t)tid < nr) {
+      const uint32_t mine = s_roots[tid];
+      for (uint32_t j = 0; j < nr; ++j) sl += s_roots[j] < mine ? 1u : 0u;
+    }
+    __syncthreads();
+    if ((uint32_t)tid < nr) par[s_rootk[tid]] = kCcRank | sl;
+    __syncthreads();  // s_rootk shares its memory with the boxes initialised below
+  } else if (sorted) {
     uint32_t np2 = 1;
     while (np2 < nr) np2 <<= 1;
     for (uint32_t j = nr + tid; j < np2; j += kCcThreads) s_roots[j] = 0xffffffffu;
@@ -529,7 +545,7 @@ __global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__r
   } else {
     nr = cc_rank_bitmap(par, pix, n, npx, bits, pre, s_scan);
   }
-  for (uint32_t k = tid; k < n; k += kCcThreads) {
+  for (uint32_t k = tid; nr > (uint32_t)kCcThreads && k < n; k += kCcThreads) {
     if (par[k] != k) continue;
     const uint32_t rp = pix[k];
     uint32_t sl;
