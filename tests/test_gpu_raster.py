@@ -144,13 +144,19 @@ def test_programmatic_launch_changes_nothing(gs):
 @pytest.mark.parametrize("case", ["small", "object_ragged", "toed_in"])
 def test_roi_raster_config_is_bit_identical(gs, case):
     """The ROI re-render in its own configuration (another tile edge than the
-    dominant eye's, also in depth_mode 2 where the strips render on a second
-    stream) gives the same stereo frame bit for bit."""
+    dominant eye's, 16-pixel tiles reading a 32-pixel binning's lists, also in
+    depth_mode 2 where the strips render on a second stream, and with the learned
+    repair running beside the ROI binning) gives the same stereo frame bit for
+    bit."""
     scene, cam, dom, aff = _case(case)
     ds = gs.DeviceScene(scene)
     ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24, min_tile=8)
-    for mode in (0, 2):
-        roi = gs.roi_params(depth_mode=mode)
+    from paper_2609_30741_gb300 import repair_train as T
+    w = T.init_weights(5, gate_bias=0.0)
+    w += np.random.default_rng(6).normal(0.0, 0.03, w.shape).astype(np.float32)
+    ctx.repair_load(w)
+    for mode, repair in ((0, 0), (2, 0), (0, 1)):
+        roi = gs.roi_params(depth_mode=mode, repair_mode=repair, gate_tau=0.4)
         for dom_cfg in ((32, 2, 64), (16, 4, 128)):
             ctx.set_raster(*dom_cfg)
             ctx.set_raster_roi(None)
@@ -164,6 +170,8 @@ def test_roi_raster_config_is_bit_identical(gs, case):
                     got = ctx.render_stereo(ds, dom, aff, cam, roi=roi)
                 ctx.check_ok()
                 for k in ("rgb_dom", "rgb_aff", "cls_aff", "roi_count", "edge_widths"):
-                    assert torch.equal(ref[k], got[k]), (mode, dom_cfg, roi_cfg, k)
+                    assert torch.equal(ref[k], got[k]), (mode, repair, dom_cfg, roi_cfg, k)
+            if repair:  # the gate passed somewhere, so the skip path was exercised
+                assert bool(((ref["cls_aff"] & gs.CLS_NET) > 0).any())
     ctx.set_raster_roi(None)
     assert ctx.raster_roi() == (ctx.raster(), False)
