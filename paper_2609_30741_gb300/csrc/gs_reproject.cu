@@ -23,6 +23,31 @@
 
 namespace gs {
 
+// The pixels of a grid-stride loop: the linear index and its column and row,
+// advanced by the grid's stride with an add and a carry instead of a division
+// per pixel.
+struct PixelWalk {
+  int64_t p, step;
+  int x, y, sx, sy, W;
+  __device__ explicit PixelWalk(int W_) : W(W_) {
+    p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    step = (int64_t)gridDim.x * blockDim.x;
+    x = (int)(p % W);
+    y = (int)(p / W);
+    sx = (int)(step % W);
+    sy = (int)(step / W);
+  }
+  __device__ void next() {
+    p += step;
+    x += sx;
+    y += sy;
+    if (x >= W) {
+      x -= W;
+      ++y;
+    }
+  }
+};
+
 constexpr unsigned long long kNoSample = ~0ull;
 constexpr uint32_t kInfBits = 0x7f800000u;
 
@@ -74,12 +99,13 @@ __global__ void __launch_bounds__(256) warp_scatter_kernel(const CamBlock *__res
   if (edge && blockIdx.x == 0) edge_roi_block(cams, ea);
   const CamBlock &cb = *cams;
   const int64_t npix = (int64_t)W * H;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
+  for (PixelWalk pw(W); pw.p < npix; pw.next()) {
+    const int64_t p = pw.p;
     const float cov = 1.f - trans[p];
     const bool surface = cov >= 0.5f;
     const float d = surface ? depth[p] / cov : 0.f;
     float u, v, z;
-    if (!transfer(cb, (float)(p % W), (float)(p / W), d, surface, u, v, z)) continue;
+    if (!transfer(cb, (float)pw.x, (float)pw.y, d, surface, u, v, z)) continue;
     const float fx = floorf(u + 0.5f), fy = floorf(v + 0.5f);
     if (!(fx >= 0.f && fx <= (float)(W - 1) && fy >= 0.f && fy <= (float)(H - 1))) continue;
     const uint32_t zb = surface ? __float_as_uint(z) : kInfBits;
@@ -217,8 +243,9 @@ __global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_
   __shared__ int s[16];
   if (threadIdx.x < 16) s[threadIdx.x] = strips[threadIdx.x];
   __syncthreads();
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(p % W), y = (int)(p / W);
+  for (PixelWalk pw(W); pw.p < npix; pw.next()) {
+    const int64_t p = pw.p;
+    const int x = pw.x, y = pw.y;
     const unsigned long long key = wv.buf[p];
     const bool hole = key == kNoSample;
     bool strip = false;
@@ -227,7 +254,10 @@ __global__ void __launch_bounds__(256) classify_kernel(WarpView wv, const int32_
     uint8_t c = (hole ? kClsHole : 0u) | (strip ? kClsStrip : 0u);
     float out[3] = {0.f, 0.f, 0.f};
     if (!hole) {
-      wv.colour(x, y, out);
+      const uint32_t src = (uint32_t)(key & 0xffffffffull);  // the source pixel
+      out[0] = wv.rgb_dom[src];
+      out[1] = wv.rgb_dom[wv.hw + src];
+      out[2] = wv.rgb_dom[2 * wv.hw + src];
       const uint32_t zb = (uint32_t)(key >> 32);
       warp_depth[p] = __uint_as_float(zb);
     } else {
@@ -602,6 +632,22 @@ static int grid_for(int64_t n, int per_block = 256) {
   return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+// A grid-stride kernel's grid: at most one wave of resident 256-thread CTAs, so
+// every CTA loops over the same number of pixels give or take one and no second,
+// partly filled wave follows the first.
+template <typename K>
+static int grid_resident(K kernel, int64_t n, int &occupancy) {
+  if (occupancy <= 0) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, 256, 0) != cudaSuccess || occ < 1) occ = 1;
+    occupancy = occ;
+  }
+  const int64_t b = (n + 255) / 256;
+  const int64_t cap = sm_grid_cap(occupancy);
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+static int g_occ_scatter = 0, g_occ_classify = 0;
+
 static EdgeArgs edge_args(const Workspace &ws, const gs_roi_params &roi, uint8_t *mask, bool assign) {
   return EdgeArgs{ws.ctr, roi.samples_per_edge, roi.margin, roi.depth_mode, roi.d_min, roi.d_max, ws.strips,
                   ws.widths, ws.drange, mask, assign ? 1 : 0};
@@ -615,8 +661,8 @@ static cudaError_t warp_launches(const Workspace &ws, int W, int H, const float 
                              tiles_x * tiles_y);
   const EdgeArgs ea = roi ? edge_args(ws, *roi, ws.tile_mask, false) : EdgeArgs{};
   if (err == cudaSuccess)
-    err = launch_k(warp_scatter_kernel, grid_for(npix), 256, 0, s, ws.cams, depth_dom, trans_dom, ws.warpbuf, W, H,
-                   roi ? 1 : 0, ea);
+    err = launch_k(warp_scatter_kernel, grid_resident(warp_scatter_kernel, npix, g_occ_scatter), 256, 0, s, ws.cams,
+                   depth_dom, trans_dom, ws.warpbuf, W, H, roi ? 1 : 0, ea);
   GS_LAUNCHED(2);
   return err;
 }
@@ -641,8 +687,9 @@ cudaError_t launch_classify(const Workspace &ws, int W, int H, int gap_thresh, c
   // is off, and the repair network's starting point in the repair modes (there
   // the ROI re-render or the network overwrites those pixels)
   const int fill_all = !roi.enable_center || roi.repair_mode != 0;
-  const cudaError_t err = launch_k(classify_kernel, grid_for(npix), 256, 0, s, wv, ws.strips, gap_thresh,
-                                   fill_all ? 0 : 1, rgb_aff, ws.warp_depth, ws.cls, ws.ctr, ws.cc_list, ws.labels);
+  const int grid = grid_resident(classify_kernel, npix, g_occ_classify);
+  const cudaError_t err = launch_k(classify_kernel, grid, 256, 0, s, wv, ws.strips, gap_thresh, fill_all ? 0 : 1,
+                                   rgb_aff, ws.warp_depth, ws.cls, ws.ctr, ws.cc_list, ws.labels);
   GS_LAUNCHED(1);
   return err;
 }
@@ -664,8 +711,9 @@ __global__ void strip_composite_kernel(const uint8_t *__restrict__ strip_mask, i
   griddep_wait();
   const int64_t npix = (int64_t)W * H;
   const int tiles_x = (W + kTile - 1) / kTile;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix; p += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(p % W), y = (int)(p / W);
+  for (PixelWalk pw(W); pw.p < npix; pw.next()) {
+    const int64_t p = pw.p;
+    const int x = pw.x, y = pw.y;
     if (!strip_mask[(y / kTile) * tiles_x + x / kTile]) continue;
     dst[p] = src[p];
     dst[npix + p] = src[npix + p];
