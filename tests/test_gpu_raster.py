@@ -141,6 +141,19 @@ def test_programmatic_launch_changes_nothing(gs):
         assert torch.equal(res[True][k], res[False][k]), k
 
 
+def _mismatch(ref, got, k):
+    """Where two stereo outputs differ: pixel count, class bits and 16-pixel tiles."""
+    d = ref[k] != got[k]
+    if k not in ("rgb_aff", "cls_aff"):
+        return f"{k}: {ref[k].flatten()[:8].tolist()} vs {got[k].flatten()[:8].tolist()}"
+    d = d.any(0) if d.dim() == 3 else d
+    ys, xs = (v.cpu().numpy() for v in torch.nonzero(d, as_tuple=True))
+    ca, cb = ref["cls_aff"][ys, xs].cpu().numpy(), got["cls_aff"][ys, xs].cpu().numpy()
+    tiles = sorted(set(zip((ys // 16).tolist(), (xs // 16).tolist())))
+    return (f"{k}: {len(ys)} pixels in {len(tiles)} tiles {tiles[:8]}, classes {np.unique(ca).tolist()} vs "
+            f"{np.unique(cb).tolist()}, cls_aff equal: {torch.equal(ref['cls_aff'], got['cls_aff'])}")
+
+
 @pytest.mark.parametrize("case", ["small", "object_ragged", "toed_in"])
 def test_roi_raster_config_is_bit_identical(gs, case):
     """The ROI re-render in its own configuration (another tile edge than the
@@ -170,7 +183,7 @@ def test_roi_raster_config_is_bit_identical(gs, case):
                     got = ctx.render_stereo(ds, dom, aff, cam, roi=roi)
                 ctx.check_ok()
                 for k in ("rgb_dom", "rgb_aff", "cls_aff", "roi_count", "edge_widths"):
-                    assert torch.equal(ref[k], got[k]), (mode, repair, dom_cfg, roi_cfg, k)
+                    assert torch.equal(ref[k], got[k]), (mode, repair, dom_cfg, roi_cfg, _mismatch(ref, got, k))
             if repair:  # the gate passed somewhere, so the skip path was exercised
                 assert bool(((ref["cls_aff"] & gs.CLS_NET) > 0).any())
     ctx.set_raster_roi(None)
