@@ -115,9 +115,18 @@ __device__ __forceinline__ void eval_pixels(const float (&fy)[PIX], float ay, fl
   }
 }
 
+// Resident CTAs per SM asked of the compiler: with one or two pixels per thread
+// the loop fits 64 registers, so 1024 threads (half the SM's warp slots) stay
+// resident whatever the block shape (the 16-pixel shape otherwise takes 72 and
+// keeps 7 CTAs of 128 threads); more pixels per thread keep their own count.
+template <int TS, int PIX>
+constexpr int raster_min_blocks() {
+  return PIX <= 2 ? 1024 / (TS * TS / PIX) : 1;
+}
+
 template <int TS, int PIX, int BATCH, bool COUNT>
-__global__ void __launch_bounds__(TS * TS / PIX) raster_kernel(const __grid_constant__ RasterTable tab,
-                                                               uint32_t *__restrict__ queue) {
+__global__ void __launch_bounds__(TS * TS / PIX, (raster_min_blocks<TS, PIX>()))
+    raster_kernel(const __grid_constant__ RasterTable tab, uint32_t *__restrict__ queue) {
   griddep_wait();
   constexpr int NT = TS * TS / PIX;  // threads
   constexpr int RS = 4;              // rows between a thread's pixels
