@@ -88,6 +88,7 @@ void layout(const gs_limits &lim, Carver &c, Workspace &ws) {
     b.rmask = c.take<uint8_t>(tiles);
     b.items = c.take<uint32_t>(tiles);
     b.items16 = c.take<uint32_t>(1 + roi_tiles);
+    b.lpt = c.take<uint32_t>(1 + tiles);
     b.rqueue = c.take<uint32_t>(2);
     b.mask_sat = c.take<uint32_t>((rty + 1) * (rtx + 1));
     b.mask_clip = c.take<uint16_t>(2 * rty * rtx);
@@ -512,10 +513,17 @@ static void mark(gs_context *ctx, int slot) {
 }
 
 // One eye through the persistent rasterizer (a table of one frame).
+// One frame in the persistent rasterizer, its tiles taken longest list first.
+// Tiles that read a coarser grid's lists keep their order: the four children
+// of a parent share its length, and the measured gain did not pay for the sort.
 static cudaError_t raster_one(gs_context *ctx, const RasterFrame &f, const RasterConfig *rc = nullptr) {
   RasterTable t;
   t.n = 1;
   t.f[0] = f;
+  if (!f.rshift) {
+    const cudaError_t e = launch_lpt_order(t.f[0], ctx->ws.bin[f.eye].lpt, ctx->stream);
+    if (e != cudaSuccess) return e;
+  }
   return launch_raster(t, rc ? *rc : ctx->rc, ctx->counting != 0, ctx->ws.bin[f.eye].rqueue, ctx->stream);
 }
 

@@ -103,6 +103,7 @@ struct BinScratch {
   uint8_t *rmask;               // the binning's mask on the rasterizer grid (tile edge 8 or 32)
   uint32_t *items;              // rasterizer tiles of the last masked binning
   uint32_t *items16;            // [1 + 16-pixel tiles]: count, then the masked 16-pixel tiles
+  uint32_t *lpt;                // [1 + tiles]: count, then the rasterizer's tiles, longest list first
   uint32_t *rqueue;             // persistent rasterizer work counter and exit ticket
   uint32_t *mask_sat;           // summed-area table of the mask [tiles_y + 1][tiles_x + 1]
   uint16_t *mask_clip;          // [2][tiles_y][tiles_x]: next / previous masked tile of the row (0xffff: none)
@@ -307,6 +308,10 @@ int raster_tshift(const RasterConfig &c);
 // clears them).
 cudaError_t launch_raster(const RasterTable &t, const RasterConfig &c, bool count_pairs, uint32_t *queue,
                           cudaStream_t s);
+// Rewrites f's work items as a list of its tiles, longest surfel list first,
+// into buf (1 + f.ntiles words: the count, then the tiles); the images do not
+// depend on the order.
+cudaError_t launch_lpt_order(RasterFrame &f, uint32_t *buf, cudaStream_t s);
 // Fills a RasterFrame for eye `eye` of a workspace; mask: 16-pixel ROI mask of a
 // masked pass (the listed tiles of the last masked binning), or null.
 RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift, const uint8_t *mask, float3 bg,

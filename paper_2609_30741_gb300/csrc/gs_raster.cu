@@ -43,6 +43,7 @@
 // depth.
 #include "gs_internal.cuh"
 #include "gs_launch.cuh"
+#include "gs_scan.cuh"
 
 namespace gs {
 
@@ -336,6 +337,58 @@ __global__ void __launch_bounds__(TS * TS / PIX, (raster_min_blocks<TS, PIX>()))
   }
 }
 
+// ---------------------------------------------------------------- work order
+// Longest tile lists first. The persistent rasterizer takes its work items in
+// list order, so a frame whose heaviest tiles come last ends on a few CTAs
+// still walking long lists while the other SMs idle. One CTA counting-sorts the
+// frame's items by a log-scale bucket of their surfel-list length (eight
+// buckets per octave, longest first; the order inside a bucket is arbitrary).
+// The order changes no pixel: every item renders its own pixels.
+constexpr int kLptThreads = 1024;
+
+__device__ __forceinline__ uint32_t lpt_bucket(uint32_t len) {
+  const uint32_t v = len + 1u;
+  const uint32_t lg = 31u - (uint32_t)__clz(v);
+  const uint32_t frac = lg >= 3u ? (v >> (lg - 3u)) & 7u : (v << (3u - lg)) & 7u;
+  return 255u - min(255u, lg * 8u + frac);
+}
+
+__global__ void __launch_bounds__(kLptThreads) lpt_order_kernel(const uint32_t *__restrict__ items,
+                                                                const uint32_t *n_items, uint32_t n_max,
+                                                                const uint2 *__restrict__ ranges, int tiles_x,
+                                                                int rshift, int rtiles_x, uint32_t *__restrict__ out) {
+  griddep_wait();
+  __shared__ uint32_t s_hist[256];
+  __shared__ uint32_t s_scan[32];
+  const uint32_t n = items ? min(*n_items, n_max) : n_max;
+  auto bucket = [&](uint32_t k, uint32_t &tile) {
+    tile = items ? items[k] : k;
+    const uint32_t rt = rshift ? (tile / (uint32_t)tiles_x >> rshift) * (uint32_t)rtiles_x +
+                                     (tile % (uint32_t)tiles_x >> rshift)
+                               : tile;
+    const uint2 rg = ranges[rt];
+    return lpt_bucket(rg.y - rg.x);
+  };
+  if (threadIdx.x < 256) s_hist[threadIdx.x] = 0u;
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < n; k += kLptThreads) {
+    uint32_t t;
+    atomicAdd(&s_hist[bucket(k, t)], 1u);
+  }
+  __syncthreads();
+  uint32_t base;
+  block_exclusive_scan<kLptThreads>(threadIdx.x < 256 ? s_hist[threadIdx.x] : 0u, &base, s_scan);
+  __syncthreads();
+  if (threadIdx.x < 256) s_hist[threadIdx.x] = base;
+  __syncthreads();
+  for (uint32_t k = threadIdx.x; k < n; k += kLptThreads) {
+    uint32_t t;
+    const uint32_t b = bucket(k, t);
+    out[1u + atomicAdd(&s_hist[b], 1u)] = t;
+  }
+  if (threadIdx.x == 0) out[0] = n;
+}
+
 // ---------------------------------------------------------------- host side
 
 namespace {
@@ -433,6 +486,15 @@ cudaError_t launch_raster(const RasterTable &t, const RasterConfig &c, bool coun
   cfg.numAttrs = g_pdl ? 1 : 0;
   const cudaError_t e = cudaLaunchKernelExC(&cfg, v.fn, args);
   GS_LAUNCHED(1);
+  return e;
+}
+
+cudaError_t launch_lpt_order(RasterFrame &f, uint32_t *buf, cudaStream_t s) {
+  const cudaError_t e = launch_k(lpt_order_kernel, 1, kLptThreads, 0, s, f.items, f.n_items, (uint32_t)f.ntiles,
+                                 f.ranges, f.tiles_x, f.rshift, f.rtiles_x, buf);
+  GS_LAUNCHED(1);
+  f.items = buf + 1;
+  f.n_items = buf;
   return e;
 }
 
