@@ -44,6 +44,19 @@ def _case(name):
     return scene, cam, dom, aff
 
 
+def _mismatch(ref, got, k):
+    """Where two stereo outputs differ: pixel count, class bits and 16-pixel tiles."""
+    d = ref[k] != got[k]
+    if k not in ("rgb_aff", "cls_aff") or "cls_aff" not in ref:
+        return f"{k}: {ref[k].flatten()[:8].tolist()} vs {got[k].flatten()[:8].tolist()}"
+    d = d.any(0) if d.dim() == 3 else d
+    ys, xs = (v.cpu().numpy() for v in torch.nonzero(d, as_tuple=True))
+    ca, cb = ref["cls_aff"][ys, xs].cpu().numpy(), got["cls_aff"][ys, xs].cpu().numpy()
+    tiles = sorted(set(zip((ys // 16).tolist(), (xs // 16).tolist())))
+    return (f"{k}: {len(ys)} pixels in {len(tiles)} tiles {tiles[:8]}, classes {np.unique(ca).tolist()} vs "
+            f"{np.unique(cb).tolist()}, cls_aff equal: {torch.equal(ref['cls_aff'], got['cls_aff'])}")
+
+
 def _run(ctx, ds, dom, aff, cam):
     ctx.set_counting(True)
     o = ctx.render_stereo(ds, dom, aff, cam, gap_thresh=2)
@@ -72,7 +85,7 @@ def test_every_raster_config_is_bit_identical(gs, case):
         assert ctx.raster() == cfg
         got, ev, co = _run(ctx, ds, dom, aff, cam)
         for k in ref:
-            assert torch.equal(ref[k], got[k]), (cfg, k)
+            assert torch.equal(ref[k], got[k]), (cfg, _mismatch(ref, got, k))
         assert co == co_ref, (cfg, co, co_ref)
         assert ev[0] >= co[0] and ev[1] >= co[1]
 
@@ -139,19 +152,6 @@ def test_programmatic_launch_changes_nothing(gs):
     gs.set_programmatic_launch(True)
     for k in res[True]:
         assert torch.equal(res[True][k], res[False][k]), k
-
-
-def _mismatch(ref, got, k):
-    """Where two stereo outputs differ: pixel count, class bits and 16-pixel tiles."""
-    d = ref[k] != got[k]
-    if k not in ("rgb_aff", "cls_aff"):
-        return f"{k}: {ref[k].flatten()[:8].tolist()} vs {got[k].flatten()[:8].tolist()}"
-    d = d.any(0) if d.dim() == 3 else d
-    ys, xs = (v.cpu().numpy() for v in torch.nonzero(d, as_tuple=True))
-    ca, cb = ref["cls_aff"][ys, xs].cpu().numpy(), got["cls_aff"][ys, xs].cpu().numpy()
-    tiles = sorted(set(zip((ys // 16).tolist(), (xs // 16).tolist())))
-    return (f"{k}: {len(ys)} pixels in {len(tiles)} tiles {tiles[:8]}, classes {np.unique(ca).tolist()} vs "
-            f"{np.unique(cb).tolist()}, cls_aff equal: {torch.equal(ref['cls_aff'], got['cls_aff'])}")
 
 
 @pytest.mark.parametrize("case", ["small", "object_ragged", "toed_in"])
