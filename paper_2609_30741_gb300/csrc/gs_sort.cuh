@@ -66,6 +66,11 @@ static __global__ void __launch_bounds__(kRsThreads) rs_hist_kernel(const uint32
     const uint32_t v = h[p][threadIdx.x];
     if (v) atomicAdd(&sc.hist[p * 256 + threadIdx.x], v);
   }
+  // every thread's counts are in before the CTA takes its exit ticket: without
+  // the fence and the barrier a lagging warp could still be adding its counts
+  // when the last CTA reads them
+  __threadfence();
+  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     s_last = atomicAdd(&sc.ctl[3], 1u) == gridDim.x - 1 ? 1u : 0u;
