@@ -432,6 +432,9 @@ gs_status gs_context_destroy(gs_context *ctx) {
   if (ctx->ev_strip) cudaEventDestroy(ctx->ev_strip);
   if (ctx->ev_net) cudaEventDestroy(ctx->ev_net);
   if (ctx->copy) cudaStreamDestroy(ctx->copy);
+  if (ctx->rows) cudaStreamDestroy(ctx->rows);
+  if (ctx->ev_rfork) cudaEventDestroy(ctx->ev_rfork);
+  if (ctx->ev_rjoin) cudaEventDestroy(ctx->ev_rjoin);
   if (ctx->ev_hfork) cudaEventDestroy(ctx->ev_hfork);
   if (ctx->ev_hjoin) cudaEventDestroy(ctx->ev_hjoin);
   delete ctx;
@@ -513,6 +516,23 @@ static void mark(gs_context *ctx, int slot) {
 }
 
 // One eye through the persistent rasterizer (a table of one frame).
+// The stream and events on which a binning computes its row spans beside its
+// compaction and depth sort (created on first use); null if they cannot be.
+static const SideRows *side_rows(gs_context *ctx) {
+  static thread_local SideRows r;
+  if (!ctx->rows) {
+    cudaError_t e = cudaStreamCreateWithFlags(&ctx->rows, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_rfork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_rjoin, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  r = SideRows{ctx->rows, ctx->ev_rfork, ctx->ev_rjoin};
+  return &r;
+}
+
 // One frame in the persistent rasterizer, its tiles taken longest list first.
 // Tiles that read a coarser grid's lists keep their order: the four children
 // of a parent share its length, and the measured gain did not pay for the sort.
@@ -534,7 +554,7 @@ static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye
   const int sh = raster_tshift(ctx->rc), ts = 1 << sh;
   const int tx = (W + ts - 1) >> sh, ty = (H + ts - 1) >> sh;
   ctx->last_tiles = tx * ty;
-  cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s, order);
+  cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s, order, nullptr, 0, 0, 4, side_rows(ctx));
   if (e != cudaSuccess) return cuda_fail(e);
   mark(ctx, slot);
   e = raster_one(ctx, raster_frame(ws, eye, W, H, sh, nullptr, bg, rgb, depth, trans, nullptr, stats));
@@ -892,8 +912,12 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
     // on their own grid)
     ctx->last_tiles = tx * ty;
     const int aorder = p.parallel ? kOrderReuse : kOrderOwn;
-    e = sh != 4 ? launch_binning(ws, 1, scene->n, tx, ty, ws.bin[1].rmask, ctx->stream, aorder, ws.tile_mask, W, H, sh)
-                : launch_binning(ws, 1, scene->n, tx, ty, ws.tile_mask, ctx->stream, aorder);
+    // (with depth_mode 2 the strip binning of this eye ran on the second stream:
+    // its spans stay in stream order)
+    const SideRows *sr = reuse ? nullptr : side_rows(ctx);
+    e = sh != 4 ? launch_binning(ws, 1, scene->n, tx, ty, ws.bin[1].rmask, ctx->stream, aorder, ws.tile_mask, W, H, sh,
+                                 sr)
+                : launch_binning(ws, 1, scene->n, tx, ty, ws.tile_mask, ctx->stream, aorder, nullptr, 0, 0, 4, sr);
     if (e != cudaSuccess) return cuda_fail(e);
     mark(ctx, 6);
     RasterFrame rf = roi_frame(ws.tile_mask, out->rgb_aff, ws.cls);

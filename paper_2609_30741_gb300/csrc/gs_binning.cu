@@ -220,7 +220,11 @@ __device__ __forceinline__ void clip_to_mask(const uint16_t *clip, int tiles_x, 
 // with one atomic, and then computes the rows 32 at a time, one per lane, so no
 // lane idles while another walks a large surfel. row_off[i] is the slot of
 // surfel i's first rectangle row. An ROI binning keeps of each range only the
-// part from its first to its last masked tile.
+// part from its first to its last masked tile. The grid strides over the
+// surfels, so a small grid can run beside other kernels; without ids the
+// candidates are all surfels by id, and with the ROI's summed-area table a
+// surfel whose rectangle holds no ROI tile is skipped (the compaction's test),
+// so the spans need neither the compaction nor the depth order.
 __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ ids, const uint32_t *n_ptr,
                                                    uint32_t n_max, const float4 *__restrict__ rec,
                                                    const ushort4 *__restrict__ rect, const uint32_t *__restrict__ cnt,
@@ -228,20 +232,26 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
                                                    uint32_t *__restrict__ row_off, uint2 *__restrict__ spans,
                                                    uint32_t cap, uint32_t *__restrict__ n_rows,
                                                    uint32_t *__restrict__ status, const uint16_t *__restrict__ clip,
-                                                   int clip_tiles_x, int clip_tiles_y) {
+                                                   int clip_tiles_x, int clip_tiles_y,
+                                                   const uint32_t *__restrict__ sat) {
   griddep_wait();
   const int lane = threadIdx.x & 31;
   const uint32_t n = load_n(n_ptr, n_max);
-  const uint32_t j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
-  if (j0 >= n) return;  // warp-uniform
-  const uint32_t j = j0 + (uint32_t)lane;
-  const uint32_t i = j < n ? ids[j] : 0u;  // the surfels being binned
   const int W = cams->eye[eye].W, H = cams->eye[eye].H, tshift = cams->eye[eye].tshift;
+  const uint32_t stride = gridDim.x * blockDim.x;  // a multiple of 32: j0 stays warp-aligned
+  for (uint32_t j0 = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; j0 < n; j0 += stride) {  // warp-uniform
+  const uint32_t j = j0 + (uint32_t)lane;
+  const uint32_t i = j < n ? (ids ? ids[j] : j) : 0u;  // the surfels being binned
   int nr = 0, ry = 0, rx0 = 0, rx1 = -1;
   Conic q{};
   float cx = 0.f, cy = 0.f;
-  if (j < n && cnt[i] > 0u) {
-    const ushort4 rc = rect[i];
+  bool bin = j < n && cnt[i] > 0u;
+  ushort4 rc = make_ushort4(0, 0, 0, 0);
+  if (bin) {
+    rc = rect[i];
+    if (sat) bin = sat_any(sat, clip_tiles_x, rc.y, rc.w, rc.x, rc.z);  // the binning's ROI test
+  }
+  if (bin) {
     nr = (int)rc.w - (int)rc.y + 1;
     ry = rc.y;
     rx0 = rc.x;
@@ -308,6 +318,7 @@ __global__ void __launch_bounds__(256) rows_kernel(const uint32_t *__restrict__ 
       spans[slot] = make_uint2((uint32_t)a0 | ((uint32_t)a1 << 16), (uint32_t)c0 | ((uint32_t)c1 << 16));
     }
   }
+  }
 }
 
 // ---------------------------------------------------------------- compaction
@@ -336,11 +347,11 @@ struct VisibleLoad {
 // count, cleared row-span, list and tile-list counters, the chunks holding
 // binned surfels and the size of the (tile, chunk) table scan over them.
 struct BinCounts {
-  uint32_t *n_out, *n_rows, *n_band, *n_items, *n_chunks, *n_table;
+  uint32_t *n_out, *n_rows, *n_band, *n_items, *n_chunks, *n_table;  // n_rows may be null
   uint32_t chunk, ntiles;
   __device__ void set(uint32_t total) const {
     *n_out = total;
-    *n_rows = 0u;
+    if (n_rows) *n_rows = 0u;  // null: the spans are computed on another stream
     *n_band = 0u;
     *n_items = 0u;
     // at least one chunk, so that every tile's range is written
@@ -850,7 +861,7 @@ cudaError_t prepare_binning(int max_tiles_x) {
 
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
                            const uint8_t *tile_mask, cudaStream_t s, int order, const uint8_t *roi16, int W,
-                           int H, int tshift) {
+                           int H, int tshift, const SideRows *rows) {
   const BinScratch &b = ws.bin[eye];
   cudaError_t err;
   Counters *ctr = ws.ctr;
@@ -863,9 +874,28 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
              roi16 ? b.items16 : nullptr);
     GS_LAUNCHED(1);
   }
+  // the row spans need only the preprocessed records (and an ROI binning's mask
+  // tables): on a second stream they run beside the compaction and the sort, a
+  // small grid so that those latency-bound kernels keep their SMs
+  const bool side_rows = rows && n > 0;
+  if (side_rows) {
+    const bool reuse = order == kOrderReuse;  // the candidates: the kept dominant order, else every surfel
+    const int grid = sm_grid_cap(2) < (n + 255) / 256 ? sm_grid_cap(2) : (n + 255) / 256;
+    err = cudaEventRecord(rows->fork, s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(rows->stream, rows->fork, 0);
+    if (err == cudaSuccess) err = cudaMemsetAsync(&ctr->n_rows[eye], 0, sizeof(uint32_t), rows->stream);
+    if (err == cudaSuccess)
+      err = launch_k(rows_kernel, grid, 256, 0, rows->stream, reuse ? ws.uval : nullptr,
+                     reuse ? &ctr->n_union : nullptr, (uint32_t)n, ws.rec[eye], ws.rect[eye], ws.cnt[eye], ws.cams,
+                     eye, ws.prim, ws.row_off[eye], ws.spans[eye], cap, &ctr->n_rows[eye], &ctr->status,
+                     tile_mask ? b.mask_clip : nullptr, tiles_x, tiles_y, tile_mask ? b.mask_sat : nullptr);
+    GS_LAUNCHED(1);
+    if (err == cudaSuccess) err = cudaEventRecord(rows->join, rows->stream);
+    if (err != cudaSuccess) return err;
+  }
   const uint32_t chunk = kBinWarps * ws.bin_warp_surfels;
-  const BinCounts bc{&ctr->n_vis[eye], &ctr->n_rows[eye], &ctr->n_band[eye], &ctr->n_items[eye],
-                     &ctr->n_chunks[eye], &ctr->n_table[eye], chunk, (uint32_t)ntiles};
+  const BinCounts bc{&ctr->n_vis[eye], side_rows ? nullptr : &ctr->n_rows[eye], &ctr->n_band[eye],
+                     &ctr->n_items[eye], &ctr->n_chunks[eye], &ctr->n_table[eye], chunk, (uint32_t)ntiles};
   // 1. compact the binned surfels: (depth bits, surfel id)
   const uint32_t *sat = tile_mask ? b.mask_sat : nullptr;
   if (order == kOrderReuse) {  // the dominant order, filtered: already depth-ordered
@@ -881,11 +911,12 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
   if (err != cudaSuccess) return err;
   // 2. tile ranges of every rectangle row of those surfels (n_rows and n_band
   // were cleared by the compaction)
-  if (n > 0) {
+  if (n > 0 && !side_rows) {
     launch_k(rows_kernel, (n + 255) / 256, 256, 0, s, b.dval[0], &ctr->n_vis[eye], (uint32_t)n, ws.rec[eye],
                                                 ws.rect[eye], ws.cnt[eye], ws.cams, eye, ws.prim, ws.row_off[eye],
                                                 ws.spans[eye], cap, &ctr->n_rows[eye],
-                                                &ctr->status, tile_mask ? b.mask_clip : nullptr, tiles_x, tiles_y);
+                                                &ctr->status, tile_mask ? b.mask_clip : nullptr, tiles_x, tiles_y,
+                                                (const uint32_t *)nullptr);
     GS_LAUNCHED(1);
   }
   // 3. depth order (the low 32 bits of the packed key; stable, so ties keep id order)
@@ -902,6 +933,7 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
     GS_LAUNCHED(1);
   }
   const int nbands = (tiles_y + kBandRows - 1) / kBandRows;
+  if (side_rows && (err = cudaStreamWaitEvent(s, rows->join, 0)) != cudaSuccess) return err;
   // 4. per chunk: each warp's depth-ordered (surfel, band) lists
   BandArgs ba;
   ba.ids = b.dval[which];

@@ -42,6 +42,8 @@ struct gs_context {
   cudaEvent_t ev_fork, ev_edge, ev_strip;
   cudaEvent_t ev_net;    // learned repair on the second stream: the network is done
   cudaStream_t copy;    // gs_render_stereo_host: the dominant eye's copy to the host
+  cudaStream_t rows;    // the binnings' row spans beside their compaction and sort
+  cudaEvent_t ev_rfork, ev_rjoin;
   cudaEvent_t ev_hfork, ev_hjoin;
 };
 

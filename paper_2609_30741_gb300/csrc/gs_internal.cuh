@@ -205,9 +205,17 @@ enum BinOrder { kOrderOwn = 0, kOrderUnion = 1, kOrderReuse = 2 };
 // ROI mask on the 16-pixel grid from which the binning derives its own mask on
 // the rasterizer grid into tile_mask (then ws.bin[eye].rmask); null when
 // tile_mask is given directly (or no mask).
+// rows (optional): a second stream and two events on which the row spans are
+// computed beside the compaction and the depth sort (forked after the mask
+// tables, joined before the band lists); null: on s, after the compaction.
+struct SideRows {
+  cudaStream_t stream;
+  cudaEvent_t fork, join;
+};
 cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int tiles_y,
                            const uint8_t *tile_mask, cudaStream_t s, int order = kOrderOwn,
-                           const uint8_t *roi16 = nullptr, int W = 0, int H = 0, int tshift = 4);
+                           const uint8_t *roi16 = nullptr, int W = 0, int H = 0, int tshift = 4,
+                           const SideRows *rows = nullptr);
 // Chunk geometry of the binning for a surfel capacity, and the one-time
 // shared-memory opt-in of its kernel for the widest image.
 uint32_t bin_warp_surfels(int max_surfels);
