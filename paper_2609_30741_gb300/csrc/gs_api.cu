@@ -548,7 +548,8 @@ static cudaError_t raster_one(gs_context *ctx, const RasterFrame &f, const Raste
 }
 
 static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye, int W, int H, float3 bg,
-                                 float *rgb, float *depth, float *trans, bool stats, int slot, int order) {
+                                 float *rgb, float *depth, float *trans, bool stats, int slot, int order,
+                                 unsigned long long *winit = nullptr) {
   const Workspace &ws = ctx->ws;
   cudaStream_t s = ctx->stream;
   const int sh = raster_tshift(ctx->rc), ts = 1 << sh;
@@ -557,7 +558,9 @@ static gs_status render_eye_full(gs_context *ctx, const gs_scene *scene, int eye
   cudaError_t e = launch_binning(ws, eye, scene->n, tx, ty, nullptr, s, order, nullptr, 0, 0, 4, side_rows(ctx));
   if (e != cudaSuccess) return cuda_fail(e);
   mark(ctx, slot);
-  e = raster_one(ctx, raster_frame(ws, eye, W, H, sh, nullptr, bg, rgb, depth, trans, nullptr, stats));
+  RasterFrame f = raster_frame(ws, eye, W, H, sh, nullptr, bg, rgb, depth, trans, nullptr, stats);
+  f.winit = winit;  // the stereo call's warp buffer, cleared pixel by pixel
+  e = raster_one(ctx, f);
   mark(ctx, slot + 1);
   return cuda_status(e);
 }
@@ -857,8 +860,10 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
       if (e != cudaSuccess) return cuda_fail(e);
     }
     // Stage 1: dominant eye, RGB + depth proxy (+ the per-frame depth range)
+    // without a reused depth range the dominant eye's rasterizer also clears the
+    // warp buffer (the two eyes share the image size)
     st = render_eye_full(ctx, scene, 0, W, H, black, out->rgb_dom, out->depth_dom, out->trans_dom, true, 2,
-                         p.parallel ? kOrderUnion : kOrderOwn);
+                         p.parallel ? kOrderUnion : kOrderOwn, reuse ? nullptr : ws.warpbuf);
     if (st != GS_OK) return st;
     if (hc) {  // the dominant eye is final: copy it out beside Stages 2-4
       if ((e = cudaEventRecord(ctx->ev_hfork, ctx->stream)) == cudaSuccess)
@@ -876,7 +881,7 @@ static gs_status stereo_impl(gs_context *ctx, const gs_scene *scene, const gs_po
       if (e == cudaSuccess) e = launch_classify(ws, W, H, gap_thresh, r, out->rgb_dom, out->rgb_aff, ctx->stream);
     } else {
       e = launch_warp_classify(ws, W, H, gap_thresh, r, out->rgb_dom, out->depth_dom, out->trans_dom, out->rgb_aff,
-                               ctx->stream);
+                               ctx->stream, true);
     }
     if (e != cudaSuccess) return cuda_fail(e);
     if (r.repair_mode != 0) {  // the repair network's inputs, kept for gs_repair_features

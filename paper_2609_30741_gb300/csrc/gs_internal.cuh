@@ -285,6 +285,7 @@ struct RasterFrame {
   const uint32_t *n_items;  // device count of the listed tiles
   float *rgb, *depth, *trans;  // [3][H][W], [H][W] (or null), [H][W] (or null)
   uint8_t *cls;             // class map: written pixels get kClsRender, or null
+  unsigned long long *winit;  // warp buffer cleared (no sample) at every written pixel, or null
   Counters *ctr;            // depth range and pair counts of this frame
   float bg[3];
   int W, H, tiles_x, ntiles, tshift;
@@ -336,6 +337,8 @@ cudaError_t launch_ssim(const float *a, const float *b, int W, int H, int C, dou
 // next frame's depth_mode 2).
 cudaError_t launch_warp(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,
                         cudaStream_t s);
+// Value of an empty warp-buffer entry (no source pixel landed there).
+constexpr unsigned long long kNoSample = ~0ull;
 cudaError_t launch_edge_roi(const Workspace &ws, const gs_roi_params &roi, uint8_t *mask, bool assign,
                             cudaStream_t s);
 cudaError_t launch_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
@@ -345,9 +348,12 @@ cudaError_t launch_strip_composite(const Workspace &ws, int W, int H, const floa
                                    cudaStream_t s);
 cudaError_t launch_mask_minus(uint8_t *mask, const uint8_t *minus, int n, cudaStream_t s);
 // Warp, edge ROIs, hole classification and gap filling (writes rgb_aff and cls).
+// cleared = true: the dominant eye's rasterizer has cleared the warp buffer
+// (RasterFrame::winit), and the edge ROI assigns every tile of the ROI mask
+// instead of adding its strips to a cleared mask.
 cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
                                  const float *rgb_dom, const float *depth_dom, const float *trans_dom,
-                                 float *rgb_aff, cudaStream_t s);
+                                 float *rgb_aff, cudaStream_t s, bool cleared = false);
 // Connected centre holes -> ROI rectangles -> tile mask.
 cudaError_t launch_centre_rois(const Workspace &ws, int W, int H, int margin, cudaStream_t s);
 

@@ -294,6 +294,7 @@ __global__ void __launch_bounds__(TS * TS / PIX, (raster_min_blocks<TS, PIX>()))
       fr.rgb[2 * hw + p] = fmaf(T[q], fr.bg[2], C2[q]);
       if (fr.depth) fr.depth[p] = D[q];
       if (fr.trans) fr.trans[p] = T[q];
+      if (fr.winit) fr.winit[p] = kNoSample;
       if (fr.cls) fr.cls[p] |= (uint8_t)kClsRender;
       if (1.f - T[q] >= 0.5f) {
         // range of the alpha-normalised depth D / (1 - T) over pixels with coverage >= 0.5
@@ -516,6 +517,7 @@ RasterFrame raster_frame(const Workspace &ws, int eye, int W, int H, int tshift,
   f.depth = depth;
   f.trans = trans;
   f.cls = cls;
+  f.winit = nullptr;
   f.ctr = ws.ctr;
   f.bg[0] = bg.x;
   f.bg[1] = bg.y;

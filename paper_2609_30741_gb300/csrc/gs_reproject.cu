@@ -48,7 +48,6 @@ struct PixelWalk {
   }
 };
 
-constexpr unsigned long long kNoSample = ~0ull;
 constexpr uint32_t kInfBits = 0x7f800000u;
 
 __device__ __forceinline__ bool transfer(const CamBlock &cb, float x, float y, float d, bool surface, float &u,
@@ -397,6 +396,19 @@ __device__ __forceinline__ uint32_t cc_find(volatile uint32_t *par, uint32_t x) 
   return x;
 }
 
+// The root of entry x without writing: while every entry is being set to its
+// root, a halving walk could write a stale grandparent over an entry another
+// thread has just set to its root. Read only, every pointer read is the entry's
+// old parent or its root, both ancestors, so the walk ends at the root.
+__device__ __forceinline__ uint32_t cc_root(const volatile uint32_t *par, uint32_t x) {
+  for (int steps = 0; steps < kMaxUnionSteps; ++steps) {
+    const uint32_t p = par[x];
+    if (p == x) return x;
+    x = p;
+  }
+  return x;
+}
+
 // Links the roots of entries a and b (pix: their pixels) with a CAS on the root
 // with the larger pixel; bounded retries.
 __device__ void cc_unite(uint32_t *par, const uint32_t *pix, uint32_t a, uint32_t b, uint32_t *status) {
@@ -525,7 +537,7 @@ __global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__r
   // 1. union; 2. parents to roots
   cc_union_all(cls, labels, pix, par, n, W, &ctr->status);
   __syncthreads();
-  for (uint32_t k = tid; k < n; k += kCcThreads) par[k] = cc_find(par, k);
+  for (uint32_t k = tid; k < n; k += kCcThreads) par[k] = cc_root(par, k);
   __syncthreads();
   // 3. the roots' slots: par[root] = kCcRank | slot
   uint32_t *s_rootk = reinterpret_cast<uint32_t *>(s_box);  // the roots' list positions, until the boxes
@@ -654,16 +666,21 @@ static EdgeArgs edge_args(const Workspace &ws, const gs_roi_params &roi, uint8_t
 }
 
 static cudaError_t warp_launches(const Workspace &ws, int W, int H, const float *depth_dom, const float *trans_dom,
-                                 const gs_roi_params *roi, cudaStream_t s) {
+                                 const gs_roi_params *roi, cudaStream_t s, bool cleared = false) {
   const int64_t npix = (int64_t)W * H;
   const int tiles_x = (W + kTile - 1) / kTile, tiles_y = (H + kTile - 1) / kTile;
-  cudaError_t err = launch_k(warp_init_kernel, grid_for(npix), 256, 0, s, ws.warpbuf, npix, ws.tile_mask,
-                             tiles_x * tiles_y);
-  const EdgeArgs ea = roi ? edge_args(ws, *roi, ws.tile_mask, false) : EdgeArgs{};
+  cudaError_t err = cudaSuccess;
+  if (!cleared) {
+    err = launch_k(warp_init_kernel, grid_for(npix), 256, 0, s, ws.warpbuf, npix, ws.tile_mask, tiles_x * tiles_y);
+    GS_LAUNCHED(1);
+  }
+  // with the buffer cleared by the rasterizer the mask is not cleared: the edge
+  // ROI then writes every tile of it
+  const EdgeArgs ea = roi ? edge_args(ws, *roi, ws.tile_mask, cleared) : EdgeArgs{};
   if (err == cudaSuccess)
     err = launch_k(warp_scatter_kernel, grid_resident(warp_scatter_kernel, npix, g_occ_scatter), 256, 0, s, ws.cams,
                    depth_dom, trans_dom, ws.warpbuf, W, H, roi ? 1 : 0, ea);
-  GS_LAUNCHED(2);
+  GS_LAUNCHED(1);
   return err;
 }
 
@@ -696,9 +713,9 @@ cudaError_t launch_classify(const Workspace &ws, int W, int H, int gap_thresh, c
 
 cudaError_t launch_warp_classify(const Workspace &ws, int W, int H, int gap_thresh, const gs_roi_params &roi,
                                  const float *rgb_dom, const float *depth_dom, const float *trans_dom,
-                                 float *rgb_aff, cudaStream_t s) {
+                                 float *rgb_aff, cudaStream_t s, bool cleared) {
   // warp and edge ROIs in one kernel, then the classification
-  cudaError_t err = warp_launches(ws, W, H, depth_dom, trans_dom, &roi, s);
+  cudaError_t err = warp_launches(ws, W, H, depth_dom, trans_dom, &roi, s, cleared);
   if (err == cudaSuccess) err = launch_classify(ws, W, H, gap_thresh, roi, rgb_dom, rgb_aff, s);
   return err;
 }
