@@ -507,6 +507,34 @@ def test_centre_rois_of_random_class_maps(gs, orc, shape, density, pattern, seed
     print({"centre_px": int((cls & 4).astype(bool).sum()), "components": n})
 
 
+@pytest.mark.parametrize("shape,density,pattern,seed", [
+    ((512, 512), 0.0, 1, 4),       # discs and serpentine snakes: long union chains
+    ((600, 800), 0.03, 0, 2),      # > 4096 components
+    ((1024, 1024), 0.04, 0, 3),    # the long-list path (parents in global memory)
+])
+def test_centre_rois_are_the_same_on_every_repeat(gs, orc, shape, density, pattern, seed):
+    """The labelling is a one-CTA union-find whose threads link, halve and flatten
+    concurrently; its rectangles and tiles must not depend on their interleaving.
+    Forty repeats of one class map all equal the oracle's Step 2 (a flatten that
+    compressed paths while other threads set entries to their roots once sent a
+    rare pixel to a wrong box)."""
+    cls = _class_map(shape, density, pattern, seed)
+    H, W = shape
+    ref, n = orc.center_rois(cls, m=32, tile=16, cap=1 << 16)
+    want = np.zeros(((H + 15) // 16, (W + 15) // 16), np.uint8)
+    for x0, y0, x1, y1 in ref[:n]:
+        want[y0 // 16:(y1 - 1) // 16 + 1, x0 // 16:(x1 - 1) // 16 + 1] = 1
+    ctx = gs.Context(16, W, H, max_instances=1 << 12, max_rects=1 << 16)
+    c = torch.from_numpy(cls).cuda()
+    for it in range(40):
+        tm = torch.zeros((H + 15) // 16, (W + 15) // 16, dtype=torch.uint8, device="cuda")
+        rects, count = ctx.centre_rois(c, margin=32, tile_mask=tm)
+        assert ctx.check() == gs.GS_OK
+        assert int(count.item()) == n, it
+        assert np.array_equal(rects[:n].cpu().numpy(), ref[:n]), it
+        assert np.array_equal(tm.cpu().numpy(), want), it
+
+
 def test_roi_tiles_equal_the_full_affiliated_render(gs, stereo_small):
     """Per-tile blending is independent of other tiles, so the ROI re-render gives
     exactly the two-pass affiliated pixels on every ROI tile (same kernels)."""
