@@ -404,8 +404,9 @@ def run_ours(args):
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     # a profiler run keeps the device footprint small (its passes save and
     # restore device memory): 32-pixel tiles at most 2^25 instances per eye
+    ctx_min_tile = 16 if args.profile_once else 8
     ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << (25 if args.profile_once else 27),
-                     device=dev, min_tile=16 if args.profile_once else 8, host_outputs=True)
+                     device=dev, min_tile=ctx_min_tile, host_outputs=True)
     ds = gs.DeviceScene(scene, device=dev)
     out = ctx.alloc_outputs(cam)
     out2 = ctx.alloc_outputs(cam, with_cls=False)
@@ -438,6 +439,7 @@ def run_ours(args):
     else:
         ctx.set_raster(*rc["stereo"])
         cands = [None, (16, 2, 64), (16, 2, 128), (16, 4, 64), (16, 4, 128), (8, 2, 64), (32, 2, 64), (32, 2, 128)]
+        cands = [c for c in cands if c is None or c[0] >= ctx_min_tile]  # tiles the context can run
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(7)]
         for cand in cands:
             ctx.set_raster_roi(cand)
