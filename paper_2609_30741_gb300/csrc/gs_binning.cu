@@ -875,12 +875,15 @@ cudaError_t launch_binning(const Workspace &ws, int eye, int n, int tiles_x, int
     GS_LAUNCHED(1);
   }
   // the row spans need only the preprocessed records (and an ROI binning's mask
-  // tables): on a second stream they run beside the compaction and the sort, a
-  // small grid so that those latency-bound kernels keep their SMs
+  // tables): on a second stream they run beside the compaction and the sort.
+  // Beside a depth sort a small grid leaves those latency-bound kernels their
+  // SMs; beside the filter scan alone (the kept dominant order) the spans are
+  // the longer branch and take a fuller grid
   const bool side_rows = rows && n > 0;
   if (side_rows) {
     const bool reuse = order == kOrderReuse;  // the candidates: the kept dominant order, else every surfel
-    const int grid = sm_grid_cap(2) < (n + 255) / 256 ? sm_grid_cap(2) : (n + 255) / 256;
+    const int cap_g = sm_grid_cap(reuse ? 6 : 2);
+    const int grid = cap_g < (n + 255) / 256 ? cap_g : (n + 255) / 256;
     err = cudaEventRecord(rows->fork, s);
     if (err == cudaSuccess) err = cudaStreamWaitEvent(rows->stream, rows->fork, 0);
     if (err == cudaSuccess) err = cudaMemsetAsync(&ctr->n_rows[eye], 0, sizeof(uint32_t), rows->stream);
