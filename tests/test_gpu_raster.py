@@ -188,3 +188,39 @@ def test_roi_raster_config_is_bit_identical(gs, case):
                 assert bool(((ref["cls_aff"] & gs.CLS_NET) > 0).any())
     ctx.set_raster_roi(None)
     assert ctx.raster_roi() == (ctx.raster(), False)
+
+
+@pytest.mark.parametrize("repair", [0, 1])
+def test_frames_are_the_same_under_concurrent_load(gs, repair):
+    """Kernels of another stream sharing the SMs change every warp's timing, not
+    the frame: the toed-in stereo frame (its affiliated eye sorted by its own
+    depth keys, the learned repair beside the ROI binning when asked) rendered
+    while a second stream runs elementwise work equals the frame rendered alone,
+    bit for bit, every time."""
+    scene, cam, dom, aff = _case("toed_in")
+    ds = gs.DeviceScene(scene)
+    ctx = gs.Context(scene.n, cam.width, cam.height, max_instances=1 << 24, min_tile=8)
+    if repair:
+        from paper_2609_30741_gb300 import repair_train as T
+        w = T.init_weights(5, gate_bias=0.0)
+        w += np.random.default_rng(6).normal(0.0, 0.03, w.shape).astype(np.float32)
+        ctx.repair_load(w)
+    roi = gs.roi_params(repair_mode=repair, gate_tau=0.4)
+    ctx.set_raster(32, 2, 64)
+    out = ctx.alloc_outputs(cam)
+    for _ in range(3):
+        ctx.render_stereo(ds, dom, aff, cam, roi=roi, out=out)
+    torch.cuda.synchronize()
+    ref = {k: v.clone() for k, v in out.items()}
+    side = torch.cuda.Stream()
+    load = torch.randn(2048, 2048, device="cuda")
+    for it in range(30):
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(4):
+                load = torch.sin(load) * 1.0001
+        ctx.render_stereo(ds, dom, aff, cam, roi=roi, out=out)
+        torch.cuda.current_stream().wait_stream(side)
+        ctx.check_ok()
+        for k in ("rgb_dom", "rgb_aff", "cls_aff", "roi_count"):
+            assert torch.equal(ref[k], out[k]), (it, _mismatch(ref, out, k))
