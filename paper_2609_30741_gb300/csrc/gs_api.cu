@@ -520,11 +520,11 @@ static void mark(gs_context *ctx, int slot) {
 // compaction and depth sort (created on first use); null if they cannot be.
 static const SideRows *side_rows(gs_context *ctx) {
   static thread_local SideRows r;
-  if (!ctx->rows) {
-    cudaError_t e = cudaStreamCreateWithFlags(&ctx->rows, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_rfork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_rjoin, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
+  if (!ctx->rows || !ctx->ev_rfork || !ctx->ev_rjoin) {
+    cudaError_t e = ctx->rows ? cudaSuccess : cudaStreamCreateWithFlags(&ctx->rows, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !ctx->ev_rfork) e = cudaEventCreateWithFlags(&ctx->ev_rfork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !ctx->ev_rjoin) e = cudaEventCreateWithFlags(&ctx->ev_rjoin, cudaEventDisableTiming);
+    if (e != cudaSuccess) {  // the binnings then compute their spans in stream order
       cudaGetLastError();
       return nullptr;
     }
