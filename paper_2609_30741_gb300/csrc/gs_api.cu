@@ -711,21 +711,20 @@ gs_status gs_render_mono(gs_context *ctx, const gs_scene *scene, const gs_pose *
 
 // The second stream and events of depth_mode 2 (created on first use).
 static gs_status ensure_side(gs_context *ctx) {
-  if (ctx->side) return GS_OK;
-  cudaError_t e = cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_edge, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_strip, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_net, cudaEventDisableTiming);
+  // each object is created once; one that failed is retried on the next call
+  cudaError_t e = ctx->side ? cudaSuccess : cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ctx->ev_fork) e = cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->ev_edge) e = cudaEventCreateWithFlags(&ctx->ev_edge, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->ev_strip) e = cudaEventCreateWithFlags(&ctx->ev_strip, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->ev_net) e = cudaEventCreateWithFlags(&ctx->ev_net, cudaEventDisableTiming);
   return cuda_status(e);
 }
 
 // The copy stream and events of gs_render_stereo_host (created on first use).
 static gs_status ensure_copy(gs_context *ctx) {
-  if (ctx->copy) return GS_OK;
-  cudaError_t e = cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_hfork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ctx->ev_hjoin, cudaEventDisableTiming);
+  cudaError_t e = ctx->copy ? cudaSuccess : cudaStreamCreateWithFlags(&ctx->copy, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ctx->ev_hfork) e = cudaEventCreateWithFlags(&ctx->ev_hfork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ctx->ev_hjoin) e = cudaEventCreateWithFlags(&ctx->ev_hjoin, cudaEventDisableTiming);
   return cuda_status(e);
 }
 
