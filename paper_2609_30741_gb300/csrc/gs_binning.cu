@@ -607,7 +607,10 @@ __device__ __forceinline__ uint32_t half16(const uint4 &v, int w) {
   return (w & 1) ? x >> 16 : x & 0xffffu;
 }
 
-__global__ void __launch_bounds__(kBinThreads, 4) bin_kernel(BinArgs a, int mode) {
+// Six resident CTAs per SM (40 registers, no spills): the walk is bound by the
+// latency of its shuffles, gathers and shared-memory atomics, and the extra
+// warps cover it (four CTAs took 56 registers and measured slower).
+__global__ void __launch_bounds__(kBinThreads, 6) bin_kernel(BinArgs a, int mode) {
   griddep_wait();
   extern __shared__ uint32_t s_dyn[];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
