@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__r
                                                               Counters *ctr, uint32_t cap, int W, int H, int m,
                                                               int tiles_x, int tiles_y, uint8_t *__restrict__ tile_mask) {
   griddep_wait();
-  extern __shared__ uint32_t s_cc[];
+  extern __shared__ __align__(16) uint32_t s_cc[];
   __shared__ uint32_t s_scan[32];
   __shared__ uint32_t s_nr;
   const int tid = threadIdx.x;
@@ -556,11 +556,19 @@ __global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__r
   uint32_t *bits = reinterpret_cast<uint32_t *>(labels), *pre = bits + (npx + 31u) / 32u;  // labels[] is free now
   if (nr <= (uint32_t)kCcThreads) {
     // up to one root per thread: its slot is the number of roots with a smaller
-    // pixel (every thread of a warp reads the same root at a time)
+    // pixel. Every thread of a warp reads the same four roots at a time; the
+    // roots are padded to a multiple of four with a value above every pixel.
+    const uint32_t nr4 = (nr + 3u) & ~3u;
+    if ((uint32_t)tid >= nr && (uint32_t)tid < nr4) s_roots[tid] = 0xffffffffu;
+    __syncthreads();
     uint32_t sl = 0;
     if ((uint32_t)tid < nr) {
       const uint32_t mine = s_roots[tid];
-      for (uint32_t j = 0; j < nr; ++j) sl += s_roots[j] < mine ? 1u : 0u;
+      const uint4 *r4 = reinterpret_cast<const uint4 *>(s_roots);
+      for (uint32_t j = 0; j < nr4 / 4u; ++j) {
+        const uint4 v = r4[j];
+        sl += (uint32_t)(v.x < mine) + (uint32_t)(v.y < mine) + (uint32_t)(v.z < mine) + (uint32_t)(v.w < mine);
+      }
     }
     __syncthreads();
     if ((uint32_t)tid < nr) par[s_rootk[tid]] = kCcRank | sl;
@@ -611,18 +619,26 @@ __global__ void __launch_bounds__(kCcThreads) cc_label_kernel(const uint8_t *__r
     if (nr > cap) atomicOr(&ctr->status, kStCapacity);
   }
   __syncthreads();
-  // 4. bounding boxes
+  // 4. bounding boxes. Consecutive list entries at consecutive pixels of one
+  // row are one run of one component: only its first entry can lower the box's
+  // x and set its rows, only its last can raise its x.
   for (uint32_t k = tid; k < n; k += kCcThreads) {
+    const uint32_t p = pix[k];
+    const uint32_t ux = p % (uint32_t)W;
+    const bool first = k == 0u || ux == 0u || pix[k - 1] != p - 1u;
+    const bool last = k + 1u >= n || ux + 1u == (uint32_t)W || pix[k + 1] != p + 1u;
+    if (!first && !last) continue;
     const uint32_t r = par[k];
     const uint32_t sl = (r & kCcRank) ? (r & ~kCcRank) : (par[r] & ~kCcRank);
     if (sl >= nbox) continue;
-    const uint32_t p = pix[k];
-    const int x = (int)(p % (uint32_t)W), y = (int)(p / (uint32_t)W);
+    const int x = (int)ux, y = (int)(p / (uint32_t)W);
     int *q = reinterpret_cast<int *>(box + sl);
-    atomicMin(q + 0, x);
-    atomicMin(q + 1, y);
-    atomicMax(q + 2, x);
-    atomicMax(q + 3, y);
+    if (first) {
+      atomicMin(q + 0, x);
+      atomicMin(q + 1, y);
+      atomicMax(q + 3, y);
+    }
+    if (last) atomicMax(q + 2, x);
   }
   __syncthreads();
   // 5. rectangles and tiles
