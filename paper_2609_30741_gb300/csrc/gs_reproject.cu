@@ -462,10 +462,14 @@ __device__ __forceinline__ void cc_union_all(const uint8_t *__restrict__ cls, co
     const bool cont = k > 0u && p % uW != 0u && pix[k - 1] == p - 1u;
     const bool need_l = !cont && p % uW != 0u, hu = p >= uW;
     const uint8_t cl = need_l ? cls[p - 1] : 0, cu = hu ? cls[p - uW] : 0, cul = hu && cont ? cls[p - 1 - uW] : 0;
-    const uint32_t kl = need_l ? (uint32_t)labels[p - 1] : 0u, ku = hu ? (uint32_t)labels[p - uW] : 0u;
-    if (need_l && (cl & kClsCentre)) cc_unite(par, pix, k, kl, status);
+    const bool link_l = need_l && (cl & kClsCentre), link_u = (cu & kClsCentre) && !(cont && (cul & kClsCentre));
+    // list positions only of centre holes: the class map was just written and
+    // sits in L2, but labels[] is written at centre holes only, so reading it at
+    // any other pixel would wait on DRAM for a value that is never used
+    const uint32_t kl = link_l ? (uint32_t)labels[p - 1] : 0u, ku = link_u ? (uint32_t)labels[p - uW] : 0u;
+    if (link_l) cc_unite(par, pix, k, kl, status);
     if (cont && lane == 0u) cc_unite(par, pix, k, k - 1, status);
-    if ((cu & kClsCentre) && !(cont && (cul & kClsCentre))) cc_unite(par, pix, k, ku, status);
+    if (link_u) cc_unite(par, pix, k, ku, status);
   }
 }
 
