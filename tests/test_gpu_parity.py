@@ -457,12 +457,20 @@ def test_centre_rois_bit_exact_given_classes(case, request, orc):
 
 def _class_map(shape, density, pattern, seed):
     """A [H, W] class map: random non-centre bits everywhere, the centre bit (4) on
-    random pixels at `density`, or on blobs and long snakes (`pattern` 1)."""
+    random pixels at `density`, on blobs and long snakes (`pattern` 1), or on row
+    ends (`pattern` 2): runs that close one row and runs that open the next, so
+    that consecutive pixels of the centre-hole list cross a row boundary without
+    touching, and two full-width rows."""
     rng = np.random.default_rng(seed)
     H, W = shape
     cls = (rng.integers(0, 16, shape) & ~4).astype(np.uint8)
     centre = rng.random(shape) < density
-    if pattern:
+    if pattern == 2:
+        centre[4:6, :] = True
+        for y in range(10, H - 2, 3):
+            centre[y, W - 1 - y % 5:] = True
+            centre[y + 1, :1 + y % 7] = True
+    if pattern == 1:
         for _ in range(60):  # discs
             cy, cx, r = rng.integers(0, H), rng.integers(0, W), rng.integers(1, 12)
             yy, xx = np.ogrid[:H, :W]
@@ -483,6 +491,7 @@ def _class_map(shape, density, pattern, seed):
     ((1024, 1024), 0.04, 0, 3, 1 << 16),   # 42k centre pixels: the long-list path
     ((512, 512), 0.0, 1, 4, 1 << 16),      # discs and serpentine snakes
     ((333, 517), 0.01, 0, 5, 1 << 16),     # ragged size
+    ((97, 517), 0.0, 2, 8, 1 << 16),       # runs at row ends: list neighbours across rows
     ((600, 800), 0.03, 0, 6, 64),          # more components than rectangles
     ((1024, 1024), 0.04, 0, 7, 64),        # the same on the long-list path
 ])
